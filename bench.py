@@ -1,0 +1,331 @@
+"""Benchmark: structure-factor terms/s and patterns/s of the powder-XRD engine on GB300.
+
+Workload: the 1024-structure small-cell batch (P1 cells, edges 3-15 A, 1-64
+atoms, Cu K-alpha, 2-theta 0-90 deg), seeded and synthetic. One step = one
+pass of the whole pattern path (geometry, enumeration, structure factor + LP,
+sort, merge, families, cutoff, scaling, compaction) over the batch, inputs
+resident in HBM. L2 is flushed (256 MiB write) between timed steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs its own replica of the batch (weak
+scaling, no collective on the data path); value = all ranks' terms / max time.
+`--impl reference` times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "structure-factor terms/s and patterns/s at 1 GB300 (FP32 vs FP64) vs SFU roofline"
+WORKLOAD = ("small: 1024 seeded P1 cells, a,b,c U[3,15] A, angles U[60,120] deg, 1-64 atoms, Z U{1..83}, "
+            "B U[0,2] A^2, occ 1, lambda 1.54184 A, 2theta 0-90 deg")
+# SFU issue rates per SM per clock measured on this GB300 (MUFU.SIN/COS 16, MUFU.EX2 32) and the
+# maximum SM clock; the structure-factor roofline of a batch follows from its mix of operations.
+MUFU_SINCOS_PER_CLK = 16.0
+MUFU_EX2_PER_CLK = 32.0
+SM_MAX_MHZ = 2070.0
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_oracle_rate(b, o, budget_s=12.0, threads=0):
+    """Oracle (FP64, full sphere) on the host cores over a bounded sample of the batch."""
+    import oracle
+    cores = oracle.max_threads() if threads == 0 else threads
+    t0 = time.perf_counter()
+    done_struct = 0
+    terms = 0
+    counts = np.diff(b.atom_off)
+    chunk = 64
+    s = 0
+    while time.perf_counter() - t0 < budget_s:
+        idx = np.arange(s, min(s + chunk, b.n_struct))
+        if len(idx) == 0:
+            s = 0
+            continue
+        sub = b.subset(idx)
+        res = oracle.pattern_batch(sub, o, threads=threads)
+        terms += int((res["n_refl"] * counts[idx]).sum())
+        done_struct += len(idx)
+        s += chunk
+    dt = time.perf_counter() - t0
+    return {"terms_per_s": terms / dt, "patterns_per_s": done_struct / dt, "cores": cores, "seconds": dt,
+            "structures": done_struct}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2602_11709_gb300 import synth
+    b, o = synth.small()
+    steps = []
+    per_step_budget = max(2.0, min(20.0, 100.0 / max(args.steps + args.warmup, 1)))
+    for i in range(args.warmup + args.steps):
+        r = cpu_oracle_rate(b, o, budget_s=per_step_budget)
+        if i >= args.warmup:
+            steps.append(r)
+    tps = float(np.mean([r["terms_per_s"] for r in steps]))
+    pps = float(np.mean([r["patterns_per_s"] for r in steps]))
+    line = {"impl": "reference", "metric": METRIC, "value": tps, "unit": "terms/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * b.n_struct / pps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_struct": b.n_struct, "precision": "oracle fp64"},
+            "patterns_per_s": pps,
+            "cpu_baseline": {"value": tps, "unit": "terms/s", "cores": steps[0]["cores"], "kind": "oracle",
+                             "sample": "consecutive 64-structure chunks of the batch, %.0f s per step" % per_step_budget},
+            "e2e": {"value": tps, "unit": "terms/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    from paper_2602_11709_gb300 import synth, xrd
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = local if torch.cuda.is_available() else 0
+    torch.cuda.set_device(dev)
+    b, o = synth.small()
+    h = xrd.Handle(dev)
+    db = xrd.DeviceBatch.from_host(b, "cuda:%d" % dev)
+    co = xrd.make_opts(o, args.precision)
+    sz = h.query_sizes(db, co)
+    out = xrd.PatternBuffers(b.n_struct, sz.n_refl, "cuda:%d" % dev)
+    ws = xrd.workspace(sz.ws_bytes, "cuda:%d" % dev)
+    counts = np.diff(b.atom_off).astype(np.int64)
+    species = np.array([len(np.unique(b.Z[b.atom_off[s]:b.atom_off[s + 1]])) for s in range(b.n_struct)])
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda:%d" % dev)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # Friedel-unique reflections per structure: half the multiplicity sum of the uncut pattern
+    half = np.zeros(b.n_struct, np.int64)
+    co0 = xrd.make_opts(synth.Opts(o.wavelength, o.tt_min, o.tt_max, o.tt_tol, 0.0, 0), args.precision)
+    out0 = xrd.PatternBuffers(b.n_struct, sz.n_refl, "cuda:%d" % dev)
+    h.pattern_batch(db, co0, out0, ws)
+    torch.cuda.synchronize()
+    po = out0.peak_off.cpu().numpy()
+    fo = out0.fam_off.cpu().numpy()
+    mult = out0.mult[: int(out0.totals[2])].cpu().numpy().astype(np.int64)
+    cm = np.concatenate([[0], np.cumsum(mult)])
+    for s in range(b.n_struct):
+        half[s] = (cm[fo[po[s + 1]]] - cm[fo[po[s]]]) // 2 if po[s + 1] > po[s] else 0
+    assert int(half.sum()) == int(sz.n_refl)
+    terms_full = int((2 * half * counts).sum())
+    terms_eval = int((half * counts).sum())
+    sfu_cycles = float((half * (counts * (2.0 / MUFU_SINCOS_PER_CLK + 1.0 / MUFU_EX2_PER_CLK) +
+                                species * (4.0 / MUFU_EX2_PER_CLK))).sum())
+
+    h.set_profiling(True)
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        h.pattern_batch(db, co, out, ws)
+    barrier()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    sf_ms = []
+    stage_acc = {}
+    barrier()
+    for i in range(args.steps):
+        flush.fill_(1.0)
+        ev[i][0].record(stream)
+        h.pattern_batch(db, co, out, ws)
+        ev[i][1].record(stream)
+        st = h.stage_times()  # synchronises on the step's last event
+        sf_ms.append(st["structure_factor"])
+        for k, v in st.items():
+            stage_acc[k] = stage_acc.get(k, 0.0) + v
+    barrier()
+    ck = clocks.stop()
+    step_ms = [a.elapsed_time(c) for a, c in ev]
+    total_s = sum(step_ms) / 1e3
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_s], dtype=torch.float64, device="cuda:%d" % dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = terms_full * args.steps * world / total_s
+    pps = b.n_struct * args.steps * world / total_s
+    sf_avg = float(np.mean(sf_ms)) / 1e3
+    sfu_floor_s = sfu_cycles / (152.0 * SM_MAX_MHZ * 1e6)
+    peak_gterms = terms_eval / sfu_floor_s / 1e9
+    achieved_gterms = terms_eval / sf_avg / 1e9
+
+    # FP64 GPU path on the same batch (a few steps), for the FP32-vs-FP64 comparison
+    extra = {}
+    if args.fp64_steps > 0:
+        for pname in ("fp64", "fp32_phase64"):
+            cp = xrd.make_opts(o, pname)
+            h.pattern_batch(db, cp, out, ws)
+            torch.cuda.synchronize()
+            tt = []
+            for _ in range(args.fp64_steps):
+                flush.fill_(1.0)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                h.pattern_batch(db, cp, out, ws)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                tt.append(e0.elapsed_time(e1))
+            ms = float(np.mean(tt))
+            extra[pname] = {"ms_per_step": ms, "terms_per_s": terms_full / (ms / 1e3)}
+
+    # end to end through the public API: pinned host inputs -> device -> pattern -> host results
+    host = {k: torch.from_numpy(np.ascontiguousarray(getattr(b, k))).pin_memory()
+            for k in ("lattice", "atom_off", "frac", "Z", "occ", "B", "coef")}
+    e2e_ms = []
+    h2d = sum(t.numel() * t.element_size() for t in host.values())
+    d2h = 0
+    h.set_profiling(False)
+    res_host = {}
+    for i in range(args.warmup + args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k, t in host.items():
+            getattr(db, k).copy_(t, non_blocking=True)
+        h.pattern_batch(db, co, out, ws)
+        tot = out.totals.cpu()
+        npk, nfm = int(tot[1]), int(tot[2])
+        outs = [out.peak_off.cpu(), out.two_theta[:npk].cpu(), out.intensity[:npk].cpu(), out.d_hkl[:npk].cpu(),
+                out.fam_off[:npk + 1].cpu(), out.hkl[:nfm].cpu(), out.mult[:nfm].cpu(), out.status.cpu()]
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        if i >= args.warmup:
+            e2e_ms.append((t1 - t0) * 1e3)
+            d2h = sum(x.numel() * x.element_size() for x in outs) + tot.numel() * 8
+    e2e_s = float(np.mean(e2e_ms)) / 1e3
+
+    if rank == 0:
+        cpu = None
+        if world == 1 and args.cpu_seconds > 0:
+            r = cpu_oracle_rate(b, o, budget_s=args.cpu_seconds)
+            cpu = {"value": r["terms_per_s"], "unit": "terms/s", "cores": r["cores"], "kind": "oracle",
+                   "sample": "%d structures of the batch (consecutive 64-structure chunks), %.1f s" %
+                             (r["structures"], r["seconds"]),
+                   "patterns_per_s": r["patterns_per_s"]}
+        line = {
+            "metric": METRIC, "value": value, "unit": "terms/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (i32 phase)" if args.precision == "fp32_phasefix"
+            else args.precision, "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_struct": b.n_struct, "precision": args.precision,
+                       "terms_full_sphere": terms_full, "terms_evaluated": terms_eval,
+                       "reflections_friedel_unique": int(sz.n_refl), "l2": "flushed between steps (256 MiB write)",
+                       "parallelism": "replica per GPU" if world > 1 else "1 GPU"},
+            "patterns_per_s": pps,
+            "roofline": {"bound": "alu", "unit": "Gterm/s", "achieved": achieved_gterms, "peak": peak_gterms,
+                         "frac": achieved_gterms / peak_gterms, "traffic": None,
+                         "kernel": "k_sf", "peak_basis": "SFU: sin+cos at 16/clk/SM, exp2 at 32/clk/SM, "
+                                                         "152 SMs, 2070 MHz; Friedel-unique terms"},
+            "cpu_baseline": cpu,
+            "e2e": {"value": terms_full / e2e_s, "unit": "terms/s", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_s * 1e3},
+            "clocks": ck,
+            "gpu_launches": 10 * args.steps,
+            "stage_ms": {k: v / args.steps for k, v in stage_acc.items()},
+            "other_precisions": extra,
+        }
+        if "fp64" in extra:
+            line["speedup_vs_fp64_gpu"] = extra["fp64"]["ms_per_step"] / (1e3 * total_s / args.steps)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32_phasefix", choices=["fp64", "fp32_phase64", "fp32_phasefix"])
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,145 @@
+/*
+ * xrd.h -- C ABI of the GB300 powder X-ray diffraction pattern engine.
+ *
+ * The library computes, for a batch of crystal structures, the powder
+ * diffraction pattern of each one: the steps of the numerical core listed in
+ * Sec. 2 of arXiv 2602.11709 (reciprocal-lattice points inside the accessible
+ * sphere, structure-factor sums over atoms, Lorentz-polarisation and
+ * Debye-Waller factors, merging of reflections within an angular tolerance,
+ * grouping of equivalent reflections into hkl families), followed by the
+ * optional intensity cutoff (Sec. 2) and the 0-100 scaling used in Sec. 3.
+ *
+ * Conventions for every entry point:
+ *  - Plain C types only. Pointers marked "device" must point to memory of the
+ *    handle's CUDA device (cudaMalloc, torch CUDA tensors, managed memory);
+ *    pointers marked "host" to host memory.
+ *  - Every buffer is owned by the caller. xrd_pattern_batch allocates no
+ *    memory: its scratch space is the caller's workspace.
+ *  - Work is queued on the caller's stream and is asynchronous; outputs are
+ *    valid after the stream has been synchronised. Calls on one handle must
+ *    not run concurrently from several host threads.
+ *  - Return value: XRD_OK or an error code. On error xrd_last_error() gives a
+ *    one-line message. Data-dependent errors found on the device (an invalid
+ *    cell, an atom with Z > zmax, a non-finite value, too little capacity) are
+ *    reported per structure in xrd_pattern.status and summed in
+ *    xrd_pattern.totals[3]; they never abort and never trap on the device.
+ */
+#ifndef XRD_H
+#define XRD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define XRD_OK 0
+#define XRD_EINVAL 1    /* invalid argument, pointer, size or input value */
+#define XRD_ECAPACITY 2 /* workspace or output capacity too small */
+#define XRD_ECUDA 3     /* a CUDA call failed; see xrd_last_error */
+#define XRD_ETIMEOUT 4  /* a bounded device-side wait ran out */
+
+/* Precision of the structure-factor sum (Sec. 2, "structure-factor evaluation"). */
+#define XRD_FP64 0          /* every step in FP64 */
+#define XRD_FP32_PHASE64 1  /* phase h.x+k.y+l.z formed and reduced mod 1 in FP64, the rest in FP32 */
+#define XRD_FP32_PHASEFIX 2 /* coordinates in 32-bit fixed point, phase reduced mod 1 exactly in integers, the rest in FP32 */
+
+typedef struct xrd_handle xrd_handle;
+
+/* Batch of structures; every pointer is device memory, layouts are row-major. */
+typedef struct {
+    int32_t n_struct;        /* number of structures, >= 0 */
+    int32_t zmax;            /* largest element number in coef, 0..255 */
+    int64_t n_atoms;         /* total atoms = atom_off[n_struct] */
+    const double* lattice;   /* [n_struct][6]: a, b, c (angstrom), alpha, beta, gamma (degrees) */
+    const int64_t* atom_off; /* [n_struct + 1]: atoms of structure s are atom_off[s] .. atom_off[s+1]-1 */
+    const double* frac;      /* [n_atoms][3]: fractional coordinates x, y, z */
+    const int16_t* Z;        /* [n_atoms]: element number, 0..zmax */
+    const double* occ;       /* [n_atoms]: site occupancy */
+    const double* B;         /* [n_atoms]: isotropic displacement (Debye-Waller) factor, angstrom^2 */
+    const double* coef;      /* [zmax + 1][4][2]: (a_i, b_i) of f(s) = Z - 41.78214 s^2 sum a_i exp(-b_i s^2) */
+} xrd_batch;
+
+/* Options (host struct). */
+typedef struct {
+    double lambda;     /* wavelength, angstrom, > 0 */
+    double tt_min;     /* 2-theta range in degrees, 0 <= tt_min < tt_max <= 180, both inclusive */
+    double tt_max;
+    double tt_tol;     /* merge tolerance in degrees (>= 0): join the peak while 2theta - anchor < tt_tol */
+    double rel_cutoff; /* keep merged peaks with I > rel_cutoff * Imax; 0 keeps all; [0, 1) */
+    int32_t scaled;    /* 1: scale intensities to 100 * (I / Imax); 0: absolute */
+    int32_t precision; /* XRD_FP64, XRD_FP32_PHASE64 or XRD_FP32_PHASEFIX */
+    int32_t tile;      /* structure-factor tile override: reflections per CTA, or -1 for the tuned value */
+    int32_t reserved;  /* must be 0 */
+} xrd_opts;
+
+/* Sizes returned by xrd_query_sizes. */
+typedef struct {
+    int64_t n_refl;   /* Friedel-unique reflections of the whole batch (each stands for g and -g) */
+    int64_t max_refl; /* largest Friedel-unique count of one structure */
+    int64_t n_tiles;  /* structure-factor tiles at the tuned tile size */
+    size_t ws_bytes;  /* workspace bytes xrd_pattern_batch needs for this batch and these options */
+} xrd_sizes;
+
+/* Pattern output: device buffers owned by the caller. Peaks and families are
+ * dense CSR arrays over the batch, in structure order; within a structure
+ * peaks ascend in 2-theta. A capacity of n_refl (from xrd_query_sizes) is
+ * always enough for both peaks and families. */
+typedef struct {
+    int64_t cap_peaks;  /* capacity of the per-peak arrays */
+    int64_t cap_fam;    /* capacity of the per-family arrays */
+    int64_t* peak_off;  /* [n_struct + 1]: peaks of structure s are peak_off[s] .. peak_off[s+1]-1 */
+    double* two_theta;  /* [cap_peaks]: peak position, degrees (2-theta of the peak's first reflection) */
+    double* intensity;  /* [cap_peaks]: merged intensity (scaled to 100 if opts.scaled) */
+    double* d_hkl;      /* [cap_peaks]: d spacing of the peak's first reflection, angstrom */
+    int64_t* fam_off;   /* [cap_peaks + 1]: families of global peak p are fam_off[p] .. fam_off[p+1]-1 */
+    int32_t* hkl;       /* [cap_fam][3]: family representative (lexicographically largest member) */
+    int32_t* mult;      /* [cap_fam]: family multiplicity (members over the full sphere) */
+    int32_t* status;    /* [n_struct]: XRD_OK, XRD_EINVAL (bad cell or atom) or XRD_ECAPACITY */
+    int64_t* totals;    /* [4]: reflections (Friedel-unique), peaks, families, structures with an error */
+} xrd_pattern;
+
+/* Create a handle bound to CUDA device `device`. Returns XRD_OK or XRD_ECUDA/XRD_EINVAL. */
+int xrd_create(xrd_handle** h, int device);
+/* Destroy a handle (NULL is ignored). */
+void xrd_destroy(xrd_handle* h);
+/* Message of the last error on this handle ("" if none); valid until the next call. */
+const char* xrd_last_error(const xrd_handle* h);
+
+/*
+ * Count the reflections of a batch (Sec. 2, "generation of reciprocal lattice
+ * points within the physically accessible sphere") and size the workspace.
+ * Runs the enumeration count on `stream` and synchronises it. May allocate
+ * device memory owned by the handle (never on the hot path). Per-structure
+ * input errors are not reported here; xrd_pattern_batch reports them.
+ */
+int xrd_query_sizes(xrd_handle* h, const xrd_batch* batch, const xrd_opts* opts, xrd_sizes* sizes,
+                    void* stream /* cudaStream_t */);
+
+/*
+ * The whole pattern of every structure (Sec. 2 steps, then Sec. 2's optional
+ * cutoff and Sec. 3's 0-100 scale): enumerate the Friedel-unique reflections
+ * with r_min <= |g| <= r_max, evaluate F(g) = sum_j occ_j f_j(s)
+ * exp(-B_j s^2) exp(2 pi i g.x_j) and I = |F|^2 LP, sort by 2-theta, merge
+ * reflections within tt_tol of a peak's first reflection, group them into
+ * families equal up to permutation and sign of (h, k, l), apply the cutoff
+ * and scale. `workspace` is device memory of at least sizes.ws_bytes (from
+ * xrd_query_sizes with the same batch and options), 256-byte aligned. No
+ * allocation, no host synchronisation: the call can be captured in a CUDA
+ * graph. Errors found on the device are reported in out->status/out->totals.
+ */
+int xrd_pattern_batch(xrd_handle* h, const xrd_batch* batch, const xrd_opts* opts, const xrd_pattern* out,
+                      void* workspace, size_t ws_bytes, void* stream /* cudaStream_t */);
+
+/* Stage timing: when enabled, xrd_pattern_batch records CUDA events around
+ * each kernel on its stream; xrd_stage_times synchronises on the last event
+ * and writes up to n stage durations in milliseconds (order: prep, atoms,
+ * count, scan, emit, structure factor, post, compact) and returns the count. */
+int xrd_set_profiling(xrd_handle* h, int enabled);
+int xrd_stage_times(xrd_handle* h, float* ms, int n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* XRD_H */

@@ -214,7 +214,7 @@ int orc_pattern(const double lat[6], long n, const double* frac, const int16_t* 
     for (long j = 0; j < n; j++) {
         if (Z[j] < 0 || Z[j] > zmax) return 1;
         if (!isfinite(frac[3 * j]) || !isfinite(frac[3 * j + 1]) || !isfinite(frac[3 * j + 2])) return 1;
-        if (!isfinite(occ[j]) || !isfinite(B[j])) return 1;
+        if (!isfinite(occ[j]) || occ[j] < 0.0 || !isfinite(B[j])) return 1;
     }
     double Gs[6];
     if (orc_metric(lat, NULL, Gs, NULL) != 0) return 1;

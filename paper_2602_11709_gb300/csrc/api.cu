@@ -1,0 +1,417 @@
+// C ABI of the powder-XRD engine: handles, argument validation, workspace
+// layout and the launch sequence of one pattern batch.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "xrd_launch.h"
+
+struct xrd_handle {
+    int device = 0;
+    int sms = 0;
+    std::string err;
+    bool profiling = false;
+    bool recorded = false;
+    cudaEvent_t ev[9] = {};
+    void* qbuf = nullptr;  // query scratch owned by the handle
+    size_t qbuf_bytes = 0;
+};
+
+namespace {
+
+constexpr int kTile = 128;      // reflections per structure-factor CTA
+constexpr int kPostCap = 2048;  // reflections per structure kept in shared memory by k_post
+constexpr int kStages = 8;
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+int fail(xrd_handle* h, int code, const std::string& msg)
+{
+    if (h) h->err = msg;
+    return code;
+}
+
+int cuda_fail(xrd_handle* h, cudaError_t e, const char* where)
+{
+    return fail(h, XRD_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+size_t al(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Byte offsets of every array in the caller's workspace.
+struct Layout {
+    size_t geo, refl_cnt, refl_off, tile_off, npk, nfm, fam_soff, flags, coef32, atom32, atom64;
+    size_t q, key, I, g_tt, g_perm, g_bkt, g_flag, g_pstart, g_psum, g_fcnt;
+    size_t st_tt, st_I, st_d, st_foff, st_hkl, st_mult;
+    size_t total;
+};
+
+Layout layout(int64_t n, int64_t natoms, int zmax, int64_t R)
+{
+    Layout L{};
+    size_t o = 0;
+    auto take = [&](size_t bytes) { const size_t at = o; o += al(bytes); return at; };
+    L.geo = take(sizeof(xrd::Geo) * n);
+    L.refl_cnt = take(8 * n);
+    L.refl_off = take(8 * (n + 1));
+    L.tile_off = take(4 * (n + 1));
+    L.npk = take(8 * n);
+    L.nfm = take(8 * n);
+    L.fam_soff = take(8 * (n + 1));
+    L.flags = take(16);
+    L.coef32 = take(sizeof(xrd::Coef32) * (zmax + 1));
+    L.atom32 = take(sizeof(xrd::Atom32) * natoms);
+    L.atom64 = take(sizeof(xrd::Atom64) * natoms);
+    L.q = take(8 * R);
+    L.key = take(4 * R);
+    L.I = take(8 * R);
+    L.g_tt = take(8 * R);
+    L.g_perm = take(4 * R);
+    L.g_bkt = take(4 * (R + n));
+    L.g_flag = take(R);
+    L.g_pstart = take(4 * R);
+    L.g_psum = take(8 * R);
+    L.g_fcnt = take(4 * R);
+    L.st_tt = take(8 * R);
+    L.st_I = take(8 * R);
+    L.st_d = take(8 * R);
+    L.st_foff = take(4 * R);
+    L.st_hkl = take(12 * R);
+    L.st_mult = take(4 * R);
+    L.total = o;
+    return L;
+}
+
+// Largest reflection capacity whose layout fits in ws_bytes.
+int64_t refl_capacity(int64_t n, int64_t natoms, int zmax, size_t ws_bytes)
+{
+    const size_t fixed = layout(n, natoms, zmax, 0).total;
+    if (ws_bytes < fixed) return -1;
+    // layout(R).total grows with R: binary search for the largest R that fits
+    int64_t lo = 0, hi = (int64_t)((ws_bytes - fixed) / 64) + 1;
+    while (hi - lo > 1) {
+        const int64_t mid = lo + (hi - lo) / 2;
+        if (layout(n, natoms, zmax, mid).total <= ws_bytes) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+int check_opts(xrd_handle* h, const xrd_opts* o)
+{
+    if (!o) return fail(h, XRD_EINVAL, "opts is NULL");
+    if (!(o->lambda > 0.0) || !std::isfinite(o->lambda)) return fail(h, XRD_EINVAL, "lambda must be finite and > 0");
+    if (!(o->tt_min >= 0.0 && o->tt_min < o->tt_max && o->tt_max <= 180.0))
+        return fail(h, XRD_EINVAL, "need 0 <= tt_min < tt_max <= 180");
+    if (!(o->tt_tol >= 0.0) || !std::isfinite(o->tt_tol)) return fail(h, XRD_EINVAL, "tt_tol must be finite and >= 0");
+    if (!(o->rel_cutoff >= 0.0 && o->rel_cutoff < 1.0)) return fail(h, XRD_EINVAL, "rel_cutoff must be in [0, 1)");
+    if (o->scaled != 0 && o->scaled != 1) return fail(h, XRD_EINVAL, "scaled must be 0 or 1");
+    if (o->precision < XRD_FP64 || o->precision > XRD_FP32_PHASEFIX) return fail(h, XRD_EINVAL, "unknown precision");
+    if (o->tile != -1 && o->tile != kTile) return fail(h, XRD_EINVAL, "tile must be -1 or 128");
+    if (o->reserved != 0) return fail(h, XRD_EINVAL, "reserved must be 0");
+    return XRD_OK;
+}
+
+int check_batch(xrd_handle* h, const xrd_batch* b)
+{
+    if (!b) return fail(h, XRD_EINVAL, "batch is NULL");
+    if (b->n_struct < 0) return fail(h, XRD_EINVAL, "n_struct < 0");
+    if (b->n_atoms < 0) return fail(h, XRD_EINVAL, "n_atoms < 0");
+    if (b->zmax < 0 || b->zmax > xrd::kZmaxLimit) return fail(h, XRD_EINVAL, "zmax must be in 0..255");
+    if (b->n_struct > 0 && (!b->lattice || !b->atom_off)) return fail(h, XRD_EINVAL, "lattice/atom_off is NULL");
+    if (!b->coef) return fail(h, XRD_EINVAL, "coef is NULL");
+    if (b->n_atoms > 0 && (!b->frac || !b->Z || !b->occ || !b->B)) return fail(h, XRD_EINVAL, "atom array is NULL");
+    return XRD_OK;
+}
+
+// sphere radii from the 2-theta range (Bragg's law), on the host in FP64
+void radii(const xrd_opts* o, double& r2min, double& r2max, double& rmax)
+{
+    const double tmin = 2.0 * std::sin(o->tt_min * (xrd::kPi / 360.0)) / o->lambda;
+    const double tmax = 2.0 * std::sin(o->tt_max * (xrd::kPi / 360.0)) / o->lambda;
+    r2min = tmin * tmin;
+    r2max = tmax * tmax;
+    rmax = std::sqrt(r2max);
+}
+
+xrd::GeomArgs geom_args(const xrd_batch* b, const xrd_opts* o, const Layout& L, char* ws, int64_t cap_refl,
+                        int64_t* totals, int32_t* status)
+{
+    xrd::GeomArgs g{};
+    g.n_struct = b->n_struct;
+    g.zmax = b->zmax;
+    g.n_atoms = b->n_atoms;
+    g.tile = kTile;
+    radii(o, g.r2min, g.r2max, g.rmax);
+    g.cap_refl = cap_refl;
+    g.lattice = b->lattice;
+    g.atom_off = b->atom_off;
+    g.frac = b->frac;
+    g.Z = b->Z;
+    g.occ = b->occ;
+    g.B = b->B;
+    g.coef = b->coef;
+    g.geo = (xrd::Geo*)(ws + L.geo);
+    g.coef32 = (xrd::Coef32*)(ws + L.coef32);
+    g.atom32 = (xrd::Atom32*)(ws + L.atom32);
+    g.atom64 = (xrd::Atom64*)(ws + L.atom64);
+    g.refl_cnt = (int64_t*)(ws + L.refl_cnt);
+    g.refl_off = (int64_t*)(ws + L.refl_off);
+    g.tile_off = (int*)(ws + L.tile_off);
+    g.abort_flag = (int*)(ws + L.flags);
+    g.totals = totals;
+    g.status = status;
+    g.q = (double*)(ws + L.q);
+    g.key = (uint32_t*)(ws + L.key);
+    return g;
+}
+
+}  // namespace
+
+extern "C" {
+
+int xrd_create(xrd_handle** h, int device)
+{
+    if (!h) return XRD_EINVAL;
+    *h = nullptr;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess) return XRD_ECUDA;
+    if (device < 0 || device >= ndev) return XRD_EINVAL;
+    xrd_handle* p = new xrd_handle();
+    p->device = device;
+    DeviceGuard g(device);
+    e = cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, device);
+    if (e != cudaSuccess) { delete p; return XRD_ECUDA; }
+    for (int i = 0; i < kStages + 1; i++) {
+        e = cudaEventCreate(&p->ev[i]);
+        if (e != cudaSuccess) { delete p; return XRD_ECUDA; }
+    }
+    *h = p;
+    return XRD_OK;
+}
+
+void xrd_destroy(xrd_handle* h)
+{
+    if (!h) return;
+    DeviceGuard g(h->device);
+    for (int i = 0; i < kStages + 1; i++)
+        if (h->ev[i]) cudaEventDestroy(h->ev[i]);
+    if (h->qbuf) cudaFree(h->qbuf);
+    delete h;
+}
+
+const char* xrd_last_error(const xrd_handle* h) { return h ? h->err.c_str() : "NULL handle"; }
+
+int xrd_set_profiling(xrd_handle* h, int enabled)
+{
+    if (!h) return XRD_EINVAL;
+    h->profiling = enabled != 0;
+    return XRD_OK;
+}
+
+int xrd_stage_times(xrd_handle* h, float* ms, int n)
+{
+    if (!h || (!ms && n > 0)) return -XRD_EINVAL;
+    if (!h->recorded) return 0;
+    DeviceGuard g(h->device);
+    cudaError_t e = cudaEventSynchronize(h->ev[kStages]);
+    if (e != cudaSuccess) return -cuda_fail(h, e, "xrd_stage_times");
+    const int m = n < kStages ? n : kStages;
+    for (int i = 0; i < m; i++) {
+        e = cudaEventElapsedTime(&ms[i], h->ev[i], h->ev[i + 1]);
+        if (e != cudaSuccess) return -cuda_fail(h, e, "xrd_stage_times");
+    }
+    return m;
+}
+
+int xrd_query_sizes(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, xrd_sizes* sizes, void* stream)
+{
+    if (!h) return XRD_EINVAL;
+    h->err.clear();
+    int rc = check_batch(h, b);
+    if (rc) return rc;
+    if ((rc = check_opts(h, o))) return rc;
+    if (!sizes) return fail(h, XRD_EINVAL, "sizes is NULL");
+    DeviceGuard g(h->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t n = b->n_struct;
+    memset(sizes, 0, sizeof(*sizes));
+    if (n == 0) {
+        sizes->ws_bytes = layout(0, b->n_atoms, b->zmax, 0).total;
+        return XRD_OK;
+    }
+    const size_t need = al(sizeof(xrd::Geo) * n) + al(8 * n);
+    if (h->qbuf_bytes < need) {
+        if (h->qbuf) cudaFree(h->qbuf);
+        h->qbuf = nullptr;
+        h->qbuf_bytes = 0;
+        cudaError_t e = cudaMalloc(&h->qbuf, need);
+        if (e != cudaSuccess) return cuda_fail(h, e, "xrd_query_sizes: cudaMalloc");
+        h->qbuf_bytes = need;
+    }
+    Layout L{};
+    L.geo = 0;
+    L.refl_cnt = al(sizeof(xrd::Geo) * n);
+    xrd::GeomArgs a{};
+    a.n_struct = (int)n;
+    radii(o, a.r2min, a.r2max, a.rmax);
+    a.lattice = b->lattice;
+    a.geo = (xrd::Geo*)((char*)h->qbuf + L.geo);
+    a.refl_cnt = (int64_t*)((char*)h->qbuf + L.refl_cnt);
+    xrd::launch_count_only(a, st);
+    std::vector<int64_t> cnt(n);
+    cudaError_t e = cudaMemcpyAsync(cnt.data(), a.refl_cnt, 8 * n, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "xrd_query_sizes");
+    int64_t tot = 0, mx = 0, tiles = 0;
+    for (int64_t c : cnt) {
+        tot += c;
+        mx = c > mx ? c : mx;
+        tiles += (c + kTile - 1) / kTile;
+    }
+    sizes->n_refl = tot;
+    sizes->max_refl = mx;
+    sizes->n_tiles = tiles;
+    sizes->ws_bytes = layout(n, b->n_atoms, b->zmax, tot).total;
+    return XRD_OK;
+}
+
+int xrd_pattern_batch(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, const xrd_pattern* out,
+                      void* workspace, size_t ws_bytes, void* stream)
+{
+    if (!h) return XRD_EINVAL;
+    h->err.clear();
+    int rc = check_batch(h, b);
+    if (rc) return rc;
+    if ((rc = check_opts(h, o))) return rc;
+    if (!out) return fail(h, XRD_EINVAL, "out is NULL");
+    const int64_t n = b->n_struct;
+    if (!out->peak_off || !out->fam_off || !out->totals || (n > 0 && !out->status))
+        return fail(h, XRD_EINVAL, "an output pointer is NULL");
+    if (out->cap_peaks < 0 || out->cap_fam < 0) return fail(h, XRD_EINVAL, "negative output capacity");
+    if (out->cap_peaks > 0 && (!out->two_theta || !out->intensity || !out->d_hkl))
+        return fail(h, XRD_EINVAL, "a peak output pointer is NULL");
+    if (out->cap_fam > 0 && (!out->hkl || !out->mult)) return fail(h, XRD_EINVAL, "a family output pointer is NULL");
+    if (!workspace || ((uintptr_t)workspace & 255)) return fail(h, XRD_EINVAL, "workspace must be 256-byte aligned");
+    const int64_t cap_refl = refl_capacity(n, b->n_atoms, b->zmax, ws_bytes);
+    if (cap_refl < 0) return fail(h, XRD_ECAPACITY, "workspace smaller than the per-structure part");
+    DeviceGuard g(h->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    char* ws = (char*)workspace;
+    const Layout L = layout(n, b->n_atoms, b->zmax, cap_refl);
+    xrd::GeomArgs ga = geom_args(b, o, L, ws, cap_refl, out->totals, out->status);
+
+    const bool prof = h->profiling;
+    int stage = 0;
+    auto mark = [&]() {
+        if (prof) cudaEventRecord(h->ev[stage], st);
+        stage++;
+    };
+    cudaMemsetAsync(ws + L.flags, 0, 16, st);
+    mark();
+    xrd::launch_prep(ga, st);
+    mark();
+    xrd::launch_atoms(ga, st);
+    mark();
+    xrd::launch_count(ga, st);
+    mark();
+    xrd::launch_scan_refl(ga, st);
+    mark();
+    xrd::launch_emit(ga, st);
+    mark();
+
+    xrd::SfArgs sa{};
+    sa.n_struct = (int)n;
+    sa.precision = o->precision;
+    sa.tile = kTile;
+    sa.grid = h->sms * 12;
+    sa.lambda = o->lambda;
+    sa.atom_off = b->atom_off;
+    sa.refl_off = ga.refl_off;
+    sa.tile_off = ga.tile_off;
+    sa.abort_flag = ga.abort_flag;
+    sa.coef32 = ga.coef32;
+    sa.coef = b->coef;
+    sa.atom32 = ga.atom32;
+    sa.atom64 = ga.atom64;
+    sa.q = ga.q;
+    sa.key = ga.key;
+    sa.I = (double*)(ws + L.I);
+    sa.F = nullptr;
+    xrd::launch_sf(sa, st);
+    mark();
+
+    xrd::PostArgs pa{};
+    pa.n_struct = (int)n;
+    pa.cap_smem = kPostCap;
+    pa.scaled = o->scaled;
+    pa.lambda = o->lambda;
+    pa.tol = o->tt_tol;
+    pa.cutoff = o->rel_cutoff;
+    pa.r2min = ga.r2min;
+    pa.r2max = ga.r2max;
+    pa.refl_off = ga.refl_off;
+    pa.abort_flag = ga.abort_flag;
+    pa.q = ga.q;
+    pa.key = ga.key;
+    pa.I = sa.I;
+    pa.g_tt = (double*)(ws + L.g_tt);
+    pa.g_perm = (int*)(ws + L.g_perm);
+    pa.g_bkt = (int*)(ws + L.g_bkt);
+    pa.g_flag = (uint8_t*)(ws + L.g_flag);
+    pa.g_pstart = (int*)(ws + L.g_pstart);
+    pa.g_psum = (double*)(ws + L.g_psum);
+    pa.g_fcnt = (int*)(ws + L.g_fcnt);
+    pa.st_tt = (double*)(ws + L.st_tt);
+    pa.st_I = (double*)(ws + L.st_I);
+    pa.st_d = (double*)(ws + L.st_d);
+    pa.st_foff = (int*)(ws + L.st_foff);
+    pa.st_hkl = (int*)(ws + L.st_hkl);
+    pa.st_mult = (int*)(ws + L.st_mult);
+    pa.npk = (int64_t*)(ws + L.npk);
+    pa.nfm = (int64_t*)(ws + L.nfm);
+    xrd::launch_post(pa, st);
+    mark();
+
+    xrd::CompactArgs ca{};
+    ca.n_struct = (int)n;
+    ca.cap_peaks = out->cap_peaks;
+    ca.cap_fam = out->cap_fam;
+    ca.refl_off = ga.refl_off;
+    ca.abort_flag = ga.abort_flag;
+    ca.npk = pa.npk;
+    ca.nfm = pa.nfm;
+    ca.fam_soff = (int64_t*)(ws + L.fam_soff);
+    ca.st_tt = pa.st_tt;
+    ca.st_I = pa.st_I;
+    ca.st_d = pa.st_d;
+    ca.st_foff = pa.st_foff;
+    ca.st_hkl = pa.st_hkl;
+    ca.st_mult = pa.st_mult;
+    ca.out_abort = ga.abort_flag + 1;
+    ca.out = *out;
+    xrd::launch_compact(ca, st);
+    mark();
+    h->recorded = prof;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(h, e, "xrd_pattern_batch launch");
+    return XRD_OK;
+}
+
+}  // extern "C"

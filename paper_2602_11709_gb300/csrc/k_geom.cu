@@ -1,0 +1,357 @@
+// Steps S0-S1: per-structure geometry, atom packing and reflection enumeration.
+//
+// Sec. 2 of the paper lists "the generation of reciprocal lattice points within
+// the physically accessible sphere" as the first step of the numerical core:
+// every integer g = (h, k, l) != 0 with r_min <= |g| <= r_max, |g|^2 = h^T G* h.
+// Friedel's law F(-g) = F(g)* makes g and -g identical in intensity, so only
+// the half-space (first nonzero of h, k, l positive) is enumerated; every kept
+// reflection stands for two.
+//
+// |g|^2 is evaluated in one fixed order with every product and sum rounded on
+// its own (no fused multiply-add), so the set of reflections on the sphere
+// boundary is decided exactly as a plain FP64 evaluation of the same order.
+#include "xrd_internal.cuh"
+#include "xrd_launch.h"
+
+namespace xrd {
+
+__device__ __forceinline__ double cosd(double deg)
+{
+    // exact cosines at 90, 60 and 120 degrees; otherwise cos(deg * pi / 180)
+    if (deg == 90.0) return 0.0;
+    if (deg == 60.0) return 0.5;
+    if (deg == 120.0) return -0.5;
+    return cos(__dmul_rn(deg, kPi / 180.0));
+}
+
+// S0: reciprocal metric G* = G^-1 from the direct metric
+// G = [[a^2, ab cos(gamma), ac cos(beta)], [., b^2, bc cos(alpha)], [., ., c^2]]
+// by cofactors over the determinant, and the enumeration box |h| <= r_max a + 1.
+__global__ void k_prep(const double* __restrict__ lattice, int n, double rmax, Geo* __restrict__ geo)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const double a = lattice[6 * s], b = lattice[6 * s + 1], c = lattice[6 * s + 2];
+    const double al = lattice[6 * s + 3], be = lattice[6 * s + 4], ga = lattice[6 * s + 5];
+    Geo g;
+    g.status = XRD_OK;
+    g.H = g.K = g.L = -1;
+    for (int i = 0; i < 6; i++) g.gs[i] = 0.0;
+    const bool finite = isfinite(a) && isfinite(b) && isfinite(c) && isfinite(al) && isfinite(be) && isfinite(ga);
+    if (!finite || !(a > 0.0 && b > 0.0 && c > 0.0)) {
+        g.status = XRD_EINVAL;
+        geo[s] = g;
+        return;
+    }
+    const double ca = cosd(al), cb = cosd(be), cg = cosd(ga);
+    // volume factor 1 - ca^2 - cb^2 - cg^2 + 2 ca cb cg, left to right
+    double vf = __dsub_rn(1.0, __dmul_rn(ca, ca));
+    vf = __dsub_rn(vf, __dmul_rn(cb, cb));
+    vf = __dsub_rn(vf, __dmul_rn(cg, cg));
+    vf = __dadd_rn(vf, __dmul_rn(__dmul_rn(__dmul_rn(2.0, ca), cb), cg));
+    if (!(vf > 1e-6)) {
+        g.status = XRD_EINVAL;
+        geo[s] = g;
+        return;
+    }
+    const double G11 = __dmul_rn(a, a), G22 = __dmul_rn(b, b), G33 = __dmul_rn(c, c);
+    const double G12 = __dmul_rn(__dmul_rn(a, b), cg);
+    const double G13 = __dmul_rn(__dmul_rn(a, c), cb);
+    const double G23 = __dmul_rn(__dmul_rn(b, c), ca);
+    const double C11 = __dsub_rn(__dmul_rn(G22, G33), __dmul_rn(G23, G23));
+    const double C22 = __dsub_rn(__dmul_rn(G11, G33), __dmul_rn(G13, G13));
+    const double C33 = __dsub_rn(__dmul_rn(G11, G22), __dmul_rn(G12, G12));
+    const double C12 = __dsub_rn(__dmul_rn(G13, G23), __dmul_rn(G12, G33));
+    const double C13 = __dsub_rn(__dmul_rn(G12, G23), __dmul_rn(G13, G22));
+    const double C23 = __dsub_rn(__dmul_rn(G12, G13), __dmul_rn(G11, G23));
+    const double det = __dadd_rn(__dadd_rn(__dmul_rn(G11, C11), __dmul_rn(G12, C12)), __dmul_rn(G13, C13));
+    g.gs[0] = __ddiv_rn(C11, det);
+    g.gs[1] = __ddiv_rn(C22, det);
+    g.gs[2] = __ddiv_rn(C33, det);
+    g.gs[3] = __ddiv_rn(C12, det);
+    g.gs[4] = __ddiv_rn(C13, det);
+    g.gs[5] = __ddiv_rn(C23, det);
+    g.H = (int)floor(__dmul_rn(rmax, a)) + 1;
+    g.K = (int)floor(__dmul_rn(rmax, b)) + 1;
+    g.L = (int)floor(__dmul_rn(rmax, c)) + 1;
+    if (g.H > kHklLimit || g.K > kHklLimit || g.L > kHklLimit) {
+        g.status = XRD_EINVAL;  // cell too large for the packed (h, k, l) key at this 2-theta range
+        g.H = g.K = g.L = -1;
+    }
+    geo[s] = g;
+}
+
+// f(s) coefficients in the form the FP32 loops use (exp2 with the scale folded in).
+__global__ void k_coef(const double* __restrict__ coef, int zmax, Coef32* __restrict__ c32)
+{
+    for (int z = threadIdx.x; z <= zmax; z += blockDim.x) {
+        Coef32 c;
+        for (int i = 0; i < 4; i++) {
+            c.a[i] = (float)(-kFScale * coef[8 * z + 2 * i]);
+            c.bl[i] = (float)(-coef[8 * z + 2 * i + 1] * 1.4426950408889634);
+        }
+        c32[z] = c;
+    }
+}
+
+// Validate and pack the atoms of one structure, sorted by element (stable:
+// ties keep their input order) so that f(s) is evaluated once per element run.
+__global__ void __launch_bounds__(128) k_atoms(const int64_t* __restrict__ atom_off, int64_t n_atoms,
+                                               const double* __restrict__ frac, const int16_t* __restrict__ Zin,
+                                               const double* __restrict__ occ, const double* __restrict__ Bf, int zmax,
+                                               Geo* __restrict__ geo, Atom32* __restrict__ a32,
+                                               Atom64* __restrict__ a64)
+{
+    __shared__ int off[kZmaxLimit + 1];
+    __shared__ int zs[128];
+    __shared__ int bad;
+    const int s = blockIdx.x;
+    int64_t a0 = atom_off[s], na = atom_off[s + 1] - a0;
+    const bool range_ok = a0 >= 0 && na >= 0 && atom_off[s + 1] <= n_atoms && na <= (1 << 30);
+    if (!range_ok) { a0 = 0; na = 0; }
+    for (int i = threadIdx.x; i <= kZmaxLimit; i += blockDim.x) off[i] = 0;
+    if (threadIdx.x == 0) bad = !range_ok;
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < na; i += blockDim.x) {
+        const int z = Zin[a0 + i];
+        const double x = frac[3 * (a0 + i)], y = frac[3 * (a0 + i) + 1], w = frac[3 * (a0 + i) + 2];
+        const bool ok = z >= 0 && z <= zmax && isfinite(x) && isfinite(y) && isfinite(w) && occ[a0 + i] >= 0.0 &&
+                        isfinite(occ[a0 + i]) &&
+                        isfinite(Bf[a0 + i]) && fabs(x) < 262144.0 && fabs(y) < 262144.0 && fabs(w) < 262144.0;
+        if (!ok) atomicOr(&bad, 1);
+        else atomicAdd(&off[z], 1);
+    }
+    __syncthreads();
+    if (bad) {
+        if (threadIdx.x == 0) geo[s].status = XRD_EINVAL;
+        return;
+    }
+    if (threadIdx.x == 0) {  // exclusive offset of each element's run (serial over <= 256 entries)
+        int run = 0;
+        for (int z = 0; z <= zmax; z++) {
+            const int c = off[z];
+            off[z] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    // stable placement, one chunk of blockDim atoms at a time
+    for (int64_t base = 0; base < na; base += blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        const int z = i < na ? (int)Zin[a0 + i] : -1;
+        zs[threadIdx.x] = z;
+        __syncthreads();
+        if (i < na) {
+            int before = 0;
+            for (int t = 0; t < (int)threadIdx.x; t++) before += zs[t] == z;
+            const int pos = off[z] + before;
+            const double x = frac[3 * (a0 + i)], y = frac[3 * (a0 + i) + 1], w = frac[3 * (a0 + i) + 2];
+            const double o = occ[a0 + i], bb = Bf[a0 + i];
+            Atom32 r;
+            r.X = fix32(x);
+            r.Y = fix32(y);
+            r.Z = fix32(w);
+            r.nb = (float)(-bb * 1.4426950408889634);
+            r.lo = o > 0.0 ? (float)log2(o) : -INFINITY;
+            r.z = z;
+            a32[a0 + pos] = r;
+            Atom64 d;
+            d.x = x; d.y = y; d.z = w; d.B = bb; d.occ = o; d.zz = z; d.pad = 0;
+            a64[a0 + pos] = d;
+        }
+        __syncthreads();  // every read of off[] for this chunk is done
+        if (i < na) atomicAdd(&off[z], 1);
+        __syncthreads();
+    }
+}
+
+// |g|^2 in the fixed order ((G11 hh + G22 kk) + G33 ll) + 2 ((G12 hk + G13 hl) + G23 kl).
+__device__ __forceinline__ double q_exact(const double* gs, int h, int k, int l)
+{
+    const double hh = (double)(h * h), kk = (double)(k * k), ll = (double)(l * l);
+    const double hk = (double)(h * k), hl = (double)(h * l), kl = (double)(k * l);
+    const double diag = __dadd_rn(__dadd_rn(__dmul_rn(gs[0], hh), __dmul_rn(gs[1], kk)), __dmul_rn(gs[2], ll));
+    const double off = __dadd_rn(__dadd_rn(__dmul_rn(gs[3], hk), __dmul_rn(gs[4], hl)), __dmul_rn(gs[5], kl));
+    return __dadd_rn(diag, __dmul_rn(2.0, off));
+}
+
+// The l interval of column (h, k) that can hold |g|^2 <= r2max, widened by one
+// on each side; every l in it is then tested exactly.
+__device__ __forceinline__ void column_range(const Geo& g, int h, int k, double r2max, int& lo, int& hi)
+{
+    const double A = g.gs[0] * (double)(h * h) + g.gs[1] * (double)(k * k) + 2.0 * g.gs[3] * (double)(h * k);
+    const double b = g.gs[4] * (double)h + g.gs[5] * (double)k;
+    const double R = r2max * (1.0 + 1e-9) + 1e-12;
+    const double disc = b * b - g.gs[2] * (A - R);
+    lo = 1;
+    hi = 0;
+    if (disc < 0.0) return;
+    const double sq = sqrt(disc);
+    lo = (int)floor((-b - sq) / g.gs[2]) - 1;
+    hi = (int)ceil((-b + sq) / g.gs[2]) + 1;
+    if (lo < -g.L) lo = -g.L;
+    if (hi > g.L) hi = g.L;
+    if (h == 0 && k == 0 && lo < 1) lo = 1;  // half-space: (0, 0, l > 0)
+}
+
+template <bool EMIT>
+__device__ void enumerate_struct(const Geo& g, double r2min, double r2max, int64_t base, int64_t cap,
+                                 double* __restrict__ qo, uint32_t* __restrict__ ko, int* counter)
+{
+    const int nk = 2 * g.K + 1;
+    const int ncol = (g.H + 1) * nk;
+    int local = 0;
+    for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
+        const int h = c / nk, k = c % nk - g.K;
+        if (h == 0 && k < 0) continue;  // half-space: h > 0, or h = 0 and k >= 0
+        int lo, hi;
+        column_range(g, h, k, r2max, lo, hi);
+        for (int l = lo; l <= hi; l++) {
+            const double q = q_exact(g.gs, h, k, l);
+            if (q < r2min || q > r2max) continue;
+            if (EMIT) {
+                const int pos = atomicAdd(counter, 1);
+                if (pos < cap) {
+                    qo[base + pos] = q;
+                    ko[base + pos] = hkl_pack(h, k, l);
+                }
+            } else {
+                local++;
+            }
+        }
+    }
+    if (!EMIT) atomicAdd(counter, local);
+}
+
+__global__ void __launch_bounds__(256) k_count(const Geo* __restrict__ geo, double r2min, double r2max,
+                                               int64_t* __restrict__ cnt)
+{
+    __shared__ int n;
+    const int s = blockIdx.x;
+    const Geo g = geo[s];
+    if (threadIdx.x == 0) n = 0;
+    __syncthreads();
+    if (g.status == XRD_OK && g.H >= 0) enumerate_struct<false>(g, r2min, r2max, 0, 0, nullptr, nullptr, &n);
+    __syncthreads();
+    if (threadIdx.x == 0) cnt[s] = n;
+}
+
+__global__ void __launch_bounds__(256) k_emit(const Geo* __restrict__ geo, double r2min, double r2max,
+                                              const int64_t* __restrict__ refl_off, const int* __restrict__ abort_flag,
+                                              double* __restrict__ q, uint32_t* __restrict__ key)
+{
+    __shared__ int n;
+    if (*abort_flag) return;
+    const int s = blockIdx.x;
+    const Geo g = geo[s];
+    if (threadIdx.x == 0) n = 0;
+    __syncthreads();
+    const int64_t base = refl_off[s], cap = refl_off[s + 1] - base;
+    if (g.status == XRD_OK && g.H >= 0) enumerate_struct<true>(g, r2min, r2max, base, cap, q, key, &n);
+}
+
+// Exclusive scans of the per-structure reflection counts and tile counts by a
+// single block; flags a capacity overflow when the total exceeds the workspace.
+__global__ void __launch_bounds__(1024) k_scan_refl(const int64_t* __restrict__ cnt, const Geo* __restrict__ geo,
+                                                    int n, int tile, int64_t cap_refl, int64_t* __restrict__ refl_off,
+                                                    int* __restrict__ tile_off, int* __restrict__ abort_flag,
+                                                    int64_t* __restrict__ totals, int32_t* __restrict__ status)
+{
+    __shared__ long long ws[32];
+    __shared__ long long wt[32];
+    __shared__ long long carry_r, carry_t;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (threadIdx.x == 0) { carry_r = 0; carry_t = 0; }
+    __syncthreads();
+    for (int base = 0; base < n; base += blockDim.x) {
+        const int i = base + threadIdx.x;
+        const long long v = i < n ? cnt[i] : 0;
+        const long long t = i < n ? (v + tile - 1) / tile : 0;
+        long long iv = v, it = t;
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long a = __shfl_up_sync(0xffffffffu, iv, o);
+            const long long b = __shfl_up_sync(0xffffffffu, it, o);
+            if (lane >= o) { iv += a; it += b; }
+        }
+        if (lane == 31) { ws[w] = iv; wt[w] = it; }
+        __syncthreads();
+        if (w == 0) {
+            long long a = lane < nw ? ws[lane] : 0, b = lane < nw ? wt[lane] : 0;
+            long long ia = a, ib = b;
+            for (int o = 1; o < 32; o <<= 1) {
+                const long long x = __shfl_up_sync(0xffffffffu, ia, o);
+                const long long y = __shfl_up_sync(0xffffffffu, ib, o);
+                if (lane >= o) { ia += x; ib += y; }
+            }
+            if (lane < nw) { ws[lane] = ia - a; wt[lane] = ib - b; }
+        }
+        __syncthreads();
+        if (i < n) {
+            refl_off[i] = carry_r + ws[w] + iv - v;
+            tile_off[i] = (int)(carry_t + wt[w] + it - t);
+        }
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) { carry_r += ws[w] + iv; carry_t += wt[w] + it; }
+        __syncthreads();
+    }
+    __shared__ int nbad;
+    const int over = carry_r > cap_refl;
+    if (threadIdx.x == 0) {
+        refl_off[n] = carry_r;
+        tile_off[n] = (int)carry_t;
+        totals[0] = carry_r;
+        totals[1] = 0;
+        totals[2] = 0;
+        *abort_flag = over;
+        nbad = 0;
+    }
+    __syncthreads();
+    int bad = 0;
+    for (int s = threadIdx.x; s < n; s += blockDim.x) {
+        const int st = over ? XRD_ECAPACITY : geo[s].status;
+        status[s] = st;
+        bad += st != XRD_OK;
+    }
+    atomicAdd(&nbad, bad);
+    __syncthreads();
+    if (threadIdx.x == 0) totals[3] = nbad;
+}
+
+void launch_prep(const GeomArgs& a, cudaStream_t st)
+{
+    const int n = a.n_struct;
+    if (n > 0) k_prep<<<(n + 127) / 128, 128, 0, st>>>(a.lattice, n, a.rmax, a.geo);
+    k_coef<<<1, 256, 0, st>>>(a.coef, a.zmax, a.coef32);
+}
+
+void launch_atoms(const GeomArgs& a, cudaStream_t st)
+{
+    if (a.n_struct > 0)
+        k_atoms<<<a.n_struct, 128, 0, st>>>(a.atom_off, a.n_atoms, a.frac, a.Z, a.occ, a.B, a.zmax, a.geo, a.atom32, a.atom64);
+}
+
+void launch_count_only(const GeomArgs& a, cudaStream_t st)
+{
+    const int n = a.n_struct;
+    if (n <= 0) return;
+    k_prep<<<(n + 127) / 128, 128, 0, st>>>(a.lattice, n, a.rmax, a.geo);
+    k_count<<<n, 256, 0, st>>>(a.geo, a.r2min, a.r2max, a.refl_cnt);
+}
+
+void launch_count(const GeomArgs& a, cudaStream_t st)
+{
+    if (a.n_struct > 0) k_count<<<a.n_struct, 256, 0, st>>>(a.geo, a.r2min, a.r2max, a.refl_cnt);
+}
+
+void launch_scan_refl(const GeomArgs& a, cudaStream_t st)
+{
+    k_scan_refl<<<1, 1024, 0, st>>>(a.refl_cnt, a.geo, a.n_struct, a.tile, a.cap_refl, a.refl_off, a.tile_off,
+                                    a.abort_flag, a.totals, a.status);
+}
+
+void launch_emit(const GeomArgs& a, cudaStream_t st)
+{
+    if (a.n_struct > 0) k_emit<<<a.n_struct, 256, 0, st>>>(a.geo, a.r2min, a.r2max, a.refl_off, a.abort_flag, a.q, a.key);
+}
+
+}  // namespace xrd

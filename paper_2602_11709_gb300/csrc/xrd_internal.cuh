@@ -1,0 +1,154 @@
+// Internal types and device helpers of the GB300 powder-XRD engine.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "xrd.h"
+
+namespace xrd {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kFScale = 41.78214;  // Mott-Bethe factor 8 pi^2 a0 of f(s) (Sec. 1, atomic scattering factors)
+constexpr int kZmaxLimit = 255;
+constexpr int kHklLimit = 511;        // |h|, |k|, |l| fit the 10-bit fields of the packed key
+
+// Per-structure geometry written by k_prep (step S0).
+struct Geo {
+    double gs[6];  // reciprocal metric G* stored as (11, 22, 33, 12, 13, 23)
+    int H, K, L;   // enumeration box |h| <= H ...
+    int status;    // XRD_OK or XRD_EINVAL
+};
+
+// Atom record for the FP32 structure-factor loops (sorted by element within a structure).
+struct __align__(8) Atom32 {
+    uint32_t X, Y, Z;  // coordinates in 32-bit fixed point: round(x * 2^32) mod 2^32
+    float nb;          // -B * log2(e): exp(-B s^2) = 2^(nb s^2)
+    float lo;          // log2(occ): occ folds into the same exp2
+    int32_t z;         // element number
+};
+
+// Atom record for the FP64 loops and the FP64 phase.
+struct __align__(16) Atom64 {
+    double x, y, z, B, occ;
+    int32_t zz, pad;
+};
+
+// f(s) = Z + s^2 sum_i a'_i 2^(bl_i s^2) with a'_i = -41.78214 a_i, bl_i = -b_i log2(e).
+struct __align__(16) Coef32 {
+    float a[4];
+    float bl[4];
+};
+
+// Reflection key: (h + 512, k + 512, l + 512) in three 10-bit fields, so that
+// the unsigned order of keys is the lexicographic order of signed (h, k, l).
+__host__ __device__ __forceinline__ uint32_t hkl_pack(int h, int k, int l)
+{
+    return ((uint32_t)(h + 512) << 20) | ((uint32_t)(k + 512) << 10) | (uint32_t)(l + 512);
+}
+__host__ __device__ __forceinline__ int hkl_h(uint32_t p) { return (int)((p >> 20) & 1023u) - 512; }
+__host__ __device__ __forceinline__ int hkl_k(uint32_t p) { return (int)((p >> 10) & 1023u) - 512; }
+__host__ __device__ __forceinline__ int hkl_l(uint32_t p) { return (int)(p & 1023u) - 512; }
+
+// Positive normal double -> float by bit arithmetic (truncation). The hardware
+// conversion unit is slow on this part; callers use it only for values that
+// are positive, normal and in float range.
+__device__ __forceinline__ float d2f_pos(double x)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
+    return __uint_as_float(((hi - (896u << 20)) << 3) | (lo >> 29));
+}
+
+// Float (finite, any sign, zero or normal) -> double by bit arithmetic; denormals become 0.
+__device__ __forceinline__ double f2d_fast(float x)
+{
+    const uint32_t u = __float_as_uint(x);
+    const uint32_t e = (u >> 23) & 0xffu;
+    if (e == 0u) return 0.0;
+    const uint32_t hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u >> 3) & 0xfffffu);
+    const uint32_t lo = u << 29;
+    return __longlong_as_double((long long)(((unsigned long long)hi << 32) | lo));
+}
+
+// round(v * 2^32) mod 2^32 for |v| < 2^19: adding 1.5 * 2^20 puts 2^-32 at the
+// last mantissa bit, so the low word of the sum is the wrapped fixed-point value.
+__device__ __forceinline__ uint32_t fix32(double v)
+{
+    const double t = __dadd_rn(v, 1572864.0);
+    return (uint32_t)(unsigned long long)__double_as_longlong(t);
+}
+
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// ---- block-wide primitives over generic pointers (shared or global memory) ----
+
+__device__ __forceinline__ int warp_incl_scan(int v)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// Exclusive prefix sum of a[0..n) in place by the whole block; returns the
+// total. `tmp` is shared scratch of at least 33 ints. All threads must call.
+__device__ __forceinline__ int block_excl_scan(int* a, int n, int* tmp)
+{
+    const int nw = (blockDim.x + 31) >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int carry = 0;
+    for (int base = 0; base < n; base += blockDim.x) {
+        const int i = base + (int)threadIdx.x;
+        const int v = i < n ? a[i] : 0;
+        const int inc = warp_incl_scan(v);
+        if (lane == 31) tmp[w] = inc;
+        __syncthreads();
+        if (w == 0) {
+            const int s = lane < nw ? tmp[lane] : 0;
+            const int si = warp_incl_scan(s);
+            if (lane < nw) tmp[lane] = si - s;
+            if (lane == 31) tmp[32] = si;
+        }
+        __syncthreads();
+        if (i < n) a[i] = carry + tmp[w] + inc - v;
+        carry += tmp[32];
+        __syncthreads();
+    }
+    return carry;
+}
+
+__device__ __forceinline__ double block_max_double(double v, double* tmp)
+{
+    const int nw = (blockDim.x + 31) >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (lane == 0) tmp[w] = v;
+    __syncthreads();
+    double r = tmp[0];
+    for (int i = 1; i < nw; i++) r = fmax(r, tmp[i]);
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ int block_sum_int(int v, int* tmp)
+{
+    const int nw = (blockDim.x + 31) >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) tmp[w] = v;
+    __syncthreads();
+    int r = 0;
+    for (int i = 0; i < nw; i++) r += tmp[i];
+    __syncthreads();
+    return r;
+}
+
+}  // namespace xrd

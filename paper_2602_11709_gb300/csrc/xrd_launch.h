@@ -1,0 +1,110 @@
+// Host-side launch arguments shared by the C ABI layer and the kernel files.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "xrd_internal.cuh"
+
+namespace xrd {
+
+struct GeomArgs {
+    int n_struct, zmax, tile;
+    int64_t n_atoms;
+    double r2min, r2max, rmax;
+    int64_t cap_refl;
+    const double* lattice;
+    const int64_t* atom_off;
+    const double* frac;
+    const int16_t* Z;
+    const double* occ;
+    const double* B;
+    const double* coef;
+    Geo* geo;
+    Coef32* coef32;
+    Atom32* atom32;
+    Atom64* atom64;
+    int64_t* refl_cnt;
+    int64_t* refl_off;
+    int* tile_off;
+    int* abort_flag;
+    int64_t* totals;
+    int32_t* status;
+    double* q;
+    uint32_t* key;
+};
+
+struct SfArgs {
+    int n_struct, precision, tile, grid;
+    double lambda;
+    const int64_t* atom_off;
+    const int64_t* refl_off;
+    const int* tile_off;
+    const int* abort_flag;
+    const Coef32* coef32;
+    const double* coef;
+    const Atom32* atom32;
+    const Atom64* atom64;
+    const double* q;
+    const uint32_t* key;
+    double* I;   // per reflection intensity |F|^2 LP (one Friedel half-space member)
+    float2* F;   // optional per-reflection F (nullptr: not stored)
+};
+
+struct PostArgs {
+    int n_struct, cap_smem, scaled;
+    double lambda, tol, cutoff, r2min, r2max;
+    const int64_t* refl_off;
+    const int* abort_flag;
+    const double* q;
+    const uint32_t* key;
+    const double* I;
+    // global scratch for structures larger than cap_smem (indexed by reflection)
+    double* g_tt;
+    int* g_perm;
+    int* g_bkt;   // n_refl + n_struct entries
+    uint8_t* g_flag;
+    int* g_pstart;
+    double* g_psum;
+    int* g_fcnt;
+    // staging of kept peaks and families (indexed by reflection offset)
+    double* st_tt;
+    double* st_I;
+    double* st_d;
+    int* st_foff;
+    int* st_hkl;   // 3 per family
+    int* st_mult;
+    int64_t* npk;  // kept peaks per structure
+    int64_t* nfm;  // families of kept peaks per structure
+};
+
+struct CompactArgs {
+    int n_struct;
+    int64_t cap_peaks, cap_fam;
+    const int64_t* refl_off;
+    const int* abort_flag;
+    const int64_t* npk;
+    const int64_t* nfm;
+    int64_t* fam_soff;  // [n_struct + 1] scratch: exclusive scan of nfm
+    const double* st_tt;
+    const double* st_I;
+    const double* st_d;
+    const int* st_foff;
+    const int* st_hkl;
+    const int* st_mult;
+    int* out_abort;     // set when the output capacity is too small
+    xrd_pattern out;
+};
+
+void launch_prep(const GeomArgs& a, cudaStream_t st);
+void launch_atoms(const GeomArgs& a, cudaStream_t st);
+void launch_count(const GeomArgs& a, cudaStream_t st);
+void launch_count_only(const GeomArgs& a, cudaStream_t st);
+void launch_scan_refl(const GeomArgs& a, cudaStream_t st);
+void launch_emit(const GeomArgs& a, cudaStream_t st);
+void launch_sf(const SfArgs& a, cudaStream_t st);
+size_t post_smem_bytes(int cap);
+void launch_post(const PostArgs& a, cudaStream_t st);
+void launch_compact(const CompactArgs& a, cudaStream_t st);
+
+}  // namespace xrd

@@ -1,0 +1,256 @@
+"""Thin Python binding of the C ABI in include/xrd.h (argument marshalling only).
+
+Device memory, streams and host<->device copies come from PyTorch; every step
+of the pattern computation runs in the library's CUDA kernels. There is no CPU
+fallback: if the compiled library is missing, load() raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libxrd.so")
+
+XRD_OK, XRD_EINVAL, XRD_ECAPACITY, XRD_ECUDA, XRD_ETIMEOUT = 0, 1, 2, 3, 4
+XRD_FP64, XRD_FP32_PHASE64, XRD_FP32_PHASEFIX = 0, 1, 2
+PRECISIONS = {"fp64": XRD_FP64, "fp32_phase64": XRD_FP32_PHASE64, "fp32_phasefix": XRD_FP32_PHASEFIX}
+STAGES = ["prep", "atoms", "count", "scan", "emit", "structure_factor", "post", "compact"]
+
+
+class xrd_batch(C.Structure):
+    _fields_ = [("n_struct", C.c_int32), ("zmax", C.c_int32), ("n_atoms", C.c_int64), ("lattice", C.c_void_p),
+                ("atom_off", C.c_void_p), ("frac", C.c_void_p), ("Z", C.c_void_p), ("occ", C.c_void_p),
+                ("B", C.c_void_p), ("coef", C.c_void_p)]
+
+
+class xrd_opts(C.Structure):
+    _fields_ = [("lambda_", C.c_double), ("tt_min", C.c_double), ("tt_max", C.c_double), ("tt_tol", C.c_double),
+                ("rel_cutoff", C.c_double), ("scaled", C.c_int32), ("precision", C.c_int32), ("tile", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+class xrd_sizes(C.Structure):
+    _fields_ = [("n_refl", C.c_int64), ("max_refl", C.c_int64), ("n_tiles", C.c_int64), ("ws_bytes", C.c_size_t)]
+
+
+class xrd_pattern(C.Structure):
+    _fields_ = [("cap_peaks", C.c_int64), ("cap_fam", C.c_int64), ("peak_off", C.c_void_p),
+                ("two_theta", C.c_void_p), ("intensity", C.c_void_p), ("d_hkl", C.c_void_p),
+                ("fam_off", C.c_void_p), ("hkl", C.c_void_p), ("mult", C.c_void_p), ("status", C.c_void_p),
+                ("totals", C.c_void_p)]
+
+
+EXPORTS = ["xrd_create", "xrd_destroy", "xrd_last_error", "xrd_query_sizes", "xrd_pattern_batch",
+           "xrd_set_profiling", "xrd_stage_times"]
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load the compiled library; raises if it was not built (no fallback path exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("CUDA library %s is missing: build it with __graft_entry__.build()" % path)
+    L = C.CDLL(path)
+    L.xrd_create.argtypes = [C.POINTER(C.c_void_p), C.c_int]
+    L.xrd_create.restype = C.c_int
+    L.xrd_destroy.argtypes = [C.c_void_p]
+    L.xrd_destroy.restype = None
+    L.xrd_last_error.argtypes = [C.c_void_p]
+    L.xrd_last_error.restype = C.c_char_p
+    L.xrd_query_sizes.argtypes = [C.c_void_p, C.POINTER(xrd_batch), C.POINTER(xrd_opts), C.POINTER(xrd_sizes),
+                                  C.c_void_p]
+    L.xrd_query_sizes.restype = C.c_int
+    L.xrd_pattern_batch.argtypes = [C.c_void_p, C.POINTER(xrd_batch), C.POINTER(xrd_opts), C.POINTER(xrd_pattern),
+                                    C.c_void_p, C.c_size_t, C.c_void_p]
+    L.xrd_pattern_batch.restype = C.c_int
+    L.xrd_set_profiling.argtypes = [C.c_void_p, C.c_int]
+    L.xrd_set_profiling.restype = C.c_int
+    L.xrd_stage_times.argtypes = [C.c_void_p, C.POINTER(C.c_float), C.c_int]
+    L.xrd_stage_times.restype = C.c_int
+    _lib = L
+    return L
+
+
+class XrdError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("xrd error %d: %s" % (code, msg))
+        self.code = code
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def make_opts(o, precision="fp32_phasefix", tile=-1) -> xrd_opts:
+    """C options from any object with wavelength/tt_min/tt_max/tt_tol/rel_cutoff/scaled."""
+    p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    return xrd_opts(float(o.wavelength), float(o.tt_min), float(o.tt_max), float(o.tt_tol), float(o.rel_cutoff),
+                    int(o.scaled), p, int(tile), 0)
+
+
+@dataclass
+class DeviceBatch:
+    """A batch resident in device memory (torch tensors) plus its C descriptor."""
+    n_struct: int
+    zmax: int
+    n_atoms: int
+    lattice: object
+    atom_off: object
+    frac: object
+    Z: object
+    occ: object
+    B: object
+    coef: object
+
+    @staticmethod
+    def from_host(b, device="cuda", pin=False):
+        torch = _torch()
+
+        def t(a, dt):
+            x = torch.from_numpy(np.ascontiguousarray(a, dtype=dt))
+            if pin:
+                x = x.pin_memory()
+            return x.to(device, non_blocking=pin)
+        return DeviceBatch(int(b.lattice.shape[0]), int(b.zmax), int(b.frac.shape[0]), t(b.lattice, np.float64),
+                           t(b.atom_off, np.int64), t(b.frac, np.float64), t(b.Z, np.int16), t(b.occ, np.float64),
+                           t(b.B, np.float64), t(b.coef, np.float64))
+
+    def c(self) -> xrd_batch:
+        return xrd_batch(self.n_struct, self.zmax, self.n_atoms, self.lattice.data_ptr(), self.atom_off.data_ptr(),
+                         self.frac.data_ptr(), self.Z.data_ptr(), self.occ.data_ptr(), self.B.data_ptr(),
+                         self.coef.data_ptr())
+
+
+class PatternBuffers:
+    """Caller-owned output arrays of xrd_pattern_batch (torch device tensors)."""
+
+    def __init__(self, n_struct, cap, device="cuda"):
+        torch = _torch()
+        cap = max(int(cap), 1)
+        self.n_struct = n_struct
+        self.cap = cap
+        self.peak_off = torch.zeros(n_struct + 1, dtype=torch.int64, device=device)
+        self.two_theta = torch.zeros(cap, dtype=torch.float64, device=device)
+        self.intensity = torch.zeros(cap, dtype=torch.float64, device=device)
+        self.d_hkl = torch.zeros(cap, dtype=torch.float64, device=device)
+        self.fam_off = torch.zeros(cap + 1, dtype=torch.int64, device=device)
+        self.hkl = torch.zeros(cap, 3, dtype=torch.int32, device=device)
+        self.mult = torch.zeros(cap, dtype=torch.int32, device=device)
+        self.status = torch.zeros(max(n_struct, 1), dtype=torch.int32, device=device)
+        self.totals = torch.zeros(4, dtype=torch.int64, device=device)
+
+    def c(self) -> xrd_pattern:
+        return xrd_pattern(self.cap, self.cap, self.peak_off.data_ptr(), self.two_theta.data_ptr(),
+                           self.intensity.data_ptr(), self.d_hkl.data_ptr(), self.fam_off.data_ptr(),
+                           self.hkl.data_ptr(), self.mult.data_ptr(), self.status.data_ptr(), self.totals.data_ptr())
+
+    def to_host(self):
+        """Per-structure arrays, in the same layout as the oracle's batch results."""
+        tot = self.totals.cpu().numpy()
+        off = self.peak_off.cpu().numpy()
+        npk, nfm = int(tot[1]), int(tot[2])
+        tt = self.two_theta[:npk].cpu().numpy()
+        I = self.intensity[:npk].cpu().numpy()
+        d = self.d_hkl[:npk].cpu().numpy()
+        fo = self.fam_off[:npk + 1].cpu().numpy()
+        hkl = self.hkl[:nfm].cpu().numpy()
+        mult = self.mult[:nfm].cpu().numpy()
+        res = {"totals": tot, "status": self.status[:self.n_struct].cpu().numpy(), "peak_tt": [], "peak_I": [],
+               "peak_d": [], "peak_fam_off": [], "fam_hkl": [], "fam_mult": []}
+        for s in range(self.n_struct):
+            p0, p1 = int(off[s]), int(off[s + 1])
+            f0 = int(fo[p0]) if p1 > p0 else 0
+            f1 = int(fo[p1]) if p1 > p0 else 0
+            res["peak_tt"].append(tt[p0:p1])
+            res["peak_I"].append(I[p0:p1])
+            res["peak_d"].append(d[p0:p1])
+            res["peak_fam_off"].append(fo[p0:p1 + 1] - f0 if p1 > p0 else np.zeros(1, np.int64))
+            res["fam_hkl"].append(hkl[f0:f1])
+            res["fam_mult"].append(mult[f0:f1])
+        return res
+
+
+class Handle:
+    """An xrd_handle bound to one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self.lib = load()
+        h = C.c_void_p()
+        rc = self.lib.xrd_create(C.byref(h), int(device))
+        if rc != XRD_OK:
+            raise XrdError(rc, "xrd_create failed")
+        self.h = h
+
+    def close(self):
+        if self.h:
+            self.lib.xrd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != XRD_OK:
+            raise XrdError(rc, self.lib.xrd_last_error(self.h).decode())
+
+    def query_sizes(self, db: DeviceBatch, opts: xrd_opts, stream=None) -> xrd_sizes:
+        sz = xrd_sizes()
+        b = db.c()
+        self._check(self.lib.xrd_query_sizes(self.h, C.byref(b), C.byref(opts), C.byref(sz), _stream_ptr(stream)))
+        return sz
+
+    def pattern_batch(self, db: DeviceBatch, opts: xrd_opts, out: PatternBuffers, ws, stream=None):
+        b = db.c()
+        o = out.c()
+        self._check(self.lib.xrd_pattern_batch(self.h, C.byref(b), C.byref(opts), C.byref(o), C.c_void_p(ws.data_ptr()),
+                                               C.c_size_t(ws.numel() * ws.element_size()), _stream_ptr(stream)))
+
+    def set_profiling(self, on: bool):
+        self._check(self.lib.xrd_set_profiling(self.h, 1 if on else 0))
+
+    def stage_times(self):
+        buf = (C.c_float * len(STAGES))()
+        n = self.lib.xrd_stage_times(self.h, buf, len(STAGES))
+        if n < 0:
+            raise XrdError(-n, self.lib.xrd_last_error(self.h).decode())
+        return {STAGES[i]: float(buf[i]) for i in range(n)}
+
+
+def workspace(nbytes: int, device="cuda"):
+    """Device workspace (256-byte aligned: torch allocations are 512-byte aligned)."""
+    torch = _torch()
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+def compute(batch, opts, precision="fp32_phasefix", handle: Handle = None, device: int = 0):
+    """One-shot convenience: upload a host batch, size, run and download the patterns."""
+    torch = _torch()
+    h = handle or Handle(device)
+    dev = "cuda:%d" % device
+    db = DeviceBatch.from_host(batch, dev)
+    o = make_opts(opts, precision)
+    sz = h.query_sizes(db, o)
+    out = PatternBuffers(db.n_struct, sz.n_refl, dev)
+    ws = workspace(sz.ws_bytes, dev)
+    h.pattern_batch(db, o, out, ws)
+    torch.cuda.synchronize(device)
+    res = out.to_host()
+    res["sizes"] = {"n_refl": sz.n_refl, "max_refl": sz.max_refl, "n_tiles": sz.n_tiles, "ws_bytes": sz.ws_bytes}
+    return res

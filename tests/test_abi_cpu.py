@@ -1,0 +1,97 @@
+"""Host-side checks of the C ABI: the library builds, loads without a GPU, exports
+every entry point declared in include/xrd.h, and the ctypes mirrors of the C
+structs have the C layout."""
+import ctypes as C
+import os
+import re
+import subprocess
+import tempfile
+
+import pytest
+
+from paper_2602_11709_gb300 import build as pkg_build
+from paper_2602_11709_gb300 import xrd
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "xrd.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    pkg_build.build()
+    return xrd.load()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(xrd_[a-z_]+)\s*\(", text)))
+
+
+def test_exports_every_declared_entry_point(lib):
+    names = declared_functions()
+    assert {"xrd_create", "xrd_destroy", "xrd_last_error", "xrd_query_sizes", "xrd_pattern_batch"} <= set(names)
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(xrd.EXPORTS) <= set(names)
+
+
+def test_struct_layouts_match_c():
+    src = r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "xrd.h"
+#define F(T, m) printf("%s.%s %zu\n", #T, #m, offsetof(T, m))
+int main(void) {
+  printf("xrd_batch %zu\nxrd_opts %zu\nxrd_sizes %zu\nxrd_pattern %zu\n", sizeof(xrd_batch), sizeof(xrd_opts),
+         sizeof(xrd_sizes), sizeof(xrd_pattern));
+  F(xrd_batch, n_atoms); F(xrd_batch, coef); F(xrd_opts, scaled); F(xrd_opts, reserved);
+  F(xrd_sizes, ws_bytes); F(xrd_pattern, fam_off); F(xrd_pattern, totals);
+  return 0;
+}
+'''
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        open(c, "w").write(src)
+        exe = os.path.join(d, "t")
+        subprocess.run(["gcc", "-I" + os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+        out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = dict(line.split() for line in out if line.strip())
+    assert int(got["xrd_batch"]) == C.sizeof(xrd.xrd_batch)
+    assert int(got["xrd_opts"]) == C.sizeof(xrd.xrd_opts)
+    assert int(got["xrd_sizes"]) == C.sizeof(xrd.xrd_sizes)
+    assert int(got["xrd_pattern"]) == C.sizeof(xrd.xrd_pattern)
+    assert int(got["xrd_batch.n_atoms"]) == xrd.xrd_batch.n_atoms.offset
+    assert int(got["xrd_batch.coef"]) == xrd.xrd_batch.coef.offset
+    assert int(got["xrd_opts.scaled"]) == xrd.xrd_opts.scaled.offset
+    assert int(got["xrd_opts.reserved"]) == xrd.xrd_opts.reserved.offset
+    assert int(got["xrd_sizes.ws_bytes"]) == xrd.xrd_sizes.ws_bytes.offset
+    assert int(got["xrd_pattern.fam_off"]) == xrd.xrd_pattern.fam_off.offset
+    assert int(got["xrd_pattern.totals"]) == xrd.xrd_pattern.totals.offset
+
+
+def test_create_without_gpu_fails_cleanly(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = C.c_void_p()
+    rc = lib.xrd_create(C.byref(h), 0)
+    assert rc in (xrd.XRD_ECUDA, xrd.XRD_EINVAL) and not h.value
+    assert lib.xrd_last_error(None) == b"NULL handle"
+
+
+def test_null_handle_arguments(lib):
+    assert lib.xrd_query_sizes(None, None, None, None, None) == xrd.XRD_EINVAL
+    assert lib.xrd_pattern_batch(None, None, None, None, None, 0, None) == xrd.XRD_EINVAL
+    assert lib.xrd_set_profiling(None, 1) == xrd.XRD_EINVAL
+    lib.xrd_destroy(None)
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    saved = xrd._lib
+    try:
+        xrd._lib = None
+        with pytest.raises(RuntimeError):
+            xrd.load(str(tmp_path / "nope.so"))
+    finally:
+        xrd._lib = saved

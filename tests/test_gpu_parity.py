@@ -1,0 +1,223 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2602_11709_gb300 import synth
+
+from parity import compare_batch, families
+
+pytestmark = pytest.mark.gpu
+
+PRECS = ["fp64", "fp32_phase64", "fp32_phasefix"]
+REPORT = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out", "parity_stats.jsonl")
+
+
+def _report(name, stats):
+    try:
+        os.makedirs(os.path.dirname(REPORT), exist_ok=True)
+        with open(REPORT, "a") as f:
+            f.write(json.dumps({"test": name, **{k: (float(v) if isinstance(v, (np.floating, float)) else v)
+                                                  for k, v in stats.items()}}) + "\n")
+    except OSError:
+        pass
+
+
+@pytest.fixture(scope="module")
+def handle(gpu_lib):
+    h = gpu_lib.Handle(0)
+    yield h
+    h.close()
+
+
+def _opts(base, **kw):
+    o = synth.Opts(base.wavelength, base.tt_min, base.tt_max, base.tt_tol, base.rel_cutoff, base.scaled)
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_nacl(gpu_lib, handle, prec):
+    b, o = synth.nacl()
+    ref = oracle.pattern_batch(b, o, threads=1)
+    got = gpu_lib.compute(b, o, prec, handle=handle)
+    st = compare_batch(got, ref, prec, o.rel_cutoff, o.scaled)
+    assert st["boundary"] == 0 and st["pairs"] == 9
+    assert got["sizes"]["n_refl"] == 293  # 586 reflections, one per Friedel pair
+    assert [families(got, 0, p) for p in range(9)][1] == [((2, 0, 0), 6)]
+    _report("nacl_" + prec, st)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_small_batch_full_size(gpu_lib, handle, prec):
+    """All 1024 structures of the small-cell workload (the benchmark's batch)."""
+    b, o = synth.small()
+    ref = oracle.pattern_batch(b, o, threads=0)
+    got = gpu_lib.compute(b, o, prec, handle=handle)
+    assert got["sizes"]["n_refl"] * 2 == int(ref["n_refl"].sum())
+    st = compare_batch(got, ref, prec, o.rel_cutoff, o.scaled)
+    _report("small_" + prec, st)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_phasefix"])
+@pytest.mark.parametrize("variant", ["nocut_unscaled", "range_5_120", "wide_tol"])
+def test_options(gpu_lib, handle, prec, variant):
+    b, o = synth.small(n=96)
+    if variant == "nocut_unscaled":
+        o = _opts(o, rel_cutoff=0.0, scaled=0)
+    elif variant == "range_5_120":
+        o = _opts(o, tt_min=5.0, tt_max=120.0, wavelength=0.71073)
+    else:
+        o = _opts(o, tt_tol=0.05)
+    ref = oracle.pattern_batch(b, o, threads=0)
+    got = gpu_lib.compute(b, o, prec, handle=handle)
+    st = compare_batch(got, ref, prec, o.rel_cutoff, o.scaled)
+    _report("options_%s_%s" % (variant, prec), st)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_large_cells(gpu_lib, handle, prec):
+    """Large cells (more reflections than one CTA keeps in shared memory)."""
+    b, o = synth.large(n=256)
+    counts = np.diff(b.atom_off)
+    idx = np.argsort(counts)[:2]
+    sub = b.subset(idx)
+    ref = oracle.pattern_batch(sub, o, threads=0)
+    got = gpu_lib.compute(sub, o, prec, handle=handle)
+    assert got["sizes"]["max_refl"] > 2048
+    st = compare_batch(got, ref, prec, o.rel_cutoff, o.scaled)
+    _report("large_" + prec, st)
+
+
+def test_mixed_sample(gpu_lib, handle):
+    b, o = synth.mixed(n=100_000)
+    sub = b.subset(np.arange(3000))
+    ref = oracle.pattern_batch(sub, o, threads=0)
+    got = gpu_lib.compute(sub, o, "fp32_phasefix", handle=handle)
+    st = compare_batch(got, ref, "fp32_phasefix", o.rel_cutoff, o.scaled)
+    _report("mixed3000_fp32_phasefix", st)
+
+
+def test_determinism(gpu_lib, handle):
+    b, o = synth.small(n=200)
+    r1 = gpu_lib.compute(b, o, "fp32_phasefix", handle=handle)
+    r2 = gpu_lib.compute(b, o, "fp32_phasefix", handle=handle)
+    for key in ("peak_tt", "peak_I", "fam_hkl", "fam_mult"):
+        for s in range(b.n_struct):
+            assert np.array_equal(r1[key][s], r2[key][s])
+
+
+def test_edge_cases(gpu_lib, handle):
+    nacl, o = synth.nacl()
+    rng = np.random.default_rng(77)
+    empty_atoms = synth.Batch(nacl.lattice.copy(), np.array([0, 0], np.int64), np.zeros((0, 3)),
+                              np.zeros(0, np.int16), np.zeros(0), np.zeros(0), nacl.coef)
+    bad_cell = synth.Batch(np.array([[5.0, 5.0, 5.0, 60.0, 60.0, 120.0]]), nacl.atom_off.copy(), nacl.frac.copy(),
+                           nacl.Z.copy(), nacl.occ.copy(), nacl.B.copy(), nacl.coef)
+    bad_z = synth.Batch(nacl.lattice.copy(), nacl.atom_off.copy(), nacl.frac.copy(),
+                        np.array([11, 11, 11, 11, 17, 17, 17, 99], np.int16), nacl.occ.copy(), nacl.B.copy(),
+                        nacl.coef)
+    nan_x = synth.Batch(nacl.lattice.copy(), nacl.atom_off.copy(), nacl.frac.copy(), nacl.Z.copy(), nacl.occ.copy(),
+                        nacl.B.copy(), nacl.coef)
+    nan_x.frac[3, 1] = np.nan
+    neg_occ = synth.Batch(nacl.lattice.copy(), nacl.atom_off.copy(), nacl.frac.copy(), nacl.Z.copy(),
+                          nacl.occ.copy(), nacl.B.copy(), nacl.coef)
+    neg_occ.occ[2] = -0.5
+    rand = synth.random_cell(rng, 5)
+    rand.coef = nacl.coef
+    batch = synth.concat([nacl, empty_atoms, bad_cell, bad_z, nan_x, neg_occ, rand])
+    got = gpu_lib.compute(batch, o, "fp32_phasefix", handle=handle)
+    st = list(got["status"])
+    assert st == [0, 0, 1, 1, 1, 1, 0]
+    assert got["totals"][3] == 4
+    assert len(got["peak_tt"][0]) == 9
+    assert len(got["peak_tt"][1]) == 0  # no atoms: every merged peak is 0 and cut off
+    for s in (2, 3, 4, 5):
+        assert len(got["peak_tt"][s]) == 0
+    ref = oracle.pattern_batch(batch.subset([0, 6]), o)
+    sub = {k: [v[0], v[6]] for k, v in got.items() if isinstance(v, list)}
+    sub["status"] = [got["status"][0], got["status"][6]]
+    compare_batch(sub, ref, "fp32_phasefix", o.rel_cutoff, o.scaled)
+    # without a cutoff the atom-free structure keeps its zero peaks
+    o0 = _opts(o, rel_cutoff=0.0)
+    got0 = gpu_lib.compute(batch.subset([1]), o0, "fp32_phasefix", handle=handle)
+    assert len(got0["peak_tt"][0]) == 23 and np.all(got0["peak_I"][0] == 0.0)
+    # no reflection in range
+    onone = _opts(o, tt_max=5.0)
+    gotn = gpu_lib.compute(nacl, onone, "fp64", handle=handle)
+    assert gotn["sizes"]["n_refl"] == 0 and len(gotn["peak_tt"][0]) == 0 and gotn["status"][0] == 0
+
+
+def test_empty_batch(gpu_lib, handle):
+    nacl, o = synth.nacl()
+    b = nacl.subset(np.zeros(0, np.int64))
+    got = gpu_lib.compute(b, o, "fp32_phasefix", handle=handle)
+    assert got["totals"][0] == 0 and got["totals"][1] == 0 and len(got["peak_tt"]) == 0
+
+
+def test_capacity_errors(gpu_lib, handle):
+    import torch
+    xrd = gpu_lib
+    b, o = synth.small(n=16)
+    db = xrd.DeviceBatch.from_host(b)
+    co = xrd.make_opts(o, "fp32_phasefix")
+    sz = handle.query_sizes(db, co)
+    # workspace with room for only half of the reflections: the device flags every structure
+    out = xrd.PatternBuffers(b.n_struct, sz.n_refl)
+    small_ws = xrd.workspace(sz.ws_bytes - 40 * sz.n_refl)
+    handle.pattern_batch(db, co, out, small_ws)
+    torch.cuda.synchronize()
+    assert np.all(out.status.cpu().numpy() == xrd.XRD_ECAPACITY)
+    assert int(out.totals[3]) == b.n_struct
+    # too small an output: flagged as well
+    out2 = xrd.PatternBuffers(b.n_struct, 10)
+    ws = xrd.workspace(sz.ws_bytes)
+    handle.pattern_batch(db, co, out2, ws)
+    torch.cuda.synchronize()
+    assert np.all(out2.status.cpu().numpy() == xrd.XRD_ECAPACITY)
+    # host-side argument errors
+    with pytest.raises(xrd.XrdError) as e:
+        handle.pattern_batch(db, xrd.make_opts(synth.Opts(wavelength=-1.0)), out, ws)
+    assert e.value.code == xrd.XRD_EINVAL
+    with pytest.raises(xrd.XrdError) as e:
+        handle.pattern_batch(db, co, out, xrd.workspace(64))
+    assert e.value.code == xrd.XRD_ECAPACITY
+
+
+@pytest.mark.parametrize("prec", ["fp32_phasefix", "fp64"])
+def test_large_full_size_sampled(gpu_lib, handle, prec):
+    """All 256 large cells in one launch; single-family peaks checked one by one
+    against the oracle's structure factor, plus size invariants."""
+    b, o = synth.large()
+    if prec == "fp64":
+        b = b.subset(np.arange(24))
+    o = _opts(o, rel_cutoff=0.0, scaled=0)
+    got = gpu_lib.compute(b, o, prec, handle=handle)
+    assert np.all(got["status"] == 0)
+    rng = np.random.default_rng(5)
+    lam = o.wavelength
+    worst = 0.0
+    for s in rng.choice(b.n_struct, size=6, replace=False):
+        tt, I, fo = got["peak_tt"][s], got["peak_I"][s], got["peak_fam_off"][s]
+        assert np.all(np.diff(tt) > 0)
+        hkl_full, _ = oracle.enumerate_refl(b.lattice[s], o)
+        assert int(got["fam_mult"][s].sum()) == len(hkl_full)
+        imax = I.max()
+        _, Gs, _ = oracle.metric(b.lattice[s])
+        picks = [p for p in rng.choice(len(tt), size=40, replace=False) if fo[p + 1] - fo[p] == 1
+                 and got["fam_mult"][s][fo[p]] == 2]
+        for p in picks[:15]:
+            h, k, l = (int(x) for x in got["fam_hkl"][s][fo[p]])
+            q = oracle.q_of(Gs, h, k, l)
+            s2, ttr, lp, d = oracle.refl(q, lam)
+            F = oracle.sf(b, s, h, k, l, s2)
+            Iref = 2 * abs(F) ** 2 * lp
+            assert abs(tt[p] - ttr) <= 1e-6
+            worst = max(worst, abs(I[p] - Iref) / imax)
+            assert abs(I[p] - Iref) <= (1e-5 if prec != "fp64" else 1e-9) * imax, (s, p, I[p], Iref)
+    _report("large_full_sampled_" + prec, {"max_abs_rel_to_max": worst})
