@@ -139,6 +139,34 @@ int xrd_pattern_batch(xrd_handle* h, const xrd_batch* batch, const xrd_opts* opt
 int xrd_set_profiling(xrd_handle* h, int enabled);
 int xrd_stage_times(xrd_handle* h, float* ms, int n);
 
+/*
+ * Allocation-free variant of xrd_pattern_batch (the paper has no counterpart:
+ * it is an interface for callers that may not allocate device memory, such as
+ * code running under a framework-owned memory pool, plug-ins whose host forbids
+ * cudaMalloc, or loops where an allocation's implicit synchronisation is not
+ * acceptable). It computes exactly what xrd_pattern_batch computes, with the
+ * same inputs and caller-owned outputs, but its scratch space is a fixed
+ * file-scope device array of XRD_NOALLOC_SCRATCH_BYTES instead of a workspace.
+ *  - Nothing is allocated by the call: no cudaMalloc, no cudaFree, no
+ *    allocating library routine.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress, which may load the module); make that first call
+ *    before any stream capture on that device. The array then stays reserved
+ *    on every device that used it until the process exits.
+ *  - Limit: the per-structure and per-atom arrays (about 110 bytes per
+ *    structure and 72 bytes per atom) plus about 105 bytes per Friedel-unique
+ *    reflection must fit in 64 MiB. A batch whose per-structure and per-atom
+ *    part does not fit is rejected on the host with XRD_ECAPACITY; one whose
+ *    reflections do not fit is flagged on the device (status XRD_ECAPACITY for
+ *    every structure, totals[3] = n_struct), as with a short workspace.
+ *  - All calls share the array and it keeps the last call's contents; the call
+ *    clears what must start at zero. Calls that overlap on the GPU (several
+ *    streams or host threads at once) race on it: serialise them.
+ */
+#define XRD_NOALLOC_SCRATCH_BYTES (64u << 20)
+int xrd_pattern_batch_noalloc(xrd_handle* h, const xrd_batch* batch, const xrd_opts* opts, const xrd_pattern* out,
+                              void* stream /* cudaStream_t */);
+
 #ifdef __cplusplus
 }
 #endif

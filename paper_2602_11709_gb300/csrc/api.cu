@@ -183,6 +183,15 @@ xrd::GeomArgs geom_args(const xrd_batch* b, const xrd_opts* o, const Layout& L, 
 
 }  // namespace
 
+namespace xrd {
+int handle_device(const xrd_handle* h) { return h ? h->device : -1; }
+int set_error(xrd_handle* h, int code, const char* msg)
+{
+    if (h) h->err = msg;
+    return code;
+}
+}  // namespace xrd
+
 extern "C" {
 
 int xrd_create(xrd_handle** h, int device)

@@ -107,4 +107,8 @@ size_t post_smem_bytes(int cap);
 void launch_post(const PostArgs& a, cudaStream_t st);
 void launch_compact(const CompactArgs& a, cudaStream_t st);
 
+// handle accessors for entry points defined outside api.cu
+int handle_device(const xrd_handle* h);
+int set_error(xrd_handle* h, int code, const char* msg);
+
 }  // namespace xrd

@@ -45,7 +45,7 @@ class xrd_pattern(C.Structure):
 
 
 EXPORTS = ["xrd_create", "xrd_destroy", "xrd_last_error", "xrd_query_sizes", "xrd_pattern_batch",
-           "xrd_set_profiling", "xrd_stage_times"]
+           "xrd_set_profiling", "xrd_stage_times", "xrd_pattern_batch_noalloc"]
 
 _lib = None
 
@@ -74,6 +74,9 @@ def load(path: str = LIB_PATH):
     L.xrd_set_profiling.restype = C.c_int
     L.xrd_stage_times.argtypes = [C.c_void_p, C.POINTER(C.c_float), C.c_int]
     L.xrd_stage_times.restype = C.c_int
+    L.xrd_pattern_batch_noalloc.argtypes = [C.c_void_p, C.POINTER(xrd_batch), C.POINTER(xrd_opts),
+                                            C.POINTER(xrd_pattern), C.c_void_p]
+    L.xrd_pattern_batch_noalloc.restype = C.c_int
     _lib = L
     return L
 
@@ -221,6 +224,19 @@ class Handle:
         o = out.c()
         self._check(self.lib.xrd_pattern_batch(self.h, C.byref(b), C.byref(opts), C.byref(o), C.c_void_p(ws.data_ptr()),
                                                C.c_size_t(ws.numel() * ws.element_size()), _stream_ptr(stream)))
+
+    def pattern_batch_noalloc(self, db: DeviceBatch, opts: xrd_opts, out: PatternBuffers, stream=None):
+        """xrd_pattern_batch on the library's fixed 64 MiB device scratch: no workspace, no allocation.
+
+        For callers that may not allocate device memory when they need a pattern
+        (a framework owns the memory pool, the host application forbids
+        cudaMalloc, or an allocation's synchronisation would stall other work).
+        Calls share the scratch: do not overlap them on the GPU.
+        """
+        b = db.c()
+        o = out.c()
+        self._check(self.lib.xrd_pattern_batch_noalloc(self.h, C.byref(b), C.byref(opts), C.byref(o),
+                                                       _stream_ptr(stream)))
 
     def set_profiling(self, on: bool):
         self._check(self.lib.xrd_set_profiling(self.h, 1 if on else 0))
