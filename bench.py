@@ -56,7 +56,7 @@ class ClockSampler:
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -66,6 +66,14 @@ class ClockSampler:
     def _read(self):
         for line in self.proc.stdout:
             self.lines.append(line.strip())
+
+    def wait_first(self, timeout=5.0):
+        """nvidia-smi's start-up stalls the driver: let it finish before timing."""
+        t0 = time.time()
+        while self.proc and not self.lines and time.time() - t0 < timeout:
+            time.sleep(0.05)
+        time.sleep(0.3)
+        self.mark = len(self.lines)
 
     def stop(self):
         if not self.proc:
@@ -78,7 +86,7 @@ class ClockSampler:
             self.proc.kill()
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in self.lines[getattr(self, "mark", 0):]:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -191,12 +199,13 @@ def run_ours(args):
                                 species * (4.0 / MUFU_EX2_PER_CLK))).sum())
 
     h.set_profiling(True)
+    clocks = ClockSampler(dev)
+    clocks.start()
+    clocks.wait_first()
     for _ in range(args.warmup):
         flush.fill_(1.0)
         h.pattern_batch(db, co, out, ws)
     barrier()
-    clocks = ClockSampler(dev)
-    clocks.start()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     sf_ms = []
     stage_acc = {}
@@ -297,7 +306,7 @@ def run_ours(args):
             "e2e": {"value": terms_full / e2e_s, "unit": "terms/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_s * 1e3},
             "clocks": ck,
-            "gpu_launches": 10 * args.steps,
+            "gpu_launches": xrd.LAUNCHES_PER_BATCH * args.steps,
             "stage_ms": {k: v / args.steps for k, v in stage_acc.items()},
             "other_precisions": extra,
         }
@@ -312,7 +321,7 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32_phasefix", choices=["fp64", "fp32_phase64", "fp32_phasefix"])

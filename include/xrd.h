@@ -154,7 +154,7 @@ int xrd_stage_times(xrd_handle* h, float* ms, int n);
  *    before any stream capture on that device. The array then stays reserved
  *    on every device that used it until the process exits.
  *  - Limit: the per-structure and per-atom arrays (about 110 bytes per
- *    structure and 72 bytes per atom) plus about 105 bytes per Friedel-unique
+ *    structure and 72 bytes per atom) plus about 100 bytes per Friedel-unique
  *    reflection must fit in 64 MiB. A batch whose per-structure and per-atom
  *    part does not fit is rejected on the host with XRD_ECAPACITY; one whose
  *    reflections do not fit is flagged on the device (status XRD_ECAPACITY for

@@ -21,7 +21,7 @@ struct xrd_handle {
 
 namespace {
 
-constexpr int kTile = 128;      // reflections per structure-factor CTA
+constexpr int kTile = 256;      // reflections per structure-factor tile (64 threads x 4)
 constexpr int kPostCap = 2048;  // reflections per structure kept in shared memory by k_post
 constexpr int kStages = 8;
 
@@ -55,8 +55,8 @@ size_t al(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Byte offsets of every array in the caller's workspace.
 struct Layout {
-    size_t geo, refl_cnt, refl_off, tile_off, npk, nfm, fam_soff, flags, coef32, atom32, atom64;
-    size_t q, key, I, g_tt, g_perm, g_bkt, g_flag, g_pstart, g_psum, g_fcnt;
+    size_t geo, refl_cnt, refl_off, tile_off, order, npk, nfm, fam_soff, flags, coef32, atom32, atom64;
+    size_t q, key, I, g_perm, g_bkt, g_flag, g_pstart, g_psum, g_fcnt;
     size_t st_tt, st_I, st_d, st_foff, st_hkl, st_mult;
     size_t total;
 };
@@ -70,6 +70,7 @@ Layout layout(int64_t n, int64_t natoms, int zmax, int64_t R)
     L.refl_cnt = take(8 * n);
     L.refl_off = take(8 * (n + 1));
     L.tile_off = take(4 * (n + 1));
+    L.order = take(4 * n);
     L.npk = take(8 * n);
     L.nfm = take(8 * n);
     L.fam_soff = take(8 * (n + 1));
@@ -80,7 +81,6 @@ Layout layout(int64_t n, int64_t natoms, int zmax, int64_t R)
     L.q = take(8 * R);
     L.key = take(4 * R);
     L.I = take(8 * R);
-    L.g_tt = take(8 * R);
     L.g_perm = take(4 * R);
     L.g_bkt = take(4 * (R + n));
     L.g_flag = take(R);
@@ -122,7 +122,7 @@ int check_opts(xrd_handle* h, const xrd_opts* o)
     if (!(o->rel_cutoff >= 0.0 && o->rel_cutoff < 1.0)) return fail(h, XRD_EINVAL, "rel_cutoff must be in [0, 1)");
     if (o->scaled != 0 && o->scaled != 1) return fail(h, XRD_EINVAL, "scaled must be 0 or 1");
     if (o->precision < XRD_FP64 || o->precision > XRD_FP32_PHASEFIX) return fail(h, XRD_EINVAL, "unknown precision");
-    if (o->tile != -1 && o->tile != kTile) return fail(h, XRD_EINVAL, "tile must be -1 or 128");
+    if (o->tile != -1 && o->tile != kTile) return fail(h, XRD_EINVAL, "tile must be -1 or 256");
     if (o->reserved != 0) return fail(h, XRD_EINVAL, "reserved must be 0");
     return XRD_OK;
 }
@@ -173,6 +173,7 @@ xrd::GeomArgs geom_args(const xrd_batch* b, const xrd_opts* o, const Layout& L, 
     g.refl_cnt = (int64_t*)(ws + L.refl_cnt);
     g.refl_off = (int64_t*)(ws + L.refl_off);
     g.tile_off = (int*)(ws + L.tile_off);
+    g.order = (int*)(ws + L.order);
     g.abort_flag = (int*)(ws + L.flags);
     g.totals = totals;
     g.status = status;
@@ -211,6 +212,9 @@ int xrd_create(xrd_handle** h, int device)
         e = cudaEventCreate(&p->ev[i]);
         if (e != cudaSuccess) { delete p; return XRD_ECUDA; }
     }
+    xrd::init_tables(0);  // device tables (2-theta), once per handle, on the legacy stream
+    e = cudaStreamSynchronize(0);
+    if (e != cudaSuccess) { delete p; return XRD_ECUDA; }
     *h = p;
     return XRD_OK;
 }
@@ -348,12 +352,15 @@ int xrd_pattern_batch(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, cons
     xrd::SfArgs sa{};
     sa.n_struct = (int)n;
     sa.precision = o->precision;
+    sa.zmax = b->zmax;
     sa.tile = kTile;
-    sa.grid = h->sms * 12;
+    sa.grid = h->sms;
     sa.lambda = o->lambda;
     sa.atom_off = b->atom_off;
     sa.refl_off = ga.refl_off;
     sa.tile_off = ga.tile_off;
+    sa.order = ga.order;
+    sa.tile_counter = ga.abort_flag + 2;
     sa.abort_flag = ga.abort_flag;
     sa.coef32 = ga.coef32;
     sa.coef = b->coef;
@@ -375,12 +382,17 @@ int xrd_pattern_batch(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, cons
     pa.cutoff = o->rel_cutoff;
     pa.r2min = ga.r2min;
     pa.r2max = ga.r2max;
+    pa.l2d = o->lambda * o->lambda * 0.25;
+    pa.tolf = (float)o->tt_tol;
+    pa.lo3 = (float)(ga.r2min * std::sqrt(ga.r2min));
+    pa.hi3 = (float)(ga.r2max * std::sqrt(ga.r2max));
+    pa.l2f = (float)pa.l2d;
+    pa.lhf = (float)(o->lambda * 0.5);
     pa.refl_off = ga.refl_off;
     pa.abort_flag = ga.abort_flag;
     pa.q = ga.q;
     pa.key = ga.key;
     pa.I = sa.I;
-    pa.g_tt = (double*)(ws + L.g_tt);
     pa.g_perm = (int*)(ws + L.g_perm);
     pa.g_bkt = (int*)(ws + L.g_bkt);
     pa.g_flag = (uint8_t*)(ws + L.g_flag);

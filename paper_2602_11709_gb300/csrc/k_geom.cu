@@ -36,7 +36,8 @@ __global__ void k_prep(const double* __restrict__ lattice, int n, double rmax, G
     Geo g;
     g.status = XRD_OK;
     g.H = g.K = g.L = -1;
-    for (int i = 0; i < 6; i++) g.gs[i] = 0.0;
+    for (int i = 0; i < 6; i++) { g.gs[i] = 0.0; g.gf[i] = 0.f; }
+    for (int i = 0; i < 3; i++) g.g2[i] = 0.0;
     const bool finite = isfinite(a) && isfinite(b) && isfinite(c) && isfinite(al) && isfinite(be) && isfinite(ga);
     if (!finite || !(a > 0.0 && b > 0.0 && c > 0.0)) {
         g.status = XRD_EINVAL;
@@ -71,6 +72,8 @@ __global__ void k_prep(const double* __restrict__ lattice, int n, double rmax, G
     g.gs[3] = __ddiv_rn(C12, det);
     g.gs[4] = __ddiv_rn(C13, det);
     g.gs[5] = __ddiv_rn(C23, det);
+    for (int i = 0; i < 3; i++) g.g2[i] = 2.0 * g.gs[3 + i];  // exact
+    for (int i = 0; i < 6; i++) g.gf[i] = (float)g.gs[i];
     g.H = (int)floor(__dmul_rn(rmax, a)) + 1;
     g.K = (int)floor(__dmul_rn(rmax, b)) + 1;
     g.L = (int)floor(__dmul_rn(rmax, c)) + 1;
@@ -175,28 +178,80 @@ __device__ __forceinline__ double q_exact(const double* gs, int h, int k, int l)
     return __dadd_rn(diag, __dmul_rn(2.0, off));
 }
 
-// The l interval of column (h, k) that can hold |g|^2 <= r2max, widened by one
-// on each side; every l in it is then tested exactly.
-__device__ __forceinline__ void column_range(const Geo& g, int h, int k, double r2max, int& lo, int& hi)
+// The l interval of column (h, k) that can hold |g|^2 <= r2max, computed in
+// FP32 and widened by two on each side (a superset: every l in it is tested).
+__device__ __forceinline__ void column_range(const float* gf, int L, int h, int k, float r2maxf, int& lo, int& hi)
 {
-    const double A = g.gs[0] * (double)(h * h) + g.gs[1] * (double)(k * k) + 2.0 * g.gs[3] * (double)(h * k);
-    const double b = g.gs[4] * (double)h + g.gs[5] * (double)k;
-    const double R = r2max * (1.0 + 1e-9) + 1e-12;
-    const double disc = b * b - g.gs[2] * (A - R);
+    const float fh = (float)h, fk = (float)k;
+    const float A = fmaf(gf[0] * fh, fh, fmaf(gf[1] * fk, fk, 2.f * gf[3] * fh * fk));
+    const float b = fmaf(gf[4], fh, gf[5] * fk);
+    const float R = r2maxf * 1.0001f;
+    const float c = A - R;
+    float disc = fmaf(b, b, -gf[2] * c);
+    const float mag = fmaf(b, b, gf[2] * fabsf(c));
     lo = 1;
     hi = 0;
-    if (disc < 0.0) return;
-    const double sq = sqrt(disc);
-    lo = (int)floor((-b - sq) / g.gs[2]) - 1;
-    hi = (int)ceil((-b + sq) / g.gs[2]) + 1;
-    if (lo < -g.L) lo = -g.L;
-    if (hi > g.L) hi = g.L;
+    if (disc < -1e-4f * mag) return;
+    disc = fmaxf(disc, 0.f);
+    const float sq = sqrtf(disc);
+    const float inv = 1.f / gf[2];
+    lo = (int)floorf((-b - sq) * inv) - 2;
+    hi = (int)ceilf((-b + sq) * inv) + 2;
+    if (lo < -L) lo = -L;
+    if (hi > L) hi = L;
     if (h == 0 && k == 0 && lo < 1) lo = 1;  // half-space: (0, 0, l > 0)
 }
 
+// Canonical |g|^2 along one column (h, k): the products and sums of the fixed
+// order ((G11 hh + G22 kk) + G33 ll) + 2((G12 hk + G13 hl) + G23 kl), with the
+// column's constant parts formed once; the doubled off-diagonal coefficients
+// give exactly the doubled sum. Bit-identical to q_exact.
+struct ColumnQ {
+    double t1, t2, g33, g13, g23;
+    int h, k;
+    __device__ ColumnQ(const Geo& g, int h_, int k_) : h(h_), k(k_)
+    {
+        t1 = __dadd_rn(__dmul_rn(g.gs[0], i2d_exact(h * h)), __dmul_rn(g.gs[1], i2d_exact(k * k)));
+        t2 = __dmul_rn(g.g2[0], i2d_exact(h * k));
+        g33 = g.gs[2];
+        g13 = g.g2[1];
+        g23 = g.g2[2];
+    }
+    __device__ __forceinline__ double at(int l) const
+    {
+        const double diag = __dadd_rn(t1, __dmul_rn(g33, i2d_exact(l * l)));
+        const double off = __dadd_rn(__dadd_rn(t2, __dmul_rn(g13, i2d_exact(h * l))), __dmul_rn(g23, i2d_exact(k * l)));
+        return __dadd_rn(diag, off);
+    }
+};
+
+// Inside test of one (h, k, l): an FP32 evaluation decides every candidate
+// farther than a bound on its rounding error from the sphere surfaces; the rest
+// take the exact FP64 test. Returns 1 (inside), 0 (outside).
+__device__ __forceinline__ int inside(const Geo& g, int h, int k, int l, double r2min, double r2max, float r2minf,
+                                      float r2maxf)
+{
+    const float* gf = g.gf;
+    const float hh = (float)(h * h), kk = (float)(k * k), ll = (float)(l * l);
+    const float hk = (float)(h * k), hl = (float)(h * l), kl = (float)(k * l);
+    const float diag = fmaf(gf[2], ll, fmaf(gf[1], kk, gf[0] * hh));
+    const float o1 = gf[3] * hk, o2 = gf[4] * hl, o3 = gf[5] * kl;
+    const float qf = fmaf(2.f, o1 + o2 + o3, diag);
+    const float qa = fmaf(2.f, fabsf(o1) + fabsf(o2) + fabsf(o3), diag);
+    const float m = 4e-6f * qa + 1e-30f;
+    if (qf > r2maxf + m || qf < r2minf - m) return 0;
+    if (qf < r2maxf - m && qf > r2minf + m) return 1;
+    const double q = q_exact(g.gs, h, k, l);
+    return (q >= r2min && q <= r2max) ? 1 : 0;
+}
+
+// Count (EMIT = false) or write (EMIT = true) the reflections of one structure.
+// Each thread takes columns (h, k) in a strided order; when emitting, a block
+// scan of the per-thread counts gives every thread a fixed output range, so
+// the emitted order is deterministic and no atomics are needed.
 template <bool EMIT>
-__device__ void enumerate_struct(const Geo& g, double r2min, double r2max, int64_t base, int64_t cap,
-                                 double* __restrict__ qo, uint32_t* __restrict__ ko, int* counter)
+__device__ int enumerate_struct(const Geo& g, double r2min, double r2max, float r2minf, float r2maxf, int64_t base,
+                                int64_t cap, double* __restrict__ qo, uint32_t* __restrict__ ko, int* tmp)
 {
     const int nk = 2 * g.K + 1;
     const int ncol = (g.H + 1) * nk;
@@ -205,101 +260,156 @@ __device__ void enumerate_struct(const Geo& g, double r2min, double r2max, int64
         const int h = c / nk, k = c % nk - g.K;
         if (h == 0 && k < 0) continue;  // half-space: h > 0, or h = 0 and k >= 0
         int lo, hi;
-        column_range(g, h, k, r2max, lo, hi);
+        column_range(g.gf, g.L, h, k, r2maxf, lo, hi);
+        for (int l = lo; l <= hi; l++) local += inside(g, h, k, l, r2min, r2max, r2minf, r2maxf);
+    }
+    if (!EMIT) return local;
+    // exclusive offset of this thread's reflections within the structure
+    const int nw = blockDim.x >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int inc = warp_incl_scan(local);
+    if (lane == 31) tmp[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        const int sv = lane < nw ? tmp[lane] : 0;
+        const int si = warp_incl_scan(sv);
+        if (lane < nw) tmp[lane] = si - sv;
+    }
+    __syncthreads();
+    int pos = tmp[w] + inc - local;
+    for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
+        const int h = c / nk, k = c % nk - g.K;
+        if (h == 0 && k < 0) continue;
+        int lo, hi;
+        column_range(g.gf, g.L, h, k, r2maxf, lo, hi);
+        const ColumnQ cq(g, h, k);
         for (int l = lo; l <= hi; l++) {
-            const double q = q_exact(g.gs, h, k, l);
-            if (q < r2min || q > r2max) continue;
-            if (EMIT) {
-                const int pos = atomicAdd(counter, 1);
-                if (pos < cap) {
-                    qo[base + pos] = q;
-                    ko[base + pos] = hkl_pack(h, k, l);
-                }
-            } else {
-                local++;
+            if (!inside(g, h, k, l, r2min, r2max, r2minf, r2maxf)) continue;
+            if (pos < cap) {
+                qo[base + pos] = cq.at(l);
+                ko[base + pos] = hkl_pack(h, k, l);
             }
+            pos++;
         }
     }
-    if (!EMIT) atomicAdd(counter, local);
+    return local;
 }
 
 __global__ void __launch_bounds__(256) k_count(const Geo* __restrict__ geo, double r2min, double r2max,
-                                               int64_t* __restrict__ cnt)
+                                               float r2minf, float r2maxf, int64_t* __restrict__ cnt)
 {
-    __shared__ int n;
+    __shared__ int tmp[34];
     const int s = blockIdx.x;
     const Geo g = geo[s];
-    if (threadIdx.x == 0) n = 0;
-    __syncthreads();
-    if (g.status == XRD_OK && g.H >= 0) enumerate_struct<false>(g, r2min, r2max, 0, 0, nullptr, nullptr, &n);
-    __syncthreads();
+    int local = 0;
+    if (g.status == XRD_OK && g.H >= 0)
+        local = enumerate_struct<false>(g, r2min, r2max, r2minf, r2maxf, 0, 0, nullptr, nullptr, tmp);
+    const int n = block_sum_int(local, tmp);
     if (threadIdx.x == 0) cnt[s] = n;
 }
 
 __global__ void __launch_bounds__(256) k_emit(const Geo* __restrict__ geo, double r2min, double r2max,
-                                              const int64_t* __restrict__ refl_off, const int* __restrict__ abort_flag,
-                                              double* __restrict__ q, uint32_t* __restrict__ key)
+                                              float r2minf, float r2maxf, const int64_t* __restrict__ refl_off,
+                                              const int* __restrict__ abort_flag, double* __restrict__ q,
+                                              uint32_t* __restrict__ key)
 {
-    __shared__ int n;
+    __shared__ int tmp[34];
     if (*abort_flag) return;
     const int s = blockIdx.x;
     const Geo g = geo[s];
-    if (threadIdx.x == 0) n = 0;
-    __syncthreads();
     const int64_t base = refl_off[s], cap = refl_off[s + 1] - base;
-    if (g.status == XRD_OK && g.H >= 0) enumerate_struct<true>(g, r2min, r2max, base, cap, q, key, &n);
+    if (g.status == XRD_OK && g.H >= 0 && cap > 0)
+        enumerate_struct<true>(g, r2min, r2max, r2minf, r2maxf, base, cap, q, key, tmp);
 }
 
-// Exclusive scans of the per-structure reflection counts and tile counts by a
-// single block; flags a capacity overflow when the total exceeds the workspace.
+// Single block: exclusive scan of the per-structure reflection counts, the
+// largest-first order of structures (counting sort on the atom count, which
+// sets the cost of a structure-factor tile) and the scan of tiles in that
+// order; flags a capacity overflow when the total exceeds the workspace.
+constexpr int kOrderBins = 4096;
+
 __global__ void __launch_bounds__(1024) k_scan_refl(const int64_t* __restrict__ cnt, const Geo* __restrict__ geo,
-                                                    int n, int tile, int64_t cap_refl, int64_t* __restrict__ refl_off,
-                                                    int* __restrict__ tile_off, int* __restrict__ abort_flag,
-                                                    int64_t* __restrict__ totals, int32_t* __restrict__ status)
+                                                    const int64_t* __restrict__ atom_off, int n, int tile,
+                                                    int64_t cap_refl, int64_t* __restrict__ refl_off,
+                                                    int* __restrict__ tile_off, int* __restrict__ order,
+                                                    int* __restrict__ abort_flag, int64_t* __restrict__ totals,
+                                                    int32_t* __restrict__ status)
 {
     __shared__ long long ws[32];
-    __shared__ long long wt[32];
-    __shared__ long long carry_r, carry_t;
+    __shared__ long long carry;
+    __shared__ int bins[kOrderBins];
+    __shared__ int tmp[34];
+    __shared__ int nbad;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    if (threadIdx.x == 0) { carry_r = 0; carry_t = 0; }
+    // 1. reflection offsets in structure order (64-bit scan)
+    if (threadIdx.x == 0) carry = 0;
     __syncthreads();
     for (int base = 0; base < n; base += blockDim.x) {
         const int i = base + threadIdx.x;
         const long long v = i < n ? cnt[i] : 0;
-        const long long t = i < n ? (v + tile - 1) / tile : 0;
-        long long iv = v, it = t;
+        long long iv = v;
         for (int o = 1; o < 32; o <<= 1) {
-            const long long a = __shfl_up_sync(0xffffffffu, iv, o);
-            const long long b = __shfl_up_sync(0xffffffffu, it, o);
-            if (lane >= o) { iv += a; it += b; }
+            const long long t = __shfl_up_sync(0xffffffffu, iv, o);
+            if (lane >= o) iv += t;
         }
-        if (lane == 31) { ws[w] = iv; wt[w] = it; }
+        if (lane == 31) ws[w] = iv;
         __syncthreads();
         if (w == 0) {
-            long long a = lane < nw ? ws[lane] : 0, b = lane < nw ? wt[lane] : 0;
-            long long ia = a, ib = b;
+            const long long a0 = lane < nw ? ws[lane] : 0;
+            long long ia = a0;
             for (int o = 1; o < 32; o <<= 1) {
-                const long long x = __shfl_up_sync(0xffffffffu, ia, o);
-                const long long y = __shfl_up_sync(0xffffffffu, ib, o);
-                if (lane >= o) { ia += x; ib += y; }
+                const long long t = __shfl_up_sync(0xffffffffu, ia, o);
+                if (lane >= o) ia += t;
             }
-            if (lane < nw) { ws[lane] = ia - a; wt[lane] = ib - b; }
+            if (lane < nw) ws[lane] = ia - a0;
         }
         __syncthreads();
-        if (i < n) {
-            refl_off[i] = carry_r + ws[w] + iv - v;
-            tile_off[i] = (int)(carry_t + wt[w] + it - t);
-        }
+        if (i < n) refl_off[i] = carry + ws[w] + iv - v;
         __syncthreads();
-        if (threadIdx.x == blockDim.x - 1) { carry_r += ws[w] + iv; carry_t += wt[w] + it; }
+        if (threadIdx.x == blockDim.x - 1) carry += ws[w] + iv;
         __syncthreads();
     }
-    __shared__ int nbad;
-    const int over = carry_r > cap_refl;
+    const long long total = carry;
+    // 2. largest-first order: counting sort on (kOrderBins - 1 - min(atoms, kOrderBins - 1))
+    for (int b = threadIdx.x; b < kOrderBins; b += blockDim.x) bins[b] = 0;
+    __syncthreads();
+    for (int s = threadIdx.x; s < n; s += blockDim.x) {
+        const long long na = atom_off[s + 1] - atom_off[s];
+        const int key = kOrderBins - 1 - (int)min(max(na, 0LL), (long long)(kOrderBins - 1));
+        atomicAdd(&bins[key], 1);
+    }
+    __syncthreads();
+    block_excl_scan(bins, kOrderBins, tmp);
+    __syncthreads();
+    for (int s = threadIdx.x; s < n; s += blockDim.x) {
+        const long long na = atom_off[s + 1] - atom_off[s];
+        const int key = kOrderBins - 1 - (int)min(max(na, 0LL), (long long)(kOrderBins - 1));
+        order[atomicAdd(&bins[key], 1)] = s;
+    }
+    __syncthreads();
+    // 3. tile offsets in that order (int scan; totals fit 32 bits)
+    int tcarry = 0;
+    for (int base = 0; base < n; base += blockDim.x) {
+        const int i = base + threadIdx.x;
+        const int v = i < n ? (int)((cnt[order[i]] + tile - 1) / tile) : 0;
+        const int inc = warp_incl_scan(v);
+        if (lane == 31) tmp[w] = inc;
+        __syncthreads();
+        if (w == 0) {
+            const int sv = lane < nw ? tmp[lane] : 0;
+            const int si = warp_incl_scan(sv);
+            if (lane < nw) tmp[lane] = si - sv;
+            if (lane == 31) tmp[32] = si;
+        }
+        __syncthreads();
+        if (i < n) tile_off[i] = tcarry + tmp[w] + inc - v;
+        tcarry += tmp[32];
+        __syncthreads();
+    }
+    const int over = total > cap_refl;
     if (threadIdx.x == 0) {
-        refl_off[n] = carry_r;
-        tile_off[n] = (int)carry_t;
-        totals[0] = carry_r;
+        refl_off[n] = total;
+        tile_off[n] = over ? 0 : tcarry;
+        totals[0] = total;
         totals[1] = 0;
         totals[2] = 0;
         *abort_flag = over;
@@ -335,23 +445,26 @@ void launch_count_only(const GeomArgs& a, cudaStream_t st)
     const int n = a.n_struct;
     if (n <= 0) return;
     k_prep<<<(n + 127) / 128, 128, 0, st>>>(a.lattice, n, a.rmax, a.geo);
-    k_count<<<n, 256, 0, st>>>(a.geo, a.r2min, a.r2max, a.refl_cnt);
+    k_count<<<n, 256, 0, st>>>(a.geo, a.r2min, a.r2max, (float)a.r2min, (float)a.r2max, a.refl_cnt);
 }
 
 void launch_count(const GeomArgs& a, cudaStream_t st)
 {
-    if (a.n_struct > 0) k_count<<<a.n_struct, 256, 0, st>>>(a.geo, a.r2min, a.r2max, a.refl_cnt);
+    if (a.n_struct > 0)
+        k_count<<<a.n_struct, 256, 0, st>>>(a.geo, a.r2min, a.r2max, (float)a.r2min, (float)a.r2max, a.refl_cnt);
 }
 
 void launch_scan_refl(const GeomArgs& a, cudaStream_t st)
 {
-    k_scan_refl<<<1, 1024, 0, st>>>(a.refl_cnt, a.geo, a.n_struct, a.tile, a.cap_refl, a.refl_off, a.tile_off,
-                                    a.abort_flag, a.totals, a.status);
+    k_scan_refl<<<1, 1024, 0, st>>>(a.refl_cnt, a.geo, a.atom_off, a.n_struct, a.tile, a.cap_refl, a.refl_off,
+                                    a.tile_off, a.order, a.abort_flag, a.totals, a.status);
 }
 
 void launch_emit(const GeomArgs& a, cudaStream_t st)
 {
-    if (a.n_struct > 0) k_emit<<<a.n_struct, 256, 0, st>>>(a.geo, a.r2min, a.r2max, a.refl_off, a.abort_flag, a.q, a.key);
+    if (a.n_struct > 0)
+        k_emit<<<a.n_struct, 256, 0, st>>>(a.geo, a.r2min, a.r2max, (float)a.r2min, (float)a.r2max, a.refl_off,
+                                           a.abort_flag, a.q, a.key);
 }
 
 }  // namespace xrd

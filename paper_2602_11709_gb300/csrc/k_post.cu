@@ -20,14 +20,96 @@
 namespace xrd {
 
 constexpr int kPostThreads = 256;
+constexpr int kCapSmall = 1536;   // reflections per structure held in shared memory, small class
+constexpr int kCapLarge = 6144;   // large class (one CTA per SM); larger structures use global scratch
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
 size_t post_smem_bytes(int cap)
 {
     const size_t c = (size_t)cap;
-    return align16(c * 8) + align16(c * 4) + align16(c * 8) + align16(c * 4) + align16((c + 1) * 4) +
-           align16(c) + align16(c * 4) + align16(c * 8) + align16(c * 4);
+    // q, key, perm (16 bit), bucket ends, flags, peak starts, peak sums, family counts
+    return align16(c * 8) + align16(c * 4) + align16(c * 2) + align16((c + 1) * 4) + align16(c) + align16(c * 4) +
+           align16(c * 8) + align16(c * 4);
+}
+
+// ---- 2-theta of a reflection from |g|^2 without FP64 transcendentals ----
+// theta in [0, pi/4] is found from a table at theta_j = j * pi / 4096 (2theta_j =
+// j * 360 / 4096 degrees, exact in binary) and a few FP32 Newton steps on the
+// small remainder u = 2 (theta - theta_j); angles above 45 degrees use the
+// complement (sin^2 theta = 1 - sin^2(90 - theta)). Error about 1e-8 degrees.
+constexpr int kTabN = 1024;
+struct TTab {
+    double S;   // sin^2 theta_j
+    float A;    // sin 2 theta_j
+    float Bc;   // cos 2 theta_j
+};
+static __device__ TTab g_ttab[kTabN + 1];
+constexpr double kTabStepDeg = 360.0 / 4096.0;  // 2theta spacing of the table
+
+__global__ void k_ttab_init()
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j > kTabN) return;
+    const double th = (j * kTabStepDeg) * (kPi / 360.0);
+    const double sn = sin(th);
+    TTab t;
+    t.S = sn * sn;
+    t.A = (float)sin(2.0 * th);
+    t.Bc = (float)cos(2.0 * th);
+    g_ttab[j] = t;
+}
+
+void init_tables(cudaStream_t st) { k_ttab_init<<<(kTabN + 1 + 255) / 256, 256, 0, st>>>(); }
+
+__device__ __forceinline__ float d2f_signed(double x)
+{
+    const float m = x == 0.0 ? 0.f : d2f_pos(fabs(x));
+    return x < 0.0 ? -m : m;
+}
+
+// 2theta in degrees of a reflection with sin^2 theta = X (FP64, 0 < X <= 1)
+__device__ double two_theta_of(double X)
+{
+    const bool comp = X > 0.5;
+    const double Y = comp ? 1.0 - X : X;  // exact for X in (0.5, 1]
+    const float Yf = Y > 0.0 ? d2f_pos(Y) : 0.f;
+    const float th0 = asinf(sqrtf(Yf));
+    int j = __float2int_rn(th0 * (float)(4.0 * kTabN / kPi));
+    j = min(max(j, 0), kTabN);
+    double t;
+    if (j <= 2) {
+        t = f2d_fast(th0 * (float)(360.0 / kPi));
+    } else {
+        const TTab e = g_ttab[j];
+        const float r = d2f_signed(Y - e.S);
+        float u = 4.f * r / (e.A + sqrtf(fmaf(4.f * e.Bc, r, e.A * e.A)));
+#pragma unroll
+        for (int it = 0; it < 2; it++) {
+            const float u2 = u * u;
+            const float su = u - u * u2 * (1.f / 6.f);
+            const float cu = u2 * (0.5f - u2 * (1.f / 24.f));
+            const float fv = fmaf(e.A, su, fmaf(e.Bc, cu, -2.f * r));
+            const float fp = fmaf(e.A, 1.f - 0.5f * u2, e.Bc * su);
+            u -= fv / fp;
+        }
+        t = (double)j * kTabStepDeg + f2d_fast(u * (float)(180.0 / kPi));
+    }
+    return comp ? 180.0 - t : t;
+}
+
+// 2theta(qb) - 2theta(qa) in degrees for qb >= qa > 0, to about 1e-6 relative:
+// asin xb - asin xa = 2 atan((xb - xa) / (cb + ca)), x = lambda sqrt(q) / 2,
+// c = sqrt(1 - x^2), xb - xa = (lambda / 2)(qb - qa) / (sqrt qb + sqrt qa), and
+// qb - qa is exact in FP64 for close values.
+__device__ __forceinline__ float tt_gap(double qa, double qb, float l2, float lh)
+{
+    if (dbits(qb) <= dbits(qa)) return 0.f;
+    const float dqf = d2f_pos(qb - qa);
+    const float qaf = d2f_pos(qa), qbf = d2f_pos(qb);
+    const float dx = lh * dqf / (sqrtf(qaf) + sqrtf(qbf));
+    const float ca = sqrtf(fmaxf(fmaf(-l2, qaf, 1.f), 0.f)), cb = sqrtf(fmaxf(fmaf(-l2, qbf, 1.f), 0.f));
+    return 4.f * atanf(dx / (ca + cb)) * (float)(180.0 / kPi);
 }
 
 // family key: |h|, |k|, |l| sorted descending, packed
@@ -44,65 +126,21 @@ __device__ __forceinline__ uint32_t family_key(uint32_t key)
 // sort order: ascending |g|^2, ties by descending (h, k, l)
 __device__ __forceinline__ bool before(double qa, uint32_t ka, double qb, uint32_t kb)
 {
-    return qa < qb || (qa == qb && ka > kb);
+    const unsigned long long a = dbits(qa), b = dbits(qb);  // q > 0: bit order is numeric order
+    return a < b || (a == b && ka > kb);
 }
 
-__global__ void __launch_bounds__(kPostThreads) k_post(const PostArgs a)
+template <typename PermT>
+__device__ void post_structure(const PostArgs& a, int s, int64_t base, int n, const double* q, const uint32_t* key,
+                               PermT* perm, int* bkt, uint8_t* flag, int* pst, double* psum, int* fcnt, int* tmp,
+                               double* dtmp)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int tmp[34];
-    __shared__ double dtmp[32];
-    if (*a.abort_flag) return;
-    const int s = blockIdx.x;
-    const int64_t base = a.refl_off[s];
-    const int n = (int)(a.refl_off[s + 1] - base);
     const int tid = threadIdx.x, nt = blockDim.x;
-    if (n == 0) {
-        if (tid == 0) { a.npk[s] = 0; a.nfm[s] = 0; }
-        return;
-    }
     const double* __restrict__ Ig = a.I + base;
-    const double* q;
-    const uint32_t* key;
-    double* tt;
-    int* perm;
-    int* bkt;
-    uint8_t* flag;
-    int* pst;
-    double* psum;
-    int* fcnt;
-    if (n <= a.cap_smem) {
-        const size_t c = (size_t)a.cap_smem;
-        unsigned char* p = smem;
-        double* sq = (double*)p; p += align16(c * 8);
-        uint32_t* sk = (uint32_t*)p; p += align16(c * 4);
-        tt = (double*)p; p += align16(c * 8);
-        perm = (int*)p; p += align16(c * 4);
-        bkt = (int*)p; p += align16((c + 1) * 4);
-        flag = (uint8_t*)p; p += align16(c);
-        pst = (int*)p; p += align16(c * 4);
-        psum = (double*)p; p += align16(c * 8);
-        fcnt = (int*)p;
-        for (int i = tid; i < n; i += nt) {
-            sq[i] = a.q[base + i];
-            sk[i] = a.key[base + i];
-        }
-        q = sq;
-        key = sk;
-    } else {
-        q = a.q + base;
-        key = a.key + base;
-        tt = a.g_tt + base;
-        perm = a.g_perm + base;
-        bkt = a.g_bkt + base + s;
-        flag = a.g_flag + base;
-        pst = a.g_pstart + base;
-        psum = a.g_psum + base;
-        fcnt = a.g_fcnt + base;
-    }
+    const float l2 = a.l2f, lh = a.lhf;
     // ---- bucket sort on |g|^3 in [r2min^1.5, r2max^1.5] ----
     const int nb = n;
-    const float lo3 = (float)(a.r2min * sqrt(a.r2min)), hi3 = (float)(a.r2max * sqrt(a.r2max));
+    const float lo3 = a.lo3, hi3 = a.hi3;
     const float scale = (float)nb / (hi3 - lo3);
     for (int i = tid; i <= nb; i += nt) bkt[i] = 0;
     __syncthreads();
@@ -119,7 +157,7 @@ __global__ void __launch_bounds__(kPostThreads) k_post(const PostArgs a)
         const float qf = d2f_pos(q[i]);
         int b = (int)((qf * sqrtf(qf) - lo3) * scale);
         b = min(max(b, 0), nb - 1);
-        perm[atomicAdd(&bkt[b], 1)] = i;
+        perm[atomicAdd(&bkt[b], 1)] = (PermT)i;
     }
     __syncthreads();
     for (int b = tid; b < nb; b += nt) {  // bkt[b] is now the end of bucket b
@@ -133,28 +171,23 @@ __global__ void __launch_bounds__(kPostThreads) k_post(const PostArgs a)
                 perm[j + 1] = perm[j];
                 j--;
             }
-            perm[j + 1] = v;
+            perm[j + 1] = (PermT)v;
         }
     }
     __syncthreads();
-    // ---- 2-theta of every reflection in sorted order (Bragg's law) ----
-    for (int i = tid; i < n; i += nt) {
-        double sth = a.lambda * sqrt(q[perm[i]]) / 2.0;
-        if (sth > 1.0) sth = 1.0;
-        tt[i] = 2.0 * asin(sth) * (180.0 / kPi);
-    }
-    __syncthreads();
-    // ---- anchor merge ----
-    for (int i = tid; i < n; i += nt) flag[i] = (i == 0) || !(tt[i] - tt[i - 1] < a.tol);
+    // ---- anchor merge: definite starts, then one thread per run ----
+    for (int i = tid; i < n; i += nt)
+        flag[i] = (i == 0) || !(tt_gap(q[perm[i - 1]], q[perm[i]], l2, lh) < a.tolf);
     __syncthreads();
     for (int i = tid; i < n; i += nt) {
         if (!flag[i]) continue;
-        int anchor = i;
+        double qa = q[perm[i]];
         pst[i] = 1;
         for (int j = i + 1; j < n && !flag[j]; j++) {
-            if (!(tt[j] - tt[anchor] < a.tol)) {
+            const double qj = q[perm[j]];
+            if (!(tt_gap(qa, qj, l2, lh) < a.tolf)) {
                 pst[j] = 1;
-                anchor = j;
+                qa = qj;
             } else {
                 pst[j] = 0;
             }
@@ -171,7 +204,7 @@ __global__ void __launch_bounds__(kPostThreads) k_post(const PostArgs a)
     if (tid == 0) bkt[np] = n;
     __syncthreads();
     // ---- per peak: merged intensity (each half-space reflection stands for g and -g) and family count ----
-    double lmax = 0.0;
+    unsigned long long lmax = 0;  // peak sums are >= 0: max through the bit patterns
     for (int p = tid; p < np; p += nt) {
         const int i0 = bkt[p], i1 = bkt[p + 1];
         double sum = 0.0;
@@ -185,12 +218,16 @@ __global__ void __launch_bounds__(kPostThreads) k_post(const PostArgs a)
         }
         psum[p] = sum;
         fcnt[p] = nfam;
-        lmax = fmax(lmax, sum);
+        lmax = max(lmax, dbits(sum));
     }
-    const double imax = block_max_double(lmax, dtmp);
+    const double imax = __longlong_as_double((long long)block_max_u64(lmax, (unsigned long long*)dtmp));
+    const unsigned long long thr = dbits(a.cutoff * imax);
+    if (tid == 0) dtmp[0] = imax > 0.0 ? 1.0 / imax : 0.0;
+    __syncthreads();
+    const double inv_imax = dtmp[0];
     // ---- cutoff, then compaction offsets of kept peaks and their families ----
     for (int p = tid; p < np; p += nt) {
-        const bool keep = a.cutoff == 0.0 || psum[p] > a.cutoff * imax;
+        const bool keep = a.cutoff == 0.0 || dbits(psum[p]) > thr;
         flag[p] = keep;
         pst[p] = keep;
         if (!keep) fcnt[p] = 0;
@@ -199,13 +236,17 @@ __global__ void __launch_bounds__(kPostThreads) k_post(const PostArgs a)
     const int nk = block_excl_scan(pst, np, tmp);
     const int nf = block_excl_scan(fcnt, np, tmp);
     __syncthreads();
+    const double l2d = a.l2d;
     for (int p = tid; p < np; p += nt) {
         if (!flag[p]) continue;
         const int i0 = bkt[p], i1 = bkt[p + 1];
         const int64_t o = base + pst[p];
-        a.st_tt[o] = tt[i0];
-        a.st_d[o] = 1.0 / sqrt(q[perm[i0]]);
-        a.st_I[o] = (a.scaled && imax > 0.0) ? 100.0 * (psum[p] / imax) : psum[p];
+        const double qa = q[perm[i0]];
+        a.st_tt[o] = two_theta_of(fmin(qa * l2d, 1.0));
+        const double y0 = f2d_fast(rsqrtf(d2f_pos(qa)));  // d = 1/sqrt(q): FP32 seed, one FP64 Newton step
+        a.st_d[o] = y0 * fma(-0.5 * qa * y0, y0, 1.5);
+        const double ps = psum[p];  // the largest peak maps to exactly 100
+        a.st_I[o] = (a.scaled && imax > 0.0) ? (ps == imax ? 100.0 : 100.0 * (ps * inv_imax)) : ps;
         a.st_foff[o] = fcnt[p];
         // families: leaders are first members of each family; rank by descending representative
         for (int i = i0; i < i1; i++) {
@@ -239,6 +280,46 @@ __global__ void __launch_bounds__(kPostThreads) k_post(const PostArgs a)
     if (tid == 0) {
         a.npk[s] = nk;
         a.nfm[s] = nf;
+    }
+}
+
+// One CTA per structure. CAP > 0: structures with cap_lo < n <= CAP, in shared
+// memory. CAP == 0: structures with n > cap_lo, on global scratch.
+template <int CAP, int NT>
+__global__ void __launch_bounds__(NT) k_post(const PostArgs a, int cap_lo)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int tmp[34];
+    __shared__ double dtmp[32];
+    if (*a.abort_flag) return;
+    const int s = blockIdx.x;
+    const int64_t base = a.refl_off[s];
+    const int n = (int)(a.refl_off[s + 1] - base);
+    if (CAP > 0 && cap_lo == 0 && n == 0) {  // the smallest class also writes empty structures
+        if (threadIdx.x == 0) { a.npk[s] = 0; a.nfm[s] = 0; }
+        return;
+    }
+    if (n <= cap_lo || (CAP > 0 && n > CAP)) return;
+    if (CAP > 0) {
+        const size_t c = (size_t)CAP;
+        unsigned char* p = smem;
+        double* sq = (double*)p; p += align16(c * 8);
+        uint32_t* sk = (uint32_t*)p; p += align16(c * 4);
+        uint16_t* perm = (uint16_t*)p; p += align16(c * 2);
+        int* bkt = (int*)p; p += align16((c + 1) * 4);
+        uint8_t* flag = (uint8_t*)p; p += align16(c);
+        int* pst = (int*)p; p += align16(c * 4);
+        double* psum = (double*)p; p += align16(c * 8);
+        int* fcnt = (int*)p;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            sq[i] = a.q[base + i];
+            sk[i] = a.key[base + i];
+        }
+        __syncthreads();
+        post_structure<uint16_t>(a, s, base, n, sq, sk, perm, bkt, flag, pst, psum, fcnt, tmp, dtmp);
+    } else {
+        post_structure<int>(a, s, base, n, a.q + base, a.key + base, a.g_perm + base, a.g_bkt + base + s,
+                            a.g_flag + base, a.g_pstart + base, a.g_psum + base, a.g_fcnt + base, tmp, dtmp);
     }
 }
 
@@ -296,38 +377,57 @@ __global__ void __launch_bounds__(1024) k_scan_out(const CompactArgs a)
         for (int s = threadIdx.x; s < n; s += blockDim.x) a.out.status[s] = XRD_ECAPACITY;
 }
 
-__global__ void __launch_bounds__(128) k_compact(const CompactArgs a)
+__global__ void __launch_bounds__(256) k_compact(const CompactArgs a)
 {
     if (*a.abort_flag || *a.out_abort) return;
     const int s = blockIdx.x;
     const int64_t base = a.refl_off[s], pb = a.out.peak_off[s], fb = a.fam_soff[s];
     const int64_t np = a.npk[s], nf = a.nfm[s];
+    const double* __restrict__ stt = a.st_tt + base;
+    const double* __restrict__ sI = a.st_I + base;
+    const double* __restrict__ sd = a.st_d + base;
+    const int* __restrict__ sfo = a.st_foff + base;
+    const int* __restrict__ shkl = a.st_hkl + 3 * base;
+    const int* __restrict__ smul = a.st_mult + base;
+    double* __restrict__ ott = a.out.two_theta + pb;
+    double* __restrict__ oI = a.out.intensity + pb;
+    double* __restrict__ od = a.out.d_hkl + pb;
+    int64_t* __restrict__ ofo = a.out.fam_off + pb;
+    int* __restrict__ ohkl = a.out.hkl + 3 * fb;
+    int* __restrict__ omul = a.out.mult + fb;
     for (int64_t p = threadIdx.x; p < np; p += blockDim.x) {
-        a.out.two_theta[pb + p] = a.st_tt[base + p];
-        a.out.intensity[pb + p] = a.st_I[base + p];
-        a.out.d_hkl[pb + p] = a.st_d[base + p];
-        a.out.fam_off[pb + p] = fb + a.st_foff[base + p];
+        const double t = stt[p], I = sI[p], d = sd[p];
+        const int fo = sfo[p];
+        ott[p] = t;
+        oI[p] = I;
+        od[p] = d;
+        ofo[p] = fb + fo;
     }
-    for (int64_t f = threadIdx.x; f < nf; f += blockDim.x) {
-        a.out.hkl[3 * (fb + f)] = a.st_hkl[3 * (base + f)];
-        a.out.hkl[3 * (fb + f) + 1] = a.st_hkl[3 * (base + f) + 1];
-        a.out.hkl[3 * (fb + f) + 2] = a.st_hkl[3 * (base + f) + 2];
-        a.out.mult[fb + f] = a.st_mult[base + f];
-    }
+    for (int64_t f = threadIdx.x; f < 3 * nf; f += blockDim.x) ohkl[f] = shkl[f];
+    for (int64_t f = threadIdx.x; f < nf; f += blockDim.x) omul[f] = smul[f];
 }
 
 void launch_post(const PostArgs& a, cudaStream_t st)
 {
     if (a.n_struct <= 0) return;
-    const size_t smem = post_smem_bytes(a.cap_smem);
-    cudaFuncSetAttribute(k_post, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_post<<<a.n_struct, kPostThreads, smem, st>>>(a);
+    const size_t s1 = post_smem_bytes(kCapSmall), s2 = post_smem_bytes(kCapLarge);
+    static bool attr_done[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || !attr_done[dev]) {
+        cudaFuncSetAttribute(k_post<kCapSmall, kPostThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s1);
+        cudaFuncSetAttribute(k_post<kCapLarge, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s2);
+        if (dev >= 0 && dev < 64) attr_done[dev] = true;
+    }
+    k_post<kCapSmall, kPostThreads><<<a.n_struct, kPostThreads, s1, st>>>(a, 0);
+    k_post<kCapLarge, 1024><<<a.n_struct, 1024, s2, st>>>(a, kCapSmall);
+    k_post<0, 1024><<<a.n_struct, 1024, 0, st>>>(a, kCapLarge);
 }
 
 void launch_compact(const CompactArgs& a, cudaStream_t st)
 {
     k_scan_out<<<1, 1024, 0, st>>>(a);
-    if (a.n_struct > 0) k_compact<<<a.n_struct, 128, 0, st>>>(a);
+    if (a.n_struct > 0) k_compact<<<a.n_struct, 256, 0, st>>>(a);
 }
 
 }  // namespace xrd

@@ -7,9 +7,10 @@
 //   f(s) = Z - 41.78214 s^2 sum_i a_i exp(-b_i s^2),  s = |g| / 2,
 //   I = |F|^2 (1 + cos^2 2theta) / (sin^2 theta cos theta),  sin theta = lambda |g| / 2.
 //
-// GB300 mapping: one thread per reflection, a CTA per tile of reflections of
-// one structure, tiles taken round-robin by a persistent grid. All lanes of a
-// warp walk the same atom list (a broadcast load per atom). Atoms are sorted by
+// GB300 mapping: a 64-thread CTA per tile of 256 reflections of one structure,
+// four reflections per thread; a persistent grid takes tiles from an atomic
+// queue in largest-first order. Atoms are staged in shared memory and every
+// lane walks the same atom list (one broadcast read per atom feeds four terms). Atoms are sorted by
 // element, so f(s) is evaluated once per element run (a warp-uniform branch).
 // The FP32 variants use the SFU for sin/cos (MUFU.SIN/COS) and exp2 (MUFU.EX2,
 // which this part issues at twice the sin/cos rate). FP64 arithmetic runs at
@@ -22,7 +23,13 @@ namespace xrd {
 
 constexpr float kTwoPiOver2p32 = 1.4629180792671596e-09f;  // 2 pi / 2^32
 
-__device__ __forceinline__ int tile_struct(const int* __restrict__ tile_off, int n, int t)
+constexpr int kSfThreads = 64;
+constexpr int kSfRB = 4;  // reflections per thread: one atom record feeds four terms
+constexpr int kSfTile = kSfThreads * kSfRB;
+constexpr int kSfChunk = 256;  // atoms staged in shared memory at a time
+
+// position in the largest-first order whose tile range holds tile t
+__device__ __forceinline__ int tile_slot(const int* __restrict__ tile_off, int n, int t)
 {
     int lo = 0, hi = n;  // largest lo with tile_off[lo] <= t
     while (hi - lo > 1) {
@@ -33,93 +40,172 @@ __device__ __forceinline__ int tile_struct(const int* __restrict__ tile_off, int
     return lo;
 }
 
-template <int PREC>
-__global__ void __launch_bounds__(128) k_sf(const SfArgs a)
+__device__ __forceinline__ float f_of(const Coef32& c, int z, float s2)
 {
-    if (*a.abort_flag) return;
-    const int ntiles = a.tile_off[a.n_struct];
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const int s = tile_struct(a.tile_off, a.n_struct, t);
-        const int64_t rb = a.refl_off[s], re = a.refl_off[s + 1];
-        const int64_t r = rb + (int64_t)(t - a.tile_off[s]) * blockDim.x + threadIdx.x;
-        const bool act = r < re;
-        const int64_t rr = act ? r : rb;
-        const double q = a.q[rr];
+    const float e0 = ex2_approx(c.bl[0] * s2), e1 = ex2_approx(c.bl[1] * s2);
+    const float e2 = ex2_approx(c.bl[2] * s2), e3 = ex2_approx(c.bl[3] * s2);
+    return fmaf(s2, fmaf(c.a[0], e0, fmaf(c.a[1], e1, fmaf(c.a[2], e2, c.a[3] * e3))), (float)z);
+}
+
+__device__ __forceinline__ float lp_of(float qf, float l2)
+{
+    const float X = qf * l2;  // sin^2 theta
+    const float c2 = fmaf(-2.f, X, 1.f);
+    return fmaf(c2, c2, 1.f) / (X * sqrtf(1.f - X));
+}
+
+// FP32 variants: RB reflections per thread share each atom record, which is
+// read from shared memory (a broadcast: every lane reads the same record).
+template <int PREC>
+__device__ void sf_tile_fp32(const SfArgs& a, int64_t r0, int64_t re, int64_t j0, int64_t j1, Atom32* sat,
+                             const Coef32* scoef)
+{
+    float s2[kSfRB], qf[kSfRB], Fr[kSfRB], Fi[kSfRB], f[kSfRB];
+    uint32_t uh[kSfRB], uk[kSfRB], ul[kSfRB];
+#pragma unroll
+    for (int i = 0; i < kSfRB; i++) {
+        const int64_t r = r0 + threadIdx.x + i * kSfThreads;
+        const int64_t rr = r < re ? r : r0;
+        qf[i] = d2f_pos(a.q[rr]);
+        s2[i] = qf[i] * 0.25f;
         const uint32_t key = a.key[rr];
-        const int h = hkl_h(key), k = hkl_k(key), l = hkl_l(key);
-        const int64_t j0 = a.atom_off[s], j1 = a.atom_off[s + 1];
-        double I;
-        if (PREC == XRD_FP64) {
-            const double s2 = q * 0.25;
-            double Fr = 0.0, Fi = 0.0, f = 0.0;
-            int zc = -1;
-            for (int64_t j = j0; j < j1; j++) {
-                const Atom64 at = a.atom64[j];
-                if (at.zz != zc) {
-                    zc = at.zz;
-                    const double* c = a.coef + 8 * zc;
-                    const double sum = c[0] * exp(-c[1] * s2) + c[2] * exp(-c[3] * s2) + c[4] * exp(-c[5] * s2) +
-                                       c[6] * exp(-c[7] * s2);
-                    f = (double)zc - kFScale * s2 * sum;
-                }
-                double phi = fma((double)h, at.x, fma((double)k, at.y, (double)l * at.z));
-                phi -= rint(phi);
-                double sn, cs;
-                sincospi(2.0 * phi, &sn, &cs);
-                const double w = at.occ * f * exp(-at.B * s2);
-                Fr = fma(w, cs, Fr);
-                Fi = fma(w, sn, Fi);
+        uh[i] = (uint32_t)hkl_h(key); uk[i] = (uint32_t)hkl_k(key); ul[i] = (uint32_t)hkl_l(key);
+        Fr[i] = 0.f; Fi[i] = 0.f; f[i] = 0.f;
+    }
+    int zc = -1;
+    for (int64_t c0 = j0; c0 < j1; c0 += kSfChunk) {
+        const int nc = (int)min((int64_t)kSfChunk, j1 - c0);
+        __syncthreads();
+        for (int i = threadIdx.x; i < nc; i += kSfThreads) sat[i] = a.atom32[c0 + i];
+        __syncthreads();
+        for (int jj = 0; jj < nc; jj++) {
+            const Atom32 at = sat[jj];
+            if (at.z != zc) {  // uniform: every lane walks the same element-sorted list
+                zc = at.z;
+                const Coef32 c = scoef[zc];
+#pragma unroll
+                for (int i = 0; i < kSfRB; i++) f[i] = f_of(c, zc, s2[i]);
             }
-            const double X = (a.lambda * a.lambda * 0.25) * q;  // sin^2 theta
-            const double c2 = 1.0 - 2.0 * X;                     // cos 2theta
-            const double lp = (1.0 + c2 * c2) / (X * sqrt(1.0 - X));
-            I = (Fr * Fr + Fi * Fi) * lp;
-            if (a.F && act) a.F[r] = make_float2((float)Fr, (float)Fi);
-        } else {
-            const float qf = d2f_pos(q);
-            const float s2 = qf * 0.25f;
-            const uint32_t uh = (uint32_t)h, uk = (uint32_t)k, ul = (uint32_t)l;
-            float Fr = 0.f, Fi = 0.f, f = 0.f;
-            int zc = -1;
-            for (int64_t j = j0; j < j1; j++) {
-                const Atom32 at = a.atom32[j];
-                if (at.z != zc) {
-                    zc = at.z;
-                    const Coef32 c = a.coef32[zc];
-                    const float e0 = ex2_approx(c.bl[0] * s2), e1 = ex2_approx(c.bl[1] * s2);
-                    const float e2 = ex2_approx(c.bl[2] * s2), e3 = ex2_approx(c.bl[3] * s2);
-                    f = fmaf(s2, fmaf(c.a[0], e0, fmaf(c.a[1], e1, fmaf(c.a[2], e2, c.a[3] * e3))), (float)zc);
-                }
+            double dx = 0.0, dy = 0.0, dz = 0.0;
+            if (PREC == XRD_FP32_PHASE64) {
+                const Atom64 d = a.atom64[c0 + jj];
+                dx = d.x; dy = d.y; dz = d.z;
+            }
+#pragma unroll
+            for (int i = 0; i < kSfRB; i++) {
                 uint32_t P;
-                if (PREC == XRD_FP32_PHASEFIX) {
-                    P = uh * at.X + uk * at.Y + ul * at.Z;
-                } else {
-                    const Atom64 d = a.atom64[j];
-                    P = fix32(fma((double)h, d.x, fma((double)k, d.y, (double)l * d.z)));
-                }
+                if (PREC == XRD_FP32_PHASEFIX)
+                    P = uh[i] * at.X + uk[i] * at.Y + ul[i] * at.Z;
+                else
+                    P = fix32(fma((double)(int)uh[i], dx, fma((double)(int)uk[i], dy, (double)(int)ul[i] * dz)));
                 float sn, cs;
                 __sincosf((float)(int32_t)P * kTwoPiOver2p32, &sn, &cs);
-                const float w = f * ex2_approx(fmaf(at.nb, s2, at.lo));
-                Fr = fmaf(w, cs, Fr);
-                Fi = fmaf(w, sn, Fi);
+                const float w = f[i] * ex2_approx(fmaf(at.nb, s2[i], at.lo));
+                Fr[i] = fmaf(w, cs, Fr[i]);
+                Fi[i] = fmaf(w, sn, Fi[i]);
             }
-            const float X = qf * (float)(a.lambda * a.lambda * 0.25);
-            const float c2 = fmaf(-2.f, X, 1.f);
-            const float lp = fmaf(c2, c2, 1.f) / (X * sqrtf(1.f - X));
-            I = f2d_fast((Fr * Fr + Fi * Fi) * lp);
-            if (a.F && act) a.F[r] = make_float2(Fr, Fi);
         }
-        if (act) a.I[r] = I;
+    }
+    const float l2 = (float)(a.lambda * a.lambda * 0.25);
+#pragma unroll
+    for (int i = 0; i < kSfRB; i++) {
+        const int64_t r = r0 + threadIdx.x + i * kSfThreads;
+        if (r >= re) continue;
+        a.I[r] = f2d_fast(fmaf(Fr[i], Fr[i], Fi[i] * Fi[i]) * lp_of(qf[i], l2));
+        if (a.F) a.F[r] = make_float2(Fr[i], Fi[i]);
     }
 }
 
+__device__ void sf_tile_fp64(const SfArgs& a, int64_t r0, int64_t re, int64_t j0, int64_t j1)
+{
+    for (int i = 0; i < kSfRB; i++) {
+        const int64_t r = r0 + threadIdx.x + i * kSfThreads;
+        const bool act = r < re;
+        const int64_t rr = act ? r : r0;
+        const double q = a.q[rr];
+        const uint32_t key = a.key[rr];
+        const int h = hkl_h(key), k = hkl_k(key), l = hkl_l(key);
+        const double s2 = q * 0.25;
+        double Fr = 0.0, Fi = 0.0, f = 0.0;
+        int zc = -1;
+        for (int64_t j = j0; j < j1; j++) {
+            const Atom64 at = a.atom64[j];
+            if (at.zz != zc) {
+                zc = at.zz;
+                const double* c = a.coef + 8 * zc;
+                const double sum = c[0] * exp(-c[1] * s2) + c[2] * exp(-c[3] * s2) + c[4] * exp(-c[5] * s2) +
+                                   c[6] * exp(-c[7] * s2);
+                f = (double)zc - kFScale * s2 * sum;
+            }
+            double phi = fma((double)h, at.x, fma((double)k, at.y, (double)l * at.z));
+            phi -= rint(phi);
+            double sn, cs;
+            sincospi(2.0 * phi, &sn, &cs);
+            const double w = at.occ * f * exp(-at.B * s2);
+            Fr = fma(w, cs, Fr);
+            Fi = fma(w, sn, Fi);
+        }
+        const double X = (a.lambda * a.lambda * 0.25) * q;  // sin^2 theta
+        const double c2 = 1.0 - 2.0 * X;                     // cos 2theta
+        const double lp = (1.0 + c2 * c2) / (X * sqrt(1.0 - X));
+        if (act) {
+            a.I[r] = (Fr * Fr + Fi * Fi) * lp;
+            if (a.F) a.F[r] = make_float2((float)Fr, (float)Fi);
+        }
+    }
+}
+
+// Persistent CTAs take tiles from a queue in largest-first order (tiles of the
+// structures with the most atoms first), so the uneven tail is short.
+template <int PREC>
+__global__ void __launch_bounds__(kSfThreads) k_sf(const SfArgs a)
+{
+    __shared__ int t_sh;
+    __shared__ Atom32 sat[kSfChunk];
+    __shared__ Coef32 scoef[kZmaxLimit + 1];
+    if (*a.abort_flag) return;
+    const int ntiles = a.tile_off[a.n_struct];
+    if (PREC != XRD_FP64)
+        for (int z = threadIdx.x; z <= a.zmax; z += kSfThreads) scoef[z] = a.coef32[z];
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) t_sh = atomicAdd(a.tile_counter, 1);
+        __syncthreads();
+        const int t = t_sh;
+        if (t >= ntiles) break;
+        const int slot = tile_slot(a.tile_off, a.n_struct, t);
+        const int s = a.order[slot];
+        const int64_t rb = a.refl_off[s], re = a.refl_off[s + 1];
+        const int64_t r0 = rb + (int64_t)(t - a.tile_off[slot]) * kSfTile;
+        const int64_t j0 = a.atom_off[s], j1 = a.atom_off[s + 1];
+        if (PREC == XRD_FP64) sf_tile_fp64(a, r0, re, j0, j1);
+        else sf_tile_fp32<PREC>(a, r0, re, j0, j1, sat, scoef);
+    }
+}
+
+template <int PREC>
+static void launch_sf_prec(const SfArgs& a, cudaStream_t st)
+{
+    static int per_sm_cache[64] = {};  // persistent grid: as many CTAs as fit on the SMs at once
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int per_sm = (dev >= 0 && dev < 64) ? per_sm_cache[dev] : 0;
+    if (per_sm < 1) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sf<PREC>, kSfThreads, 0) != cudaSuccess || per_sm < 1)
+            per_sm = 4;
+        if (dev >= 0 && dev < 64) per_sm_cache[dev] = per_sm;
+    }
+    k_sf<PREC><<<a.grid * per_sm, kSfThreads, 0, st>>>(a);
+}
+
+// a.grid = number of SMs
 void launch_sf(const SfArgs& a, cudaStream_t st)
 {
     if (a.n_struct <= 0) return;
     switch (a.precision) {
-    case XRD_FP64: k_sf<XRD_FP64><<<a.grid, 128, 0, st>>>(a); break;
-    case XRD_FP32_PHASE64: k_sf<XRD_FP32_PHASE64><<<a.grid, 128, 0, st>>>(a); break;
-    default: k_sf<XRD_FP32_PHASEFIX><<<a.grid, 128, 0, st>>>(a); break;
+    case XRD_FP64: launch_sf_prec<XRD_FP64>(a, st); break;
+    case XRD_FP32_PHASE64: launch_sf_prec<XRD_FP32_PHASE64>(a, st); break;
+    default: launch_sf_prec<XRD_FP32_PHASEFIX>(a, st); break;
     }
 }
 

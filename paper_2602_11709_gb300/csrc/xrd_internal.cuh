@@ -16,6 +16,8 @@ constexpr int kHklLimit = 511;        // |h|, |k|, |l| fit the 10-bit fields of 
 // Per-structure geometry written by k_prep (step S0).
 struct Geo {
     double gs[6];  // reciprocal metric G* stored as (11, 22, 33, 12, 13, 23)
+    double g2[3];  // 2 G*12, 2 G*13, 2 G*23 (exact doubles of the off-diagonal terms)
+    float gf[6];   // G* rounded to FP32, for the enumeration filter
     int H, K, L;   // enumeration box |h| <= H ...
     int status;    // XRD_OK or XRD_EINVAL
 };
@@ -79,6 +81,21 @@ __device__ __forceinline__ uint32_t fix32(double v)
     return (uint32_t)(unsigned long long)__double_as_longlong(t);
 }
 
+// Exact int -> double by bit assembly (|v| < 2^31); keeps the conversion off
+// the FP64 unit, which this part has little of.
+__device__ __forceinline__ double i2d_exact(int v)
+{
+    if (v == 0) return 0.0;
+    const unsigned long long sign = v < 0 ? 0x8000000000000000ull : 0ull;
+    const unsigned a = v < 0 ? (unsigned)(-v) : (unsigned)v;
+    const int e = 31 - __clz(a);
+    const unsigned long long m = ((unsigned long long)a << (52 - e)) & 0x000FFFFFFFFFFFFFull;
+    return __longlong_as_double((long long)(sign | ((unsigned long long)(1023 + e) << 52) | m));
+}
+
+// Order of non-negative doubles through their bit patterns (integer compare).
+__device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
+
 __device__ __forceinline__ float ex2_approx(float x)
 {
     float y;
@@ -134,6 +151,19 @@ __device__ __forceinline__ double block_max_double(double v, double* tmp)
     __syncthreads();
     double r = tmp[0];
     for (int i = 1; i < nw; i++) r = fmax(r, tmp[i]);
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ unsigned long long block_max_u64(unsigned long long v, unsigned long long* tmp)
+{
+    const int nw = (blockDim.x + 31) >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = max(v, (unsigned long long)__shfl_xor_sync(0xffffffffu, v, o));
+    if (lane == 0) tmp[w] = v;
+    __syncthreads();
+    unsigned long long r = tmp[0];
+    for (int i = 1; i < nw; i++) r = max(r, tmp[i]);
     __syncthreads();
     return r;
 }

@@ -27,6 +27,7 @@ struct GeomArgs {
     int64_t* refl_cnt;
     int64_t* refl_off;
     int* tile_off;
+    int* order;
     int* abort_flag;
     int64_t* totals;
     int32_t* status;
@@ -35,11 +36,13 @@ struct GeomArgs {
 };
 
 struct SfArgs {
-    int n_struct, precision, tile, grid;
+    int n_struct, precision, tile, grid, zmax;
     double lambda;
     const int64_t* atom_off;
     const int64_t* refl_off;
-    const int* tile_off;
+    const int* tile_off;  // [n_struct + 1] exclusive scan of tiles in largest-first order
+    const int* order;     // [n_struct] structures in largest-first order
+    int* tile_counter;    // work-queue head, zeroed by the caller
     const int* abort_flag;
     const Coef32* coef32;
     const double* coef;
@@ -54,13 +57,14 @@ struct SfArgs {
 struct PostArgs {
     int n_struct, cap_smem, scaled;
     double lambda, tol, cutoff, r2min, r2max;
+    double l2d;                          // lambda^2 / 4
+    float tolf, lo3, hi3, l2f, lhf;      // FP32 copies: tol, r2min^1.5, r2max^1.5, lambda^2/4, lambda/2
     const int64_t* refl_off;
     const int* abort_flag;
     const double* q;
     const uint32_t* key;
     const double* I;
     // global scratch for structures larger than cap_smem (indexed by reflection)
-    double* g_tt;
     int* g_perm;
     int* g_bkt;   // n_refl + n_struct entries
     uint8_t* g_flag;
@@ -106,6 +110,7 @@ void launch_sf(const SfArgs& a, cudaStream_t st);
 size_t post_smem_bytes(int cap);
 void launch_post(const PostArgs& a, cudaStream_t st);
 void launch_compact(const CompactArgs& a, cudaStream_t st);
+void init_tables(cudaStream_t st);
 
 // handle accessors for entry points defined outside api.cu
 int handle_device(const xrd_handle* h);

@@ -1,7 +1,7 @@
 """Comparison of CUDA-path patterns with oracle patterns (test helper).
 
 Bar (see the tolerance table of the design notes):
-* peak positions: |d 2theta| <= 1e-6 deg;
+* peak positions: |d 2theta| <= 1e-6 deg; d spacings to 1e-12 relative;
 * hkl families and multiplicities: identical;
 * intensities: |dI| <= tol * I_max for every peak (tol = 1e-5 for the FP32
   variants, 1e-9 for FP64), i.e. relative to the largest peak, the scale on
@@ -54,8 +54,10 @@ def compare_structure(got, ref, s, prec, cutoff, scaled, imax_ref=None):
             ("missing GPU peak", s, k, rt[k], rI[k], thr)
     worst_abs = 0.0
     worst_rel = 0.0
+    gd, rd = np.asarray(got["peak_d"][s]), np.asarray(ref["peak_d"][s])
     for a, b in pairs:
         assert families(got, s, a) == families(ref, s, b), ("families", s, a, families(got, s, a), families(ref, s, b))
+        assert abs(gd[a] - rd[b]) <= 1e-12 * rd[b], ("d spacing", s, a, gd[a], rd[b])
         d = abs(gI[a] - rI[b])
         worst_abs = max(worst_abs, d / imax if imax > 0 else d)
         if rI[b] > 1e-6 * imax:
