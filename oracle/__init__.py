@@ -60,6 +60,10 @@ def lib():
                                            _I64, _I64, _I32]
         _lib.orc_pattern_batch.restype = C.c_int
         _lib.orc_max_threads.restype = C.c_int
+        _lib.orc_broadened.argtypes = [_D, C.c_long, _D, _I16, _D, _D, _D, C.c_double, C.c_long, _I32, C.c_double,
+                                       C.c_double, C.c_int, C.c_double, _D]
+        _lib.orc_broadened_grad.argtypes = [_D, C.c_long, _D, _I16, _D, _D, _D, C.c_double, C.c_long, _I32,
+                                            C.c_double, C.c_double, C.c_int, C.c_double, _D, _D, _D, _D]
     return _lib
 
 
@@ -223,3 +227,35 @@ def pattern_batch(batch, o, threads: int = 0):
 
 def max_threads() -> int:
     return int(lib().orc_max_threads())
+
+
+def _struct_arrays(batch, s):
+    sl = batch.atoms_of(s)
+    return (np.ascontiguousarray(batch.lattice[s], dtype=np.float64), np.ascontiguousarray(batch.frac[sl]),
+            np.ascontiguousarray(batch.Z[sl], dtype=np.int16), np.ascontiguousarray(batch.occ[sl]),
+            np.ascontiguousarray(batch.B[sl]), np.ascontiguousarray(batch.coef, dtype=np.float64))
+
+
+def broadened(batch, s, hkl, lam, grid):
+    """y over the grid for structure s and a fixed full-sphere reflection list hkl[nr][3]."""
+    lat, frac, Z, occ, B, coef = _struct_arrays(batch, s)
+    hkl = np.ascontiguousarray(hkl, dtype=np.int32)
+    y = np.zeros(int(grid.n_pts))
+    lib().orc_broadened(_p(lat, _D), len(Z), _p(frac, _D), _p(Z, _I16), _p(occ, _D), _p(B, _D), _p(coef, _D),
+                        float(lam), len(hkl), _p(hkl, _I32), float(grid.t0), float(grid.dt), int(grid.n_pts),
+                        float(grid.fwhm), _p(y, _D))
+    return y
+
+
+def broadened_grad(batch, s, hkl, lam, grid, dLdy):
+    """(d_frac [n][3], d_B [n], d_lattice [6]) of L = sum(dLdy * y)."""
+    lat, frac, Z, occ, B, coef = _struct_arrays(batch, s)
+    hkl = np.ascontiguousarray(hkl, dtype=np.int32)
+    g = np.ascontiguousarray(dLdy, dtype=np.float64)
+    df = np.zeros((len(Z), 3))
+    dB = np.zeros(len(Z))
+    dl = np.zeros(6)
+    lib().orc_broadened_grad(_p(lat, _D), len(Z), _p(frac, _D), _p(Z, _I16), _p(occ, _D), _p(B, _D), _p(coef, _D),
+                             float(lam), len(hkl), _p(hkl, _I32), float(grid.t0), float(grid.dt), int(grid.n_pts),
+                             float(grid.fwhm), _p(g, _D), _p(df, _D), _p(dB, _D), _p(dl, _D))
+    return df, dB, dl

@@ -335,6 +335,129 @@ int orc_pattern(const double lat[6], long n, const double* frac, const int16_t* 
     return rc;
 }
 
+/* Gaussian width from the full width at half maximum: FWHM = 2 sqrt(2 ln 2) sigma. */
+static double orc_sigma(double fwhm) { return fwhm / (2.0 * sqrt(2.0 * log(2.0))); }
+
+/*
+ * Broadened pattern (the differentiable profile used for refinement and for
+ * training data with peak broadening, Sec. 1): each reflection of the fixed
+ * list adds a unit-height Gaussian of its intensity at its 2-theta.
+ */
+void orc_broadened(const double lat[6], long n, const double* frac, const int16_t* Z, const double* occ,
+                   const double* B, const double* coef, double lambda, long nr, const int32_t* hkl, double t0,
+                   double dt, int npts, double fwhm, double* y)
+{
+    double Gs[6];
+    for (int k = 0; k < npts; k++) y[k] = 0.0;
+    if (orc_metric(lat, NULL, Gs, NULL) != 0) return;
+    const double sg = orc_sigma(fwhm);
+    for (long r = 0; r < nr; r++) {
+        const int h = hkl[3 * r], k = hkl[3 * r + 1], l = hkl[3 * r + 2];
+        double s2, tt, lp, Fr, Fi;
+        orc_refl(orc_q(Gs, h, k, l), lambda, &s2, &tt, &lp, NULL);
+        orc_sf(h, k, l, s2, n, frac, Z, occ, B, coef, &Fr, &Fi);
+        const double I = (Fr * Fr + Fi * Fi) * lp;
+        for (int i = 0; i < npts; i++) {
+            const double u = t0 + i * dt - tt;
+            y[i] += I * exp(-u * u / (2.0 * sg * sg));
+        }
+    }
+}
+
+/* d f(s) / d s^2 = -41.78214 sum_i a_i exp(-b_i s^2) (1 - b_i s^2). */
+static double orc_fprime(const double* coef, int Z, double s2)
+{
+    const double* cz = coef + 8 * Z;
+    double sum = 0.0;
+    for (int i = 0; i < 4; i++) sum += cz[2 * i] * exp(-cz[2 * i + 1] * s2) * (1.0 - cz[2 * i + 1] * s2);
+    return -ORC_F_SCALE * sum;
+}
+
+/* Derivative of the direct metric G with respect to lattice parameter m
+ * (0..2: a, b, c in angstrom; 3..5: alpha, beta, gamma in degrees), as a full 3x3. */
+static void orc_dG(const double lat[6], int m, double D[3][3])
+{
+    const double a = lat[0], b = lat[1], c = lat[2];
+    const double ca = orc_cosd(lat[3]), cb = orc_cosd(lat[4]), cg = orc_cosd(lat[5]);
+    const double rad = M_PI / 180.0;
+    memset(D, 0, sizeof(double) * 9);
+    switch (m) {
+    case 0: D[0][0] = 2 * a; D[0][1] = D[1][0] = b * cg; D[0][2] = D[2][0] = c * cb; break;
+    case 1: D[1][1] = 2 * b; D[0][1] = D[1][0] = a * cg; D[1][2] = D[2][1] = c * ca; break;
+    case 2: D[2][2] = 2 * c; D[0][2] = D[2][0] = a * cb; D[1][2] = D[2][1] = b * ca; break;
+    case 3: D[1][2] = D[2][1] = -b * c * sin(lat[3] * rad) * rad; break;
+    case 4: D[0][2] = D[2][0] = -a * c * sin(lat[4] * rad) * rad; break;
+    default: D[0][1] = D[1][0] = -a * b * sin(lat[5] * rad) * rad; break;
+    }
+}
+
+void orc_broadened_grad(const double lat[6], long n, const double* frac, const int16_t* Z, const double* occ,
+                        const double* B, const double* coef, double lambda, long nr, const int32_t* hkl, double t0,
+                        double dt, int npts, double fwhm, const double* dLdy, double* dfrac, double* dB,
+                        double* dlat)
+{
+    double Gs[6];
+    for (long j = 0; j < 3 * n; j++) dfrac[j] = 0.0;
+    for (long j = 0; j < n; j++) dB[j] = 0.0;
+    for (int m = 0; m < 6; m++) dlat[m] = 0.0;
+    if (orc_metric(lat, NULL, Gs, NULL) != 0) return;
+    const double S[3][3] = {{Gs[0], Gs[3], Gs[4]}, {Gs[3], Gs[1], Gs[5]}, {Gs[4], Gs[5], Gs[2]}};
+    double dG[6][3][3];
+    for (int m = 0; m < 6; m++) orc_dG(lat, m, dG[m]);
+    const double sg = orc_sigma(fwhm);
+    const double l2 = lambda * lambda / 4.0;
+    for (long r = 0; r < nr; r++) {
+        const int hv[3] = {hkl[3 * r], hkl[3 * r + 1], hkl[3 * r + 2]};
+        const double q = orc_q(Gs, hv[0], hv[1], hv[2]);
+        double s2, tt, lp, Fr, Fi;
+        orc_refl(q, lambda, &s2, &tt, &lp, NULL);
+        orc_sf(hv[0], hv[1], hv[2], s2, n, frac, Z, occ, B, coef, &Fr, &Fi);
+        const double I = (Fr * Fr + Fi * Fi) * lp;
+        /* dL/dI and dL/d(2theta) from the Gaussians */
+        double dLdI = 0.0, dLdT = 0.0;
+        for (int i = 0; i < npts; i++) {
+            const double u = t0 + i * dt - tt;
+            const double g = exp(-u * u / (2.0 * sg * sg));
+            dLdI += dLdy[i] * g;
+            dLdT += dLdy[i] * I * g * u / (sg * sg);
+        }
+        /* atoms: dF/dx_j = 2 pi i h w_j e^{i phi_j}, dF/dB_j = -s^2 w_j e^{i phi_j}; dI = 2 lp Re(conj(F) dF) */
+        double dFq_r = 0.0, dFq_i = 0.0; /* dF/dq */
+        for (long j = 0; j < n; j++) {
+            const double f = orc_f(coef, Z[j], s2), dw = exp(-B[j] * s2);
+            const double w = occ[j] * f * dw;
+            const double phi = 2.0 * M_PI * ((double)hv[0] * frac[3 * j] + (double)hv[1] * frac[3 * j + 1] +
+                                             (double)hv[2] * frac[3 * j + 2]);
+            const double c = cos(phi), s = sin(phi);
+            /* Re(conj(F) * i * w e^{i phi}) = w (Fi c - Fr s) */
+            const double im_part = w * (Fi * c - Fr * s);
+            for (int d = 0; d < 3; d++) dfrac[3 * j + d] += dLdI * 2.0 * lp * 2.0 * M_PI * hv[d] * im_part;
+            dB[j] += dLdI * 2.0 * lp * (-s2) * w * (Fr * c + Fi * s);
+            const double dwds2 = occ[j] * dw * (orc_fprime(coef, Z[j], s2) - B[j] * f);
+            dFq_r += 0.25 * dwds2 * c;
+            dFq_i += 0.25 * dwds2 * s;
+        }
+        /* lattice: through |g|^2 into s^2 (f, Debye-Waller), LP and 2-theta */
+        const double X = l2 * q;
+        const double c2 = 1.0 - 2.0 * X, rt = sqrt(1.0 - X);
+        const double N = 1.0 + c2 * c2, D = X * rt;
+        const double dN = -4.0 * c2, dD = rt - X / (2.0 * rt);
+        const double dlp_dq = (dN * D - N * dD) / (D * D) * l2;
+        const double dT_dq = (360.0 / M_PI) / (2.0 * sqrt(X) * rt) * l2;
+        const double dI_dq = 2.0 * lp * (Fr * dFq_r + Fi * dFq_i) + (Fr * Fr + Fi * Fi) * dlp_dq;
+        const double dLdq = dLdI * dI_dq + dLdT * dT_dq;
+        /* dq/dp = -v^T (dG/dp) v with v = G* h */
+        double v[3];
+        for (int a = 0; a < 3; a++) v[a] = S[a][0] * hv[0] + S[a][1] * hv[1] + S[a][2] * hv[2];
+        for (int m = 0; m < 6; m++) {
+            double qf = 0.0;
+            for (int a = 0; a < 3; a++)
+                for (int b = 0; b < 3; b++) qf += v[a] * dG[m][a][b] * v[b];
+            dlat[m] += dLdq * (-qf);
+        }
+    }
+}
+
 int orc_max_threads(void)
 {
 #ifdef _OPENMP

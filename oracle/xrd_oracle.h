@@ -87,6 +87,25 @@ int orc_pattern_batch(int n_struct, const double* lattice, const int64_t* atom_o
                       int64_t* peak_fam_off, int32_t* fam_hkl, int32_t* fam_mult,
                       int64_t* n_peaks, int64_t* n_fam, int32_t* status);
 
+/*
+ * Gaussian-broadened pattern of one structure over a fixed list of full-sphere
+ * reflections hkl[nr][3] (no merge, no cutoff, no scaling):
+ *   y_k = sum_r I_r exp(-(t_k - 2theta_r)^2 / (2 sigma^2)),  t_k = t0 + k dt,
+ *   sigma = fwhm / (2 sqrt(2 ln 2)).
+ * Every grid point sees every reflection (no window).
+ */
+void orc_broadened(const double lat[6], long n, const double* frac, const int16_t* Z, const double* occ,
+                   const double* B, const double* coef, double lambda, long nr, const int32_t* hkl, double t0,
+                   double dt, int npts, double fwhm, double* y);
+
+/* Analytic gradient of L = sum_k dLdy_k y_k (same fixed list) with respect to the
+ * fractional coordinates dfrac[n][3], the B factors dB[n] and the lattice
+ * parameters dlat[6] (per angstrom and per degree). Outputs are overwritten. */
+void orc_broadened_grad(const double lat[6], long n, const double* frac, const int16_t* Z, const double* occ,
+                        const double* B, const double* coef, double lambda, long nr, const int32_t* hkl, double t0,
+                        double dt, int npts, double fwhm, const double* dLdy, double* dfrac, double* dB,
+                        double* dlat);
+
 /* Number of threads OpenMP would use for threads = 0 (all cores). */
 int orc_max_threads(void);
 
