@@ -76,11 +76,22 @@ typedef struct {
 
 /* Sizes returned by xrd_query_sizes. */
 typedef struct {
-    int64_t n_refl;   /* Friedel-unique reflections of the whole batch (each stands for g and -g) */
-    int64_t max_refl; /* largest Friedel-unique count of one structure */
-    int64_t n_tiles;  /* structure-factor tiles at the tuned tile size */
-    size_t ws_bytes;  /* workspace bytes xrd_pattern_batch needs for this batch and these options */
+    int64_t n_refl;       /* Friedel-unique reflections of the whole batch (each stands for g and -g) */
+    int64_t max_refl;     /* largest Friedel-unique count of one structure */
+    int64_t n_tiles;      /* structure-factor tiles at the tuned tile size */
+    size_t ws_bytes;      /* workspace bytes xrd_pattern_batch needs for this batch and these options */
+    size_t ws_grad_bytes; /* workspace bytes xrd_pattern_broadened + xrd_pattern_grad need */
 } xrd_sizes;
+
+/* Uniform 2-theta grid of a broadened pattern: t_k = t0 + k dt, k = 0 .. n_pts - 1,
+ * Gaussian peaks of full width at half maximum fwhm (degrees). */
+typedef struct {
+    double t0;        /* degrees */
+    double dt;        /* degrees, > 0 */
+    double fwhm;      /* degrees, > 0 */
+    int32_t n_pts;    /* > 0 */
+    int32_t reserved; /* must be 0 */
+} xrd_grid;
 
 /* Pattern output: device buffers owned by the caller. Peaks and families are
  * dense CSR arrays over the batch, in structure order; within a structure
@@ -131,6 +142,39 @@ int xrd_query_sizes(xrd_handle* h, const xrd_batch* batch, const xrd_opts* opts,
  */
 int xrd_pattern_batch(xrd_handle* h, const xrd_batch* batch, const xrd_opts* opts, const xrd_pattern* out,
                       void* workspace, size_t ws_bytes, void* stream /* cudaStream_t */);
+
+/*
+ * Gaussian-broadened pattern of every structure (the differentiable profile
+ * used for refinement and for generating training patterns with peak
+ * broadening; Sec. 1 motivates both):
+ *   y[s][k] = sum over reflections g of structure s in the 2-theta range of
+ *             I_g exp(-(t_k - 2theta_g)^2 / (2 sigma^2)),  sigma = fwhm / (2 sqrt(2 ln 2)),
+ * with I_g = |F(g)|^2 LP unscaled and unmerged (g and -g both counted), each
+ * Gaussian cut at |t_k - 2theta_g| <= about 6 sigma (grid points b - W .. b + W + 1
+ * around the grid cell b of 2theta_g, W = ceil(6 sigma / dt); the cut changes y by
+ * less than 2e-8 of a peak). opts.precision must be XRD_FP32_PHASEFIX;
+ * rel_cutoff, scaled and tt_tol are ignored. y is device float [n_struct][n_pts].
+ * status (device [n_struct]) and totals (device [4]) as in xrd_pattern. The
+ * workspace (>= sizes.ws_grad_bytes) keeps the reflection list, F and dF/ds^2
+ * for xrd_pattern_grad: pass the same workspace, unmodified, to that call.
+ */
+int xrd_pattern_broadened(xrd_handle* h, const xrd_batch* batch, const xrd_opts* opts, const xrd_grid* grid,
+                          float* y, int32_t* status, int64_t* totals, void* workspace, size_t ws_bytes,
+                          void* stream /* cudaStream_t */);
+
+/*
+ * Gradient of a loss L through the broadened pattern of the preceding
+ * xrd_pattern_broadened call (same batch, options, grid and workspace), given
+ * dL_dy (device float [n_struct][n_pts]): writes d_frac (device float
+ * [n_atoms][3], dL/dx per fractional unit), d_B (device float [n_atoms],
+ * per angstrom^2) and d_lattice (device float [n_struct][6]: dL/da, dL/db,
+ * dL/dc per angstrom, dL/dalpha, dL/dbeta, dL/dgamma per degree). The
+ * reflection set is the one enumerated by the forward call, held fixed.
+ * Structures with a non-OK status get zero gradients.
+ */
+int xrd_pattern_grad(xrd_handle* h, const xrd_batch* batch, const xrd_opts* opts, const xrd_grid* grid,
+                     const float* dL_dy, float* d_frac, float* d_B, float* d_lattice, void* workspace,
+                     size_t ws_bytes, void* stream /* cudaStream_t */);
 
 /* Stage timing: when enabled, xrd_pattern_batch records CUDA events around
  * each kernel on its stream; xrd_stage_times synchronises on the last event

@@ -17,6 +17,7 @@ struct xrd_handle {
     cudaEvent_t ev[9] = {};
     void* qbuf = nullptr;  // query scratch owned by the handle
     size_t qbuf_bytes = 0;
+    const xrd::TTab* ttab = nullptr;  // 2-theta table on the handle's device
 };
 
 namespace {
@@ -97,6 +98,55 @@ Layout layout(int64_t n, int64_t natoms, int zmax, int64_t R)
     return L;
 }
 
+// Workspace of the broadened-pattern / gradient path: the geometry prefix of
+// the pattern layout plus the per-reflection state kept for the backward pass.
+struct LayoutG {
+    size_t geo, refl_cnt, refl_off, tile_off, order, flags, coef32, atom32, atom64, atom_src;
+    size_t q, key, Fx, Ig, tb, td, perm, U, V;
+    size_t total;
+};
+
+LayoutG layout_grad(int64_t n, int64_t natoms, int zmax, int64_t R)
+{
+    LayoutG L{};
+    size_t o = 0;
+    auto take = [&](size_t bytes) { const size_t at = o; o += al(bytes); return at; };
+    L.geo = take(sizeof(xrd::Geo) * n);
+    L.refl_cnt = take(8 * n);
+    L.refl_off = take(8 * (n + 1));
+    L.tile_off = take(4 * (n + 1));
+    L.order = take(4 * n);
+    L.flags = take(16);
+    L.coef32 = take(sizeof(xrd::Coef32) * (zmax + 1));
+    L.atom32 = take(sizeof(xrd::Atom32) * natoms);
+    L.atom64 = take(sizeof(xrd::Atom64) * natoms);
+    L.atom_src = take(4 * natoms);
+    L.q = take(8 * R);
+    L.key = take(4 * R);
+    L.Fx = take(16 * R);
+    L.Ig = take(4 * R);
+    L.tb = take(4 * R);
+    L.td = take(4 * R);
+    L.perm = take(4 * R);
+    L.U = take(4 * R);
+    L.V = take(4 * R);
+    L.total = o;
+    return L;
+}
+
+int64_t refl_capacity_grad(int64_t n, int64_t natoms, int zmax, size_t ws_bytes)
+{
+    const size_t fixed = layout_grad(n, natoms, zmax, 0).total;
+    if (ws_bytes < fixed) return -1;
+    int64_t lo = 0, hi = (int64_t)((ws_bytes - fixed) / 32) + 1;
+    while (hi - lo > 1) {
+        const int64_t mid = lo + (hi - lo) / 2;
+        if (layout_grad(n, natoms, zmax, mid).total <= ws_bytes) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
 // Largest reflection capacity whose layout fits in ws_bytes.
 int64_t refl_capacity(int64_t n, int64_t natoms, int zmax, size_t ws_bytes)
 {
@@ -136,6 +186,20 @@ int check_batch(xrd_handle* h, const xrd_batch* b)
     if (b->n_struct > 0 && (!b->lattice || !b->atom_off)) return fail(h, XRD_EINVAL, "lattice/atom_off is NULL");
     if (!b->coef) return fail(h, XRD_EINVAL, "coef is NULL");
     if (b->n_atoms > 0 && (!b->frac || !b->Z || !b->occ || !b->B)) return fail(h, XRD_EINVAL, "atom array is NULL");
+    return XRD_OK;
+}
+
+int check_grid(xrd_handle* h, const xrd_grid* g, int& W, double& sigma)
+{
+    if (!g) return fail(h, XRD_EINVAL, "grid is NULL");
+    if (!(g->dt > 0.0) || !std::isfinite(g->dt) || !std::isfinite(g->t0)) return fail(h, XRD_EINVAL, "grid dt/t0 invalid");
+    if (!(g->fwhm > 0.0) || !std::isfinite(g->fwhm)) return fail(h, XRD_EINVAL, "grid fwhm must be > 0");
+    if (g->n_pts <= 0 || g->reserved != 0) return fail(h, XRD_EINVAL, "grid n_pts must be > 0, reserved 0");
+    sigma = g->fwhm / (2.0 * std::sqrt(2.0 * std::log(2.0)));
+    const double w = std::ceil(6.0 * sigma / g->dt);
+    if (w > 1e6) return fail(h, XRD_EINVAL, "grid spacing too fine for the Gaussian window");
+    W = (int)w;
+    if (xrd::broaden_smem_bytes(g->n_pts, W) > 200 * 1024) return fail(h, XRD_EINVAL, "grid has too many points");
     return XRD_OK;
 }
 
@@ -212,9 +276,9 @@ int xrd_create(xrd_handle** h, int device)
         e = cudaEventCreate(&p->ev[i]);
         if (e != cudaSuccess) { delete p; return XRD_ECUDA; }
     }
-    xrd::init_tables(0);  // device tables (2-theta), once per handle, on the legacy stream
+    p->ttab = xrd::init_tables(0);  // device tables (2-theta), once per handle, on the legacy stream
     e = cudaStreamSynchronize(0);
-    if (e != cudaSuccess) { delete p; return XRD_ECUDA; }
+    if (e != cudaSuccess || !p->ttab) { delete p; return XRD_ECUDA; }
     *h = p;
     return XRD_OK;
 }
@@ -267,6 +331,7 @@ int xrd_query_sizes(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, xrd_si
     memset(sizes, 0, sizeof(*sizes));
     if (n == 0) {
         sizes->ws_bytes = layout(0, b->n_atoms, b->zmax, 0).total;
+        sizes->ws_grad_bytes = layout_grad(0, b->n_atoms, b->zmax, 0).total;
         return XRD_OK;
     }
     const size_t need = al(sizeof(xrd::Geo) * n) + al(8 * n);
@@ -302,6 +367,7 @@ int xrd_query_sizes(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, xrd_si
     sizes->max_refl = mx;
     sizes->n_tiles = tiles;
     sizes->ws_bytes = layout(n, b->n_atoms, b->zmax, tot).total;
+    sizes->ws_grad_bytes = layout_grad(n, b->n_atoms, b->zmax, tot).total;
     return XRD_OK;
 }
 
@@ -383,6 +449,7 @@ int xrd_pattern_batch(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, cons
     pa.r2min = ga.r2min;
     pa.r2max = ga.r2max;
     pa.l2d = o->lambda * o->lambda * 0.25;
+    pa.ttab = h->ttab;
     pa.tolf = (float)o->tt_tol;
     pa.lo3 = (float)(ga.r2min * std::sqrt(ga.r2min));
     pa.hi3 = (float)(ga.r2max * std::sqrt(ga.r2max));
@@ -432,6 +499,157 @@ int xrd_pattern_batch(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, cons
     h->recorded = prof;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(h, e, "xrd_pattern_batch launch");
+    return XRD_OK;
+}
+
+static xrd::GradArgs grad_args(xrd_handle* h, const xrd_batch* b, const xrd_grid* g, int W, double sigma,
+                               const xrd_opts* o, const LayoutG& L, char* ws)
+{
+    xrd::GradArgs a{};
+    a.n_struct = b->n_struct;
+    a.n_pts = g->n_pts;
+    a.W = W;
+    a.n_atoms = b->n_atoms;
+    a.t0 = g->t0;
+    a.dt = g->dt;
+    a.sigma = sigma;
+    a.l2d = o->lambda * o->lambda * 0.25;
+    a.ttab = h->ttab;
+    a.geo = (const xrd::Geo*)(ws + L.geo);
+    a.lattice = b->lattice;
+    a.refl_off = (const int64_t*)(ws + L.refl_off);
+    a.atom_off = b->atom_off;
+    a.abort_flag = (const int*)(ws + L.flags);
+    a.q = (const double*)(ws + L.q);
+    a.key = (const uint32_t*)(ws + L.key);
+    a.Fx = (const float4*)(ws + L.Fx);
+    a.Ig = (const float*)(ws + L.Ig);
+    a.tb = (int*)(ws + L.tb);
+    a.td = (float*)(ws + L.td);
+    a.perm = (int*)(ws + L.perm);
+    a.U = (float*)(ws + L.U);
+    a.V = (float*)(ws + L.V);
+    a.atom32 = (const xrd::Atom32*)(ws + L.atom32);
+    a.coef32 = (const xrd::Coef32*)(ws + L.coef32);
+    a.atom_src = (const int*)(ws + L.atom_src);
+    return a;
+}
+
+int xrd_pattern_broadened(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, const xrd_grid* grid, float* y,
+                          int32_t* status, int64_t* totals, void* workspace, size_t ws_bytes, void* stream)
+{
+    if (!h) return XRD_EINVAL;
+    h->err.clear();
+    int rc = check_batch(h, b);
+    if (rc) return rc;
+    if ((rc = check_opts(h, o))) return rc;
+    if (o->precision != XRD_FP32_PHASEFIX) return fail(h, XRD_EINVAL, "the broadened path runs XRD_FP32_PHASEFIX");
+    int W;
+    double sigma;
+    if ((rc = check_grid(h, grid, W, sigma))) return rc;
+    const int64_t n = b->n_struct;
+    if (!totals || (n > 0 && (!y || !status))) return fail(h, XRD_EINVAL, "an output pointer is NULL");
+    if (!workspace || ((uintptr_t)workspace & 255)) return fail(h, XRD_EINVAL, "workspace must be 256-byte aligned");
+    const int64_t cap_refl = refl_capacity_grad(n, b->n_atoms, b->zmax, ws_bytes);
+    if (cap_refl < 0) return fail(h, XRD_ECAPACITY, "workspace smaller than the per-structure part");
+    DeviceGuard dg(h->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    char* ws = (char*)workspace;
+    const LayoutG L = layout_grad(n, b->n_atoms, b->zmax, cap_refl);
+    xrd::GeomArgs ga{};
+    ga.n_struct = (int)n;
+    ga.zmax = b->zmax;
+    ga.n_atoms = b->n_atoms;
+    ga.tile = kTile;
+    radii(o, ga.r2min, ga.r2max, ga.rmax);
+    ga.cap_refl = cap_refl;
+    ga.lattice = b->lattice;
+    ga.atom_off = b->atom_off;
+    ga.frac = b->frac;
+    ga.Z = b->Z;
+    ga.occ = b->occ;
+    ga.B = b->B;
+    ga.coef = b->coef;
+    ga.geo = (xrd::Geo*)(ws + L.geo);
+    ga.coef32 = (xrd::Coef32*)(ws + L.coef32);
+    ga.atom32 = (xrd::Atom32*)(ws + L.atom32);
+    ga.atom64 = (xrd::Atom64*)(ws + L.atom64);
+    ga.atom_src = (int*)(ws + L.atom_src);
+    ga.refl_cnt = (int64_t*)(ws + L.refl_cnt);
+    ga.refl_off = (int64_t*)(ws + L.refl_off);
+    ga.tile_off = (int*)(ws + L.tile_off);
+    ga.order = (int*)(ws + L.order);
+    ga.abort_flag = (int*)(ws + L.flags);
+    ga.totals = totals;
+    ga.status = status;
+    ga.q = (double*)(ws + L.q);
+    ga.key = (uint32_t*)(ws + L.key);
+    cudaMemsetAsync(ws + L.flags, 0, 16, st);
+    xrd::launch_prep(ga, st);
+    xrd::launch_atoms(ga, st);
+    xrd::launch_count(ga, st);
+    xrd::launch_scan_refl(ga, st);
+    xrd::launch_emit(ga, st);
+    xrd::SfArgs sa{};
+    sa.n_struct = (int)n;
+    sa.precision = XRD_FP32_PHASEFIX;
+    sa.zmax = b->zmax;
+    sa.tile = kTile;
+    sa.grid = h->sms;
+    sa.lambda = o->lambda;
+    sa.atom_off = b->atom_off;
+    sa.refl_off = ga.refl_off;
+    sa.tile_off = ga.tile_off;
+    sa.order = ga.order;
+    sa.tile_counter = ga.abort_flag + 2;
+    sa.abort_flag = ga.abort_flag;
+    sa.coef32 = ga.coef32;
+    sa.coef = b->coef;
+    sa.atom32 = ga.atom32;
+    sa.atom64 = ga.atom64;
+    sa.q = ga.q;
+    sa.key = ga.key;
+    sa.Fx = (float4*)(ws + L.Fx);
+    sa.Ig = (float*)(ws + L.Ig);
+    xrd::launch_sf(sa, st);
+    xrd::GradArgs gr = grad_args(h, b, grid, W, sigma, o, L, ws);
+    gr.y = y;
+    xrd::launch_broaden(gr, st);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(h, e, "xrd_pattern_broadened launch");
+    return XRD_OK;
+}
+
+int xrd_pattern_grad(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, const xrd_grid* grid, const float* dL_dy,
+                     float* d_frac, float* d_B, float* d_lattice, void* workspace, size_t ws_bytes, void* stream)
+{
+    if (!h) return XRD_EINVAL;
+    h->err.clear();
+    int rc = check_batch(h, b);
+    if (rc) return rc;
+    if ((rc = check_opts(h, o))) return rc;
+    if (o->precision != XRD_FP32_PHASEFIX) return fail(h, XRD_EINVAL, "the broadened path runs XRD_FP32_PHASEFIX");
+    int W;
+    double sigma;
+    if ((rc = check_grid(h, grid, W, sigma))) return rc;
+    const int64_t n = b->n_struct;
+    if (n > 0 && (!dL_dy || !d_lattice)) return fail(h, XRD_EINVAL, "an input/output pointer is NULL");
+    if (b->n_atoms > 0 && (!d_frac || !d_B)) return fail(h, XRD_EINVAL, "an output pointer is NULL");
+    if (!workspace || ((uintptr_t)workspace & 255)) return fail(h, XRD_EINVAL, "workspace must be 256-byte aligned");
+    const int64_t cap_refl = refl_capacity_grad(n, b->n_atoms, b->zmax, ws_bytes);
+    if (cap_refl < 0) return fail(h, XRD_ECAPACITY, "workspace smaller than the per-structure part");
+    DeviceGuard dg(h->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    char* ws = (char*)workspace;
+    const LayoutG L = layout_grad(n, b->n_atoms, b->zmax, cap_refl);
+    xrd::GradArgs gr = grad_args(h, b, grid, W, sigma, o, L, ws);
+    gr.dLdy = dL_dy;
+    gr.d_frac = d_frac;
+    gr.d_B = d_B;
+    gr.d_lat = d_lattice;
+    xrd::launch_grad(gr, st);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(h, e, "xrd_pattern_grad launch");
     return XRD_OK;
 }
 

@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(128) k_atoms(const int64_t* __restrict__ atom_
                                                const double* __restrict__ frac, const int16_t* __restrict__ Zin,
                                                const double* __restrict__ occ, const double* __restrict__ Bf, int zmax,
                                                Geo* __restrict__ geo, Atom32* __restrict__ a32,
-                                               Atom64* __restrict__ a64)
+                                               Atom64* __restrict__ a64, int* __restrict__ src)
 {
     __shared__ int off[kZmaxLimit + 1];
     __shared__ int zs[128];
@@ -161,6 +161,7 @@ __global__ void __launch_bounds__(128) k_atoms(const int64_t* __restrict__ atom_
             Atom64 d;
             d.x = x; d.y = y; d.z = w; d.B = bb; d.occ = o; d.zz = z; d.pad = 0;
             a64[a0 + pos] = d;
+            if (src) src[a0 + pos] = (int)i;
         }
         __syncthreads();  // every read of off[] for this chunk is done
         if (i < na) atomicAdd(&off[z], 1);
@@ -437,7 +438,8 @@ void launch_prep(const GeomArgs& a, cudaStream_t st)
 void launch_atoms(const GeomArgs& a, cudaStream_t st)
 {
     if (a.n_struct > 0)
-        k_atoms<<<a.n_struct, 128, 0, st>>>(a.atom_off, a.n_atoms, a.frac, a.Z, a.occ, a.B, a.zmax, a.geo, a.atom32, a.atom64);
+        k_atoms<<<a.n_struct, 128, 0, st>>>(a.atom_off, a.n_atoms, a.frac, a.Z, a.occ, a.B, a.zmax, a.geo, a.atom32,
+                                            a.atom64, a.atom_src);
 }
 
 void launch_count_only(const GeomArgs& a, cudaStream_t st)

@@ -33,19 +33,7 @@ size_t post_smem_bytes(int cap)
            align16(c * 8) + align16(c * 4);
 }
 
-// ---- 2-theta of a reflection from |g|^2 without FP64 transcendentals ----
-// theta in [0, pi/4] is found from a table at theta_j = j * pi / 4096 (2theta_j =
-// j * 360 / 4096 degrees, exact in binary) and a few FP32 Newton steps on the
-// small remainder u = 2 (theta - theta_j); angles above 45 degrees use the
-// complement (sin^2 theta = 1 - sin^2(90 - theta)). Error about 1e-8 degrees.
-constexpr int kTabN = 1024;
-struct TTab {
-    double S;   // sin^2 theta_j
-    float A;    // sin 2 theta_j
-    float Bc;   // cos 2 theta_j
-};
 static __device__ TTab g_ttab[kTabN + 1];
-constexpr double kTabStepDeg = 360.0 / 4096.0;  // 2theta spacing of the table
 
 __global__ void k_ttab_init()
 {
@@ -60,42 +48,12 @@ __global__ void k_ttab_init()
     g_ttab[j] = t;
 }
 
-void init_tables(cudaStream_t st) { k_ttab_init<<<(kTabN + 1 + 255) / 256, 256, 0, st>>>(); }
-
-__device__ __forceinline__ float d2f_signed(double x)
+const TTab* init_tables(cudaStream_t st)
 {
-    const float m = x == 0.0 ? 0.f : d2f_pos(fabs(x));
-    return x < 0.0 ? -m : m;
-}
-
-// 2theta in degrees of a reflection with sin^2 theta = X (FP64, 0 < X <= 1)
-__device__ double two_theta_of(double X)
-{
-    const bool comp = X > 0.5;
-    const double Y = comp ? 1.0 - X : X;  // exact for X in (0.5, 1]
-    const float Yf = Y > 0.0 ? d2f_pos(Y) : 0.f;
-    const float th0 = asinf(sqrtf(Yf));
-    int j = __float2int_rn(th0 * (float)(4.0 * kTabN / kPi));
-    j = min(max(j, 0), kTabN);
-    double t;
-    if (j <= 2) {
-        t = f2d_fast(th0 * (float)(360.0 / kPi));
-    } else {
-        const TTab e = g_ttab[j];
-        const float r = d2f_signed(Y - e.S);
-        float u = 4.f * r / (e.A + sqrtf(fmaf(4.f * e.Bc, r, e.A * e.A)));
-#pragma unroll
-        for (int it = 0; it < 2; it++) {
-            const float u2 = u * u;
-            const float su = u - u * u2 * (1.f / 6.f);
-            const float cu = u2 * (0.5f - u2 * (1.f / 24.f));
-            const float fv = fmaf(e.A, su, fmaf(e.Bc, cu, -2.f * r));
-            const float fp = fmaf(e.A, 1.f - 0.5f * u2, e.Bc * su);
-            u -= fv / fp;
-        }
-        t = (double)j * kTabStepDeg + f2d_fast(u * (float)(180.0 / kPi));
-    }
-    return comp ? 180.0 - t : t;
+    k_ttab_init<<<(kTabN + 1 + 255) / 256, 256, 0, st>>>();
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_ttab) != cudaSuccess) return nullptr;
+    return (const TTab*)p;
 }
 
 // 2theta(qb) - 2theta(qa) in degrees for qb >= qa > 0, to about 1e-6 relative:
@@ -242,7 +200,7 @@ __device__ void post_structure(const PostArgs& a, int s, int64_t base, int n, co
         const int i0 = bkt[p], i1 = bkt[p + 1];
         const int64_t o = base + pst[p];
         const double qa = q[perm[i0]];
-        a.st_tt[o] = two_theta_of(fmin(qa * l2d, 1.0));
+        a.st_tt[o] = two_theta_of(fmin(qa * l2d, 1.0), a.ttab);
         const double y0 = f2d_fast(rsqrtf(d2f_pos(qa)));  // d = 1/sqrt(q): FP32 seed, one FP64 Newton step
         a.st_d[o] = y0 * fma(-0.5 * qa * y0, y0, 1.5);
         const double ps = psum[p];  // the largest peak maps to exactly 100

@@ -54,13 +54,26 @@ __device__ __forceinline__ float lp_of(float qf, float l2)
     return fmaf(c2, c2, 1.f) / (X * sqrtf(1.f - X));
 }
 
+// d f / d s^2 = -41.78214 sum_i a_i exp(-b_i s^2)(1 - b_i s^2); with b_i = -bl_i ln 2
+__device__ __forceinline__ float fprime_of(const Coef32& c, float s2)
+{
+    constexpr float ln2 = 0.69314718055994531f;
+    float acc = 0.f;
+#pragma unroll
+    for (int i = 0; i < 4; i++) acc = fmaf(c.a[i] * ex2_approx(c.bl[i] * s2), fmaf(c.bl[i] * ln2, s2, 1.f), acc);
+    return acc;
+}
+
 // FP32 variants: RB reflections per thread share each atom record, which is
 // read from shared memory (a broadcast: every lane reads the same record).
-template <int PREC>
+// GRAD also accumulates dF/ds^2 = sum_j occ_j exp(-B_j s^2)(f_j' - B_j f_j) e^{i phi_j}.
+template <int PREC, bool GRAD>
 __device__ void sf_tile_fp32(const SfArgs& a, int64_t r0, int64_t re, int64_t j0, int64_t j1, Atom32* sat,
                              const Coef32* scoef)
 {
+    constexpr float ln2 = 0.69314718055994531f;
     float s2[kSfRB], qf[kSfRB], Fr[kSfRB], Fi[kSfRB], f[kSfRB];
+    float Gr[kSfRB], Gi[kSfRB], fp[kSfRB];
     uint32_t uh[kSfRB], uk[kSfRB], ul[kSfRB];
 #pragma unroll
     for (int i = 0; i < kSfRB; i++) {
@@ -71,6 +84,7 @@ __device__ void sf_tile_fp32(const SfArgs& a, int64_t r0, int64_t re, int64_t j0
         const uint32_t key = a.key[rr];
         uh[i] = (uint32_t)hkl_h(key); uk[i] = (uint32_t)hkl_k(key); ul[i] = (uint32_t)hkl_l(key);
         Fr[i] = 0.f; Fi[i] = 0.f; f[i] = 0.f;
+        Gr[i] = 0.f; Gi[i] = 0.f; fp[i] = 0.f;
     }
     int zc = -1;
     for (int64_t c0 = j0; c0 < j1; c0 += kSfChunk) {
@@ -84,7 +98,10 @@ __device__ void sf_tile_fp32(const SfArgs& a, int64_t r0, int64_t re, int64_t j0
                 zc = at.z;
                 const Coef32 c = scoef[zc];
 #pragma unroll
-                for (int i = 0; i < kSfRB; i++) f[i] = f_of(c, zc, s2[i]);
+                for (int i = 0; i < kSfRB; i++) {
+                    f[i] = f_of(c, zc, s2[i]);
+                    if (GRAD) fp[i] = fprime_of(c, s2[i]);
+                }
             }
             double dx = 0.0, dy = 0.0, dz = 0.0;
             if (PREC == XRD_FP32_PHASE64) {
@@ -100,9 +117,15 @@ __device__ void sf_tile_fp32(const SfArgs& a, int64_t r0, int64_t re, int64_t j0
                     P = fix32(fma((double)(int)uh[i], dx, fma((double)(int)uk[i], dy, (double)(int)ul[i] * dz)));
                 float sn, cs;
                 __sincosf((float)(int32_t)P * kTwoPiOver2p32, &sn, &cs);
-                const float w = f[i] * ex2_approx(fmaf(at.nb, s2[i], at.lo));
+                const float dw = ex2_approx(fmaf(at.nb, s2[i], at.lo));
+                const float w = f[i] * dw;
                 Fr[i] = fmaf(w, cs, Fr[i]);
                 Fi[i] = fmaf(w, sn, Fi[i]);
+                if (GRAD) {
+                    const float wd = fmaf(at.nb * ln2, f[i], fp[i]) * dw;
+                    Gr[i] = fmaf(wd, cs, Gr[i]);
+                    Gi[i] = fmaf(wd, sn, Gi[i]);
+                }
             }
         }
     }
@@ -111,8 +134,14 @@ __device__ void sf_tile_fp32(const SfArgs& a, int64_t r0, int64_t re, int64_t j0
     for (int i = 0; i < kSfRB; i++) {
         const int64_t r = r0 + threadIdx.x + i * kSfThreads;
         if (r >= re) continue;
-        a.I[r] = f2d_fast(fmaf(Fr[i], Fr[i], Fi[i] * Fi[i]) * lp_of(qf[i], l2));
-        if (a.F) a.F[r] = make_float2(Fr[i], Fi[i]);
+        const float I = fmaf(Fr[i], Fr[i], Fi[i] * Fi[i]) * lp_of(qf[i], l2);
+        if (GRAD) {
+            a.Fx[r] = make_float4(Fr[i], Fi[i], Gr[i], Gi[i]);
+            a.Ig[r] = I;
+        } else {
+            a.I[r] = f2d_fast(I);
+            if (a.F) a.F[r] = make_float2(Fr[i], Fi[i]);
+        }
     }
 }
 
@@ -157,7 +186,7 @@ __device__ void sf_tile_fp64(const SfArgs& a, int64_t r0, int64_t re, int64_t j0
 
 // Persistent CTAs take tiles from a queue in largest-first order (tiles of the
 // structures with the most atoms first), so the uneven tail is short.
-template <int PREC>
+template <int PREC, bool GRAD>
 __global__ void __launch_bounds__(kSfThreads) k_sf(const SfArgs a)
 {
     __shared__ int t_sh;
@@ -179,11 +208,11 @@ __global__ void __launch_bounds__(kSfThreads) k_sf(const SfArgs a)
         const int64_t r0 = rb + (int64_t)(t - a.tile_off[slot]) * kSfTile;
         const int64_t j0 = a.atom_off[s], j1 = a.atom_off[s + 1];
         if (PREC == XRD_FP64) sf_tile_fp64(a, r0, re, j0, j1);
-        else sf_tile_fp32<PREC>(a, r0, re, j0, j1, sat, scoef);
+        else sf_tile_fp32<PREC, GRAD>(a, r0, re, j0, j1, sat, scoef);
     }
 }
 
-template <int PREC>
+template <int PREC, bool GRAD>
 static void launch_sf_prec(const SfArgs& a, cudaStream_t st)
 {
     static int per_sm_cache[64] = {};  // persistent grid: as many CTAs as fit on the SMs at once
@@ -191,21 +220,26 @@ static void launch_sf_prec(const SfArgs& a, cudaStream_t st)
     cudaGetDevice(&dev);
     int per_sm = (dev >= 0 && dev < 64) ? per_sm_cache[dev] : 0;
     if (per_sm < 1) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sf<PREC>, kSfThreads, 0) != cudaSuccess || per_sm < 1)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sf<PREC, GRAD>, kSfThreads, 0) != cudaSuccess ||
+            per_sm < 1)
             per_sm = 4;
         if (dev >= 0 && dev < 64) per_sm_cache[dev] = per_sm;
     }
-    k_sf<PREC><<<a.grid * per_sm, kSfThreads, 0, st>>>(a);
+    k_sf<PREC, GRAD><<<a.grid * per_sm, kSfThreads, 0, st>>>(a);
 }
 
 // a.grid = number of SMs
 void launch_sf(const SfArgs& a, cudaStream_t st)
 {
     if (a.n_struct <= 0) return;
+    if (a.Fx) {  // gradient path: FP32 with the integer phase
+        launch_sf_prec<XRD_FP32_PHASEFIX, true>(a, st);
+        return;
+    }
     switch (a.precision) {
-    case XRD_FP64: launch_sf_prec<XRD_FP64>(a, st); break;
-    case XRD_FP32_PHASE64: launch_sf_prec<XRD_FP32_PHASE64>(a, st); break;
-    default: launch_sf_prec<XRD_FP32_PHASEFIX>(a, st); break;
+    case XRD_FP64: launch_sf_prec<XRD_FP64, false>(a, st); break;
+    case XRD_FP32_PHASE64: launch_sf_prec<XRD_FP32_PHASE64, false>(a, st); break;
+    default: launch_sf_prec<XRD_FP32_PHASEFIX, false>(a, st); break;
     }
 }
 

@@ -103,6 +103,55 @@ __device__ __forceinline__ float ex2_approx(float x)
     return y;
 }
 
+// ---- 2-theta of a reflection from sin^2 theta without FP64 transcendentals ----
+// theta in [0, pi/4] is found from a table at theta_j = j * pi / 4096 (2theta_j =
+// j * 360 / 4096 degrees, exact in binary) and FP32 Newton steps on the small
+// remainder u = 2 (theta - theta_j); angles above 45 degrees use the complement
+// (sin^2 theta = 1 - sin^2(90 deg - theta)). Error about 1e-8 degrees.
+constexpr int kTabN = 1024;
+constexpr double kTabStepDeg = 360.0 / 4096.0;  // 2theta spacing of the table
+struct TTab {
+    double S;  // sin^2 theta_j
+    float A;   // sin 2 theta_j
+    float Bc;  // cos 2 theta_j
+};
+
+__device__ __forceinline__ float d2f_signed(double x)
+{
+    const float m = x == 0.0 ? 0.f : d2f_pos(fabs(x));
+    return x < 0.0 ? -m : m;
+}
+
+// 2theta in degrees of a reflection with sin^2 theta = X (FP64, 0 < X <= 1)
+__device__ __forceinline__ double two_theta_of(double X, const TTab* __restrict__ tab)
+{
+    const bool comp = X > 0.5;
+    const double Y = comp ? 1.0 - X : X;  // exact for X in (0.5, 1]
+    const float Yf = Y > 0.0 ? d2f_pos(Y) : 0.f;
+    const float th0 = asinf(sqrtf(Yf));
+    int j = __float2int_rn(th0 * (float)(4.0 * kTabN / kPi));
+    j = min(max(j, 0), kTabN);
+    double t;
+    if (j <= 2) {
+        t = f2d_fast(th0 * (float)(360.0 / kPi));
+    } else {
+        const TTab e = tab[j];
+        const float r = d2f_signed(Y - e.S);
+        float u = 4.f * r / (e.A + sqrtf(fmaf(4.f * e.Bc, r, e.A * e.A)));
+#pragma unroll
+        for (int it = 0; it < 2; it++) {
+            const float u2 = u * u;
+            const float su = u - u * u2 * (1.f / 6.f);
+            const float cu = u2 * (0.5f - u2 * (1.f / 24.f));
+            const float fv = fmaf(e.A, su, fmaf(e.Bc, cu, -2.f * r));
+            const float fp = fmaf(e.A, 1.f - 0.5f * u2, e.Bc * su);
+            u -= fv / fp;
+        }
+        t = (double)j * kTabStepDeg + f2d_fast(u * (float)(180.0 / kPi));
+    }
+    return comp ? 180.0 - t : t;
+}
+
 // ---- block-wide primitives over generic pointers (shared or global memory) ----
 
 __device__ __forceinline__ int warp_incl_scan(int v)

@@ -24,6 +24,7 @@ struct GeomArgs {
     Coef32* coef32;
     Atom32* atom32;
     Atom64* atom64;
+    int* atom_src;  // [n_atoms] index within its structure of each packed atom
     int64_t* refl_cnt;
     int64_t* refl_off;
     int* tile_off;
@@ -52,12 +53,15 @@ struct SfArgs {
     const uint32_t* key;
     double* I;   // per reflection intensity |F|^2 LP (one Friedel half-space member)
     float2* F;   // optional per-reflection F (nullptr: not stored)
+    float4* Fx;  // gradient path: (Re F, Im F, Re dF/ds^2, Im dF/ds^2) per reflection (nullptr otherwise)
+    float* Ig;   // gradient path: |F|^2 LP per reflection
 };
 
 struct PostArgs {
     int n_struct, cap_smem, scaled;
     double lambda, tol, cutoff, r2min, r2max;
     double l2d;                          // lambda^2 / 4
+    const TTab* ttab;                    // 2-theta table (device)
     float tolf, lo3, hi3, l2f, lhf;      // FP32 copies: tol, r2min^1.5, r2max^1.5, lambda^2/4, lambda/2
     const int64_t* refl_off;
     const int* abort_flag;
@@ -100,6 +104,35 @@ struct CompactArgs {
     xrd_pattern out;
 };
 
+struct GradArgs {
+    int n_struct, n_pts, W;
+    int64_t n_atoms;
+    double t0, dt, sigma, l2d;
+    const TTab* ttab;
+    const Geo* geo;
+    const double* lattice;
+    const int64_t* refl_off;
+    const int64_t* atom_off;
+    const int* abort_flag;
+    const double* q;
+    const uint32_t* key;
+    const float4* Fx;  // (Re F, Im F, Re dF/ds^2, Im dF/ds^2)
+    const float* Ig;   // |F|^2 LP
+    int* tb;           // grid cell of each reflection's 2theta (INT_MIN: off the grid)
+    float* td;         // position within the cell, [0, 1)
+    int* perm;         // per-reflection scratch
+    float* y;          // [n_struct][n_pts]
+    const float* dLdy; // [n_struct][n_pts]
+    float* U;          // dL/dI LP Re F per reflection
+    float* V;          // dL/dI LP Im F
+    const Atom32* atom32;
+    const Coef32* coef32;
+    const int* atom_src;
+    float* d_frac;
+    float* d_B;
+    float* d_lat;
+};
+
 void launch_prep(const GeomArgs& a, cudaStream_t st);
 void launch_atoms(const GeomArgs& a, cudaStream_t st);
 void launch_count(const GeomArgs& a, cudaStream_t st);
@@ -110,7 +143,10 @@ void launch_sf(const SfArgs& a, cudaStream_t st);
 size_t post_smem_bytes(int cap);
 void launch_post(const PostArgs& a, cudaStream_t st);
 void launch_compact(const CompactArgs& a, cudaStream_t st);
-void init_tables(cudaStream_t st);
+const TTab* init_tables(cudaStream_t st);
+size_t broaden_smem_bytes(int n_pts, int W);
+void launch_broaden(const GradArgs& a, cudaStream_t st);
+void launch_grad(const GradArgs& a, cudaStream_t st);  // fills the 2-theta table, returns its device address
 
 // handle accessors for entry points defined outside api.cu
 int handle_device(const xrd_handle* h);

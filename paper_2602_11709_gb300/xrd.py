@@ -37,7 +37,13 @@ class xrd_opts(C.Structure):
 
 
 class xrd_sizes(C.Structure):
-    _fields_ = [("n_refl", C.c_int64), ("max_refl", C.c_int64), ("n_tiles", C.c_int64), ("ws_bytes", C.c_size_t)]
+    _fields_ = [("n_refl", C.c_int64), ("max_refl", C.c_int64), ("n_tiles", C.c_int64), ("ws_bytes", C.c_size_t),
+                ("ws_grad_bytes", C.c_size_t)]
+
+
+class xrd_grid(C.Structure):
+    _fields_ = [("t0", C.c_double), ("dt", C.c_double), ("fwhm", C.c_double), ("n_pts", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class xrd_pattern(C.Structure):
@@ -48,7 +54,8 @@ class xrd_pattern(C.Structure):
 
 
 EXPORTS = ["xrd_create", "xrd_destroy", "xrd_last_error", "xrd_query_sizes", "xrd_pattern_batch",
-           "xrd_set_profiling", "xrd_stage_times", "xrd_pattern_batch_noalloc"]
+           "xrd_set_profiling", "xrd_stage_times", "xrd_pattern_batch_noalloc", "xrd_pattern_broadened",
+           "xrd_pattern_grad"]
 
 _lib = None
 
@@ -80,6 +87,13 @@ def load(path: str = LIB_PATH):
     L.xrd_pattern_batch_noalloc.argtypes = [C.c_void_p, C.POINTER(xrd_batch), C.POINTER(xrd_opts),
                                             C.POINTER(xrd_pattern), C.c_void_p]
     L.xrd_pattern_batch_noalloc.restype = C.c_int
+    L.xrd_pattern_broadened.argtypes = [C.c_void_p, C.POINTER(xrd_batch), C.POINTER(xrd_opts), C.POINTER(xrd_grid),
+                                        C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]
+    L.xrd_pattern_broadened.restype = C.c_int
+    L.xrd_pattern_grad.argtypes = [C.c_void_p, C.POINTER(xrd_batch), C.POINTER(xrd_opts), C.POINTER(xrd_grid),
+                                   C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t,
+                                   C.c_void_p]
+    L.xrd_pattern_grad.restype = C.c_int
     _lib = L
     return L
 
@@ -99,6 +113,11 @@ def _stream_ptr(stream):
     torch = _torch()
     s = stream if stream is not None else torch.cuda.current_stream()
     return C.c_void_p(s.cuda_stream)
+
+
+def make_grid(g) -> xrd_grid:
+    """C grid from any object with t0/dt/fwhm/n_pts."""
+    return xrd_grid(float(g.t0), float(g.dt), float(g.fwhm), int(g.n_pts), 0)
 
 
 def make_opts(o, precision="fp32_phasefix", tile=-1) -> xrd_opts:
@@ -240,6 +259,24 @@ class Handle:
         o = out.c()
         self._check(self.lib.xrd_pattern_batch_noalloc(self.h, C.byref(b), C.byref(opts), C.byref(o),
                                                        _stream_ptr(stream)))
+
+    def pattern_broadened(self, db: DeviceBatch, opts: xrd_opts, grid: xrd_grid, y, status, totals, ws, stream=None):
+        """Gaussian-broadened patterns y [n_struct][n_pts] (float32); ws keeps the state for pattern_grad."""
+        b = db.c()
+        self._check(self.lib.xrd_pattern_broadened(self.h, C.byref(b), C.byref(opts), C.byref(grid),
+                                                   C.c_void_p(y.data_ptr()), C.c_void_p(status.data_ptr()),
+                                                   C.c_void_p(totals.data_ptr()), C.c_void_p(ws.data_ptr()),
+                                                   C.c_size_t(ws.numel() * ws.element_size()), _stream_ptr(stream)))
+
+    def pattern_grad(self, db: DeviceBatch, opts: xrd_opts, grid: xrd_grid, dLdy, d_frac, d_B, d_lat, ws,
+                     stream=None):
+        """Gradients of L through the preceding pattern_broadened call on the same workspace."""
+        b = db.c()
+        self._check(self.lib.xrd_pattern_grad(self.h, C.byref(b), C.byref(opts), C.byref(grid),
+                                              C.c_void_p(dLdy.data_ptr()), C.c_void_p(d_frac.data_ptr()),
+                                              C.c_void_p(d_B.data_ptr()), C.c_void_p(d_lat.data_ptr()),
+                                              C.c_void_p(ws.data_ptr()), C.c_size_t(ws.numel() * ws.element_size()),
+                                              _stream_ptr(stream)))
 
     def set_profiling(self, on: bool):
         self._check(self.lib.xrd_set_profiling(self.h, 1 if on else 0))

@@ -1,0 +1,153 @@
+"""Broadened pattern and its gradient on the GPU against the FP64 oracle.
+
+Bar: broadened profile within 1e-5 of the structure's largest value; gradients
+(coordinates, B factors, lattice parameters, each group separately) within
+1e-3 relative in norm of the FP64 oracle gradient and with cosine similarity
+>= 0.99999 (FP32 arithmetic; the oracle sums every Gaussian over the whole
+grid, the GPU cuts each one at about 6 sigma, a 2e-8 effect).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2602_11709_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _grad_case(n=None, idx=None):
+    base, target, o, grid = synth.grad()
+    if idx is not None:
+        base = base.subset(idx)
+        target = target.subset(idx)
+    return base, target, o, grid
+
+
+def _run(xrd, handle, b, o, grid, dLdy=None):
+    import torch
+    db = xrd.DeviceBatch.from_host(b)
+    co = xrd.make_opts(o, "fp32_phasefix")
+    cg = xrd.make_grid(grid)
+    sz = handle.query_sizes(db, co)
+    ws = xrd.workspace(sz.ws_grad_bytes)
+    y = torch.empty(b.n_struct, grid.n_pts, dtype=torch.float32, device="cuda")
+    status = torch.zeros(b.n_struct, dtype=torch.int32, device="cuda")
+    totals = torch.zeros(4, dtype=torch.int64, device="cuda")
+    handle.pattern_broadened(db, co, cg, y, status, totals, ws)
+    out = {"y": y, "status": status, "totals": totals}
+    if dLdy is not None:
+        g = torch.from_numpy(np.ascontiguousarray(dLdy, dtype=np.float32)).cuda()
+        d_frac = torch.full((b.n_atoms, 3), np.nan, dtype=torch.float32, device="cuda")
+        d_B = torch.full((b.n_atoms,), np.nan, dtype=torch.float32, device="cuda")
+        d_lat = torch.full((b.n_struct, 6), np.nan, dtype=torch.float32, device="cuda")
+        handle.pattern_grad(db, co, cg, g, d_frac, d_B, d_lat, ws)
+        out.update(d_frac=d_frac, d_B=d_B, d_lat=d_lat)
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy() for k, v in out.items()}
+
+
+def _cmp(a, b):
+    a, b = np.asarray(a, np.float64).ravel(), np.asarray(b, np.float64).ravel()
+    rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+    cos = float(np.dot(a, b) / max(np.linalg.norm(a) * np.linalg.norm(b), 1e-300))
+    return rel, cos
+
+
+@pytest.fixture(scope="module")
+def handle(gpu_lib):
+    h = gpu_lib.Handle(0)
+    yield h
+    h.close()
+
+
+def test_broadened_matches_oracle(gpu_lib, handle):
+    idx = np.array([0, 1, 2, 3, 4, 5])
+    b, _, o, grid = _grad_case(idx=idx)
+    got = _run(gpu_lib, handle, b, o, grid)
+    assert np.all(got["status"] == 0)
+    for s in range(b.n_struct):
+        hkl, _ = oracle.enumerate_refl(b.lattice[s], o)
+        ref = oracle.broadened(b, s, hkl, o.wavelength, grid)
+        assert np.abs(got["y"][s] - ref).max() <= 1e-5 * ref.max(), s
+
+
+def test_gradient_matches_oracle(gpu_lib, handle):
+    idx = np.array([7, 11, 19, 23, 42])
+    b, _, o, grid = _grad_case(idx=idx)
+    rng = np.random.default_rng(99)
+    g = rng.standard_normal((b.n_struct, grid.n_pts))
+    got = _run(gpu_lib, handle, b, o, grid, dLdy=g)
+    worst = {}
+    for s in range(b.n_struct):
+        hkl, _ = oracle.enumerate_refl(b.lattice[s], o)
+        df, dB, dl = oracle.broadened_grad(b, s, hkl, o.wavelength, grid, g[s].astype(np.float32).astype(np.float64))
+        sl = b.atoms_of(s)
+        for name, gv, rv in (("frac", got["d_frac"][sl], df), ("B", got["d_B"][sl], dB), ("lattice", got["d_lat"][s], dl)):
+            rel, cos = _cmp(gv, rv)
+            worst[name] = max(worst.get(name, 0.0), rel)
+            assert rel <= 1e-3 and cos >= 0.99999, (s, name, rel, cos)
+
+
+def test_autograd_function_mse_loss(gpu_lib, handle):
+    import torch
+    from paper_2602_11709_gb300 import autograd as ag
+    idx = np.array([3, 8, 13])
+    b, t, o, grid = _grad_case(idx=idx)
+    fixed = ag.FixedBatch.from_host(b)
+    frac = torch.tensor(b.frac, device="cuda", requires_grad=True)
+    B = torch.tensor(b.B, device="cuda", requires_grad=True)
+    lat = torch.tensor(b.lattice, device="cuda", requires_grad=True)
+    with torch.no_grad():
+        ft = ag.FixedBatch.from_host(t)
+        yt = ag.broadened_pattern(torch.tensor(t.frac, device="cuda"), torch.tensor(t.B, device="cuda"),
+                                  torch.tensor(t.lattice, device="cuda"), ft, o, grid, handle)
+    scale = yt.amax(dim=1, keepdim=True)
+    y = ag.broadened_pattern(frac, B, lat, fixed, o, grid, handle)
+    y.retain_grad()
+    loss = (((y - yt) / scale) ** 2).mean()
+    loss.backward()
+    gy = y.grad.detach().cpu().numpy().astype(np.float64)
+    assert frac.grad is not None and B.grad is not None and lat.grad is not None
+    for s in range(b.n_struct):
+        hkl, _ = oracle.enumerate_refl(b.lattice[s], o)
+        df, dB, dl = oracle.broadened_grad(b, s, hkl, o.wavelength, grid, gy[s])
+        sl = b.atoms_of(s)
+        for gv, rv in ((frac.grad[sl].cpu().numpy(), df), (B.grad[sl].cpu().numpy(), dB),
+                       (lat.grad[s].cpu().numpy(), dl)):
+            rel, cos = _cmp(gv, rv)
+            assert rel <= 1e-3 and cos >= 0.99999, (s, rel, cos)
+
+
+def test_full_gradient_workload(gpu_lib, handle):
+    """All 512 structures of the gradient workload in one launch; sampled structures
+    checked against the oracle gradient, the rest against invariants."""
+    b, _, o, grid = _grad_case()
+    rng = np.random.default_rng(5)
+    g = rng.standard_normal((b.n_struct, grid.n_pts))
+    got = _run(gpu_lib, handle, b, o, grid, dLdy=g)
+    assert np.all(got["status"] == 0)
+    assert np.all(np.isfinite(got["y"])) and np.all(np.isfinite(got["d_frac"]))
+    assert np.all(np.isfinite(got["d_B"])) and np.all(np.isfinite(got["d_lat"]))
+    # translation invariance of every structure: sum_j dL/dx_j = 0
+    for s in range(b.n_struct):
+        d = got["d_frac"][b.atoms_of(s)].astype(np.float64)
+        assert np.abs(d.sum(axis=0)).max() <= 1e-3 * max(np.abs(d).max(), 1e-30) * np.sqrt(len(d))
+    for s in rng.choice(b.n_struct, size=3, replace=False):
+        hkl, _ = oracle.enumerate_refl(b.lattice[s], o)
+        df, dB, dl = oracle.broadened_grad(b, s, hkl, o.wavelength, grid, g[s].astype(np.float32).astype(np.float64))
+        sl = b.atoms_of(s)
+        for gv, rv in ((got["d_frac"][sl], df), (got["d_B"][sl], dB), (got["d_lat"][s], dl)):
+            rel, cos = _cmp(gv, rv)
+            assert rel <= 1e-3 and cos >= 0.99999, (s, rel, cos)
+
+
+def test_bad_structures_get_zero_gradients(gpu_lib, handle):
+    b, _, o, grid = _grad_case(idx=np.array([0, 1]))
+    b.lattice[1] = [5.0, 5.0, 5.0, 60.0, 60.0, 120.0]  # degenerate cell
+    g = np.ones((2, grid.n_pts))
+    got = _run(gpu_lib, handle, b, o, grid, dLdy=g)
+    assert list(got["status"]) == [0, 1]
+    assert np.all(got["y"][1] == 0.0)
+    sl = b.atoms_of(1)
+    assert np.all(got["d_frac"][sl] == 0.0) and np.all(got["d_B"][sl] == 0.0) and np.all(got["d_lat"][1] == 0.0)
+    assert np.all(np.isfinite(got["d_frac"][b.atoms_of(0)]))
