@@ -176,6 +176,38 @@ int xrd_pattern_grad(xrd_handle* h, const xrd_batch* batch, const xrd_opts* opts
                      const float* dL_dy, float* d_frac, float* d_B, float* d_lattice, void* workspace,
                      size_t ws_bytes, void* stream /* cudaStream_t */);
 
+/*
+ * Launch-shape tuning of the structure-factor kernel (the batching pattern of
+ * the engine: thousands of uneven structures in one persistent launch). Runs
+ * xrd_pattern_batch (same arguments) with each shape -- 2 or 4 reflections per
+ * lane (warp tiles of 64 or 128 reflections) and, for XRD_FP32_PHASEFIX, 1, 2
+ * or 4 warps per CTA -- times the structure-factor stage with CUDA events,
+ * synchronising `stream`, and keeps the fastest shape in the handle; later calls
+ * with opts.tile = -1 use it. Writes the chosen tile and warps if the pointers
+ * are not NULL. Not capturable (it synchronises).
+ */
+int xrd_autotune(xrd_handle* h, const xrd_batch* batch, const xrd_opts* opts, const xrd_pattern* out,
+                 void* workspace, size_t ws_bytes, void* stream /* cudaStream_t */, int32_t* best_tile,
+                 int32_t* best_warps);
+
+/* Set the structure-factor launch shape directly (tile 64 or 128 reflections per
+ * warp, 1, 2 or 4 warps per CTA; warps apply to XRD_FP32_PHASEFIX). */
+int xrd_set_sf_shape(xrd_handle* h, int tile, int warps);
+
+/*
+ * CUDA graph of one xrd_pattern_batch call with exactly these arguments (the
+ * device buffers are baked into the graph: replays read the batch's current
+ * contents and rewrite the outputs). xrd_graph_create runs one eager call on a
+ * private stream, synchronises it, then captures a second call; *graph gets an
+ * opaque executable. xrd_graph_launch replays it on `stream`;
+ * xrd_graph_destroy frees it. The batch's sizes (and so the workspace) must
+ * not grow between replays.
+ */
+int xrd_graph_create(xrd_handle* h, const xrd_batch* batch, const xrd_opts* opts, const xrd_pattern* out,
+                     void* workspace, size_t ws_bytes, void** graph);
+int xrd_graph_launch(xrd_handle* h, void* graph, void* stream /* cudaStream_t */);
+void xrd_graph_destroy(void* graph);
+
 /* Stage timing: when enabled, xrd_pattern_batch records CUDA events around
  * each kernel on its stream; xrd_stage_times synchronises on the last event
  * and writes up to n stage durations in milliseconds (order: prep, atoms,

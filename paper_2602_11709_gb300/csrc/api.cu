@@ -18,11 +18,12 @@ struct xrd_handle {
     void* qbuf = nullptr;  // query scratch owned by the handle
     size_t qbuf_bytes = 0;
     const xrd::TTab* ttab = nullptr;  // 2-theta table on the handle's device
+    int sf_rb = 4, sf_warps = 2;        // structure-factor launch shape (xrd_autotune)
 };
 
 namespace {
 
-constexpr int kTile = 256;      // reflections per structure-factor tile (64 threads x 4)
+constexpr int kTileMin = 64;    // smallest structure-factor warp tile (32 lanes x 2 reflections)
 constexpr int kPostCap = 2048;  // reflections per structure kept in shared memory by k_post
 constexpr int kStages = 8;
 
@@ -56,7 +57,7 @@ size_t al(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Byte offsets of every array in the caller's workspace.
 struct Layout {
-    size_t geo, refl_cnt, refl_off, tile_off, order, npk, nfm, fam_soff, flags, coef32, atom32, atom64;
+    size_t geo, refl_cnt, refl_off, tile_off, order, tile_tab, npk, nfm, fam_soff, flags, coef32, atom32, atom64;
     size_t q, key, I, g_perm, g_bkt, g_flag, g_pstart, g_psum, g_fcnt;
     size_t st_tt, st_I, st_d, st_foff, st_hkl, st_mult;
     size_t total;
@@ -79,6 +80,7 @@ Layout layout(int64_t n, int64_t natoms, int zmax, int64_t R)
     L.coef32 = take(sizeof(xrd::Coef32) * (zmax + 1));
     L.atom32 = take(sizeof(xrd::Atom32) * natoms);
     L.atom64 = take(sizeof(xrd::Atom64) * natoms);
+    L.tile_tab = take(8 * (R / kTileMin + n + 1));
     L.q = take(8 * R);
     L.key = take(4 * R);
     L.I = take(8 * R);
@@ -101,7 +103,7 @@ Layout layout(int64_t n, int64_t natoms, int zmax, int64_t R)
 // Workspace of the broadened-pattern / gradient path: the geometry prefix of
 // the pattern layout plus the per-reflection state kept for the backward pass.
 struct LayoutG {
-    size_t geo, refl_cnt, refl_off, tile_off, order, flags, coef32, atom32, atom64, atom_src;
+    size_t geo, refl_cnt, refl_off, tile_off, order, tile_tab, flags, coef32, atom32, atom64;
     size_t q, key, Fx, Ig, tb, td, perm, U, V;
     size_t total;
 };
@@ -120,7 +122,7 @@ LayoutG layout_grad(int64_t n, int64_t natoms, int zmax, int64_t R)
     L.coef32 = take(sizeof(xrd::Coef32) * (zmax + 1));
     L.atom32 = take(sizeof(xrd::Atom32) * natoms);
     L.atom64 = take(sizeof(xrd::Atom64) * natoms);
-    L.atom_src = take(4 * natoms);
+    L.tile_tab = take(8 * (R / kTileMin + n + 1));
     L.q = take(8 * R);
     L.key = take(4 * R);
     L.Fx = take(16 * R);
@@ -172,9 +174,16 @@ int check_opts(xrd_handle* h, const xrd_opts* o)
     if (!(o->rel_cutoff >= 0.0 && o->rel_cutoff < 1.0)) return fail(h, XRD_EINVAL, "rel_cutoff must be in [0, 1)");
     if (o->scaled != 0 && o->scaled != 1) return fail(h, XRD_EINVAL, "scaled must be 0 or 1");
     if (o->precision < XRD_FP64 || o->precision > XRD_FP32_PHASEFIX) return fail(h, XRD_EINVAL, "unknown precision");
-    if (o->tile != -1 && o->tile != kTile) return fail(h, XRD_EINVAL, "tile must be -1 or 256");
+    if (o->tile != -1 && o->tile != 64 && o->tile != 128) return fail(h, XRD_EINVAL, "tile must be -1, 64 or 128");
     if (o->reserved != 0) return fail(h, XRD_EINVAL, "reserved must be 0");
     return XRD_OK;
+}
+
+// launch shape of the structure-factor kernel for this call
+void sf_shape(const xrd_handle* h, const xrd_opts* o, int& rb, int& warps)
+{
+    rb = o->tile == 64 ? 2 : (o->tile == 128 ? 4 : h->sf_rb);
+    warps = (o->precision == XRD_FP32_PHASEFIX) ? h->sf_warps : 2;
 }
 
 int check_batch(xrd_handle* h, const xrd_batch* b)
@@ -214,13 +223,13 @@ void radii(const xrd_opts* o, double& r2min, double& r2max, double& rmax)
 }
 
 xrd::GeomArgs geom_args(const xrd_batch* b, const xrd_opts* o, const Layout& L, char* ws, int64_t cap_refl,
-                        int64_t* totals, int32_t* status)
+                        int64_t* totals, int32_t* status, int tile)
 {
     xrd::GeomArgs g{};
     g.n_struct = b->n_struct;
     g.zmax = b->zmax;
     g.n_atoms = b->n_atoms;
-    g.tile = kTile;
+    g.tile = tile;
     radii(o, g.r2min, g.r2max, g.rmax);
     g.cap_refl = cap_refl;
     g.lattice = b->lattice;
@@ -238,6 +247,7 @@ xrd::GeomArgs geom_args(const xrd_batch* b, const xrd_opts* o, const Layout& L, 
     g.refl_off = (int64_t*)(ws + L.refl_off);
     g.tile_off = (int*)(ws + L.tile_off);
     g.order = (int*)(ws + L.order);
+    g.tile_tab = (int2*)(ws + L.tile_tab);
     g.abort_flag = (int*)(ws + L.flags);
     g.totals = totals;
     g.status = status;
@@ -361,7 +371,7 @@ int xrd_query_sizes(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, xrd_si
     for (int64_t c : cnt) {
         tot += c;
         mx = c > mx ? c : mx;
-        tiles += (c + kTile - 1) / kTile;
+        tiles += (c + 32 * h->sf_rb - 1) / (32 * h->sf_rb);
     }
     sizes->n_refl = tot;
     sizes->max_refl = mx;
@@ -394,12 +404,20 @@ int xrd_pattern_batch(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, cons
     cudaStream_t st = (cudaStream_t)stream;
     char* ws = (char*)workspace;
     const Layout L = layout(n, b->n_atoms, b->zmax, cap_refl);
-    xrd::GeomArgs ga = geom_args(b, o, L, ws, cap_refl, out->totals, out->status);
+    int rb, warps;
+    sf_shape(h, o, rb, warps);
+    xrd::GeomArgs ga = geom_args(b, o, L, ws, cap_refl, out->totals, out->status, 32 * rb);
 
     const bool prof = h->profiling;
+    unsigned rec_flags = 0;  // inside a stream capture, stage events become timed graph nodes
+    if (prof) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+            rec_flags = cudaEventRecordExternal;
+    }
     int stage = 0;
     auto mark = [&]() {
-        if (prof) cudaEventRecord(h->ev[stage], st);
+        if (prof) cudaEventRecordWithFlags(h->ev[stage], st, rec_flags);
         stage++;
     };
     cudaMemsetAsync(ws + L.flags, 0, 16, st);
@@ -419,13 +437,15 @@ int xrd_pattern_batch(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, cons
     sa.n_struct = (int)n;
     sa.precision = o->precision;
     sa.zmax = b->zmax;
-    sa.tile = kTile;
+    sa.tile = 32 * rb;
+    sa.rb = rb;
+    sa.warps = warps;
     sa.grid = h->sms;
     sa.lambda = o->lambda;
     sa.atom_off = b->atom_off;
     sa.refl_off = ga.refl_off;
     sa.tile_off = ga.tile_off;
-    sa.order = ga.order;
+    sa.tile_tab = ga.tile_tab;
     sa.tile_counter = ga.abort_flag + 2;
     sa.abort_flag = ga.abort_flag;
     sa.coef32 = ga.coef32;
@@ -502,6 +522,126 @@ int xrd_pattern_batch(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, cons
     return XRD_OK;
 }
 
+int xrd_set_sf_shape(xrd_handle* h, int tile, int warps)
+{
+    if (!h) return XRD_EINVAL;
+    if ((tile != 64 && tile != 128) || (warps != 1 && warps != 2 && warps != 4))
+        return fail(h, XRD_EINVAL, "shape must be tile 64 or 128, warps 1, 2 or 4");
+    h->sf_rb = tile / 32;
+    h->sf_warps = warps;
+    return XRD_OK;
+}
+
+int xrd_autotune(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, const xrd_pattern* out, void* workspace,
+                 size_t ws_bytes, void* stream, int32_t* best_tile, int32_t* best_warps)
+{
+    if (!h) return XRD_EINVAL;
+    static const int shapes[6][2] = {{4, 2}, {4, 1}, {4, 4}, {2, 2}, {2, 1}, {2, 4}};
+    const bool all = o && o->precision == XRD_FP32_PHASEFIX;
+    const int nshape = all ? 6 : 2;
+    const int keep_rb = h->sf_rb, keep_w = h->sf_warps;
+    const bool keep_prof = h->profiling;
+    xrd_opts oo = o ? *o : xrd_opts{};
+    oo.tile = -1;
+    float best = 1e30f;
+    int brb = keep_rb, bw = keep_w;
+    h->profiling = true;
+    for (int i = 0; i < nshape; i++) {
+        const int rb = all ? shapes[i][0] : (i == 0 ? 4 : 2);
+        h->sf_rb = rb;
+        h->sf_warps = all ? shapes[i][1] : 2;
+        float t = 1e30f;
+        for (int rep = 0; rep < 3; rep++) {
+            const int rc = xrd_pattern_batch(h, b, &oo, out, workspace, ws_bytes, stream);
+            if (rc != XRD_OK) {
+                h->sf_rb = keep_rb; h->sf_warps = keep_w; h->profiling = keep_prof;
+                return rc;
+            }
+            float ms[8];
+            const int m = xrd_stage_times(h, ms, 8);
+            if (m < 0) {
+                h->sf_rb = keep_rb; h->sf_warps = keep_w; h->profiling = keep_prof;
+                return -m;
+            }
+            if (m >= 6 && rep > 0 && ms[5] < t) t = ms[5];  // structure-factor stage, after one warm-up
+        }
+        if (t < best) { best = t; brb = h->sf_rb; bw = h->sf_warps; }
+    }
+    h->sf_rb = brb;
+    h->sf_warps = bw;
+    h->profiling = keep_prof;
+    if (best_tile) *best_tile = 32 * brb;
+    if (best_warps) *best_warps = bw;
+    return XRD_OK;
+}
+
+struct xrd_graph_exec {
+    cudaGraphExec_t exec = nullptr;
+    int device = 0;
+};
+
+int xrd_graph_create(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, const xrd_pattern* out, void* workspace,
+                     size_t ws_bytes, void** graph)
+{
+    if (!h || !graph) return XRD_EINVAL;
+    *graph = nullptr;
+    DeviceGuard dg(h->device);
+    cudaStream_t st = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(h, e, "xrd_graph_create: stream");
+    // one eager call validates the arguments and settles the per-device launch caches
+    int rc = xrd_pattern_batch(h, b, o, out, workspace, ws_bytes, st);
+    if (rc == XRD_OK) {
+        e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rc = cuda_fail(h, e, "xrd_graph_create: warm-up");
+    }
+    cudaGraph_t g = nullptr;
+    if (rc == XRD_OK) {
+        e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) rc = cuda_fail(h, e, "xrd_graph_create: begin capture");
+    }
+    if (rc == XRD_OK) {
+        const int rc2 = xrd_pattern_batch(h, b, o, out, workspace, ws_bytes, st);
+        e = cudaStreamEndCapture(st, &g);
+        if (rc2 != XRD_OK) rc = rc2;
+        else if (e != cudaSuccess) rc = cuda_fail(h, e, "xrd_graph_create: end capture");
+    }
+    xrd_graph_exec* x = nullptr;
+    if (rc == XRD_OK) {
+        x = new xrd_graph_exec();
+        x->device = h->device;
+        e = cudaGraphInstantiate(&x->exec, g, 0);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(h, e, "xrd_graph_create: instantiate");
+            delete x;
+            x = nullptr;
+        }
+    }
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(st);
+    *graph = x;
+    return rc;
+}
+
+int xrd_graph_launch(xrd_handle* h, void* graph, void* stream)
+{
+    if (!h || !graph) return XRD_EINVAL;
+    xrd_graph_exec* x = (xrd_graph_exec*)graph;
+    DeviceGuard dg(x->device);
+    const cudaError_t e = cudaGraphLaunch(x->exec, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "xrd_graph_launch");
+    return XRD_OK;
+}
+
+void xrd_graph_destroy(void* graph)
+{
+    if (!graph) return;
+    xrd_graph_exec* x = (xrd_graph_exec*)graph;
+    DeviceGuard dg(x->device);
+    if (x->exec) cudaGraphExecDestroy(x->exec);
+    delete x;
+}
+
 static xrd::GradArgs grad_args(xrd_handle* h, const xrd_batch* b, const xrd_grid* g, int W, double sigma,
                                const xrd_opts* o, const LayoutG& L, char* ws)
 {
@@ -531,7 +671,6 @@ static xrd::GradArgs grad_args(xrd_handle* h, const xrd_batch* b, const xrd_grid
     a.V = (float*)(ws + L.V);
     a.atom32 = (const xrd::Atom32*)(ws + L.atom32);
     a.coef32 = (const xrd::Coef32*)(ws + L.coef32);
-    a.atom_src = (const int*)(ws + L.atom_src);
     return a;
 }
 
@@ -560,7 +699,9 @@ int xrd_pattern_broadened(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, 
     ga.n_struct = (int)n;
     ga.zmax = b->zmax;
     ga.n_atoms = b->n_atoms;
-    ga.tile = kTile;
+    int rb, warps;
+    sf_shape(h, o, rb, warps);
+    ga.tile = 32 * rb;
     radii(o, ga.r2min, ga.r2max, ga.rmax);
     ga.cap_refl = cap_refl;
     ga.lattice = b->lattice;
@@ -574,11 +715,11 @@ int xrd_pattern_broadened(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, 
     ga.coef32 = (xrd::Coef32*)(ws + L.coef32);
     ga.atom32 = (xrd::Atom32*)(ws + L.atom32);
     ga.atom64 = (xrd::Atom64*)(ws + L.atom64);
-    ga.atom_src = (int*)(ws + L.atom_src);
     ga.refl_cnt = (int64_t*)(ws + L.refl_cnt);
     ga.refl_off = (int64_t*)(ws + L.refl_off);
     ga.tile_off = (int*)(ws + L.tile_off);
     ga.order = (int*)(ws + L.order);
+    ga.tile_tab = (int2*)(ws + L.tile_tab);
     ga.abort_flag = (int*)(ws + L.flags);
     ga.totals = totals;
     ga.status = status;
@@ -594,13 +735,15 @@ int xrd_pattern_broadened(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, 
     sa.n_struct = (int)n;
     sa.precision = XRD_FP32_PHASEFIX;
     sa.zmax = b->zmax;
-    sa.tile = kTile;
+    sa.tile = 32 * rb;
+    sa.rb = rb;
+    sa.warps = 2;
     sa.grid = h->sms;
     sa.lambda = o->lambda;
     sa.atom_off = b->atom_off;
     sa.refl_off = ga.refl_off;
     sa.tile_off = ga.tile_off;
-    sa.order = ga.order;
+    sa.tile_tab = ga.tile_tab;
     sa.tile_counter = ga.abort_flag + 2;
     sa.abort_flag = ga.abort_flag;
     sa.coef32 = ga.coef32;

@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(128) k_atoms(const int64_t* __restrict__ atom_
                                                const double* __restrict__ frac, const int16_t* __restrict__ Zin,
                                                const double* __restrict__ occ, const double* __restrict__ Bf, int zmax,
                                                Geo* __restrict__ geo, Atom32* __restrict__ a32,
-                                               Atom64* __restrict__ a64, int* __restrict__ src)
+                                               Atom64* __restrict__ a64)
 {
     __shared__ int off[kZmaxLimit + 1];
     __shared__ int zs[128];
@@ -155,13 +155,14 @@ __global__ void __launch_bounds__(128) k_atoms(const int64_t* __restrict__ atom_
             r.Y = fix32(y);
             r.Z = fix32(w);
             r.nb = (float)(-bb * 1.4426950408889634);
-            r.lo = o > 0.0 ? (float)log2(o) : -INFINITY;
+            r.lo = o == 1.0 ? 0.f : (o > 0.0 ? (float)log2(o) : -INFINITY);
             r.z = z;
+            r.src = (int)i;
+            r.pad = 0;
             a32[a0 + pos] = r;
             Atom64 d;
             d.x = x; d.y = y; d.z = w; d.B = bb; d.occ = o; d.zz = z; d.pad = 0;
             a64[a0 + pos] = d;
-            if (src) src[a0 + pos] = (int)i;
         }
         __syncthreads();  // every read of off[] for this chunk is done
         if (i < na) atomicAdd(&off[z], 1);
@@ -332,8 +333,8 @@ __global__ void __launch_bounds__(1024) k_scan_refl(const int64_t* __restrict__ 
                                                     const int64_t* __restrict__ atom_off, int n, int tile,
                                                     int64_t cap_refl, int64_t* __restrict__ refl_off,
                                                     int* __restrict__ tile_off, int* __restrict__ order,
-                                                    int* __restrict__ abort_flag, int64_t* __restrict__ totals,
-                                                    int32_t* __restrict__ status)
+                                                    int2* __restrict__ tile_tab, int* __restrict__ abort_flag,
+                                                    int64_t* __restrict__ totals, int32_t* __restrict__ status)
 {
     __shared__ long long ws[32];
     __shared__ long long carry;
@@ -407,6 +408,15 @@ __global__ void __launch_bounds__(1024) k_scan_refl(const int64_t* __restrict__ 
         __syncthreads();
     }
     const int over = total > cap_refl;
+    // 4. tile table: (structure, first reflection of the tile within it), largest-first order
+    __syncthreads();
+    if (!over && tile_tab)
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const int s = order[i];
+            const int nt = (int)((cnt[s] + tile - 1) / tile);
+            const int t0 = tile_off[i];
+            for (int t = 0; t < nt; t++) tile_tab[t0 + t] = make_int2(s, t * tile);
+        }
     if (threadIdx.x == 0) {
         refl_off[n] = total;
         tile_off[n] = over ? 0 : tcarry;
@@ -431,7 +441,7 @@ __global__ void __launch_bounds__(1024) k_scan_refl(const int64_t* __restrict__ 
 void launch_prep(const GeomArgs& a, cudaStream_t st)
 {
     const int n = a.n_struct;
-    if (n > 0) k_prep<<<(n + 127) / 128, 128, 0, st>>>(a.lattice, n, a.rmax, a.geo);
+    if (n > 0) k_prep<<<(n + 31) / 32, 32, 0, st>>>(a.lattice, n, a.rmax, a.geo);
     k_coef<<<1, 256, 0, st>>>(a.coef, a.zmax, a.coef32);
 }
 
@@ -439,14 +449,14 @@ void launch_atoms(const GeomArgs& a, cudaStream_t st)
 {
     if (a.n_struct > 0)
         k_atoms<<<a.n_struct, 128, 0, st>>>(a.atom_off, a.n_atoms, a.frac, a.Z, a.occ, a.B, a.zmax, a.geo, a.atom32,
-                                            a.atom64, a.atom_src);
+                                            a.atom64);
 }
 
 void launch_count_only(const GeomArgs& a, cudaStream_t st)
 {
     const int n = a.n_struct;
     if (n <= 0) return;
-    k_prep<<<(n + 127) / 128, 128, 0, st>>>(a.lattice, n, a.rmax, a.geo);
+    k_prep<<<(n + 31) / 32, 32, 0, st>>>(a.lattice, n, a.rmax, a.geo);
     k_count<<<n, 256, 0, st>>>(a.geo, a.r2min, a.r2max, (float)a.r2min, (float)a.r2max, a.refl_cnt);
 }
 
@@ -459,7 +469,7 @@ void launch_count(const GeomArgs& a, cudaStream_t st)
 void launch_scan_refl(const GeomArgs& a, cudaStream_t st)
 {
     k_scan_refl<<<1, 1024, 0, st>>>(a.refl_cnt, a.geo, a.atom_off, a.n_struct, a.tile, a.cap_refl, a.refl_off,
-                                    a.tile_off, a.order, a.abort_flag, a.totals, a.status);
+                                    a.tile_off, a.order, a.tile_tab, a.abort_flag, a.totals, a.status);
 }
 
 void launch_emit(const GeomArgs& a, cudaStream_t st)

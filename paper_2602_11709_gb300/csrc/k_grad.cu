@@ -310,7 +310,7 @@ __global__ void __launch_bounds__(kGradThreads) k_grad_atoms(const GradArgs a)
                 sz += v[2];
                 sb += v[3];
             }
-            const int64_t o = j0 + a.atom_src[j0 + at_i];
+            const int64_t o = j0 + at.src;
             const float fourpi = (float)(4.0 * kPi);
             a.d_frac[3 * o] = fourpi * sx;
             a.d_frac[3 * o + 1] = fourpi * sy;

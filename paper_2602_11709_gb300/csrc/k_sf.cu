@@ -7,10 +7,11 @@
 //   f(s) = Z - 41.78214 s^2 sum_i a_i exp(-b_i s^2),  s = |g| / 2,
 //   I = |F|^2 (1 + cos^2 2theta) / (sin^2 theta cos theta),  sin theta = lambda |g| / 2.
 //
-// GB300 mapping: a 64-thread CTA per tile of 256 reflections of one structure,
-// four reflections per thread; a persistent grid takes tiles from an atomic
-// queue in largest-first order. Atoms are staged in shared memory and every
-// lane walks the same atom list (one broadcast read per atom feeds four terms). Atoms are sorted by
+// GB300 mapping: every warp of a persistent grid takes 128-reflection tiles of
+// one structure (four reflections per lane) from an atomic queue in
+// largest-first order. The warp stages the structure's atoms in shared memory
+// and every lane walks the same atom list (one broadcast read per atom feeds
+// four terms). Atoms are sorted by
 // element, so f(s) is evaluated once per element run (a warp-uniform branch).
 // The FP32 variants use the SFU for sin/cos (MUFU.SIN/COS) and exp2 (MUFU.EX2,
 // which this part issues at twice the sin/cos rate). FP64 arithmetic runs at
@@ -23,22 +24,10 @@ namespace xrd {
 
 constexpr float kTwoPiOver2p32 = 1.4629180792671596e-09f;  // 2 pi / 2^32
 
-constexpr int kSfThreads = 64;
-constexpr int kSfRB = 4;  // reflections per thread: one atom record feeds four terms
-constexpr int kSfTile = kSfThreads * kSfRB;
-constexpr int kSfChunk = 256;  // atoms staged in shared memory at a time
-
-// position in the largest-first order whose tile range holds tile t
-__device__ __forceinline__ int tile_slot(const int* __restrict__ tile_off, int n, int t)
-{
-    int lo = 0, hi = n;  // largest lo with tile_off[lo] <= t
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (tile_off[mid] <= t) lo = mid;
-        else hi = mid;
-    }
-    return lo;
-}
+// Launch shapes (chosen by xrd_autotune; default RB = 4, 2 warps per CTA):
+// RB reflections per lane (one atom record feeds RB terms; tile = 32 RB
+// reflections per warp) and WARPS warps per CTA.
+constexpr int kSfChunk = 128;  // atoms staged per warp at a time
 
 __device__ __forceinline__ float f_of(const Coef32& c, int z, float s2)
 {
@@ -64,20 +53,21 @@ __device__ __forceinline__ float fprime_of(const Coef32& c, float s2)
     return acc;
 }
 
-// FP32 variants: RB reflections per thread share each atom record, which is
-// read from shared memory (a broadcast: every lane reads the same record).
+// FP32 variants: RB reflections per lane share each atom record, which the
+// warp stages in shared memory and every lane reads (a broadcast).
 // GRAD also accumulates dF/ds^2 = sum_j occ_j exp(-B_j s^2)(f_j' - B_j f_j) e^{i phi_j}.
-template <int PREC, bool GRAD>
+template <int PREC, bool GRAD, int kSfRB>
 __device__ void sf_tile_fp32(const SfArgs& a, int64_t r0, int64_t re, int64_t j0, int64_t j1, Atom32* sat,
                              const Coef32* scoef)
 {
     constexpr float ln2 = 0.69314718055994531f;
+    const int lane = threadIdx.x & 31;
     float s2[kSfRB], qf[kSfRB], Fr[kSfRB], Fi[kSfRB], f[kSfRB];
     float Gr[kSfRB], Gi[kSfRB], fp[kSfRB];
     uint32_t uh[kSfRB], uk[kSfRB], ul[kSfRB];
 #pragma unroll
     for (int i = 0; i < kSfRB; i++) {
-        const int64_t r = r0 + threadIdx.x + i * kSfThreads;
+        const int64_t r = r0 + lane + i * 32;
         const int64_t rr = r < re ? r : r0;
         qf[i] = d2f_pos(a.q[rr]);
         s2[i] = qf[i] * 0.25f;
@@ -89,9 +79,9 @@ __device__ void sf_tile_fp32(const SfArgs& a, int64_t r0, int64_t re, int64_t j0
     int zc = -1;
     for (int64_t c0 = j0; c0 < j1; c0 += kSfChunk) {
         const int nc = (int)min((int64_t)kSfChunk, j1 - c0);
-        __syncthreads();
-        for (int i = threadIdx.x; i < nc; i += kSfThreads) sat[i] = a.atom32[c0 + i];
-        __syncthreads();
+        __syncwarp();
+        for (int i = lane; i < nc; i += 32) sat[i] = a.atom32[c0 + i];
+        __syncwarp();
         for (int jj = 0; jj < nc; jj++) {
             const Atom32 at = sat[jj];
             if (at.z != zc) {  // uniform: every lane walks the same element-sorted list
@@ -132,7 +122,7 @@ __device__ void sf_tile_fp32(const SfArgs& a, int64_t r0, int64_t re, int64_t j0
     const float l2 = (float)(a.lambda * a.lambda * 0.25);
 #pragma unroll
     for (int i = 0; i < kSfRB; i++) {
-        const int64_t r = r0 + threadIdx.x + i * kSfThreads;
+        const int64_t r = r0 + lane + i * 32;
         if (r >= re) continue;
         const float I = fmaf(Fr[i], Fr[i], Fi[i] * Fi[i]) * lp_of(qf[i], l2);
         if (GRAD) {
@@ -145,10 +135,12 @@ __device__ void sf_tile_fp32(const SfArgs& a, int64_t r0, int64_t re, int64_t j0
     }
 }
 
+template <int kSfRB>
 __device__ void sf_tile_fp64(const SfArgs& a, int64_t r0, int64_t re, int64_t j0, int64_t j1)
 {
+    const int lane = threadIdx.x & 31;
     for (int i = 0; i < kSfRB; i++) {
-        const int64_t r = r0 + threadIdx.x + i * kSfThreads;
+        const int64_t r = r0 + lane + i * 32;
         const bool act = r < re;
         const int64_t rr = act ? r : r0;
         const double q = a.q[rr];
@@ -184,51 +176,64 @@ __device__ void sf_tile_fp64(const SfArgs& a, int64_t r0, int64_t re, int64_t j0
     }
 }
 
-// Persistent CTAs take tiles from a queue in largest-first order (tiles of the
-// structures with the most atoms first), so the uneven tail is short.
-template <int PREC, bool GRAD>
-__global__ void __launch_bounds__(kSfThreads) k_sf(const SfArgs a)
+// Persistent CTAs; every warp takes 128-reflection tiles from a queue in
+// largest-first order (tiles of the structures with the most atoms first).
+template <int PREC, bool GRAD, int RB, int WARPS>
+__global__ void __launch_bounds__(32 * WARPS) k_sf(const SfArgs a)
 {
-    __shared__ int t_sh;
-    __shared__ Atom32 sat[kSfChunk];
-    __shared__ Coef32 scoef[kZmaxLimit + 1];
+    constexpr int kSfThreads = 32 * WARPS;
+    __shared__ Atom32 sat[WARPS][kSfChunk];
+    extern __shared__ Coef32 scoef[];  // [zmax + 1]
     if (*a.abort_flag) return;
     const int ntiles = a.tile_off[a.n_struct];
-    if (PREC != XRD_FP64)
+    if (PREC != XRD_FP64) {
         for (int z = threadIdx.x; z <= a.zmax; z += kSfThreads) scoef[z] = a.coef32[z];
-    for (;;) {
         __syncthreads();
-        if (threadIdx.x == 0) t_sh = atomicAdd(a.tile_counter, 1);
-        __syncthreads();
-        const int t = t_sh;
-        if (t >= ntiles) break;
-        const int slot = tile_slot(a.tile_off, a.n_struct, t);
-        const int s = a.order[slot];
-        const int64_t rb = a.refl_off[s], re = a.refl_off[s + 1];
-        const int64_t r0 = rb + (int64_t)(t - a.tile_off[slot]) * kSfTile;
-        const int64_t j0 = a.atom_off[s], j1 = a.atom_off[s + 1];
-        if (PREC == XRD_FP64) sf_tile_fp64(a, r0, re, j0, j1);
-        else sf_tile_fp32<PREC, GRAD>(a, r0, re, j0, j1, sat, scoef);
     }
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (;;) {
+        int t = 0;
+        if (lane == 0) t = atomicAdd(a.tile_counter, 1);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= ntiles) break;
+        const int2 e = a.tile_tab[t];
+        const int s = e.x;
+        const int64_t rb = a.refl_off[s], re = a.refl_off[s + 1];
+        const int64_t r0 = rb + e.y;
+        const int64_t j0 = a.atom_off[s], j1 = a.atom_off[s + 1];
+        if (PREC == XRD_FP64) sf_tile_fp64<RB>(a, r0, re, j0, j1);
+        else sf_tile_fp32<PREC, GRAD, RB>(a, r0, re, j0, j1, sat[w], scoef);
+    }
+}
+
+template <int PREC, bool GRAD, int RB, int WARPS>
+static void launch_sf_shape(const SfArgs& a, cudaStream_t st)
+{
+    // persistent grid: as many CTAs as fit on the SMs at once (cached per device and zmax)
+    static int cache_per_sm[64] = {}, cache_zmax[64] = {};
+    const size_t smem = PREC == XRD_FP64 ? 0 : sizeof(Coef32) * (size_t)(a.zmax + 1);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const bool cached = dev >= 0 && dev < 64 && cache_per_sm[dev] > 0 && cache_zmax[dev] == a.zmax;
+    int per_sm = cached ? cache_per_sm[dev] : 0;
+    if (!cached) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sf<PREC, GRAD, RB, WARPS>, 32 * WARPS, smem) !=
+                cudaSuccess ||
+            per_sm < 1)
+            per_sm = 4;
+        if (dev >= 0 && dev < 64) { cache_per_sm[dev] = per_sm; cache_zmax[dev] = a.zmax; }
+    }
+    k_sf<PREC, GRAD, RB, WARPS><<<a.grid * per_sm, 32 * WARPS, smem, st>>>(a);
 }
 
 template <int PREC, bool GRAD>
 static void launch_sf_prec(const SfArgs& a, cudaStream_t st)
 {
-    static int per_sm_cache[64] = {};  // persistent grid: as many CTAs as fit on the SMs at once
-    int dev = 0;
-    cudaGetDevice(&dev);
-    int per_sm = (dev >= 0 && dev < 64) ? per_sm_cache[dev] : 0;
-    if (per_sm < 1) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sf<PREC, GRAD>, kSfThreads, 0) != cudaSuccess ||
-            per_sm < 1)
-            per_sm = 4;
-        if (dev >= 0 && dev < 64) per_sm_cache[dev] = per_sm;
-    }
-    k_sf<PREC, GRAD><<<a.grid * per_sm, kSfThreads, 0, st>>>(a);
+    if (a.rb == 2) launch_sf_shape<PREC, GRAD, 2, 2>(a, st);
+    else launch_sf_shape<PREC, GRAD, 4, 2>(a, st);
 }
 
-// a.grid = number of SMs
+// a.grid = number of SMs; a.rb, a.warps = launch shape (tile = 32 rb reflections)
 void launch_sf(const SfArgs& a, cudaStream_t st)
 {
     if (a.n_struct <= 0) return;
@@ -239,7 +244,17 @@ void launch_sf(const SfArgs& a, cudaStream_t st)
     switch (a.precision) {
     case XRD_FP64: launch_sf_prec<XRD_FP64, false>(a, st); break;
     case XRD_FP32_PHASE64: launch_sf_prec<XRD_FP32_PHASE64, false>(a, st); break;
-    default: launch_sf_prec<XRD_FP32_PHASEFIX, false>(a, st); break;
+    default:
+        if (a.rb == 2) {
+            if (a.warps == 1) launch_sf_shape<XRD_FP32_PHASEFIX, false, 2, 1>(a, st);
+            else if (a.warps == 4) launch_sf_shape<XRD_FP32_PHASEFIX, false, 2, 4>(a, st);
+            else launch_sf_shape<XRD_FP32_PHASEFIX, false, 2, 2>(a, st);
+        } else {
+            if (a.warps == 1) launch_sf_shape<XRD_FP32_PHASEFIX, false, 4, 1>(a, st);
+            else if (a.warps == 4) launch_sf_shape<XRD_FP32_PHASEFIX, false, 4, 4>(a, st);
+            else launch_sf_shape<XRD_FP32_PHASEFIX, false, 4, 2>(a, st);
+        }
+        break;
     }
 }
 

@@ -22,12 +22,15 @@ struct Geo {
     int status;    // XRD_OK or XRD_EINVAL
 };
 
-// Atom record for the FP32 structure-factor loops (sorted by element within a structure).
-struct __align__(8) Atom32 {
+// Atom record for the FP32 structure-factor loops (sorted by element within a
+// structure); 32 bytes, read as two 16-byte shared-memory loads.
+struct __align__(16) Atom32 {
     uint32_t X, Y, Z;  // coordinates in 32-bit fixed point: round(x * 2^32) mod 2^32
     float nb;          // -B * log2(e): exp(-B s^2) = 2^(nb s^2)
     float lo;          // log2(occ): occ folds into the same exp2
     int32_t z;         // element number
+    int32_t src;       // index of the atom within its structure in the caller's order
+    int32_t pad;
 };
 
 // Atom record for the FP64 loops and the FP64 phase.

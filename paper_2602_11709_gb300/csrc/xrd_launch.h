@@ -24,11 +24,11 @@ struct GeomArgs {
     Coef32* coef32;
     Atom32* atom32;
     Atom64* atom64;
-    int* atom_src;  // [n_atoms] index within its structure of each packed atom
     int64_t* refl_cnt;
     int64_t* refl_off;
     int* tile_off;
     int* order;
+    int2* tile_tab;  // [tiles] (structure, first reflection) of each structure-factor tile
     int* abort_flag;
     int64_t* totals;
     int32_t* status;
@@ -38,11 +38,12 @@ struct GeomArgs {
 
 struct SfArgs {
     int n_struct, precision, tile, grid, zmax;
+    int rb, warps;  // launch shape: reflections per lane (2 or 4), warps per CTA (1, 2 or 4)
     double lambda;
     const int64_t* atom_off;
     const int64_t* refl_off;
     const int* tile_off;  // [n_struct + 1] exclusive scan of tiles in largest-first order
-    const int* order;     // [n_struct] structures in largest-first order
+    const int2* tile_tab; // [tiles] (structure, first reflection within it), largest-first order
     int* tile_counter;    // work-queue head, zeroed by the caller
     const int* abort_flag;
     const Coef32* coef32;
@@ -127,7 +128,6 @@ struct GradArgs {
     float* V;          // dL/dI LP Im F
     const Atom32* atom32;
     const Coef32* coef32;
-    const int* atom_src;
     float* d_frac;
     float* d_B;
     float* d_lat;

@@ -55,7 +55,8 @@ class xrd_pattern(C.Structure):
 
 EXPORTS = ["xrd_create", "xrd_destroy", "xrd_last_error", "xrd_query_sizes", "xrd_pattern_batch",
            "xrd_set_profiling", "xrd_stage_times", "xrd_pattern_batch_noalloc", "xrd_pattern_broadened",
-           "xrd_pattern_grad"]
+           "xrd_pattern_grad", "xrd_autotune", "xrd_set_sf_shape", "xrd_graph_create", "xrd_graph_launch",
+           "xrd_graph_destroy"]
 
 _lib = None
 
@@ -94,6 +95,18 @@ def load(path: str = LIB_PATH):
                                    C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t,
                                    C.c_void_p]
     L.xrd_pattern_grad.restype = C.c_int
+    L.xrd_autotune.argtypes = [C.c_void_p, C.POINTER(xrd_batch), C.POINTER(xrd_opts), C.POINTER(xrd_pattern),
+                               C.c_void_p, C.c_size_t, C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+    L.xrd_autotune.restype = C.c_int
+    L.xrd_set_sf_shape.argtypes = [C.c_void_p, C.c_int, C.c_int]
+    L.xrd_set_sf_shape.restype = C.c_int
+    L.xrd_graph_create.argtypes = [C.c_void_p, C.POINTER(xrd_batch), C.POINTER(xrd_opts), C.POINTER(xrd_pattern),
+                                   C.c_void_p, C.c_size_t, C.POINTER(C.c_void_p)]
+    L.xrd_graph_create.restype = C.c_int
+    L.xrd_graph_launch.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+    L.xrd_graph_launch.restype = C.c_int
+    L.xrd_graph_destroy.argtypes = [C.c_void_p]
+    L.xrd_graph_destroy.restype = None
     _lib = L
     return L
 
@@ -278,6 +291,22 @@ class Handle:
                                               C.c_void_p(ws.data_ptr()), C.c_size_t(ws.numel() * ws.element_size()),
                                               _stream_ptr(stream)))
 
+    def autotune(self, db: DeviceBatch, opts: xrd_opts, out: PatternBuffers, ws, stream=None):
+        """Pick the fastest structure-factor launch shape for this batch; returns (tile, warps)."""
+        b, o = db.c(), out.c()
+        tile, warps = C.c_int32(), C.c_int32()
+        self._check(self.lib.xrd_autotune(self.h, C.byref(b), C.byref(opts), C.byref(o), C.c_void_p(ws.data_ptr()),
+                                          C.c_size_t(ws.numel() * ws.element_size()), _stream_ptr(stream),
+                                          C.byref(tile), C.byref(warps)))
+        return tile.value, warps.value
+
+    def set_sf_shape(self, tile: int, warps: int):
+        self._check(self.lib.xrd_set_sf_shape(self.h, int(tile), int(warps)))
+
+    def graph(self, db: DeviceBatch, opts: xrd_opts, out: PatternBuffers, ws):
+        """A CUDA graph of one pattern_batch call with these buffers."""
+        return Graph(self, db, opts, out, ws)
+
     def set_profiling(self, on: bool):
         self._check(self.lib.xrd_set_profiling(self.h, 1 if on else 0))
 
@@ -287,6 +316,33 @@ class Handle:
         if n < 0:
             raise XrdError(-n, self.lib.xrd_last_error(self.h).decode())
         return {STAGES[i]: float(buf[i]) for i in range(n)}
+
+
+class Graph:
+    """Captured xrd_pattern_batch call (xrd_graph_create); keeps its buffers alive."""
+
+    def __init__(self, handle: Handle, db: DeviceBatch, opts: xrd_opts, out: PatternBuffers, ws):
+        self.handle, self.keep = handle, (db, opts, out, ws)
+        b, o = db.c(), out.c()
+        g = C.c_void_p()
+        handle._check(handle.lib.xrd_graph_create(handle.h, C.byref(b), C.byref(opts), C.byref(o),
+                                                  C.c_void_p(ws.data_ptr()),
+                                                  C.c_size_t(ws.numel() * ws.element_size()), C.byref(g)))
+        self.g = g
+
+    def launch(self, stream=None):
+        self.handle._check(self.handle.lib.xrd_graph_launch(self.handle.h, self.g, _stream_ptr(stream)))
+
+    def close(self):
+        if self.g:
+            self.handle.lib.xrd_graph_destroy(self.g)
+            self.g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def workspace(nbytes: int, device="cuda"):
