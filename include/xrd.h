@@ -229,7 +229,7 @@ int xrd_stage_times(xrd_handle* h, float* ms, int n);
  *    (cudaGetSymbolAddress, which may load the module); make that first call
  *    before any stream capture on that device. The array then stays reserved
  *    on every device that used it until the process exits.
- *  - Limit: the per-structure and per-atom arrays (about 110 bytes per
+ *  - Limit: the per-structure and per-atom arrays (about 1.2 KB per
  *    structure and 72 bytes per atom) plus about 100 bytes per Friedel-unique
  *    reflection must fit in 64 MiB. A batch whose per-structure and per-atom
  *    part does not fit is rejected on the host with XRD_ECAPACITY; one whose

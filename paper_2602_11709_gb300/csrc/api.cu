@@ -57,9 +57,10 @@ size_t al(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Byte offsets of every array in the caller's workspace.
 struct Layout {
-    size_t geo, refl_cnt, refl_off, tile_off, order, tile_tab, npk, nfm, fam_soff, flags, coef32, atom32, atom64;
+    size_t geo, refl_cnt, tcnt, refl_off, tile_off, order, cls_list, tile_tab, npk, nfm, fam_soff, flags, coef32, atom32,
+        atom64;
     size_t q, key, I, g_perm, g_bkt, g_flag, g_pstart, g_psum, g_fcnt;
-    size_t st_tt, st_I, st_d, st_foff, st_hkl, st_mult;
+    size_t st_q, st_I, st_foff, st_hkl, st_mult;
     size_t total;
 };
 
@@ -70,13 +71,15 @@ Layout layout(int64_t n, int64_t natoms, int zmax, int64_t R)
     auto take = [&](size_t bytes) { const size_t at = o; o += al(bytes); return at; };
     L.geo = take(sizeof(xrd::Geo) * n);
     L.refl_cnt = take(8 * n);
+    L.tcnt = take(4 * 256 * n);
     L.refl_off = take(8 * (n + 1));
     L.tile_off = take(4 * (n + 1));
     L.order = take(4 * n);
+    L.cls_list = take(16 * n);
     L.npk = take(8 * n);
     L.nfm = take(8 * n);
     L.fam_soff = take(8 * (n + 1));
-    L.flags = take(16);
+    L.flags = take(64);
     L.coef32 = take(sizeof(xrd::Coef32) * (zmax + 1));
     L.atom32 = take(sizeof(xrd::Atom32) * natoms);
     L.atom64 = take(sizeof(xrd::Atom64) * natoms);
@@ -90,9 +93,8 @@ Layout layout(int64_t n, int64_t natoms, int zmax, int64_t R)
     L.g_pstart = take(4 * R);
     L.g_psum = take(8 * R);
     L.g_fcnt = take(4 * R);
-    L.st_tt = take(8 * R);
+    L.st_q = take(8 * R);
     L.st_I = take(8 * R);
-    L.st_d = take(8 * R);
     L.st_foff = take(4 * R);
     L.st_hkl = take(12 * R);
     L.st_mult = take(4 * R);
@@ -103,7 +105,7 @@ Layout layout(int64_t n, int64_t natoms, int zmax, int64_t R)
 // Workspace of the broadened-pattern / gradient path: the geometry prefix of
 // the pattern layout plus the per-reflection state kept for the backward pass.
 struct LayoutG {
-    size_t geo, refl_cnt, refl_off, tile_off, order, tile_tab, flags, coef32, atom32, atom64;
+    size_t geo, refl_cnt, tcnt, refl_off, tile_off, order, tile_tab, flags, coef32, atom32, atom64;
     size_t q, key, Fx, Ig, tb, td, perm, U, V;
     size_t total;
 };
@@ -115,10 +117,11 @@ LayoutG layout_grad(int64_t n, int64_t natoms, int zmax, int64_t R)
     auto take = [&](size_t bytes) { const size_t at = o; o += al(bytes); return at; };
     L.geo = take(sizeof(xrd::Geo) * n);
     L.refl_cnt = take(8 * n);
+    L.tcnt = take(4 * 256 * n);
     L.refl_off = take(8 * (n + 1));
     L.tile_off = take(4 * (n + 1));
     L.order = take(4 * n);
-    L.flags = take(16);
+    L.flags = take(64);
     L.coef32 = take(sizeof(xrd::Coef32) * (zmax + 1));
     L.atom32 = take(sizeof(xrd::Atom32) * natoms);
     L.atom64 = take(sizeof(xrd::Atom64) * natoms);
@@ -244,10 +247,12 @@ xrd::GeomArgs geom_args(const xrd_batch* b, const xrd_opts* o, const Layout& L, 
     g.atom32 = (xrd::Atom32*)(ws + L.atom32);
     g.atom64 = (xrd::Atom64*)(ws + L.atom64);
     g.refl_cnt = (int64_t*)(ws + L.refl_cnt);
+    g.tcnt = (int*)(ws + L.tcnt);
     g.refl_off = (int64_t*)(ws + L.refl_off);
     g.tile_off = (int*)(ws + L.tile_off);
     g.order = (int*)(ws + L.order);
     g.tile_tab = (int2*)(ws + L.tile_tab);
+    g.cls_list = (int*)(ws + L.cls_list);
     g.abort_flag = (int*)(ws + L.flags);
     g.totals = totals;
     g.status = status;
@@ -420,7 +425,7 @@ int xrd_pattern_batch(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, cons
         if (prof) cudaEventRecordWithFlags(h->ev[stage], st, rec_flags);
         stage++;
     };
-    cudaMemsetAsync(ws + L.flags, 0, 16, st);
+    cudaMemsetAsync(ws + L.flags, 0, 64, st);
     mark();
     xrd::launch_prep(ga, st);
     mark();
@@ -454,7 +459,8 @@ int xrd_pattern_batch(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, cons
     sa.atom64 = ga.atom64;
     sa.q = ga.q;
     sa.key = ga.key;
-    sa.I = (double*)(ws + L.I);
+    if (o->precision == XRD_FP64) sa.I = (double*)(ws + L.I);
+    else sa.If = (float*)(ws + L.I);
     sa.F = nullptr;
     xrd::launch_sf(sa, st);
     mark();
@@ -480,15 +486,18 @@ int xrd_pattern_batch(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, cons
     pa.q = ga.q;
     pa.key = ga.key;
     pa.I = sa.I;
+    pa.If = sa.If;
+    pa.cls_list = ga.cls_list;
+    pa.cls_cnt = ga.abort_flag + 4;
+    pa.grid = h->sms;
     pa.g_perm = (int*)(ws + L.g_perm);
     pa.g_bkt = (int*)(ws + L.g_bkt);
     pa.g_flag = (uint8_t*)(ws + L.g_flag);
     pa.g_pstart = (int*)(ws + L.g_pstart);
     pa.g_psum = (double*)(ws + L.g_psum);
     pa.g_fcnt = (int*)(ws + L.g_fcnt);
-    pa.st_tt = (double*)(ws + L.st_tt);
+    pa.st_q = (double*)(ws + L.st_q);
     pa.st_I = (double*)(ws + L.st_I);
-    pa.st_d = (double*)(ws + L.st_d);
     pa.st_foff = (int*)(ws + L.st_foff);
     pa.st_hkl = (int*)(ws + L.st_hkl);
     pa.st_mult = (int*)(ws + L.st_mult);
@@ -499,6 +508,7 @@ int xrd_pattern_batch(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, cons
 
     xrd::CompactArgs ca{};
     ca.n_struct = (int)n;
+    ca.grid = h->sms;
     ca.cap_peaks = out->cap_peaks;
     ca.cap_fam = out->cap_fam;
     ca.refl_off = ga.refl_off;
@@ -506,9 +516,10 @@ int xrd_pattern_batch(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, cons
     ca.npk = pa.npk;
     ca.nfm = pa.nfm;
     ca.fam_soff = (int64_t*)(ws + L.fam_soff);
-    ca.st_tt = pa.st_tt;
+    ca.st_q = pa.st_q;
     ca.st_I = pa.st_I;
-    ca.st_d = pa.st_d;
+    ca.l2d = pa.l2d;
+    ca.ttab = h->ttab;
     ca.st_foff = pa.st_foff;
     ca.st_hkl = pa.st_hkl;
     ca.st_mult = pa.st_mult;
@@ -716,6 +727,7 @@ int xrd_pattern_broadened(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, 
     ga.atom32 = (xrd::Atom32*)(ws + L.atom32);
     ga.atom64 = (xrd::Atom64*)(ws + L.atom64);
     ga.refl_cnt = (int64_t*)(ws + L.refl_cnt);
+    ga.tcnt = (int*)(ws + L.tcnt);
     ga.refl_off = (int64_t*)(ws + L.refl_off);
     ga.tile_off = (int*)(ws + L.tile_off);
     ga.order = (int*)(ws + L.order);
@@ -725,7 +737,7 @@ int xrd_pattern_broadened(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, 
     ga.status = status;
     ga.q = (double*)(ws + L.q);
     ga.key = (uint32_t*)(ws + L.key);
-    cudaMemsetAsync(ws + L.flags, 0, 16, st);
+    cudaMemsetAsync(ws + L.flags, 0, 64, st);
     xrd::launch_prep(ga, st);
     xrd::launch_atoms(ga, st);
     xrd::launch_count(ga, st);

@@ -251,21 +251,26 @@ __device__ __forceinline__ int inside(const Geo& g, int h, int k, int l, double 
 // Each thread takes columns (h, k) in a strided order; when emitting, a block
 // scan of the per-thread counts gives every thread a fixed output range, so
 // the emitted order is deterministic and no atomics are needed.
+// The counting pass (k_count) keeps each thread's count, so the emitting pass
+// (k_emit, same block size and column order) skips the recount.
 template <bool EMIT>
 __device__ int enumerate_struct(const Geo& g, double r2min, double r2max, float r2minf, float r2maxf, int64_t base,
-                                int64_t cap, double* __restrict__ qo, uint32_t* __restrict__ ko, int* tmp)
+                                int64_t cap, double* __restrict__ qo, uint32_t* __restrict__ ko, int* tmp,
+                                int local_in)
 {
     const int nk = 2 * g.K + 1;
     const int ncol = (g.H + 1) * nk;
-    int local = 0;
-    for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
-        const int h = c / nk, k = c % nk - g.K;
-        if (h == 0 && k < 0) continue;  // half-space: h > 0, or h = 0 and k >= 0
-        int lo, hi;
-        column_range(g.gf, g.L, h, k, r2maxf, lo, hi);
-        for (int l = lo; l <= hi; l++) local += inside(g, h, k, l, r2min, r2max, r2minf, r2maxf);
+    int local = local_in;
+    if (!EMIT) {
+        for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
+            const int h = c / nk, k = c % nk - g.K;
+            if (h == 0 && k < 0) continue;  // half-space: h > 0, or h = 0 and k >= 0
+            int lo, hi;
+            column_range(g.gf, g.L, h, k, r2maxf, lo, hi);
+            for (int l = lo; l <= hi; l++) local += inside(g, h, k, l, r2min, r2max, r2minf, r2maxf);
+        }
+        return local;
     }
-    if (!EMIT) return local;
     // exclusive offset of this thread's reflections within the structure
     const int nw = blockDim.x >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int inc = warp_incl_scan(local);
@@ -297,22 +302,24 @@ __device__ int enumerate_struct(const Geo& g, double r2min, double r2max, float 
 }
 
 __global__ void __launch_bounds__(256) k_count(const Geo* __restrict__ geo, double r2min, double r2max,
-                                               float r2minf, float r2maxf, int64_t* __restrict__ cnt)
+                                               float r2minf, float r2maxf, int64_t* __restrict__ cnt,
+                                               int* __restrict__ tcnt)
 {
     __shared__ int tmp[34];
     const int s = blockIdx.x;
     const Geo g = geo[s];
     int local = 0;
     if (g.status == XRD_OK && g.H >= 0)
-        local = enumerate_struct<false>(g, r2min, r2max, r2minf, r2maxf, 0, 0, nullptr, nullptr, tmp);
+        local = enumerate_struct<false>(g, r2min, r2max, r2minf, r2maxf, 0, 0, nullptr, nullptr, tmp, 0);
+    if (tcnt) tcnt[(int64_t)s * blockDim.x + threadIdx.x] = local;
     const int n = block_sum_int(local, tmp);
     if (threadIdx.x == 0) cnt[s] = n;
 }
 
 __global__ void __launch_bounds__(256) k_emit(const Geo* __restrict__ geo, double r2min, double r2max,
                                               float r2minf, float r2maxf, const int64_t* __restrict__ refl_off,
-                                              const int* __restrict__ abort_flag, double* __restrict__ q,
-                                              uint32_t* __restrict__ key)
+                                              const int* __restrict__ tcnt, const int* __restrict__ abort_flag,
+                                              double* __restrict__ q, uint32_t* __restrict__ key)
 {
     __shared__ int tmp[34];
     if (*abort_flag) return;
@@ -320,7 +327,8 @@ __global__ void __launch_bounds__(256) k_emit(const Geo* __restrict__ geo, doubl
     const Geo g = geo[s];
     const int64_t base = refl_off[s], cap = refl_off[s + 1] - base;
     if (g.status == XRD_OK && g.H >= 0 && cap > 0)
-        enumerate_struct<true>(g, r2min, r2max, r2minf, r2maxf, base, cap, q, key, tmp);
+        enumerate_struct<true>(g, r2min, r2max, r2minf, r2maxf, base, cap, q, key, tmp,
+                               tcnt[(int64_t)s * blockDim.x + threadIdx.x]);
 }
 
 // Single block: exclusive scan of the per-structure reflection counts, the
@@ -333,8 +341,9 @@ __global__ void __launch_bounds__(1024) k_scan_refl(const int64_t* __restrict__ 
                                                     const int64_t* __restrict__ atom_off, int n, int tile,
                                                     int64_t cap_refl, int64_t* __restrict__ refl_off,
                                                     int* __restrict__ tile_off, int* __restrict__ order,
-                                                    int2* __restrict__ tile_tab, int* __restrict__ abort_flag,
-                                                    int64_t* __restrict__ totals, int32_t* __restrict__ status)
+                                                    int2* __restrict__ tile_tab, int* __restrict__ cls_list,
+                                                    int* __restrict__ abort_flag, int64_t* __restrict__ totals,
+                                                    int32_t* __restrict__ status)
 {
     __shared__ long long ws[32];
     __shared__ long long carry;
@@ -417,6 +426,19 @@ __global__ void __launch_bounds__(1024) k_scan_refl(const int64_t* __restrict__ 
             const int t0 = tile_off[i];
             for (int t = 0; t < nt; t++) tile_tab[t0 + t] = make_int2(s, t * tile);
         }
+    // 5. post-processing size classes, filled in largest-first order
+    __shared__ int ccnt[4];
+    if (threadIdx.x < 4) ccnt[threadIdx.x] = 0;
+    __syncthreads();
+    if (!over && cls_list)
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const int s = order[i];
+            const long long c = cnt[s];
+            const int k = c <= kPostCapSmall ? 0 : (c <= kPostCapLarge ? 1 : 2);
+            cls_list[(int64_t)k * n + atomicAdd(&ccnt[k], 1)] = s;
+        }
+    __syncthreads();
+    if (threadIdx.x < 4) abort_flag[4 + threadIdx.x] = ccnt[threadIdx.x];
     if (threadIdx.x == 0) {
         refl_off[n] = total;
         tile_off[n] = over ? 0 : tcarry;
@@ -457,26 +479,27 @@ void launch_count_only(const GeomArgs& a, cudaStream_t st)
     const int n = a.n_struct;
     if (n <= 0) return;
     k_prep<<<(n + 31) / 32, 32, 0, st>>>(a.lattice, n, a.rmax, a.geo);
-    k_count<<<n, 256, 0, st>>>(a.geo, a.r2min, a.r2max, (float)a.r2min, (float)a.r2max, a.refl_cnt);
+    k_count<<<n, 256, 0, st>>>(a.geo, a.r2min, a.r2max, (float)a.r2min, (float)a.r2max, a.refl_cnt, nullptr);
 }
 
 void launch_count(const GeomArgs& a, cudaStream_t st)
 {
     if (a.n_struct > 0)
-        k_count<<<a.n_struct, 256, 0, st>>>(a.geo, a.r2min, a.r2max, (float)a.r2min, (float)a.r2max, a.refl_cnt);
+        k_count<<<a.n_struct, 256, 0, st>>>(a.geo, a.r2min, a.r2max, (float)a.r2min, (float)a.r2max, a.refl_cnt,
+                                            a.tcnt);
 }
 
 void launch_scan_refl(const GeomArgs& a, cudaStream_t st)
 {
     k_scan_refl<<<1, 1024, 0, st>>>(a.refl_cnt, a.geo, a.atom_off, a.n_struct, a.tile, a.cap_refl, a.refl_off,
-                                    a.tile_off, a.order, a.tile_tab, a.abort_flag, a.totals, a.status);
+                                    a.tile_off, a.order, a.tile_tab, a.cls_list, a.abort_flag, a.totals, a.status);
 }
 
 void launch_emit(const GeomArgs& a, cudaStream_t st)
 {
     if (a.n_struct > 0)
         k_emit<<<a.n_struct, 256, 0, st>>>(a.geo, a.r2min, a.r2max, (float)a.r2min, (float)a.r2max, a.refl_off,
-                                           a.abort_flag, a.q, a.key);
+                                           a.tcnt, a.abort_flag, a.q, a.key);
 }
 
 }  // namespace xrd

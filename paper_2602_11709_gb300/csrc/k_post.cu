@@ -20,8 +20,10 @@
 namespace xrd {
 
 constexpr int kPostThreads = 256;
-constexpr int kCapSmall = 1536;   // reflections per structure held in shared memory, small class
-constexpr int kCapLarge = 6144;   // large class (one CTA per SM); larger structures use global scratch
+// Size classes (reflections per structure held in shared memory); the scan
+// kernel sorts structures into them with the same bounds.
+constexpr int kCapSmall = kPostCapSmall;  // 256 threads, four CTAs per SM
+constexpr int kCapLarge = kPostCapLarge;  // 1024 threads, one CTA per SM; larger: global scratch
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
@@ -43,6 +45,7 @@ __global__ void k_ttab_init()
     const double sn = sin(th);
     TTab t;
     t.S = sn * sn;
+    t.T = j * kTabStepDeg;
     t.A = (float)sin(2.0 * th);
     t.Bc = (float)cos(2.0 * th);
     g_ttab[j] = t;
@@ -88,13 +91,14 @@ __device__ __forceinline__ bool before(double qa, uint32_t ka, double qb, uint32
     return a < b || (a == b && ka > kb);
 }
 
-template <typename PermT>
+// FI: intensities are FP32 (the FP32 structure-factor variants) and peak sums,
+// cutoff and scaling run in FP32; otherwise FP64 throughout.
+template <typename PermT, bool FI>
 __device__ void post_structure(const PostArgs& a, int s, int64_t base, int n, const double* q, const uint32_t* key,
                                PermT* perm, int* bkt, uint8_t* flag, int* pst, double* psum, int* fcnt, int* tmp,
                                double* dtmp)
 {
     const int tid = threadIdx.x, nt = blockDim.x;
-    const double* __restrict__ Ig = a.I + base;
     const float l2 = a.l2f, lh = a.lhf;
     // ---- bucket sort on |g|^3 in [r2min^1.5, r2max^1.5] ----
     const int nb = n;
@@ -162,49 +166,84 @@ __device__ void post_structure(const PostArgs& a, int s, int64_t base, int n, co
     if (tid == 0) bkt[np] = n;
     __syncthreads();
     // ---- per peak: merged intensity (each half-space reflection stands for g and -g) and family count ----
-    unsigned long long lmax = 0;  // peak sums are >= 0: max through the bit patterns
-    for (int p = tid; p < np; p += nt) {
-        const int i0 = bkt[p], i1 = bkt[p + 1];
-        double sum = 0.0;
-        int nfam = 0;
-        for (int i = i0; i < i1; i++) {
-            sum += 2.0 * Ig[perm[i]];
-            const uint32_t fk = family_key(key[perm[i]]);
-            bool lead = true;
-            for (int j = i0; j < i && lead; j++) lead = family_key(key[perm[j]]) != fk;
-            nfam += lead;
+    // Peak sums are >= 0, so their maximum is taken through the bit patterns.
+    double imax = 0.0, inv_imax = 0.0;
+    float imaxf = 0.f, inv_imaxf = 0.f;
+    if (FI) {
+        const float* __restrict__ Ig = a.If + base;
+        float* ps = (float*)psum;
+        unsigned long long lmax = 0;
+        for (int p = tid; p < np; p += nt) {
+            const int i0 = bkt[p], i1 = bkt[p + 1];
+            float sum = 0.f;
+            int nfam = 0;
+            for (int i = i0; i < i1; i++) {
+                sum = fmaf(2.f, Ig[perm[i]], sum);
+                const uint32_t fk = family_key(key[perm[i]]);
+                bool lead = true;
+                for (int j = i0; j < i && lead; j++) lead = family_key(key[perm[j]]) != fk;
+                nfam += lead;
+            }
+            ps[p] = sum;
+            fcnt[p] = nfam;
+            lmax = max(lmax, (unsigned long long)__float_as_uint(sum));
         }
-        psum[p] = sum;
-        fcnt[p] = nfam;
-        lmax = max(lmax, dbits(sum));
-    }
-    const double imax = __longlong_as_double((long long)block_max_u64(lmax, (unsigned long long*)dtmp));
-    const unsigned long long thr = dbits(a.cutoff * imax);
-    if (tid == 0) dtmp[0] = imax > 0.0 ? 1.0 / imax : 0.0;
-    __syncthreads();
-    const double inv_imax = dtmp[0];
-    // ---- cutoff, then compaction offsets of kept peaks and their families ----
-    for (int p = tid; p < np; p += nt) {
-        const bool keep = a.cutoff == 0.0 || dbits(psum[p]) > thr;
-        flag[p] = keep;
-        pst[p] = keep;
-        if (!keep) fcnt[p] = 0;
+        imaxf = __uint_as_float((uint32_t)block_max_u64(lmax, (unsigned long long*)dtmp));
+        inv_imaxf = imaxf > 0.f ? 1.f / imaxf : 0.f;
+        const uint32_t thr = __float_as_uint((float)a.cutoff * imaxf);
+        for (int p = tid; p < np; p += nt) {
+            const bool keep = a.cutoff == 0.0 || __float_as_uint(ps[p]) > thr;
+            flag[p] = keep;
+            pst[p] = keep;
+            if (!keep) fcnt[p] = 0;
+        }
+    } else {
+        const double* __restrict__ Ig = a.I + base;
+        unsigned long long lmax = 0;
+        for (int p = tid; p < np; p += nt) {
+            const int i0 = bkt[p], i1 = bkt[p + 1];
+            double sum = 0.0;
+            int nfam = 0;
+            for (int i = i0; i < i1; i++) {
+                sum += 2.0 * Ig[perm[i]];
+                const uint32_t fk = family_key(key[perm[i]]);
+                bool lead = true;
+                for (int j = i0; j < i && lead; j++) lead = family_key(key[perm[j]]) != fk;
+                nfam += lead;
+            }
+            psum[p] = sum;
+            fcnt[p] = nfam;
+            lmax = max(lmax, dbits(sum));
+        }
+        imax = __longlong_as_double((long long)block_max_u64(lmax, (unsigned long long*)dtmp));
+        const unsigned long long thr = dbits(a.cutoff * imax);
+        if (tid == 0) dtmp[0] = imax > 0.0 ? 1.0 / imax : 0.0;
+        __syncthreads();
+        inv_imax = dtmp[0];
+        // ---- cutoff, then compaction offsets of kept peaks and their families ----
+        for (int p = tid; p < np; p += nt) {
+            const bool keep = a.cutoff == 0.0 || dbits(psum[p]) > thr;
+            flag[p] = keep;
+            pst[p] = keep;
+            if (!keep) fcnt[p] = 0;
+        }
     }
     __syncthreads();
     const int nk = block_excl_scan(pst, np, tmp);
     const int nf = block_excl_scan(fcnt, np, tmp);
     __syncthreads();
-    const double l2d = a.l2d;
     for (int p = tid; p < np; p += nt) {
         if (!flag[p]) continue;
         const int i0 = bkt[p], i1 = bkt[p + 1];
         const int64_t o = base + pst[p];
-        const double qa = q[perm[i0]];
-        a.st_tt[o] = two_theta_of(fmin(qa * l2d, 1.0), a.ttab);
-        const double y0 = f2d_fast(rsqrtf(d2f_pos(qa)));  // d = 1/sqrt(q): FP32 seed, one FP64 Newton step
-        a.st_d[o] = y0 * fma(-0.5 * qa * y0, y0, 1.5);
-        const double ps = psum[p];  // the largest peak maps to exactly 100
-        a.st_I[o] = (a.scaled && imax > 0.0) ? (ps == imax ? 100.0 : 100.0 * (ps * inv_imax)) : ps;
+        a.st_q[o] = q[perm[i0]];  // anchor |g|^2: 2-theta and d are formed during compaction
+        if (FI) {  // the largest peak maps to exactly 100
+            const float ps = ((const float*)psum)[p];
+            a.st_I[o] = f2d_fast((a.scaled && imaxf > 0.f) ? (ps == imaxf ? 100.f : 100.f * (ps * inv_imaxf)) : ps);
+        } else {
+            const double ps = psum[p];
+            a.st_I[o] = (a.scaled && imax > 0.0) ? (ps == imax ? 100.0 : 100.0 * (ps * inv_imax)) : ps;
+        }
         a.st_foff[o] = fcnt[p];
         // families: leaders are first members of each family; rank by descending representative
         for (int i = i0; i < i1; i++) {
@@ -241,43 +280,48 @@ __device__ void post_structure(const PostArgs& a, int s, int64_t base, int n, co
     }
 }
 
-// One CTA per structure. CAP > 0: structures with cap_lo < n <= CAP, in shared
-// memory. CAP == 0: structures with n > cap_lo, on global scratch.
-template <int CAP, int NT>
-__global__ void __launch_bounds__(NT) k_post(const PostArgs a, int cap_lo)
+// Persistent CTAs over one size class of structures (a list built by the scan
+// kernel, largest first). CAP > 0: the structure's reflections live in shared
+// memory (n <= CAP). CAP == 0: global scratch.
+template <int CAP, int NT, bool FI>
+__global__ void __launch_bounds__(NT) k_post(const PostArgs a, int cls)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int tmp[34];
     __shared__ double dtmp[32];
     if (*a.abort_flag) return;
-    const int s = blockIdx.x;
-    const int64_t base = a.refl_off[s];
-    const int n = (int)(a.refl_off[s + 1] - base);
-    if (CAP > 0 && cap_lo == 0 && n == 0) {  // the smallest class also writes empty structures
-        if (threadIdx.x == 0) { a.npk[s] = 0; a.nfm[s] = 0; }
-        return;
-    }
-    if (n <= cap_lo || (CAP > 0 && n > CAP)) return;
-    if (CAP > 0) {
-        const size_t c = (size_t)CAP;
-        unsigned char* p = smem;
-        double* sq = (double*)p; p += align16(c * 8);
-        uint32_t* sk = (uint32_t*)p; p += align16(c * 4);
-        uint16_t* perm = (uint16_t*)p; p += align16(c * 2);
-        int* bkt = (int*)p; p += align16((c + 1) * 4);
-        uint8_t* flag = (uint8_t*)p; p += align16(c);
-        int* pst = (int*)p; p += align16(c * 4);
-        double* psum = (double*)p; p += align16(c * 8);
-        int* fcnt = (int*)p;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            sq[i] = a.q[base + i];
-            sk[i] = a.key[base + i];
+    const int cnt = a.cls_cnt[cls];
+    const int* __restrict__ list = a.cls_list + (int64_t)cls * a.n_struct;
+    for (int li = blockIdx.x; li < cnt; li += gridDim.x) {
+        __syncthreads();  // the previous structure is done with shared memory
+        const int s = list[li];
+        const int64_t base = a.refl_off[s];
+        const int n = (int)(a.refl_off[s + 1] - base);
+        if (n == 0) {
+            if (threadIdx.x == 0) { a.npk[s] = 0; a.nfm[s] = 0; }
+            continue;
         }
-        __syncthreads();
-        post_structure<uint16_t>(a, s, base, n, sq, sk, perm, bkt, flag, pst, psum, fcnt, tmp, dtmp);
-    } else {
-        post_structure<int>(a, s, base, n, a.q + base, a.key + base, a.g_perm + base, a.g_bkt + base + s,
-                            a.g_flag + base, a.g_pstart + base, a.g_psum + base, a.g_fcnt + base, tmp, dtmp);
+        if (CAP > 0) {
+            const size_t c = (size_t)CAP;
+            unsigned char* p = smem;
+            double* sq = (double*)p; p += align16(c * 8);
+            uint32_t* sk = (uint32_t*)p; p += align16(c * 4);
+            uint16_t* perm = (uint16_t*)p; p += align16(c * 2);
+            int* bkt = (int*)p; p += align16((c + 1) * 4);
+            uint8_t* flag = (uint8_t*)p; p += align16(c);
+            int* pst = (int*)p; p += align16(c * 4);
+            double* psum = (double*)p; p += align16(c * 8);
+            int* fcnt = (int*)p;
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                sq[i] = a.q[base + i];
+                sk[i] = a.key[base + i];
+            }
+            __syncthreads();
+            post_structure<uint16_t, FI>(a, s, base, n, sq, sk, perm, bkt, flag, pst, psum, fcnt, tmp, dtmp);
+        } else {
+            post_structure<int, FI>(a, s, base, n, a.q + base, a.key + base, a.g_perm + base, a.g_bkt + base + s,
+                                    a.g_flag + base, a.g_pstart + base, a.g_psum + base, a.g_fcnt + base, tmp, dtmp);
+        }
     }
 }
 
@@ -335,57 +379,98 @@ __global__ void __launch_bounds__(1024) k_scan_out(const CompactArgs a)
         for (int s = threadIdx.x; s < n; s += blockDim.x) a.out.status[s] = XRD_ECAPACITY;
 }
 
-__global__ void __launch_bounds__(256) k_compact(const CompactArgs a)
+// largest s with off[s] <= i, for off[0] = 0 <= i < off[n]
+__device__ __forceinline__ int owner(const int64_t* __restrict__ off, int n, int64_t i)
 {
-    if (*a.abort_flag || *a.out_abort) return;
-    const int s = blockIdx.x;
-    const int64_t base = a.refl_off[s], pb = a.out.peak_off[s], fb = a.fam_soff[s];
-    const int64_t np = a.npk[s], nf = a.nfm[s];
-    const double* __restrict__ stt = a.st_tt + base;
-    const double* __restrict__ sI = a.st_I + base;
-    const double* __restrict__ sd = a.st_d + base;
-    const int* __restrict__ sfo = a.st_foff + base;
-    const int* __restrict__ shkl = a.st_hkl + 3 * base;
-    const int* __restrict__ smul = a.st_mult + base;
-    double* __restrict__ ott = a.out.two_theta + pb;
-    double* __restrict__ oI = a.out.intensity + pb;
-    double* __restrict__ od = a.out.d_hkl + pb;
-    int64_t* __restrict__ ofo = a.out.fam_off + pb;
-    int* __restrict__ ohkl = a.out.hkl + 3 * fb;
-    int* __restrict__ omul = a.out.mult + fb;
-    for (int64_t p = threadIdx.x; p < np; p += blockDim.x) {
-        const double t = stt[p], I = sI[p], d = sd[p];
-        const int fo = sfo[p];
-        ott[p] = t;
-        oI[p] = I;
-        od[p] = d;
-        ofo[p] = fb + fo;
+    int lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (off[mid] <= i) lo = mid;
+        else hi = mid;
     }
-    for (int64_t f = threadIdx.x; f < 3 * nf; f += blockDim.x) ohkl[f] = shkl[f];
-    for (int64_t f = threadIdx.x; f < nf; f += blockDim.x) omul[f] = smul[f];
+    return lo;
 }
 
+// Kept peaks into the dense CSR outputs, one thread per output peak over the
+// whole batch: 2-theta and d are formed here from the anchor |g|^2, so their
+// FP64 work is spread evenly over the GPU.
+__global__ void __launch_bounds__(256) k_compact_peaks(const CompactArgs a)
+{
+    if (*a.abort_flag || *a.out_abort) return;
+    const int n = a.n_struct;
+    const int64_t total = a.out.peak_off[n];
+    for (int64_t P = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; P < total; P += (int64_t)gridDim.x * blockDim.x) {
+        const int s = owner(a.out.peak_off, n, P);
+        const int64_t src = a.refl_off[s] + (P - a.out.peak_off[s]);
+        const double qa = a.st_q[src], I = a.st_I[src];
+        const int fo = a.st_foff[src];
+        double X = qa * a.l2d;  // sin^2 theta, at most 1 (bit compare: X >= 0)
+        if ((unsigned long long)__double_as_longlong(X) > 0x3FF0000000000000ull) X = 1.0;
+        a.out.two_theta[P] = two_theta_of(X, a.ttab);
+        a.out.d_hkl[P] = inv_sqrt_df(qa);
+        a.out.intensity[P] = I;
+        a.out.fam_off[P] = a.fam_soff[s] + fo;
+    }
+}
+
+// Families into the dense CSR outputs, one thread per output family.
+__global__ void __launch_bounds__(256) k_compact_fams(const CompactArgs a)
+{
+    if (*a.abort_flag || *a.out_abort) return;
+    const int n = a.n_struct;
+    const int64_t total = a.fam_soff[n];
+    for (int64_t F = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; F < total; F += (int64_t)gridDim.x * blockDim.x) {
+        const int s = owner(a.fam_soff, n, F);
+        const int64_t src = a.refl_off[s] + (F - a.fam_soff[s]);
+        a.out.hkl[3 * F] = a.st_hkl[3 * src];
+        a.out.hkl[3 * F + 1] = a.st_hkl[3 * src + 1];
+        a.out.hkl[3 * F + 2] = a.st_hkl[3 * src + 2];
+        a.out.mult[F] = a.st_mult[src];
+    }
+}
+
+template <int CAP, int NT, bool FI>
+static void launch_post_class(const PostArgs& a, int cls, cudaStream_t st)
+{
+    const size_t smem = CAP > 0 ? post_smem_bytes(CAP) : 0;
+    static int per_sm_cache[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int per_sm = (dev >= 0 && dev < 64) ? per_sm_cache[dev] : 0;
+    if (per_sm < 1) {
+        if (smem > 48 * 1024) cudaFuncSetAttribute(k_post<CAP, NT, FI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_post<CAP, NT, FI>, NT, smem) != cudaSuccess ||
+            per_sm < 1)
+            per_sm = 1;
+        if (dev >= 0 && dev < 64) per_sm_cache[dev] = per_sm;
+    }
+    const int grid = min(a.grid * per_sm, a.n_struct);
+    k_post<CAP, NT, FI><<<grid, NT, smem, st>>>(a, cls);
+}
+
+template <bool FI>
+static void launch_post_fi(const PostArgs& a, cudaStream_t st)
+{
+    launch_post_class<kCapSmall, kPostThreads, FI>(a, 0, st);
+    launch_post_class<kCapLarge, 1024, FI>(a, 1, st);
+    launch_post_class<0, 1024, FI>(a, 2, st);
+}
+
+// a.grid = number of SMs
 void launch_post(const PostArgs& a, cudaStream_t st)
 {
     if (a.n_struct <= 0) return;
-    const size_t s1 = post_smem_bytes(kCapSmall), s2 = post_smem_bytes(kCapLarge);
-    static bool attr_done[64] = {};
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev < 0 || dev >= 64 || !attr_done[dev]) {
-        cudaFuncSetAttribute(k_post<kCapSmall, kPostThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s1);
-        cudaFuncSetAttribute(k_post<kCapLarge, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s2);
-        if (dev >= 0 && dev < 64) attr_done[dev] = true;
-    }
-    k_post<kCapSmall, kPostThreads><<<a.n_struct, kPostThreads, s1, st>>>(a, 0);
-    k_post<kCapLarge, 1024><<<a.n_struct, 1024, s2, st>>>(a, kCapSmall);
-    k_post<0, 1024><<<a.n_struct, 1024, 0, st>>>(a, kCapLarge);
+    if (a.If) launch_post_fi<true>(a, st);
+    else launch_post_fi<false>(a, st);
 }
 
 void launch_compact(const CompactArgs& a, cudaStream_t st)
 {
     k_scan_out<<<1, 1024, 0, st>>>(a);
-    if (a.n_struct > 0) k_compact<<<a.n_struct, 256, 0, st>>>(a);
+    if (a.n_struct > 0) {
+        k_compact_peaks<<<a.grid * 8, 256, 0, st>>>(a);
+        k_compact_fams<<<a.grid * 8, 256, 0, st>>>(a);
+    }
 }
 
 }  // namespace xrd

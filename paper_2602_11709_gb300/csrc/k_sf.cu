@@ -129,7 +129,7 @@ __device__ void sf_tile_fp32(const SfArgs& a, int64_t r0, int64_t re, int64_t j0
             a.Fx[r] = make_float4(Fr[i], Fi[i], Gr[i], Gi[i]);
             a.Ig[r] = I;
         } else {
-            a.I[r] = f2d_fast(I);
+            a.If[r] = I;
             if (a.F) a.F[r] = make_float2(Fr[i], Fi[i]);
         }
     }

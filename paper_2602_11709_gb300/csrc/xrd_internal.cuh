@@ -12,6 +12,8 @@ constexpr double kPi = 3.14159265358979323846;
 constexpr double kFScale = 41.78214;  // Mott-Bethe factor 8 pi^2 a0 of f(s) (Sec. 1, atomic scattering factors)
 constexpr int kZmaxLimit = 255;
 constexpr int kHklLimit = 511;        // |h|, |k|, |l| fit the 10-bit fields of the packed key
+constexpr int kPostCapSmall = 1536;   // post-processing size classes (reflections per structure)
+constexpr int kPostCapLarge = 6144;
 
 // Per-structure geometry written by k_prep (step S0).
 struct Geo {
@@ -115,22 +117,31 @@ constexpr int kTabN = 1024;
 constexpr double kTabStepDeg = 360.0 / 4096.0;  // 2theta spacing of the table
 struct TTab {
     double S;  // sin^2 theta_j
+    double T;  // 2 theta_j in degrees (= j * 360 / 4096, exact)
     float A;   // sin 2 theta_j
     float Bc;  // cos 2 theta_j
 };
 
+// Any finite double -> float by bit arithmetic (truncation; magnitudes below
+// the float range become 0). Keeps the conversion off the FP64 unit.
 __device__ __forceinline__ float d2f_signed(double x)
 {
-    const float m = x == 0.0 ? 0.f : d2f_pos(fabs(x));
-    return x < 0.0 ? -m : m;
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned long long m = b & 0x7FFFFFFFFFFFFFFFull;
+    if (m < 0x3810000000000000ull) return 0.f;  // |x| < 2^-126
+    const float f = d2f_pos(__longlong_as_double((long long)m));
+    return (b >> 63) ? -f : f;
 }
 
-// 2theta in degrees of a reflection with sin^2 theta = X (FP64, 0 < X <= 1)
+// 2theta in degrees of a reflection with sin^2 theta = X (FP64, 0 < X <= 1).
+// Comparisons run on the bit patterns (X >= 0), so the FP64 unit sees only the
+// few subtractions that need its precision.
 __device__ __forceinline__ double two_theta_of(double X, const TTab* __restrict__ tab)
 {
-    const bool comp = X > 0.5;
-    const double Y = comp ? 1.0 - X : X;  // exact for X in (0.5, 1]
-    const float Yf = Y > 0.0 ? d2f_pos(Y) : 0.f;
+    const unsigned long long xb = (unsigned long long)__double_as_longlong(X);
+    const bool comp = xb > 0x3FE0000000000000ull;  // X > 0.5
+    const double Y = comp ? 1.0 - X : X;            // exact for X in (0.5, 1]
+    const float Yf = d2f_signed(Y);
     const float th0 = asinf(sqrtf(Yf));
     int j = __float2int_rn(th0 * (float)(4.0 * kTabN / kPi));
     j = min(max(j, 0), kTabN);
@@ -150,9 +161,23 @@ __device__ __forceinline__ double two_theta_of(double X, const TTab* __restrict_
             const float fp = fmaf(e.A, 1.f - 0.5f * u2, e.Bc * su);
             u -= fv / fp;
         }
-        t = (double)j * kTabStepDeg + f2d_fast(u * (float)(180.0 / kPi));
+        t = e.T + f2d_fast(u * (float)(180.0 / kPi));
     }
     return comp ? 180.0 - t : t;
+}
+
+// d = 1/sqrt(q) for q > 0 in float range: an FP32 seed refined by one Newton
+// step whose residual 1 - q y0^2 is formed exactly in FP32 (q split into two
+// floats, y0^2 into two floats); about 1e-13 relative, two FP64 additions.
+__device__ __forceinline__ double inv_sqrt_df(double q)
+{
+    const float qh = d2f_pos(q);
+    const float ql = d2f_signed(q - f2d_fast(qh));  // exact: qh is q truncated
+    const float y0 = rsqrtf(qh);
+    const float p = y0 * y0, pe = fmaf(y0, y0, -p);
+    float r = fmaf(-qh, p, 1.f);
+    r = fmaf(-qh, pe, fmaf(-ql, p, r));
+    return f2d_fast(y0) + f2d_fast(0.5f * y0 * r);
 }
 
 // ---- block-wide primitives over generic pointers (shared or global memory) ----

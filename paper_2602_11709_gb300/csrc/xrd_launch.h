@@ -25,11 +25,13 @@ struct GeomArgs {
     Atom32* atom32;
     Atom64* atom64;
     int64_t* refl_cnt;
+    int* tcnt;       // [n_struct][256] per-thread reflection counts of the counting pass
     int64_t* refl_off;
     int* tile_off;
     int* order;
     int2* tile_tab;  // [tiles] (structure, first reflection) of each structure-factor tile
-    int* abort_flag;
+    int* cls_list;   // [4][n_struct] post-processing size classes (nullptr: not built)
+    int* abort_flag; // flags[0]; flags[1] output abort, flags[2] tile queue, flags[4..7] class counts
     int64_t* totals;
     int32_t* status;
     double* q;
@@ -52,14 +54,15 @@ struct SfArgs {
     const Atom64* atom64;
     const double* q;
     const uint32_t* key;
-    double* I;   // per reflection intensity |F|^2 LP (one Friedel half-space member)
+    double* I;   // per reflection intensity |F|^2 LP (one Friedel half-space member), XRD_FP64
+    float* If;   // the same in FP32 for the FP32 variants
     float2* F;   // optional per-reflection F (nullptr: not stored)
     float4* Fx;  // gradient path: (Re F, Im F, Re dF/ds^2, Im dF/ds^2) per reflection (nullptr otherwise)
     float* Ig;   // gradient path: |F|^2 LP per reflection
 };
 
 struct PostArgs {
-    int n_struct, cap_smem, scaled;
+    int n_struct, cap_smem, scaled, grid;  // grid = number of SMs
     double lambda, tol, cutoff, r2min, r2max;
     double l2d;                          // lambda^2 / 4
     const TTab* ttab;                    // 2-theta table (device)
@@ -68,7 +71,10 @@ struct PostArgs {
     const int* abort_flag;
     const double* q;
     const uint32_t* key;
-    const double* I;
+    const double* I;    // FP64 intensities (XRD_FP64), or
+    const float* If;    // FP32 intensities (the FP32 variants)
+    const int* cls_list;  // [4][n_struct] structures of each size class, largest first
+    const int* cls_cnt;   // [4]
     // global scratch for structures larger than cap_smem (indexed by reflection)
     int* g_perm;
     int* g_bkt;   // n_refl + n_struct entries
@@ -77,9 +83,8 @@ struct PostArgs {
     double* g_psum;
     int* g_fcnt;
     // staging of kept peaks and families (indexed by reflection offset)
-    double* st_tt;
+    double* st_q;   // anchor |g|^2 of each kept peak
     double* st_I;
-    double* st_d;
     int* st_foff;
     int* st_hkl;   // 3 per family
     int* st_mult;
@@ -88,16 +93,17 @@ struct PostArgs {
 };
 
 struct CompactArgs {
-    int n_struct;
+    int n_struct, grid;  // grid = number of SMs
     int64_t cap_peaks, cap_fam;
     const int64_t* refl_off;
     const int* abort_flag;
     const int64_t* npk;
     const int64_t* nfm;
     int64_t* fam_soff;  // [n_struct + 1] scratch: exclusive scan of nfm
-    const double* st_tt;
+    const double* st_q;
     const double* st_I;
-    const double* st_d;
+    double l2d;            // lambda^2 / 4
+    const TTab* ttab;      // 2-theta table
     const int* st_foff;
     const int* st_hkl;
     const int* st_mult;

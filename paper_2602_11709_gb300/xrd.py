@@ -20,8 +20,8 @@ XRD_FP64, XRD_FP32_PHASE64, XRD_FP32_PHASEFIX = 0, 1, 2
 PRECISIONS = {"fp64": XRD_FP64, "fp32_phase64": XRD_FP32_PHASE64, "fp32_phasefix": XRD_FP32_PHASEFIX}
 STAGES = ["prep", "atoms", "count", "scan", "emit", "structure_factor", "post", "compact"]
 # kernels xrd_pattern_batch launches per call: prep, coef, atoms, count, scan, emit, structure factor,
-# post (three size classes), output scan, compact
-LAUNCHES_PER_BATCH = 12
+# post (three size classes), output scan, peak and family compaction
+LAUNCHES_PER_BATCH = 13
 
 
 class xrd_batch(C.Structure):
