@@ -29,8 +29,19 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "structure-factor terms/s and patterns/s at 1 GB300 (FP32 vs FP64) vs SFU roofline"
-WORKLOAD = ("small: 1024 seeded P1 cells, a,b,c U[3,15] A, angles U[60,120] deg, 1-64 atoms, Z U{1..83}, "
-            "B U[0,2] A^2, occ 1, lambda 1.54184 A, 2theta 0-90 deg")
+WORKLOADS = {
+    "small": ("small: 1024 seeded P1 cells, a,b,c U[3,15] A, angles U[60,120] deg, 1-64 atoms, Z U{1..83}, "
+              "B U[0,2] A^2, occ 1, lambda 1.54184 A, 2theta 0-90 deg"),
+    "mixed": ("mixed: 100000 seeded cells, atoms lognormal (median 20, <= 500), edges lognormal (median 7 A, "
+              "3-30 A), angles U[60,120] deg, Z U{1..83}, B U[0,2] A^2, lambda 1.54184 A, 2theta 0-90 deg"),
+    "large": ("large: 256 seeded P1 cells, a,b,c U[15,40] A, 200-2000 atoms, 20% sites occ U[0.5,1], "
+              "B U[0,3] A^2, lambda 1.54184 A, 2theta 5-120 deg"),
+}
+
+
+def load_workload(name):
+    from paper_2602_11709_gb300 import synth
+    return {"small": synth.small, "mixed": synth.mixed, "large": synth.large}[name]()
 # SFU issue rates per SM per clock measured on this GB300 (MUFU.SIN/COS 16, MUFU.EX2 32) and the
 # maximum SM clock; the structure-factor roofline of a batch follows from its mix of operations.
 MUFU_SINCOS_PER_CLK = 16.0
@@ -131,8 +142,7 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    from paper_2602_11709_gb300 import synth
-    b, o = synth.small()
+    b, o = load_workload(args.workload)
     steps = []
     per_step_budget = max(2.0, min(20.0, 100.0 / max(args.steps + args.warmup, 1)))
     for i in range(args.warmup + args.steps):
@@ -144,7 +154,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": tps, "unit": "terms/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * b.n_struct / pps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_struct": b.n_struct, "precision": "oracle fp64"},
+            "config": {"workload": WORKLOADS[args.workload], "n_struct": b.n_struct, "precision": "oracle fp64"},
             "patterns_per_s": pps,
             "cpu_baseline": {"value": tps, "unit": "terms/s", "cores": steps[0]["cores"], "kind": "oracle",
                              "sample": "consecutive 64-structure chunks of the batch, %.0f s per step" % per_step_budget},
@@ -162,7 +172,7 @@ def run_ours(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     dev = local if torch.cuda.is_available() else 0
     torch.cuda.set_device(dev)
-    b, o = synth.small()
+    b, o = load_workload(args.workload)
     h = xrd.Handle(dev)
     db = xrd.DeviceBatch.from_host(b, "cuda:%d" % dev)
     co = xrd.make_opts(o, args.precision)
@@ -302,7 +312,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 (i32 phase)" if args.precision == "fp32_phasefix"
             else args.precision, "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_struct": b.n_struct, "precision": args.precision,
+            "config": {"workload": WORKLOADS[args.workload], "n_struct": b.n_struct, "precision": args.precision,
                        "terms_full_sphere": terms_full, "terms_evaluated": terms_eval,
                        "reflections_friedel_unique": int(sz.n_refl), "l2": "flushed between steps (256 MiB write)",
                        "parallelism": "replica per GPU" if world > 1 else "1 GPU",
@@ -340,6 +350,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-graph", action="store_true", help="launch the step eagerly instead of as a CUDA graph")
     ap.add_argument("--no-tune", action="store_true", help="skip the launch-shape autotuner")
+    ap.add_argument("--workload", default="small", choices=sorted(WORKLOADS),
+                    help="small (default, the benchmark configuration), mixed or large")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -476,7 +476,8 @@ int xrd_pattern_batch(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, cons
     pa.r2max = ga.r2max;
     pa.l2d = o->lambda * o->lambda * 0.25;
     pa.ttab = h->ttab;
-    pa.tolf = (float)o->tt_tol;
+    // gaps never exceed 180 degrees: a larger tolerance merges everything
+    pa.ttol = o->tt_tol > 180.0 ? INFINITY : (float)tan(o->tt_tol * (xrd::kPi / 720.0));
     pa.lo3 = (float)(ga.r2min * std::sqrt(ga.r2min));
     pa.hi3 = (float)(ga.r2max * std::sqrt(ga.r2max));
     pa.l2f = (float)pa.l2d;

@@ -36,7 +36,7 @@ __global__ void k_prep(const double* __restrict__ lattice, int n, double rmax, G
     Geo g;
     g.status = XRD_OK;
     g.H = g.K = g.L = -1;
-    for (int i = 0; i < 6; i++) { g.gs[i] = 0.0; g.gf[i] = 0.f; }
+    for (int i = 0; i < 6; i++) { g.gs[i] = 0.0; g.gf[i] = 0.f; g.gl[i] = 0.f; }
     for (int i = 0; i < 3; i++) g.g2[i] = 0.0;
     const bool finite = isfinite(a) && isfinite(b) && isfinite(c) && isfinite(al) && isfinite(be) && isfinite(ga);
     if (!finite || !(a > 0.0 && b > 0.0 && c > 0.0)) {
@@ -73,7 +73,10 @@ __global__ void k_prep(const double* __restrict__ lattice, int n, double rmax, G
     g.gs[4] = __ddiv_rn(C13, det);
     g.gs[5] = __ddiv_rn(C23, det);
     for (int i = 0; i < 3; i++) g.g2[i] = 2.0 * g.gs[3 + i];  // exact
-    for (int i = 0; i < 6; i++) g.gf[i] = (float)g.gs[i];
+    for (int i = 0; i < 6; i++) {
+        g.gf[i] = __double2float_rn(g.gs[i]);
+        g.gl[i] = __double2float_rn(g.gs[i] - (double)g.gf[i]);
+    }
     g.H = (int)floor(__dmul_rn(rmax, a)) + 1;
     g.K = (int)floor(__dmul_rn(rmax, b)) + 1;
     g.L = (int)floor(__dmul_rn(rmax, c)) + 1;
@@ -204,26 +207,30 @@ __device__ __forceinline__ void column_range(const float* gf, int L, int h, int 
     if (h == 0 && k == 0 && lo < 1) lo = 1;  // half-space: (0, 0, l > 0)
 }
 
-// Canonical |g|^2 along one column (h, k): the products and sums of the fixed
-// order ((G11 hh + G22 kk) + G33 ll) + 2((G12 hk + G13 hl) + G23 kl), with the
-// column's constant parts formed once; the doubled off-diagonal coefficients
-// give exactly the doubled sum. Bit-identical to q_exact.
+// |g|^2 of the emitted reflections along one column (h, k), in two-float
+// arithmetic (about 1e-14 relative): the value that sorting, merging and the
+// outputs use. The inside/outside decision on the sphere boundary does not use
+// it; that one is made on the fixed-order FP64 value (q_exact).
 struct ColumnQ {
-    double t1, t2, g33, g13, g23;
-    int h, k;
-    __device__ ColumnQ(const Geo& g, int h_, int k_) : h(h_), k(k_)
+    F2 t, g33, g13, g23;
+    float fh, fk;
+    __device__ ColumnQ(const Geo& g, int h, int k)
     {
-        t1 = __dadd_rn(__dmul_rn(g.gs[0], i2d_exact(h * h)), __dmul_rn(g.gs[1], i2d_exact(k * k)));
-        t2 = __dmul_rn(g.g2[0], i2d_exact(h * k));
-        g33 = g.gs[2];
-        g13 = g.g2[1];
-        g23 = g.g2[2];
+        fh = (float)h;
+        fk = (float)k;
+        const F2 G11{g.gf[0], g.gl[0]}, G22{g.gf[1], g.gl[1]}, G12{2.f * g.gf[3], 2.f * g.gl[3]};
+        t = f2_add(f2_add(f2_mul_int(G11, (float)(h * h)), f2_mul_int(G22, (float)(k * k))),
+                   f2_mul_int(G12, (float)(h * k)));
+        g33 = F2{g.gf[2], g.gl[2]};
+        g13 = F2{2.f * g.gf[4], 2.f * g.gl[4]};
+        g23 = F2{2.f * g.gf[5], 2.f * g.gl[5]};
     }
     __device__ __forceinline__ double at(int l) const
     {
-        const double diag = __dadd_rn(t1, __dmul_rn(g33, i2d_exact(l * l)));
-        const double off = __dadd_rn(__dadd_rn(t2, __dmul_rn(g13, i2d_exact(h * l))), __dmul_rn(g23, i2d_exact(k * l)));
-        return __dadd_rn(diag, off);
+        const float fl = (float)l;
+        const F2 v = f2_add(f2_add(t, f2_mul_int(g33, fl * fl)),
+                            f2_add(f2_mul_int(g13, fh * fl), f2_mul_int(g23, fk * fl)));
+        return f2d_fast(v.hi) + f2d_fast(v.lo);
     }
 };
 

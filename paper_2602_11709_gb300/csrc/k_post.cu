@@ -9,8 +9,9 @@
 // One CTA per structure. Reflections of structures up to `cap_smem` live in
 // shared memory; larger ones use the same code on global scratch (generic
 // pointers). The sort is a bucket sort in |g|^3 (reflections are uniform in
-// the volume of the sphere, so buckets are nearly equally full) followed by an
-// insertion sort of each bucket on the full key (|g|^2, then -h, -k, -l).
+// the volume of the sphere, so buckets are nearly equally full); each
+// reflection then takes its rank among the members of its own bucket on the
+// full key (|g|^2, then -h, -k, -l), one thread per reflection.
 // The anchor rule is sequential, so it is split: a reflection whose gap to its
 // predecessor is >= tol always opens a peak (a definite start); the short runs
 // between definite starts are resolved one thread per run.
@@ -59,18 +60,21 @@ const TTab* init_tables(cudaStream_t st)
     return (const TTab*)p;
 }
 
-// 2theta(qb) - 2theta(qa) in degrees for qb >= qa > 0, to about 1e-6 relative:
-// asin xb - asin xa = 2 atan((xb - xa) / (cb + ca)), x = lambda sqrt(q) / 2,
-// c = sqrt(1 - x^2), xb - xa = (lambda / 2)(qb - qa) / (sqrt qb + sqrt qa), and
-// qb - qa is exact in FP64 for close values.
-__device__ __forceinline__ float tt_gap(double qa, double qb, float l2, float lh)
+// Merge test: 2theta(qb) - 2theta(qa) < tol for qb >= qa > 0, decided to about
+// 1e-6 relative. With x = lambda sqrt(q) / 2 = sin theta and c = cos theta,
+// tan((2theta_b - 2theta_a) / 4) = (xb - xa) / (ca + cb) and
+// xb - xa = (lambda / 2)(qb - qa) / (sqrt qa + sqrt qb); qb - qa is exact in FP64
+// for close values. Comparing against ttol = tan(tol / 4) (tol in radians)
+// leaves neither a division nor an arctangent.
+__device__ __forceinline__ bool tt_close(double qa, double qb, float l2, float lh, float ttol)
 {
-    if (dbits(qb) <= dbits(qa)) return 0.f;
+    if (dbits(qb) <= dbits(qa)) return ttol > 0.f;  // equal |g|^2: a gap of 0
     const float dqf = d2f_pos(qb - qa);
     const float qaf = d2f_pos(qa), qbf = d2f_pos(qb);
-    const float dx = lh * dqf / (sqrtf(qaf) + sqrtf(qbf));
-    const float ca = sqrtf(fmaxf(fmaf(-l2, qaf, 1.f), 0.f)), cb = sqrtf(fmaxf(fmaf(-l2, qbf, 1.f), 0.f));
-    return 4.f * atanf(dx / (ca + cb)) * (float)(180.0 / kPi);
+    const float ua = fmaxf(fmaf(-l2, qaf, 1.f), 1e-30f), ub = fmaxf(fmaf(-l2, qbf, 1.f), 1e-30f);
+    const float sq = qaf * rsqrtf(qaf) + qbf * rsqrtf(qbf);
+    const float c = ua * rsqrtf(ua) + ub * rsqrtf(ub);
+    return lh * dqf < ttol * (sq * c);
 }
 
 // family key: |h|, |k|, |l| sorted descending, packed
@@ -82,6 +86,20 @@ __device__ __forceinline__ uint32_t family_key(uint32_t key)
     if (c > b) { t = b; b = c; c = t; }
     if (b > a) { t = a; a = b; b = t; }
     return ((uint32_t)a << 20) | ((uint32_t)b << 10) | (uint32_t)c;
+}
+
+// number of distinct families among the members i0..i1-1 of one peak
+template <typename PermT>
+__device__ __forceinline__ int count_families(const uint32_t* key, const PermT* perm, int i0, int i1)
+{
+    int nfam = 0;
+    for (int i = i0; i < i1; i++) {
+        const uint32_t fk = family_key(key[perm[i]]);
+        bool lead = true;
+        for (int j = i0; j < i && lead; j++) lead = family_key(key[perm[j]]) != fk;
+        nfam += lead;
+    }
+    return nfam;
 }
 
 // sort order: ascending |g|^2, ties by descending (h, k, l)
@@ -99,8 +117,12 @@ __device__ void post_structure(const PostArgs& a, int s, int64_t base, int n, co
                                double* dtmp)
 {
     const int tid = threadIdx.x, nt = blockDim.x;
-    const float l2 = a.l2f, lh = a.lhf;
-    // ---- bucket sort on |g|^3 in [r2min^1.5, r2max^1.5] ----
+    const float l2 = a.l2f, lh = a.lhf, ttol = a.ttol;
+    // ---- bucket sort on |g|^3 in [r2min^1.5, r2max^1.5] (a monotone map of |g|^2) ----
+    // fcnt holds each reflection's bucket and pst the bucket-ordered reflections
+    // until the merge step needs them.
+    int* const bid = fcnt;
+    int* const perm1 = pst;
     const int nb = n;
     const float lo3 = a.lo3, hi3 = a.hi3;
     const float scale = (float)nb / (hi3 - lo3);
@@ -110,36 +132,32 @@ __device__ void post_structure(const PostArgs& a, int s, int64_t base, int n, co
         const float qf = d2f_pos(q[i]);
         int b = (int)((qf * sqrtf(qf) - lo3) * scale);
         b = min(max(b, 0), nb - 1);
+        bid[i] = b;
         atomicAdd(&bkt[b], 1);
     }
     __syncthreads();
     block_excl_scan(bkt, nb, tmp);
+    for (int i = tid; i < n; i += nt) perm1[atomicAdd(&bkt[bid[i]], 1)] = i;
     __syncthreads();
-    for (int i = tid; i < n; i += nt) {
-        const float qf = d2f_pos(q[i]);
-        int b = (int)((qf * sqrtf(qf) - lo3) * scale);
-        b = min(max(b, 0), nb - 1);
-        perm[atomicAdd(&bkt[b], 1)] = (PermT)i;
-    }
-    __syncthreads();
-    for (int b = tid; b < nb; b += nt) {  // bkt[b] is now the end of bucket b
+    // bkt[b] is now the end of bucket b; rank within the bucket gives the position
+    for (int p = tid; p < n; p += nt) {
+        const int v = perm1[p];
+        const int b = bid[v];
         const int b0 = b ? bkt[b - 1] : 0, b1 = bkt[b];
-        for (int i = b0 + 1; i < b1; i++) {
-            const int v = perm[i];
+        int r = b0;
+        if (b1 - b0 > 1) {
             const double qv = q[v];
             const uint32_t kv = key[v];
-            int j = i - 1;
-            while (j >= b0 && before(qv, kv, q[perm[j]], key[perm[j]])) {
-                perm[j + 1] = perm[j];
-                j--;
+            for (int j = b0; j < b1; j++) {
+                const int u = perm1[j];
+                r += before(q[u], key[u], qv, kv);  // false for u == v
             }
-            perm[j + 1] = (PermT)v;
         }
+        perm[r] = (PermT)v;
     }
     __syncthreads();
     // ---- anchor merge: definite starts, then one thread per run ----
-    for (int i = tid; i < n; i += nt)
-        flag[i] = (i == 0) || !(tt_gap(q[perm[i - 1]], q[perm[i]], l2, lh) < a.tolf);
+    for (int i = tid; i < n; i += nt) flag[i] = (i == 0) || !tt_close(q[perm[i - 1]], q[perm[i]], l2, lh, ttol);
     __syncthreads();
     for (int i = tid; i < n; i += nt) {
         if (!flag[i]) continue;
@@ -147,7 +165,7 @@ __device__ void post_structure(const PostArgs& a, int s, int64_t base, int n, co
         pst[i] = 1;
         for (int j = i + 1; j < n && !flag[j]; j++) {
             const double qj = q[perm[j]];
-            if (!(tt_gap(qa, qj, l2, lh) < a.tolf)) {
+            if (!tt_close(qa, qj, l2, lh, ttol)) {
                 pst[j] = 1;
                 qa = qj;
             } else {
@@ -156,13 +174,10 @@ __device__ void post_structure(const PostArgs& a, int s, int64_t base, int n, co
         }
     }
     __syncthreads();
-    // peak starts -> peak ids; bkt becomes the list of peak start positions
-    for (int i = tid; i < n; i += nt) fcnt[i] = pst[i];
-    __syncthreads();
+    // peak starts -> peak ids (exclusive scan); bkt becomes the list of peak start positions
     const int np = block_excl_scan(pst, n, tmp);
-    __syncthreads();
     for (int i = tid; i < n; i += nt)
-        if (fcnt[i]) bkt[pst[i]] = i;
+        if ((i + 1 < n ? pst[i + 1] : np) != pst[i]) bkt[pst[i]] = i;
     if (tid == 0) bkt[np] = n;
     __syncthreads();
     // ---- per peak: merged intensity (each half-space reflection stands for g and -g) and family count ----
@@ -175,17 +190,10 @@ __device__ void post_structure(const PostArgs& a, int s, int64_t base, int n, co
         unsigned long long lmax = 0;
         for (int p = tid; p < np; p += nt) {
             const int i0 = bkt[p], i1 = bkt[p + 1];
-            float sum = 0.f;
-            int nfam = 0;
-            for (int i = i0; i < i1; i++) {
-                sum = fmaf(2.f, Ig[perm[i]], sum);
-                const uint32_t fk = family_key(key[perm[i]]);
-                bool lead = true;
-                for (int j = i0; j < i && lead; j++) lead = family_key(key[perm[j]]) != fk;
-                nfam += lead;
-            }
+            float sum = 2.f * Ig[perm[i0]];
+            for (int i = i0 + 1; i < i1; i++) sum = fmaf(2.f, Ig[perm[i]], sum);
             ps[p] = sum;
-            fcnt[p] = nfam;
+            fcnt[p] = i1 - i0 == 1 ? 1 : count_families(key, perm, i0, i1);
             lmax = max(lmax, (unsigned long long)__float_as_uint(sum));
         }
         imaxf = __uint_as_float((uint32_t)block_max_u64(lmax, (unsigned long long*)dtmp));
@@ -203,16 +211,9 @@ __device__ void post_structure(const PostArgs& a, int s, int64_t base, int n, co
         for (int p = tid; p < np; p += nt) {
             const int i0 = bkt[p], i1 = bkt[p + 1];
             double sum = 0.0;
-            int nfam = 0;
-            for (int i = i0; i < i1; i++) {
-                sum += 2.0 * Ig[perm[i]];
-                const uint32_t fk = family_key(key[perm[i]]);
-                bool lead = true;
-                for (int j = i0; j < i && lead; j++) lead = family_key(key[perm[j]]) != fk;
-                nfam += lead;
-            }
+            for (int i = i0; i < i1; i++) sum += 2.0 * Ig[perm[i]];
             psum[p] = sum;
-            fcnt[p] = nfam;
+            fcnt[p] = i1 - i0 == 1 ? 1 : count_families(key, perm, i0, i1);
             lmax = max(lmax, dbits(sum));
         }
         imax = __longlong_as_double((long long)block_max_u64(lmax, (unsigned long long*)dtmp));
@@ -229,9 +230,8 @@ __device__ void post_structure(const PostArgs& a, int s, int64_t base, int n, co
         }
     }
     __syncthreads();
-    const int nk = block_excl_scan(pst, np, tmp);
-    const int nf = block_excl_scan(fcnt, np, tmp);
-    __syncthreads();
+    int nk, nf;
+    block_excl_scan2(pst, fcnt, np, tmp, nk, nf);
     for (int p = tid; p < np; p += nt) {
         if (!flag[p]) continue;
         const int i0 = bkt[p], i1 = bkt[p + 1];
@@ -245,6 +245,15 @@ __device__ void post_structure(const PostArgs& a, int s, int64_t base, int n, co
             a.st_I[o] = (a.scaled && imax > 0.0) ? (ps == imax ? 100.0 : 100.0 * (ps * inv_imax)) : ps;
         }
         a.st_foff[o] = fcnt[p];
+        if (i1 - i0 == 1) {  // one reflection: one family of multiplicity 2 (g and -g)
+            const uint32_t rep = key[perm[i0]];
+            const int64_t fo = base + fcnt[p];
+            a.st_hkl[3 * fo] = hkl_h(rep);
+            a.st_hkl[3 * fo + 1] = hkl_k(rep);
+            a.st_hkl[3 * fo + 2] = hkl_l(rep);
+            a.st_mult[fo] = 2;
+            continue;
+        }
         // families: leaders are first members of each family; rank by descending representative
         for (int i = i0; i < i1; i++) {
             const uint32_t fk = family_key(key[perm[i]]);
@@ -287,7 +296,7 @@ template <int CAP, int NT, bool FI>
 __global__ void __launch_bounds__(NT) k_post(const PostArgs a, int cls)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int tmp[34];
+    __shared__ int tmp[66];
     __shared__ double dtmp[32];
     if (*a.abort_flag) return;
     const int cnt = a.cls_cnt[cls];

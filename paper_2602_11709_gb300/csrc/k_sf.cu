@@ -178,8 +178,12 @@ __device__ void sf_tile_fp64(const SfArgs& a, int64_t r0, int64_t re, int64_t j0
 
 // Persistent CTAs; every warp takes 128-reflection tiles from a queue in
 // largest-first order (tiles of the structures with the most atoms first).
+// Register caps: 64 for the integer-phase variant (32 resident warps per SM),
+// about 85 for the FP64-phase and gradient variants (24 warps).
 template <int PREC, bool GRAD, int RB, int WARPS>
-__global__ void __launch_bounds__(32 * WARPS) k_sf(const SfArgs a)
+__global__ void __launch_bounds__(32 * WARPS, PREC == XRD_FP64 ? 1 : ((PREC == XRD_FP32_PHASEFIX && !GRAD) ? 32 / WARPS
+                                                                                                          : 24 / WARPS))
+    k_sf(const SfArgs a)
 {
     constexpr int kSfThreads = 32 * WARPS;
     __shared__ Atom32 sat[WARPS][kSfChunk];

@@ -20,6 +20,7 @@ struct Geo {
     double gs[6];  // reciprocal metric G* stored as (11, 22, 33, 12, 13, 23)
     double g2[3];  // 2 G*12, 2 G*13, 2 G*23 (exact doubles of the off-diagonal terms)
     float gf[6];   // G* rounded to FP32, for the enumeration filter
+    float gl[6];   // G* - gf (the low words of a two-float G*; off-diagonals doubled in hi and lo below)
     int H, K, L;   // enumeration box |h| <= H ...
     int status;    // XRD_OK or XRD_EINVAL
 };
@@ -84,6 +85,30 @@ __device__ __forceinline__ uint32_t fix32(double v)
 {
     const double t = __dadd_rn(v, 1572864.0);
     return (uint32_t)(unsigned long long)__double_as_longlong(t);
+}
+
+// ---- two-float ("double-float") arithmetic: value = hi + lo, |lo| <= ulp(hi) / 2 ----
+struct F2 {
+    float hi, lo;
+};
+__device__ __forceinline__ F2 f2_quick(float a, float b)  // |a| >= |b|
+{
+    const float s = a + b;
+    return F2{s, b - (s - a)};
+}
+__device__ __forceinline__ F2 f2_add(F2 a, F2 b)
+{
+    const float s = a.hi + b.hi;
+    const float bb = s - a.hi;
+    const float e = (a.hi - (s - bb)) + (b.hi - bb) + (a.lo + b.lo);
+    return f2_quick(s, e);
+}
+// a * n for an integer n exactly representable in FP32
+__device__ __forceinline__ F2 f2_mul_int(F2 a, float n)
+{
+    const float p = a.hi * n;
+    const float e = fmaf(a.hi, n, -p) + a.lo * n;
+    return f2_quick(p, e);
 }
 
 // Exact int -> double by bit assembly (|v| < 2^31); keeps the conversion off
@@ -195,28 +220,79 @@ __device__ __forceinline__ int warp_incl_scan(int v)
 
 // Exclusive prefix sum of a[0..n) in place by the whole block; returns the
 // total. `tmp` is shared scratch of at least 33 ints. All threads must call.
+// In-place exclusive scan of a[0..n) in shared memory by the whole block; each
+// thread takes one contiguous segment, so the block synchronises three times
+// whatever n is. Returns the total. tmp: 33 ints of shared memory.
 __device__ __forceinline__ int block_excl_scan(int* a, int n, int* tmp)
 {
-    const int nw = (blockDim.x + 31) >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int carry = 0;
-    for (int base = 0; base < n; base += blockDim.x) {
-        const int i = base + (int)threadIdx.x;
-        const int v = i < n ? a[i] : 0;
-        const int inc = warp_incl_scan(v);
-        if (lane == 31) tmp[w] = inc;
-        __syncthreads();
-        if (w == 0) {
-            const int s = lane < nw ? tmp[lane] : 0;
-            const int si = warp_incl_scan(s);
-            if (lane < nw) tmp[lane] = si - s;
-            if (lane == 31) tmp[32] = si;
-        }
-        __syncthreads();
-        if (i < n) a[i] = carry + tmp[w] + inc - v;
-        carry += tmp[32];
-        __syncthreads();
+    const int nt = blockDim.x, nw = (nt + 31) >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int seg = (n + nt - 1) / nt;
+    const int i0 = min((int)threadIdx.x * seg, n), i1 = min(i0 + seg, n);
+    int s = 0;
+    for (int i = i0; i < i1; i++) s += a[i];
+    const int inc = warp_incl_scan(s);
+    if (lane == 31) tmp[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        const int v = lane < nw ? tmp[lane] : 0;
+        const int si = warp_incl_scan(v);
+        if (lane < nw) tmp[lane] = si - v;
+        if (lane == 31) tmp[32] = si;
     }
-    return carry;
+    __syncthreads();
+    int run = tmp[w] + inc - s;
+    const int total = tmp[32];
+    for (int i = i0; i < i1; i++) {
+        const int v = a[i];
+        a[i] = run;
+        run += v;
+    }
+    __syncthreads();
+    return total;
+}
+
+// Two exclusive scans of the same length at once (a and b); totals in ta, tb.
+// tmp: 66 ints of shared memory.
+__device__ __forceinline__ void block_excl_scan2(int* a, int* b, int n, int* tmp, int& ta, int& tb)
+{
+    const int nt = blockDim.x, nw = (nt + 31) >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int seg = (n + nt - 1) / nt;
+    const int i0 = min((int)threadIdx.x * seg, n), i1 = min(i0 + seg, n);
+    int sa = 0, sb = 0;
+    for (int i = i0; i < i1; i++) {
+        sa += a[i];
+        sb += b[i];
+    }
+    const int ia = warp_incl_scan(sa), ib = warp_incl_scan(sb);
+    if (lane == 31) {
+        tmp[w] = ia;
+        tmp[33 + w] = ib;
+    }
+    __syncthreads();
+    if (w == 0) {
+        const int va = lane < nw ? tmp[lane] : 0, vb = lane < nw ? tmp[33 + lane] : 0;
+        const int xa = warp_incl_scan(va), xb = warp_incl_scan(vb);
+        if (lane < nw) {
+            tmp[lane] = xa - va;
+            tmp[33 + lane] = xb - vb;
+        }
+        if (lane == 31) {
+            tmp[32] = xa;
+            tmp[65] = xb;
+        }
+    }
+    __syncthreads();
+    int ra = tmp[w] + ia - sa, rb = tmp[33 + w] + ib - sb;
+    ta = tmp[32];
+    tb = tmp[65];
+    for (int i = i0; i < i1; i++) {
+        const int va = a[i], vb = b[i];
+        a[i] = ra;
+        b[i] = rb;
+        ra += va;
+        rb += vb;
+    }
+    __syncthreads();
 }
 
 __device__ __forceinline__ double block_max_double(double v, double* tmp)

@@ -66,7 +66,7 @@ struct PostArgs {
     double lambda, tol, cutoff, r2min, r2max;
     double l2d;                          // lambda^2 / 4
     const TTab* ttab;                    // 2-theta table (device)
-    float tolf, lo3, hi3, l2f, lhf;      // FP32 copies: tol, r2min^1.5, r2max^1.5, lambda^2/4, lambda/2
+    float ttol, lo3, hi3, l2f, lhf;      // FP32: tan(tol / 4) (tol in radians), r2min^1.5, r2max^1.5, lambda^2/4, lambda/2
     const int64_t* refl_off;
     const int* abort_flag;
     const double* q;

@@ -221,3 +221,26 @@ def test_large_full_size_sampled(gpu_lib, handle, prec):
             worst = max(worst, abs(I[p] - Iref) / imax)
             assert abs(I[p] - Iref) <= (1e-5 if prec != "fp64" else 1e-9) * imax, (s, p, I[p], Iref)
     _report("large_full_sampled_" + prec, {"max_abs_rel_to_max": worst})
+
+
+def test_mixed_full_size_sampled(gpu_lib, handle):
+    """All 100 000 mixed cells in one launch sequence; sampled structures against the
+    oracle, every structure against invariants."""
+    b, o = synth.mixed()
+    got = gpu_lib.compute(b, o, "fp32_phasefix", handle=handle)
+    assert np.all(got["status"] == 0)
+    assert got["totals"][3] == 0
+    for s in range(b.n_struct):
+        tt, I = got["peak_tt"][s], got["peak_I"][s]
+        if len(tt):
+            assert np.all(np.diff(tt) > 0) and I.max() == 100.0
+    rng = np.random.default_rng(17)
+    idx = rng.choice(b.n_struct, size=40, replace=False)
+    # the largest structures too (longest per-structure paths)
+    idx = np.concatenate([idx, np.argsort(np.diff(b.atom_off))[-5:]])
+    sub = b.subset(idx)
+    ref = oracle.pattern_batch(sub, o, threads=0)
+    picked = {k: [v[s] for s in idx] for k, v in got.items() if isinstance(v, list)}
+    picked["status"] = got["status"][idx]
+    st = compare_batch(picked, ref, "fp32_phasefix", o.rel_cutoff, o.scaled)
+    _report("mixed_full_sampled_fp32_phasefix", st)
