@@ -111,7 +111,13 @@ typedef struct {
     int64_t* totals;    /* [4]: reflections (Friedel-unique), peaks, families, structures with an error */
 } xrd_pattern;
 
-/* Create a handle bound to CUDA device `device`. Returns XRD_OK or XRD_ECUDA/XRD_EINVAL. */
+/*
+ * Create a handle bound to CUDA device `device`. Returns XRD_OK or
+ * XRD_ECUDA/XRD_EINVAL. The handle owns three non-blocking side streams: the
+ * post-processing size classes of xrd_pattern_batch run on them concurrently,
+ * forked from and joined back into the caller's stream by events (so a
+ * capture of the call on the caller's stream takes them in as branches).
+ */
 int xrd_create(xrd_handle** h, int device);
 /* Destroy a handle (NULL is ignored). */
 void xrd_destroy(xrd_handle* h);

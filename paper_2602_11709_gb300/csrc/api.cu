@@ -19,6 +19,9 @@ struct xrd_handle {
     size_t qbuf_bytes = 0;
     const xrd::TTab* ttab = nullptr;  // 2-theta table on the handle's device
     int sf_rb = 4, sf_warps = 2;        // structure-factor launch shape (xrd_autotune)
+    // side streams for the concurrent post-processing size classes (fork/join by events)
+    cudaStream_t side[xrd::kPostClasses - 1] = {};
+    cudaEvent_t fork = nullptr, join[xrd::kPostClasses - 1] = {};
 };
 
 namespace {
@@ -286,14 +289,21 @@ int xrd_create(xrd_handle** h, int device)
     p->device = device;
     DeviceGuard g(device);
     e = cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, device);
-    if (e != cudaSuccess) { delete p; return XRD_ECUDA; }
+    if (e != cudaSuccess) { xrd_destroy(p); return XRD_ECUDA; }
     for (int i = 0; i < kStages + 1; i++) {
         e = cudaEventCreate(&p->ev[i]);
-        if (e != cudaSuccess) { delete p; return XRD_ECUDA; }
+        if (e != cudaSuccess) { xrd_destroy(p); return XRD_ECUDA; }
     }
+    for (int i = 0; i < xrd::kPostClasses - 1; i++) {
+        e = cudaStreamCreateWithFlags(&p->side[i], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->join[i], cudaEventDisableTiming);
+        if (e != cudaSuccess) { xrd_destroy(p); return XRD_ECUDA; }
+    }
+    e = cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming);
+    if (e != cudaSuccess) { xrd_destroy(p); return XRD_ECUDA; }
     p->ttab = xrd::init_tables(0);  // device tables (2-theta), once per handle, on the legacy stream
     e = cudaStreamSynchronize(0);
-    if (e != cudaSuccess || !p->ttab) { delete p; return XRD_ECUDA; }
+    if (e != cudaSuccess || !p->ttab) { xrd_destroy(p); return XRD_ECUDA; }
     *h = p;
     return XRD_OK;
 }
@@ -304,6 +314,11 @@ void xrd_destroy(xrd_handle* h)
     DeviceGuard g(h->device);
     for (int i = 0; i < kStages + 1; i++)
         if (h->ev[i]) cudaEventDestroy(h->ev[i]);
+    for (int i = 0; i < xrd::kPostClasses - 1; i++) {
+        if (h->side[i]) cudaStreamDestroy(h->side[i]);
+        if (h->join[i]) cudaEventDestroy(h->join[i]);
+    }
+    if (h->fork) cudaEventDestroy(h->fork);
     if (h->qbuf) cudaFree(h->qbuf);
     delete h;
 }
@@ -490,6 +505,7 @@ int xrd_pattern_batch(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, cons
     pa.If = sa.If;
     pa.cls_list = ga.cls_list;
     pa.cls_cnt = ga.abort_flag + 4;
+    pa.cls_next = ga.abort_flag + 8;
     pa.grid = h->sms;
     pa.g_perm = (int*)(ws + L.g_perm);
     pa.g_bkt = (int*)(ws + L.g_bkt);
@@ -504,7 +520,19 @@ int xrd_pattern_batch(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, cons
     pa.st_mult = (int*)(ws + L.st_mult);
     pa.npk = (int64_t*)(ws + L.npk);
     pa.nfm = (int64_t*)(ws + L.nfm);
-    xrd::launch_post(pa, st);
+    {  // the size classes run concurrently: fork to the side streams, join back
+        cudaStream_t cs[xrd::kPostClasses] = {st};
+        cudaEventRecord(h->fork, st);
+        for (int i = 1; i < xrd::kPostClasses; i++) {
+            cs[i] = h->side[i - 1];
+            cudaStreamWaitEvent(cs[i], h->fork, 0);
+        }
+        xrd::launch_post(pa, cs);
+        for (int i = 1; i < xrd::kPostClasses; i++) {
+            cudaEventRecord(h->join[i - 1], cs[i]);
+            cudaStreamWaitEvent(st, h->join[i - 1], 0);
+        }
+    }
     mark();
 
     xrd::CompactArgs ca{};
@@ -519,7 +547,8 @@ int xrd_pattern_batch(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, cons
     ca.fam_soff = (int64_t*)(ws + L.fam_soff);
     ca.st_q = pa.st_q;
     ca.st_I = pa.st_I;
-    ca.l2d = pa.l2d;
+    ca.l2h = (float)pa.l2d;
+    ca.l2l = (float)(pa.l2d - (double)ca.l2h);
     ca.ttab = h->ttab;
     ca.st_foff = pa.st_foff;
     ca.st_hkl = pa.st_hkl;
@@ -666,6 +695,8 @@ static xrd::GradArgs grad_args(xrd_handle* h, const xrd_batch* b, const xrd_grid
     a.dt = g->dt;
     a.sigma = sigma;
     a.l2d = o->lambda * o->lambda * 0.25;
+    a.l2h = (float)a.l2d;
+    a.l2l = (float)(a.l2d - (double)a.l2h);
     a.ttab = h->ttab;
     a.geo = (const xrd::Geo*)(ws + L.geo);
     a.lattice = b->lattice;

@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(128) k_atoms(const int64_t* __restrict__ atom_
             r.lo = o == 1.0 ? 0.f : (o > 0.0 ? (float)log2(o) : -INFINITY);
             r.z = z;
             r.src = (int)i;
-            r.pad = 0;
+            r.zf = (float)z;
             a32[a0 + pos] = r;
             Atom64 d;
             d.x = x; d.y = y; d.z = w; d.B = bb; d.occ = o; d.zz = z; d.pad = 0;
@@ -441,7 +441,7 @@ __global__ void __launch_bounds__(1024) k_scan_refl(const int64_t* __restrict__ 
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
             const int s = order[i];
             const long long c = cnt[s];
-            const int k = c <= kPostCapSmall ? 0 : (c <= kPostCapLarge ? 1 : 2);
+            const int k = c <= kPostCapSmall ? 0 : (c <= kPostCapMid ? 1 : (c <= kPostCapLarge ? 2 : 3));
             cls_list[(int64_t)k * n + atomicAdd(&ccnt[k], 1)] = s;
         }
     __syncthreads();

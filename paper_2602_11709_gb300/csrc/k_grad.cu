@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(kGradThreads) k_broaden(const GradArgs a)
     const float cg = (float)(kLog2e / (2.0 * a.sigma * a.sigma));
     // cell and fractional offset of every reflection's 2theta on the grid
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const double T = two_theta_of(fmin(a.q[base + i] * a.l2d, 1.0), a.ttab);
+        const double T = two_theta_q(a.q[base + i], a.l2h, a.l2l, a.ttab);
         const double pos = (T - a.t0) / a.dt;
         const double fb = floor(pos);
         int b;

@@ -24,6 +24,7 @@ constexpr int kPostThreads = 256;
 // Size classes (reflections per structure held in shared memory); the scan
 // kernel sorts structures into them with the same bounds.
 constexpr int kCapSmall = kPostCapSmall;  // 256 threads, four CTAs per SM
+constexpr int kCapMid = kPostCapMid;      // 512 threads, two CTAs per SM
 constexpr int kCapLarge = kPostCapLarge;  // 1024 threads, one CTA per SM; larger: global scratch
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
@@ -42,11 +43,12 @@ __global__ void k_ttab_init()
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j > kTabN) return;
-    const double th = (j * kTabStepDeg) * (kPi / 360.0);
+    const double th = (j * (double)kTabStepDeg) * (kPi / 360.0);
     const double sn = sin(th);
+    const double S = sn * sn;
     TTab t;
-    t.S = sn * sn;
-    t.T = j * kTabStepDeg;
+    t.Sh = (float)S;
+    t.Sl = (float)(S - (double)t.Sh);
     t.A = (float)sin(2.0 * th);
     t.Bc = (float)cos(2.0 * th);
     g_ttab[j] = t;
@@ -111,10 +113,11 @@ __device__ __forceinline__ bool before(double qa, uint32_t ka, double qb, uint32
 
 // FI: intensities are FP32 (the FP32 structure-factor variants) and peak sums,
 // cutoff and scaling run in FP32; otherwise FP64 throughout.
+// Is: the FP32 intensities of the structure (shared or global memory).
 template <typename PermT, bool FI>
 __device__ void post_structure(const PostArgs& a, int s, int64_t base, int n, const double* q, const uint32_t* key,
-                               PermT* perm, int* bkt, uint8_t* flag, int* pst, double* psum, int* fcnt, int* tmp,
-                               double* dtmp)
+                               const float* Is, PermT* perm, int* bkt, uint8_t* flag, int* pst, double* psum,
+                               int* fcnt, int* tmp, double* dtmp)
 {
     const int tid = threadIdx.x, nt = blockDim.x;
     const float l2 = a.l2f, lh = a.lhf, ttol = a.ttol;
@@ -185,7 +188,7 @@ __device__ void post_structure(const PostArgs& a, int s, int64_t base, int n, co
     double imax = 0.0, inv_imax = 0.0;
     float imaxf = 0.f, inv_imaxf = 0.f;
     if (FI) {
-        const float* __restrict__ Ig = a.If + base;
+        const float* __restrict__ Ig = Is;
         float* ps = (float*)psum;
         unsigned long long lmax = 0;
         for (int p = tid; p < np; p += nt) {
@@ -290,19 +293,26 @@ __device__ void post_structure(const PostArgs& a, int s, int64_t base, int n, co
 }
 
 // Persistent CTAs over one size class of structures (a list built by the scan
-// kernel, largest first). CAP > 0: the structure's reflections live in shared
-// memory (n <= CAP). CAP == 0: global scratch.
+// kernel, largest first), each CTA claiming the next structure from a counter.
+// CAP > 0: the structure's reflections live in shared memory (n <= CAP); the
+// FP32 variants also stage the intensities there, in the second half of the
+// peak-sum area (FP32 peak sums use the first half). CAP == 0: global scratch.
 template <int CAP, int NT, bool FI>
 __global__ void __launch_bounds__(NT) k_post(const PostArgs a, int cls)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int tmp[66];
     __shared__ double dtmp[32];
+    __shared__ int claim;
     if (*a.abort_flag) return;
     const int cnt = a.cls_cnt[cls];
     const int* __restrict__ list = a.cls_list + (int64_t)cls * a.n_struct;
-    for (int li = blockIdx.x; li < cnt; li += gridDim.x) {
-        __syncthreads();  // the previous structure is done with shared memory
+    for (;;) {
+        __syncthreads();  // the previous structure is done with shared memory and claim
+        if (threadIdx.x == 0) claim = atomicAdd(a.cls_next + cls, 1);
+        __syncthreads();
+        const int li = claim;
+        if (li >= cnt) break;
         const int s = list[li];
         const int64_t base = a.refl_off[s];
         const int n = (int)(a.refl_off[s + 1] - base);
@@ -321,15 +331,18 @@ __global__ void __launch_bounds__(NT) k_post(const PostArgs a, int cls)
             int* pst = (int*)p; p += align16(c * 4);
             double* psum = (double*)p; p += align16(c * 8);
             int* fcnt = (int*)p;
+            float* sI = (float*)psum + c;
             for (int i = threadIdx.x; i < n; i += blockDim.x) {
                 sq[i] = a.q[base + i];
                 sk[i] = a.key[base + i];
+                if (FI) sI[i] = a.If[base + i];
             }
             __syncthreads();
-            post_structure<uint16_t, FI>(a, s, base, n, sq, sk, perm, bkt, flag, pst, psum, fcnt, tmp, dtmp);
+            post_structure<uint16_t, FI>(a, s, base, n, sq, sk, sI, perm, bkt, flag, pst, psum, fcnt, tmp, dtmp);
         } else {
-            post_structure<int, FI>(a, s, base, n, a.q + base, a.key + base, a.g_perm + base, a.g_bkt + base + s,
-                                    a.g_flag + base, a.g_pstart + base, a.g_psum + base, a.g_fcnt + base, tmp, dtmp);
+            post_structure<int, FI>(a, s, base, n, a.q + base, a.key + base, FI ? a.If + base : nullptr,
+                                    a.g_perm + base, a.g_bkt + base + s, a.g_flag + base, a.g_pstart + base,
+                                    a.g_psum + base, a.g_fcnt + base, tmp, dtmp);
         }
     }
 }
@@ -413,9 +426,7 @@ __global__ void __launch_bounds__(256) k_compact_peaks(const CompactArgs a)
         const int64_t src = a.refl_off[s] + (P - a.out.peak_off[s]);
         const double qa = a.st_q[src], I = a.st_I[src];
         const int fo = a.st_foff[src];
-        double X = qa * a.l2d;  // sin^2 theta, at most 1 (bit compare: X >= 0)
-        if ((unsigned long long)__double_as_longlong(X) > 0x3FF0000000000000ull) X = 1.0;
-        a.out.two_theta[P] = two_theta_of(X, a.ttab);
+        a.out.two_theta[P] = two_theta_q(qa, a.l2h, a.l2l, a.ttab);
         a.out.d_hkl[P] = inv_sqrt_df(qa);
         a.out.intensity[P] = I;
         a.out.fam_off[P] = a.fam_soff[s] + fo;
@@ -457,16 +468,18 @@ static void launch_post_class(const PostArgs& a, int cls, cudaStream_t st)
     k_post<CAP, NT, FI><<<grid, NT, smem, st>>>(a, cls);
 }
 
+// st[c]: the stream of size class c (the caller forks and joins them)
 template <bool FI>
-static void launch_post_fi(const PostArgs& a, cudaStream_t st)
+static void launch_post_fi(const PostArgs& a, const cudaStream_t* st)
 {
-    launch_post_class<kCapSmall, kPostThreads, FI>(a, 0, st);
-    launch_post_class<kCapLarge, 1024, FI>(a, 1, st);
-    launch_post_class<0, 1024, FI>(a, 2, st);
+    launch_post_class<0, 1024, FI>(a, 3, st[3]);
+    launch_post_class<kCapLarge, 1024, FI>(a, 2, st[2]);
+    launch_post_class<kCapMid, 512, FI>(a, 1, st[1]);
+    launch_post_class<kCapSmall, kPostThreads, FI>(a, 0, st[0]);
 }
 
 // a.grid = number of SMs
-void launch_post(const PostArgs& a, cudaStream_t st)
+void launch_post(const PostArgs& a, const cudaStream_t* st)
 {
     if (a.n_struct <= 0) return;
     if (a.If) launch_post_fi<true>(a, st);

@@ -29,11 +29,11 @@ constexpr float kTwoPiOver2p32 = 1.4629180792671596e-09f;  // 2 pi / 2^32
 // reflections per warp) and WARPS warps per CTA.
 constexpr int kSfChunk = 128;  // atoms staged per warp at a time
 
-__device__ __forceinline__ float f_of(const Coef32& c, int z, float s2)
+__device__ __forceinline__ float f_of(const Coef32& c, float zf, float s2)
 {
     const float e0 = ex2_approx(c.bl[0] * s2), e1 = ex2_approx(c.bl[1] * s2);
     const float e2 = ex2_approx(c.bl[2] * s2), e3 = ex2_approx(c.bl[3] * s2);
-    return fmaf(s2, fmaf(c.a[0], e0, fmaf(c.a[1], e1, fmaf(c.a[2], e2, c.a[3] * e3))), (float)z);
+    return fmaf(s2, fmaf(c.a[0], e0, fmaf(c.a[1], e1, fmaf(c.a[2], e2, c.a[3] * e3))), zf);
 }
 
 __device__ __forceinline__ float lp_of(float qf, float l2)
@@ -89,7 +89,7 @@ __device__ void sf_tile_fp32(const SfArgs& a, int64_t r0, int64_t re, int64_t j0
                 const Coef32 c = scoef[zc];
 #pragma unroll
                 for (int i = 0; i < kSfRB; i++) {
-                    f[i] = f_of(c, zc, s2[i]);
+                    f[i] = f_of(c, at.zf, s2[i]);
                     if (GRAD) fp[i] = fprime_of(c, s2[i]);
                 }
             }

@@ -12,8 +12,10 @@ constexpr double kPi = 3.14159265358979323846;
 constexpr double kFScale = 41.78214;  // Mott-Bethe factor 8 pi^2 a0 of f(s) (Sec. 1, atomic scattering factors)
 constexpr int kZmaxLimit = 255;
 constexpr int kHklLimit = 511;        // |h|, |k|, |l| fit the 10-bit fields of the packed key
-constexpr int kPostCapSmall = 1536;   // post-processing size classes (reflections per structure)
-constexpr int kPostCapLarge = 6144;
+constexpr int kPostCapSmall = 1536;   // post-processing size classes (reflections per structure):
+constexpr int kPostCapMid = 3072;     // 256, 512 and 1024 threads with the reflections in shared memory,
+constexpr int kPostCapLarge = 6144;   // larger structures on global scratch
+constexpr int kPostClasses = 4;
 
 // Per-structure geometry written by k_prep (step S0).
 struct Geo {
@@ -33,7 +35,7 @@ struct __align__(16) Atom32 {
     float lo;          // log2(occ): occ folds into the same exp2
     int32_t z;         // element number
     int32_t src;       // index of the atom within its structure in the caller's order
-    int32_t pad;
+    float zf;          // element number as a float (f(s) = Z + ...)
 };
 
 // Atom record for the FP64 loops and the FP64 phase.
@@ -133,49 +135,62 @@ __device__ __forceinline__ float ex2_approx(float x)
     return y;
 }
 
-// ---- 2-theta of a reflection from sin^2 theta without FP64 transcendentals ----
+// Positive normal double -> two floats, q = qh + ql to about 2^-47 relative,
+// by bit arithmetic only: qh is q truncated to 24 significant bits, ql holds the
+// next 23 bits (built exactly in the mantissa of 2^23 and scaled by a power of
+// two; it becomes 0 when q < 2^-80).
+__device__ __forceinline__ void split_pos(double q, float& qh, float& ql)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(q);
+    qh = d2f_pos(q);
+    const uint32_t rest = (uint32_t)b & 0x1FFFFFFFu;  // significand bits below qh's
+    const int e = (int)((uint32_t)(b >> 52) & 0x7FFu) - 1023;
+    const float m = __int_as_float(0x4B000000 | (rest >> 6)) - 8388608.f;
+    ql = m * __int_as_float(max(e + 81, 0) << 23);  // weight of bit 6 of rest: 2^(e - 46)
+}
+
+// ---- 2-theta of a reflection from |g|^2 without FP64 arithmetic but one addition ----
 // theta in [0, pi/4] is found from a table at theta_j = j * pi / 4096 (2theta_j =
 // j * 360 / 4096 degrees, exact in binary) and FP32 Newton steps on the small
 // remainder u = 2 (theta - theta_j); angles above 45 degrees use the complement
-// (sin^2 theta = 1 - sin^2(90 deg - theta)). Error about 1e-8 degrees.
+// (sin^2 theta = 1 - sin^2(90 deg - theta)). sin^2 theta = q lambda^2 / 4 and the
+// table's sin^2 theta_j are carried as two floats, so the remainder is exact to
+// about 1e-14. Error about 1e-8 degrees.
 constexpr int kTabN = 1024;
-constexpr double kTabStepDeg = 360.0 / 4096.0;  // 2theta spacing of the table
-struct TTab {
-    double S;  // sin^2 theta_j
-    double T;  // 2 theta_j in degrees (= j * 360 / 4096, exact)
-    float A;   // sin 2 theta_j
-    float Bc;  // cos 2 theta_j
+constexpr float kTabStepDeg = 360.f / 4096.f;  // 2theta spacing of the table (exact)
+struct __align__(16) TTab {
+    float Sh, Sl;  // sin^2 theta_j as two floats
+    float A;       // sin 2 theta_j
+    float Bc;      // cos 2 theta_j
 };
 
-// Any finite double -> float by bit arithmetic (truncation; magnitudes below
-// the float range become 0). Keeps the conversion off the FP64 unit.
-__device__ __forceinline__ float d2f_signed(double x)
+// 2theta in degrees for |g|^2 = q (> 0, normal) and lambda^2 / 4 = Lh + Ll;
+// sin^2 theta above 1 is taken as 1 (90 degrees theta).
+__device__ __forceinline__ double two_theta_q(double q, float Lh, float Ll, const TTab* __restrict__ tab)
 {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const unsigned long long m = b & 0x7FFFFFFFFFFFFFFFull;
-    if (m < 0x3810000000000000ull) return 0.f;  // |x| < 2^-126
-    const float f = d2f_pos(__longlong_as_double((long long)m));
-    return (b >> 63) ? -f : f;
-}
-
-// 2theta in degrees of a reflection with sin^2 theta = X (FP64, 0 < X <= 1).
-// Comparisons run on the bit patterns (X >= 0), so the FP64 unit sees only the
-// few subtractions that need its precision.
-__device__ __forceinline__ double two_theta_of(double X, const TTab* __restrict__ tab)
-{
-    const unsigned long long xb = (unsigned long long)__double_as_longlong(X);
-    const bool comp = xb > 0x3FE0000000000000ull;  // X > 0.5
-    const double Y = comp ? 1.0 - X : X;            // exact for X in (0.5, 1]
-    const float Yf = d2f_signed(Y);
-    const float th0 = asinf(sqrtf(Yf));
+    float qh, ql;
+    split_pos(q, qh, ql);
+    // X = q L as two floats
+    float Xh = qh * Lh;
+    float Xl = fmaf(qh, Lh, -Xh) + fmaf(qh, Ll, ql * Lh);
+    if (Xh > 1.f || (Xh == 1.f && Xl > 0.f)) {
+        Xh = 1.f;
+        Xl = 0.f;
+    }
+    const bool comp = Xh > 0.5f || (Xh == 0.5f && Xl > 0.f);
+    const float Yh = comp ? 1.f - Xh : Xh;  // exact for Xh in [0.5, 1]
+    const float Yl = comp ? -Xl : Xl;
+    const float Yf = Yh + Yl;
+    const float th0 = asinf(sqrtf(fmaxf(Yf, 0.f)));
     int j = __float2int_rn(th0 * (float)(4.0 * kTabN / kPi));
     j = min(max(j, 0), kTabN);
-    double t;
+    float T, v;  // 2theta = T + v with T a multiple of the table step (exact in float)
     if (j <= 2) {
-        t = f2d_fast(th0 * (float)(360.0 / kPi));
+        T = 0.f;
+        v = th0 * (float)(360.0 / kPi);
     } else {
         const TTab e = tab[j];
-        const float r = d2f_signed(Y - e.S);
+        const float r = (Yh - e.Sh) + (Yl - e.Sl);
         float u = 4.f * r / (e.A + sqrtf(fmaf(4.f * e.Bc, r, e.A * e.A)));
 #pragma unroll
         for (int it = 0; it < 2; it++) {
@@ -186,23 +201,28 @@ __device__ __forceinline__ double two_theta_of(double X, const TTab* __restrict_
             const float fp = fmaf(e.A, 1.f - 0.5f * u2, e.Bc * su);
             u -= fv / fp;
         }
-        t = e.T + f2d_fast(u * (float)(180.0 / kPi));
+        T = (float)j * kTabStepDeg;
+        v = u * (float)(180.0 / kPi);
     }
-    return comp ? 180.0 - t : t;
+    if (comp) {
+        T = 180.f - T;  // exact: both are multiples of 45 / 512
+        v = -v;
+    }
+    return f2d_fast(T) + f2d_fast(v);
 }
 
 // d = 1/sqrt(q) for q > 0 in float range: an FP32 seed refined by one Newton
 // step whose residual 1 - q y0^2 is formed exactly in FP32 (q split into two
-// floats, y0^2 into two floats); about 1e-13 relative, two FP64 additions.
+// floats, y0^2 into two floats); about 1e-13 relative, one FP64 addition.
 __device__ __forceinline__ double inv_sqrt_df(double q)
 {
-    const float qh = d2f_pos(q);
-    const float ql = d2f_signed(q - f2d_fast(qh));  // exact: qh is q truncated
+    float qh, ql;
+    split_pos(q, qh, ql);
     const float y0 = rsqrtf(qh);
     const float p = y0 * y0, pe = fmaf(y0, y0, -p);
     float r = fmaf(-qh, p, 1.f);
     r = fmaf(-qh, pe, fmaf(-ql, p, r));
-    return f2d_fast(y0) + f2d_fast(0.5f * y0 * r);
+    return f2d_fast(y0) + f2d_fast(0.5f * y0 * r * fmaf(0.75f, r, 1.f));
 }
 
 // ---- block-wide primitives over generic pointers (shared or global memory) ----

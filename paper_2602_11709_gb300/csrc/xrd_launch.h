@@ -75,6 +75,7 @@ struct PostArgs {
     const float* If;    // FP32 intensities (the FP32 variants)
     const int* cls_list;  // [4][n_struct] structures of each size class, largest first
     const int* cls_cnt;   // [4]
+    int* cls_next;        // [4] work counters (zero at launch)
     // global scratch for structures larger than cap_smem (indexed by reflection)
     int* g_perm;
     int* g_bkt;   // n_refl + n_struct entries
@@ -102,7 +103,7 @@ struct CompactArgs {
     int64_t* fam_soff;  // [n_struct + 1] scratch: exclusive scan of nfm
     const double* st_q;
     const double* st_I;
-    double l2d;            // lambda^2 / 4
+    float l2h, l2l;        // lambda^2 / 4 as two floats
     const TTab* ttab;      // 2-theta table
     const int* st_foff;
     const int* st_hkl;
@@ -115,6 +116,7 @@ struct GradArgs {
     int n_struct, n_pts, W;
     int64_t n_atoms;
     double t0, dt, sigma, l2d;
+    float l2h, l2l;  // lambda^2 / 4 as two floats
     const TTab* ttab;
     const Geo* geo;
     const double* lattice;
@@ -147,7 +149,7 @@ void launch_scan_refl(const GeomArgs& a, cudaStream_t st);
 void launch_emit(const GeomArgs& a, cudaStream_t st);
 void launch_sf(const SfArgs& a, cudaStream_t st);
 size_t post_smem_bytes(int cap);
-void launch_post(const PostArgs& a, cudaStream_t st);
+void launch_post(const PostArgs& a, const cudaStream_t* st);  // st[kPostClasses]
 void launch_compact(const CompactArgs& a, cudaStream_t st);
 const TTab* init_tables(cudaStream_t st);
 size_t broaden_smem_bytes(int n_pts, int W);

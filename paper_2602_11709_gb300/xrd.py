@@ -222,6 +222,55 @@ class PatternBuffers:
         return res
 
 
+class HostPattern:
+    """Pinned host mirror of a PatternBuffers, reused across calls.
+
+    download() reads the totals first (they size the copies), then copies exactly
+    the used prefix of every dense CSR output into page-locked memory with
+    asynchronous copies on one stream, and returns numpy views of it.
+    """
+
+    def __init__(self, n_struct, cap):
+        torch = _torch()
+        cap = max(int(cap), 1)
+        pin = dict(pin_memory=True)
+        self.n_struct = n_struct
+        self.peak_off = torch.zeros(n_struct + 1, dtype=torch.int64, **pin)
+        self.two_theta = torch.zeros(cap, dtype=torch.float64, **pin)
+        self.intensity = torch.zeros(cap, dtype=torch.float64, **pin)
+        self.d_hkl = torch.zeros(cap, dtype=torch.float64, **pin)
+        self.fam_off = torch.zeros(cap + 1, dtype=torch.int64, **pin)
+        self.hkl = torch.zeros(cap, 3, dtype=torch.int32, **pin)
+        self.mult = torch.zeros(cap, dtype=torch.int32, **pin)
+        self.status = torch.zeros(max(n_struct, 1), dtype=torch.int32, **pin)
+        self.totals = torch.zeros(4, dtype=torch.int64, **pin)
+        self.bytes_last = 0
+
+    def download(self, out: "PatternBuffers", stream=None) -> dict:
+        torch = _torch()
+        st = stream or torch.cuda.current_stream()
+        with torch.cuda.stream(st):
+            self.totals.copy_(out.totals, non_blocking=True)
+            st.synchronize()
+            npk, nfm = int(self.totals[1]), int(self.totals[2])
+            n = self.n_struct
+            pairs = [(self.peak_off, out.peak_off, n + 1), (self.status, out.status, n),
+                     (self.two_theta, out.two_theta, npk), (self.intensity, out.intensity, npk),
+                     (self.d_hkl, out.d_hkl, npk), (self.fam_off, out.fam_off, npk + 1),
+                     (self.hkl, out.hkl, nfm), (self.mult, out.mult, nfm)]
+            nbytes = self.totals.numel() * 8
+            for dst, src, k in pairs:
+                if k > 0:
+                    dst[:k].copy_(src[:k], non_blocking=True)
+                    nbytes += dst[:k].numel() * dst.element_size()
+            st.synchronize()
+        self.bytes_last = nbytes
+        return {"totals": self.totals.numpy(), "peak_off": self.peak_off.numpy(), "status": self.status[:n].numpy(),
+                "two_theta": self.two_theta[:npk].numpy(), "intensity": self.intensity[:npk].numpy(),
+                "d_hkl": self.d_hkl[:npk].numpy(), "fam_off": self.fam_off[:npk + 1].numpy(),
+                "hkl": self.hkl[:nfm].numpy(), "mult": self.mult[:nfm].numpy()}
+
+
 class Handle:
     """An xrd_handle bound to one CUDA device."""
 

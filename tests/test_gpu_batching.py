@@ -87,3 +87,29 @@ def test_graph_replay_matches_eager_and_follows_inputs(gpu_lib):
         g.close()
     finally:
         h.close()
+
+
+def test_pinned_host_download_matches_device_outputs(gpu_lib):
+    """HostPattern.download copies exactly the used prefix of every output."""
+    xrd = gpu_lib
+    b, o = synth.small(n=64)
+    h = xrd.Handle(0)
+    try:
+        db, co = _setup(xrd, b, o)
+        sz = h.query_sizes(db, co)
+        ws = xrd.workspace(sz.ws_bytes)
+        out = xrd.PatternBuffers(db.n_struct, sz.n_refl)
+        h.pattern_batch(db, co, out, ws)
+        hp = xrd.HostPattern(db.n_struct, sz.n_refl)
+        got = hp.download(out)
+        npk, nfm = int(got["totals"][1]), int(got["totals"][2])
+        assert npk > 0 and nfm >= npk
+        ref = {"peak_off": out.peak_off, "two_theta": out.two_theta[:npk], "intensity": out.intensity[:npk],
+               "d_hkl": out.d_hkl[:npk], "fam_off": out.fam_off[:npk + 1], "hkl": out.hkl[:nfm],
+               "mult": out.mult[:nfm], "status": out.status[:db.n_struct]}
+        for k, v in ref.items():
+            assert np.array_equal(got[k], v.cpu().numpy()), k
+        expect = 8 * 4 + 8 * (db.n_struct + 1) + 4 * db.n_struct + 24 * npk + 8 * (npk + 1) + 16 * nfm
+        assert hp.bytes_last == expect
+    finally:
+        h.close()
