@@ -78,7 +78,7 @@ Layout layout(int64_t n, int64_t natoms, int zmax, int64_t R)
     L.refl_off = take(8 * (n + 1));
     L.tile_off = take(4 * (n + 1));
     L.order = take(4 * n);
-    L.cls_list = take(16 * n);
+    L.cls_list = take(4 * xrd::kPostClasses * n);
     L.npk = take(8 * n);
     L.nfm = take(8 * n);
     L.fam_soff = take(8 * (n + 1));
@@ -505,7 +505,7 @@ int xrd_pattern_batch(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, cons
     pa.If = sa.If;
     pa.cls_list = ga.cls_list;
     pa.cls_cnt = ga.abort_flag + 4;
-    pa.cls_next = ga.abort_flag + 8;
+    pa.cls_next = ga.abort_flag + 4 + xrd::kPostClasses;
     pa.grid = h->sms;
     pa.g_perm = (int*)(ws + L.g_perm);
     pa.g_bkt = (int*)(ws + L.g_bkt);

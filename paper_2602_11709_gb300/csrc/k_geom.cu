@@ -338,133 +338,171 @@ __global__ void __launch_bounds__(256) k_emit(const Geo* __restrict__ geo, doubl
                                tcnt[(int64_t)s * blockDim.x + threadIdx.x]);
 }
 
-// Single block: exclusive scan of the per-structure reflection counts, the
-// largest-first order of structures (counting sort on the atom count, which
-// sets the cost of a structure-factor tile) and the scan of tiles in that
-// order; flags a capacity overflow when the total exceeds the workspace.
+// Single block. Every pass walks the batch in chunks of kScanItems * blockDim
+// structures (or positions in the largest-first order): coalesced loads into
+// registers, a transpose through shared memory when a pass needs a prefix,
+// and warp-aggregated shared-memory atomics where it needs ranks.
+//  1. reflection offsets (64-bit exclusive scan of the counts), the capacity
+//     check and the per-structure status;
+//  2. the largest-first order of structures: a counting sort on the atom
+//     count, which sets the cost of a structure-factor tile;
+//  3. in that order, the tile offsets and the post-processing size-class
+//     lists (post_class; within a class the order follows the chunks).
+// The tile table itself is written by k_tiles over the whole GPU.
 constexpr int kOrderBins = 4096;
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
 
-__global__ void __launch_bounds__(1024) k_scan_refl(const int64_t* __restrict__ cnt, const Geo* __restrict__ geo,
-                                                    const int64_t* __restrict__ atom_off, int n, int tile,
-                                                    int64_t cap_refl, int64_t* __restrict__ refl_off,
-                                                    int* __restrict__ tile_off, int* __restrict__ order,
-                                                    int2* __restrict__ tile_tab, int* __restrict__ cls_list,
-                                                    int* __restrict__ abort_flag, int64_t* __restrict__ totals,
-                                                    int32_t* __restrict__ status)
+__device__ __forceinline__ int order_bin(const int64_t* __restrict__ atom_off, int s)
 {
-    __shared__ long long ws[32];
-    __shared__ long long carry;
-    __shared__ int bins[kOrderBins];
-    __shared__ int tmp[34];
-    __shared__ int nbad;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    // 1. reflection offsets in structure order (64-bit scan)
-    if (threadIdx.x == 0) carry = 0;
-    __syncthreads();
-    for (int base = 0; base < n; base += blockDim.x) {
-        const int i = base + threadIdx.x;
-        const long long v = i < n ? cnt[i] : 0;
-        long long iv = v;
-        for (int o = 1; o < 32; o <<= 1) {
-            const long long t = __shfl_up_sync(0xffffffffu, iv, o);
-            if (lane >= o) iv += t;
+    const long long na = atom_off[s + 1] - atom_off[s];
+    return kOrderBins - 1 - (int)min(max(na, 0LL), (long long)(kOrderBins - 1));
+}
+
+// Rank of this lane among the lanes of its warp with the same key, and the
+// base the group's leader obtained with one shared-memory atomicAdd on ctr[key].
+__device__ __forceinline__ int warp_aggregated_slot(int* ctr, int key, bool active)
+{
+    const unsigned act = __ballot_sync(0xffffffffu, active);
+    if (!active) return 0;
+    const unsigned peers = __match_any_sync(act, key);
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(peers) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(&ctr[key], __popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    return base + __popc(peers & ((1u << lane) - 1u));
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_refl(const int64_t* __restrict__ cnt, const Geo* __restrict__ geo,
+                                                            const int64_t* __restrict__ atom_off, int n, int tile,
+                                                            int64_t cap_refl, int64_t* __restrict__ refl_off,
+                                                            int* __restrict__ tile_off, int* __restrict__ order,
+                                                            int* __restrict__ cls_list, int* __restrict__ abort_flag,
+                                                            int64_t* __restrict__ totals, int32_t* __restrict__ status)
+{
+    __shared__ long long ws[33];
+    __shared__ __align__(16) long long buf[kScanItems * kScanThreads];  // also the order bins
+    __shared__ int ccnt[kPostClasses];
+    int* bins = (int*)buf;
+    const int nt = blockDim.x, tid = threadIdx.x, CH = kScanItems * nt;
+    long long tot;
+    // 1. reflection offsets in structure order, and the status of each structure
+    long long carry = 0, bad = 0;
+    for (int base = 0; base < n; base += CH) {
+        long long v[kScanItems];
+        int st[kScanItems];
+#pragma unroll
+        for (int u = 0; u < kScanItems; u++) {
+            const int i = base + u * nt + tid;
+            v[u] = i < n ? cnt[i] : 0;
+            st[u] = i < n ? geo[i].status : XRD_OK;
         }
-        if (lane == 31) ws[w] = iv;
-        __syncthreads();
-        if (w == 0) {
-            const long long a0 = lane < nw ? ws[lane] : 0;
-            long long ia = a0;
-            for (int o = 1; o < 32; o <<= 1) {
-                const long long t = __shfl_up_sync(0xffffffffu, ia, o);
-                if (lane >= o) ia += t;
+        chunk_scan<kScanItems>(v, buf, ws, &tot);
+#pragma unroll
+        for (int u = 0; u < kScanItems; u++) {
+            const int i = base + u * nt + tid;
+            if (i < n) {
+                refl_off[i] = carry + v[u];
+                status[i] = st[u];
             }
-            if (lane < nw) ws[lane] = ia - a0;
+            bad += st[u] != XRD_OK;
         }
-        __syncthreads();
-        if (i < n) refl_off[i] = carry + ws[w] + iv - v;
-        __syncthreads();
-        if (threadIdx.x == blockDim.x - 1) carry += ws[w] + iv;
-        __syncthreads();
+        carry += tot;
     }
     const long long total = carry;
-    // 2. largest-first order: counting sort on (kOrderBins - 1 - min(atoms, kOrderBins - 1))
-    for (int b = threadIdx.x; b < kOrderBins; b += blockDim.x) bins[b] = 0;
+    const bool over = total > cap_refl;
+    block_prefix_ll(bad, ws, &tot);
+    const long long nbad = over ? n : tot;
+    if (over)
+        for (int i = tid; i < n; i += nt) status[i] = XRD_ECAPACITY;
+    // 2. largest-first order: counting sort on (kOrderBins - 1 - min(atoms, kOrderBins - 1));
+    //    warp-aggregated, so structures of one bin keep their warp's order
+    for (int b = tid; b < kOrderBins; b += nt) bins[b] = 0;
     __syncthreads();
-    for (int s = threadIdx.x; s < n; s += blockDim.x) {
-        const long long na = atom_off[s + 1] - atom_off[s];
-        const int key = kOrderBins - 1 - (int)min(max(na, 0LL), (long long)(kOrderBins - 1));
-        atomicAdd(&bins[key], 1);
+    for (int base = 0; base < n; base += CH) {
+        int b[kScanItems];
+#pragma unroll
+        for (int u = 0; u < kScanItems; u++) {
+            const int i = base + u * nt + tid;
+            b[u] = i < n ? order_bin(atom_off, i) : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < kScanItems; u++) warp_aggregated_slot(bins, b[u], base + u * nt + tid < n);
     }
     __syncthreads();
-    block_excl_scan(bins, kOrderBins, tmp);
-    __syncthreads();
-    for (int s = threadIdx.x; s < n; s += blockDim.x) {
-        const long long na = atom_off[s + 1] - atom_off[s];
-        const int key = kOrderBins - 1 - (int)min(max(na, 0LL), (long long)(kOrderBins - 1));
-        order[atomicAdd(&bins[key], 1)] = s;
+    block_excl_scan(bins, kOrderBins, (int*)ws);
+    for (int base = 0; base < n; base += CH) {
+        int b[kScanItems];
+#pragma unroll
+        for (int u = 0; u < kScanItems; u++) {
+            const int i = base + u * nt + tid;
+            b[u] = i < n ? order_bin(atom_off, i) : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < kScanItems; u++) {
+            const int i = base + u * nt + tid;
+            const int slot = warp_aggregated_slot(bins, b[u], i < n);
+            if (i < n) order[slot] = i;
+        }
     }
-    __syncthreads();
-    // 3. tile offsets in that order (int scan; totals fit 32 bits)
-    int tcarry = 0;
-    for (int base = 0; base < n; base += blockDim.x) {
-        const int i = base + threadIdx.x;
-        const int v = i < n ? (int)((cnt[order[i]] + tile - 1) / tile) : 0;
-        const int inc = warp_incl_scan(v);
-        if (lane == 31) tmp[w] = inc;
-        __syncthreads();
-        if (w == 0) {
-            const int sv = lane < nw ? tmp[lane] : 0;
-            const int si = warp_incl_scan(sv);
-            if (lane < nw) tmp[lane] = si - sv;
-            if (lane == 31) tmp[32] = si;
+    if (tid < kPostClasses) ccnt[tid] = 0;
+    __syncthreads();  // order[] (global) is visible to the whole block; bins are free
+    // 3. tiles and size classes in that order
+    long long tcarry = 0;
+    for (int base = 0; base < n; base += CH) {
+        long long v[kScanItems];
+        int sv[kScanItems];
+#pragma unroll
+        for (int u = 0; u < kScanItems; u++) {
+            const int p = base + u * nt + tid;
+            sv[u] = p < n ? order[p] : -1;
         }
-        __syncthreads();
-        if (i < n) tile_off[i] = tcarry + tmp[w] + inc - v;
-        tcarry += tmp[32];
-        __syncthreads();
+        long long c[kScanItems];
+#pragma unroll
+        for (int u = 0; u < kScanItems; u++) {
+            c[u] = sv[u] >= 0 ? cnt[sv[u]] : 0;
+            v[u] = (c[u] + tile - 1) / tile;
+        }
+        chunk_scan<kScanItems>(v, buf, ws, &tot);
+#pragma unroll
+        for (int u = 0; u < kScanItems; u++) {
+            const int p = base + u * nt + tid;
+            if (p < n) tile_off[p] = (int)(tcarry + v[u]);
+            if (!over && cls_list) {
+                const int k = post_class(c[u]);
+                const int slot = warp_aggregated_slot(ccnt, k, p < n);
+                if (p < n) cls_list[(int64_t)k * n + slot] = sv[u];
+            }
+        }
+        tcarry += tot;
+        __syncthreads();  // this chunk's class slots are taken before the next chunk's
     }
-    const int over = total > cap_refl;
-    // 4. tile table: (structure, first reflection of the tile within it), largest-first order
-    __syncthreads();
-    if (!over && tile_tab)
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            const int s = order[i];
-            const int nt = (int)((cnt[s] + tile - 1) / tile);
-            const int t0 = tile_off[i];
-            for (int t = 0; t < nt; t++) tile_tab[t0 + t] = make_int2(s, t * tile);
-        }
-    // 5. post-processing size classes, filled in largest-first order
-    __shared__ int ccnt[4];
-    if (threadIdx.x < 4) ccnt[threadIdx.x] = 0;
-    __syncthreads();
-    if (!over && cls_list)
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            const int s = order[i];
-            const long long c = cnt[s];
-            const int k = c <= kPostCapSmall ? 0 : (c <= kPostCapMid ? 1 : (c <= kPostCapLarge ? 2 : 3));
-            cls_list[(int64_t)k * n + atomicAdd(&ccnt[k], 1)] = s;
-        }
-    __syncthreads();
-    if (threadIdx.x < 4) abort_flag[4 + threadIdx.x] = ccnt[threadIdx.x];
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
         refl_off[n] = total;
-        tile_off[n] = over ? 0 : tcarry;
+        tile_off[n] = over ? 0 : (int)tcarry;
+        for (int k = 0; k < kPostClasses; k++) abort_flag[4 + k] = over ? 0 : ccnt[k];
         totals[0] = total;
         totals[1] = 0;
         totals[2] = 0;
+        totals[3] = nbad;
         *abort_flag = over;
-        nbad = 0;
     }
-    __syncthreads();
-    int bad = 0;
-    for (int s = threadIdx.x; s < n; s += blockDim.x) {
-        const int st = over ? XRD_ECAPACITY : geo[s].status;
-        status[s] = st;
-        bad += st != XRD_OK;
+}
+
+// Tile table: (structure, first reflection of the tile within it) in the
+// largest-first order, one thread per structure.
+__global__ void __launch_bounds__(256) k_tiles(const int64_t* __restrict__ cnt, const int* __restrict__ order,
+                                               const int* __restrict__ tile_off, int n, int tile,
+                                               const int* __restrict__ abort_flag, int2* __restrict__ tile_tab)
+{
+    if (*abort_flag) return;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+        const int s = order[p];
+        const int nt = (int)((cnt[s] + tile - 1) / tile);
+        const int t0 = tile_off[p];
+        for (int t = 0; t < nt; t++) tile_tab[t0 + t] = make_int2(s, t * tile);
     }
-    atomicAdd(&nbad, bad);
-    __syncthreads();
-    if (threadIdx.x == 0) totals[3] = nbad;
 }
 
 void launch_prep(const GeomArgs& a, cudaStream_t st)
@@ -499,7 +537,10 @@ void launch_count(const GeomArgs& a, cudaStream_t st)
 void launch_scan_refl(const GeomArgs& a, cudaStream_t st)
 {
     k_scan_refl<<<1, 1024, 0, st>>>(a.refl_cnt, a.geo, a.atom_off, a.n_struct, a.tile, a.cap_refl, a.refl_off,
-                                    a.tile_off, a.order, a.tile_tab, a.cls_list, a.abort_flag, a.totals, a.status);
+                                    a.tile_off, a.order, a.cls_list, a.abort_flag, a.totals, a.status);
+    if (a.n_struct > 0 && a.tile_tab)
+        k_tiles<<<(a.n_struct + 255) / 256, 256, 0, st>>>(a.refl_cnt, a.order, a.tile_off, a.n_struct, a.tile,
+                                                         a.abort_flag, a.tile_tab);
 }
 
 void launch_emit(const GeomArgs& a, cudaStream_t st)

@@ -20,12 +20,8 @@
 
 namespace xrd {
 
-constexpr int kPostThreads = 256;
 // Size classes (reflections per structure held in shared memory); the scan
 // kernel sorts structures into them with the same bounds.
-constexpr int kCapSmall = kPostCapSmall;  // 256 threads, four CTAs per SM
-constexpr int kCapMid = kPostCapMid;      // 512 threads, two CTAs per SM
-constexpr int kCapLarge = kPostCapLarge;  // 1024 threads, one CTA per SM; larger: global scratch
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
@@ -348,63 +344,59 @@ __global__ void __launch_bounds__(NT) k_post(const PostArgs a, int cls)
 }
 
 // Exclusive scans of kept peaks and families per structure (single block),
-// output capacity check, totals.
-__global__ void __launch_bounds__(1024) k_scan_out(const CompactArgs a)
+// output capacity check, totals. The structures are walked in chunks of
+// kOutItems * blockDim: coalesced loads into registers, then a transpose
+// through shared memory so that each thread scans consecutive structures.
+constexpr int kOutThreads = 1024;
+constexpr int kOutItems = 4;
+
+__global__ void __launch_bounds__(kOutThreads) k_scan_out(const CompactArgs a)
 {
-    __shared__ long long wp[32], wf[32];
-    __shared__ long long cp, cf;
+    __shared__ long long ws[33];
+    __shared__ long long buf[kOutItems * kOutThreads];
     if (*a.abort_flag) return;
-    const int n = a.n_struct;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    if (threadIdx.x == 0) { cp = 0; cf = 0; }
-    __syncthreads();
-    for (int base = 0; base < n; base += blockDim.x) {
-        const int i = base + threadIdx.x;
-        const long long vp = i < n ? a.npk[i] : 0, vf = i < n ? a.nfm[i] : 0;
-        long long ip = vp, jf = vf;
-        for (int o = 1; o < 32; o <<= 1) {
-            const long long x = __shfl_up_sync(0xffffffffu, ip, o), y = __shfl_up_sync(0xffffffffu, jf, o);
-            if (lane >= o) { ip += x; jf += y; }
+    const int n = a.n_struct, nt = blockDim.x, tid = threadIdx.x, CH = kOutItems * nt;
+    long long cp = 0, cf = 0;
+    for (int base = 0; base < n; base += CH) {
+        long long vp[kOutItems], vf[kOutItems];
+#pragma unroll
+        for (int u = 0; u < kOutItems; u++) {
+            const int i = base + u * nt + tid;
+            vp[u] = i < n ? a.npk[i] : 0;
+            vf[u] = i < n ? a.nfm[i] : 0;
         }
-        if (lane == 31) { wp[w] = ip; wf[w] = jf; }
-        __syncthreads();
-        if (w == 0) {
-            const long long x0 = lane < nw ? wp[lane] : 0, y0 = lane < nw ? wf[lane] : 0;
-            long long x = x0, y = y0;
-            for (int o = 1; o < 32; o <<= 1) {
-                const long long u = __shfl_up_sync(0xffffffffu, x, o), v = __shfl_up_sync(0xffffffffu, y, o);
-                if (lane >= o) { x += u; y += v; }
+        long long tp, tf;
+        chunk_scan<kOutItems>(vp, buf, ws, &tp);
+        chunk_scan<kOutItems>(vf, buf, ws, &tf);
+#pragma unroll
+        for (int u = 0; u < kOutItems; u++) {
+            const int i = base + u * nt + tid;
+            if (i < n) {
+                a.out.peak_off[i] = cp + vp[u];
+                a.fam_soff[i] = cf + vf[u];
             }
-            if (lane < nw) { wp[lane] = x - x0; wf[lane] = y - y0; }
         }
-        __syncthreads();
-        if (i < n) {
-            a.out.peak_off[i] = cp + wp[w] + ip - vp;
-            a.fam_soff[i] = cf + wf[w] + jf - vf;
-        }
-        __syncthreads();
-        if (threadIdx.x == blockDim.x - 1) { cp += wp[w] + ip; cf += wf[w] + jf; }
-        __syncthreads();
+        cp += tp;
+        cf += tf;
     }
-    if (threadIdx.x == 0) {
+    const bool over = cp > a.cap_peaks || cf > a.cap_fam;
+    if (over)
+        for (int i = tid; i < n; i += nt) a.out.status[i] = XRD_ECAPACITY;
+    if (tid == 0) {
         a.out.peak_off[n] = cp;
         a.fam_soff[n] = cf;
         a.out.totals[1] = cp;
         a.out.totals[2] = cf;
-        const int over = cp > a.cap_peaks || cf > a.cap_fam;
         *a.out_abort = over;
         if (over) a.out.totals[3] = n;
         else a.out.fam_off[cp] = cf;
     }
-    __syncthreads();
-    if (cp > a.cap_peaks || cf > a.cap_fam)
-        for (int s = threadIdx.x; s < n; s += blockDim.x) a.out.status[s] = XRD_ECAPACITY;
 }
 
-// largest s with off[s] <= i, for off[0] = 0 <= i < off[n]
-__device__ __forceinline__ int owner(const int64_t* __restrict__ off, int n, int64_t i)
+// largest s in [lo, n) with off[s] <= i, for off[lo] <= i < off[n]
+__device__ __forceinline__ int owner(const int64_t* __restrict__ off, int lo, int n, int64_t i)
 {
-    int lo = 0, hi = n;
+    int hi = n;
     while (hi - lo > 1) {
         const int mid = (lo + hi) >> 1;
         if (off[mid] <= i) lo = mid;
@@ -413,39 +405,54 @@ __device__ __forceinline__ int owner(const int64_t* __restrict__ off, int n, int
     return lo;
 }
 
-// Kept peaks into the dense CSR outputs, one thread per output peak over the
-// whole batch: 2-theta and d are formed here from the anchor |g|^2, so their
-// FP64 work is spread evenly over the GPU.
-__global__ void __launch_bounds__(256) k_compact_peaks(const CompactArgs a)
-{
-    if (*a.abort_flag || *a.out_abort) return;
-    const int n = a.n_struct;
-    const int64_t total = a.out.peak_off[n];
-    for (int64_t P = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; P < total; P += (int64_t)gridDim.x * blockDim.x) {
-        const int s = owner(a.out.peak_off, n, P);
-        const int64_t src = a.refl_off[s] + (P - a.out.peak_off[s]);
-        const double qa = a.st_q[src], I = a.st_I[src];
-        const int fo = a.st_foff[src];
-        a.out.two_theta[P] = two_theta_q(qa, a.l2h, a.l2l, a.ttab);
-        a.out.d_hkl[P] = inv_sqrt_df(qa);
-        a.out.intensity[P] = I;
-        a.out.fam_off[P] = a.fam_soff[s] + fo;
-    }
-}
+// Kept peaks and their families into the dense CSR outputs, one thread per
+// output peak. Each block takes one contiguous range of output peaks: thread 0
+// finds the structure of the range's first peak by bisection, and every
+// thread then walks forward from the structure of the previous 256 peaks (a
+// few steps; bisection again past eight). 2-theta and d are formed here from
+// the anchor |g|^2.
+constexpr int kCompactThreads = 256;
 
-// Families into the dense CSR outputs, one thread per output family.
-__global__ void __launch_bounds__(256) k_compact_fams(const CompactArgs a)
+__global__ void __launch_bounds__(kCompactThreads) k_compact(const CompactArgs a)
 {
+    __shared__ int s_cur;
     if (*a.abort_flag || *a.out_abort) return;
-    const int n = a.n_struct;
-    const int64_t total = a.fam_soff[n];
-    for (int64_t F = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; F < total; F += (int64_t)gridDim.x * blockDim.x) {
-        const int s = owner(a.fam_soff, n, F);
-        const int64_t src = a.refl_off[s] + (F - a.fam_soff[s]);
-        a.out.hkl[3 * F] = a.st_hkl[3 * src];
-        a.out.hkl[3 * F + 1] = a.st_hkl[3 * src + 1];
-        a.out.hkl[3 * F + 2] = a.st_hkl[3 * src + 2];
-        a.out.mult[F] = a.st_mult[src];
+    const int n = a.n_struct, tid = threadIdx.x;
+    const int64_t* __restrict__ poff = a.out.peak_off;
+    const int64_t total = poff[n];
+    const int64_t per = ((total + gridDim.x - 1) / gridDim.x + kCompactThreads - 1) / kCompactThreads * kCompactThreads;
+    const int64_t start = (int64_t)blockIdx.x * per, end = min(start + per, total);
+    if (start >= end) return;
+    if (tid == 0) s_cur = owner(poff, 0, n, start);
+    __syncthreads();
+    for (int64_t P0 = start; P0 < end; P0 += kCompactThreads) {
+        const int64_t P = P0 + tid;
+        int s = s_cur;
+        if (P < end) {
+            for (int k = 0; k < 8 && poff[s + 1] <= P; k++) s++;
+            if (poff[s + 1] <= P) s = owner(poff, s + 1, n, P);
+            const int64_t pe = poff[s + 1];
+            const int64_t rb = a.refl_off[s];
+            const int64_t src = rb + (P - poff[s]);
+            const double qa = a.st_q[src];
+            a.out.two_theta[P] = two_theta_q(qa, a.l2h, a.l2l, a.ttab);
+            a.out.d_hkl[P] = inv_sqrt_df(qa);
+            a.out.intensity[P] = a.st_I[src];
+            const int64_t fs = a.fam_soff[s];
+            const int64_t f0 = fs + a.st_foff[src];
+            const int64_t f1 = P + 1 < pe ? fs + a.st_foff[src + 1] : a.fam_soff[s + 1];
+            a.out.fam_off[P] = f0;
+            for (int64_t F = f0; F < f1; F++) {
+                const int64_t fsrc = rb + (F - fs);
+                a.out.hkl[3 * F] = a.st_hkl[3 * fsrc];
+                a.out.hkl[3 * F + 1] = a.st_hkl[3 * fsrc + 1];
+                a.out.hkl[3 * F + 2] = a.st_hkl[3 * fsrc + 2];
+                a.out.mult[F] = a.st_mult[fsrc];
+            }
+        }
+        __syncthreads();  // every thread has read s_cur
+        if (tid == kCompactThreads - 1) s_cur = s;  // owner of this round's last peak
+        __syncthreads();
     }
 }
 
@@ -472,10 +479,12 @@ static void launch_post_class(const PostArgs& a, int cls, cudaStream_t st)
 template <bool FI>
 static void launch_post_fi(const PostArgs& a, const cudaStream_t* st)
 {
-    launch_post_class<0, 1024, FI>(a, 3, st[3]);
-    launch_post_class<kCapLarge, 1024, FI>(a, 2, st[2]);
-    launch_post_class<kCapMid, 512, FI>(a, 1, st[1]);
-    launch_post_class<kCapSmall, kPostThreads, FI>(a, 0, st[0]);
+    launch_post_class<0, 1024, FI>(a, 5, st[5]);
+    launch_post_class<kPostCap4, 1024, FI>(a, 4, st[4]);
+    launch_post_class<kPostCap3, 512, FI>(a, 3, st[3]);
+    launch_post_class<kPostCap2, 256, FI>(a, 2, st[2]);
+    launch_post_class<kPostCap1, 128, FI>(a, 1, st[1]);
+    launch_post_class<kPostCap0, 64, FI>(a, 0, st[0]);
 }
 
 // a.grid = number of SMs
@@ -488,11 +497,8 @@ void launch_post(const PostArgs& a, const cudaStream_t* st)
 
 void launch_compact(const CompactArgs& a, cudaStream_t st)
 {
-    k_scan_out<<<1, 1024, 0, st>>>(a);
-    if (a.n_struct > 0) {
-        k_compact_peaks<<<a.grid * 8, 256, 0, st>>>(a);
-        k_compact_fams<<<a.grid * 8, 256, 0, st>>>(a);
-    }
+    k_scan_out<<<1, kOutThreads, 0, st>>>(a);
+    if (a.n_struct > 0) k_compact<<<a.grid * 8, kCompactThreads, 0, st>>>(a);
 }
 
 }  // namespace xrd

@@ -56,9 +56,11 @@ __device__ __forceinline__ float fprime_of(const Coef32& c, float s2)
 // FP32 variants: RB reflections per lane share each atom record, which the
 // warp stages in shared memory and every lane reads (a broadcast).
 // GRAD also accumulates dF/ds^2 = sum_j occ_j exp(-B_j s^2)(f_j' - B_j f_j) e^{i phi_j}.
+// staged: the structure's atoms (at most kSfChunk) are already in sat from the
+// previous tile of the same structure.
 template <int PREC, bool GRAD, int kSfRB>
 __device__ void sf_tile_fp32(const SfArgs& a, int64_t r0, int64_t re, int64_t j0, int64_t j1, Atom32* sat,
-                             const Coef32* scoef)
+                             const Coef32* scoef, bool staged)
 {
     constexpr float ln2 = 0.69314718055994531f;
     const int lane = threadIdx.x & 31;
@@ -79,9 +81,11 @@ __device__ void sf_tile_fp32(const SfArgs& a, int64_t r0, int64_t re, int64_t j0
     int zc = -1;
     for (int64_t c0 = j0; c0 < j1; c0 += kSfChunk) {
         const int nc = (int)min((int64_t)kSfChunk, j1 - c0);
-        __syncwarp();
-        for (int i = lane; i < nc; i += 32) sat[i] = a.atom32[c0 + i];
-        __syncwarp();
+        if (!staged) {
+            __syncwarp();
+            for (int i = lane; i < nc; i += 32) sat[i] = a.atom32[c0 + i];
+            __syncwarp();
+        }
         for (int jj = 0; jj < nc; jj++) {
             const Atom32 at = sat[jj];
             if (at.z != zc) {  // uniform: every lane walks the same element-sorted list
@@ -176,8 +180,10 @@ __device__ void sf_tile_fp64(const SfArgs& a, int64_t r0, int64_t re, int64_t j0
     }
 }
 
-// Persistent CTAs; every warp takes 128-reflection tiles from a queue in
-// largest-first order (tiles of the structures with the most atoms first).
+// Persistent CTAs; every warp takes tiles of 32 RB reflections from a queue in
+// largest-first order (tiles of the structures with the most atoms first). A
+// structure's atoms stay staged in the warp's shared memory while its
+// consecutive tiles follow (when they fit one chunk).
 // Register caps: 64 for the integer-phase variant (32 resident warps per SM),
 // about 85 for the FP64-phase and gradient variants (24 warps).
 template <int PREC, bool GRAD, int RB, int WARPS>
@@ -195,6 +201,7 @@ __global__ void __launch_bounds__(32 * WARPS, PREC == XRD_FP64 ? 1 : ((PREC == X
         __syncthreads();
     }
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int staged_s = -1;  // structure whose atoms (one chunk at most) are in sat[w]
     for (;;) {
         int t = 0;
         if (lane == 0) t = atomicAdd(a.tile_counter, 1);
@@ -205,8 +212,13 @@ __global__ void __launch_bounds__(32 * WARPS, PREC == XRD_FP64 ? 1 : ((PREC == X
         const int64_t rb = a.refl_off[s], re = a.refl_off[s + 1];
         const int64_t r0 = rb + e.y;
         const int64_t j0 = a.atom_off[s], j1 = a.atom_off[s + 1];
-        if (PREC == XRD_FP64) sf_tile_fp64<RB>(a, r0, re, j0, j1);
-        else sf_tile_fp32<PREC, GRAD, RB>(a, r0, re, j0, j1, sat[w], scoef);
+        if (PREC == XRD_FP64) {
+            sf_tile_fp64<RB>(a, r0, re, j0, j1);
+        } else {
+            const bool one_chunk = j1 - j0 <= kSfChunk;
+            sf_tile_fp32<PREC, GRAD, RB>(a, r0, re, j0, j1, sat[w], scoef, one_chunk && s == staged_s);
+            staged_s = one_chunk ? s : -1;
+        }
     }
 }
 

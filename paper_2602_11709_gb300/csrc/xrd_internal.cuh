@@ -12,10 +12,15 @@ constexpr double kPi = 3.14159265358979323846;
 constexpr double kFScale = 41.78214;  // Mott-Bethe factor 8 pi^2 a0 of f(s) (Sec. 1, atomic scattering factors)
 constexpr int kZmaxLimit = 255;
 constexpr int kHklLimit = 511;        // |h|, |k|, |l| fit the 10-bit fields of the packed key
-constexpr int kPostCapSmall = 1536;   // post-processing size classes (reflections per structure):
-constexpr int kPostCapMid = 3072;     // 256, 512 and 1024 threads with the reflections in shared memory,
-constexpr int kPostCapLarge = 6144;   // larger structures on global scratch
-constexpr int kPostClasses = 4;
+// Post-processing size classes: structures with at most kPostCap[c] reflections
+// (held in shared memory) go to class c; larger ones to the last class (global
+// scratch). Threads per CTA: 64, 128, 256, 512, 1024, 1024.
+constexpr int kPostClasses = 6;
+constexpr int kPostCap0 = 256, kPostCap1 = 512, kPostCap2 = 1536, kPostCap3 = 3072, kPostCap4 = 6144;
+__host__ __device__ __forceinline__ int post_class(long long c)
+{
+    return c <= kPostCap0 ? 0 : c <= kPostCap1 ? 1 : c <= kPostCap2 ? 2 : c <= kPostCap3 ? 3 : c <= kPostCap4 ? 4 : 5;
+}
 
 // Per-structure geometry written by k_prep (step S0).
 struct Geo {
@@ -312,6 +317,68 @@ __device__ __forceinline__ void block_excl_scan2(int* a, int* b, int n, int* tmp
         ra += va;
         rb += vb;
     }
+    __syncthreads();
+}
+
+// Exclusive block-wide prefix of one 64-bit value per thread (two barriers;
+// ws: 33 long longs of shared memory, free again on return). Returns this
+// thread's exclusive prefix; *total gets the block total.
+__device__ __forceinline__ long long block_prefix_ll(long long v, long long* ws, long long* total)
+{
+    const int nw = (blockDim.x + 31) >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    long long inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane == 31) ws[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        const long long x = lane < nw ? ws[lane] : 0;
+        long long y = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long t = __shfl_up_sync(0xffffffffu, y, o);
+            if (lane >= o) y += t;
+        }
+        if (lane < nw) ws[lane] = y - x;
+        if (lane == 31) ws[32] = y;
+    }
+    __syncthreads();
+    const long long r = ws[w] + inc - v;
+    *total = ws[32];
+    __syncthreads();
+    return r;
+}
+
+// Exclusive scan of one chunk of ITEMS * blockDim values held as v[u] for
+// element u * blockDim + tid (the coalesced order they were loaded in):
+// transposed through buf (ITEMS * blockDim long longs of shared memory) so
+// that each thread scans ITEMS consecutive elements, then back. v receives the
+// exclusive prefixes in the same order; *total the chunk's total.
+template <int kScanItems>
+__device__ __forceinline__ void chunk_scan(long long (&v)[kScanItems], long long* buf, long long* ws, long long* total)
+{
+    const int nt = blockDim.x, tid = threadIdx.x;
+#pragma unroll
+    for (int u = 0; u < kScanItems; u++) buf[u * nt + tid] = v[u];
+    __syncthreads();
+    long long loc[kScanItems], sum = 0;
+#pragma unroll
+    for (int u = 0; u < kScanItems; u++) {
+        loc[u] = buf[tid * kScanItems + u];
+        sum += loc[u];
+    }
+    long long run = block_prefix_ll(sum, ws, total);
+#pragma unroll
+    for (int u = 0; u < kScanItems; u++) {
+        buf[tid * kScanItems + u] = run;
+        run += loc[u];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < kScanItems; u++) v[u] = buf[u * nt + tid];
     __syncthreads();
 }
 

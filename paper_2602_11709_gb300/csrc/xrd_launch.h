@@ -30,8 +30,9 @@ struct GeomArgs {
     int* tile_off;
     int* order;
     int2* tile_tab;  // [tiles] (structure, first reflection) of each structure-factor tile
-    int* cls_list;   // [4][n_struct] post-processing size classes (nullptr: not built)
-    int* abort_flag; // flags[0]; flags[1] output abort, flags[2] tile queue, flags[4..7] class counts
+    int* cls_list;   // [kPostClasses][n_struct] post-processing size classes (nullptr: not built)
+    int* abort_flag; // flags[0]; flags[1] output abort, flags[2] tile queue, flags[4..9] class counts,
+                     // flags[10..15] class work counters
     int64_t* totals;
     int32_t* status;
     double* q;
@@ -73,9 +74,9 @@ struct PostArgs {
     const uint32_t* key;
     const double* I;    // FP64 intensities (XRD_FP64), or
     const float* If;    // FP32 intensities (the FP32 variants)
-    const int* cls_list;  // [4][n_struct] structures of each size class, largest first
-    const int* cls_cnt;   // [4]
-    int* cls_next;        // [4] work counters (zero at launch)
+    const int* cls_list;  // [kPostClasses][n_struct] structures of each size class, largest first
+    const int* cls_cnt;   // [kPostClasses]
+    int* cls_next;        // [kPostClasses] work counters (zero at launch)
     // global scratch for structures larger than cap_smem (indexed by reflection)
     int* g_perm;
     int* g_bkt;   // n_refl + n_struct entries
