@@ -39,9 +39,41 @@ WORKLOADS = {
 }
 
 
-def load_workload(name):
+def load_workload(name, world=1):
+    """The named workload; with world > 1 the batch holds world times as many structures (same
+    generator), of which each rank takes one contiguous shard (weak scaling)."""
     from paper_2602_11709_gb300 import synth
-    return {"small": synth.small, "mixed": synth.mixed, "large": synth.large}[name]()
+    gen = {"small": synth.small, "mixed": synth.mixed, "large": synth.large}[name]
+    if world == 1:
+        return gen()
+    import inspect
+    return gen(n=inspect.signature(gen).parameters["n"].default * world)
+
+
+def shard_bounds(n_total, rank, world):
+    """Contiguous shard [start, end) of n_total structures for one rank; shards cover the batch."""
+    q, r = divmod(n_total, world)
+    start = rank * q + min(rank, r)
+    return start, start + q + (1 if rank < r else 0)
+
+
+def reduce_over_ranks(terms, structures, seconds, world, device="cpu"):
+    """Whole-job totals: terms and structures summed over ranks, time = the slowest rank's.
+    Host-side measurement only (the pattern path itself exchanges nothing between ranks)."""
+    if world == 1:
+        return terms, structures, seconds
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(terms), float(structures)], dtype=torch.float64, device=device)
+    m = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    dist.all_reduce(m, op=dist.ReduceOp.MAX)
+    return int(t[0].item()), int(t[1].item()), float(m[0].item())
+
+
+# DRAM bytes (read + write) of one k_sf launch on the small workload, from one ncu capture of
+# the kernel as it stands (dram__bytes_read.sum + dram__bytes_write.sum); other workloads: not captured
+SF_TRAFFIC_BYTES = {"small": 13556224}
 # SFU issue rates per SM per clock measured on this GB300 (MUFU.SIN/COS 16, MUFU.EX2 32) and the
 # maximum SM clock; the structure-factor roofline of a batch follows from its mix of operations.
 MUFU_SINCOS_PER_CLK = 16.0
@@ -172,7 +204,10 @@ def run_ours(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     dev = local if torch.cuda.is_available() else 0
     torch.cuda.set_device(dev)
-    b, o = load_workload(args.workload)
+    b, o = load_workload(args.workload, world)
+    if world > 1:  # this rank's shard of the world-times-larger batch
+        lo, hi = shard_bounds(b.n_struct, rank, world)
+        b = b.subset(np.arange(lo, hi))
     h = xrd.Handle(dev)
     db = xrd.DeviceBatch.from_host(b, "cuda:%d" % dev)
     co = xrd.make_opts(o, args.precision)
@@ -241,14 +276,10 @@ def run_ours(args):
     barrier()
     ck = clocks.stop()
     step_ms = [a.elapsed_time(c) for a, c in ev]
-    total_s = sum(step_ms) / 1e3
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_s], dtype=torch.float64, device="cuda:%d" % dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = terms_full * args.steps * world / total_s
-    pps = b.n_struct * args.steps * world / total_s
+    total_terms, total_structs, total_s = reduce_over_ranks(terms_full, b.n_struct, sum(step_ms) / 1e3, world,
+                                                            "cuda:%d" % dev)
+    value = total_terms * args.steps / total_s
+    pps = total_structs * args.steps / total_s
     sf_avg = float(np.mean(sf_ms)) / 1e3
     sfu_floor_s = sfu_cycles / (152.0 * SM_MAX_MHZ * 1e6)
     peak_gterms = terms_eval / sfu_floor_s / 1e9
@@ -294,7 +325,8 @@ def run_ours(args):
             e2e_ms.append((t1 - t0) * 1e3)
             d2h = hp.bytes_last
         assert int(res["totals"][3]) == 0
-    e2e_s = float(np.mean(e2e_ms)) / 1e3
+    e2e_terms, _, e2e_s = reduce_over_ranks(terms_full, b.n_struct, float(np.mean(e2e_ms)) / 1e3, world,
+                                            "cuda:%d" % dev)
 
     if rank == 0:
         cpu = None
@@ -312,16 +344,17 @@ def run_ours(args):
             "config": {"workload": WORKLOADS[args.workload], "n_struct": b.n_struct, "precision": args.precision,
                        "terms_full_sphere": terms_full, "terms_evaluated": terms_eval,
                        "reflections_friedel_unique": int(sz.n_refl), "l2": "flushed between steps (256 MiB write)",
-                       "parallelism": "replica per GPU" if world > 1 else "1 GPU",
+                       "parallelism": "one structure shard per GPU" if world > 1 else "1 GPU",
                        "launch": "CUDA graph" if graph is not None else "eager",
                        "sf_shape": {"tile": tuned[0], "warps": tuned[1]} if tuned else "default"},
             "patterns_per_s": pps,
             "roofline": {"bound": "alu", "unit": "Gterm/s", "achieved": achieved_gterms, "peak": peak_gterms,
-                         "frac": achieved_gterms / peak_gterms, "traffic": None,
+                         "frac": achieved_gterms / peak_gterms,
+                         "traffic": SF_TRAFFIC_BYTES.get(args.workload), "traffic_unit": "bytes per launch",
                          "kernel": "k_sf", "peak_basis": "SFU: sin+cos at 16/clk/SM, exp2 at 32/clk/SM, "
                                                          "152 SMs, 2070 MHz; Friedel-unique terms"},
             "cpu_baseline": cpu,
-            "e2e": {"value": terms_full / e2e_s, "unit": "terms/s", "h2d_bytes_per_step": int(h2d),
+            "e2e": {"value": e2e_terms / e2e_s, "unit": "terms/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_s * 1e3},
             "clocks": ck,
             "gpu_launches": xrd.LAUNCHES_PER_BATCH * args.steps,
