@@ -190,7 +190,8 @@ int xrd_pattern_grad(xrd_handle* h, const xrd_batch* batch, const xrd_opts* opts
  * or 4 warps per CTA -- times the structure-factor stage with CUDA events,
  * synchronising `stream`, and keeps the fastest shape in the handle; later calls
  * with opts.tile = -1 use it. Writes the chosen tile and warps if the pointers
- * are not NULL. Not capturable (it synchronises).
+ * are not NULL. Returns after `stream` has been synchronised (every tuning
+ * call has finished). Not capturable.
  */
 int xrd_autotune(xrd_handle* h, const xrd_batch* batch, const xrd_opts* opts, const xrd_pattern* out,
                  void* workspace, size_t ws_bytes, void* stream /* cudaStream_t */, int32_t* best_tile,
@@ -203,7 +204,8 @@ int xrd_set_sf_shape(xrd_handle* h, int tile, int warps);
 /*
  * CUDA graph of one xrd_pattern_batch call with exactly these arguments (the
  * device buffers are baked into the graph: replays read the batch's current
- * contents and rewrite the outputs). xrd_graph_create runs one eager call on a
+ * contents and rewrite the outputs). xrd_graph_create synchronises the device
+ * (earlier work on these buffers must be finished), runs one eager call on a
  * private stream, synchronises it, then captures a second call; *graph gets an
  * opaque executable. xrd_graph_launch replays it on `stream`;
  * xrd_graph_destroy frees it. The batch's sizes (and so the workspace) must
@@ -214,10 +216,14 @@ int xrd_graph_create(xrd_handle* h, const xrd_batch* batch, const xrd_opts* opts
 int xrd_graph_launch(xrd_handle* h, void* graph, void* stream /* cudaStream_t */);
 void xrd_graph_destroy(void* graph);
 
-/* Stage timing: when enabled, xrd_pattern_batch records CUDA events around
- * each kernel on its stream; xrd_stage_times synchronises on the last event
- * and writes up to n stage durations in milliseconds (order: prep, atoms,
- * count, scan, emit, structure factor, post, compact) and returns the count. */
+/* Stage timing. Mode 1: xrd_pattern_batch records CUDA events between all
+ * stages on its stream; mode 2: only around the structure-factor stage (each
+ * event is a node of a captured graph and costs time, so mode 2 perturbs a
+ * timed run least); 0: off (XRD_EINVAL for another value). xrd_stage_times
+ * synchronises on the last event of the last recorded call and writes up to n
+ * stage durations in milliseconds (order: prep, atoms, count, scan, emit,
+ * structure factor, post, compact; in mode 2 every stage but the structure
+ * factor reads 0) and returns the count. */
 int xrd_set_profiling(xrd_handle* h, int enabled);
 int xrd_stage_times(xrd_handle* h, float* ms, int n);
 

@@ -12,8 +12,8 @@ struct xrd_handle {
     int device = 0;
     int sms = 0;
     std::string err;
-    bool profiling = false;
-    bool recorded = false;
+    int profiling = 0;  // 0 off, 1 every stage, 2 the structure-factor stage only
+    int recorded = 0;   // the mode of the last recorded call
     cudaEvent_t ev[9] = {};
     void* qbuf = nullptr;  // query scratch owned by the handle
     size_t qbuf_bytes = 0;
@@ -29,6 +29,7 @@ namespace {
 constexpr int kTileMin = 64;    // smallest structure-factor warp tile (32 lanes x 2 reflections)
 constexpr int kPostCap = 2048;  // reflections per structure kept in shared memory by k_post
 constexpr int kStages = 8;
+constexpr int kSfStage = 5;  // index of the structure-factor stage
 
 struct DeviceGuard {
     int prev = -1;
@@ -328,7 +329,8 @@ const char* xrd_last_error(const xrd_handle* h) { return h ? h->err.c_str() : "N
 int xrd_set_profiling(xrd_handle* h, int enabled)
 {
     if (!h) return XRD_EINVAL;
-    h->profiling = enabled != 0;
+    if (enabled < 0 || enabled > 2) return fail(h, XRD_EINVAL, "profiling mode must be 0, 1 or 2");
+    h->profiling = enabled;
     return XRD_OK;
 }
 
@@ -337,10 +339,13 @@ int xrd_stage_times(xrd_handle* h, float* ms, int n)
     if (!h || (!ms && n > 0)) return -XRD_EINVAL;
     if (!h->recorded) return 0;
     DeviceGuard g(h->device);
-    cudaError_t e = cudaEventSynchronize(h->ev[kStages]);
+    const bool sf_only = h->recorded == 2;
+    cudaError_t e = cudaEventSynchronize(h->ev[sf_only ? kSfStage + 1 : kStages]);
     if (e != cudaSuccess) return -cuda_fail(h, e, "xrd_stage_times");
     const int m = n < kStages ? n : kStages;
     for (int i = 0; i < m; i++) {
+        ms[i] = 0.f;
+        if (sf_only && i != kSfStage) continue;
         e = cudaEventElapsedTime(&ms[i], h->ev[i], h->ev[i + 1]);
         if (e != cudaSuccess) return -cuda_fail(h, e, "xrd_stage_times");
     }
@@ -428,7 +433,7 @@ int xrd_pattern_batch(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, cons
     sf_shape(h, o, rb, warps);
     xrd::GeomArgs ga = geom_args(b, o, L, ws, cap_refl, out->totals, out->status, 32 * rb);
 
-    const bool prof = h->profiling;
+    const int prof = h->profiling;
     unsigned rec_flags = 0;  // inside a stream capture, stage events become timed graph nodes
     if (prof) {
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -436,8 +441,9 @@ int xrd_pattern_batch(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, cons
             rec_flags = cudaEventRecordExternal;
     }
     int stage = 0;
-    auto mark = [&]() {
-        if (prof) cudaEventRecordWithFlags(h->ev[stage], st, rec_flags);
+    auto mark = [&]() {  // mode 2 marks only the two ends of the structure-factor stage
+        if (prof == 1 || (prof == 2 && (stage == kSfStage || stage == kSfStage + 1)))
+            cudaEventRecordWithFlags(h->ev[stage], st, rec_flags);
         stage++;
     };
     cudaMemsetAsync(ws + L.flags, 0, 64, st);
@@ -581,12 +587,20 @@ int xrd_autotune(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, const xrd
     const bool all = o && o->precision == XRD_FP32_PHASEFIX;
     const int nshape = all ? 6 : 2;
     const int keep_rb = h->sf_rb, keep_w = h->sf_warps;
-    const bool keep_prof = h->profiling;
+    const int keep_prof = h->profiling;
     xrd_opts oo = o ? *o : xrd_opts{};
     oo.tile = -1;
     float best = 1e30f;
     int brb = keep_rb, bw = keep_w;
-    h->profiling = true;
+    // the stage events of mode 2 end with the structure factor, so the calls' later kernels may
+    // still run when xrd_stage_times returns: the stream is synchronised before every return
+    auto finish = [&](int rc) {
+        DeviceGuard dg(h->device);
+        const cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+        if (rc == XRD_OK && e != cudaSuccess) rc = cuda_fail(h, e, "xrd_autotune");
+        return rc;
+    };
+    h->profiling = 2;
     for (int i = 0; i < nshape; i++) {
         const int rb = all ? shapes[i][0] : (i == 0 ? 4 : 2);
         h->sf_rb = rb;
@@ -596,13 +610,13 @@ int xrd_autotune(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, const xrd
             const int rc = xrd_pattern_batch(h, b, &oo, out, workspace, ws_bytes, stream);
             if (rc != XRD_OK) {
                 h->sf_rb = keep_rb; h->sf_warps = keep_w; h->profiling = keep_prof;
-                return rc;
+                return finish(rc);
             }
             float ms[8];
             const int m = xrd_stage_times(h, ms, 8);
             if (m < 0) {
                 h->sf_rb = keep_rb; h->sf_warps = keep_w; h->profiling = keep_prof;
-                return -m;
+                return finish(-m);
             }
             if (m >= 6 && rep > 0 && ms[5] < t) t = ms[5];  // structure-factor stage, after one warm-up
         }
@@ -613,7 +627,7 @@ int xrd_autotune(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, const xrd
     h->profiling = keep_prof;
     if (best_tile) *best_tile = 32 * brb;
     if (best_warps) *best_warps = bw;
-    return XRD_OK;
+    return finish(XRD_OK);
 }
 
 struct xrd_graph_exec {
@@ -627,8 +641,12 @@ int xrd_graph_create(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, const
     if (!h || !graph) return XRD_EINVAL;
     *graph = nullptr;
     DeviceGuard dg(h->device);
+    // the eager call below runs on a private stream: work of earlier calls on the caller's
+    // streams (same workspace and outputs) must be finished first
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(h, e, "xrd_graph_create: synchronise");
     cudaStream_t st = nullptr;
-    cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
     if (e != cudaSuccess) return cuda_fail(h, e, "xrd_graph_create: stream");
     // one eager call validates the arguments and settles the per-device launch caches
     int rc = xrd_pattern_batch(h, b, o, out, workspace, ws_bytes, st);

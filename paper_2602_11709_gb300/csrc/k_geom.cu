@@ -29,6 +29,7 @@ __device__ __forceinline__ double cosd(double deg)
 // by cofactors over the determinant, and the enumeration box |h| <= r_max a + 1.
 __global__ void k_prep(const double* __restrict__ lattice, int n, double rmax, Geo* __restrict__ geo)
 {
+    pdl_enter();
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     const double a = lattice[6 * s], b = lattice[6 * s + 1], c = lattice[6 * s + 2];
@@ -90,6 +91,7 @@ __global__ void k_prep(const double* __restrict__ lattice, int n, double rmax, G
 // f(s) coefficients in the form the FP32 loops use (exp2 with the scale folded in).
 __global__ void k_coef(const double* __restrict__ coef, int zmax, Coef32* __restrict__ c32)
 {
+    pdl_enter();
     for (int z = threadIdx.x; z <= zmax; z += blockDim.x) {
         Coef32 c;
         for (int i = 0; i < 4; i++) {
@@ -108,6 +110,7 @@ __global__ void __launch_bounds__(128) k_atoms(const int64_t* __restrict__ atom_
                                                Geo* __restrict__ geo, Atom32* __restrict__ a32,
                                                Atom64* __restrict__ a64)
 {
+    pdl_enter();
     __shared__ int off[kZmaxLimit + 1];
     __shared__ int zs[128];
     __shared__ int bad;
@@ -312,6 +315,7 @@ __global__ void __launch_bounds__(256) k_count(const Geo* __restrict__ geo, doub
                                                float r2minf, float r2maxf, int64_t* __restrict__ cnt,
                                                int* __restrict__ tcnt)
 {
+    pdl_enter();
     __shared__ int tmp[34];
     const int s = blockIdx.x;
     const Geo g = geo[s];
@@ -328,6 +332,7 @@ __global__ void __launch_bounds__(256) k_emit(const Geo* __restrict__ geo, doubl
                                               const int* __restrict__ tcnt, const int* __restrict__ abort_flag,
                                               double* __restrict__ q, uint32_t* __restrict__ key)
 {
+    pdl_enter();
     __shared__ int tmp[34];
     if (*abort_flag) return;
     const int s = blockIdx.x;
@@ -381,6 +386,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_refl(const int64_t* __res
                                                             int* __restrict__ cls_list, int* __restrict__ abort_flag,
                                                             int64_t* __restrict__ totals, int32_t* __restrict__ status)
 {
+    pdl_enter();
     __shared__ long long ws[33];
     __shared__ __align__(16) long long buf[kScanItems * kScanThreads];  // also the order bins
     __shared__ int ccnt[kPostClasses];
@@ -496,6 +502,7 @@ __global__ void __launch_bounds__(256) k_tiles(const int64_t* __restrict__ cnt, 
                                                const int* __restrict__ tile_off, int n, int tile,
                                                const int* __restrict__ abort_flag, int2* __restrict__ tile_tab)
 {
+    pdl_enter();
     if (*abort_flag) return;
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
         const int s = order[p];
@@ -509,14 +516,14 @@ void launch_prep(const GeomArgs& a, cudaStream_t st)
 {
     const int n = a.n_struct;
     if (n > 0) k_prep<<<(n + 31) / 32, 32, 0, st>>>(a.lattice, n, a.rmax, a.geo);
-    k_coef<<<1, 256, 0, st>>>(a.coef, a.zmax, a.coef32);
+    launch_pdl(k_coef, 1, 256, 0, st, a.coef, a.zmax, a.coef32);
 }
 
 void launch_atoms(const GeomArgs& a, cudaStream_t st)
 {
     if (a.n_struct > 0)
-        k_atoms<<<a.n_struct, 128, 0, st>>>(a.atom_off, a.n_atoms, a.frac, a.Z, a.occ, a.B, a.zmax, a.geo, a.atom32,
-                                            a.atom64);
+        launch_pdl(k_atoms, a.n_struct, 128, 0, st, a.atom_off, a.n_atoms, a.frac, a.Z, a.occ, a.B, a.zmax, a.geo,
+                   a.atom32, a.atom64);
 }
 
 void launch_count_only(const GeomArgs& a, cudaStream_t st)
@@ -524,30 +531,30 @@ void launch_count_only(const GeomArgs& a, cudaStream_t st)
     const int n = a.n_struct;
     if (n <= 0) return;
     k_prep<<<(n + 31) / 32, 32, 0, st>>>(a.lattice, n, a.rmax, a.geo);
-    k_count<<<n, 256, 0, st>>>(a.geo, a.r2min, a.r2max, (float)a.r2min, (float)a.r2max, a.refl_cnt, nullptr);
+    launch_pdl(k_count, n, 256, 0, st, a.geo, a.r2min, a.r2max, (float)a.r2min, (float)a.r2max, a.refl_cnt, (int*)nullptr);
 }
 
 void launch_count(const GeomArgs& a, cudaStream_t st)
 {
     if (a.n_struct > 0)
-        k_count<<<a.n_struct, 256, 0, st>>>(a.geo, a.r2min, a.r2max, (float)a.r2min, (float)a.r2max, a.refl_cnt,
-                                            a.tcnt);
+        launch_pdl(k_count, a.n_struct, 256, 0, st, a.geo, a.r2min, a.r2max, (float)a.r2min, (float)a.r2max,
+                   a.refl_cnt, a.tcnt);
 }
 
 void launch_scan_refl(const GeomArgs& a, cudaStream_t st)
 {
-    k_scan_refl<<<1, 1024, 0, st>>>(a.refl_cnt, a.geo, a.atom_off, a.n_struct, a.tile, a.cap_refl, a.refl_off,
-                                    a.tile_off, a.order, a.cls_list, a.abort_flag, a.totals, a.status);
+    launch_pdl(k_scan_refl, 1, 1024, 0, st, a.refl_cnt, a.geo, a.atom_off, a.n_struct, a.tile, a.cap_refl,
+               a.refl_off, a.tile_off, a.order, a.cls_list, a.abort_flag, a.totals, a.status);
     if (a.n_struct > 0 && a.tile_tab)
-        k_tiles<<<(a.n_struct + 255) / 256, 256, 0, st>>>(a.refl_cnt, a.order, a.tile_off, a.n_struct, a.tile,
-                                                         a.abort_flag, a.tile_tab);
+        launch_pdl(k_tiles, (a.n_struct + 255) / 256, 256, 0, st, a.refl_cnt, a.order, a.tile_off, a.n_struct,
+                   a.tile, a.abort_flag, a.tile_tab);
 }
 
 void launch_emit(const GeomArgs& a, cudaStream_t st)
 {
     if (a.n_struct > 0)
-        k_emit<<<a.n_struct, 256, 0, st>>>(a.geo, a.r2min, a.r2max, (float)a.r2min, (float)a.r2max, a.refl_off,
-                                           a.tcnt, a.abort_flag, a.q, a.key);
+        launch_pdl(k_emit, a.n_struct, 256, 0, st, a.geo, a.r2min, a.r2max, (float)a.r2min, (float)a.r2max,
+                   a.refl_off, a.tcnt, a.abort_flag, a.q, a.key);
 }
 
 }  // namespace xrd

@@ -30,6 +30,7 @@ constexpr float kLog2e = 1.4426950408889634f;
 
 __global__ void __launch_bounds__(kGradThreads) k_broaden(const GradArgs a)
 {
+    pdl_enter();
     extern __shared__ int bins[];  // cell counts, then offsets; cells c = b + W + 1 in [0, nb)
     __shared__ int tmp[34];
     const int s = blockIdx.x;
@@ -124,6 +125,7 @@ __device__ __forceinline__ void dG_dp(const double* lat, int m, double D[3][3])
 
 __global__ void __launch_bounds__(kGradThreads) k_grad_refl(const GradArgs a)
 {
+    pdl_enter();
     __shared__ double red[6][kGradThreads / 32];
     const int s = blockIdx.x;
     const bool ok = !*a.abort_flag && a.geo[s].status == XRD_OK;
@@ -230,6 +232,7 @@ __global__ void __launch_bounds__(kGradThreads) k_grad_refl(const GradArgs a)
 // residues in a fixed order.
 __global__ void __launch_bounds__(kGradThreads) k_grad_atoms(const GradArgs a)
 {
+    pdl_enter();
     __shared__ uint32_t skey[kAtomChunkRefl];
     __shared__ float ss2[kAtomChunkRefl], sU[kAtomChunkRefl], sV[kAtomChunkRefl];
     __shared__ float red[kGradThreads][4];
@@ -328,14 +331,14 @@ void launch_broaden(const GradArgs& a, cudaStream_t st)
     if (a.n_struct <= 0) return;
     const size_t smem = broaden_smem_bytes(a.n_pts, a.W);
     if (smem > 48 * 1024) cudaFuncSetAttribute(k_broaden, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_broaden<<<a.n_struct, kGradThreads, smem, st>>>(a);
+    launch_pdl(k_broaden, a.n_struct, kGradThreads, smem, st, a);
 }
 
 void launch_grad(const GradArgs& a, cudaStream_t st)
 {
     if (a.n_struct <= 0) return;
     k_grad_refl<<<a.n_struct, kGradThreads, 0, st>>>(a);
-    k_grad_atoms<<<a.n_struct, kGradThreads, 0, st>>>(a);
+    launch_pdl(k_grad_atoms, a.n_struct, kGradThreads, 0, st, a);
 }
 
 }  // namespace xrd

@@ -296,6 +296,7 @@ __device__ void post_structure(const PostArgs& a, int s, int64_t base, int n, co
 template <int CAP, int NT, bool FI>
 __global__ void __launch_bounds__(NT) k_post(const PostArgs a, int cls)
 {
+    pdl_enter();
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int tmp[66];
     __shared__ double dtmp[32];
@@ -352,6 +353,7 @@ constexpr int kOutItems = 4;
 
 __global__ void __launch_bounds__(kOutThreads) k_scan_out(const CompactArgs a)
 {
+    pdl_enter();
     __shared__ long long ws[33];
     __shared__ long long buf[kOutItems * kOutThreads];
     if (*a.abort_flag) return;
@@ -415,6 +417,7 @@ constexpr int kCompactThreads = 256;
 
 __global__ void __launch_bounds__(kCompactThreads) k_compact(const CompactArgs a)
 {
+    pdl_enter();
     __shared__ int s_cur;
     if (*a.abort_flag || *a.out_abort) return;
     const int n = a.n_struct, tid = threadIdx.x;
@@ -498,7 +501,7 @@ void launch_post(const PostArgs& a, const cudaStream_t* st)
 void launch_compact(const CompactArgs& a, cudaStream_t st)
 {
     k_scan_out<<<1, kOutThreads, 0, st>>>(a);
-    if (a.n_struct > 0) k_compact<<<a.grid * 8, kCompactThreads, 0, st>>>(a);
+    if (a.n_struct > 0) launch_pdl(k_compact, a.grid * 8, kCompactThreads, 0, st, a);
 }
 
 }  // namespace xrd

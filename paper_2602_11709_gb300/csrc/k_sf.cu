@@ -191,6 +191,7 @@ __global__ void __launch_bounds__(32 * WARPS, PREC == XRD_FP64 ? 1 : ((PREC == X
                                                                                                           : 24 / WARPS))
     k_sf(const SfArgs a)
 {
+    pdl_enter();
     constexpr int kSfThreads = 32 * WARPS;
     __shared__ Atom32 sat[WARPS][kSfChunk];
     extern __shared__ Coef32 scoef[];  // [zmax + 1]
@@ -239,7 +240,7 @@ static void launch_sf_shape(const SfArgs& a, cudaStream_t st)
             per_sm = 4;
         if (dev >= 0 && dev < 64) { cache_per_sm[dev] = per_sm; cache_zmax[dev] = a.zmax; }
     }
-    k_sf<PREC, GRAD, RB, WARPS><<<a.grid * per_sm, 32 * WARPS, smem, st>>>(a);
+    launch_pdl(k_sf<PREC, GRAD, RB, WARPS>, a.grid * per_sm, 32 * WARPS, smem, st, a);
 }
 
 template <int PREC, bool GRAD>

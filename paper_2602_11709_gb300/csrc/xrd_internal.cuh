@@ -94,6 +94,36 @@ __device__ __forceinline__ uint32_t fix32(double v)
     return (uint32_t)(unsigned long long)__double_as_longlong(t);
 }
 
+// ---- programmatic dependent launch ----
+// Every kernel starts with pdl_enter(): it waits until the grid it depends on
+// has completed and its memory is visible (a no-op when the kernel was launched
+// the ordinary way), then lets the next grid on the stream be launched, so that
+// grid's launch and rasterisation overlap this one's execution. A dependent
+// grid can start only once every CTA of this grid is resident, and it waits in
+// its own pdl_enter(), so the order of the stream is kept.
+__device__ __forceinline__ void pdl_enter()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Launch k on st as a programmatic dependent of the previous kernel on st.
+template <typename... P, typename... A>
+inline cudaError_t launch_pdl(void (*k)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, A... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, static_cast<P>(args)...);
+}
+
 // ---- two-float ("double-float") arithmetic: value = hi + lo, |lo| <= ulp(hi) / 2 ----
 struct F2 {
     float hi, lo;

@@ -356,8 +356,9 @@ class Handle:
         """A CUDA graph of one pattern_batch call with these buffers."""
         return Graph(self, db, opts, out, ws)
 
-    def set_profiling(self, on: bool):
-        self._check(self.lib.xrd_set_profiling(self.h, 1 if on else 0))
+    def set_profiling(self, mode):
+        """0/False off, 1/True events between all stages, 2 events around the structure factor only."""
+        self._check(self.lib.xrd_set_profiling(self.h, int(mode)))
 
     def stage_times(self):
         buf = (C.c_float * len(STAGES))()

@@ -113,3 +113,55 @@ def test_pinned_host_download_matches_device_outputs(gpu_lib):
         assert hp.bytes_last == expect
     finally:
         h.close()
+
+
+def test_profiling_modes(gpu_lib):
+    """Mode 1 times every stage, mode 2 the structure-factor stage only; other modes are refused."""
+    xrd = gpu_lib
+    b, o = synth.small(n=64)
+    h = xrd.Handle(0)
+    try:
+        db, co = _setup(xrd, b, o)
+        sz = h.query_sizes(db, co)
+        ws = xrd.workspace(sz.ws_bytes)
+        out = xrd.PatternBuffers(db.n_struct, sz.n_refl)
+        h.set_profiling(1)
+        h.pattern_batch(db, co, out, ws)
+        st = h.stage_times()
+        assert len(st) == 8 and all(v > 0.0 for v in st.values())
+        h.set_profiling(2)
+        h.pattern_batch(db, co, out, ws)
+        st = h.stage_times()
+        assert st["structure_factor"] > 0.0
+        assert all(v == 0.0 for k, v in st.items() if k != "structure_factor")
+        with pytest.raises(xrd.XrdError):
+            h.set_profiling(3)
+        h.set_profiling(0)
+    finally:
+        h.close()
+
+
+def test_autotune_then_graph_on_another_stream(gpu_lib):
+    """xrd_autotune returns only after its calls have finished, and xrd_graph_create
+    (whose warm-up call runs on a private stream) waits for earlier work on the
+    same buffers: the replayed pattern equals an eager one."""
+    import torch
+    xrd = gpu_lib
+    b, o = synth.mixed(n=100_000)
+    b = b.subset(np.arange(4000))
+    h = xrd.Handle(0)
+    try:
+        db, co = _setup(xrd, b, o)
+        sz = h.query_sizes(db, co)
+        ws = xrd.workspace(sz.ws_bytes)
+        ref = _run(xrd, h, db, co, sz.n_refl, ws)
+        out = xrd.PatternBuffers(db.n_struct, sz.n_refl)
+        h.set_profiling(2)
+        h.autotune(db, co, out, ws)
+        g = h.graph(db, co, out, ws)
+        g.launch(torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        _same(ref, out.to_host())
+        h.set_profiling(0)
+    finally:
+        h.close()
