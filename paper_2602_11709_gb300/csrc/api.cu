@@ -22,6 +22,9 @@ struct xrd_handle {
     // side streams for the concurrent post-processing size classes (fork/join by events)
     cudaStream_t side[xrd::kPostClasses - 1] = {};
     cudaEvent_t fork = nullptr, join[xrd::kPostClasses - 1] = {};
+    // the input-only front (coefficients, atom packing, largest-first order) runs on side[0]
+    // beside the enumeration: forked by front, joined by order_done and atoms_done
+    cudaEvent_t front = nullptr, order_done = nullptr, atoms_done = nullptr;
 };
 
 namespace {
@@ -61,8 +64,8 @@ size_t al(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Byte offsets of every array in the caller's workspace.
 struct Layout {
-    size_t geo, refl_cnt, tcnt, refl_off, tile_off, order, cls_list, tile_tab, npk, nfm, fam_soff, flags, coef32, atom32,
-        atom64;
+    size_t geo, refl_cnt, tcnt, refl_off, tile_off, order, atom_bad, cls_list, tile_tab, npk, nfm, fam_soff, flags,
+        coef32, atom32, atom64;
     size_t q, key, I, g_perm, g_bkt, g_flag, g_pstart, g_psum, g_fcnt;
     size_t st_q, st_I, st_foff, st_hkl, st_mult;
     size_t total;
@@ -79,6 +82,7 @@ Layout layout(int64_t n, int64_t natoms, int zmax, int64_t R)
     L.refl_off = take(8 * (n + 1));
     L.tile_off = take(4 * (n + 1));
     L.order = take(4 * n);
+    L.atom_bad = take(4 * n);
     L.cls_list = take(4 * xrd::kPostClasses * n);
     L.npk = take(8 * n);
     L.nfm = take(8 * n);
@@ -109,7 +113,7 @@ Layout layout(int64_t n, int64_t natoms, int zmax, int64_t R)
 // Workspace of the broadened-pattern / gradient path: the geometry prefix of
 // the pattern layout plus the per-reflection state kept for the backward pass.
 struct LayoutG {
-    size_t geo, refl_cnt, tcnt, refl_off, tile_off, order, tile_tab, flags, coef32, atom32, atom64;
+    size_t geo, refl_cnt, tcnt, refl_off, tile_off, order, atom_bad, tile_tab, flags, coef32, atom32, atom64;
     size_t q, key, Fx, Ig, tb, td, perm, U, V;
     size_t total;
 };
@@ -125,6 +129,7 @@ LayoutG layout_grad(int64_t n, int64_t natoms, int zmax, int64_t R)
     L.refl_off = take(8 * (n + 1));
     L.tile_off = take(4 * (n + 1));
     L.order = take(4 * n);
+    L.atom_bad = take(4 * n);
     L.flags = take(64);
     L.coef32 = take(sizeof(xrd::Coef32) * (zmax + 1));
     L.atom32 = take(sizeof(xrd::Atom32) * natoms);
@@ -255,6 +260,7 @@ xrd::GeomArgs geom_args(const xrd_batch* b, const xrd_opts* o, const Layout& L, 
     g.refl_off = (int64_t*)(ws + L.refl_off);
     g.tile_off = (int*)(ws + L.tile_off);
     g.order = (int*)(ws + L.order);
+    g.atom_bad = (int*)(ws + L.atom_bad);
     g.tile_tab = (int2*)(ws + L.tile_tab);
     g.cls_list = (int*)(ws + L.cls_list);
     g.abort_flag = (int*)(ws + L.flags);
@@ -301,6 +307,9 @@ int xrd_create(xrd_handle** h, int device)
         if (e != cudaSuccess) { xrd_destroy(p); return XRD_ECUDA; }
     }
     e = cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->front, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->order_done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->atoms_done, cudaEventDisableTiming);
     if (e != cudaSuccess) { xrd_destroy(p); return XRD_ECUDA; }
     p->ttab = xrd::init_tables(0);  // device tables (2-theta), once per handle, on the legacy stream
     e = cudaStreamSynchronize(0);
@@ -320,6 +329,8 @@ void xrd_destroy(xrd_handle* h)
         if (h->join[i]) cudaEventDestroy(h->join[i]);
     }
     if (h->fork) cudaEventDestroy(h->fork);
+    for (cudaEvent_t ev : {h->front, h->order_done, h->atoms_done})
+        if (ev) cudaEventDestroy(ev);
     if (h->qbuf) cudaFree(h->qbuf);
     delete h;
 }
@@ -446,18 +457,31 @@ int xrd_pattern_batch(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, cons
             cudaEventRecordWithFlags(h->ev[stage], st, rec_flags);
         stage++;
     };
+    const bool pdl = prof != 1;  // programmatic launches where no stage event separates two kernels
     cudaMemsetAsync(ws + L.flags, 0, 64, st);
     mark();
-    xrd::launch_prep(ga, st);
+    // the input-only front beside the enumeration: order (needed by the scan), then
+    // coefficients and atoms (needed by the structure factor)
+    cudaStream_t side = h->side[0];
+    ga.atoms_set_geo = 0;
+    cudaEventRecord(h->front, st);
+    cudaStreamWaitEvent(side, h->front, 0);
+    xrd::launch_order(ga, side, false);
+    cudaEventRecord(h->order_done, side);
+    xrd::launch_coef(ga, side, true);
+    xrd::launch_atoms(ga, side, true);
+    cudaEventRecord(h->atoms_done, side);
+    xrd::launch_prep(ga, st, false);
     mark();
-    xrd::launch_atoms(ga, st);
+    mark();  // the atom packing stage runs on the side stream: nothing on this one
+    xrd::launch_count(ga, st, pdl);
     mark();
-    xrd::launch_count(ga, st);
+    cudaStreamWaitEvent(st, h->order_done, 0);
+    xrd::launch_scan_refl(ga, st, false);
     mark();
-    xrd::launch_scan_refl(ga, st);
+    xrd::launch_emit(ga, st, pdl);
     mark();
-    xrd::launch_emit(ga, st);
-    mark();
+    cudaStreamWaitEvent(st, h->atoms_done, 0);
 
     xrd::SfArgs sa{};
     sa.n_struct = (int)n;
@@ -483,7 +507,7 @@ int xrd_pattern_batch(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, cons
     if (o->precision == XRD_FP64) sa.I = (double*)(ws + L.I);
     else sa.If = (float*)(ws + L.I);
     sa.F = nullptr;
-    xrd::launch_sf(sa, st);
+    xrd::launch_sf(sa, st, false);
     mark();
 
     xrd::PostArgs pa{};
@@ -512,6 +536,9 @@ int xrd_pattern_batch(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, cons
     pa.cls_list = ga.cls_list;
     pa.cls_cnt = ga.abort_flag + 4;
     pa.cls_next = ga.abort_flag + 4 + xrd::kPostClasses;
+    pa.atom_bad = ga.atom_bad;
+    pa.status = out->status;
+    pa.totals = out->totals;
     pa.grid = h->sms;
     pa.g_perm = (int*)(ws + L.g_perm);
     pa.g_bkt = (int*)(ws + L.g_bkt);
@@ -781,6 +808,8 @@ int xrd_pattern_broadened(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, 
     ga.refl_off = (int64_t*)(ws + L.refl_off);
     ga.tile_off = (int*)(ws + L.tile_off);
     ga.order = (int*)(ws + L.order);
+    ga.atom_bad = (int*)(ws + L.atom_bad);
+    ga.atoms_set_geo = 1;  // atoms run before the enumeration here
     ga.tile_tab = (int2*)(ws + L.tile_tab);
     ga.abort_flag = (int*)(ws + L.flags);
     ga.totals = totals;
@@ -788,11 +817,13 @@ int xrd_pattern_broadened(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, 
     ga.q = (double*)(ws + L.q);
     ga.key = (uint32_t*)(ws + L.key);
     cudaMemsetAsync(ws + L.flags, 0, 64, st);
-    xrd::launch_prep(ga, st);
-    xrd::launch_atoms(ga, st);
-    xrd::launch_count(ga, st);
-    xrd::launch_scan_refl(ga, st);
-    xrd::launch_emit(ga, st);
+    xrd::launch_prep(ga, st, false);
+    xrd::launch_coef(ga, st, true);
+    xrd::launch_atoms(ga, st, true);
+    xrd::launch_order(ga, st, true);
+    xrd::launch_count(ga, st, true);
+    xrd::launch_scan_refl(ga, st, true);
+    xrd::launch_emit(ga, st, true);
     xrd::SfArgs sa{};
     sa.n_struct = (int)n;
     sa.precision = XRD_FP32_PHASEFIX;
@@ -816,7 +847,7 @@ int xrd_pattern_broadened(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, 
     sa.key = ga.key;
     sa.Fx = (float4*)(ws + L.Fx);
     sa.Ig = (float*)(ws + L.Ig);
-    xrd::launch_sf(sa, st);
+    xrd::launch_sf(sa, st, true);
     xrd::GradArgs gr = grad_args(h, b, grid, W, sigma, o, L, ws);
     gr.y = y;
     xrd::launch_broaden(gr, st);

@@ -107,8 +107,8 @@ __global__ void k_coef(const double* __restrict__ coef, int zmax, Coef32* __rest
 __global__ void __launch_bounds__(128) k_atoms(const int64_t* __restrict__ atom_off, int64_t n_atoms,
                                                const double* __restrict__ frac, const int16_t* __restrict__ Zin,
                                                const double* __restrict__ occ, const double* __restrict__ Bf, int zmax,
-                                               Geo* __restrict__ geo, Atom32* __restrict__ a32,
-                                               Atom64* __restrict__ a64)
+                                               Geo* __restrict__ geo, int set_geo, int* __restrict__ atom_bad,
+                                               Atom32* __restrict__ a32, Atom64* __restrict__ a64)
 {
     pdl_enter();
     __shared__ int off[kZmaxLimit + 1];
@@ -131,8 +131,19 @@ __global__ void __launch_bounds__(128) k_atoms(const int64_t* __restrict__ atom_
         else atomicAdd(&off[z], 1);
     }
     __syncthreads();
+    if (threadIdx.x == 0) atom_bad[s] = bad;
     if (bad) {
-        if (threadIdx.x == 0) geo[s].status = XRD_EINVAL;
+        // neutral records (weight 0, element 0) keep the structure-factor kernel's reads in bounds;
+        // the structure reports XRD_EINVAL and gets no peaks
+        if (threadIdx.x == 0 && set_geo) geo[s].status = XRD_EINVAL;
+        for (int64_t i = threadIdx.x; i < na; i += blockDim.x) {
+            Atom32 r{};
+            r.lo = -INFINITY;
+            r.src = (int)i;
+            a32[a0 + i] = r;
+            Atom64 d{};
+            a64[a0 + i] = d;
+        }
         return;
     }
     if (threadIdx.x == 0) {  // exclusive offset of each element's run (serial over <= 256 entries)
@@ -327,10 +338,13 @@ __global__ void __launch_bounds__(256) k_count(const Geo* __restrict__ geo, doub
     if (threadIdx.x == 0) cnt[s] = n;
 }
 
+// Also writes the structure's entries of the structure-factor tile table:
+// (s, first reflection) of each tile of `tile` reflections, from tile_off[s].
 __global__ void __launch_bounds__(256) k_emit(const Geo* __restrict__ geo, double r2min, double r2max,
                                               float r2minf, float r2maxf, const int64_t* __restrict__ refl_off,
                                               const int* __restrict__ tcnt, const int* __restrict__ abort_flag,
-                                              double* __restrict__ q, uint32_t* __restrict__ key)
+                                              double* __restrict__ q, uint32_t* __restrict__ key, int tile,
+                                              const int* __restrict__ tile_off, int2* __restrict__ tile_tab)
 {
     pdl_enter();
     __shared__ int tmp[34];
@@ -338,6 +352,10 @@ __global__ void __launch_bounds__(256) k_emit(const Geo* __restrict__ geo, doubl
     const int s = blockIdx.x;
     const Geo g = geo[s];
     const int64_t base = refl_off[s], cap = refl_off[s + 1] - base;
+    if (tile_tab) {
+        const int nt = (int)((cap + tile - 1) / tile), t0 = tile_off[s];
+        for (int t = threadIdx.x; t < nt; t += blockDim.x) tile_tab[t0 + t] = make_int2(s, t * tile);
+    }
     if (g.status == XRD_OK && g.H >= 0 && cap > 0)
         enumerate_struct<true>(g, r2min, r2max, r2minf, r2maxf, base, cap, q, key, tmp,
                                tcnt[(int64_t)s * blockDim.x + threadIdx.x]);
@@ -349,11 +367,10 @@ __global__ void __launch_bounds__(256) k_emit(const Geo* __restrict__ geo, doubl
 // and warp-aggregated shared-memory atomics where it needs ranks.
 //  1. reflection offsets (64-bit exclusive scan of the counts), the capacity
 //     check and the per-structure status;
-//  2. the largest-first order of structures: a counting sort on the atom
-//     count, which sets the cost of a structure-factor tile;
-//  3. in that order, the tile offsets and the post-processing size-class
-//     lists (post_class; within a class the order follows the chunks).
-// The tile table itself is written by k_tiles over the whole GPU.
+//  2. in the largest-first order (k_order), each structure's first tile and
+//     the post-processing size-class lists (post_class; within a class the
+//     order follows the chunks).
+// The tile table itself is written by k_emit, one CTA per structure.
 constexpr int kOrderBins = 4096;
 constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 4;
@@ -382,15 +399,14 @@ __device__ __forceinline__ int warp_aggregated_slot(int* ctr, int key, bool acti
 __global__ void __launch_bounds__(kScanThreads) k_scan_refl(const int64_t* __restrict__ cnt, const Geo* __restrict__ geo,
                                                             const int64_t* __restrict__ atom_off, int n, int tile,
                                                             int64_t cap_refl, int64_t* __restrict__ refl_off,
-                                                            int* __restrict__ tile_off, int* __restrict__ order,
+                                                            int* __restrict__ tile_off, const int* __restrict__ order,
                                                             int* __restrict__ cls_list, int* __restrict__ abort_flag,
                                                             int64_t* __restrict__ totals, int32_t* __restrict__ status)
 {
     pdl_enter();
     __shared__ long long ws[33];
-    __shared__ __align__(16) long long buf[kScanItems * kScanThreads];  // also the order bins
+    __shared__ __align__(16) long long buf[kScanItems * kScanThreads];
     __shared__ int ccnt[kPostClasses];
-    int* bins = (int*)buf;
     const int nt = blockDim.x, tid = threadIdx.x, CH = kScanItems * nt;
     long long tot;
     // 1. reflection offsets in structure order, and the status of each structure
@@ -422,39 +438,9 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_refl(const int64_t* __res
     const long long nbad = over ? n : tot;
     if (over)
         for (int i = tid; i < n; i += nt) status[i] = XRD_ECAPACITY;
-    // 2. largest-first order: counting sort on (kOrderBins - 1 - min(atoms, kOrderBins - 1));
-    //    warp-aggregated, so structures of one bin keep their warp's order
-    for (int b = tid; b < kOrderBins; b += nt) bins[b] = 0;
-    __syncthreads();
-    for (int base = 0; base < n; base += CH) {
-        int b[kScanItems];
-#pragma unroll
-        for (int u = 0; u < kScanItems; u++) {
-            const int i = base + u * nt + tid;
-            b[u] = i < n ? order_bin(atom_off, i) : 0;
-        }
-#pragma unroll
-        for (int u = 0; u < kScanItems; u++) warp_aggregated_slot(bins, b[u], base + u * nt + tid < n);
-    }
-    __syncthreads();
-    block_excl_scan(bins, kOrderBins, (int*)ws);
-    for (int base = 0; base < n; base += CH) {
-        int b[kScanItems];
-#pragma unroll
-        for (int u = 0; u < kScanItems; u++) {
-            const int i = base + u * nt + tid;
-            b[u] = i < n ? order_bin(atom_off, i) : 0;
-        }
-#pragma unroll
-        for (int u = 0; u < kScanItems; u++) {
-            const int i = base + u * nt + tid;
-            const int slot = warp_aggregated_slot(bins, b[u], i < n);
-            if (i < n) order[slot] = i;
-        }
-    }
     if (tid < kPostClasses) ccnt[tid] = 0;
-    __syncthreads();  // order[] (global) is visible to the whole block; bins are free
-    // 3. tiles and size classes in that order
+    __syncthreads();
+    // 2. tiles and size classes in the largest-first order
     long long tcarry = 0;
     for (int base = 0; base < n; base += CH) {
         long long v[kScanItems];
@@ -474,7 +460,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_refl(const int64_t* __res
 #pragma unroll
         for (int u = 0; u < kScanItems; u++) {
             const int p = base + u * nt + tid;
-            if (p < n) tile_off[p] = (int)(tcarry + v[u]);
+            if (p < n) tile_off[sv[u]] = (int)(tcarry + v[u]);  // first tile of the structure
             if (!over && cls_list) {
                 const int k = post_class(c[u]);
                 const int slot = warp_aggregated_slot(ccnt, k, p < n);
@@ -496,34 +482,76 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_refl(const int64_t* __res
     }
 }
 
-// Tile table: (structure, first reflection of the tile within it) in the
-// largest-first order, one thread per structure.
-__global__ void __launch_bounds__(256) k_tiles(const int64_t* __restrict__ cnt, const int* __restrict__ order,
-                                               const int* __restrict__ tile_off, int n, int tile,
-                                               const int* __restrict__ abort_flag, int2* __restrict__ tile_tab)
+// Largest-first order of the structures: a counting sort on the atom count
+// (which sets the cost of a structure-factor tile), in descending order; one
+// block, warp-aggregated shared-memory atomics, so structures of one bin keep
+// the order of their warp. It depends on the input only and runs beside the
+// enumeration.
+__global__ void __launch_bounds__(kScanThreads) k_order(const int64_t* __restrict__ atom_off, int n,
+                                                        int* __restrict__ order)
 {
     pdl_enter();
-    if (*abort_flag) return;
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
-        const int s = order[p];
-        const int nt = (int)((cnt[s] + tile - 1) / tile);
-        const int t0 = tile_off[p];
-        for (int t = 0; t < nt; t++) tile_tab[t0 + t] = make_int2(s, t * tile);
+    __shared__ int bins[kOrderBins];
+    __shared__ int tmp[66];
+    const int nt = blockDim.x, tid = threadIdx.x, CH = kScanItems * nt;
+    for (int b = tid; b < kOrderBins; b += nt) bins[b] = 0;
+    __syncthreads();
+    for (int base = 0; base < n; base += CH) {
+        int b[kScanItems];
+#pragma unroll
+        for (int u = 0; u < kScanItems; u++) {
+            const int i = base + u * nt + tid;
+            b[u] = i < n ? order_bin(atom_off, i) : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < kScanItems; u++) warp_aggregated_slot(bins, b[u], base + u * nt + tid < n);
+    }
+    __syncthreads();
+    block_excl_scan(bins, kOrderBins, tmp);
+    for (int base = 0; base < n; base += CH) {
+        int b[kScanItems];
+#pragma unroll
+        for (int u = 0; u < kScanItems; u++) {
+            const int i = base + u * nt + tid;
+            b[u] = i < n ? order_bin(atom_off, i) : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < kScanItems; u++) {
+            const int i = base + u * nt + tid;
+            const int slot = warp_aggregated_slot(bins, b[u], i < n);
+            if (i < n) order[slot] = i;
+        }
     }
 }
 
-void launch_prep(const GeomArgs& a, cudaStream_t st)
+template <typename... P, typename... A>
+static void launch_k(bool pdl, void (*k)(P...), dim3 grid, dim3 block, cudaStream_t st, A... args)
 {
-    const int n = a.n_struct;
-    if (n > 0) k_prep<<<(n + 31) / 32, 32, 0, st>>>(a.lattice, n, a.rmax, a.geo);
-    launch_pdl(k_coef, 1, 256, 0, st, a.coef, a.zmax, a.coef32);
+    if (pdl) launch_pdl(k, grid, block, 0, st, args...);
+    else k<<<grid, block, 0, st>>>(static_cast<P>(args)...);
 }
 
-void launch_atoms(const GeomArgs& a, cudaStream_t st)
+void launch_prep(const GeomArgs& a, cudaStream_t st, bool pdl)
+{
+    const int n = a.n_struct;
+    if (n > 0) launch_k(pdl, k_prep, (n + 31) / 32, 32, st, a.lattice, n, a.rmax, a.geo);
+}
+
+void launch_coef(const GeomArgs& a, cudaStream_t st, bool pdl)
+{
+    launch_k(pdl, k_coef, 1, 256, st, a.coef, a.zmax, a.coef32);
+}
+
+void launch_atoms(const GeomArgs& a, cudaStream_t st, bool pdl)
 {
     if (a.n_struct > 0)
-        launch_pdl(k_atoms, a.n_struct, 128, 0, st, a.atom_off, a.n_atoms, a.frac, a.Z, a.occ, a.B, a.zmax, a.geo,
-                   a.atom32, a.atom64);
+        launch_k(pdl, k_atoms, a.n_struct, 128, st, a.atom_off, a.n_atoms, a.frac, a.Z, a.occ, a.B, a.zmax, a.geo,
+                 a.atoms_set_geo, a.atom_bad, a.atom32, a.atom64);
+}
+
+void launch_order(const GeomArgs& a, cudaStream_t st, bool pdl)
+{
+    if (a.n_struct > 0) launch_k(pdl, k_order, 1, kScanThreads, st, a.atom_off, a.n_struct, a.order);
 }
 
 void launch_count_only(const GeomArgs& a, cudaStream_t st)
@@ -531,30 +559,28 @@ void launch_count_only(const GeomArgs& a, cudaStream_t st)
     const int n = a.n_struct;
     if (n <= 0) return;
     k_prep<<<(n + 31) / 32, 32, 0, st>>>(a.lattice, n, a.rmax, a.geo);
-    launch_pdl(k_count, n, 256, 0, st, a.geo, a.r2min, a.r2max, (float)a.r2min, (float)a.r2max, a.refl_cnt, (int*)nullptr);
+    launch_pdl(k_count, n, 256, 0, st, a.geo, a.r2min, a.r2max, (float)a.r2min, (float)a.r2max, a.refl_cnt,
+               (int*)nullptr);
 }
 
-void launch_count(const GeomArgs& a, cudaStream_t st)
+void launch_count(const GeomArgs& a, cudaStream_t st, bool pdl)
 {
     if (a.n_struct > 0)
-        launch_pdl(k_count, a.n_struct, 256, 0, st, a.geo, a.r2min, a.r2max, (float)a.r2min, (float)a.r2max,
-                   a.refl_cnt, a.tcnt);
+        launch_k(pdl, k_count, a.n_struct, 256, st, a.geo, a.r2min, a.r2max, (float)a.r2min, (float)a.r2max,
+                 a.refl_cnt, a.tcnt);
 }
 
-void launch_scan_refl(const GeomArgs& a, cudaStream_t st)
+void launch_scan_refl(const GeomArgs& a, cudaStream_t st, bool pdl)
 {
-    launch_pdl(k_scan_refl, 1, 1024, 0, st, a.refl_cnt, a.geo, a.atom_off, a.n_struct, a.tile, a.cap_refl,
-               a.refl_off, a.tile_off, a.order, a.cls_list, a.abort_flag, a.totals, a.status);
-    if (a.n_struct > 0 && a.tile_tab)
-        launch_pdl(k_tiles, (a.n_struct + 255) / 256, 256, 0, st, a.refl_cnt, a.order, a.tile_off, a.n_struct,
-                   a.tile, a.abort_flag, a.tile_tab);
+    launch_k(pdl, k_scan_refl, 1, kScanThreads, st, a.refl_cnt, a.geo, a.atom_off, a.n_struct, a.tile, a.cap_refl,
+             a.refl_off, a.tile_off, (const int*)a.order, a.cls_list, a.abort_flag, a.totals, a.status);
 }
 
-void launch_emit(const GeomArgs& a, cudaStream_t st)
+void launch_emit(const GeomArgs& a, cudaStream_t st, bool pdl)
 {
     if (a.n_struct > 0)
-        launch_pdl(k_emit, a.n_struct, 256, 0, st, a.geo, a.r2min, a.r2max, (float)a.r2min, (float)a.r2max,
-                   a.refl_off, a.tcnt, a.abort_flag, a.q, a.key);
+        launch_k(pdl, k_emit, a.n_struct, 256, st, a.geo, a.r2min, a.r2max, (float)a.r2min, (float)a.r2max,
+                 a.refl_off, a.tcnt, a.abort_flag, a.q, a.key, a.tile, (const int*)a.tile_off, a.tile_tab);
 }
 
 }  // namespace xrd

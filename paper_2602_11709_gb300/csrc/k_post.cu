@@ -107,6 +107,72 @@ __device__ __forceinline__ bool before(double qa, uint32_t ka, double qb, uint32
     return a < b || (a == b && ka > kb);
 }
 
+// The common case of a structure whose sorted reflections are all farther apart
+// than the tolerance: every reflection is a peak of one family (g and -g, so
+// multiplicity 2), and the merge runs, the peak-start scan and the family
+// search are skipped. Same arithmetic and outputs as the general path.
+template <typename PermT, bool FI>
+__device__ void post_singles(const PostArgs& a, int s, int64_t base, int n, const double* q, const uint32_t* key,
+                             const float* Is, const PermT* perm, uint8_t* flag, int* pst, double* psum, int* tmp,
+                             double* dtmp)
+{
+    const int tid = threadIdx.x, nt = blockDim.x;
+    double imax = 0.0, inv_imax = 0.0;
+    float imaxf = 0.f, inv_imaxf = 0.f;
+    unsigned long long lmax = 0;
+    for (int p = tid; p < n; p += nt) {
+        if (FI) {
+            const float v = 2.f * Is[perm[p]];
+            ((float*)psum)[p] = v;
+            lmax = max(lmax, (unsigned long long)__float_as_uint(v));
+        } else {
+            const double v = 0.0 + 2.0 * a.I[base + perm[p]];
+            psum[p] = v;
+            lmax = max(lmax, dbits(v));
+        }
+    }
+    const unsigned long long m = block_max_u64(lmax, (unsigned long long*)dtmp);
+    if (FI) {
+        imaxf = __uint_as_float((uint32_t)m);
+        inv_imaxf = imaxf > 0.f ? 1.f / imaxf : 0.f;
+    } else {
+        imax = __longlong_as_double((long long)m);
+        inv_imax = imax > 0.0 ? 1.0 / imax : 0.0;
+    }
+    const uint32_t thrf = __float_as_uint((float)a.cutoff * imaxf);
+    const unsigned long long thr = dbits(a.cutoff * imax);
+    for (int p = tid; p < n; p += nt) {
+        const bool keep = a.cutoff == 0.0 || (FI ? __float_as_uint(((float*)psum)[p]) > thrf : dbits(psum[p]) > thr);
+        flag[p] = keep;
+        pst[p] = keep;
+    }
+    __syncthreads();
+    const int nk = block_excl_scan(pst, n, tmp);
+    for (int p = tid; p < n; p += nt) {
+        if (!flag[p]) continue;
+        const int64_t o = base + pst[p];
+        const int v = perm[p];
+        a.st_q[o] = q[v];
+        if (FI) {
+            const float ps = ((const float*)psum)[p];
+            a.st_I[o] = f2d_fast((a.scaled && imaxf > 0.f) ? (ps == imaxf ? 100.f : 100.f * (ps * inv_imaxf)) : ps);
+        } else {
+            const double ps = psum[p];
+            a.st_I[o] = (a.scaled && imax > 0.0) ? (ps == imax ? 100.0 : 100.0 * (ps * inv_imax)) : ps;
+        }
+        a.st_foff[o] = pst[p];  // one family per kept peak
+        const uint32_t rep = key[v];
+        a.st_hkl[3 * o] = hkl_h(rep);
+        a.st_hkl[3 * o + 1] = hkl_k(rep);
+        a.st_hkl[3 * o + 2] = hkl_l(rep);
+        a.st_mult[o] = 2;
+    }
+    if (tid == 0) {
+        a.npk[s] = nk;
+        a.nfm[s] = nk;
+    }
+}
+
 // FI: intensities are FP32 (the FP32 structure-factor variants) and peak sums,
 // cutoff and scaling run in FP32; otherwise FP64 throughout.
 // Is: the FP32 intensities of the structure (shared or global memory).
@@ -156,8 +222,16 @@ __device__ void post_structure(const PostArgs& a, int s, int64_t base, int n, co
     }
     __syncthreads();
     // ---- anchor merge: definite starts, then one thread per run ----
-    for (int i = tid; i < n; i += nt) flag[i] = (i == 0) || !tt_close(q[perm[i - 1]], q[perm[i]], l2, lh, ttol);
-    __syncthreads();
+    int close_pair = 0;
+    for (int i = tid; i < n; i += nt) {
+        const bool start = (i == 0) || !tt_close(q[perm[i - 1]], q[perm[i]], l2, lh, ttol);
+        flag[i] = start;
+        close_pair |= !start;
+    }
+    if (!__syncthreads_or(close_pair)) {  // no two reflections within the tolerance: every one is a peak
+        post_singles<PermT, FI>(a, s, base, n, q, key, Is, perm, flag, pst, psum, tmp, dtmp);
+        return;
+    }
     for (int i = tid; i < n; i += nt) {
         if (!flag[i]) continue;
         double qa = q[perm[i]];
@@ -311,6 +385,17 @@ __global__ void __launch_bounds__(NT) k_post(const PostArgs a, int cls)
         const int li = claim;
         if (li >= cnt) break;
         const int s = list[li];
+        if (a.atom_bad && a.atom_bad[s]) {  // an invalid atom: no peaks, the structure reports XRD_EINVAL
+            if (threadIdx.x == 0) {
+                a.npk[s] = 0;
+                a.nfm[s] = 0;
+                if (a.status[s] == XRD_OK) {
+                    a.status[s] = XRD_EINVAL;
+                    atomicAdd((unsigned long long*)&a.totals[3], 1ull);
+                }
+            }
+            continue;
+        }
         const int64_t base = a.refl_off[s];
         const int n = (int)(a.refl_off[s + 1] - base);
         if (n == 0) {

@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(32 * WARPS, PREC == XRD_FP64 ? 1 : ((PREC == X
 }
 
 template <int PREC, bool GRAD, int RB, int WARPS>
-static void launch_sf_shape(const SfArgs& a, cudaStream_t st)
+static void launch_sf_shape(const SfArgs& a, cudaStream_t st, bool pdl)
 {
     // persistent grid: as many CTAs as fit on the SMs at once (cached per device and zmax)
     static int cache_per_sm[64] = {}, cache_zmax[64] = {};
@@ -240,36 +240,37 @@ static void launch_sf_shape(const SfArgs& a, cudaStream_t st)
             per_sm = 4;
         if (dev >= 0 && dev < 64) { cache_per_sm[dev] = per_sm; cache_zmax[dev] = a.zmax; }
     }
-    launch_pdl(k_sf<PREC, GRAD, RB, WARPS>, a.grid * per_sm, 32 * WARPS, smem, st, a);
+    if (pdl) launch_pdl(k_sf<PREC, GRAD, RB, WARPS>, a.grid * per_sm, 32 * WARPS, smem, st, a);
+    else k_sf<PREC, GRAD, RB, WARPS><<<a.grid * per_sm, 32 * WARPS, smem, st>>>(a);
 }
 
 template <int PREC, bool GRAD>
-static void launch_sf_prec(const SfArgs& a, cudaStream_t st)
+static void launch_sf_prec(const SfArgs& a, cudaStream_t st, bool pdl)
 {
-    if (a.rb == 2) launch_sf_shape<PREC, GRAD, 2, 2>(a, st);
-    else launch_sf_shape<PREC, GRAD, 4, 2>(a, st);
+    if (a.rb == 2) launch_sf_shape<PREC, GRAD, 2, 2>(a, st, pdl);
+    else launch_sf_shape<PREC, GRAD, 4, 2>(a, st, pdl);
 }
 
 // a.grid = number of SMs; a.rb, a.warps = launch shape (tile = 32 rb reflections)
-void launch_sf(const SfArgs& a, cudaStream_t st)
+void launch_sf(const SfArgs& a, cudaStream_t st, bool pdl)
 {
     if (a.n_struct <= 0) return;
     if (a.Fx) {  // gradient path: FP32 with the integer phase
-        launch_sf_prec<XRD_FP32_PHASEFIX, true>(a, st);
+        launch_sf_prec<XRD_FP32_PHASEFIX, true>(a, st, pdl);
         return;
     }
     switch (a.precision) {
-    case XRD_FP64: launch_sf_prec<XRD_FP64, false>(a, st); break;
-    case XRD_FP32_PHASE64: launch_sf_prec<XRD_FP32_PHASE64, false>(a, st); break;
+    case XRD_FP64: launch_sf_prec<XRD_FP64, false>(a, st, pdl); break;
+    case XRD_FP32_PHASE64: launch_sf_prec<XRD_FP32_PHASE64, false>(a, st, pdl); break;
     default:
         if (a.rb == 2) {
-            if (a.warps == 1) launch_sf_shape<XRD_FP32_PHASEFIX, false, 2, 1>(a, st);
-            else if (a.warps == 4) launch_sf_shape<XRD_FP32_PHASEFIX, false, 2, 4>(a, st);
-            else launch_sf_shape<XRD_FP32_PHASEFIX, false, 2, 2>(a, st);
+            if (a.warps == 1) launch_sf_shape<XRD_FP32_PHASEFIX, false, 2, 1>(a, st, pdl);
+            else if (a.warps == 4) launch_sf_shape<XRD_FP32_PHASEFIX, false, 2, 4>(a, st, pdl);
+            else launch_sf_shape<XRD_FP32_PHASEFIX, false, 2, 2>(a, st, pdl);
         } else {
-            if (a.warps == 1) launch_sf_shape<XRD_FP32_PHASEFIX, false, 4, 1>(a, st);
-            else if (a.warps == 4) launch_sf_shape<XRD_FP32_PHASEFIX, false, 4, 4>(a, st);
-            else launch_sf_shape<XRD_FP32_PHASEFIX, false, 4, 2>(a, st);
+            if (a.warps == 1) launch_sf_shape<XRD_FP32_PHASEFIX, false, 4, 1>(a, st, pdl);
+            else if (a.warps == 4) launch_sf_shape<XRD_FP32_PHASEFIX, false, 4, 4>(a, st, pdl);
+            else launch_sf_shape<XRD_FP32_PHASEFIX, false, 4, 2>(a, st, pdl);
         }
         break;
     }

@@ -27,9 +27,11 @@ struct GeomArgs {
     int64_t* refl_cnt;
     int* tcnt;       // [n_struct][256] per-thread reflection counts of the counting pass
     int64_t* refl_off;
-    int* tile_off;
-    int* order;
+    int* tile_off;   // [n_struct + 1] first structure-factor tile of each structure; [n_struct] = tiles
+    int* order;      // [n_struct] structures by atom count, largest first
     int2* tile_tab;  // [tiles] (structure, first reflection) of each structure-factor tile
+    int* atom_bad;   // [n_struct] 1 where an atom of the structure is invalid
+    int atoms_set_geo;  // k_atoms also marks such structures invalid in geo (only when it runs before k_count)
     int* cls_list;   // [kPostClasses][n_struct] post-processing size classes (nullptr: not built)
     int* abort_flag; // flags[0]; flags[1] output abort, flags[2] tile queue, flags[4..9] class counts,
                      // flags[10..15] class work counters
@@ -45,7 +47,7 @@ struct SfArgs {
     double lambda;
     const int64_t* atom_off;
     const int64_t* refl_off;
-    const int* tile_off;  // [n_struct + 1] exclusive scan of tiles in largest-first order
+    const int* tile_off;  // [n_struct + 1]: [n_struct] is the number of tiles
     const int2* tile_tab; // [tiles] (structure, first reflection within it), largest-first order
     int* tile_counter;    // work-queue head, zeroed by the caller
     const int* abort_flag;
@@ -92,6 +94,10 @@ struct PostArgs {
     int* st_mult;
     int64_t* npk;  // kept peaks per structure
     int64_t* nfm;  // families of kept peaks per structure
+    // structures with an invalid atom: no peaks, status XRD_EINVAL (counted in totals[3])
+    const int* atom_bad;
+    int32_t* status;
+    int64_t* totals;
 };
 
 struct CompactArgs {
@@ -142,13 +148,17 @@ struct GradArgs {
     float* d_lat;
 };
 
-void launch_prep(const GeomArgs& a, cudaStream_t st);
-void launch_atoms(const GeomArgs& a, cudaStream_t st);
-void launch_count(const GeomArgs& a, cudaStream_t st);
+// pdl: launch as a programmatic dependent of the previous kernel on st (only
+// when that kernel directly precedes it on the stream)
+void launch_prep(const GeomArgs& a, cudaStream_t st, bool pdl);
+void launch_coef(const GeomArgs& a, cudaStream_t st, bool pdl);
+void launch_atoms(const GeomArgs& a, cudaStream_t st, bool pdl);
+void launch_order(const GeomArgs& a, cudaStream_t st, bool pdl);
+void launch_count(const GeomArgs& a, cudaStream_t st, bool pdl);
 void launch_count_only(const GeomArgs& a, cudaStream_t st);
-void launch_scan_refl(const GeomArgs& a, cudaStream_t st);
-void launch_emit(const GeomArgs& a, cudaStream_t st);
-void launch_sf(const SfArgs& a, cudaStream_t st);
+void launch_scan_refl(const GeomArgs& a, cudaStream_t st, bool pdl);
+void launch_emit(const GeomArgs& a, cudaStream_t st, bool pdl);
+void launch_sf(const SfArgs& a, cudaStream_t st, bool pdl);
 size_t post_smem_bytes(int cap);
 void launch_post(const PostArgs& a, const cudaStream_t* st);  // st[kPostClasses]
 void launch_compact(const CompactArgs& a, cudaStream_t st);

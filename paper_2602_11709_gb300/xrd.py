@@ -19,7 +19,7 @@ XRD_OK, XRD_EINVAL, XRD_ECAPACITY, XRD_ECUDA, XRD_ETIMEOUT = 0, 1, 2, 3, 4
 XRD_FP64, XRD_FP32_PHASE64, XRD_FP32_PHASEFIX = 0, 1, 2
 PRECISIONS = {"fp64": XRD_FP64, "fp32_phase64": XRD_FP32_PHASE64, "fp32_phasefix": XRD_FP32_PHASEFIX}
 STAGES = ["prep", "atoms", "count", "scan", "emit", "structure_factor", "post", "compact"]
-# kernels xrd_pattern_batch launches per call: prep, coef, atoms, count, scan, tile table, emit,
+# kernels xrd_pattern_batch launches per call: order, coef, atoms (a side stream), prep, count, scan, emit,
 # structure factor, post (six size classes), output scan, compaction
 LAUNCHES_PER_BATCH = 16
 
