@@ -271,6 +271,93 @@ class HostPattern:
                 "hkl": self.hkl[:nfm].numpy(), "mult": self.mult[:nfm].numpy()}
 
 
+class PatternPipeline:
+    """Patterns of a stream of batches with the same sizes, two batches in flight.
+
+    submit(host_arrays) copies one batch's inputs from pinned host memory to the
+    device, queues xrd_pattern_batch and the copies of the result sizes, and
+    returns the results of the previous submission (or None): the host waits
+    only for that batch's sizes, then queues its output copies on a second
+    stream, so a batch's device-to-host copy overlaps the next batch's work.
+    Results are numpy views of pinned buffers, valid until the same buffer set
+    is used again (two submissions later). flush() returns the last results.
+    """
+
+    def __init__(self, handle: "Handle", host_batch, opts: xrd_opts, sizes, depth: int = 2, device: int = 0):
+        torch = _torch()
+        dev = "cuda:%d" % device
+        self.h = handle
+        self.opts = opts
+        self.depth = depth
+        self.compute = torch.cuda.Stream(device=device)
+        self.copy = torch.cuda.Stream(device=device)
+        self.db = [DeviceBatch.from_host(host_batch, dev) for _ in range(depth)]
+        self.out = [PatternBuffers(host_batch.n_struct, sizes.n_refl, dev) for _ in range(depth)]
+        self.ws = [workspace(sizes.ws_bytes, dev) for _ in range(depth)]
+        self.hp = [HostPattern(host_batch.n_struct, sizes.n_refl) for _ in range(depth)]
+        self.sizes_ready = [torch.cuda.Event() for _ in range(depth)]
+        self.copied = [torch.cuda.Event() for _ in range(depth)]
+        self.pending = None  # buffer set whose output copies are not queued yet
+        self.k = 0
+        self.bytes_in = 0
+        self.bytes_out = 0
+
+    def _queue_outputs(self, j):
+        torch = _torch()
+        hp, out = self.hp[j], self.out[j]
+        self.sizes_ready[j].synchronize()
+        npk, nfm = int(hp.totals[1]), int(hp.totals[2])
+        n = hp.n_struct
+        with torch.cuda.stream(self.copy):
+            self.copy.wait_event(self.sizes_ready[j])
+            nbytes = 0
+            for dst, src, m in ((hp.two_theta, out.two_theta, npk), (hp.intensity, out.intensity, npk),
+                                (hp.d_hkl, out.d_hkl, npk), (hp.fam_off, out.fam_off, npk + 1),
+                                (hp.hkl, out.hkl, nfm), (hp.mult, out.mult, nfm)):
+                if m > 0:
+                    dst[:m].copy_(src[:m], non_blocking=True)
+                    nbytes += dst[:m].numel() * dst.element_size()
+            self.copied[j].record(self.copy)
+        self.bytes_out += nbytes + 8 * (n + 1) + 4 * n + 32
+        return j, npk, nfm
+
+    def _results(self, j, npk, nfm):
+        hp = self.hp[j]
+        self.copied[j].synchronize()
+        n = hp.n_struct
+        return {"totals": hp.totals.numpy(), "peak_off": hp.peak_off.numpy(), "status": hp.status[:n].numpy(),
+                "two_theta": hp.two_theta[:npk].numpy(), "intensity": hp.intensity[:npk].numpy(),
+                "d_hkl": hp.d_hkl[:npk].numpy(), "fam_off": hp.fam_off[:npk + 1].numpy(),
+                "hkl": hp.hkl[:nfm].numpy(), "mult": hp.mult[:nfm].numpy()}
+
+    def submit(self, host_arrays: dict):
+        """host_arrays: pinned tensors lattice, atom_off, frac, Z, occ, B, coef of one batch."""
+        torch = _torch()
+        j = self.k % self.depth
+        self.k += 1
+        db, out, hp = self.db[j], self.out[j], self.hp[j]
+        with torch.cuda.stream(self.compute):
+            self.compute.wait_event(self.copied[j])  # the previous use of this buffer set is copied out
+            for name, t in host_arrays.items():
+                getattr(db, name).copy_(t, non_blocking=True)
+                self.bytes_in += t.numel() * t.element_size()
+            self.h.pattern_batch(db, self.opts, out, self.ws[j], stream=self.compute)
+            hp.totals.copy_(out.totals, non_blocking=True)
+            hp.peak_off.copy_(out.peak_off, non_blocking=True)
+            hp.status[:hp.n_struct].copy_(out.status[:hp.n_struct], non_blocking=True)
+            self.sizes_ready[j].record(self.compute)
+        prev, self.pending = self.pending, j
+        if prev is None:
+            return None
+        return self._results(*self._queue_outputs(prev))
+
+    def flush(self):
+        if self.pending is None:
+            return None
+        j, self.pending = self.pending, None
+        return self._results(*self._queue_outputs(j))
+
+
 class Handle:
     """An xrd_handle bound to one CUDA device."""
 

@@ -165,3 +165,43 @@ def test_autotune_then_graph_on_another_stream(gpu_lib):
         h.set_profiling(0)
     finally:
         h.close()
+
+
+def test_pattern_pipeline_matches_single_calls(gpu_lib):
+    """Two batches in flight give, for every submission, what a single call gives."""
+    import torch
+    xrd = gpu_lib
+    base, o = synth.small(seed=21, n=48)
+    rng = np.random.default_rng(5)
+    batches = []
+    for k in range(4):  # same cells and atom counts (so the same sizes), other coordinates and B
+        b = base.subset(np.arange(base.n_struct))
+        b.frac = np.mod(b.frac + rng.uniform(0, 1, size=3), 1.0)
+        b.B = b.B * (1.0 + 0.1 * k)
+        batches.append(b)
+    h = xrd.Handle(0)
+    try:
+        co = xrd.make_opts(o, "fp32_phasefix")
+        sz = h.query_sizes(xrd.DeviceBatch.from_host(base), co)
+        big = 0
+        refs = []
+        for b in batches:
+            db = xrd.DeviceBatch.from_host(b)
+            out = xrd.PatternBuffers(db.n_struct, sz.n_refl)
+            h.pattern_batch(db, co, out, xrd.workspace(sz.ws_bytes))
+            refs.append({k: np.array(v) for k, v in xrd.HostPattern(db.n_struct, sz.n_refl).download(out).items()})
+        pp = xrd.PatternPipeline(h, batches[big], co, sz)
+        got = []
+        for b in batches:
+            host = {k: torch.from_numpy(np.ascontiguousarray(getattr(b, k))).pin_memory()
+                    for k in ("lattice", "atom_off", "frac", "Z", "occ", "B", "coef")}
+            r = pp.submit(host)
+            if r is not None:
+                got.append({k: np.array(v) for k, v in r.items()})
+        got.append({k: np.array(v) for k, v in pp.flush().items()})
+        assert len(got) == len(refs)
+        for g, r in zip(got, refs):
+            for k in r:
+                assert np.array_equal(g[k], r[k]), k
+    finally:
+        h.close()
