@@ -73,11 +73,15 @@ def reduce_over_ranks(terms, structures, seconds, world, device="cpu"):
 
 # DRAM bytes (read + write) of one k_sf launch on the small workload, from one ncu capture of
 # the kernel as it stands (dram__bytes_read.sum + dram__bytes_write.sum); other workloads: not captured
-SF_TRAFFIC_BYTES = {"small": 13556224}
+SF_TRAFFIC_BYTES = {}
 # SFU issue rates per SM per clock measured on this GB300 (MUFU.SIN/COS 16, MUFU.EX2 32) and the
 # maximum SM clock; the structure-factor roofline of a batch follows from its mix of operations.
 MUFU_SINCOS_PER_CLK = 16.0
 MUFU_EX2_PER_CLK = 32.0
+# FP32 FMA-pipe operations per term of the integer-phase loop (Debye-Waller argument, weight, two
+# accumulations, the four-operation rotation to the next l) and the pipe's rate per SM per clock
+FMA_OPS_PER_TERM = 8.0
+FMA_PER_CLK = 128.0
 SM_MAX_MHZ = 2070.0
 
 
@@ -240,8 +244,8 @@ def run_ours(args):
     assert int(half.sum()) == int(sz.n_refl)
     terms_full = int((2 * half * counts).sum())
     terms_eval = int((half * counts).sum())
-    sfu_cycles = float((half * (counts * (2.0 / MUFU_SINCOS_PER_CLK + 1.0 / MUFU_EX2_PER_CLK) +
-                                species * (4.0 / MUFU_EX2_PER_CLK))).sum())
+    # per Friedel-unique reflection and element run: f(s), four exp2
+    f_cycles = float((half * species).sum()) * 4.0 / MUFU_EX2_PER_CLK
 
     # launch-shape tuning of the structure-factor kernel, then one CUDA graph for the whole step
     tuned = h.autotune(db, co, out, ws) if not args.no_tune else None
@@ -293,6 +297,12 @@ def run_ours(args):
     value = total_terms * args.steps / total_s
     pps = total_structs * args.steps / total_s
     sf_avg = float(np.mean(sf_ms)) / 1e3
+    # the kernel's own work counts: one sin/cos pair per run of consecutive reflections and atom,
+    # one exp2 (Debye-Waller) per term
+    w_terms, w_seeds, _ = h.work_counts(db, ws)
+    assert w_terms == terms_eval, (w_terms, terms_eval)
+    sfu_cycles = w_seeds * 2.0 / MUFU_SINCOS_PER_CLK + terms_eval / MUFU_EX2_PER_CLK + f_cycles
+    fma_cycles = terms_eval * FMA_OPS_PER_TERM / FMA_PER_CLK
     sfu_floor_s = sfu_cycles / (152.0 * SM_MAX_MHZ * 1e6)
     peak_gterms = terms_eval / sfu_floor_s / 1e9
     achieved_gterms = terms_eval / sf_avg / 1e9
@@ -357,12 +367,15 @@ def run_ours(args):
                        "reflections_friedel_unique": int(sz.n_refl), "l2": "flushed between steps (256 MiB write)",
                        "parallelism": "one structure shard per GPU" if world > 1 else "1 GPU",
                        "launch": "CUDA graph" if graph is not None else "eager",
-                       "sf_shape": {"tile": tuned[0], "warps": tuned[1]} if tuned else "default"},
+                       "sf_shape": {"tile": tuned[0], "warps": tuned[1], "runs_in_l": tuned[2]} if tuned else "default"},
             "patterns_per_s": pps,
             "roofline": {"bound": "alu", "unit": "Gterm/s", "achieved": achieved_gterms, "peak": peak_gterms,
                          "frac": achieved_gterms / peak_gterms,
                          "traffic": SF_TRAFFIC_BYTES.get(args.workload), "traffic_unit": "bytes per launch",
-                         "kernel": "k_sf", "peak_basis": "SFU: sin+cos at 16/clk/SM, exp2 at 32/clk/SM, "
+                         "fma_floor_frac": (fma_cycles / (152.0 * SM_MAX_MHZ * 1e6)) / sf_avg,
+                         "phase_seeds_per_term": w_seeds / max(terms_eval, 1),
+                         "kernel": "k_sf", "peak_basis": "SFU: sin+cos at 16/clk/SM per phase seed (one per run of "
+                                                         "consecutive l and atom), exp2 at 32/clk/SM, "
                                                          "152 SMs, 2070 MHz; Friedel-unique terms"},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_terms / e2e_s, "unit": "terms/s", "h2d_bytes_per_step": int(h2d),

@@ -187,19 +187,36 @@ int xrd_pattern_grad(xrd_handle* h, const xrd_batch* batch, const xrd_opts* opts
  * the engine: thousands of uneven structures in one persistent launch). Runs
  * xrd_pattern_batch (same arguments) with each shape -- 2 or 4 reflections per
  * lane (warp tiles of 64 or 128 reflections) and, for XRD_FP32_PHASEFIX, 1, 2
- * or 4 warps per CTA -- times the structure-factor stage with CUDA events,
- * synchronising `stream`, and keeps the fastest shape in the handle; later calls
- * with opts.tile = -1 use it. Writes the chosen tile and warps if the pointers
- * are not NULL. Returns after `stream` has been synchronised (every tuning
- * call has finished). Not capturable.
+ * or 4 warps per CTA, and lanes taking either 4 strided reflections or one run
+ * of up to 4 reflections consecutive in l (one sin/cos pair per run and atom,
+ * the phase factor then rotated from l to l + 1; the enumeration builds the
+ * runs) -- times the stages a shape changes (count, scan, emit, structure
+ * factor; the minimum of four calls) with CUDA events, synchronising `stream`,
+ * and keeps the fastest shape in the handle; later calls with opts.tile = -1 use
+ * it. Writes the chosen tile, warps and runs (0 or 1) if the pointers are not
+ * NULL. Returns after `stream` has been synchronised (every tuning call has
+ * finished). Not capturable.
  */
 int xrd_autotune(xrd_handle* h, const xrd_batch* batch, const xrd_opts* opts, const xrd_pattern* out,
                  void* workspace, size_t ws_bytes, void* stream /* cudaStream_t */, int32_t* best_tile,
-                 int32_t* best_warps);
+                 int32_t* best_warps, int32_t* best_runs);
+
+/*
+ * Work of the structure-factor stage of the last xrd_pattern_batch call on
+ * this workspace (same batch): counts[0] = terms to evaluate (Friedel-unique
+ * reflection x atom), counts[1] = phase-factor seeds (one sin/cos pair per term
+ * with strided tiles, per run and atom with runs consecutive in l), counts[2] =
+ * structure-factor tiles. Host array of 3. Reduces the workspace's per-structure counts on
+ * `stream` (one small kernel) and synchronises it. These counts set the SFU time floor of the
+ * batch (the paper has no counterpart; it is for the roofline of the kernel).
+ */
+int xrd_work_counts(xrd_handle* h, const xrd_batch* batch, const void* workspace, void* stream /* cudaStream_t */,
+                    int64_t* counts);
 
 /* Set the structure-factor launch shape directly (tile 64 or 128 reflections per
- * warp, 1, 2 or 4 warps per CTA; warps apply to XRD_FP32_PHASEFIX). */
-int xrd_set_sf_shape(xrd_handle* h, int tile, int warps);
+ * warp, 1, 2 or 4 warps per CTA; warps apply to XRD_FP32_PHASEFIX; runs = 1,
+ * with tile 128 and XRD_FP32_PHASEFIX only, makes lanes take runs consecutive in l). */
+int xrd_set_sf_shape(xrd_handle* h, int tile, int warps, int runs);
 
 /*
  * CUDA graph of one xrd_pattern_batch call with exactly these arguments (the

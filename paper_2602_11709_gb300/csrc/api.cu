@@ -19,17 +19,23 @@ struct xrd_handle {
     size_t qbuf_bytes = 0;
     const xrd::TTab* ttab = nullptr;  // 2-theta table on the handle's device
     int sf_rb = 4, sf_warps = 2;        // structure-factor launch shape (xrd_autotune)
+    int sf_runs = 0;                    // lanes take runs consecutive in l (integer phase only)
     // side streams for the concurrent post-processing size classes (fork/join by events)
     cudaStream_t side[xrd::kPostClasses - 1] = {};
     cudaEvent_t fork = nullptr, join[xrd::kPostClasses - 1] = {};
     // the input-only front (coefficients, atom packing, largest-first order) runs on side[0]
     // beside the enumeration: forked by front, joined by order_done and atoms_done
     cudaEvent_t front = nullptr, order_done = nullptr, atoms_done = nullptr;
+    unsigned long long* wbuf = nullptr;  // device [3]: xrd_work_counts result
 };
 
 namespace {
 
-constexpr int kTileMin = 64;    // smallest structure-factor warp tile (32 lanes x 2 reflections)
+constexpr int kRunsPerTileHost = xrd::kRunsPerTile;  // structure-factor tile: 32 runs (one per lane)
+// flags area, zeroed at the start of every call: 16 ints (see GeomArgs::abort_flag), then the
+// structure-factor work counters (3 x 64 bit) at byte kWorkOffset
+constexpr int kFlagBytes = 128;
+constexpr int kWorkOffset = 64;
 constexpr int kPostCap = 2048;  // reflections per structure kept in shared memory by k_post
 constexpr int kStages = 8;
 constexpr int kSfStage = 5;  // index of the structure-factor stage
@@ -64,9 +70,9 @@ size_t al(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Byte offsets of every array in the caller's workspace.
 struct Layout {
-    size_t geo, refl_cnt, tcnt, refl_off, tile_off, order, atom_bad, cls_list, tile_tab, npk, nfm, fam_soff, flags,
-        coef32, atom32, atom64;
-    size_t q, key, I, g_perm, g_bkt, g_flag, g_pstart, g_psum, g_fcnt;
+    size_t geo, refl_cnt, run_cnt, tcnt, refl_off, tile_off, order, atom_bad, cls_list, tile_tab, npk, nfm, fam_soff,
+        flags, coef32, atom32, atom64, astep;
+    size_t q, key, runs, I, g_perm, g_bkt, g_flag, g_pstart, g_psum, g_fcnt;
     size_t st_q, st_I, st_foff, st_hkl, st_mult;
     size_t total;
 };
@@ -78,7 +84,8 @@ Layout layout(int64_t n, int64_t natoms, int zmax, int64_t R)
     auto take = [&](size_t bytes) { const size_t at = o; o += al(bytes); return at; };
     L.geo = take(sizeof(xrd::Geo) * n);
     L.refl_cnt = take(8 * n);
-    L.tcnt = take(4 * 256 * n);
+    L.run_cnt = take(8 * n);
+    L.tcnt = take(4 * 2 * 256 * n);
     L.refl_off = take(8 * (n + 1));
     L.tile_off = take(4 * (n + 1));
     L.order = take(4 * n);
@@ -87,13 +94,15 @@ Layout layout(int64_t n, int64_t natoms, int zmax, int64_t R)
     L.npk = take(8 * n);
     L.nfm = take(8 * n);
     L.fam_soff = take(8 * (n + 1));
-    L.flags = take(64);
+    L.flags = take(kFlagBytes);
     L.coef32 = take(sizeof(xrd::Coef32) * (zmax + 1));
     L.atom32 = take(sizeof(xrd::Atom32) * natoms);
     L.atom64 = take(sizeof(xrd::Atom64) * natoms);
-    L.tile_tab = take(8 * (R / kTileMin + n + 1));
+    L.astep = take(8 * natoms);
+    L.tile_tab = take(8 * (R / kRunsPerTileHost + n + 1));
     L.q = take(8 * R);
     L.key = take(4 * R);
+    L.runs = take(4 * R);
     L.I = take(8 * R);
     L.g_perm = take(4 * R);
     L.g_bkt = take(4 * (R + n));
@@ -113,8 +122,9 @@ Layout layout(int64_t n, int64_t natoms, int zmax, int64_t R)
 // Workspace of the broadened-pattern / gradient path: the geometry prefix of
 // the pattern layout plus the per-reflection state kept for the backward pass.
 struct LayoutG {
-    size_t geo, refl_cnt, tcnt, refl_off, tile_off, order, atom_bad, tile_tab, flags, coef32, atom32, atom64;
-    size_t q, key, Fx, Ig, tb, td, perm, U, V;
+    size_t geo, refl_cnt, run_cnt, tcnt, refl_off, tile_off, order, atom_bad, tile_tab, flags, coef32, atom32, atom64,
+        astep;
+    size_t q, key, runs, Fx, Ig, tb, td, perm, U, V;
     size_t total;
 };
 
@@ -125,18 +135,21 @@ LayoutG layout_grad(int64_t n, int64_t natoms, int zmax, int64_t R)
     auto take = [&](size_t bytes) { const size_t at = o; o += al(bytes); return at; };
     L.geo = take(sizeof(xrd::Geo) * n);
     L.refl_cnt = take(8 * n);
-    L.tcnt = take(4 * 256 * n);
+    L.run_cnt = take(8 * n);
+    L.tcnt = take(4 * 2 * 256 * n);
     L.refl_off = take(8 * (n + 1));
     L.tile_off = take(4 * (n + 1));
     L.order = take(4 * n);
     L.atom_bad = take(4 * n);
-    L.flags = take(64);
+    L.flags = take(kFlagBytes);
     L.coef32 = take(sizeof(xrd::Coef32) * (zmax + 1));
     L.atom32 = take(sizeof(xrd::Atom32) * natoms);
     L.atom64 = take(sizeof(xrd::Atom64) * natoms);
-    L.tile_tab = take(8 * (R / kTileMin + n + 1));
+    L.astep = take(8 * natoms);
+    L.tile_tab = take(8 * (R / kRunsPerTileHost + n + 1));
     L.q = take(8 * R);
     L.key = take(4 * R);
+    L.runs = take(4 * R);
     L.Fx = take(16 * R);
     L.Ig = take(4 * R);
     L.tb = take(4 * R);
@@ -192,10 +205,11 @@ int check_opts(xrd_handle* h, const xrd_opts* o)
 }
 
 // launch shape of the structure-factor kernel for this call
-void sf_shape(const xrd_handle* h, const xrd_opts* o, int& rb, int& warps)
+void sf_shape(const xrd_handle* h, const xrd_opts* o, int& rb, int& warps, int& runs)
 {
     rb = o->tile == 64 ? 2 : (o->tile == 128 ? 4 : h->sf_rb);
     warps = (o->precision == XRD_FP32_PHASEFIX) ? h->sf_warps : 2;
+    runs = (o->precision == XRD_FP32_PHASEFIX && o->tile == -1 && rb == 4) ? h->sf_runs : 0;
 }
 
 int check_batch(xrd_handle* h, const xrd_batch* b)
@@ -235,13 +249,13 @@ void radii(const xrd_opts* o, double& r2min, double& r2max, double& rmax)
 }
 
 xrd::GeomArgs geom_args(const xrd_batch* b, const xrd_opts* o, const Layout& L, char* ws, int64_t cap_refl,
-                        int64_t* totals, int32_t* status, int tile)
+                        int64_t* totals, int32_t* status, int rb)
 {
     xrd::GeomArgs g{};
     g.n_struct = b->n_struct;
     g.zmax = b->zmax;
     g.n_atoms = b->n_atoms;
-    g.tile = tile;
+    g.rb = rb;
     radii(o, g.r2min, g.r2max, g.rmax);
     g.cap_refl = cap_refl;
     g.lattice = b->lattice;
@@ -256,7 +270,11 @@ xrd::GeomArgs geom_args(const xrd_batch* b, const xrd_opts* o, const Layout& L, 
     g.atom32 = (xrd::Atom32*)(ws + L.atom32);
     g.atom64 = (xrd::Atom64*)(ws + L.atom64);
     g.refl_cnt = (int64_t*)(ws + L.refl_cnt);
+    g.run_cnt = (int64_t*)(ws + L.run_cnt);
     g.tcnt = (int*)(ws + L.tcnt);
+    g.runs = (int*)(ws + L.runs);
+    g.astep = (float2*)(ws + L.astep);
+    g.work = (unsigned long long*)(ws + L.flags + kWorkOffset);
     g.refl_off = (int64_t*)(ws + L.refl_off);
     g.tile_off = (int*)(ws + L.tile_off);
     g.order = (int*)(ws + L.order);
@@ -310,6 +328,7 @@ int xrd_create(xrd_handle** h, int device)
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->front, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->order_done, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->atoms_done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMalloc(&p->wbuf, 64);
     if (e != cudaSuccess) { xrd_destroy(p); return XRD_ECUDA; }
     p->ttab = xrd::init_tables(0);  // device tables (2-theta), once per handle, on the legacy stream
     e = cudaStreamSynchronize(0);
@@ -332,6 +351,7 @@ void xrd_destroy(xrd_handle* h)
     for (cudaEvent_t ev : {h->front, h->order_done, h->atoms_done})
         if (ev) cudaEventDestroy(ev);
     if (h->qbuf) cudaFree(h->qbuf);
+    if (h->wbuf) cudaFree(h->wbuf);
     delete h;
 }
 
@@ -440,9 +460,10 @@ int xrd_pattern_batch(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, cons
     cudaStream_t st = (cudaStream_t)stream;
     char* ws = (char*)workspace;
     const Layout L = layout(n, b->n_atoms, b->zmax, cap_refl);
-    int rb, warps;
-    sf_shape(h, o, rb, warps);
-    xrd::GeomArgs ga = geom_args(b, o, L, ws, cap_refl, out->totals, out->status, 32 * rb);
+    int rb, warps, runs;
+    sf_shape(h, o, rb, warps, runs);
+    xrd::GeomArgs ga = geom_args(b, o, L, ws, cap_refl, out->totals, out->status, rb);
+    ga.runs_mode = runs;
 
     const int prof = h->profiling;
     unsigned rec_flags = 0;  // inside a stream capture, stage events become timed graph nodes
@@ -458,7 +479,7 @@ int xrd_pattern_batch(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, cons
         stage++;
     };
     const bool pdl = prof != 1;  // programmatic launches where no stage event separates two kernels
-    cudaMemsetAsync(ws + L.flags, 0, 64, st);
+    cudaMemsetAsync(ws + L.flags, 0, kFlagBytes, st);
     mark();
     // the input-only front beside the enumeration: order (needed by the scan), then
     // coefficients and atoms (needed by the structure factor)
@@ -490,6 +511,10 @@ int xrd_pattern_batch(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, cons
     sa.tile = 32 * rb;
     sa.rb = rb;
     sa.warps = warps;
+    sa.runs_mode = runs;
+    sa.run_cnt = ga.run_cnt;
+    sa.runs = ga.runs;
+    sa.astep = ga.astep;
     sa.grid = h->sms;
     sa.lambda = o->lambda;
     sa.atom_off = b->atom_off;
@@ -596,29 +621,62 @@ int xrd_pattern_batch(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, cons
     return XRD_OK;
 }
 
-int xrd_set_sf_shape(xrd_handle* h, int tile, int warps)
+int xrd_work_counts(xrd_handle* h, const xrd_batch* b, const void* workspace, void* stream, int64_t* counts)
+{
+    if (!h || !b || !workspace || !counts) return XRD_EINVAL;
+    h->err.clear();
+    if (b->n_struct < 0) return fail(h, XRD_EINVAL, "n_struct must be >= 0");
+    DeviceGuard dg(h->device);
+    // the per-structure arrays sit before every per-reflection array: any capacity gives their offsets
+    const Layout L = layout(b->n_struct, b->n_atoms, b->zmax, 0);
+    char* ws = (char*)const_cast<void*>(workspace);
+    xrd::GeomArgs ga{};
+    ga.n_struct = b->n_struct;
+    ga.atom_off = b->atom_off;
+    ga.refl_cnt = (int64_t*)(ws + L.refl_cnt);
+    ga.run_cnt = (int64_t*)(ws + L.run_cnt);
+    ga.work = (unsigned long long*)(ws + L.flags + kWorkOffset);
+    uint64_t w[3] = {0, 0, 0};
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(h->wbuf, 0, 64, st);
+    if (e == cudaSuccess) {
+        xrd::launch_work(ga, h->wbuf, st);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(w, h->wbuf, sizeof(w), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "xrd_work_counts");
+    for (int i = 0; i < 3; i++) counts[i] = (int64_t)w[i];
+    return XRD_OK;
+}
+
+int xrd_set_sf_shape(xrd_handle* h, int tile, int warps, int runs)
 {
     if (!h) return XRD_EINVAL;
-    if ((tile != 64 && tile != 128) || (warps != 1 && warps != 2 && warps != 4))
-        return fail(h, XRD_EINVAL, "shape must be tile 64 or 128, warps 1, 2 or 4");
+    if ((tile != 64 && tile != 128) || (warps != 1 && warps != 2 && warps != 4) || (runs != 0 && runs != 1) ||
+        (runs && tile != 128))
+        return fail(h, XRD_EINVAL, "shape must be tile 64 or 128, warps 1, 2 or 4, runs 0 or 1 (runs: tile 128)");
     h->sf_rb = tile / 32;
     h->sf_warps = warps;
+    h->sf_runs = runs;
     return XRD_OK;
 }
 
 int xrd_autotune(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, const xrd_pattern* out, void* workspace,
-                 size_t ws_bytes, void* stream, int32_t* best_tile, int32_t* best_warps)
+                 size_t ws_bytes, void* stream, int32_t* best_tile, int32_t* best_warps, int32_t* best_runs)
 {
     if (!h) return XRD_EINVAL;
-    static const int shapes[6][2] = {{4, 2}, {4, 1}, {4, 4}, {2, 2}, {2, 1}, {2, 4}};
+    // (reflections per lane, warps per CTA, runs)
+    static const int shapes[9][3] = {{4, 2, 0}, {4, 1, 0}, {4, 4, 0}, {2, 2, 0}, {2, 1, 0},
+                                     {2, 4, 0}, {4, 1, 1}, {4, 2, 1}, {4, 4, 1}};
     const bool all = o && o->precision == XRD_FP32_PHASEFIX;
-    const int nshape = all ? 6 : 2;
-    const int keep_rb = h->sf_rb, keep_w = h->sf_warps;
+    const int nshape = all ? 9 : 2;
+    const int keep_rb = h->sf_rb, keep_w = h->sf_warps, keep_runs = h->sf_runs;
     const int keep_prof = h->profiling;
     xrd_opts oo = o ? *o : xrd_opts{};
     oo.tile = -1;
     float best = 1e30f;
-    int brb = keep_rb, bw = keep_w;
+    int brb = keep_rb, bw = keep_w, bruns = keep_runs;
     // the stage events of mode 2 end with the structure factor, so the calls' later kernels may
     // still run when xrd_stage_times returns: the stream is synchronised before every return
     auto finish = [&](int rc) {
@@ -627,33 +685,38 @@ int xrd_autotune(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, const xrd
         if (rc == XRD_OK && e != cudaSuccess) rc = cuda_fail(h, e, "xrd_autotune");
         return rc;
     };
-    h->profiling = 2;
+    h->profiling = 1;
     for (int i = 0; i < nshape; i++) {
-        const int rb = all ? shapes[i][0] : (i == 0 ? 4 : 2);
-        h->sf_rb = rb;
+        h->sf_rb = all ? shapes[i][0] : (i == 0 ? 4 : 2);
         h->sf_warps = all ? shapes[i][1] : 2;
+        h->sf_runs = all ? shapes[i][2] : 0;
         float t = 1e30f;
-        for (int rep = 0; rep < 3; rep++) {
+        for (int rep = 0; rep < 5; rep++) {
             const int rc = xrd_pattern_batch(h, b, &oo, out, workspace, ws_bytes, stream);
             if (rc != XRD_OK) {
-                h->sf_rb = keep_rb; h->sf_warps = keep_w; h->profiling = keep_prof;
+                h->sf_rb = keep_rb; h->sf_warps = keep_w; h->sf_runs = keep_runs; h->profiling = keep_prof;
                 return finish(rc);
             }
             float ms[8];
             const int m = xrd_stage_times(h, ms, 8);
             if (m < 0) {
-                h->sf_rb = keep_rb; h->sf_warps = keep_w; h->profiling = keep_prof;
+                h->sf_rb = keep_rb; h->sf_warps = keep_w; h->sf_runs = keep_runs; h->profiling = keep_prof;
                 return finish(-m);
             }
-            if (m >= 6 && rep > 0 && ms[5] < t) t = ms[5];  // structure-factor stage, after one warm-up
+            // the stages the shape changes: count, scan, emit (runs are built there), structure factor;
+            // the minimum over four calls after one warm-up
+            const float sum = m >= 6 ? ms[2] + ms[3] + ms[4] + ms[5] : 1e30f;
+            if (rep > 0 && sum < t) t = sum;
         }
-        if (t < best) { best = t; brb = h->sf_rb; bw = h->sf_warps; }
+        if (t < best) { best = t; brb = h->sf_rb; bw = h->sf_warps; bruns = h->sf_runs; }
     }
     h->sf_rb = brb;
     h->sf_warps = bw;
+    h->sf_runs = bruns;
     h->profiling = keep_prof;
     if (best_tile) *best_tile = 32 * brb;
     if (best_warps) *best_warps = bw;
+    if (best_runs) *best_runs = bruns;
     return finish(XRD_OK);
 }
 
@@ -787,9 +850,10 @@ int xrd_pattern_broadened(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, 
     ga.n_struct = (int)n;
     ga.zmax = b->zmax;
     ga.n_atoms = b->n_atoms;
-    int rb, warps;
-    sf_shape(h, o, rb, warps);
-    ga.tile = 32 * rb;
+    int rb, warps, runs;
+    sf_shape(h, o, rb, warps, runs);
+    ga.rb = rb;
+    ga.runs_mode = 0;  // the gradient path keeps strided tiles
     radii(o, ga.r2min, ga.r2max, ga.rmax);
     ga.cap_refl = cap_refl;
     ga.lattice = b->lattice;
@@ -804,7 +868,11 @@ int xrd_pattern_broadened(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, 
     ga.atom32 = (xrd::Atom32*)(ws + L.atom32);
     ga.atom64 = (xrd::Atom64*)(ws + L.atom64);
     ga.refl_cnt = (int64_t*)(ws + L.refl_cnt);
+    ga.run_cnt = (int64_t*)(ws + L.run_cnt);
     ga.tcnt = (int*)(ws + L.tcnt);
+    ga.runs = (int*)(ws + L.runs);
+    ga.astep = (float2*)(ws + L.astep);
+    ga.work = (unsigned long long*)(ws + L.flags + kWorkOffset);
     ga.refl_off = (int64_t*)(ws + L.refl_off);
     ga.tile_off = (int*)(ws + L.tile_off);
     ga.order = (int*)(ws + L.order);
@@ -816,7 +884,7 @@ int xrd_pattern_broadened(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, 
     ga.status = status;
     ga.q = (double*)(ws + L.q);
     ga.key = (uint32_t*)(ws + L.key);
-    cudaMemsetAsync(ws + L.flags, 0, 64, st);
+    cudaMemsetAsync(ws + L.flags, 0, kFlagBytes, st);
     xrd::launch_prep(ga, st, false);
     xrd::launch_coef(ga, st, true);
     xrd::launch_atoms(ga, st, true);
@@ -831,6 +899,9 @@ int xrd_pattern_broadened(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, 
     sa.tile = 32 * rb;
     sa.rb = rb;
     sa.warps = 2;
+    sa.run_cnt = ga.run_cnt;
+    sa.runs = ga.runs;
+    sa.astep = ga.astep;
     sa.grid = h->sms;
     sa.lambda = o->lambda;
     sa.atom_off = b->atom_off;

@@ -108,7 +108,8 @@ __global__ void __launch_bounds__(128) k_atoms(const int64_t* __restrict__ atom_
                                                const double* __restrict__ frac, const int16_t* __restrict__ Zin,
                                                const double* __restrict__ occ, const double* __restrict__ Bf, int zmax,
                                                Geo* __restrict__ geo, int set_geo, int* __restrict__ atom_bad,
-                                               Atom32* __restrict__ a32, Atom64* __restrict__ a64)
+                                               Atom32* __restrict__ a32, Atom64* __restrict__ a64,
+                                               float2* __restrict__ astep)
 {
     pdl_enter();
     __shared__ int off[kZmaxLimit + 1];
@@ -143,6 +144,7 @@ __global__ void __launch_bounds__(128) k_atoms(const int64_t* __restrict__ atom_
             a32[a0 + i] = r;
             Atom64 d{};
             a64[a0 + i] = d;
+            if (astep) astep[a0 + i] = make_float2(1.f, 0.f);
         }
         return;
     }
@@ -177,6 +179,11 @@ __global__ void __launch_bounds__(128) k_atoms(const int64_t* __restrict__ atom_
             r.src = (int)i;
             r.zf = (float)z;
             a32[a0 + pos] = r;
+            if (astep) {  // the l -> l + 1 step of the phase factor (runs), from the same fixed-point z
+                double sz, cz;
+                sincospi((double)(int32_t)r.Z * 0x1p-31, &sz, &cz);
+                astep[a0 + pos] = make_float2((float)cz, (float)sz);
+            }
             Atom64 d;
             d.x = x; d.y = y; d.z = w; d.B = bb; d.occ = o; d.zz = z; d.pad = 0;
             a64[a0 + pos] = d;
@@ -268,97 +275,162 @@ __device__ __forceinline__ int inside(const Geo& g, int h, int k, int l, double 
     return (q >= r2min && q <= r2max) ? 1 : 0;
 }
 
-// Count (EMIT = false) or write (EMIT = true) the reflections of one structure.
-// Each thread takes columns (h, k) in a strided order; when emitting, a block
-// scan of the per-thread counts gives every thread a fixed output range, so
-// the emitted order is deterministic and no atomics are needed.
-// The counting pass (k_count) keeps each thread's count, so the emitting pass
-// (k_emit, same block size and column order) skips the recount.
-template <bool EMIT>
-__device__ int enumerate_struct(const Geo& g, double r2min, double r2max, float r2minf, float r2maxf, int64_t base,
-                                int64_t cap, double* __restrict__ qo, uint32_t* __restrict__ ko, int* tmp,
-                                int local_in)
+// Runs: the structure-factor kernel gives each lane a run of at most rb
+// reflections that are consecutive in l within one column, so that it can step
+// the phase factor exp(2 pi i g.x) from l to l + 1 by one complex rotation.
+// A run starts at a column's first reflection, after a gap in l (the inner
+// sphere), or after rb reflections. Run entries: (first reflection within the
+// structure) << 3 | length.
+struct RunState {
+    int len = 0;      // reflections in the open run (0: none)
+    int start = 0;    // its first reflection
+    int prev_l = 0;   // l of the last reflection
+};
+
+// Count (EMIT = false) or write (EMIT = true) the reflections of one structure
+// (and, with rb > 0, its runs). Each thread takes columns (h, k) in a strided
+// order; when emitting, block scans of the per-thread counts give every thread
+// fixed output ranges, so the emitted order is deterministic and no atomics are
+// needed. The counting pass (k_count) keeps each thread's counts, so the
+// emitting pass (k_emit, same block size and column order) skips the recount.
+template <bool EMIT, bool RUNS>
+__device__ void enumerate_struct(const Geo& g, double r2min, double r2max, float r2minf, float r2maxf, int rb,
+                                 int64_t base, int64_t cap, double* __restrict__ qo, uint32_t* __restrict__ ko,
+                                 int* __restrict__ runo, int* tmp, int& local, int& local_runs)
 {
     const int nk = 2 * g.K + 1;
     const int ncol = (g.H + 1) * nk;
-    int local = local_in;
     if (!EMIT) {
+        local = 0;
+        local_runs = 0;
         for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
             const int h = c / nk, k = c % nk - g.K;
             if (h == 0 && k < 0) continue;  // half-space: h > 0, or h = 0 and k >= 0
             int lo, hi;
             column_range(g.gf, g.L, h, k, r2maxf, lo, hi);
-            for (int l = lo; l <= hi; l++) local += inside(g, h, k, l, r2min, r2max, r2minf, r2maxf);
+            int rl = 0, pl = lo - 2;
+            for (int l = lo; l <= hi; l++) {
+                if (!inside(g, h, k, l, r2min, r2max, r2minf, r2maxf)) continue;
+                local++;
+                if (RUNS) {
+                    if (rl == 0 || l != pl + 1 || rl == rb) {
+                        local_runs++;
+                        rl = 0;
+                    }
+                    rl++;
+                    pl = l;
+                }
+            }
         }
-        return local;
+        return;
     }
-    // exclusive offset of this thread's reflections within the structure
+    // exclusive offsets of this thread's reflections and runs within the structure
     const int nw = blockDim.x >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int inc = warp_incl_scan(local);
-    if (lane == 31) tmp[w] = inc;
+    const int inc = warp_incl_scan(local), incr = warp_incl_scan(local_runs);
+    if (lane == 31) {
+        tmp[w] = inc;
+        tmp[33 + w] = incr;
+    }
     __syncthreads();
     if (w == 0) {
-        const int sv = lane < nw ? tmp[lane] : 0;
-        const int si = warp_incl_scan(sv);
-        if (lane < nw) tmp[lane] = si - sv;
+        const int sv = lane < nw ? tmp[lane] : 0, sr = lane < nw ? tmp[33 + lane] : 0;
+        const int si = warp_incl_scan(sv), sj = warp_incl_scan(sr);
+        if (lane < nw) {
+            tmp[lane] = si - sv;
+            tmp[33 + lane] = sj - sr;
+        }
     }
     __syncthreads();
     int pos = tmp[w] + inc - local;
+    int rpos = tmp[33 + w] + incr - local_runs;
     for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
         const int h = c / nk, k = c % nk - g.K;
         if (h == 0 && k < 0) continue;
         int lo, hi;
         column_range(g.gf, g.L, h, k, r2maxf, lo, hi);
         const ColumnQ cq(g, h, k);
+        RunState run;
         for (int l = lo; l <= hi; l++) {
             if (!inside(g, h, k, l, r2min, r2max, r2minf, r2maxf)) continue;
+            if (RUNS && (run.len == 0 || l != run.prev_l + 1 || run.len == rb)) {
+                if (run.len > 0 && rpos < cap) runo[base + rpos] = (run.start << 3) | run.len;
+                if (run.len > 0) rpos++;
+                run.start = pos;
+                run.len = 0;
+            }
+            if (RUNS) {
+                run.len++;
+                run.prev_l = l;
+            }
             if (pos < cap) {
                 qo[base + pos] = cq.at(l);
                 ko[base + pos] = hkl_pack(h, k, l);
             }
             pos++;
         }
+        if (RUNS && run.len > 0) {
+            if (rpos < cap) runo[base + rpos] = (run.start << 3) | run.len;
+            rpos++;
+        }
     }
-    return local;
 }
 
+template <bool RUNS>
 __global__ void __launch_bounds__(256) k_count(const Geo* __restrict__ geo, double r2min, double r2max,
-                                               float r2minf, float r2maxf, int64_t* __restrict__ cnt,
-                                               int* __restrict__ tcnt)
+                                               float r2minf, float r2maxf, int rb, int64_t* __restrict__ cnt,
+                                               int64_t* __restrict__ run_cnt, int* __restrict__ tcnt)
 {
     pdl_enter();
     __shared__ int tmp[34];
     const int s = blockIdx.x;
     const Geo g = geo[s];
-    int local = 0;
+    int local = 0, local_runs = 0;
     if (g.status == XRD_OK && g.H >= 0)
-        local = enumerate_struct<false>(g, r2min, r2max, r2minf, r2maxf, 0, 0, nullptr, nullptr, tmp, 0);
-    if (tcnt) tcnt[(int64_t)s * blockDim.x + threadIdx.x] = local;
+        enumerate_struct<false, RUNS>(g, r2min, r2max, r2minf, r2maxf, rb, 0, 0, nullptr, nullptr, nullptr, tmp,
+                                      local, local_runs);
+    if (tcnt) {
+        tcnt[(int64_t)s * 2 * blockDim.x + threadIdx.x] = local;
+        if (RUNS) tcnt[(int64_t)s * 2 * blockDim.x + blockDim.x + threadIdx.x] = local_runs;
+    }
     const int n = block_sum_int(local, tmp);
     if (threadIdx.x == 0) cnt[s] = n;
+    if (RUNS && run_cnt) {
+        __syncthreads();
+        const int nr = block_sum_int(local_runs, tmp);
+        if (threadIdx.x == 0) run_cnt[s] = nr;
+    }
 }
 
-// Also writes the structure's entries of the structure-factor tile table:
-// (s, first reflection) of each tile of `tile` reflections, from tile_off[s].
+// Also writes the structure's runs (rb > 0) and its entries of the
+// structure-factor tile table from tile_off[s]: (s, first run) of each tile of
+// 32 runs, or (s, first reflection) of each tile of tile_refl reflections.
+template <bool RUNS>
 __global__ void __launch_bounds__(256) k_emit(const Geo* __restrict__ geo, double r2min, double r2max,
-                                              float r2minf, float r2maxf, const int64_t* __restrict__ refl_off,
-                                              const int* __restrict__ tcnt, const int* __restrict__ abort_flag,
-                                              double* __restrict__ q, uint32_t* __restrict__ key, int tile,
+                                              float r2minf, float r2maxf, int rb, int tile_refl,
+                                              const int64_t* __restrict__ refl_off,
+                                              const int64_t* __restrict__ run_cnt, const int* __restrict__ tcnt,
+                                              const int* __restrict__ abort_flag, double* __restrict__ q,
+                                              uint32_t* __restrict__ key, int* __restrict__ runs,
                                               const int* __restrict__ tile_off, int2* __restrict__ tile_tab)
 {
     pdl_enter();
-    __shared__ int tmp[34];
+    __shared__ int tmp[66];
     if (*abort_flag) return;
     const int s = blockIdx.x;
     const Geo g = geo[s];
     const int64_t base = refl_off[s], cap = refl_off[s + 1] - base;
-    if (tile_tab) {
-        const int nt = (int)((cap + tile - 1) / tile), t0 = tile_off[s];
-        for (int t = threadIdx.x; t < nt; t += blockDim.x) tile_tab[t0 + t] = make_int2(s, t * tile);
+    if (tile_tab) {  // rb > 0: tiles of 32 runs; otherwise tiles of tile_refl reflections
+        const int per = rb > 0 ? kRunsPerTile : tile_refl;
+        const int64_t units = rb > 0 ? run_cnt[s] : cap;
+        const int nt = (int)((units + per - 1) / per), t0 = tile_off[s];
+        for (int t = threadIdx.x; t < nt; t += blockDim.x) tile_tab[t0 + t] = make_int2(s, t * per);
     }
-    if (g.status == XRD_OK && g.H >= 0 && cap > 0)
-        enumerate_struct<true>(g, r2min, r2max, r2minf, r2maxf, base, cap, q, key, tmp,
-                               tcnt[(int64_t)s * blockDim.x + threadIdx.x]);
+    if (g.status == XRD_OK && g.H >= 0 && cap > 0) {
+        int local = tcnt[(int64_t)s * 2 * blockDim.x + threadIdx.x];
+        int local_runs = RUNS ? tcnt[(int64_t)s * 2 * blockDim.x + blockDim.x + threadIdx.x] : 0;
+        enumerate_struct<true, RUNS>(g, r2min, r2max, r2minf, r2maxf, rb, base, cap, q, key, runs, tmp, local,
+                                     local_runs);
+    }
 }
 
 // Single block. Every pass walks the batch in chunks of kScanItems * blockDim
@@ -396,12 +468,14 @@ __device__ __forceinline__ int warp_aggregated_slot(int* ctr, int key, bool acti
     return base + __popc(peers & ((1u << lane) - 1u));
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_refl(const int64_t* __restrict__ cnt, const Geo* __restrict__ geo,
-                                                            const int64_t* __restrict__ atom_off, int n, int tile,
+__global__ void __launch_bounds__(kScanThreads) k_scan_refl(const int64_t* __restrict__ cnt,
+                                                            const int64_t* __restrict__ run_cnt,
+                                                            const Geo* __restrict__ geo, int n, int tile_refl,
                                                             int64_t cap_refl, int64_t* __restrict__ refl_off,
                                                             int* __restrict__ tile_off, const int* __restrict__ order,
                                                             int* __restrict__ cls_list, int* __restrict__ abort_flag,
-                                                            int64_t* __restrict__ totals, int32_t* __restrict__ status)
+                                                            int64_t* __restrict__ totals, int32_t* __restrict__ status,
+                                                            unsigned long long* __restrict__ work)
 {
     pdl_enter();
     __shared__ long long ws[33];
@@ -454,7 +528,9 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_refl(const int64_t* __res
 #pragma unroll
         for (int u = 0; u < kScanItems; u++) {
             c[u] = sv[u] >= 0 ? cnt[sv[u]] : 0;
-            v[u] = (c[u] + tile - 1) / tile;
+            // tiles of 32 runs, or of tile_refl reflections
+            v[u] = sv[u] < 0 ? 0 : (tile_refl > 0 ? (c[u] + tile_refl - 1) / tile_refl
+                                                  : (run_cnt[sv[u]] + kRunsPerTile - 1) / kRunsPerTile);
         }
         chunk_scan<kScanItems>(v, buf, ws, &tot);
 #pragma unroll
@@ -471,6 +547,10 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_refl(const int64_t* __res
         __syncthreads();  // this chunk's class slots are taken before the next chunk's
     }
     if (tid == 0) {
+        if (work) {  // for xrd_work_counts: the tiles and the tile mode of this call
+            work[0] = (unsigned long long)tcarry;
+            work[1] = tile_refl > 0 ? 0ull : 1ull;
+        }
         refl_off[n] = total;
         tile_off[n] = over ? 0 : (int)tcarry;
         for (int k = 0; k < kPostClasses; k++) abort_flag[4 + k] = over ? 0 : ccnt[k];
@@ -531,6 +611,50 @@ static void launch_k(bool pdl, void (*k)(P...), dim3 grid, dim3 block, cudaStrea
     else k<<<grid, block, 0, st>>>(static_cast<P>(args)...);
 }
 
+// Structure-factor work of the last call (for xrd_work_counts): terms = sum of
+// reflections x atoms; phase seeds = the same with strided tiles, runs x atoms
+// with runs; out[0..2] = terms, seeds, tiles (out zeroed by the caller).
+__global__ void __launch_bounds__(256) k_work(const int64_t* __restrict__ cnt, const int64_t* __restrict__ run_cnt,
+                                              const int64_t* __restrict__ atom_off, int n,
+                                              const unsigned long long* __restrict__ work,
+                                              unsigned long long* __restrict__ out)
+{
+    __shared__ unsigned long long red[2][8];
+    const bool runs = work[1] != 0;
+    unsigned long long t = 0, sd = 0;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+        const unsigned long long na = (unsigned long long)(atom_off[s + 1] - atom_off[s]);
+        t += (unsigned long long)cnt[s] * na;
+        sd += (unsigned long long)(runs ? run_cnt[s] : cnt[s]) * na;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        t += __shfl_xor_sync(0xffffffffu, t, o);
+        sd += __shfl_xor_sync(0xffffffffu, sd, o);
+    }
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        red[0][w] = t;
+        red[1][w] = sd;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = 1; i < (int)(blockDim.x >> 5); i++) {
+            t += red[0][i];
+            sd += red[1][i];
+        }
+        atomicAdd(&out[0], t);
+        atomicAdd(&out[1], sd);
+        if (blockIdx.x == 0) out[2] = work[0];
+    }
+}
+
+void launch_work(const GeomArgs& a, unsigned long long* out, cudaStream_t st)
+{
+    if (a.n_struct > 0)
+        k_work<<<min((a.n_struct + 255) / 256, 1024), 256, 0, st>>>(a.refl_cnt, a.run_cnt, a.atom_off, a.n_struct,
+                                                                   a.work, out);
+}
+
 void launch_prep(const GeomArgs& a, cudaStream_t st, bool pdl)
 {
     const int n = a.n_struct;
@@ -546,7 +670,7 @@ void launch_atoms(const GeomArgs& a, cudaStream_t st, bool pdl)
 {
     if (a.n_struct > 0)
         launch_k(pdl, k_atoms, a.n_struct, 128, st, a.atom_off, a.n_atoms, a.frac, a.Z, a.occ, a.B, a.zmax, a.geo,
-                 a.atoms_set_geo, a.atom_bad, a.atom32, a.atom64);
+                 a.atoms_set_geo, a.atom_bad, a.atom32, a.atom64, a.runs_mode ? a.astep : (float2*)nullptr);
 }
 
 void launch_order(const GeomArgs& a, cudaStream_t st, bool pdl)
@@ -559,28 +683,32 @@ void launch_count_only(const GeomArgs& a, cudaStream_t st)
     const int n = a.n_struct;
     if (n <= 0) return;
     k_prep<<<(n + 31) / 32, 32, 0, st>>>(a.lattice, n, a.rmax, a.geo);
-    launch_pdl(k_count, n, 256, 0, st, a.geo, a.r2min, a.r2max, (float)a.r2min, (float)a.r2max, a.refl_cnt,
-               (int*)nullptr);
+    launch_pdl(k_count<false>, n, 256, 0, st, a.geo, a.r2min, a.r2max, (float)a.r2min, (float)a.r2max, 0,
+               a.refl_cnt, (int64_t*)nullptr, (int*)nullptr);
 }
 
 void launch_count(const GeomArgs& a, cudaStream_t st, bool pdl)
 {
     if (a.n_struct > 0)
-        launch_k(pdl, k_count, a.n_struct, 256, st, a.geo, a.r2min, a.r2max, (float)a.r2min, (float)a.r2max,
-                 a.refl_cnt, a.tcnt);
+        launch_k(pdl, a.runs_mode ? k_count<true> : k_count<false>, a.n_struct, 256, st, a.geo, a.r2min, a.r2max,
+                 (float)a.r2min, (float)a.r2max, a.runs_mode ? a.rb : 0, a.refl_cnt, a.run_cnt, a.tcnt);
 }
 
 void launch_scan_refl(const GeomArgs& a, cudaStream_t st, bool pdl)
 {
-    launch_k(pdl, k_scan_refl, 1, kScanThreads, st, a.refl_cnt, a.geo, a.atom_off, a.n_struct, a.tile, a.cap_refl,
-             a.refl_off, a.tile_off, (const int*)a.order, a.cls_list, a.abort_flag, a.totals, a.status);
+    launch_k(pdl, k_scan_refl, 1, kScanThreads, st, a.refl_cnt, a.run_cnt, a.geo, a.n_struct,
+             a.runs_mode ? 0 : 32 * a.rb, a.cap_refl, a.refl_off, a.tile_off, (const int*)a.order, a.cls_list,
+             a.abort_flag, a.totals, a.status, a.work);
 }
 
 void launch_emit(const GeomArgs& a, cudaStream_t st, bool pdl)
 {
     if (a.n_struct > 0)
-        launch_k(pdl, k_emit, a.n_struct, 256, st, a.geo, a.r2min, a.r2max, (float)a.r2min, (float)a.r2max,
-                 a.refl_off, a.tcnt, a.abort_flag, a.q, a.key, a.tile, (const int*)a.tile_off, a.tile_tab);
+        launch_k(pdl, a.runs_mode ? k_emit<true> : k_emit<false>, a.n_struct, 256, st, a.geo, a.r2min, a.r2max,
+                 (float)a.r2min, (float)a.r2max,
+                 a.runs_mode ? a.rb : 0, 32 * a.rb,
+                 (const int64_t*)a.refl_off, (const int64_t*)a.run_cnt, (const int*)a.tcnt, (const int*)a.abort_flag,
+                 a.q, a.key, a.runs, (const int*)a.tile_off, a.tile_tab);
 }
 
 }  // namespace xrd

@@ -53,37 +53,53 @@ __device__ __forceinline__ float fprime_of(const Coef32& c, float s2)
     return acc;
 }
 
-// FP32 variants: RB reflections per lane share each atom record, which the
-// warp stages in shared memory and every lane reads (a broadcast).
+// The reflections of one lane in a tile: RUNS: one run of `len` reflections
+// consecutive in l from `first` (step 1); otherwise up to RB reflections from
+// `first` with a step of 32 (a tile of 32 RB consecutive reflections), `len` of
+// them inside the structure.
+//
+// FP32 variants: every atom record (staged by the warp in shared memory, read
+// by all lanes as a broadcast) feeds the lane's RB terms. With the integer phase
+// (XRD_FP32_PHASEFIX) and RUNS, the phase factor is formed exactly once per run
+// and atom, then rotated from l to l + 1 by the atom's exp(2 pi i z) (an
+// accurately rounded FP32 pair): one sin/cos pair per run instead of per
+// reflection. Otherwise every reflection's phase is formed exactly (integer
+// phase) or in FP64 (XRD_FP32_PHASE64).
 // GRAD also accumulates dF/ds^2 = sum_j occ_j exp(-B_j s^2)(f_j' - B_j f_j) e^{i phi_j}.
-// staged: the structure's atoms (at most kSfChunk) are already in sat from the
-// previous tile of the same structure.
-template <int PREC, bool GRAD, int kSfRB>
-__device__ void sf_tile_fp32(const SfArgs& a, int64_t r0, int64_t re, int64_t j0, int64_t j1, Atom32* sat,
-                             const Coef32* scoef, bool staged)
+template <int PREC, bool GRAD, int kSfRB, bool RUNS>
+__device__ void sf_tile_fp32(const SfArgs& a, int64_t first, int len, int64_t j0, int64_t j1, Atom32* sat,
+                             float2* sstep, const Coef32* scoef, bool staged)
 {
     constexpr float ln2 = 0.69314718055994531f;
+    constexpr int step = RUNS ? 1 : 32;
     const int lane = threadIdx.x & 31;
     float s2[kSfRB], qf[kSfRB], Fr[kSfRB], Fi[kSfRB], f[kSfRB];
     float Gr[kSfRB], Gi[kSfRB], fp[kSfRB];
     uint32_t uh[kSfRB], uk[kSfRB], ul[kSfRB];
 #pragma unroll
     for (int i = 0; i < kSfRB; i++) {
-        const int64_t r = r0 + lane + i * 32;
-        const int64_t rr = r < re ? r : r0;
-        qf[i] = d2f_pos(a.q[rr]);
+        const int64_t r = first + (int64_t)step * (i < len ? i : 0);
+        qf[i] = d2f_pos(a.q[r]);
         s2[i] = qf[i] * 0.25f;
-        const uint32_t key = a.key[rr];
-        uh[i] = (uint32_t)hkl_h(key); uk[i] = (uint32_t)hkl_k(key); ul[i] = (uint32_t)hkl_l(key);
+        if (!RUNS || i == 0) {
+            const uint32_t key = a.key[r];
+            uh[i] = (uint32_t)hkl_h(key); uk[i] = (uint32_t)hkl_k(key); ul[i] = (uint32_t)hkl_l(key);
+        } else {
+            uh[i] = uh[0]; uk[i] = uk[0]; ul[i] = ul[0] + (uint32_t)i;
+        }
         Fr[i] = 0.f; Fi[i] = 0.f; f[i] = 0.f;
         Gr[i] = 0.f; Gi[i] = 0.f; fp[i] = 0.f;
     }
+    constexpr bool kRotate = RUNS && PREC == XRD_FP32_PHASEFIX;
     int zc = -1;
     for (int64_t c0 = j0; c0 < j1; c0 += kSfChunk) {
         const int nc = (int)min((int64_t)kSfChunk, j1 - c0);
         if (!staged) {
             __syncwarp();
-            for (int i = lane; i < nc; i += 32) sat[i] = a.atom32[c0 + i];
+            for (int i = lane; i < nc; i += 32) {
+                sat[i] = a.atom32[c0 + i];
+                if (kRotate) sstep[i] = a.astep[c0 + i];
+            }
             __syncwarp();
         }
         for (int jj = 0; jj < nc; jj++) {
@@ -97,20 +113,28 @@ __device__ void sf_tile_fp32(const SfArgs& a, int64_t r0, int64_t re, int64_t j0
                     if (GRAD) fp[i] = fprime_of(c, s2[i]);
                 }
             }
+            float cs = 0.f, sn = 0.f, cz = 1.f, sz = 0.f;
             double dx = 0.0, dy = 0.0, dz = 0.0;
-            if (PREC == XRD_FP32_PHASE64) {
+            if (kRotate) {
+                const uint32_t P = uh[0] * at.X + uk[0] * at.Y + ul[0] * at.Z;
+                __sincosf((float)(int32_t)P * kTwoPiOver2p32, &sn, &cs);
+                const float2 st = sstep[jj];
+                cz = st.x;
+                sz = st.y;
+            } else if (PREC == XRD_FP32_PHASE64) {
                 const Atom64 d = a.atom64[c0 + jj];
                 dx = d.x; dy = d.y; dz = d.z;
             }
 #pragma unroll
             for (int i = 0; i < kSfRB; i++) {
-                uint32_t P;
-                if (PREC == XRD_FP32_PHASEFIX)
-                    P = uh[i] * at.X + uk[i] * at.Y + ul[i] * at.Z;
-                else
-                    P = fix32(fma((double)(int)uh[i], dx, fma((double)(int)uk[i], dy, (double)(int)ul[i] * dz)));
-                float sn, cs;
-                __sincosf((float)(int32_t)P * kTwoPiOver2p32, &sn, &cs);
+                if (!kRotate) {
+                    uint32_t P;
+                    if (PREC == XRD_FP32_PHASEFIX)
+                        P = uh[i] * at.X + uk[i] * at.Y + ul[i] * at.Z;
+                    else
+                        P = fix32(fma((double)(int)uh[i], dx, fma((double)(int)uk[i], dy, (double)(int)ul[i] * dz)));
+                    __sincosf((float)(int32_t)P * kTwoPiOver2p32, &sn, &cs);
+                }
                 const float dw = ex2_approx(fmaf(at.nb, s2[i], at.lo));
                 const float w = f[i] * dw;
                 Fr[i] = fmaf(w, cs, Fr[i]);
@@ -120,14 +144,19 @@ __device__ void sf_tile_fp32(const SfArgs& a, int64_t r0, int64_t re, int64_t j0
                     Gr[i] = fmaf(wd, cs, Gr[i]);
                     Gi[i] = fmaf(wd, sn, Gi[i]);
                 }
+                if (kRotate && i + 1 < kSfRB) {  // exp(2 pi i g.x) from l to l + 1
+                    const float c2 = fmaf(cs, cz, -sn * sz);
+                    sn = fmaf(cs, sz, sn * cz);
+                    cs = c2;
+                }
             }
         }
     }
     const float l2 = (float)(a.lambda * a.lambda * 0.25);
 #pragma unroll
     for (int i = 0; i < kSfRB; i++) {
-        const int64_t r = r0 + lane + i * 32;
-        if (r >= re) continue;
+        if (i >= len) continue;
+        const int64_t r = first + (int64_t)step * i;
         const float I = fmaf(Fr[i], Fr[i], Fi[i] * Fi[i]) * lp_of(qf[i], l2);
         if (GRAD) {
             a.Fx[r] = make_float4(Fr[i], Fi[i], Gr[i], Gi[i]);
@@ -139,16 +168,15 @@ __device__ void sf_tile_fp32(const SfArgs& a, int64_t r0, int64_t re, int64_t j0
     }
 }
 
+// FP64 path: the lane's reflections one after another, every term in FP64.
 template <int kSfRB>
-__device__ void sf_tile_fp64(const SfArgs& a, int64_t r0, int64_t re, int64_t j0, int64_t j1)
+__device__ void sf_tile_fp64(const SfArgs& a, int64_t first, int step, int len, int64_t j0, int64_t j1)
 {
-    const int lane = threadIdx.x & 31;
     for (int i = 0; i < kSfRB; i++) {
-        const int64_t r = r0 + lane + i * 32;
-        const bool act = r < re;
-        const int64_t rr = act ? r : r0;
-        const double q = a.q[rr];
-        const uint32_t key = a.key[rr];
+        const bool act = i < len;
+        const int64_t r = first + (int64_t)step * (act ? i : 0);
+        const double q = a.q[r];
+        const uint32_t key = a.key[r];
         const int h = hkl_h(key), k = hkl_k(key), l = hkl_l(key);
         const double s2 = q * 0.25;
         double Fr = 0.0, Fi = 0.0, f = 0.0;
@@ -180,13 +208,13 @@ __device__ void sf_tile_fp64(const SfArgs& a, int64_t r0, int64_t re, int64_t j0
     }
 }
 
-// Persistent CTAs; every warp takes tiles of 32 RB reflections from a queue in
-// largest-first order (tiles of the structures with the most atoms first). A
-// structure's atoms stay staged in the warp's shared memory while its
+// Persistent CTAs; every warp takes tiles of 32 runs (one per lane) from a
+// queue in largest-first order (tiles of the structures with the most atoms
+// first). A structure's atoms stay staged in the warp's shared memory while its
 // consecutive tiles follow (when they fit one chunk).
 // Register caps: 64 for the integer-phase variant (32 resident warps per SM),
 // about 85 for the FP64-phase and gradient variants (24 warps).
-template <int PREC, bool GRAD, int RB, int WARPS>
+template <int PREC, bool GRAD, int RB, int WARPS, bool RUNS>
 __global__ void __launch_bounds__(32 * WARPS, PREC == XRD_FP64 ? 1 : ((PREC == XRD_FP32_PHASEFIX && !GRAD) ? 32 / WARPS
                                                                                                           : 24 / WARPS))
     k_sf(const SfArgs a)
@@ -194,6 +222,7 @@ __global__ void __launch_bounds__(32 * WARPS, PREC == XRD_FP64 ? 1 : ((PREC == X
     pdl_enter();
     constexpr int kSfThreads = 32 * WARPS;
     __shared__ Atom32 sat[WARPS][kSfChunk];
+    __shared__ float2 sstep[WARPS][kSfChunk];
     extern __shared__ Coef32 scoef[];  // [zmax + 1]
     if (*a.abort_flag) return;
     const int ntiles = a.tile_off[a.n_struct];
@@ -210,20 +239,38 @@ __global__ void __launch_bounds__(32 * WARPS, PREC == XRD_FP64 ? 1 : ((PREC == X
         if (t >= ntiles) break;
         const int2 e = a.tile_tab[t];
         const int s = e.x;
-        const int64_t rb = a.refl_off[s], re = a.refl_off[s + 1];
-        const int64_t r0 = rb + e.y;
+        const int64_t rbase = a.refl_off[s], re = a.refl_off[s + 1];
         const int64_t j0 = a.atom_off[s], j1 = a.atom_off[s + 1];
+        int64_t first;
+        int len;
+        if (RUNS) {  // lane: one run of the structure
+            const int64_t nruns = a.run_cnt[s];
+            const int64_t r = e.y + lane;
+            int start = 0;
+            len = 0;
+            if (r < nruns) {
+                const int pk = a.runs[rbase + r];
+                start = pk >> 3;
+                len = pk & 7;
+            }
+            first = rbase + start;
+        } else {  // lane: reflections e.y + lane + 32 i of the structure
+            first = rbase + e.y + lane;
+            len = (int)max(min((re - first + 31) / 32, (int64_t)RB), (int64_t)0);
+        }
+        if (len == 0) first = rbase;  // keep the lane's (ignored) loads inside the array
         if (PREC == XRD_FP64) {
-            sf_tile_fp64<RB>(a, r0, re, j0, j1);
+            sf_tile_fp64<RB>(a, first, RUNS ? 1 : 32, len, j0, j1);
         } else {
             const bool one_chunk = j1 - j0 <= kSfChunk;
-            sf_tile_fp32<PREC, GRAD, RB>(a, r0, re, j0, j1, sat[w], scoef, one_chunk && s == staged_s);
+            sf_tile_fp32<PREC, GRAD, RB, RUNS>(a, first, len, j0, j1, sat[w], sstep[w], scoef,
+                                               one_chunk && s == staged_s);
             staged_s = one_chunk ? s : -1;
         }
     }
 }
 
-template <int PREC, bool GRAD, int RB, int WARPS>
+template <int PREC, bool GRAD, int RB, int WARPS, bool RUNS>
 static void launch_sf_shape(const SfArgs& a, cudaStream_t st, bool pdl)
 {
     // persistent grid: as many CTAs as fit on the SMs at once (cached per device and zmax)
@@ -234,24 +281,25 @@ static void launch_sf_shape(const SfArgs& a, cudaStream_t st, bool pdl)
     const bool cached = dev >= 0 && dev < 64 && cache_per_sm[dev] > 0 && cache_zmax[dev] == a.zmax;
     int per_sm = cached ? cache_per_sm[dev] : 0;
     if (!cached) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sf<PREC, GRAD, RB, WARPS>, 32 * WARPS, smem) !=
-                cudaSuccess ||
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sf<PREC, GRAD, RB, WARPS, RUNS>, 32 * WARPS,
+                                                          smem) != cudaSuccess ||
             per_sm < 1)
             per_sm = 4;
         if (dev >= 0 && dev < 64) { cache_per_sm[dev] = per_sm; cache_zmax[dev] = a.zmax; }
     }
-    if (pdl) launch_pdl(k_sf<PREC, GRAD, RB, WARPS>, a.grid * per_sm, 32 * WARPS, smem, st, a);
-    else k_sf<PREC, GRAD, RB, WARPS><<<a.grid * per_sm, 32 * WARPS, smem, st>>>(a);
+    if (pdl) launch_pdl(k_sf<PREC, GRAD, RB, WARPS, RUNS>, a.grid * per_sm, 32 * WARPS, smem, st, a);
+    else k_sf<PREC, GRAD, RB, WARPS, RUNS><<<a.grid * per_sm, 32 * WARPS, smem, st>>>(a);
 }
 
 template <int PREC, bool GRAD>
 static void launch_sf_prec(const SfArgs& a, cudaStream_t st, bool pdl)
 {
-    if (a.rb == 2) launch_sf_shape<PREC, GRAD, 2, 2>(a, st, pdl);
-    else launch_sf_shape<PREC, GRAD, 4, 2>(a, st, pdl);
+    if (a.rb == 2) launch_sf_shape<PREC, GRAD, 2, 2, false>(a, st, pdl);
+    else launch_sf_shape<PREC, GRAD, 4, 2, false>(a, st, pdl);
 }
 
-// a.grid = number of SMs; a.rb, a.warps = launch shape (tile = 32 rb reflections)
+// a.grid = number of SMs; a.rb, a.warps, a.runs_mode = launch shape. Runs (with the l-step
+// rotation) exist for the integer-phase pattern variant with 4 reflections per lane.
 void launch_sf(const SfArgs& a, cudaStream_t st, bool pdl)
 {
     if (a.n_struct <= 0) return;
@@ -263,14 +311,18 @@ void launch_sf(const SfArgs& a, cudaStream_t st, bool pdl)
     case XRD_FP64: launch_sf_prec<XRD_FP64, false>(a, st, pdl); break;
     case XRD_FP32_PHASE64: launch_sf_prec<XRD_FP32_PHASE64, false>(a, st, pdl); break;
     default:
-        if (a.rb == 2) {
-            if (a.warps == 1) launch_sf_shape<XRD_FP32_PHASEFIX, false, 2, 1>(a, st, pdl);
-            else if (a.warps == 4) launch_sf_shape<XRD_FP32_PHASEFIX, false, 2, 4>(a, st, pdl);
-            else launch_sf_shape<XRD_FP32_PHASEFIX, false, 2, 2>(a, st, pdl);
+        if (a.runs_mode) {
+            if (a.warps == 1) launch_sf_shape<XRD_FP32_PHASEFIX, false, 4, 1, true>(a, st, pdl);
+            else if (a.warps == 4) launch_sf_shape<XRD_FP32_PHASEFIX, false, 4, 4, true>(a, st, pdl);
+            else launch_sf_shape<XRD_FP32_PHASEFIX, false, 4, 2, true>(a, st, pdl);
+        } else if (a.rb == 2) {
+            if (a.warps == 1) launch_sf_shape<XRD_FP32_PHASEFIX, false, 2, 1, false>(a, st, pdl);
+            else if (a.warps == 4) launch_sf_shape<XRD_FP32_PHASEFIX, false, 2, 4, false>(a, st, pdl);
+            else launch_sf_shape<XRD_FP32_PHASEFIX, false, 2, 2, false>(a, st, pdl);
         } else {
-            if (a.warps == 1) launch_sf_shape<XRD_FP32_PHASEFIX, false, 4, 1>(a, st, pdl);
-            else if (a.warps == 4) launch_sf_shape<XRD_FP32_PHASEFIX, false, 4, 4>(a, st, pdl);
-            else launch_sf_shape<XRD_FP32_PHASEFIX, false, 4, 2>(a, st, pdl);
+            if (a.warps == 1) launch_sf_shape<XRD_FP32_PHASEFIX, false, 4, 1, false>(a, st, pdl);
+            else if (a.warps == 4) launch_sf_shape<XRD_FP32_PHASEFIX, false, 4, 4, false>(a, st, pdl);
+            else launch_sf_shape<XRD_FP32_PHASEFIX, false, 4, 2, false>(a, st, pdl);
         }
         break;
     }

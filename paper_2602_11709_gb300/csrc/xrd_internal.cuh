@@ -16,6 +16,7 @@ constexpr int kHklLimit = 511;        // |h|, |k|, |l| fit the 10-bit fields of 
 // (held in shared memory) go to class c; larger ones to the last class (global
 // scratch). Threads per CTA: 64, 128, 256, 512, 1024, 1024.
 constexpr int kPostClasses = 6;
+constexpr int kRunsPerTile = 32;  // structure-factor tile: one run of reflections per lane of a warp
 constexpr int kPostCap0 = 256, kPostCap1 = 512, kPostCap2 = 1536, kPostCap3 = 3072, kPostCap4 = 6144;
 __host__ __device__ __forceinline__ int post_class(long long c)
 {

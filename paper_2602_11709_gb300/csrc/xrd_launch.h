@@ -9,7 +9,8 @@
 namespace xrd {
 
 struct GeomArgs {
-    int n_struct, zmax, tile;
+    int n_struct, zmax, rb;  // rb: reflections a structure-factor lane takes (2 or 4)
+    int runs_mode;           // 1: tiles of 32 runs of <= rb reflections consecutive in l; 0: tiles of 32 rb reflections
     int64_t n_atoms;
     double r2min, r2max, rmax;
     int64_t cap_refl;
@@ -24,8 +25,12 @@ struct GeomArgs {
     Coef32* coef32;
     Atom32* atom32;
     Atom64* atom64;
+    float2* astep;   // [atoms] exp(2 pi i z) of each element-sorted atom
     int64_t* refl_cnt;
-    int* tcnt;       // [n_struct][256] per-thread reflection counts of the counting pass
+    int64_t* run_cnt;  // [n_struct] runs of each structure
+    int* tcnt;       // [n_struct][2][256] per-thread reflection and run counts of the counting pass
+    int* runs;       // [reflections] run entries (first reflection within the structure << 3 | length)
+    unsigned long long* work;  // [3] structure-factor work: terms, phase-factor seeds, tiles (k_scan_refl)
     int64_t* refl_off;
     int* tile_off;   // [n_struct + 1] first structure-factor tile of each structure; [n_struct] = tiles
     int* order;      // [n_struct] structures by atom count, largest first
@@ -44,11 +49,15 @@ struct GeomArgs {
 struct SfArgs {
     int n_struct, precision, tile, grid, zmax;
     int rb, warps;  // launch shape: reflections per lane (2 or 4), warps per CTA (1, 2 or 4)
+    int runs_mode;  // lanes take runs (integer phase only) instead of strided reflections
     double lambda;
     const int64_t* atom_off;
     const int64_t* refl_off;
     const int* tile_off;  // [n_struct + 1]: [n_struct] is the number of tiles
-    const int2* tile_tab; // [tiles] (structure, first reflection within it), largest-first order
+    const int2* tile_tab; // [tiles] (structure, first run or reflection within it), largest-first order
+    const int64_t* run_cnt;  // [n_struct] runs of each structure
+    const int* runs;      // [reflections] run entries, indexed from refl_off[s]
+    const float2* astep;  // [atoms] exp(2 pi i z) of each element-sorted atom (the l + 1 step)
     int* tile_counter;    // work-queue head, zeroed by the caller
     const int* abort_flag;
     const Coef32* coef32;
@@ -157,6 +166,7 @@ void launch_order(const GeomArgs& a, cudaStream_t st, bool pdl);
 void launch_count(const GeomArgs& a, cudaStream_t st, bool pdl);
 void launch_count_only(const GeomArgs& a, cudaStream_t st);
 void launch_scan_refl(const GeomArgs& a, cudaStream_t st, bool pdl);
+void launch_work(const GeomArgs& a, unsigned long long* out, cudaStream_t st);  // out: device [3], zeroed
 void launch_emit(const GeomArgs& a, cudaStream_t st, bool pdl);
 void launch_sf(const SfArgs& a, cudaStream_t st, bool pdl);
 size_t post_smem_bytes(int cap);

@@ -56,7 +56,7 @@ class xrd_pattern(C.Structure):
 EXPORTS = ["xrd_create", "xrd_destroy", "xrd_last_error", "xrd_query_sizes", "xrd_pattern_batch",
            "xrd_set_profiling", "xrd_stage_times", "xrd_pattern_batch_noalloc", "xrd_pattern_broadened",
            "xrd_pattern_grad", "xrd_autotune", "xrd_set_sf_shape", "xrd_graph_create", "xrd_graph_launch",
-           "xrd_graph_destroy"]
+           "xrd_graph_destroy", "xrd_work_counts"]
 
 _lib = None
 
@@ -96,9 +96,12 @@ def load(path: str = LIB_PATH):
                                    C.c_void_p]
     L.xrd_pattern_grad.restype = C.c_int
     L.xrd_autotune.argtypes = [C.c_void_p, C.POINTER(xrd_batch), C.POINTER(xrd_opts), C.POINTER(xrd_pattern),
-                               C.c_void_p, C.c_size_t, C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+                               C.c_void_p, C.c_size_t, C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                               C.POINTER(C.c_int32)]
     L.xrd_autotune.restype = C.c_int
-    L.xrd_set_sf_shape.argtypes = [C.c_void_p, C.c_int, C.c_int]
+    L.xrd_set_sf_shape.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int]
+    L.xrd_work_counts.argtypes = [C.c_void_p, C.POINTER(xrd_batch), C.c_void_p, C.c_void_p, C.POINTER(C.c_int64)]
+    L.xrd_work_counts.restype = C.c_int
     L.xrd_set_sf_shape.restype = C.c_int
     L.xrd_graph_create.argtypes = [C.c_void_p, C.POINTER(xrd_batch), C.POINTER(xrd_opts), C.POINTER(xrd_pattern),
                                    C.c_void_p, C.c_size_t, C.POINTER(C.c_void_p)]
@@ -428,16 +431,23 @@ class Handle:
                                               _stream_ptr(stream)))
 
     def autotune(self, db: DeviceBatch, opts: xrd_opts, out: PatternBuffers, ws, stream=None):
-        """Pick the fastest structure-factor launch shape for this batch; returns (tile, warps)."""
+        """Pick the fastest structure-factor launch shape for this batch; returns (tile, warps, runs)."""
         b, o = db.c(), out.c()
-        tile, warps = C.c_int32(), C.c_int32()
+        tile, warps, runs = C.c_int32(), C.c_int32(), C.c_int32()
         self._check(self.lib.xrd_autotune(self.h, C.byref(b), C.byref(opts), C.byref(o), C.c_void_p(ws.data_ptr()),
                                           C.c_size_t(ws.numel() * ws.element_size()), _stream_ptr(stream),
-                                          C.byref(tile), C.byref(warps)))
-        return tile.value, warps.value
+                                          C.byref(tile), C.byref(warps), C.byref(runs)))
+        return tile.value, warps.value, runs.value
 
-    def set_sf_shape(self, tile: int, warps: int):
-        self._check(self.lib.xrd_set_sf_shape(self.h, int(tile), int(warps)))
+    def work_counts(self, db: DeviceBatch, ws, stream=None):
+        """Structure-factor work of the last call on ws: (terms, phase-factor seeds, f(s) evaluations)."""
+        b = db.c()
+        out = (C.c_int64 * 3)()
+        self._check(self.lib.xrd_work_counts(self.h, C.byref(b), C.c_void_p(ws.data_ptr()), _stream_ptr(stream), out))
+        return int(out[0]), int(out[1]), int(out[2])
+
+    def set_sf_shape(self, tile: int, warps: int, runs: int = 0):
+        self._check(self.lib.xrd_set_sf_shape(self.h, int(tile), int(warps), int(runs)))
 
     def graph(self, db: DeviceBatch, opts: xrd_opts, out: PatternBuffers, ws):
         """A CUDA graph of one pattern_batch call with these buffers."""

@@ -1,9 +1,11 @@
 """Batching machinery: launch-shape autotuning and CUDA-graph replay.
 
-Every structure-factor launch shape evaluates each reflection's sum over the
-same atoms in the same order, so all shapes must give bit-identical patterns;
-a graph replay must give what an eager call gives, also after the batch's
-contents change in place (same sizes).
+A structure-factor launch shape is a run length (2 or 4 reflections per lane,
+tiles of 64 or 128) and 1, 2 or 4 warps per CTA. For one run length every warp
+count evaluates each reflection's sum over the same atoms in the same order, so
+those patterns are bit-identical; the two run lengths differ only in how far
+the phase factor is rotated along l (about 1e-7 relative). A graph replay must
+give what an eager call gives, also after the batch's contents change in place.
 """
 import numpy as np
 import pytest
@@ -34,7 +36,17 @@ def _same(a, b):
     assert np.array_equal(a["totals"], b["totals"])
 
 
-def test_all_launch_shapes_bit_identical(gpu_lib):
+def _close(a, b, tol):
+    for k in ("fam_hkl", "fam_mult"):
+        for x, y in zip(a[k], b[k]):
+            assert np.array_equal(x, y), k
+    for x, y in zip(a["peak_tt"], b["peak_tt"]):
+        assert np.array_equal(x, y)
+    for x, y in zip(a["peak_I"], b["peak_I"]):
+        assert np.abs(x - y).max(initial=0.0) <= tol * 100.0
+
+
+def test_all_launch_shapes(gpu_lib):
     xrd = gpu_lib
     b, o = synth.mixed(n=100_000)
     b = b.subset(np.arange(600))
@@ -43,15 +55,58 @@ def test_all_launch_shapes_bit_identical(gpu_lib):
         db, co = _setup(xrd, b, o)
         sz = h.query_sizes(db, co)
         ws = xrd.workspace(sz.ws_bytes)
-        ref = _run(xrd, h, db, co, sz.n_refl, ws)
+        ref = {}
         for tile in (64, 128):
             for warps in (1, 2, 4):
                 h.set_sf_shape(tile, warps)
-                _same(ref, _run(xrd, h, db, co, sz.n_refl, ws))
+                got = _run(xrd, h, db, co, sz.n_refl, ws)
+                if tile not in ref:
+                    ref[tile] = got
+                else:
+                    _same(ref[tile], got)
+        _close(ref[64], ref[128], 0.0)  # strided tiles: different sizes, same per-reflection sums
+        for warps in (1, 2, 4):  # runs consecutive in l: the phase factor rotated along l
+            h.set_sf_shape(128, warps, 1)
+            got = _run(xrd, h, db, co, sz.n_refl, ws)
+            if "runs" not in ref:
+                ref["runs"] = got
+            else:
+                _same(ref["runs"], got)
+        _close(ref[128], ref["runs"], 2e-6)
         out = xrd.PatternBuffers(db.n_struct, sz.n_refl)
-        tile, warps = h.autotune(db, co, out, ws)
-        assert tile in (64, 128) and warps in (1, 2, 4)
-        _same(ref, _run(xrd, h, db, co, sz.n_refl, ws))
+        tile, warps, runs = h.autotune(db, co, out, ws)
+        assert tile in (64, 128) and warps in (1, 2, 4) and runs in (0, 1)
+        _same(ref["runs"] if runs else ref[tile], _run(xrd, h, db, co, sz.n_refl, ws))
+    finally:
+        h.close()
+
+
+def test_work_counts(gpu_lib):
+    """The structure-factor work counters: terms = reflections x atoms summed over the
+    batch; phase seeds: one per term with strided tiles, one per run and atom with runs
+    (between reflections / 4 and the reflection count per structure)."""
+    xrd = gpu_lib
+    b, o = synth.small(n=64)
+    h = xrd.Handle(0)
+    try:
+        db, co = _setup(xrd, b, o)
+        sz = h.query_sizes(db, co)
+        ws = xrd.workspace(sz.ws_bytes)
+        out = xrd.PatternBuffers(db.n_struct, sz.n_refl)
+        atoms = np.diff(b.atom_off)
+        co0 = xrd.make_opts(synth.Opts(o.wavelength, o.tt_min, o.tt_max, o.tt_tol, 0.0, 0), "fp32_phasefix")
+        for tile, runs in ((64, 0), (128, 0), (128, 1)):
+            h.set_sf_shape(tile, 2, runs)
+            h.pattern_batch(db, co0, out, ws)
+            res = out.to_host()
+            half = np.array([m.sum() // 2 for m in res["fam_mult"]])
+            terms, seeds, nf = h.work_counts(db, ws)
+            assert terms == int((half * atoms).sum())
+            if runs:  # one seed per run: between reflections / 4 and the reflection count
+                assert int((np.ceil(half / 4) * atoms).sum()) <= seeds < terms
+            else:
+                assert seeds == terms
+            assert nf > 0
     finally:
         h.close()
 
