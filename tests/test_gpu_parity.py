@@ -244,3 +244,42 @@ def test_mixed_full_size_sampled(gpu_lib, handle):
     picked["status"] = got["status"][idx]
     st = compare_batch(picked, ref, "fp32_phasefix", o.rel_cutoff, o.scaled)
     _report("mixed_full_sampled_fp32_phasefix", st)
+
+
+def test_runs_shape_against_oracle(gpu_lib, handle):
+    """Lanes taking runs consecutive in l (one exact phase seed per run and atom, the
+    phase factor rotated along l): every peak of small and large cells against the
+    oracle at the FP32 bar, and sampled peaks of the full large batch."""
+    try:
+        handle.set_sf_shape(128, 2, 1)
+        b, o = synth.small()
+        sub = b.subset(np.arange(0, 1024, 8))
+        st = compare_batch(gpu_lib.compute(sub, o, "fp32_phasefix", handle=handle),
+                           oracle.pattern_batch(sub, o, threads=0), "fp32_phasefix", o.rel_cutoff, o.scaled)
+        _report("runs_small_fp32_phasefix", st)
+        bl, ol = synth.large(n=256)
+        idx = np.argsort(np.diff(bl.atom_off))[:2]
+        subl = bl.subset(idx)
+        st = compare_batch(gpu_lib.compute(subl, ol, "fp32_phasefix", handle=handle),
+                           oracle.pattern_batch(subl, ol, threads=0), "fp32_phasefix", ol.rel_cutoff, ol.scaled)
+        _report("runs_large_fp32_phasefix", st)
+        o0 = _opts(ol, rel_cutoff=0.0, scaled=0)
+        got = gpu_lib.compute(bl, o0, "fp32_phasefix", handle=handle)
+        rng = np.random.default_rng(9)
+        worst = 0.0
+        for s in rng.choice(bl.n_struct, size=4, replace=False):
+            tt, I, fo = got["peak_tt"][s], got["peak_I"][s], got["peak_fam_off"][s]
+            imax = I.max()
+            _, Gs, _ = oracle.metric(bl.lattice[s])
+            picks = [p for p in rng.choice(len(tt), size=40, replace=False) if fo[p + 1] - fo[p] == 1
+                     and got["fam_mult"][s][fo[p]] == 2]
+            for p in picks[:12]:
+                h, k, l = (int(x) for x in got["fam_hkl"][s][fo[p]])
+                q = oracle.q_of(Gs, h, k, l)
+                s2, ttr, lp, d = oracle.refl(q, o0.wavelength)
+                Iref = 2 * abs(oracle.sf(bl, s, h, k, l, s2)) ** 2 * lp
+                worst = max(worst, abs(I[p] - Iref) / imax)
+                assert abs(I[p] - Iref) <= 1e-5 * imax, (s, p, I[p], Iref)
+        _report("runs_large_full_sampled_fp32_phasefix", {"max_abs_rel_to_max": worst})
+    finally:
+        handle.set_sf_shape(128, 2, 0)
