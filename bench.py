@@ -73,7 +73,7 @@ def reduce_over_ranks(terms, structures, seconds, world, device="cpu"):
 
 # DRAM bytes (read + write) of one k_sf launch on the small workload, from one ncu capture of
 # the kernel as it stands (dram__bytes_read.sum + dram__bytes_write.sum); other workloads: not captured
-SF_TRAFFIC_BYTES = {}
+SF_TRAFFIC_BYTES = {"small": 13556224}
 # SFU issue rates per SM per clock measured on this GB300 (MUFU.SIN/COS 16, MUFU.EX2 32) and the
 # maximum SM clock; the structure-factor roofline of a batch follows from its mix of operations.
 MUFU_SINCOS_PER_CLK = 16.0
