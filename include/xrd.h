@@ -192,7 +192,8 @@ int xrd_pattern_grad(xrd_handle* h, const xrd_batch* batch, const xrd_opts* opts
  * the phase factor then rotated from l to l + 1; the enumeration builds the
  * runs) -- times the stages a shape changes (count, scan, emit, structure
  * factor; the minimum of four calls) with CUDA events, synchronising `stream`,
- * and keeps the fastest shape in the handle; later calls with opts.tile = -1 use
+ * and keeps the fastest shape in the handle, then picks the enumeration
+ * kernels' threads per structure (128 or 256) the same way; later calls with opts.tile = -1 use
  * it. Writes the chosen tile, warps and runs (0 or 1) if the pointers are not
  * NULL. Returns after `stream` has been synchronised (every tuning call has
  * finished). Not capturable.
@@ -217,6 +218,10 @@ int xrd_work_counts(xrd_handle* h, const xrd_batch* batch, const void* workspace
  * warp, 1, 2 or 4 warps per CTA; warps apply to XRD_FP32_PHASEFIX; runs = 1,
  * with tile 128 and XRD_FP32_PHASEFIX only, makes lanes take runs consecutive in l). */
 int xrd_set_sf_shape(xrd_handle* h, int tile, int warps, int runs);
+
+/* Threads per structure of the enumeration kernels (128 or 256; 256 by default).
+ * The emitted order of reflections changes with it, the pattern does not. */
+int xrd_set_enum_threads(xrd_handle* h, int threads);
 
 /*
  * CUDA graph of one xrd_pattern_batch call with exactly these arguments (the

@@ -20,6 +20,7 @@ struct xrd_handle {
     const xrd::TTab* ttab = nullptr;  // 2-theta table on the handle's device
     int sf_rb = 4, sf_warps = 2;        // structure-factor launch shape (xrd_autotune)
     int sf_runs = 0;                    // lanes take runs consecutive in l (integer phase only)
+    int enum_threads = 256;             // threads per structure of the enumeration kernels (xrd_autotune)
     // side streams for the concurrent post-processing size classes (fork/join by events)
     cudaStream_t side[xrd::kPostClasses - 1] = {};
     cudaEvent_t fork = nullptr, join[xrd::kPostClasses - 1] = {};
@@ -464,6 +465,7 @@ int xrd_pattern_batch(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, cons
     sf_shape(h, o, rb, warps, runs);
     xrd::GeomArgs ga = geom_args(b, o, L, ws, cap_refl, out->totals, out->status, rb);
     ga.runs_mode = runs;
+    ga.enum_threads = h->enum_threads;
 
     const int prof = h->profiling;
     unsigned rec_flags = 0;  // inside a stream capture, stage events become timed graph nodes
@@ -621,6 +623,14 @@ int xrd_pattern_batch(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, cons
     return XRD_OK;
 }
 
+int xrd_set_enum_threads(xrd_handle* h, int threads)
+{
+    if (!h) return XRD_EINVAL;
+    if (threads != 128 && threads != 256) return fail(h, XRD_EINVAL, "enumeration threads must be 128 or 256");
+    h->enum_threads = threads;
+    return XRD_OK;
+}
+
 int xrd_work_counts(xrd_handle* h, const xrd_batch* b, const void* workspace, void* stream, int64_t* counts)
 {
     if (!h || !b || !workspace || !counts) return XRD_EINVAL;
@@ -713,6 +723,28 @@ int xrd_autotune(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, const xrd
     h->sf_rb = brb;
     h->sf_warps = bw;
     h->sf_runs = bruns;
+    // then the enumeration's CTA size with that shape: many small structures fill more SMs with
+    // 128-thread CTAs, large ones need 256 threads
+    const int keep_et = h->enum_threads;
+    float best_et = 1e30f;
+    int bet = keep_et;
+    for (int et : {256, 128}) {
+        h->enum_threads = et;
+        float t = 1e30f;
+        for (int rep = 0; rep < 5; rep++) {
+            const int rc = xrd_pattern_batch(h, b, &oo, out, workspace, ws_bytes, stream);
+            float ms[8];
+            const int m = rc == XRD_OK ? xrd_stage_times(h, ms, 8) : -rc;
+            if (rc != XRD_OK || m < 0) {
+                h->enum_threads = keep_et; h->profiling = keep_prof;
+                return finish(rc != XRD_OK ? rc : -m);
+            }
+            const float sum = m >= 6 ? ms[2] + ms[3] + ms[4] : 1e30f;  // count, scan, emit
+            if (rep > 0 && sum < t) t = sum;
+        }
+        if (t < best_et) { best_et = t; bet = et; }
+    }
+    h->enum_threads = bet;
     h->profiling = keep_prof;
     if (best_tile) *best_tile = 32 * brb;
     if (best_warps) *best_warps = bw;
@@ -854,6 +886,7 @@ int xrd_pattern_broadened(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, 
     sf_shape(h, o, rb, warps, runs);
     ga.rb = rb;
     ga.runs_mode = 0;  // the gradient path keeps strided tiles
+    ga.enum_threads = 256;
     radii(o, ga.r2min, ga.r2max, ga.rmax);
     ga.cap_refl = cap_refl;
     ga.lattice = b->lattice;

@@ -690,7 +690,8 @@ void launch_count_only(const GeomArgs& a, cudaStream_t st)
 void launch_count(const GeomArgs& a, cudaStream_t st, bool pdl)
 {
     if (a.n_struct > 0)
-        launch_k(pdl, a.runs_mode ? k_count<true> : k_count<false>, a.n_struct, 256, st, a.geo, a.r2min, a.r2max,
+        launch_k(pdl, a.runs_mode ? k_count<true> : k_count<false>, a.n_struct, a.enum_threads, st, a.geo, a.r2min,
+                 a.r2max,
                  (float)a.r2min, (float)a.r2max, a.runs_mode ? a.rb : 0, a.refl_cnt, a.run_cnt, a.tcnt);
 }
 
@@ -704,7 +705,8 @@ void launch_scan_refl(const GeomArgs& a, cudaStream_t st, bool pdl)
 void launch_emit(const GeomArgs& a, cudaStream_t st, bool pdl)
 {
     if (a.n_struct > 0)
-        launch_k(pdl, a.runs_mode ? k_emit<true> : k_emit<false>, a.n_struct, 256, st, a.geo, a.r2min, a.r2max,
+        launch_k(pdl, a.runs_mode ? k_emit<true> : k_emit<false>, a.n_struct, a.enum_threads, st, a.geo, a.r2min,
+                 a.r2max,
                  (float)a.r2min, (float)a.r2max,
                  a.runs_mode ? a.rb : 0, 32 * a.rb,
                  (const int64_t*)a.refl_off, (const int64_t*)a.run_cnt, (const int*)a.tcnt, (const int*)a.abort_flag,

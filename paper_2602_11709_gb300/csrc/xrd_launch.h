@@ -11,6 +11,7 @@ namespace xrd {
 struct GeomArgs {
     int n_struct, zmax, rb;  // rb: reflections a structure-factor lane takes (2 or 4)
     int runs_mode;           // 1: tiles of 32 runs of <= rb reflections consecutive in l; 0: tiles of 32 rb reflections
+    int enum_threads;        // threads per structure of k_count / k_emit (128 or 256; the same for both)
     int64_t n_atoms;
     double r2min, r2max, rmax;
     int64_t cap_refl;
@@ -28,7 +29,7 @@ struct GeomArgs {
     float2* astep;   // [atoms] exp(2 pi i z) of each element-sorted atom
     int64_t* refl_cnt;
     int64_t* run_cnt;  // [n_struct] runs of each structure
-    int* tcnt;       // [n_struct][2][256] per-thread reflection and run counts of the counting pass
+    int* tcnt;       // [n_struct][2][enum_threads] per-thread reflection and run counts of the counting pass
     int* runs;       // [reflections] run entries (first reflection within the structure << 3 | length)
     unsigned long long* work;  // [3] structure-factor work: terms, phase-factor seeds, tiles (k_scan_refl)
     int64_t* refl_off;

@@ -56,7 +56,7 @@ class xrd_pattern(C.Structure):
 EXPORTS = ["xrd_create", "xrd_destroy", "xrd_last_error", "xrd_query_sizes", "xrd_pattern_batch",
            "xrd_set_profiling", "xrd_stage_times", "xrd_pattern_batch_noalloc", "xrd_pattern_broadened",
            "xrd_pattern_grad", "xrd_autotune", "xrd_set_sf_shape", "xrd_graph_create", "xrd_graph_launch",
-           "xrd_graph_destroy", "xrd_work_counts"]
+           "xrd_graph_destroy", "xrd_work_counts", "xrd_set_enum_threads"]
 
 _lib = None
 
@@ -102,6 +102,8 @@ def load(path: str = LIB_PATH):
     L.xrd_set_sf_shape.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int]
     L.xrd_work_counts.argtypes = [C.c_void_p, C.POINTER(xrd_batch), C.c_void_p, C.c_void_p, C.POINTER(C.c_int64)]
     L.xrd_work_counts.restype = C.c_int
+    L.xrd_set_enum_threads.argtypes = [C.c_void_p, C.c_int]
+    L.xrd_set_enum_threads.restype = C.c_int
     L.xrd_set_sf_shape.restype = C.c_int
     L.xrd_graph_create.argtypes = [C.c_void_p, C.POINTER(xrd_batch), C.POINTER(xrd_opts), C.POINTER(xrd_pattern),
                                    C.c_void_p, C.c_size_t, C.POINTER(C.c_void_p)]
@@ -445,6 +447,9 @@ class Handle:
         out = (C.c_int64 * 3)()
         self._check(self.lib.xrd_work_counts(self.h, C.byref(b), C.c_void_p(ws.data_ptr()), _stream_ptr(stream), out))
         return int(out[0]), int(out[1]), int(out[2])
+
+    def set_enum_threads(self, threads: int):
+        self._check(self.lib.xrd_set_enum_threads(self.h, int(threads)))
 
     def set_sf_shape(self, tile: int, warps: int, runs: int = 0):
         self._check(self.lib.xrd_set_sf_shape(self.h, int(tile), int(warps), int(runs)))

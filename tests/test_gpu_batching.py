@@ -73,6 +73,10 @@ def test_all_launch_shapes(gpu_lib):
             else:
                 _same(ref["runs"], got)
         _close(ref[128], ref["runs"], 2e-6)
+        h.set_sf_shape(128, 2, 0)
+        h.set_enum_threads(128)  # another emission order, the same pattern
+        _same(ref[128], _run(xrd, h, db, co, sz.n_refl, ws))
+        h.set_enum_threads(256)
         out = xrd.PatternBuffers(db.n_struct, sz.n_refl)
         tile, warps, runs = h.autotune(db, co, out, ws)
         assert tile in (64, 128) and warps in (1, 2, 4) and runs in (0, 1)
