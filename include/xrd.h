@@ -193,7 +193,7 @@ int xrd_pattern_grad(xrd_handle* h, const xrd_batch* batch, const xrd_opts* opts
  * runs) -- times the stages a shape changes (count, scan, emit, structure
  * factor; the minimum of four calls) with CUDA events, synchronising `stream`,
  * and keeps the fastest shape in the handle, then picks the enumeration
- * kernels' threads per structure (128 or 256) the same way; later calls with opts.tile = -1 use
+ * kernels' threads per structure (64, 128 or 256) the same way; later calls with opts.tile = -1 use
  * it. Writes the chosen tile, warps and runs (0 or 1) if the pointers are not
  * NULL. Returns after `stream` has been synchronised (every tuning call has
  * finished). Not capturable.
@@ -219,7 +219,7 @@ int xrd_work_counts(xrd_handle* h, const xrd_batch* batch, const void* workspace
  * with tile 128 and XRD_FP32_PHASEFIX only, makes lanes take runs consecutive in l). */
 int xrd_set_sf_shape(xrd_handle* h, int tile, int warps, int runs);
 
-/* Threads per structure of the enumeration kernels (128 or 256; 256 by default).
+/* Threads per structure of the enumeration kernels (64, 128 or 256; 256 by default).
  * The emitted order of reflections changes with it, the pattern does not. */
 int xrd_set_enum_threads(xrd_handle* h, int threads);
 

@@ -626,7 +626,8 @@ int xrd_pattern_batch(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, cons
 int xrd_set_enum_threads(xrd_handle* h, int threads)
 {
     if (!h) return XRD_EINVAL;
-    if (threads != 128 && threads != 256) return fail(h, XRD_EINVAL, "enumeration threads must be 128 or 256");
+    if (threads != 64 && threads != 128 && threads != 256)
+        return fail(h, XRD_EINVAL, "enumeration threads must be 64, 128 or 256");
     h->enum_threads = threads;
     return XRD_OK;
 }
@@ -724,11 +725,11 @@ int xrd_autotune(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, const xrd
     h->sf_warps = bw;
     h->sf_runs = bruns;
     // then the enumeration's CTA size with that shape: many small structures fill more SMs with
-    // 128-thread CTAs, large ones need 256 threads
+    // 64- or 128-thread CTAs, large ones need 256 threads
     const int keep_et = h->enum_threads;
     float best_et = 1e30f;
     int bet = keep_et;
-    for (int et : {256, 128}) {
+    for (int et : {256, 128, 64}) {
         h->enum_threads = et;
         float t = 1e30f;
         for (int rep = 0; rep < 5; rep++) {

@@ -11,7 +11,7 @@ namespace xrd {
 struct GeomArgs {
     int n_struct, zmax, rb;  // rb: reflections a structure-factor lane takes (2 or 4)
     int runs_mode;           // 1: tiles of 32 runs of <= rb reflections consecutive in l; 0: tiles of 32 rb reflections
-    int enum_threads;        // threads per structure of k_count / k_emit (128 or 256; the same for both)
+    int enum_threads;        // threads per structure of k_count / k_emit (64, 128 or 256; the same for both)
     int64_t n_atoms;
     double r2min, r2max, rmax;
     int64_t cap_refl;
