@@ -64,6 +64,11 @@ def lib():
                                        C.c_double, C.c_int, C.c_double, _D]
         _lib.orc_broadened_grad.argtypes = [_D, C.c_long, _D, _I16, _D, _D, _D, C.c_double, C.c_long, _I32,
                                             C.c_double, C.c_double, C.c_int, C.c_double, _D, _D, _D, _D]
+        _lib.orc_augmented.argtypes = [_D, C.c_long, _D, _I16, _D, _D, _D, C.c_double, C.c_long, _I32, C.c_double,
+                                       C.c_double, C.c_int, C.c_double, C.c_double, _D, C.c_double, C.c_void_p,
+                                       C.c_double, _D]
+        _lib.orc_march_dollase.argtypes = [_D, C.c_int, C.c_int, C.c_int, _D, C.c_double]
+        _lib.orc_march_dollase.restype = C.c_double
     return _lib
 
 
@@ -245,6 +250,29 @@ def broadened(batch, s, hkl, lam, grid):
                         float(lam), len(hkl), _p(hkl, _I32), float(grid.t0), float(grid.dt), int(grid.n_pts),
                         float(grid.fwhm), _p(y, _D))
     return y
+
+
+def augmented(batch, s, hkl, lam, t0, dt, n_pts, fwhm, eta, po_dir=(0.0, 0.0, 1.0), po_r=1.0, z=None, sigma=0.0):
+    """Augmented pattern of structure s on the grid t0 + i dt (i < n_pts) for a fixed full-sphere
+    reflection list: March-Dollase about po_dir (reciprocal-lattice components), area-normalised
+    pseudo-Voigt (fwhm, eta), then y += sigma sqrt(y) z when z (standard normal draws) is given."""
+    lat, frac, Z, occ, B, coef = _struct_arrays(batch, s)
+    hkl = np.ascontiguousarray(hkl, dtype=np.int32)
+    y = np.zeros(int(n_pts))
+    d = np.ascontiguousarray(po_dir, dtype=np.float64)
+    zz = None if z is None else np.ascontiguousarray(z, dtype=np.float64)
+    lib().orc_augmented(_p(lat, _D), len(Z), _p(frac, _D), _p(Z, _I16), _p(occ, _D), _p(B, _D), _p(coef, _D),
+                        float(lam), len(hkl), _p(hkl, _I32), float(t0), float(dt), int(n_pts), float(fwhm),
+                        float(eta), _p(d, _D), float(po_r), None if zz is None else zz.ctypes.data, float(sigma),
+                        _p(y, _D))
+    return y
+
+
+def march_dollase(lat, h, k, l, po_dir, po_r):
+    _, Gs, _ = metric(lat)
+    d = np.ascontiguousarray(po_dir, dtype=np.float64)
+    return lib().orc_march_dollase(_p(np.ascontiguousarray(Gs, dtype=np.float64), _D), int(h), int(k), int(l),
+                                   _p(d, _D), float(po_r))
 
 
 def broadened_grad(batch, s, hkl, lam, grid, dLdy):

@@ -364,6 +364,48 @@ void orc_broadened(const double lat[6], long n, const double* frac, const int16_
     }
 }
 
+/* g^T Gs n for integer g and real n (Gs stored as 11, 22, 33, 12, 13, 23). */
+static double orc_dot(const double Gs[6], const double g[3], const double n[3])
+{
+    return g[0] * (Gs[0] * n[0] + Gs[3] * n[1] + Gs[4] * n[2]) + g[1] * (Gs[3] * n[0] + Gs[1] * n[1] + Gs[5] * n[2]) +
+           g[2] * (Gs[4] * n[0] + Gs[5] * n[1] + Gs[2] * n[2]);
+}
+
+double orc_march_dollase(const double Gs[6], int h, int k, int l, const double po_dir[3], double po_r)
+{
+    const double g[3] = {(double)h, (double)k, (double)l};
+    const double gn = orc_dot(Gs, g, po_dir);
+    const double gg = orc_dot(Gs, g, g), nn = orc_dot(Gs, po_dir, po_dir);
+    const double c2 = gn * gn / (gg * nn);
+    return pow(po_r * po_r * c2 + (1.0 - c2) / po_r, -1.5);
+}
+
+void orc_augmented(const double lat[6], long n, const double* frac, const int16_t* Z, const double* occ,
+                   const double* B, const double* coef, double lambda, long nr, const int32_t* hkl, double t0,
+                   double dt, int npts, double fwhm, double eta, const double po_dir[3], double po_r,
+                   const double* z, double sigma, double* y)
+{
+    double Gs[6];
+    for (int k = 0; k < npts; k++) y[k] = 0.0;
+    if (orc_metric(lat, NULL, Gs, NULL) != 0) return;
+    const double cl = eta * 2.0 / (M_PI * fwhm);
+    const double cg = (1.0 - eta) * (2.0 / fwhm) * sqrt(log(2.0) / M_PI);
+    for (long r = 0; r < nr; r++) {
+        const int h = hkl[3 * r], k = hkl[3 * r + 1], l = hkl[3 * r + 2];
+        double s2, tt, lp, Fr, Fi;
+        orc_refl(orc_q(Gs, h, k, l), lambda, &s2, &tt, &lp, NULL);
+        orc_sf(h, k, l, s2, n, frac, Z, occ, B, coef, &Fr, &Fi);
+        const double I = (Fr * Fr + Fi * Fi) * lp * orc_march_dollase(Gs, h, k, l, po_dir, po_r);
+        for (int i = 0; i < npts; i++) {
+            const double u = t0 + i * dt - tt;
+            const double x2 = 4.0 * u * u / (fwhm * fwhm);
+            y[i] += I * (cl / (1.0 + x2) + cg * exp(-log(2.0) * x2));
+        }
+    }
+    if (z)
+        for (int i = 0; i < npts; i++) y[i] += sigma * sqrt(y[i] > 0.0 ? y[i] : 0.0) * z[i];
+}
+
 /* d f(s) / d s^2 = -41.78214 sum_i a_i exp(-b_i s^2) (1 - b_i s^2). */
 static double orc_fprime(const double* coef, int Z, double s2)
 {

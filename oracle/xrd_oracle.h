@@ -106,6 +106,28 @@ void orc_broadened_grad(const double lat[6], long n, const double* frac, const i
                         double dt, int npts, double fwhm, const double* dLdy, double* dfrac, double* dB,
                         double* dlat);
 
+/*
+ * Augmented pattern (Sec. 1: training sets for ML models are patterns modified
+ * with broadening, noise and preferred orientation; the paper gives no formulas,
+ * so these are the standard textbook forms): every reflection of the
+ * fixed list adds its intensity I = |F|^2 LP, times the March-Dollase factor
+ *   P = (r^2 cos^2(alpha) + sin^2(alpha) / r)^(-3/2),
+ * alpha the angle between g and the reciprocal-lattice direction po_dir (g.n and
+ * |g|, |n| in the reciprocal metric), times an area-normalised pseudo-Voigt of
+ * full width at half maximum fwhm (degrees) and Lorentzian fraction eta,
+ *   PV(u) = eta (2 / (pi fwhm)) / (1 + 4 u^2 / fwhm^2)
+ *         + (1 - eta) (2 / fwhm) sqrt(ln 2 / pi) exp(-4 ln 2 u^2 / fwhm^2),
+ * u = t - 2theta, at every grid point (no window). Then, when z is not NULL,
+ * y_k += sigma sqrt(max(y_k, 0)) z_k (z: the caller's standard normal draws).
+ */
+void orc_augmented(const double lat[6], long n, const double* frac, const int16_t* Z, const double* occ,
+                   const double* B, const double* coef, double lambda, long nr, const int32_t* hkl, double t0,
+                   double dt, int npts, double fwhm, double eta, const double po_dir[3], double po_r,
+                   const double* z, double sigma, double* y);
+
+/* March-Dollase factor of one reflection (h, k, l) about po_dir in reciprocal metric Gs. */
+double orc_march_dollase(const double Gs[6], int h, int k, int l, const double po_dir[3], double po_r);
+
 /* Number of threads OpenMP would use for threads = 0 (all cores). */
 int orc_max_threads(void);
 
