@@ -183,6 +183,48 @@ int xrd_pattern_grad(xrd_handle* h, const xrd_batch* batch, const xrd_opts* opts
                      size_t ws_bytes, void* stream /* cudaStream_t */);
 
 /*
+ * Experimental effects of an augmented pattern (Sec. 1: synthetic training
+ * patterns for ML models carry peak broadening, noise and preferred
+ * orientation), one set per structure. Every pointer is a device array owned
+ * by the caller and read during the call only.
+ */
+typedef struct {
+    const double* fwhm;        /* [n_struct] pseudo-Voigt FWHM, degrees: 0 < fwhm <= 1e6 and 2 dt / fwhm <= 1e6 */
+    const double* eta;         /* [n_struct] Lorentzian fraction, 0 <= eta <= 1 */
+    const double* po_dir;      /* [n_struct][3] preferred-orientation direction, reciprocal-lattice components
+                                  (not zero), or NULL: no preferred orientation */
+    const double* po_r;        /* [n_struct] March-Dollase r, 1e-6 <= r <= 1e6; NULL exactly when po_dir is */
+    const float* noise_z;      /* [n_struct][n_pts] standard normal draws, or NULL: no noise */
+    const double* noise_sigma; /* [n_struct] noise scale >= 0; NULL exactly when noise_z is */
+} xrd_augment;
+
+/*
+ * Augmented pattern of every structure on the grid t_k = t0 + k dt:
+ *   y[s][k] = sum over reflections g of structure s in the 2-theta range
+ *             (g and -g both counted, unmerged, no cutoff) of
+ *             |F(g)|^2 LP P(g) PV(t_k - 2theta_g),
+ *   P(g)  = (r^2 cos^2 a + sin^2 a / r)^(-3/2)   (March-Dollase; a = angle between g
+ *           and po_dir in the reciprocal metric; P = 1 without po_dir),
+ *   PV(u) = eta (2 / (pi w)) / (1 + x^2) + (1 - eta) (2 / w) sqrt(ln 2 / pi) 2^(-x^2),
+ *           x = 2 u / w, w = fwhm (area-normalised pseudo-Voigt),
+ * then, with noise_z, y[s][k] += sigma sqrt(max(y[s][k], 0)) z[s][k]. The
+ * Lorentzian is summed over every grid point (no window); the Gaussian is
+ * skipped only where all 32 points of a warp have x^2 >= 40 (below 2^-40 of
+ * that reflection's Gaussian peak). grid.fwhm is ignored; grid.n_pts <= 2^22
+ * and every 2-theta in [tt_min, tt_max] lies within 2^22 dt of t0.
+ * opts.precision must be XRD_FP32_PHASEFIX; rel_cutoff, scaled and tt_tol are
+ * ignored. y is device float [n_struct][n_pts]; status and totals as in
+ * xrd_pattern_broadened. A structure whose effect parameters break the rules
+ * of xrd_augment gets status XRD_EINVAL and a zero row, and counts in
+ * totals[3]. Workspace as xrd_pattern_broadened (>= sizes.ws_grad_bytes); the
+ * call overwrites the state a following xrd_pattern_grad would need.
+ * Returns XRD_EINVAL for NULL or inconsistent pointers and an invalid grid.
+ */
+int xrd_pattern_augmented(xrd_handle* h, const xrd_batch* batch, const xrd_opts* opts, const xrd_grid* grid,
+                          const xrd_augment* aug, float* y, int32_t* status, int64_t* totals, void* workspace,
+                          size_t ws_bytes, void* stream /* cudaStream_t */);
+
+/*
  * Launch-shape tuning of the structure-factor kernel (the batching pattern of
  * the engine: thousands of uneven structures in one persistent launch). Runs
  * xrd_pattern_batch (same arguments) with each shape -- 2 or 4 reflections per

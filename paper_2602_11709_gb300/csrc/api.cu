@@ -1,5 +1,6 @@
 // C ABI of the powder-XRD engine: handles, argument validation, workspace
 // layout and the launch sequence of one pattern batch.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -125,7 +126,7 @@ Layout layout(int64_t n, int64_t natoms, int zmax, int64_t R)
 struct LayoutG {
     size_t geo, refl_cnt, run_cnt, tcnt, refl_off, tile_off, order, atom_bad, tile_tab, flags, coef32, atom32, atom64,
         astep;
-    size_t q, key, runs, Fx, Ig, tb, td, perm, U, V;
+    size_t q, key, runs, Fx, Ig, tb, td, perm, U, V, rec;
     size_t total;
 };
 
@@ -158,6 +159,7 @@ LayoutG layout_grad(int64_t n, int64_t natoms, int zmax, int64_t R)
     L.perm = take(4 * R);
     L.U = take(4 * R);
     L.V = take(4 * R);
+    L.rec = take(16 * n);
     L.total = o;
     return L;
 }
@@ -858,27 +860,13 @@ static xrd::GradArgs grad_args(xrd_handle* h, const xrd_batch* b, const xrd_grid
     return a;
 }
 
-int xrd_pattern_broadened(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, const xrd_grid* grid, float* y,
-                          int32_t* status, int64_t* totals, void* workspace, size_t ws_bytes, void* stream)
+// Geometry and structure factors of the broadened and augmented paths, one
+// stream: grad = true keeps strided tiles and stores F, dF/ds^2 and I for the
+// adjoint; grad = false runs the tuned pattern shape and stores I only.
+static void launch_front(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, const LayoutG& L, char* ws,
+                         int64_t cap_refl, int32_t* status, int64_t* totals, cudaStream_t st, bool grad)
 {
-    if (!h) return XRD_EINVAL;
-    h->err.clear();
-    int rc = check_batch(h, b);
-    if (rc) return rc;
-    if ((rc = check_opts(h, o))) return rc;
-    if (o->precision != XRD_FP32_PHASEFIX) return fail(h, XRD_EINVAL, "the broadened path runs XRD_FP32_PHASEFIX");
-    int W;
-    double sigma;
-    if ((rc = check_grid(h, grid, W, sigma))) return rc;
     const int64_t n = b->n_struct;
-    if (!totals || (n > 0 && (!y || !status))) return fail(h, XRD_EINVAL, "an output pointer is NULL");
-    if (!workspace || ((uintptr_t)workspace & 255)) return fail(h, XRD_EINVAL, "workspace must be 256-byte aligned");
-    const int64_t cap_refl = refl_capacity_grad(n, b->n_atoms, b->zmax, ws_bytes);
-    if (cap_refl < 0) return fail(h, XRD_ECAPACITY, "workspace smaller than the per-structure part");
-    DeviceGuard dg(h->device);
-    cudaStream_t st = (cudaStream_t)stream;
-    char* ws = (char*)workspace;
-    const LayoutG L = layout_grad(n, b->n_atoms, b->zmax, cap_refl);
     xrd::GeomArgs ga{};
     ga.n_struct = (int)n;
     ga.zmax = b->zmax;
@@ -886,8 +874,8 @@ int xrd_pattern_broadened(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, 
     int rb, warps, runs;
     sf_shape(h, o, rb, warps, runs);
     ga.rb = rb;
-    ga.runs_mode = 0;  // the gradient path keeps strided tiles
-    ga.enum_threads = 256;
+    ga.runs_mode = grad ? 0 : runs;
+    ga.enum_threads = grad ? 256 : h->enum_threads;
     radii(o, ga.r2min, ga.r2max, ga.rmax);
     ga.cap_refl = cap_refl;
     ga.lattice = b->lattice;
@@ -905,7 +893,7 @@ int xrd_pattern_broadened(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, 
     ga.run_cnt = (int64_t*)(ws + L.run_cnt);
     ga.tcnt = (int*)(ws + L.tcnt);
     ga.runs = (int*)(ws + L.runs);
-    ga.astep = (float2*)(ws + L.astep);
+    ga.astep = ga.runs_mode ? (float2*)(ws + L.astep) : nullptr;
     ga.work = (unsigned long long*)(ws + L.flags + kWorkOffset);
     ga.refl_off = (int64_t*)(ws + L.refl_off);
     ga.tile_off = (int*)(ws + L.tile_off);
@@ -932,7 +920,8 @@ int xrd_pattern_broadened(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, 
     sa.zmax = b->zmax;
     sa.tile = 32 * rb;
     sa.rb = rb;
-    sa.warps = 2;
+    sa.warps = grad ? 2 : warps;
+    sa.runs_mode = ga.runs_mode;
     sa.run_cnt = ga.run_cnt;
     sa.runs = ga.runs;
     sa.astep = ga.astep;
@@ -950,14 +939,111 @@ int xrd_pattern_broadened(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, 
     sa.atom64 = ga.atom64;
     sa.q = ga.q;
     sa.key = ga.key;
-    sa.Fx = (float4*)(ws + L.Fx);
-    sa.Ig = (float*)(ws + L.Ig);
+    if (grad) {
+        sa.Fx = (float4*)(ws + L.Fx);
+        sa.Ig = (float*)(ws + L.Ig);
+    } else {
+        sa.If = (float*)(ws + L.Ig);
+    }
     xrd::launch_sf(sa, st, true);
+}
+
+int xrd_pattern_broadened(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, const xrd_grid* grid, float* y,
+                          int32_t* status, int64_t* totals, void* workspace, size_t ws_bytes, void* stream)
+{
+    if (!h) return XRD_EINVAL;
+    h->err.clear();
+    int rc = check_batch(h, b);
+    if (rc) return rc;
+    if ((rc = check_opts(h, o))) return rc;
+    if (o->precision != XRD_FP32_PHASEFIX) return fail(h, XRD_EINVAL, "the broadened path runs XRD_FP32_PHASEFIX");
+    int W;
+    double sigma;
+    if ((rc = check_grid(h, grid, W, sigma))) return rc;
+    const int64_t n = b->n_struct;
+    if (!totals || (n > 0 && (!y || !status))) return fail(h, XRD_EINVAL, "an output pointer is NULL");
+    if (!workspace || ((uintptr_t)workspace & 255)) return fail(h, XRD_EINVAL, "workspace must be 256-byte aligned");
+    const int64_t cap_refl = refl_capacity_grad(n, b->n_atoms, b->zmax, ws_bytes);
+    if (cap_refl < 0) return fail(h, XRD_ECAPACITY, "workspace smaller than the per-structure part");
+    DeviceGuard dg(h->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    char* ws = (char*)workspace;
+    const LayoutG L = layout_grad(n, b->n_atoms, b->zmax, cap_refl);
+    launch_front(h, b, o, L, ws, cap_refl, status, totals, st, true);
     xrd::GradArgs gr = grad_args(h, b, grid, W, sigma, o, L, ws);
     gr.y = y;
     xrd::launch_broaden(gr, st);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(h, e, "xrd_pattern_broadened launch");
+    return XRD_OK;
+}
+
+int xrd_pattern_augmented(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, const xrd_grid* grid,
+                          const xrd_augment* aug, float* y, int32_t* status, int64_t* totals, void* workspace,
+                          size_t ws_bytes, void* stream)
+{
+    if (!h) return XRD_EINVAL;
+    h->err.clear();
+    int rc = check_batch(h, b);
+    if (rc) return rc;
+    if ((rc = check_opts(h, o))) return rc;
+    if (o->precision != XRD_FP32_PHASEFIX) return fail(h, XRD_EINVAL, "the augmented path runs XRD_FP32_PHASEFIX");
+    if (!grid) return fail(h, XRD_EINVAL, "grid is NULL");
+    if (!(grid->dt > 0.0) || !std::isfinite(grid->dt) || !std::isfinite(grid->t0))
+        return fail(h, XRD_EINVAL, "grid dt/t0 invalid");
+    if (grid->n_pts <= 0 || grid->n_pts > (1 << 22) || grid->reserved != 0)
+        return fail(h, XRD_EINVAL, "grid n_pts must be in 1 .. 2^22, reserved 0");
+    const double reach = std::max(std::fabs(o->tt_min - grid->t0), std::fabs(o->tt_max - grid->t0)) / grid->dt;
+    if (!(reach < (double)(1 << 22))) return fail(h, XRD_EINVAL, "2-theta range more than 2^22 grid steps from t0");
+    const int64_t n = b->n_struct;
+    if (!aug || !totals || (n > 0 && (!y || !status))) return fail(h, XRD_EINVAL, "an output pointer is NULL");
+    if (n > 0 && (!aug->fwhm || !aug->eta)) return fail(h, XRD_EINVAL, "aug fwhm and eta are required");
+    if ((aug->po_dir == nullptr) != (aug->po_r == nullptr))
+        return fail(h, XRD_EINVAL, "aug po_dir and po_r must be both set or both NULL");
+    if ((aug->noise_z == nullptr) != (aug->noise_sigma == nullptr))
+        return fail(h, XRD_EINVAL, "aug noise_z and noise_sigma must be both set or both NULL");
+    const int64_t nblk = (grid->n_pts + 1023) / 1024;
+    if (n * nblk > INT32_MAX) return fail(h, XRD_EINVAL, "n_struct x grid blocks exceeds the launch limit");
+    if (!workspace || ((uintptr_t)workspace & 255)) return fail(h, XRD_EINVAL, "workspace must be 256-byte aligned");
+    const int64_t cap_refl = refl_capacity_grad(n, b->n_atoms, b->zmax, ws_bytes);
+    if (cap_refl < 0) return fail(h, XRD_ECAPACITY, "workspace smaller than the per-structure part");
+    DeviceGuard dg(h->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    char* ws = (char*)workspace;
+    const LayoutG L = layout_grad(n, b->n_atoms, b->zmax, cap_refl);
+    launch_front(h, b, o, L, ws, cap_refl, status, totals, st, false);
+    xrd::AugArgs a{};
+    a.n_struct = (int)n;
+    a.n_pts = grid->n_pts;
+    a.t0 = grid->t0;
+    a.dt = grid->dt;
+    const double l2d = o->lambda * o->lambda * 0.25;
+    a.l2h = (float)l2d;
+    a.l2l = (float)(l2d - (double)a.l2h);
+    a.ttab = h->ttab;
+    a.geo = (const xrd::Geo*)(ws + L.geo);
+    a.refl_off = (const int64_t*)(ws + L.refl_off);
+    a.abort_flag = (const int*)(ws + L.flags);
+    a.q = (const double*)(ws + L.q);
+    a.key = (const uint32_t*)(ws + L.key);
+    a.Ig = (const float*)(ws + L.Ig);
+    a.fwhm = aug->fwhm;
+    a.eta = aug->eta;
+    a.po_dir = aug->po_dir;
+    a.po_r = aug->po_r;
+    a.noise_z = aug->noise_z;
+    a.noise_sigma = aug->noise_sigma;
+    a.rb = (int*)(ws + L.tb);
+    a.rd = (float*)(ws + L.td);
+    a.aL = (float*)(ws + L.U);
+    a.aG = (float*)(ws + L.V);
+    a.rec = (int4*)(ws + L.rec);
+    a.status = status;
+    a.totals = totals;
+    a.y = y;
+    xrd::launch_aug(a, st);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(h, e, "xrd_pattern_augmented launch");
     return XRD_OK;
 }
 

@@ -158,6 +158,34 @@ struct GradArgs {
     float* d_lat;
 };
 
+struct AugArgs {
+    int n_struct, n_pts;
+    double t0, dt;
+    float l2h, l2l;  // lambda^2 / 4 as two floats
+    const TTab* ttab;
+    const Geo* geo;
+    const int64_t* refl_off;
+    const int* abort_flag;
+    const double* q;
+    const uint32_t* key;
+    const float* Ig;  // |F|^2 LP per reflection (one Friedel member)
+    // effect parameters (device, per structure; po_* and noise_* may be nullptr)
+    const double* fwhm;
+    const double* eta;
+    const double* po_dir;
+    const double* po_r;
+    const float* noise_z;
+    const double* noise_sigma;
+    int* rb;     // grid cell of each reflection's 2theta
+    float* rd;   // offset of 2theta within the cell, times 2 dt / fwhm
+    float* aL;   // Lorentzian amplitude 2 I P eta 2 / (pi fwhm)
+    float* aG;   // Gaussian amplitude 2 I P (1 - eta) (2 / fwhm) sqrt(ln 2 / pi)
+    int4* rec;   // per structure: reflections, bits of 2 dt / fwhm (float), flags (1 Lorentzian, 2 Gaussian, 4 valid)
+    int32_t* status;
+    int64_t* totals;
+    float* y;    // [n_struct][n_pts]
+};
+
 // pdl: launch as a programmatic dependent of the previous kernel on st (only
 // when that kernel directly precedes it on the stream)
 void launch_prep(const GeomArgs& a, cudaStream_t st, bool pdl);
@@ -173,10 +201,11 @@ void launch_sf(const SfArgs& a, cudaStream_t st, bool pdl);
 size_t post_smem_bytes(int cap);
 void launch_post(const PostArgs& a, const cudaStream_t* st);  // st[kPostClasses]
 void launch_compact(const CompactArgs& a, cudaStream_t st);
-const TTab* init_tables(cudaStream_t st);
+const TTab* init_tables(cudaStream_t st);  // fills the 2-theta table, returns its device address
 size_t broaden_smem_bytes(int n_pts, int W);
 void launch_broaden(const GradArgs& a, cudaStream_t st);
-void launch_grad(const GradArgs& a, cudaStream_t st);  // fills the 2-theta table, returns its device address
+void launch_grad(const GradArgs& a, cudaStream_t st);
+void launch_aug(const AugArgs& a, cudaStream_t st);   // per-reflection amplitudes, then the profile sums
 
 // handle accessors for entry points defined outside api.cu
 int handle_device(const xrd_handle* h);

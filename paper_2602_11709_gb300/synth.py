@@ -15,6 +15,10 @@ The five workloads stand in for the paper's MC3D and COD benchmark sets
 * ``mixed``    -- 100 000 cells, lognormal atom counts (median 20) and edges
                   (median 7 A): spans all reflection-count bins of Sec. 4.2.
 * ``grad``     -- 512 cells of 8-128 atoms for the broadened-pattern gradient.
+* ``augment``  -- per-structure experimental effects of ML training patterns
+                  (Sec. 1): pseudo-Voigt FWHM 0.05-0.3 deg and mixing 0-1,
+                  March-Dollase r 0.6-1.4 about a low-index direction, noise
+                  scale 0-1 with standard normal draws.
 
 All arrays follow the C ABI layout: ``lattice`` float64 [n, 6] (a, b, c in
 angstrom; alpha, beta, gamma in degrees), ``atom_off`` int64 [n + 1],
@@ -182,6 +186,26 @@ def grad(seed: int = 5, n: int = 512) -> tuple[Batch, Batch, Opts, Grid]:
     ta = ang + rng.uniform(-0.2, 0.2, size=ang.shape)
     target = Batch(np.hstack([te, ta]), off.copy(), tf, Z.copy(), occ.copy(), tB, coef)
     return base, target, Opts(CU_KA, 5.0, 90.0, 1e-5, 0.0, 0), Grid()
+
+
+@dataclasses.dataclass
+class Augment:
+    """Experimental effects per structure: fwhm, eta, po_r, noise_sigma float64 [n]; po_dir float64 [n, 3]
+    (reciprocal-lattice components); z float32 [n, n_pts] standard normal draws."""
+    fwhm: np.ndarray
+    eta: np.ndarray
+    po_dir: np.ndarray
+    po_r: np.ndarray
+    noise_sigma: np.ndarray
+    z: np.ndarray
+
+
+def augment(n: int, n_pts: int, seed: int = 6) -> Augment:
+    rng = np.random.default_rng(seed)
+    d = rng.integers(-2, 3, size=(n, 3)).astype(np.float64)
+    d[~d.any(axis=1), 2] = 1.0  # never the zero direction
+    return Augment(rng.uniform(0.05, 0.3, n), rng.uniform(0.0, 1.0, n), d, rng.uniform(0.6, 1.4, n),
+                   rng.uniform(0.0, 1.0, n), rng.standard_normal((n, n_pts)).astype(np.float32))
 
 
 def random_cell(rng: np.random.Generator, n_atoms: int, edge=(3.0, 15.0), bmax=2.0, zs=None) -> Batch:

@@ -46,6 +46,11 @@ class xrd_grid(C.Structure):
                 ("reserved", C.c_int32)]
 
 
+class xrd_augment(C.Structure):
+    _fields_ = [("fwhm", C.c_void_p), ("eta", C.c_void_p), ("po_dir", C.c_void_p), ("po_r", C.c_void_p),
+                ("noise_z", C.c_void_p), ("noise_sigma", C.c_void_p)]
+
+
 class xrd_pattern(C.Structure):
     _fields_ = [("cap_peaks", C.c_int64), ("cap_fam", C.c_int64), ("peak_off", C.c_void_p),
                 ("two_theta", C.c_void_p), ("intensity", C.c_void_p), ("d_hkl", C.c_void_p),
@@ -56,7 +61,7 @@ class xrd_pattern(C.Structure):
 EXPORTS = ["xrd_create", "xrd_destroy", "xrd_last_error", "xrd_query_sizes", "xrd_pattern_batch",
            "xrd_set_profiling", "xrd_stage_times", "xrd_pattern_batch_noalloc", "xrd_pattern_broadened",
            "xrd_pattern_grad", "xrd_autotune", "xrd_set_sf_shape", "xrd_graph_create", "xrd_graph_launch",
-           "xrd_graph_destroy", "xrd_work_counts", "xrd_set_enum_threads"]
+           "xrd_graph_destroy", "xrd_work_counts", "xrd_set_enum_threads", "xrd_pattern_augmented"]
 
 _lib = None
 
@@ -95,6 +100,10 @@ def load(path: str = LIB_PATH):
                                    C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t,
                                    C.c_void_p]
     L.xrd_pattern_grad.restype = C.c_int
+    L.xrd_pattern_augmented.argtypes = [C.c_void_p, C.POINTER(xrd_batch), C.POINTER(xrd_opts), C.POINTER(xrd_grid),
+                                        C.POINTER(xrd_augment), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                        C.c_size_t, C.c_void_p]
+    L.xrd_pattern_augmented.restype = C.c_int
     L.xrd_autotune.argtypes = [C.c_void_p, C.POINTER(xrd_batch), C.POINTER(xrd_opts), C.POINTER(xrd_pattern),
                                C.c_void_p, C.c_size_t, C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                C.POINTER(C.c_int32)]
@@ -418,6 +427,19 @@ class Handle:
         """Gaussian-broadened patterns y [n_struct][n_pts] (float32); ws keeps the state for pattern_grad."""
         b = db.c()
         self._check(self.lib.xrd_pattern_broadened(self.h, C.byref(b), C.byref(opts), C.byref(grid),
+                                                   C.c_void_p(y.data_ptr()), C.c_void_p(status.data_ptr()),
+                                                   C.c_void_p(totals.data_ptr()), C.c_void_p(ws.data_ptr()),
+                                                   C.c_size_t(ws.numel() * ws.element_size()), _stream_ptr(stream)))
+
+    def pattern_augmented(self, db: DeviceBatch, opts: xrd_opts, grid: xrd_grid, fwhm, eta, y, status, totals, ws,
+                          po_dir=None, po_r=None, noise_z=None, noise_sigma=None, stream=None):
+        """Augmented patterns y [n_struct][n_pts] (float32): per-structure pseudo-Voigt (fwhm, eta: float64
+        device tensors [n_struct]), March-Dollase (po_dir [n_struct][3], po_r [n_struct]) and noise
+        (noise_z float32 [n_struct][n_pts] standard normal draws, noise_sigma float64 [n_struct])."""
+        b = db.c()
+        ptr = lambda t: None if t is None else t.data_ptr()  # noqa: E731
+        aug = xrd_augment(ptr(fwhm), ptr(eta), ptr(po_dir), ptr(po_r), ptr(noise_z), ptr(noise_sigma))
+        self._check(self.lib.xrd_pattern_augmented(self.h, C.byref(b), C.byref(opts), C.byref(grid), C.byref(aug),
                                                    C.c_void_p(y.data_ptr()), C.c_void_p(status.data_ptr()),
                                                    C.c_void_p(totals.data_ptr()), C.c_void_p(ws.data_ptr()),
                                                    C.c_size_t(ws.numel() * ws.element_size()), _stream_ptr(stream)))

@@ -47,6 +47,7 @@ int main(void) {
          sizeof(xrd_sizes), sizeof(xrd_pattern));
   F(xrd_batch, n_atoms); F(xrd_batch, coef); F(xrd_opts, scaled); F(xrd_opts, reserved);
   F(xrd_sizes, ws_bytes); F(xrd_pattern, fam_off); F(xrd_pattern, totals);
+  printf("xrd_augment %zu\n", sizeof(xrd_augment)); F(xrd_augment, po_r); F(xrd_augment, noise_sigma);
   return 0;
 }
 '''
@@ -68,6 +69,9 @@ int main(void) {
     assert int(got["xrd_sizes.ws_bytes"]) == xrd.xrd_sizes.ws_bytes.offset
     assert int(got["xrd_pattern.fam_off"]) == xrd.xrd_pattern.fam_off.offset
     assert int(got["xrd_pattern.totals"]) == xrd.xrd_pattern.totals.offset
+    assert int(got["xrd_augment"]) == C.sizeof(xrd.xrd_augment)
+    assert int(got["xrd_augment.po_r"]) == xrd.xrd_augment.po_r.offset
+    assert int(got["xrd_augment.noise_sigma"]) == xrd.xrd_augment.noise_sigma.offset
 
 
 def test_create_without_gpu_fails_cleanly(lib):
