@@ -208,9 +208,9 @@ typedef struct {
  *   PV(u) = eta (2 / (pi w)) / (1 + x^2) + (1 - eta) (2 / w) sqrt(ln 2 / pi) 2^(-x^2),
  *           x = 2 u / w, w = fwhm (area-normalised pseudo-Voigt),
  * then, with noise_z, y[s][k] += sigma sqrt(max(y[s][k], 0)) z[s][k]. The
- * Lorentzian is summed over every grid point (no window); the Gaussian is
- * skipped only where all 32 points of a warp have x^2 >= 40 (below 2^-40 of
- * that reflection's Gaussian peak). grid.fwhm is ignored; grid.n_pts <= 2^22
+ * Lorentzian is summed over every grid point (no window); a reflection's
+ * Gaussian is skipped only on runs of 256 consecutive grid points where it
+ * stays below 2^-40 of its peak (x^2 >= 40). grid.fwhm is ignored; grid.n_pts <= 2^22
  * and every 2-theta in [tt_min, tt_max] lies within 2^22 dt of t0.
  * opts.precision must be XRD_FP32_PHASEFIX; rel_cutoff, scaled and tt_tol are
  * ignored. y is device float [n_struct][n_pts]; status and totals as in

@@ -126,7 +126,7 @@ Layout layout(int64_t n, int64_t natoms, int zmax, int64_t R)
 struct LayoutG {
     size_t geo, refl_cnt, run_cnt, tcnt, refl_off, tile_off, order, atom_bad, tile_tab, flags, coef32, atom32, atom64,
         astep;
-    size_t q, key, runs, Fx, Ig, tb, td, perm, U, V, rec;
+    size_t q, key, runs, Fx, Ig, tb, td, perm, U, V, aorder;
     size_t total;
 };
 
@@ -159,7 +159,7 @@ LayoutG layout_grad(int64_t n, int64_t natoms, int zmax, int64_t R)
     L.perm = take(4 * R);
     L.U = take(4 * R);
     L.V = take(4 * R);
-    L.rec = take(16 * n);
+    L.aorder = take(4 * n);
     L.total = o;
     return L;
 }
@@ -1017,6 +1017,7 @@ int xrd_pattern_augmented(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, 
     a.n_pts = grid->n_pts;
     a.t0 = grid->t0;
     a.dt = grid->dt;
+    a.inv_dt = 1.0 / grid->dt;
     const double l2d = o->lambda * o->lambda * 0.25;
     a.l2h = (float)l2d;
     a.l2l = (float)(l2d - (double)a.l2h);
@@ -1033,11 +1034,7 @@ int xrd_pattern_augmented(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, 
     a.po_r = aug->po_r;
     a.noise_z = aug->noise_z;
     a.noise_sigma = aug->noise_sigma;
-    a.rb = (int*)(ws + L.tb);
-    a.rd = (float*)(ws + L.td);
-    a.aL = (float*)(ws + L.U);
-    a.aG = (float*)(ws + L.V);
-    a.rec = (int4*)(ws + L.rec);
+    a.aorder = (int*)(ws + L.aorder);
     a.status = status;
     a.totals = totals;
     a.y = y;

@@ -160,7 +160,7 @@ struct GradArgs {
 
 struct AugArgs {
     int n_struct, n_pts;
-    double t0, dt;
+    double t0, dt, inv_dt;
     float l2h, l2l;  // lambda^2 / 4 as two floats
     const TTab* ttab;
     const Geo* geo;
@@ -176,11 +176,7 @@ struct AugArgs {
     const double* po_r;
     const float* noise_z;
     const double* noise_sigma;
-    int* rb;     // grid cell of each reflection's 2theta
-    float* rd;   // offset of 2theta within the cell, times 2 dt / fwhm
-    float* aL;   // Lorentzian amplitude 2 I P eta 2 / (pi fwhm)
-    float* aG;   // Gaussian amplitude 2 I P (1 - eta) (2 / fwhm) sqrt(ln 2 / pi)
-    int4* rec;   // per structure: reflections, bits of 2 dt / fwhm (float), flags (1 Lorentzian, 2 Gaussian, 4 valid)
+    int* aorder; // [n_struct] structures by reflection count, largest first
     int32_t* status;
     int64_t* totals;
     float* y;    // [n_struct][n_pts]

@@ -3,6 +3,7 @@
 Bar: every grid point within 1e-5 of the structure's largest oracle value
 (FP32 structure factors and FP32 sums over every (point, reflection) pair;
 the Gaussian component is skipped on the GPU only below 2^-40 of its peak).
+Repeated calls give identical bytes (fixed summation order).
 """
 import numpy as np
 import pytest
@@ -66,6 +67,7 @@ def test_augmented_matches_oracle(gpu_lib, handle, po, noise):
     b = base.subset(np.array([0, 1, 2, 3, 4, 5, 6, 7]))
     aug = synth.augment(b.n_struct, grid.n_pts)
     aug.eta[0], aug.eta[1] = 0.0, 1.0  # pure Gaussian, pure Lorentzian
+    aug.fwhm[2] = 0.6 * grid.dt        # undersampled peaks: 2 dt / fwhm > 1
     y, status, totals = _run(gpu_lib, handle, b, o, grid, aug, po, noise)
     assert np.all(status == 0) and totals[3] == 0
     for s in range(b.n_struct):
@@ -172,3 +174,12 @@ def test_small_workload_sampled_structures(gpu_lib, handle):
     assert np.all(np.isfinite(y))
     for s in (0, 17, 511, 1023):
         _check(y[s], _ref(b, s, o, grid, aug), s)
+
+
+def test_repeated_calls_are_bitwise_identical(gpu_lib, handle):
+    base, _, o, grid = synth.grad()
+    b = base.subset(np.arange(20, 28))
+    aug = synth.augment(b.n_struct, grid.n_pts, seed=12)
+    y0, _, _ = _run(gpu_lib, handle, b, o, grid, aug)
+    y1, _, _ = _run(gpu_lib, handle, b, o, grid, aug)
+    assert np.array_equal(y0.view(np.uint32), y1.view(np.uint32))
