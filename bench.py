@@ -29,6 +29,10 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "structure-factor terms/s and patterns/s at 1 GB300 (FP32 vs FP64) vs SFU roofline"
+AUG_METRIC = "augmented patterns/s (pseudo-Voigt, March-Dollase, noise; 4096-point grid) at 1 GB300 vs MUFU roofline"
+AUG_GRID = (0.0, 90.0 / 4095.0, 4096)  # t0, dt (degrees), points: the workload's 2-theta range
+AUG_LAUNCHES = 10  # prep, coef, atoms, order, count, scan, emit, structure factor, structure order, profile sum
+
 WORKLOADS = {
     "small": ("small: 1024 seeded P1 cells, a,b,c U[3,15] A, angles U[60,120] deg, 1-64 atoms, Z U{1..83}, "
               "B U[0,2] A^2, occ 1, lambda 1.54184 A, 2theta 0-90 deg"),
@@ -395,6 +399,174 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def cpu_oracle_augmented_rate(b, o, aug, budget_s=12.0):
+    """Oracle augmented pattern (FP64, full sphere, every grid point) over a bounded sample."""
+    import oracle
+    t0g, dtg, npts = AUG_GRID
+    t0 = time.perf_counter()
+    done = 0
+    s = 0
+    while time.perf_counter() - t0 < budget_s:
+        hkl, _ = oracle.enumerate_refl(b.lattice[s], o)
+        oracle.augmented(b, s, hkl, o.wavelength, t0g, dtg, npts, aug.fwhm[s], aug.eta[s], aug.po_dir[s],
+                         aug.po_r[s], z=aug.z[s].astype(np.float64), sigma=aug.noise_sigma[s])
+        done += 1
+        s = (s + 1) % b.n_struct
+    dt = time.perf_counter() - t0
+    return {"patterns_per_s": done / dt, "structures": done, "seconds": dt, "cores": 1}
+
+
+def run_augmented(args):
+    """The augmented-pattern path (xrd_pattern_augmented) on the workload's batch: one step = the
+    geometry, structure factors and the pseudo-Voigt / March-Dollase / noise profile of every
+    structure on the 4096-point grid."""
+    import torch
+    from paper_2602_11709_gb300 import synth, xrd
+
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        b, o = load_workload(args.workload)
+        aug = synth.augment(b.n_struct, AUG_GRID[2], seed=7)
+        per_step = max(2.0, min(20.0, 100.0 / max(args.steps + args.warmup, 1)))
+        rates = [cpu_oracle_augmented_rate(b, o, aug, per_step) for _ in range(args.warmup + args.steps)]
+        pps = float(np.mean([r["patterns_per_s"] for r in rates[args.warmup:]]))
+        print(json.dumps({"impl": "reference", "metric": AUG_METRIC, "value": pps, "unit": "patterns/s",
+                          "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                          "ms_per_step": 1e3 * b.n_struct / pps, "higher_is_better": True, "scaling": "weak",
+                          "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                          "config": {"workload": WORKLOADS[args.workload], "path": "augmented"},
+                          "cpu_baseline": {"value": pps, "unit": "patterns/s", "cores": 1, "kind": "oracle",
+                                           "sample": "consecutive structures, %.0f s per step" % per_step},
+                          "e2e": {"value": pps, "unit": "patterns/s", "h2d_bytes_per_step": 0,
+                                  "d2h_bytes_per_step": 0}}), flush=True)
+        return
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = local if torch.cuda.is_available() else 0
+    torch.cuda.set_device(dev)
+    b, o = load_workload(args.workload, world)
+    if world > 1:
+        lo, hi = shard_bounds(b.n_struct, rank, world)
+        b = b.subset(np.arange(lo, hi))
+    aug = synth.augment(b.n_struct, AUG_GRID[2], seed=7)
+    d = "cuda:%d" % dev
+    h = xrd.Handle(dev)
+    db = xrd.DeviceBatch.from_host(b, d)
+    co = xrd.make_opts(o, "fp32_phasefix")
+    grid = xrd.make_grid(synth.Grid(t0=AUG_GRID[0], dt=AUG_GRID[1], n_pts=AUG_GRID[2]))
+    sz = h.query_sizes(db, co)
+    ws = xrd.workspace(sz.ws_grad_bytes, d)
+    tuned = h.autotune(db, co, xrd.PatternBuffers(b.n_struct, sz.n_refl, d), xrd.workspace(sz.ws_bytes, d)) \
+        if not args.no_tune else None
+    host = {k: torch.from_numpy(np.ascontiguousarray(getattr(aug, k))).pin_memory()
+            for k in ("fwhm", "eta", "po_dir", "po_r", "noise_sigma", "z")}
+    dv = {k: v.to(d) for k, v in host.items()}
+    n, npts = b.n_struct, AUG_GRID[2]
+    y = torch.empty((n, npts), dtype=torch.float32, device=d)
+    status = torch.zeros(n, dtype=torch.int32, device=d)
+    totals = torch.zeros(4, dtype=torch.int64, device=d)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=d)
+    stream = torch.cuda.current_stream()
+
+    def call(t):
+        h.pattern_augmented(db, co, grid, t["fwhm"], t["eta"], y, status, totals, ws, po_dir=t["po_dir"],
+                            po_r=t["po_r"], noise_z=t["z"], noise_sigma=t["noise_sigma"])
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+    h.set_profiling(2)
+    clocks = ClockSampler(dev)
+    clocks.start()
+    clocks.wait_first()
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        call(dv)
+    barrier()
+    assert int(totals[3]) == 0 and int(status.abs().sum()) == 0
+    R = int(totals[0])
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    sum_ms = []
+    for i in range(args.steps):
+        flush.fill_(1.0)
+        ev[i][0].record(stream)
+        call(dv)
+        ev[i][1].record(stream)
+        sum_ms.append(h.stage_times()["profile_sum"])
+    barrier()
+    ck = clocks.stop()
+    h.set_profiling(0)
+    step_s = sum(a.elapsed_time(c) for a, c in ev) / 1e3
+    tot_terms, tot_structs, tot_s = reduce_over_ranks(R * npts, n, step_s, world, d)
+    pps = tot_structs * args.steps / tot_s
+    # end to end: every step copies its inputs (batch arrays and effect parameters, noise draws
+    # included) from pinned host memory, runs the call and reads the patterns back to pinned memory
+    hb = {k: torch.from_numpy(np.ascontiguousarray(getattr(b, k))).pin_memory()
+          for k in ("lattice", "atom_off", "frac", "Z", "occ", "B", "coef")}
+    y_host = torch.empty((n, npts), dtype=torch.float32).pin_memory()
+    bytes_in = sum(t.numel() * t.element_size() for t in list(hb.values()) + list(host.values()))
+    bytes_out = y_host.numel() * 4
+
+    def e2e_step():
+        for k, t in hb.items():
+            getattr(db, k).copy_(t, non_blocking=True)
+        for k, t in host.items():
+            dv[k].copy_(t, non_blocking=True)
+        call(dv)
+        y_host.copy_(y, non_blocking=True)
+    for _ in range(args.warmup):
+        e2e_step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    _, e2e_structs, e2e_max = reduce_over_ranks(R * npts, n, e2e_s, world, d)
+    if rank == 0:
+        sum_s = float(np.mean(sum_ms)) / 1e3
+        # profile sum: one MUFU reciprocal per two (point, reflection) pairs, 16 MUFU/clk/SM
+        peak_terms = 2.0 * 16.0 * 152.0 * SM_MAX_MHZ * 1e6
+        cpu = None
+        if world == 1 and args.cpu_seconds > 0:
+            r = cpu_oracle_augmented_rate(b, o, aug, args.cpu_seconds)
+            cpu = {"value": r["patterns_per_s"], "unit": "patterns/s", "cores": r["cores"], "kind": "oracle",
+                   "sample": "%d structures of the batch in order, %.1f s" % (r["structures"], r["seconds"])}
+        line = {
+            "metric": AUG_METRIC, "value": pps, "unit": "patterns/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (i32 phase)", "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.workload], "path": "augmented", "n_struct": n,
+                       "grid": {"t0": AUG_GRID[0], "dt": AUG_GRID[1], "n_pts": npts},
+                       "effects": "fwhm U[0.05,0.3] deg, eta U[0,1], March-Dollase r U[0.6,1.4] about a "
+                                  "low-index direction, noise sigma U[0,1] with standard normal draws",
+                       "point_reflection_terms": R * npts, "l2": "flushed between steps (256 MiB write)",
+                       "sf_shape": {"tile": tuned[0], "warps": tuned[1], "runs_in_l": tuned[2]} if tuned else
+                       "default"},
+            "terms_per_s": tot_terms * args.steps / tot_s,
+            "roofline": {"bound": "alu", "unit": "Gterm/s", "achieved": R * npts / sum_s / 1e9,
+                         "peak": peak_terms / 1e9, "frac": (R * npts / sum_s) / peak_terms, "traffic": None,
+                         "kernel": "k_aug_order + k_aug_sum",
+                         "peak_basis": "MUFU: one reciprocal per two (point, reflection) terms at 16/clk/SM, "
+                                       "152 SMs, 2070 MHz"},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_structs / e2e_max, "unit": "patterns/s", "h2d_bytes_per_step": int(bytes_in),
+                    "d2h_bytes_per_step": int(bytes_out), "ms_per_step": e2e_max * 1e3,
+                    "api": "Handle.pattern_augmented with pinned host copies each step"},
+            "clocks": ck,
+            "gpu_launches": AUG_LAUNCHES * args.steps,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -408,10 +580,15 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="skip the launch-shape autotuner")
     ap.add_argument("--workload", default="small", choices=sorted(WORKLOADS),
                     help="small (default, the benchmark configuration), mixed or large")
+    ap.add_argument("--path", default="pattern", choices=["pattern", "augmented"],
+                    help="pattern (default): the peak list of every structure; augmented: the "
+                         "pseudo-Voigt / preferred-orientation / noise profile on a 4096-point grid")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.impl == "reference":
+    if args.path == "augmented":
+        run_augmented(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -286,8 +286,10 @@ void xrd_graph_destroy(void* graph);
  * timed run least); 0: off (XRD_EINVAL for another value). xrd_stage_times
  * synchronises on the last event of the last recorded call and writes up to n
  * stage durations in milliseconds (order: prep, atoms, count, scan, emit,
- * structure factor, post, compact; in mode 2 every stage but the structure
- * factor reads 0) and returns the count. */
+ * structure factor, post, compact, profile sum; in mode 2 every stage but the
+ * structure factor reads 0; after an xrd_pattern_augmented call, in either
+ * mode, only the profile sum -- the two kernels after the structure factors --
+ * is timed and the others read 0) and returns the count. */
 int xrd_set_profiling(xrd_handle* h, int enabled);
 int xrd_stage_times(xrd_handle* h, float* ms, int n);
 

@@ -9,13 +9,15 @@
 
 #include "xrd_launch.h"
 
+constexpr int kEvents = 11;
+
 struct xrd_handle {
     int device = 0;
     int sms = 0;
     std::string err;
     int profiling = 0;  // 0 off, 1 every stage, 2 the structure-factor stage only
-    int recorded = 0;   // the mode of the last recorded call
-    cudaEvent_t ev[9] = {};
+    int recorded = 0;   // the mode of the last recorded call (3: an augmented-pattern call)
+    cudaEvent_t ev[kEvents] = {};  // stage boundaries; the last two bracket the augmented profile sum
     void* qbuf = nullptr;  // query scratch owned by the handle
     size_t qbuf_bytes = 0;
     const xrd::TTab* ttab = nullptr;  // 2-theta table on the handle's device
@@ -318,7 +320,7 @@ int xrd_create(xrd_handle** h, int device)
     DeviceGuard g(device);
     e = cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, device);
     if (e != cudaSuccess) { xrd_destroy(p); return XRD_ECUDA; }
-    for (int i = 0; i < kStages + 1; i++) {
+    for (int i = 0; i < kEvents; i++) {
         e = cudaEventCreate(&p->ev[i]);
         if (e != cudaSuccess) { xrd_destroy(p); return XRD_ECUDA; }
     }
@@ -344,7 +346,7 @@ void xrd_destroy(xrd_handle* h)
 {
     if (!h) return;
     DeviceGuard g(h->device);
-    for (int i = 0; i < kStages + 1; i++)
+    for (int i = 0; i < kEvents; i++)
         if (h->ev[i]) cudaEventDestroy(h->ev[i]);
     for (int i = 0; i < xrd::kPostClasses - 1; i++) {
         if (h->side[i]) cudaStreamDestroy(h->side[i]);
@@ -373,14 +375,17 @@ int xrd_stage_times(xrd_handle* h, float* ms, int n)
     if (!h || (!ms && n > 0)) return -XRD_EINVAL;
     if (!h->recorded) return 0;
     DeviceGuard g(h->device);
-    const bool sf_only = h->recorded == 2;
-    cudaError_t e = cudaEventSynchronize(h->ev[sf_only ? kSfStage + 1 : kStages]);
+    const int m = n < kStages + 1 ? n : kStages + 1;  // the pattern stages, then the augmented profile sum
+    const bool aug = h->recorded == 3, sf_only = h->recorded == 2;
+    cudaError_t e = cudaEventSynchronize(h->ev[aug ? kEvents - 1 : (sf_only ? kSfStage + 1 : kStages)]);
     if (e != cudaSuccess) return -cuda_fail(h, e, "xrd_stage_times");
-    const int m = n < kStages ? n : kStages;
     for (int i = 0; i < m; i++) {
         ms[i] = 0.f;
-        if (sf_only && i != kSfStage) continue;
-        e = cudaEventElapsedTime(&ms[i], h->ev[i], h->ev[i + 1]);
+        if (i == kStages) {
+            if (aug) e = cudaEventElapsedTime(&ms[i], h->ev[kEvents - 2], h->ev[kEvents - 1]);
+        } else if (!aug && (!sf_only || i == kSfStage)) {
+            e = cudaEventElapsedTime(&ms[i], h->ev[i], h->ev[i + 1]);
+        }
         if (e != cudaSuccess) return -cuda_fail(h, e, "xrd_stage_times");
     }
     return m;
@@ -1038,7 +1043,12 @@ int xrd_pattern_augmented(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, 
     a.status = status;
     a.totals = totals;
     a.y = y;
+    if (h->profiling) cudaEventRecord(h->ev[kEvents - 2], st);
     xrd::launch_aug(a, st);
+    if (h->profiling) {
+        cudaEventRecord(h->ev[kEvents - 1], st);
+        h->recorded = 3;
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(h, e, "xrd_pattern_augmented launch");
     return XRD_OK;

@@ -183,3 +183,16 @@ def test_repeated_calls_are_bitwise_identical(gpu_lib, handle):
     y0, _, _ = _run(gpu_lib, handle, b, o, grid, aug)
     y1, _, _ = _run(gpu_lib, handle, b, o, grid, aug)
     assert np.array_equal(y0.view(np.uint32), y1.view(np.uint32))
+
+
+def test_profiling_times_the_profile_sum(gpu_lib, handle):
+    base, _, o, grid = synth.grad()
+    b = base.subset(np.arange(4))
+    aug = synth.augment(b.n_struct, grid.n_pts)
+    handle.set_profiling(2)
+    try:
+        _run(gpu_lib, handle, b, o, grid, aug)
+        st = handle.stage_times()
+    finally:
+        handle.set_profiling(0)
+    assert st["profile_sum"] > 0.0 and all(v == 0.0 for k, v in st.items() if k != "profile_sum")
