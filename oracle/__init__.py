@@ -69,6 +69,8 @@ def lib():
                                        C.c_double, _D]
         _lib.orc_march_dollase.argtypes = [_D, C.c_int, C.c_int, C.c_int, _D, C.c_double]
         _lib.orc_march_dollase.restype = C.c_double
+        _lib.orc_is_hexagonal.argtypes = [_D]
+        _lib.orc_is_hexagonal.restype = C.c_int
     return _lib
 
 
@@ -266,6 +268,11 @@ def augmented(batch, s, hkl, lam, t0, dt, n_pts, fwhm, eta, po_dir=(0.0, 0.0, 1.
                         float(eta), _p(d, _D), float(po_r), None if zz is None else zz.ctypes.data, float(sigma),
                         _p(y, _D))
     return y
+
+
+def is_hexagonal(lat):
+    lat = np.ascontiguousarray(lat, dtype=np.float64)
+    return bool(lib().orc_is_hexagonal(_p(lat, _D)))
 
 
 def march_dollase(lat, h, k, l, po_dir, po_r):

@@ -187,14 +187,22 @@ static int orc_cmp(const void* pa, const void* pb)
     return 0;
 }
 
-/* Family key: |h|, |k|, |l| sorted in descending order. */
-static void orc_family_key(int h, int k, int l, int key[3])
+int orc_is_hexagonal(const double lat[6])
 {
-    int v[3] = {abs(h), abs(k), abs(l)};
-    for (int i = 0; i < 3; i++)
-        for (int j = i + 1; j < 3; j++)
+    return fabs(lat[3] - 90.0) < 5.0 && fabs(lat[4] - 90.0) < 5.0 && fabs(lat[5] - 120.0) < 5.0 &&
+           fabs(lat[0] - lat[1]) < 0.01;
+}
+
+/* Family key: the absolute values of the indices sorted in descending order:
+ * (h, k, l) padded with 0, or for a hexagonal cell the Miller-Bravais
+ * (h, k, i = -h - k, l). */
+static void orc_family_key(int h, int k, int l, int hex, int key[4])
+{
+    int v[4] = {abs(h), abs(k), abs(l), hex ? abs(h + k) : 0};
+    for (int i = 0; i < 4; i++)
+        for (int j = i + 1; j < 4; j++)
             if (v[j] > v[i]) { int t = v[i]; v[i] = v[j]; v[j] = t; }
-    key[0] = v[0]; key[1] = v[1]; key[2] = v[2];
+    for (int i = 0; i < 4; i++) key[i] = v[i];
 }
 
 /* Lexicographic comparison of signed (h, k, l) triples: >0 when a > b. */
@@ -281,7 +289,8 @@ int orc_pattern(const double lat[6], long n, const double* frac, const int16_t* 
     /* cutoff relative to the largest peak, then scaling to 100 */
     int rc = 0;
     long nk = 0, nf = 0;
-    int* fkey = (int*)malloc(sizeof(int) * 3 * (size_t)(nr > 0 ? nr : 1));
+    const int hex = orc_is_hexagonal(lat);
+    int* fkey = (int*)malloc(sizeof(int) * 4 * (size_t)(nr > 0 ? nr : 1));
     int* frep = (int*)malloc(sizeof(int) * 3 * (size_t)(nr > 0 ? nr : 1));
     int* fmul = (int*)malloc(sizeof(int) * (size_t)(nr > 0 ? nr : 1));
     for (long p = 0; p < np; p++) {
@@ -293,16 +302,19 @@ int orc_pattern(const double lat[6], long n, const double* frac, const int16_t* 
         out->peak_I[nk] = (o->scaled && imax > 0.0) ? 100.0 * (pI[p] / imax) : pI[p];
         out->peak_fam_off[nk] = nf;
 
-        /* families: members equal up to permutation and sign of (h, k, l) */
+        /* families: members equal up to permutation and sign of (h, k, l), or of
+         * (h, k, i, l) for a hexagonal cell */
         long m = 0;
         for (long i = i0; i < start[p + 1]; i++) {
-            int key[3], hv[3] = {r[i].h, r[i].k, r[i].l};
-            orc_family_key(hv[0], hv[1], hv[2], key);
+            int key[4], hv[3] = {r[i].h, r[i].k, r[i].l};
+            orc_family_key(hv[0], hv[1], hv[2], hex, key);
             long f;
             for (f = 0; f < m; f++)
-                if (fkey[3 * f] == key[0] && fkey[3 * f + 1] == key[1] && fkey[3 * f + 2] == key[2]) break;
+                if (fkey[4 * f] == key[0] && fkey[4 * f + 1] == key[1] && fkey[4 * f + 2] == key[2] &&
+                    fkey[4 * f + 3] == key[3])
+                    break;
             if (f == m) {
-                fkey[3 * m] = key[0]; fkey[3 * m + 1] = key[1]; fkey[3 * m + 2] = key[2];
+                for (int t = 0; t < 4; t++) fkey[4 * m + t] = key[t];
                 frep[3 * m] = hv[0]; frep[3 * m + 1] = hv[1]; frep[3 * m + 2] = hv[2];
                 fmul[m] = 0;
                 m++;

@@ -128,6 +128,15 @@ void orc_augmented(const double lat[6], long n, const double* frac, const int16_
 /* March-Dollase factor of one reflection (h, k, l) about po_dir in reciprocal metric Gs. */
 double orc_march_dollase(const double Gs[6], int h, int k, int l, const double po_dir[3], double po_r);
 
+/*
+ * 1 when the cell is hexagonal in the standard setting: alpha and beta within
+ * 5 degrees of 90, gamma within 5 degrees of 120, |a - b| < 0.01 angstrom.
+ * Families of such a cell group reflections by permutation and sign of the
+ * Miller-Bravais indices (h, k, i = -h - k, l) (the 4-index convention of the
+ * pymatgen calculator the paper accelerates, Sec. 2), else of (h, k, l).
+ */
+int orc_is_hexagonal(const double lat[6]);
+
 /* Number of threads OpenMP would use for threads = 0 (all cores). */
 int orc_max_threads(void);
 
