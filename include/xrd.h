@@ -56,7 +56,8 @@ typedef struct {
     const int64_t* atom_off; /* [n_struct + 1]: atoms of structure s are atom_off[s] .. atom_off[s+1]-1 */
     const double* frac;      /* [n_atoms][3]: fractional coordinates x, y, z */
     const int16_t* Z;        /* [n_atoms]: element number, 0..zmax */
-    const double* occ;       /* [n_atoms]: site occupancy */
+    const double* occ;       /* [n_atoms]: site occupancy; a site shared by several species is one
+                                record per species at the same coordinates */
     const double* B;         /* [n_atoms]: isotropic displacement (Debye-Waller) factor, angstrom^2 */
     const double* coef;      /* [zmax + 1][4][2]: (a_i, b_i) of f(s) = Z - 41.78214 s^2 sum a_i exp(-b_i s^2) */
 } xrd_batch;
@@ -106,7 +107,11 @@ typedef struct {
     double* d_hkl;      /* [cap_peaks]: d spacing of the peak's first reflection, angstrom */
     int64_t* fam_off;   /* [cap_peaks + 1]: families of global peak p are fam_off[p] .. fam_off[p+1]-1 */
     int32_t* hkl;       /* [cap_fam][3]: family representative (lexicographically largest member) */
-    int32_t* mult;      /* [cap_fam]: family multiplicity (members over the full sphere) */
+    int32_t* mult;      /* [cap_fam]: family multiplicity (members over the full sphere). A family is
+                           the reflections of a peak equal up to permutation and sign of (h, k, l); in a
+                           hexagonal cell (alpha, beta within 5 deg of 90, gamma within 5 deg of 120,
+                           |a - b| < 0.01 A) of the Miller-Bravais (h, k, i, l), i = -h - k, the 4-index
+                           convention of the calculator the paper accelerates (Sec. 2) */
     int32_t* status;    /* [n_struct]: XRD_OK, XRD_EINVAL (bad cell or atom) or XRD_ECAPACITY */
     int64_t* totals;    /* [4]: reflections (Friedel-unique), peaks, families, structures with an error */
 } xrd_pattern;

@@ -546,6 +546,7 @@ int xrd_pattern_batch(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, cons
 
     xrd::PostArgs pa{};
     pa.n_struct = (int)n;
+    pa.geo = ga.geo;
     pa.cap_smem = kPostCap;
     pa.scaled = o->scaled;
     pa.lambda = o->lambda;

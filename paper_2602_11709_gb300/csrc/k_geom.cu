@@ -36,6 +36,7 @@ __global__ void k_prep(const double* __restrict__ lattice, int n, double rmax, G
     const double al = lattice[6 * s + 3], be = lattice[6 * s + 4], ga = lattice[6 * s + 5];
     Geo g;
     g.status = XRD_OK;
+    g.hex = fabs(al - 90.0) < 5.0 && fabs(be - 90.0) < 5.0 && fabs(ga - 120.0) < 5.0 && fabs(a - b) < 0.01;
     g.H = g.K = g.L = -1;
     for (int i = 0; i < 6; i++) { g.gs[i] = 0.0; g.gf[i] = 0.f; g.gl[i] = 0.f; }
     for (int i = 0; i < 3; i++) g.g2[i] = 0.0;

@@ -75,26 +75,32 @@ __device__ __forceinline__ bool tt_close(double qa, double qb, float l2, float l
     return lh * dqf < ttol * (sq * c);
 }
 
-// family key: |h|, |k|, |l| sorted descending, packed
-__device__ __forceinline__ uint32_t family_key(uint32_t key)
+// Family key: the absolute values of the indices sorted descending, packed:
+// (h, k, l) and a 0, or for a hexagonal cell the Miller-Bravais (h, k, i = -h - k, l)
+// (|i| <= 1022 fits the 10-bit fields). Families are the classes of equal keys.
+__device__ __forceinline__ unsigned long long family_key(uint32_t key, bool hex)
 {
-    int a = abs(hkl_h(key)), b = abs(hkl_k(key)), c = abs(hkl_l(key));
-    int t;
-    if (b > a) { t = a; a = b; b = t; }
-    if (c > b) { t = b; b = c; c = t; }
-    if (b > a) { t = a; a = b; b = t; }
-    return ((uint32_t)a << 20) | ((uint32_t)b << 10) | (uint32_t)c;
+    const int h = hkl_h(key), k = hkl_k(key);
+    int v0 = abs(h), v1 = abs(k), v2 = abs(hkl_l(key)), v3 = hex ? abs(h + k) : 0, t;
+    // sorting network for 4 values, descending
+    if (v1 > v0) { t = v0; v0 = v1; v1 = t; }
+    if (v3 > v2) { t = v2; v2 = v3; v3 = t; }
+    if (v2 > v0) { t = v0; v0 = v2; v2 = t; }
+    if (v3 > v1) { t = v1; v1 = v3; v3 = t; }
+    if (v2 > v1) { t = v1; v1 = v2; v2 = t; }
+    return ((unsigned long long)v0 << 30) | ((unsigned long long)v1 << 20) | ((unsigned long long)v2 << 10) |
+           (unsigned long long)v3;
 }
 
 // number of distinct families among the members i0..i1-1 of one peak
 template <typename PermT>
-__device__ __forceinline__ int count_families(const uint32_t* key, const PermT* perm, int i0, int i1)
+__device__ __forceinline__ int count_families(const uint32_t* key, const PermT* perm, int i0, int i1, bool hex)
 {
     int nfam = 0;
     for (int i = i0; i < i1; i++) {
-        const uint32_t fk = family_key(key[perm[i]]);
+        const unsigned long long fk = family_key(key[perm[i]], hex);
         bool lead = true;
-        for (int j = i0; j < i && lead; j++) lead = family_key(key[perm[j]]) != fk;
+        for (int j = i0; j < i && lead; j++) lead = family_key(key[perm[j]], hex) != fk;
         nfam += lead;
     }
     return nfam;
@@ -183,6 +189,7 @@ __device__ void post_structure(const PostArgs& a, int s, int64_t base, int n, co
 {
     const int tid = threadIdx.x, nt = blockDim.x;
     const float l2 = a.l2f, lh = a.lhf, ttol = a.ttol;
+    const bool hex = a.geo[s].hex != 0;  // Miller-Bravais families
     // ---- bucket sort on |g|^3 in [r2min^1.5, r2max^1.5] (a monotone map of |g|^2) ----
     // fcnt holds each reflection's bucket and pst the bucket-ordered reflections
     // until the merge step needs them.
@@ -266,7 +273,7 @@ __device__ void post_structure(const PostArgs& a, int s, int64_t base, int n, co
             float sum = 2.f * Ig[perm[i0]];
             for (int i = i0 + 1; i < i1; i++) sum = fmaf(2.f, Ig[perm[i]], sum);
             ps[p] = sum;
-            fcnt[p] = i1 - i0 == 1 ? 1 : count_families(key, perm, i0, i1);
+            fcnt[p] = i1 - i0 == 1 ? 1 : count_families(key, perm, i0, i1, hex);
             lmax = max(lmax, (unsigned long long)__float_as_uint(sum));
         }
         imaxf = __uint_as_float((uint32_t)block_max_u64(lmax, (unsigned long long*)dtmp));
@@ -286,7 +293,7 @@ __device__ void post_structure(const PostArgs& a, int s, int64_t base, int n, co
             double sum = 0.0;
             for (int i = i0; i < i1; i++) sum += 2.0 * Ig[perm[i]];
             psum[p] = sum;
-            fcnt[p] = i1 - i0 == 1 ? 1 : count_families(key, perm, i0, i1);
+            fcnt[p] = i1 - i0 == 1 ? 1 : count_families(key, perm, i0, i1, hex);
             lmax = max(lmax, dbits(sum));
         }
         imax = __longlong_as_double((long long)block_max_u64(lmax, (unsigned long long*)dtmp));
@@ -329,24 +336,24 @@ __device__ void post_structure(const PostArgs& a, int s, int64_t base, int n, co
         }
         // families: leaders are first members of each family; rank by descending representative
         for (int i = i0; i < i1; i++) {
-            const uint32_t fk = family_key(key[perm[i]]);
+            const unsigned long long fk = family_key(key[perm[i]], hex);
             bool lead = true;
-            for (int j = i0; j < i && lead; j++) lead = family_key(key[perm[j]]) != fk;
+            for (int j = i0; j < i && lead; j++) lead = family_key(key[perm[j]], hex) != fk;
             if (!lead) continue;
             uint32_t rep = 0;
             int cnt = 0;
             for (int j = i0; j < i1; j++)
-                if (family_key(key[perm[j]]) == fk) { rep = max(rep, key[perm[j]]); cnt++; }
+                if (family_key(key[perm[j]], hex) == fk) { rep = max(rep, key[perm[j]]); cnt++; }
             int rank = 0;
             for (int m = i0; m < i1; m++) {  // other leaders with a larger representative
-                const uint32_t fm = family_key(key[perm[m]]);
+                const unsigned long long fm = family_key(key[perm[m]], hex);
                 if (fm == fk) continue;
                 bool lm = true;
-                for (int j = i0; j < m && lm; j++) lm = family_key(key[perm[j]]) != fm;
+                for (int j = i0; j < m && lm; j++) lm = family_key(key[perm[j]], hex) != fm;
                 if (!lm) continue;
                 uint32_t rm = 0;
                 for (int j = i0; j < i1; j++)
-                    if (family_key(key[perm[j]]) == fm) rm = max(rm, key[perm[j]]);
+                    if (family_key(key[perm[j]], hex) == fm) rm = max(rm, key[perm[j]]);
                 rank += rm > rep;
             }
             const int64_t fo = base + fcnt[p] + rank;

@@ -31,6 +31,8 @@ struct Geo {
     float gl[6];   // G* - gf (the low words of a two-float G*; off-diagonals doubled in hi and lo below)
     int H, K, L;   // enumeration box |h| <= H ...
     int status;    // XRD_OK or XRD_EINVAL
+    int hex;       // 1: hexagonal cell (alpha, beta within 5 deg of 90, gamma within 5 deg of 120,
+                   // |a - b| < 0.01 A): families by Miller-Bravais indices
 };
 
 // Atom record for the FP32 structure-factor loops (sorted by element within a

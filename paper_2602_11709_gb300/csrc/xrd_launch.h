@@ -80,6 +80,7 @@ struct PostArgs {
     double l2d;                          // lambda^2 / 4
     const TTab* ttab;                    // 2-theta table (device)
     float ttol, lo3, hi3, l2f, lhf;      // FP32: tan(tol / 4) (tol in radians), r2min^1.5, r2max^1.5, lambda^2/4, lambda/2
+    const Geo* geo;     // per structure: the hexagonal flag picks the family grouping
     const int64_t* refl_off;
     const int* abort_flag;
     const double* q;

@@ -15,6 +15,10 @@ The five workloads stand in for the paper's MC3D and COD benchmark sets
 * ``mixed``    -- 100 000 cells, lognormal atom counts (median 20) and edges
                   (median 7 A): spans all reflection-count bins of Sec. 4.2.
 * ``grad``     -- 512 cells of 8-128 atoms for the broadened-pattern gradient.
+* ``hexdis``   -- 256 cells, half hexagonal (a = b U[2.5, 6] A, c U[3, 12] A,
+                  gamma 120 deg) and half P1, 2-24 sites each, a third of the
+                  sites shared by 2-3 species with occupancies summing to 1
+                  (real COD/MC3D entries carry both: Sec. 1 inputs).
 * ``augment``  -- per-structure experimental effects of ML training patterns
                   (Sec. 1): pseudo-Voigt FWHM 0.05-0.3 deg and mixing 0-1,
                   March-Dollase r 0.6-1.4 about a low-index direction, noise
@@ -113,6 +117,43 @@ def _atoms(rng, counts, bmax, partial=False):
         part = rng.random(n) < 0.2
         occ[part] = rng.uniform(0.5, 1.0, size=int(part.sum()))
     return off, frac, Z, occ, B
+
+
+def hexdis(seed: int = 8, n: int = 256) -> tuple[Batch, Opts]:
+    """Hexagonal and P1 cells whose sites may be shared by several species.
+
+    A shared site is one atom record per species at the same coordinates, with
+    the species' occupancies (Dirichlet(1, ..)) summing to 1 and one B per record.
+    """
+    rng = np.random.default_rng(seed)
+    coef = coef_table(rng)
+    lat = np.zeros((n, 6))
+    for s in range(n):
+        if s % 2 == 0:
+            a = rng.uniform(2.5, 6.0)
+            lat[s] = [a, a, rng.uniform(3.0, 12.0), 90.0, 90.0, 120.0]
+        else:
+            lat[s, :3] = rng.uniform(3.0, 10.0, 3)
+            lat[s, 3:] = _angles(rng, 1)[0]
+    frac, Z, occ, B, counts = [], [], [], [], []
+    for s in range(n):
+        n_sites = int(rng.integers(2, 25))
+        c = 0
+        for _ in range(n_sites):
+            x = rng.random(3)
+            k = int(rng.integers(2, 4)) if rng.random() < 1.0 / 3.0 else 1
+            w = rng.dirichlet(np.ones(k)) if k > 1 else np.ones(1)
+            for j in range(k):
+                frac.append(x)
+                Z.append(rng.integers(1, ZMAX + 1))
+                occ.append(w[j])
+                B.append(rng.uniform(0.0, 1.5))
+            c += k
+        counts.append(c)
+    off = np.zeros(n + 1, dtype=np.int64)
+    off[1:] = np.cumsum(counts)
+    return (Batch(lat, off, np.array(frac), np.array(Z, dtype=np.int16), np.array(occ), np.array(B), coef),
+            Opts(CU_KA, 5.0, 110.0, 1e-5, 1e-3, 1))
 
 
 def nacl(seed: int = 1) -> tuple[Batch, Opts]:

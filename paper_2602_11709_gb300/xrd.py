@@ -142,6 +142,21 @@ def _stream_ptr(stream):
     return C.c_void_p(s.cuda_stream)
 
 
+def is_hexagonal(lattice):
+    """Per structure: the cell counts as hexagonal (families by Miller-Bravais indices) when alpha and
+    beta lie within 5 degrees of 90, gamma within 5 degrees of 120 and |a - b| < 0.01 A -- the
+    device's rule, evaluated with the same double comparisons."""
+    lat = np.atleast_2d(np.asarray(lattice, dtype=np.float64))
+    return ((np.abs(lat[:, 3] - 90.0) < 5.0) & (np.abs(lat[:, 4] - 90.0) < 5.0) &
+            (np.abs(lat[:, 5] - 120.0) < 5.0) & (np.abs(lat[:, 0] - lat[:, 1]) < 0.01))
+
+
+def miller_bravais(hkl):
+    """(h, k, l) rows -> (h, k, i = -h - k, l) rows: the 4-index form of hexagonal family representatives."""
+    hkl = np.asarray(hkl)
+    return np.stack([hkl[..., 0], hkl[..., 1], -hkl[..., 0] - hkl[..., 1], hkl[..., 2]], axis=-1)
+
+
 def make_grid(g) -> xrd_grid:
     """C grid from any object with t0/dt/fwhm/n_pts."""
     return xrd_grid(float(g.t0), float(g.dt), float(g.fwhm), int(g.n_pts), 0)
