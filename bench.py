@@ -75,9 +75,12 @@ def reduce_over_ranks(terms, structures, seconds, world, device="cpu"):
     return int(t[0].item()), int(t[1].item()), float(m[0].item())
 
 
-# DRAM bytes (read + write) of one k_sf launch on the small workload, from one ncu capture of
-# the kernel as it stands (dram__bytes_read.sum + dram__bytes_write.sum); other workloads: not captured
-SF_TRAFFIC_BYTES = {"small": 13556224}
+# DRAM bytes (read + write) of one k_sf launch per (workload, tile, warps, runs), from one ncu
+# capture of each shape as the kernel stands (dram__bytes_read.sum + dram__bytes_write.sum, the
+# written intensities stay in L2); other workloads and shapes: not captured (null)
+SF_TRAFFIC_BYTES = {("small", 64, 1, 0): 13618432, ("small", 64, 2, 0): 13618688, ("small", 64, 4, 0): 13618176,
+                    ("small", 128, 1, 0): 13556224, ("small", 128, 2, 0): 13555968, ("small", 128, 4, 0): 13556224,
+                    ("small", 128, 2, 1): 15159040}
 # SFU issue rates per SM per clock measured on this GB300 (MUFU.SIN/COS 16, MUFU.EX2 32) and the
 # maximum SM clock; the structure-factor roofline of a batch follows from its mix of operations.
 MUFU_SINCOS_PER_CLK = 16.0
@@ -217,6 +220,10 @@ def run_ours(args):
         lo, hi = shard_bounds(b.n_struct, rank, world)
         b = b.subset(np.arange(lo, hi))
     h = xrd.Handle(dev)
+    fixed_shape = None
+    if args.sf_shape:  # every call of the run, the first included, uses this shape
+        fixed_shape = tuple(int(v) for v in args.sf_shape.split(","))
+        h.set_sf_shape(*fixed_shape)
     db = xrd.DeviceBatch.from_host(b, "cuda:%d" % dev)
     co = xrd.make_opts(o, args.precision)
     sz = h.query_sizes(db, co)
@@ -252,7 +259,10 @@ def run_ours(args):
     f_cycles = float((half * species).sum()) * 4.0 / MUFU_EX2_PER_CLK
 
     # launch-shape tuning of the structure-factor kernel, then one CUDA graph for the whole step
-    tuned = h.autotune(db, co, out, ws) if not args.no_tune else None
+    if args.sf_shape:
+        tuned = fixed_shape
+    else:
+        tuned = h.autotune(db, co, out, ws) if not args.no_tune else None
     # timed steps carry events around the structure-factor kernel only (every event is a graph
     # node and costs time); the per-stage breakdown comes from a separate pass afterwards
     h.set_profiling(2)
@@ -375,7 +385,8 @@ def run_ours(args):
             "patterns_per_s": pps,
             "roofline": {"bound": "alu", "unit": "Gterm/s", "achieved": achieved_gterms, "peak": peak_gterms,
                          "frac": achieved_gterms / peak_gterms,
-                         "traffic": SF_TRAFFIC_BYTES.get(args.workload), "traffic_unit": "bytes per launch",
+                         "traffic": SF_TRAFFIC_BYTES.get((args.workload,) + tuple(tuned or (128, 2, 0))),
+                         "traffic_unit": "bytes per launch (dram read + write, ncu, this shape)",
                          "fma_floor_frac": (fma_cycles / (152.0 * SM_MAX_MHZ * 1e6)) / sf_avg,
                          "phase_seeds_per_term": w_seeds / max(terms_eval, 1),
                          "kernel": "k_sf", "peak_basis": "SFU: sin+cos at 16/clk/SM per phase seed (one per run of "
@@ -578,6 +589,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-graph", action="store_true", help="launch the step eagerly instead of as a CUDA graph")
     ap.add_argument("--no-tune", action="store_true", help="skip the launch-shape autotuner")
+    ap.add_argument("--sf-shape", default="", help="tile,warps,runs: set the structure-factor shape, no tuning")
     ap.add_argument("--workload", default="small", choices=sorted(WORKLOADS),
                     help="small (default, the benchmark configuration), mixed or large")
     ap.add_argument("--path", default="pattern", choices=["pattern", "augmented"],

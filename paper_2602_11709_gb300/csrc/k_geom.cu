@@ -27,66 +27,79 @@ __device__ __forceinline__ double cosd(double deg)
 // S0: reciprocal metric G* = G^-1 from the direct metric
 // G = [[a^2, ab cos(gamma), ac cos(beta)], [., b^2, bc cos(alpha)], [., ., c^2]]
 // by cofactors over the determinant, and the enumeration box |h| <= r_max a + 1.
+// FP64 latency-bound (this part has little FP64 throughput), so each structure
+// takes 8 lanes: lanes 0-2 form the three cosines, every lane the cofactors and
+// determinant (same operations, same order), lane j < 6 the element j of G*
+// (one division each), lane 6 the box, status and hexagonal flag. Every value is
+// rounded exactly as in a one-thread evaluation.
+constexpr int kPrepLanes = 8;
+
 __global__ void k_prep(const double* __restrict__ lattice, int n, double rmax, Geo* __restrict__ geo)
 {
     pdl_enter();
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n) return;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int s_raw = t / kPrepLanes, j = t % kPrepLanes;
+    const bool live = s_raw < n;
+    const int s = live ? s_raw : n - 1;  // lanes past the batch compute a copy and store nothing
     const double a = lattice[6 * s], b = lattice[6 * s + 1], c = lattice[6 * s + 2];
     const double al = lattice[6 * s + 3], be = lattice[6 * s + 4], ga = lattice[6 * s + 5];
-    Geo g;
-    g.status = XRD_OK;
-    g.hex = fabs(al - 90.0) < 5.0 && fabs(be - 90.0) < 5.0 && fabs(ga - 120.0) < 5.0 && fabs(a - b) < 0.01;
-    g.H = g.K = g.L = -1;
-    for (int i = 0; i < 6; i++) { g.gs[i] = 0.0; g.gf[i] = 0.f; g.gl[i] = 0.f; }
-    for (int i = 0; i < 3; i++) g.g2[i] = 0.0;
+    Geo& g = geo[s];
     const bool finite = isfinite(a) && isfinite(b) && isfinite(c) && isfinite(al) && isfinite(be) && isfinite(ga);
-    if (!finite || !(a > 0.0 && b > 0.0 && c > 0.0)) {
-        g.status = XRD_EINVAL;
-        geo[s] = g;
-        return;
-    }
-    const double ca = cosd(al), cb = cosd(be), cg = cosd(ga);
+    bool ok = finite && a > 0.0 && b > 0.0 && c > 0.0;
+    const double cj = (ok && j < 3) ? cosd(j == 0 ? al : (j == 1 ? be : ga)) : 0.0;
+    const double ca = __shfl_sync(0xffffffffu, cj, 0, kPrepLanes);
+    const double cb = __shfl_sync(0xffffffffu, cj, 1, kPrepLanes);
+    const double cg = __shfl_sync(0xffffffffu, cj, 2, kPrepLanes);
     // volume factor 1 - ca^2 - cb^2 - cg^2 + 2 ca cb cg, left to right
     double vf = __dsub_rn(1.0, __dmul_rn(ca, ca));
     vf = __dsub_rn(vf, __dmul_rn(cb, cb));
     vf = __dsub_rn(vf, __dmul_rn(cg, cg));
     vf = __dadd_rn(vf, __dmul_rn(__dmul_rn(__dmul_rn(2.0, ca), cb), cg));
-    if (!(vf > 1e-6)) {
-        g.status = XRD_EINVAL;
-        geo[s] = g;
-        return;
-    }
+    ok = ok && vf > 1e-6;
     const double G11 = __dmul_rn(a, a), G22 = __dmul_rn(b, b), G33 = __dmul_rn(c, c);
     const double G12 = __dmul_rn(__dmul_rn(a, b), cg);
     const double G13 = __dmul_rn(__dmul_rn(a, c), cb);
     const double G23 = __dmul_rn(__dmul_rn(b, c), ca);
     const double C11 = __dsub_rn(__dmul_rn(G22, G33), __dmul_rn(G23, G23));
-    const double C22 = __dsub_rn(__dmul_rn(G11, G33), __dmul_rn(G13, G13));
-    const double C33 = __dsub_rn(__dmul_rn(G11, G22), __dmul_rn(G12, G12));
     const double C12 = __dsub_rn(__dmul_rn(G13, G23), __dmul_rn(G12, G33));
     const double C13 = __dsub_rn(__dmul_rn(G12, G23), __dmul_rn(G13, G22));
-    const double C23 = __dsub_rn(__dmul_rn(G12, G13), __dmul_rn(G11, G23));
     const double det = __dadd_rn(__dadd_rn(__dmul_rn(G11, C11), __dmul_rn(G12, C12)), __dmul_rn(G13, C13));
-    g.gs[0] = __ddiv_rn(C11, det);
-    g.gs[1] = __ddiv_rn(C22, det);
-    g.gs[2] = __ddiv_rn(C33, det);
-    g.gs[3] = __ddiv_rn(C12, det);
-    g.gs[4] = __ddiv_rn(C13, det);
-    g.gs[5] = __ddiv_rn(C23, det);
-    for (int i = 0; i < 3; i++) g.g2[i] = 2.0 * g.gs[3 + i];  // exact
-    for (int i = 0; i < 6; i++) {
-        g.gf[i] = __double2float_rn(g.gs[i]);
-        g.gl[i] = __double2float_rn(g.gs[i] - (double)g.gf[i]);
+    if (!live) return;
+    if (j < 6) {
+        // element j of G* (stored as 11, 22, 33, 12, 13, 23)
+        double Cj;
+        switch (j) {
+        case 0: Cj = C11; break;
+        case 1: Cj = __dsub_rn(__dmul_rn(G11, G33), __dmul_rn(G13, G13)); break;
+        case 2: Cj = __dsub_rn(__dmul_rn(G11, G22), __dmul_rn(G12, G12)); break;
+        case 3: Cj = C12; break;
+        case 4: Cj = C13; break;
+        default: Cj = __dsub_rn(__dmul_rn(G12, G13), __dmul_rn(G11, G23)); break;
+        }
+        const double v = ok ? __ddiv_rn(Cj, det) : 0.0;
+        g.gs[j] = v;
+        if (j >= 3) g.g2[j - 3] = 2.0 * v;  // exact
+        const float vf32 = ok ? __double2float_rn(v) : 0.f;
+        g.gf[j] = vf32;
+        g.gl[j] = ok ? __double2float_rn(v - (double)vf32) : 0.f;
+    } else if (j == 6) {
+        g.hex = fabs(al - 90.0) < 5.0 && fabs(be - 90.0) < 5.0 && fabs(ga - 120.0) < 5.0 && fabs(a - b) < 0.01;
+        int H = -1, K = -1, L = -1, st = XRD_EINVAL;
+        if (ok) {
+            H = (int)floor(__dmul_rn(rmax, a)) + 1;
+            K = (int)floor(__dmul_rn(rmax, b)) + 1;
+            L = (int)floor(__dmul_rn(rmax, c)) + 1;
+            st = XRD_OK;
+            if (H > kHklLimit || K > kHklLimit || L > kHklLimit) {
+                st = XRD_EINVAL;  // cell too large for the packed (h, k, l) key at this 2-theta range
+                H = K = L = -1;
+            }
+        }
+        g.H = H;
+        g.K = K;
+        g.L = L;
+        g.status = st;
     }
-    g.H = (int)floor(__dmul_rn(rmax, a)) + 1;
-    g.K = (int)floor(__dmul_rn(rmax, b)) + 1;
-    g.L = (int)floor(__dmul_rn(rmax, c)) + 1;
-    if (g.H > kHklLimit || g.K > kHklLimit || g.L > kHklLimit) {
-        g.status = XRD_EINVAL;  // cell too large for the packed (h, k, l) key at this 2-theta range
-        g.H = g.K = g.L = -1;
-    }
-    geo[s] = g;
 }
 
 // f(s) coefficients in the form the FP32 loops use (exp2 with the scale folded in).
@@ -658,8 +671,8 @@ void launch_work(const GeomArgs& a, unsigned long long* out, cudaStream_t st)
 
 void launch_prep(const GeomArgs& a, cudaStream_t st, bool pdl)
 {
-    const int n = a.n_struct;
-    if (n > 0) launch_k(pdl, k_prep, (n + 31) / 32, 32, st, a.lattice, n, a.rmax, a.geo);
+    const int n = a.n_struct;  // 8 lanes per structure, 4 structures per 32-thread CTA
+    if (n > 0) launch_k(pdl, k_prep, (n + 3) / 4, 32, st, a.lattice, n, a.rmax, a.geo);
 }
 
 void launch_coef(const GeomArgs& a, cudaStream_t st, bool pdl)
@@ -683,7 +696,7 @@ void launch_count_only(const GeomArgs& a, cudaStream_t st)
 {
     const int n = a.n_struct;
     if (n <= 0) return;
-    k_prep<<<(n + 31) / 32, 32, 0, st>>>(a.lattice, n, a.rmax, a.geo);
+    k_prep<<<(n + 3) / 4, 32, 0, st>>>(a.lattice, n, a.rmax, a.geo);  // 8 lanes per structure
     launch_pdl(k_count<false>, n, 256, 0, st, a.geo, a.r2min, a.r2max, (float)a.r2min, (float)a.r2max, 0,
                a.refl_cnt, (int64_t*)nullptr, (int*)nullptr);
 }

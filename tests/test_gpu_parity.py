@@ -283,3 +283,14 @@ def test_runs_shape_against_oracle(gpu_lib, handle):
         _report("runs_large_full_sampled_fp32_phasefix", {"max_abs_rel_to_max": worst})
     finally:
         handle.set_sf_shape(128, 2, 0)
+
+
+@pytest.mark.parametrize("n", [1, 7, 37, 1024])
+def test_query_sizes_counts_every_structure(gpu_lib, handle, n):
+    """xrd_query_sizes: the Friedel-unique count of every structure of the batch (sizes that are not
+    multiples of the kernels' CTA or lane groups), against the oracle's full-sphere count / 2."""
+    b, o = synth.small(n=n)
+    db = gpu_lib.DeviceBatch.from_host(b)
+    sz = handle.query_sizes(db, gpu_lib.make_opts(o, "fp32_phasefix"))
+    counts = [len(oracle.enumerate_refl(b.lattice[s], o)[0]) // 2 for s in range(n)]
+    assert sz.n_refl == sum(counts) and sz.max_refl == max(counts)
