@@ -78,8 +78,12 @@ struct Layout {
         flags, coef32, atom32, atom64, astep;
     size_t q, key, runs, I, g_perm, g_bkt, g_flag, g_pstart, g_psum, g_fcnt;
     size_t st_q, st_I, st_foff, st_hkl, st_mult;
+    size_t parts;
     size_t total;
 };
+
+// chunk sums of the multi-block scans: 9 words per chunk of 4096 structures
+size_t scan_parts_bytes(int64_t n) { return 8 * 9 * (size_t)((n + 4095) / 4096 + 1); }
 
 Layout layout(int64_t n, int64_t natoms, int zmax, int64_t R)
 {
@@ -119,6 +123,7 @@ Layout layout(int64_t n, int64_t natoms, int zmax, int64_t R)
     L.st_foff = take(4 * R);
     L.st_hkl = take(12 * R);
     L.st_mult = take(4 * R);
+    L.parts = take(scan_parts_bytes(n));
     L.total = o;
     return L;
 }
@@ -128,7 +133,7 @@ Layout layout(int64_t n, int64_t natoms, int zmax, int64_t R)
 struct LayoutG {
     size_t geo, refl_cnt, run_cnt, tcnt, refl_off, tile_off, order, atom_bad, tile_tab, flags, coef32, atom32, atom64,
         astep;
-    size_t q, key, runs, Fx, Ig, tb, td, perm, U, V, aorder;
+    size_t q, key, runs, Fx, Ig, tb, td, perm, U, V, aorder, parts;
     size_t total;
 };
 
@@ -162,6 +167,7 @@ LayoutG layout_grad(int64_t n, int64_t natoms, int zmax, int64_t R)
     L.U = take(4 * R);
     L.V = take(4 * R);
     L.aorder = take(4 * n);
+    L.parts = take(scan_parts_bytes(n));
     L.total = o;
     return L;
 }
@@ -291,6 +297,7 @@ xrd::GeomArgs geom_args(const xrd_batch* b, const xrd_opts* o, const Layout& L, 
     g.status = status;
     g.q = (double*)(ws + L.q);
     g.key = (uint32_t*)(ws + L.key);
+    g.parts = (long long*)(ws + L.parts);
     return g;
 }
 
@@ -605,6 +612,7 @@ int xrd_pattern_batch(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, cons
 
     xrd::CompactArgs ca{};
     ca.n_struct = (int)n;
+    ca.parts = (long long*)(ws + L.parts);
     ca.grid = h->sms;
     ca.cap_peaks = out->cap_peaks;
     ca.cap_fam = out->cap_fam;
@@ -912,6 +920,7 @@ static void launch_front(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, c
     ga.status = status;
     ga.q = (double*)(ws + L.q);
     ga.key = (uint32_t*)(ws + L.key);
+    ga.parts = (long long*)(ws + L.parts);
     cudaMemsetAsync(ws + L.flags, 0, kFlagBytes, st);
     xrd::launch_prep(ga, st, false);
     xrd::launch_coef(ga, st, true);

@@ -27,29 +27,38 @@ __device__ __forceinline__ double cosd(double deg)
 // S0: reciprocal metric G* = G^-1 from the direct metric
 // G = [[a^2, ab cos(gamma), ac cos(beta)], [., b^2, bc cos(alpha)], [., ., c^2]]
 // by cofactors over the determinant, and the enumeration box |h| <= r_max a + 1.
-// FP64 latency-bound (this part has little FP64 throughput), so each structure
-// takes 8 lanes: lanes 0-2 form the three cosines, every lane the cofactors and
-// determinant (same operations, same order), lane j < 6 the element j of G*
-// (one division each), lane 6 the box, status and hexagonal flag. Every value is
-// rounded exactly as in a one-thread evaluation.
-constexpr int kPrepLanes = 8;
-
+// The part has little FP64 throughput. A small batch is latency-bound, so
+// each structure takes LANES = 8 lanes: lanes 0-2 form the three cosines,
+// every lane the cofactors and determinant (same operations, same order), lane
+// j < 6 the element j of G* (one division each), lane 6 the box, status and
+// hexagonal flag. A large batch is throughput-bound and takes one lane per
+// structure (LANES = 1, no redundant work). Every value is rounded exactly as
+// in a one-thread evaluation either way.
+template <int LANES>
 __global__ void k_prep(const double* __restrict__ lattice, int n, double rmax, Geo* __restrict__ geo)
 {
     pdl_enter();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const int s_raw = t / kPrepLanes, j = t % kPrepLanes;
+    const int s_raw = t / LANES, lane = t % LANES;
     const bool live = s_raw < n;
+    if (LANES == 1 && !live) return;
     const int s = live ? s_raw : n - 1;  // lanes past the batch compute a copy and store nothing
     const double a = lattice[6 * s], b = lattice[6 * s + 1], c = lattice[6 * s + 2];
     const double al = lattice[6 * s + 3], be = lattice[6 * s + 4], ga = lattice[6 * s + 5];
     Geo& g = geo[s];
     const bool finite = isfinite(a) && isfinite(b) && isfinite(c) && isfinite(al) && isfinite(be) && isfinite(ga);
     bool ok = finite && a > 0.0 && b > 0.0 && c > 0.0;
-    const double cj = (ok && j < 3) ? cosd(j == 0 ? al : (j == 1 ? be : ga)) : 0.0;
-    const double ca = __shfl_sync(0xffffffffu, cj, 0, kPrepLanes);
-    const double cb = __shfl_sync(0xffffffffu, cj, 1, kPrepLanes);
-    const double cg = __shfl_sync(0xffffffffu, cj, 2, kPrepLanes);
+    double ca, cb, cg;
+    if (LANES == 1) {
+        ca = ok ? cosd(al) : 0.0;
+        cb = ok ? cosd(be) : 0.0;
+        cg = ok ? cosd(ga) : 0.0;
+    } else {
+        const double cj = (ok && lane < 3) ? cosd(lane == 0 ? al : (lane == 1 ? be : ga)) : 0.0;
+        ca = __shfl_sync(0xffffffffu, cj, 0, LANES);
+        cb = __shfl_sync(0xffffffffu, cj, 1, LANES);
+        cg = __shfl_sync(0xffffffffu, cj, 2, LANES);
+    }
     // volume factor 1 - ca^2 - cb^2 - cg^2 + 2 ca cb cg, left to right
     double vf = __dsub_rn(1.0, __dmul_rn(ca, ca));
     vf = __dsub_rn(vf, __dmul_rn(cb, cb));
@@ -65,42 +74,50 @@ __global__ void k_prep(const double* __restrict__ lattice, int n, double rmax, G
     const double C13 = __dsub_rn(__dmul_rn(G12, G23), __dmul_rn(G13, G22));
     const double det = __dadd_rn(__dadd_rn(__dmul_rn(G11, C11), __dmul_rn(G12, C12)), __dmul_rn(G13, C13));
     if (!live) return;
-    if (j < 6) {
-        // element j of G* (stored as 11, 22, 33, 12, 13, 23)
-        double Cj;
-        switch (j) {
-        case 0: Cj = C11; break;
-        case 1: Cj = __dsub_rn(__dmul_rn(G11, G33), __dmul_rn(G13, G13)); break;
-        case 2: Cj = __dsub_rn(__dmul_rn(G11, G22), __dmul_rn(G12, G12)); break;
-        case 3: Cj = C12; break;
-        case 4: Cj = C13; break;
-        default: Cj = __dsub_rn(__dmul_rn(G12, G13), __dmul_rn(G11, G23)); break;
-        }
-        const double v = ok ? __ddiv_rn(Cj, det) : 0.0;
-        g.gs[j] = v;
-        if (j >= 3) g.g2[j - 3] = 2.0 * v;  // exact
-        const float vf32 = ok ? __double2float_rn(v) : 0.f;
-        g.gf[j] = vf32;
-        g.gl[j] = ok ? __double2float_rn(v - (double)vf32) : 0.f;
-    } else if (j == 6) {
-        g.hex = fabs(al - 90.0) < 5.0 && fabs(be - 90.0) < 5.0 && fabs(ga - 120.0) < 5.0 && fabs(a - b) < 0.01;
-        int H = -1, K = -1, L = -1, st = XRD_EINVAL;
-        if (ok) {
-            H = (int)floor(__dmul_rn(rmax, a)) + 1;
-            K = (int)floor(__dmul_rn(rmax, b)) + 1;
-            L = (int)floor(__dmul_rn(rmax, c)) + 1;
-            st = XRD_OK;
-            if (H > kHklLimit || K > kHklLimit || L > kHklLimit) {
-                st = XRD_EINVAL;  // cell too large for the packed (h, k, l) key at this 2-theta range
-                H = K = L = -1;
+#pragma unroll
+    for (int j = (LANES == 1 ? 0 : lane); j < (LANES == 1 ? 7 : lane + 1); j++) {
+        if (j < 6) {
+            // element j of G* (stored as 11, 22, 33, 12, 13, 23)
+            double Cj;
+            switch (j) {
+            case 0: Cj = C11; break;
+            case 1: Cj = __dsub_rn(__dmul_rn(G11, G33), __dmul_rn(G13, G13)); break;
+            case 2: Cj = __dsub_rn(__dmul_rn(G11, G22), __dmul_rn(G12, G12)); break;
+            case 3: Cj = C12; break;
+            case 4: Cj = C13; break;
+            default: Cj = __dsub_rn(__dmul_rn(G12, G13), __dmul_rn(G11, G23)); break;
             }
+            const double v = ok ? __ddiv_rn(Cj, det) : 0.0;
+            g.gs[j] = v;
+            if (j >= 3) g.g2[j - 3] = 2.0 * v;  // exact
+            const float v32 = ok ? __double2float_rn(v) : 0.f;
+            g.gf[j] = v32;
+            g.gl[j] = ok ? __double2float_rn(v - (double)v32) : 0.f;
+        } else if (j == 6) {
+            g.hex = fabs(al - 90.0) < 5.0 && fabs(be - 90.0) < 5.0 && fabs(ga - 120.0) < 5.0 && fabs(a - b) < 0.01;
+            int H = -1, K = -1, L = -1, st = XRD_EINVAL;
+            if (ok) {
+                H = (int)floor(__dmul_rn(rmax, a)) + 1;
+                K = (int)floor(__dmul_rn(rmax, b)) + 1;
+                L = (int)floor(__dmul_rn(rmax, c)) + 1;
+                st = XRD_OK;
+                if (H > kHklLimit || K > kHklLimit || L > kHklLimit) {
+                    st = XRD_EINVAL;  // cell too large for the packed (h, k, l) key at this 2-theta range
+                    H = K = L = -1;
+                }
+            }
+            g.H = H;
+            g.K = K;
+            g.L = L;
+            g.status = st;
         }
-        g.H = H;
-        g.K = K;
-        g.L = L;
-        g.status = st;
     }
 }
+
+// 8 lanes per structure up to this many structures (latency-bound), one above (throughput-bound)
+constexpr int kPrepWideMax = 8192;
+
+static void prep_launch(bool pdl, const double* lattice, int n, double rmax, Geo* geo, cudaStream_t st);
 
 // f(s) coefficients in the form the FP32 loops use (exp2 with the scale folded in).
 __global__ void k_coef(const double* __restrict__ coef, int zmax, Coef32* __restrict__ c32)
@@ -576,6 +593,146 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_refl(const int64_t* __res
     }
 }
 
+// Multi-block form of k_scan_refl for batches of more than two chunks (one
+// chunk of kScanItems * kScanThreads structures per CTA): k_scan_refl_parts
+// writes each chunk's sums (reflections, invalid structures, tiles in the
+// largest-first order, structures per size class); k_scan_refl_final offsets
+// every chunk by the sums of the chunks before it and repeats the single-block
+// passes on its own chunk. Class-list slots follow the chunk order.
+constexpr int kScanPartWords = 3 + kPostClasses;  // refl, bad, tiles, class counts
+
+__device__ __forceinline__ long long tiles_of(const int64_t* __restrict__ run_cnt, int s, long long c, int tile_refl)
+{
+    return tile_refl > 0 ? (c + tile_refl - 1) / tile_refl : (run_cnt[s] + kRunsPerTile - 1) / kRunsPerTile;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_refl_parts(const int64_t* __restrict__ cnt,
+                                                                  const int64_t* __restrict__ run_cnt,
+                                                                  const Geo* __restrict__ geo, int n, int tile_refl,
+                                                                  const int* __restrict__ order,
+                                                                  long long* __restrict__ parts)
+{
+    pdl_enter();
+    __shared__ long long ws[33];
+    __shared__ int cc[kPostClasses];
+    const int nt = blockDim.x, tid = threadIdx.x, base = blockIdx.x * kScanItems * nt;
+    if (tid < kPostClasses) cc[tid] = 0;
+    __syncthreads();
+    long long refl = 0, bad = 0, tiles = 0;
+#pragma unroll
+    for (int u = 0; u < kScanItems; u++) {
+        const int i = base + u * nt + tid;
+        if (i < n) {
+            refl += cnt[i];
+            bad += geo[i].status != XRD_OK;
+            const int sv = order[i];  // position i of the largest-first order
+            const long long c = cnt[sv];
+            tiles += tiles_of(run_cnt, sv, c, tile_refl);
+            atomicAdd(&cc[post_class(c)], 1);
+        }
+    }
+    long long t;
+    block_prefix_ll(refl, ws, &t);
+    refl = t;
+    block_prefix_ll(bad, ws, &t);
+    bad = t;
+    block_prefix_ll(tiles, ws, &t);
+    tiles = t;
+    if (tid == 0) {
+        long long* o = parts + (int64_t)blockIdx.x * kScanPartWords;
+        o[0] = refl;
+        o[1] = bad;
+        o[2] = tiles;
+        for (int k = 0; k < kPostClasses; k++) o[3 + k] = cc[k];
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_refl_final(const int64_t* __restrict__ cnt,
+                                                                  const int64_t* __restrict__ run_cnt,
+                                                                  const Geo* __restrict__ geo, int n, int tile_refl,
+                                                                  int64_t cap_refl, int64_t* __restrict__ refl_off,
+                                                                  int* __restrict__ tile_off, const int* __restrict__ order,
+                                                                  int* __restrict__ cls_list, int* __restrict__ abort_flag,
+                                                                  int64_t* __restrict__ totals, int32_t* __restrict__ status,
+                                                                  unsigned long long* __restrict__ work,
+                                                                  const long long* __restrict__ parts)
+{
+    pdl_enter();
+    __shared__ long long ws[33];
+    __shared__ __align__(16) long long buf[kScanItems * kScanThreads];
+    __shared__ long long pre[kScanPartWords], all[kScanPartWords];
+    __shared__ int ccnt[kPostClasses];
+    const int nt = blockDim.x, tid = threadIdx.x, b = blockIdx.x, base = b * kScanItems * nt;
+    const int nch = gridDim.x;
+    if (tid < kScanPartWords) {  // sums of the chunks before this one, and of all chunks
+        long long p = 0, a = 0;
+        for (int c = 0; c < nch; c++) {
+            const long long v = parts[(int64_t)c * kScanPartWords + tid];
+            p += c < b ? v : 0;
+            a += v;
+        }
+        pre[tid] = p;
+        all[tid] = a;
+    }
+    if (tid < kPostClasses) ccnt[tid] = 0;
+    __syncthreads();
+    const long long total = all[0];
+    const bool over = total > cap_refl;
+    long long v[kScanItems], tot;
+    int st[kScanItems];
+    // 1. reflection offsets and status
+#pragma unroll
+    for (int u = 0; u < kScanItems; u++) {
+        const int i = base + u * nt + tid;
+        v[u] = i < n ? cnt[i] : 0;
+        st[u] = i < n ? geo[i].status : XRD_OK;
+    }
+    chunk_scan<kScanItems>(v, buf, ws, &tot);
+#pragma unroll
+    for (int u = 0; u < kScanItems; u++) {
+        const int i = base + u * nt + tid;
+        if (i < n) {
+            refl_off[i] = pre[0] + v[u];
+            status[i] = over ? XRD_ECAPACITY : st[u];
+        }
+    }
+    // 2. first tile of each structure and the size-class lists, in the largest-first order
+    int sv[kScanItems];
+    long long c[kScanItems];
+#pragma unroll
+    for (int u = 0; u < kScanItems; u++) {
+        const int p = base + u * nt + tid;
+        sv[u] = p < n ? order[p] : -1;
+        c[u] = sv[u] >= 0 ? cnt[sv[u]] : 0;
+        v[u] = sv[u] < 0 ? 0 : tiles_of(run_cnt, sv[u], c[u], tile_refl);
+    }
+    chunk_scan<kScanItems>(v, buf, ws, &tot);
+#pragma unroll
+    for (int u = 0; u < kScanItems; u++) {
+        const int p = base + u * nt + tid;
+        if (p < n) tile_off[sv[u]] = (int)(pre[2] + v[u]);
+        if (!over && cls_list) {
+            const int k = post_class(c[u]);
+            const int slot = warp_aggregated_slot(ccnt, k, p < n);
+            if (p < n) cls_list[(int64_t)k * n + (int)pre[3 + k] + slot] = sv[u];
+        }
+    }
+    if (b == 0 && tid == 0) {
+        if (work) {
+            work[0] = (unsigned long long)all[2];
+            work[1] = tile_refl > 0 ? 0ull : 1ull;
+        }
+        refl_off[n] = total;
+        tile_off[n] = over ? 0 : (int)all[2];
+        for (int k = 0; k < kPostClasses; k++) abort_flag[4 + k] = over ? 0 : (int)all[3 + k];
+        totals[0] = total;
+        totals[1] = 0;
+        totals[2] = 0;
+        totals[3] = over ? n : all[1];
+        *abort_flag = over;
+    }
+}
+
 // Largest-first order of the structures: a counting sort on the atom count
 // (which sets the cost of a structure-factor tile), in descending order; one
 // block, warp-aggregated shared-memory atomics, so structures of one bin keep
@@ -625,6 +782,12 @@ static void launch_k(bool pdl, void (*k)(P...), dim3 grid, dim3 block, cudaStrea
     else k<<<grid, block, 0, st>>>(static_cast<P>(args)...);
 }
 
+static void prep_launch(bool pdl, const double* lattice, int n, double rmax, Geo* geo, cudaStream_t st)
+{
+    if (n <= kPrepWideMax) launch_k(pdl, k_prep<8>, (n + 3) / 4, 32, st, lattice, n, rmax, geo);  // 4 per CTA
+    else launch_k(pdl, k_prep<1>, (n + 127) / 128, 128, st, lattice, n, rmax, geo);
+}
+
 // Structure-factor work of the last call (for xrd_work_counts): terms = sum of
 // reflections x atoms; phase seeds = the same with strided tiles, runs x atoms
 // with runs; out[0..2] = terms, seeds, tiles (out zeroed by the caller).
@@ -671,8 +834,7 @@ void launch_work(const GeomArgs& a, unsigned long long* out, cudaStream_t st)
 
 void launch_prep(const GeomArgs& a, cudaStream_t st, bool pdl)
 {
-    const int n = a.n_struct;  // 8 lanes per structure, 4 structures per 32-thread CTA
-    if (n > 0) launch_k(pdl, k_prep, (n + 3) / 4, 32, st, a.lattice, n, a.rmax, a.geo);
+    if (a.n_struct > 0) prep_launch(pdl, a.lattice, a.n_struct, a.rmax, a.geo, st);
 }
 
 void launch_coef(const GeomArgs& a, cudaStream_t st, bool pdl)
@@ -696,7 +858,7 @@ void launch_count_only(const GeomArgs& a, cudaStream_t st)
 {
     const int n = a.n_struct;
     if (n <= 0) return;
-    k_prep<<<(n + 3) / 4, 32, 0, st>>>(a.lattice, n, a.rmax, a.geo);  // 8 lanes per structure
+    prep_launch(false, a.lattice, n, a.rmax, a.geo, st);
     launch_pdl(k_count<false>, n, 256, 0, st, a.geo, a.r2min, a.r2max, (float)a.r2min, (float)a.r2max, 0,
                a.refl_cnt, (int64_t*)nullptr, (int*)nullptr);
 }
@@ -709,11 +871,23 @@ void launch_count(const GeomArgs& a, cudaStream_t st, bool pdl)
                  (float)a.r2min, (float)a.r2max, a.runs_mode ? a.rb : 0, a.refl_cnt, a.run_cnt, a.tcnt);
 }
 
+int scan_chunks(int n) { return (n + kScanItems * kScanThreads - 1) / (kScanItems * kScanThreads); }
+
 void launch_scan_refl(const GeomArgs& a, cudaStream_t st, bool pdl)
 {
-    launch_k(pdl, k_scan_refl, 1, kScanThreads, st, a.refl_cnt, a.run_cnt, a.geo, a.n_struct,
-             a.runs_mode ? 0 : 32 * a.rb, a.cap_refl, a.refl_off, a.tile_off, (const int*)a.order, a.cls_list,
-             a.abort_flag, a.totals, a.status, a.work);
+    const int nch = scan_chunks(a.n_struct);
+    const int tile_refl = a.runs_mode ? 0 : 32 * a.rb;
+    if (nch <= 2 || !a.parts) {  // one block walks the chunks
+        launch_k(pdl, k_scan_refl, 1, kScanThreads, st, a.refl_cnt, a.run_cnt, a.geo, a.n_struct, tile_refl,
+                 a.cap_refl, a.refl_off, a.tile_off, (const int*)a.order, a.cls_list, a.abort_flag, a.totals,
+                 a.status, a.work);
+        return;
+    }
+    launch_k(pdl, k_scan_refl_parts, nch, kScanThreads, st, a.refl_cnt, a.run_cnt, a.geo, a.n_struct, tile_refl,
+             (const int*)a.order, a.parts);
+    launch_k(true, k_scan_refl_final, nch, kScanThreads, st, a.refl_cnt, a.run_cnt, a.geo, a.n_struct, tile_refl,
+             a.cap_refl, a.refl_off, a.tile_off, (const int*)a.order, a.cls_list, a.abort_flag, a.totals, a.status,
+             a.work, (const long long*)a.parts);
 }
 
 void launch_emit(const GeomArgs& a, cudaStream_t st, bool pdl)

@@ -487,6 +487,83 @@ __global__ void __launch_bounds__(kOutThreads) k_scan_out(const CompactArgs a)
     }
 }
 
+// Multi-block form of k_scan_out for batches of more than two chunks: chunk
+// sums of kept peaks and families first, then every chunk scans its own
+// structures from the sums of the chunks before it.
+__global__ void __launch_bounds__(kOutThreads) k_scan_out_parts(const CompactArgs a)
+{
+    pdl_enter();
+    __shared__ long long ws[33];
+    if (*a.abort_flag) return;
+    const int n = a.n_struct, nt = blockDim.x, tid = threadIdx.x, base = blockIdx.x * kOutItems * nt;
+    long long p = 0, f = 0;
+#pragma unroll
+    for (int u = 0; u < kOutItems; u++) {
+        const int i = base + u * nt + tid;
+        if (i < n) {
+            p += a.npk[i];
+            f += a.nfm[i];
+        }
+    }
+    long long tp, tf;
+    block_prefix_ll(p, ws, &tp);
+    block_prefix_ll(f, ws, &tf);
+    if (tid == 0) {
+        a.parts[2 * blockIdx.x] = tp;
+        a.parts[2 * blockIdx.x + 1] = tf;
+    }
+}
+
+__global__ void __launch_bounds__(kOutThreads) k_scan_out_final(const CompactArgs a)
+{
+    pdl_enter();
+    __shared__ long long ws[33];
+    __shared__ long long buf[kOutItems * kOutThreads];
+    __shared__ long long pre[2], all[2];
+    if (*a.abort_flag) return;
+    const int n = a.n_struct, nt = blockDim.x, tid = threadIdx.x, b = blockIdx.x, base = b * kOutItems * nt;
+    if (tid < 2) {
+        long long q = 0, t = 0;
+        for (int c = 0; c < (int)gridDim.x; c++) {
+            const long long v = a.parts[2 * c + tid];
+            q += c < b ? v : 0;
+            t += v;
+        }
+        pre[tid] = q;
+        all[tid] = t;
+    }
+    __syncthreads();
+    const long long cp = all[0], cf = all[1];
+    const bool over = cp > a.cap_peaks || cf > a.cap_fam;
+    long long vp[kOutItems], vf[kOutItems], tp, tf;
+#pragma unroll
+    for (int u = 0; u < kOutItems; u++) {
+        const int i = base + u * nt + tid;
+        vp[u] = i < n ? a.npk[i] : 0;
+        vf[u] = i < n ? a.nfm[i] : 0;
+    }
+    chunk_scan<kOutItems>(vp, buf, ws, &tp);
+    chunk_scan<kOutItems>(vf, buf, ws, &tf);
+#pragma unroll
+    for (int u = 0; u < kOutItems; u++) {
+        const int i = base + u * nt + tid;
+        if (i < n) {
+            a.out.peak_off[i] = pre[0] + vp[u];
+            a.fam_soff[i] = pre[1] + vf[u];
+            if (over) a.out.status[i] = XRD_ECAPACITY;
+        }
+    }
+    if (b == 0 && tid == 0) {
+        a.out.peak_off[n] = cp;
+        a.fam_soff[n] = cf;
+        a.out.totals[1] = cp;
+        a.out.totals[2] = cf;
+        *a.out_abort = over;
+        if (over) a.out.totals[3] = n;
+        else a.out.fam_off[cp] = cf;
+    }
+}
+
 // largest s in [lo, n) with off[s] <= i, for off[lo] <= i < off[n]
 __device__ __forceinline__ int owner(const int64_t* __restrict__ off, int lo, int n, int64_t i)
 {
@@ -592,7 +669,13 @@ void launch_post(const PostArgs& a, const cudaStream_t* st)
 
 void launch_compact(const CompactArgs& a, cudaStream_t st)
 {
-    k_scan_out<<<1, kOutThreads, 0, st>>>(a);
+    const int nch = (a.n_struct + kOutItems * kOutThreads - 1) / (kOutItems * kOutThreads);
+    if (nch <= 2 || !a.parts) {
+        k_scan_out<<<1, kOutThreads, 0, st>>>(a);
+    } else {
+        k_scan_out_parts<<<nch, kOutThreads, 0, st>>>(a);
+        launch_pdl(k_scan_out_final, nch, kOutThreads, 0, st, a);
+    }
     if (a.n_struct > 0) launch_pdl(k_compact, a.grid * 8, kCompactThreads, 0, st, a);
 }
 

@@ -45,6 +45,7 @@ struct GeomArgs {
     int32_t* status;
     double* q;
     uint32_t* key;
+    long long* parts;  // chunk sums of the multi-block scan (nullptr: single-block scan)
 };
 
 struct SfArgs {
@@ -127,6 +128,7 @@ struct CompactArgs {
     const int* st_hkl;
     const int* st_mult;
     int* out_abort;     // set when the output capacity is too small
+    long long* parts;   // chunk sums of the multi-block scan (nullptr: single-block scan)
     xrd_pattern out;
 };
 

@@ -294,3 +294,15 @@ def test_query_sizes_counts_every_structure(gpu_lib, handle, n):
     sz = handle.query_sizes(db, gpu_lib.make_opts(o, "fp32_phasefix"))
     counts = [len(oracle.enumerate_refl(b.lattice[s], o)[0]) // 2 for s in range(n)]
     assert sz.n_refl == sum(counts) and sz.max_refl == max(counts)
+
+
+def test_multi_block_scans(gpu_lib, handle):
+    """9000 structures: three 4096-structure chunks (the last one ragged) take the multi-block
+    reflection and output scans; every structure against the oracle."""
+    b, o = synth.small(n=9000)
+    ref = oracle.pattern_batch(b, o, threads=0)
+    got = gpu_lib.compute(b, o, "fp32_phasefix", handle=handle)
+    st = compare_batch(got, ref, "fp32_phasefix", o.rel_cutoff, o.scaled)
+    assert st["pairs"] > 7_000_000 // 2
+    assert int(got["totals"][0]) == sum(int(x) for x in ref["n_refl"]) // 2
+    _report("multi_block_scans", st)
