@@ -306,3 +306,48 @@ def test_multi_block_scans(gpu_lib, handle):
     assert st["pairs"] > 7_000_000 // 2
     assert int(got["totals"][0]) == sum(int(x) for x in ref["n_refl"]) // 2
     _report("multi_block_scans", st)
+
+
+@pytest.mark.parametrize("workload", ["small", "mixed_sample"])
+def test_bench_launch_configuration_against_oracle(gpu_lib, workload):
+    """The configuration bench.py times: the autotuned launch shapes, the call captured as a CUDA
+    graph (profiling mode 2, the structure-factor events), replayed after an L2 flush on the
+    caller's stream; every structure of the small batch (sampled ones of 20 000 mixed cells)
+    against the oracle."""
+    import torch
+    xrd = gpu_lib
+    if workload == "small":
+        b, o = synth.small()
+        idx = np.arange(b.n_struct)
+    else:
+        b, o = synth.mixed(n=100_000)
+        b = b.subset(np.arange(20_000))
+        idx = np.random.default_rng(17).choice(b.n_struct, 400, replace=False)
+    h = xrd.Handle(0)
+    try:
+        db = xrd.DeviceBatch.from_host(b)
+        co = xrd.make_opts(o, "fp32_phasefix")
+        sz = h.query_sizes(db, co)
+        out = xrd.PatternBuffers(b.n_struct, sz.n_refl)
+        ws = xrd.workspace(sz.ws_bytes)
+        h.autotune(db, co, out, ws)
+        h.set_profiling(2)
+        g = h.graph(db, co, out, ws)
+        flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+        for _ in range(2):
+            flush.fill_(1.0)
+            g.launch(torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        h.set_profiling(0)
+        got = out.to_host()
+        assert np.all(got["status"] == 0)
+        sub = b.subset(idx)
+        ref = oracle.pattern_batch(sub, o, threads=0)
+        picked = {k: [got[k][i] for i in idx] for k in ("peak_tt", "peak_I", "peak_d", "peak_fam_off", "fam_hkl",
+                                                        "fam_mult")}
+        picked["status"] = got["status"][idx]
+        st = compare_batch(picked, ref, "fp32_phasefix", o.rel_cutoff, o.scaled)
+        _report("bench_configuration_" + workload, st)
+        g.close()
+    finally:
+        h.close()
