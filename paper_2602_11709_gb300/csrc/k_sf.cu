@@ -61,9 +61,11 @@ __device__ __forceinline__ float fprime_of(const Coef32& c, float s2)
 // FP32 variants: every atom record (staged by the warp in shared memory, read
 // by all lanes as a broadcast) feeds the lane's RB terms. With the integer phase
 // (XRD_FP32_PHASEFIX) and RUNS, the phase factor is formed exactly once per run
-// and atom, then rotated from l to l + 1 by the atom's exp(2 pi i z) (an
-// accurately rounded FP32 pair): one sin/cos pair per run instead of per
-// reflection. Otherwise every reflection's phase is formed exactly (integer
+// and atom, rotated from l to l + 1 by the atom's exp(2 pi i z) (an accurately
+// rounded FP32 pair), and carried to l + 2 and l + 3 by the two-term recurrence
+// e^{i(k+1)t} = 2 cos t e^{ikt} - e^{i(k-1)t} (two operations instead of four;
+// rounding grows by a few ulp over a run of four): one sin/cos pair per run
+// instead of per reflection. Otherwise every reflection's phase is formed exactly (integer
 // phase) or in FP64 (XRD_FP32_PHASE64).
 // GRAD also accumulates dF/ds^2 = sum_j occ_j exp(-B_j s^2)(f_j' - B_j f_j) e^{i phi_j}.
 template <int PREC, bool GRAD, int kSfRB, bool RUNS>
@@ -113,7 +115,7 @@ __device__ void sf_tile_fp32(const SfArgs& a, int64_t first, int len, int64_t j0
                     if (GRAD) fp[i] = fprime_of(c, s2[i]);
                 }
             }
-            float cs = 0.f, sn = 0.f, cz = 1.f, sz = 0.f;
+            float cs = 0.f, sn = 0.f, cz = 1.f, sz = 0.f, tcz = 2.f, cp = 0.f, sp = 0.f;
             double dx = 0.0, dy = 0.0, dz = 0.0;
             if (kRotate) {
                 const uint32_t P = uh[0] * at.X + uk[0] * at.Y + ul[0] * at.Z;
@@ -121,6 +123,7 @@ __device__ void sf_tile_fp32(const SfArgs& a, int64_t first, int len, int64_t j0
                 const float2 st = sstep[jj];
                 cz = st.x;
                 sz = st.y;
+                tcz = cz + cz;  // exact
             } else if (PREC == XRD_FP32_PHASE64) {
                 const Atom64 d = a.atom64[c0 + jj];
                 dx = d.x; dy = d.y; dz = d.z;
@@ -145,9 +148,18 @@ __device__ void sf_tile_fp32(const SfArgs& a, int64_t first, int len, int64_t j0
                     Gi[i] = fmaf(wd, sn, Gi[i]);
                 }
                 if (kRotate && i + 1 < kSfRB) {  // exp(2 pi i g.x) from l to l + 1
-                    const float c2 = fmaf(cs, cz, -sn * sz);
-                    sn = fmaf(cs, sz, sn * cz);
+                    float c2, s2n;
+                    if (i == 0) {  // the rotation by exp(2 pi i z)
+                        c2 = fmaf(cs, cz, -sn * sz);
+                        s2n = fmaf(cs, sz, sn * cz);
+                    } else {  // two-term recurrence: e^{i(k+1)t} = 2 cos t e^{ikt} - e^{i(k-1)t}
+                        c2 = fmaf(tcz, cs, -cp);
+                        s2n = fmaf(tcz, sn, -sp);
+                    }
+                    cp = cs;
+                    sp = sn;
                     cs = c2;
+                    sn = s2n;
                 }
             }
         }
