@@ -80,7 +80,9 @@ def reduce_over_ranks(terms, structures, seconds, world, device="cpu"):
 # written intensities stay in L2); other workloads and shapes: not captured (null)
 SF_TRAFFIC_BYTES = {("small", 64, 1, 0): 13618432, ("small", 64, 2, 0): 13618688, ("small", 64, 4, 0): 13618176,
                     ("small", 128, 1, 0): 13556224, ("small", 128, 2, 0): 13555968, ("small", 128, 4, 0): 13556224,
-                    ("small", 128, 2, 1): 15159040}
+                    ("small", 128, 2, 1): 15159040, ("mixed", 128, 1, 0): 1243995648,
+                    ("mixed", 64, 1, 0): 1247074816, ("large", 128, 1, 1): 228812544,
+                    ("large", 128, 2, 1): 228943360}
 # SFU issue rates per SM per clock measured on this GB300 (MUFU.SIN/COS 16, MUFU.EX2 32) and the
 # maximum SM clock; the structure-factor roofline of a batch follows from its mix of operations.
 MUFU_SINCOS_PER_CLK = 16.0
