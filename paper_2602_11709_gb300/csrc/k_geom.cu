@@ -179,12 +179,22 @@ __global__ void __launch_bounds__(128) k_atoms(const int64_t* __restrict__ atom_
         }
         return;
     }
-    if (threadIdx.x == 0) {  // exclusive offset of each element's run (serial over <= 256 entries)
-        int run = 0;
-        for (int z = 0; z <= zmax; z++) {
-            const int c = off[z];
-            off[z] = run;
-            run += c;
+    if (threadIdx.x < 32) {  // exclusive offset of each element's run: one warp, 8 elements a lane
+        constexpr int per = (kZmaxLimit + 1) / 32;
+        const int lane = threadIdx.x;
+        int v[per], sum = 0;
+#pragma unroll
+        for (int k = 0; k < per; k++) {
+            const int z = lane * per + k;
+            v[k] = z <= zmax ? off[z] : 0;
+            sum += v[k];
+        }
+        int run = warp_incl_scan(sum) - sum;
+#pragma unroll
+        for (int k = 0; k < per; k++) {
+            const int z = lane * per + k;
+            if (z <= zmax) off[z] = run;
+            run += v[k];
         }
     }
     __syncthreads();
