@@ -399,7 +399,7 @@ def run_ours(args):
                     "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_s * 1e3,
                     "api": "xrd.PatternPipeline, two batches in flight"},
             "clocks": ck,
-            "gpu_launches": xrd.LAUNCHES_PER_BATCH * args.steps,
+            "gpu_launches": xrd.launches_per_batch(b.n_struct) * args.steps,
             "stage_ms": {k: v / n_stage_steps for k, v in stage_acc.items()},
             "stage_ms_note": "separate pass with events between all stages (adds time per stage)",
             "other_precisions": extra,

@@ -24,6 +24,12 @@ STAGES = ["prep", "atoms", "count", "scan", "emit", "structure_factor", "post", 
 LAUNCHES_PER_BATCH = 16
 
 
+def launches_per_batch(n_struct: int) -> int:
+    """Kernels of one xrd_pattern_batch call: above two chunks of 4096 structures the reflection
+    scan and the output scan each take two kernels (chunk sums, then the chunks)."""
+    return LAUNCHES_PER_BATCH + (2 if (n_struct + 4095) // 4096 > 2 else 0)
+
+
 class xrd_batch(C.Structure):
     _fields_ = [("n_struct", C.c_int32), ("zmax", C.c_int32), ("n_atoms", C.c_int64), ("lattice", C.c_void_p),
                 ("atom_off", C.c_void_p), ("frac", C.c_void_p), ("Z", C.c_void_p), ("occ", C.c_void_p),
