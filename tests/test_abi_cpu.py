@@ -99,3 +99,9 @@ def test_missing_library_fails_loudly(tmp_path):
             xrd.load(str(tmp_path / "nope.so"))
     finally:
         xrd._lib = saved
+
+
+def test_launch_count_per_call():
+    """Kernels per xrd_pattern_batch call: 18 above two chunks of 4096 structures (two-kernel scans)."""
+    assert xrd.launches_per_batch(1024) == 16 and xrd.launches_per_batch(8192) == 16
+    assert xrd.launches_per_batch(8193) == 18 and xrd.launches_per_batch(100_000) == 18

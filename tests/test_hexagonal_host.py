@@ -25,8 +25,3 @@ def test_miller_bravais():
     mb = xrd.miller_bravais(hkl)
     assert mb.tolist() == [[1, 0, -1, 0], [1, -1, 0, 2], [-2, 3, -1, 5]]
     assert np.all(mb[:, :3].sum(axis=1) == 0)
-
-
-def test_launch_count():
-    assert xrd.launches_per_batch(1024) == 16 and xrd.launches_per_batch(8192) == 16
-    assert xrd.launches_per_batch(8193) == 18 and xrd.launches_per_batch(100_000) == 18
