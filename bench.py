@@ -7,10 +7,14 @@ sort, merge, families, cutoff, scaling, compaction) over the batch, inputs
 resident in HBM. L2 is flushed (256 MiB write) between timed steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload small|mixed|large] [--path pattern|augmented]
+                  [--sf-shape TILE,WARPS,RUNS | --no-tune] [--no-graph]
 
-Under torchrun (N > 1) every rank runs its own replica of the batch (weak
-scaling, no collective on the data path); value = all ranks' terms / max time.
-`--impl reference` times the FP64 CPU oracle on the host cores instead.
+Under torchrun (N > 1) each rank takes one shard of a batch N times larger
+(weak scaling, no collective on the data path); value = all ranks' terms / max
+time. `--impl reference` times the FP64 CPU oracle on the host cores instead.
+`--path augmented` times xrd_pattern_augmented (pseudo-Voigt profiles,
+March-Dollase orientation and noise on a 4096-point grid) on the same batch.
 """
 from __future__ import annotations
 
