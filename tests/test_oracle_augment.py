@@ -5,8 +5,9 @@ The profile is pinned by its integral (the closed forms of the Lorentzian and
 Gaussian areas between the grid ends), by the half maximum at 2theta +- fwhm/2
 for every mixing eta, and by its Gaussian limit against the oracle's
 unit-height broadened pattern; the March-Dollase factor by its closed forms at
-0, 45 and 90 degrees, its symmetries, and its normalisation over the sphere
-(mean 1 over uniformly distributed directions); the noise by its limits.
+0, 45 and 90 degrees, its symmetries, its normalisation over the sphere (mean 1
+over uniformly distributed directions) and, in a triclinic cell, the angle
+between g and n taken from Cartesian reciprocal vectors; the noise by its limits.
 """
 import math
 
@@ -120,3 +121,26 @@ def test_noise_limits():
     d2 = oracle.augmented(b, 0, hkl, *args, z=z, sigma=1.0) - y
     assert np.allclose(d2, 2 * d1, rtol=1e-12, atol=1e-12 * np.abs(d2).max())
     assert np.all(np.sign(d1[y > 0]) == np.sign(z[y > 0]))
+
+
+def test_march_dollase_angle_in_a_triclinic_cell():
+    """The angle between g and n from Cartesian reciprocal vectors (rows of inv(A).T for the
+    direct cell vectors A, built from a, b, c, alpha, beta, gamma independently of the metric
+    tensors) agrees with the oracle's metric form for a low-symmetry cell."""
+    lat = np.array([4.1, 5.3, 6.2, 81.0, 97.0, 104.0])
+    a, b, c = lat[:3]
+    al, be, ga = np.radians(lat[3:])
+    A = np.zeros((3, 3))
+    A[0] = [a, 0.0, 0.0]
+    A[1] = [b * np.cos(ga), b * np.sin(ga), 0.0]
+    cx = c * np.cos(be)
+    cy = c * (np.cos(al) - np.cos(be) * np.cos(ga)) / np.sin(ga)
+    A[2] = [cx, cy, np.sqrt(c * c - cx * cx - cy * cy)]
+    Bstar = np.linalg.inv(A).T  # rows: a*, b*, c*
+    r = 1.3
+    for g in ((1, 2, 3), (-2, 1, 0), (3, -1, 2), (0, 0, 1)):
+        for n in ((1.0, -1.0, 2.0), (0.0, 1.0, 0.0), (2.0, 0.5, -1.0)):
+            gc, nc = np.asarray(g) @ Bstar, np.asarray(n) @ Bstar
+            cos2 = (gc @ nc) ** 2 / ((gc @ gc) * (nc @ nc))
+            want = (r * r * cos2 + (1.0 - cos2) / r) ** -1.5
+            assert oracle.march_dollase(lat, *g, n, r) == pytest.approx(want, rel=1e-12), (g, n)
