@@ -49,7 +49,7 @@ class BroadenedPattern(torch.autograd.Function):
         ws = xrd.workspace(sz.ws_grad_bytes, frac.device)
         n = db.n_struct
         y = torch.empty(n, int(grid.n_pts), dtype=torch.float32, device=frac.device)
-        status = torch.zeros(max(n, 1), dtype=torch.int32, device=frac.device)
+        status = torch.zeros(n, dtype=torch.int32, device=frac.device)
         totals = torch.zeros(4, dtype=torch.int64, device=frac.device)
         handle.pattern_broadened(db, co, cg, y, status, totals, ws)
         ctx.state = (db, co, cg, ws, handle, status)

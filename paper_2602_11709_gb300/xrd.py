@@ -142,6 +142,20 @@ def _torch():
     return torch
 
 
+def check_tensor(name, t, dtype, shape, optional=False):
+    """Argument check of the binding: a contiguous tensor of this dtype and shape (None when optional).
+    Raises XrdError(XRD_EINVAL) otherwise, before any pointer reaches the library."""
+    if t is None:
+        if optional:
+            return
+        raise XrdError(XRD_EINVAL, "%s is required" % name)
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or t.dtype != dtype or not t.is_contiguous():
+        raise XrdError(XRD_EINVAL, "%s must be a contiguous %s tensor" % (name, dtype))
+    if tuple(t.shape) != tuple(shape):
+        raise XrdError(XRD_EINVAL, "%s has shape %s, expected %s" % (name, tuple(t.shape), tuple(shape)))
+
+
 def _stream_ptr(stream):
     torch = _torch()
     s = stream if stream is not None else torch.cuda.current_stream()
@@ -446,6 +460,10 @@ class Handle:
 
     def pattern_broadened(self, db: DeviceBatch, opts: xrd_opts, grid: xrd_grid, y, status, totals, ws, stream=None):
         """Gaussian-broadened patterns y [n_struct][n_pts] (float32); ws keeps the state for pattern_grad."""
+        torch = _torch()
+        check_tensor("y", y, torch.float32, (db.n_struct, int(grid.n_pts)))
+        check_tensor("status", status, torch.int32, (db.n_struct,))
+        check_tensor("totals", totals, torch.int64, (4,))
         b = db.c()
         self._check(self.lib.xrd_pattern_broadened(self.h, C.byref(b), C.byref(opts), C.byref(grid),
                                                    C.c_void_p(y.data_ptr()), C.c_void_p(status.data_ptr()),
@@ -457,6 +475,18 @@ class Handle:
         """Augmented patterns y [n_struct][n_pts] (float32): per-structure pseudo-Voigt (fwhm, eta: float64
         device tensors [n_struct]), March-Dollase (po_dir [n_struct][3], po_r [n_struct]) and noise
         (noise_z float32 [n_struct][n_pts] standard normal draws, noise_sigma float64 [n_struct])."""
+        torch = _torch()
+        n, npts = db.n_struct, int(grid.n_pts)
+        f64, f32 = torch.float64, torch.float32
+        check_tensor("fwhm", fwhm, f64, (n,))
+        check_tensor("eta", eta, f64, (n,))
+        check_tensor("po_dir", po_dir, f64, (n, 3), optional=True)
+        check_tensor("po_r", po_r, f64, (n,), optional=True)
+        check_tensor("noise_z", noise_z, f32, (n, npts), optional=True)
+        check_tensor("noise_sigma", noise_sigma, f64, (n,), optional=True)
+        check_tensor("y", y, f32, (n, npts))
+        check_tensor("status", status, torch.int32, (n,))
+        check_tensor("totals", totals, torch.int64, (4,))
         b = db.c()
         ptr = lambda t: None if t is None else t.data_ptr()  # noqa: E731
         aug = xrd_augment(ptr(fwhm), ptr(eta), ptr(po_dir), ptr(po_r), ptr(noise_z), ptr(noise_sigma))
@@ -468,6 +498,11 @@ class Handle:
     def pattern_grad(self, db: DeviceBatch, opts: xrd_opts, grid: xrd_grid, dLdy, d_frac, d_B, d_lat, ws,
                      stream=None):
         """Gradients of L through the preceding pattern_broadened call on the same workspace."""
+        torch = _torch()
+        check_tensor("dLdy", dLdy, torch.float32, (db.n_struct, int(grid.n_pts)))
+        check_tensor("d_frac", d_frac, torch.float32, (db.n_atoms, 3))
+        check_tensor("d_B", d_B, torch.float32, (db.n_atoms,))
+        check_tensor("d_lat", d_lat, torch.float32, (db.n_struct, 6))
         b = db.c()
         self._check(self.lib.xrd_pattern_grad(self.h, C.byref(b), C.byref(opts), C.byref(grid),
                                               C.c_void_p(dLdy.data_ptr()), C.c_void_p(d_frac.data_ptr()),

@@ -105,3 +105,17 @@ def test_launch_count_per_call():
     """Kernels per xrd_pattern_batch call: 18 above two chunks of 4096 structures (two-kernel scans)."""
     assert xrd.launches_per_batch(1024) == 16 and xrd.launches_per_batch(8192) == 16
     assert xrd.launches_per_batch(8193) == 18 and xrd.launches_per_batch(100_000) == 18
+
+
+def test_binding_argument_checks():
+    """The binding refuses a tensor of the wrong dtype, layout or shape before calling the library."""
+    import torch
+    xrd.check_tensor("y", torch.zeros(2, 5, dtype=torch.float32), torch.float32, (2, 5))
+    xrd.check_tensor("po_dir", None, torch.float64, (2, 3), optional=True)
+    bad = [(None, torch.float64, (2,), False),                                   # required
+           (torch.zeros(2, dtype=torch.float32), torch.float64, (2,), False),    # dtype
+           (torch.zeros(2, 3, dtype=torch.float64).t(), torch.float64, (3, 2), False),  # not contiguous
+           (torch.zeros(3, dtype=torch.float64), torch.float64, (2,), False)]    # shape
+    for t, dt, shape, opt in bad:
+        with pytest.raises(xrd.XrdError):
+            xrd.check_tensor("x", t, dt, shape, optional=opt)
