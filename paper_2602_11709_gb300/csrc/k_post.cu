@@ -623,7 +623,7 @@ __global__ void __launch_bounds__(kCompactThreads) k_compact(const CompactArgs a
             }
         }
         __syncthreads();  // every thread has read s_cur
-        if (tid == kCompactThreads - 1) s_cur = s;  // owner of this round's last peak
+        if (tid == kCompactThreads - 1) s_cur = s;  // owner of this pass's last peak
         __syncthreads();
     }
 }
