@@ -196,3 +196,15 @@ def test_profiling_times_the_profile_sum(gpu_lib, handle):
     finally:
         handle.set_profiling(0)
     assert st["profile_sum"] > 0.0 and all(v == 0.0 for k, v in st.items() if k != "profile_sum")
+
+
+def test_large_batch_takes_the_multi_block_scans(gpu_lib, handle):
+    """9000 structures (three 4096-structure scan chunks): the augmented path's front runs the
+    multi-block reflection scan; sampled structures against the oracle."""
+    b, o = synth.small(n=9000)
+    grid = synth.Grid(t0=0.0, dt=90.0 / 1023.0, n_pts=1024)
+    aug = synth.augment(b.n_struct, grid.n_pts, seed=13)
+    y, status, totals = _run(gpu_lib, handle, b, o, grid, aug)
+    assert np.all(status == 0) and totals[3] == 0 and np.all(np.isfinite(y))
+    for s in (0, 4095, 4096, 8191, 8999):
+        _check(y[s], _ref(b, s, o, grid, aug), s)
