@@ -124,3 +124,32 @@ def test_mixed_site_is_linear_in_the_species_occupancies():
         rest = F(np.zeros(3), hkl)
         parts = [F(np.eye(3)[j], hkl) - rest for j in range(3)]
         assert abs(full - (rest + sum(x[j] * parts[j] for j in range(3)))) <= 1e-12 * max(abs(full), 1.0)
+
+
+@pytest.mark.parametrize("seed", [50, 51, 52, 53])
+def test_family_multiplicities_partition_the_sphere(seed):
+    """Without a cutoff every reflection of the sphere is in exactly one family of exactly one
+    peak, P1 and hexagonal cells alike, and every family representative lies inside the sphere
+    within the merge tolerance above its peak's anchor."""
+    rng = np.random.default_rng(seed)
+    coef = synth.coef_table(rng)
+    hexa = seed % 2 == 0
+    if hexa:
+        a = rng.uniform(2.5, 6.0)
+        lat = [a, a, rng.uniform(3.0, 9.0), 90.0, 90.0, 120.0]
+    else:
+        lat = list(rng.uniform(3.0, 9.0, 3)) + list(synth._angles(rng, 1)[0])
+    n = int(rng.integers(2, 9))
+    b = _struct(lat, rng.random((n, 3)), rng.integers(1, 84, n), np.ones(n), rng.uniform(0, 1, n), coef)
+    o = _opts(tt_min=0.0, tt_max=100.0, rel_cutoff=0.0, scaled=0)
+    res = oracle.pattern(b, 0, o)
+    assert oracle.is_hexagonal(lat) == hexa
+    assert int(res["fam_mult"].sum()) == res["n_refl"]
+    _, Gs, _ = oracle.metric(b.lattice[0])
+    off = res["peak_fam_off"]
+    for p in range(len(res["peak_tt"])):
+        for f in range(off[p], off[p + 1]):
+            q = oracle.q_of(Gs, *(int(v) for v in res["fam_hkl"][f]))
+            _, tt, _, _ = oracle.refl(q, o.wavelength)
+            # the anchor rule: every member of a peak lies in [anchor, anchor + tol)
+            assert 0.0 < tt <= o.tt_max and -1e-12 <= tt - res["peak_tt"][p] < o.tt_tol
