@@ -74,6 +74,30 @@ int main(void) {
     assert int(got["xrd_augment.noise_sigma"]) == xrd.xrd_augment.noise_sigma.offset
 
 
+def test_every_struct_field_matches_c():
+    """Size and every field offset of each ctypes mirror against the C compiler's layout of xrd.h."""
+    structs = [xrd.xrd_batch, xrd.xrd_opts, xrd.xrd_sizes, xrd.xrd_grid, xrd.xrd_augment, xrd.xrd_pattern]
+    lines = []
+    for S in structs:
+        lines.append('printf("%%s %%zu\\n", "%s", sizeof(%s));' % (S.__name__, S.__name__))
+        for f, _ in S._fields_:
+            cname = f.rstrip("_")  # lambda is a Python keyword
+            lines.append('printf("%%s %%zu\\n", "%s.%s", offsetof(%s, %s));' % (S.__name__, f, S.__name__, cname))
+    src = "#include <stdio.h>\n#include <stddef.h>\n#include \"xrd.h\"\nint main(void) {\n" + "\n".join(lines) + \
+        "\nreturn 0;\n}\n"
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        open(c, "w").write(src)
+        exe = os.path.join(d, "t")
+        subprocess.run(["gcc", "-I" + os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+        out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = dict(line.split() for line in out if line.strip())
+    for S in structs:
+        assert int(got[S.__name__]) == C.sizeof(S), S.__name__
+        for f, _ in S._fields_:
+            assert int(got["%s.%s" % (S.__name__, f)]) == getattr(S, f).offset, (S.__name__, f)
+
+
 def test_create_without_gpu_fails_cleanly(lib):
     import torch
     if torch.cuda.is_available():
