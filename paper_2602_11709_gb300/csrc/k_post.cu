@@ -58,21 +58,39 @@ const TTab* init_tables(cudaStream_t st)
     return (const TTab*)p;
 }
 
-// Merge test: 2theta(qb) - 2theta(qa) < tol for qb >= qa > 0, decided to about
-// 1e-6 relative. With x = lambda sqrt(q) / 2 = sin theta and c = cos theta,
+// 2-theta in degrees from |g|^2 in FP64, the definition 2 asin(lambda |g| / 2)
+// with every step rounded on its own (no contraction), sin(theta) clamped at 1.
+__device__ __noinline__ double tt_deg64(double q, double lambda)
+{
+    double sth = __dmul_rn(__dmul_rn(lambda, __dsqrt_rn(q)), 0.5);
+    if (sth > 1.0) sth = 1.0;
+    return __dmul_rn(__dmul_rn(2.0, asin(sth)), 180.0 / kPi);
+}
+
+// Merge test: 2theta(qb) - 2theta(qa) < tol for qb >= qa > 0. With
+// x = lambda sqrt(q) / 2 = sin theta and c = cos theta,
 // tan((2theta_b - 2theta_a) / 4) = (xb - xa) / (ca + cb) and
 // xb - xa = (lambda / 2)(qb - qa) / (sqrt qa + sqrt qb); qb - qa is exact in FP64
 // for close values. Comparing against ttol = tan(tol / 4) (tol in radians)
-// leaves neither a division nor an arctangent.
-__device__ __forceinline__ bool tt_close(double qa, double qb, float l2, float lh, float ttol)
+// leaves neither a division nor an arctangent. This FP32 form is good to about
+// 1e-6 relative, plus the rounding of 1 - lambda^2 q / 4 relative to cos^2(theta)
+// (~1.3e-7 / cos^2); a pair within 1e-5 + 1e-6 / cos^2 of the tolerance is
+// decided in FP64 from the definition instead, so that every merge decision is
+// the FP64 one.
+__device__ __forceinline__ bool tt_close(double qa, double qb, float l2, float lh, float ttol, double lambda,
+                                         double tol)
 {
     if (dbits(qb) <= dbits(qa)) return ttol > 0.f;  // equal |g|^2: a gap of 0
+    if (ttol == INFINITY) return true;              // tol above 180 degrees: every gap is below it
     const float dqf = d2f_pos(qb - qa);
     const float qaf = d2f_pos(qa), qbf = d2f_pos(qb);
     const float ua = fmaxf(fmaf(-l2, qaf, 1.f), 1e-30f), ub = fmaxf(fmaf(-l2, qbf, 1.f), 1e-30f);
     const float sq = qaf * rsqrtf(qaf) + qbf * rsqrtf(qbf);
     const float c = ua * rsqrtf(ua) + ub * rsqrtf(ub);
-    return lh * dqf < ttol * (sq * c);
+    const float lhs = lh * dqf, rhs = ttol * (sq * c);
+    const float band = fmaf(1e-6f, __frcp_rn(fminf(ua, ub)), 1e-5f);
+    if (!(fabsf(lhs - rhs) <= band * rhs)) return lhs < rhs;
+    return __dsub_rn(tt_deg64(qb, lambda), tt_deg64(qa, lambda)) < tol;
 }
 
 // Family key: the absolute values of the indices sorted descending, packed:
@@ -189,6 +207,7 @@ __device__ void post_structure(const PostArgs& a, int s, int64_t base, int n, co
 {
     const int tid = threadIdx.x, nt = blockDim.x;
     const float l2 = a.l2f, lh = a.lhf, ttol = a.ttol;
+    const double lam = a.lambda, tol = a.tol;
     const bool hex = a.geo[s].hex != 0;  // Miller-Bravais families
     // ---- bucket sort on |g|^3 in [r2min^1.5, r2max^1.5] (a monotone map of |g|^2) ----
     // fcnt holds each reflection's bucket and pst the bucket-ordered reflections
@@ -231,7 +250,7 @@ __device__ void post_structure(const PostArgs& a, int s, int64_t base, int n, co
     // ---- anchor merge: definite starts, then one thread per run ----
     int close_pair = 0;
     for (int i = tid; i < n; i += nt) {
-        const bool start = (i == 0) || !tt_close(q[perm[i - 1]], q[perm[i]], l2, lh, ttol);
+        const bool start = (i == 0) || !tt_close(q[perm[i - 1]], q[perm[i]], l2, lh, ttol, lam, tol);
         flag[i] = start;
         close_pair |= !start;
     }
@@ -245,7 +264,7 @@ __device__ void post_structure(const PostArgs& a, int s, int64_t base, int n, co
         pst[i] = 1;
         for (int j = i + 1; j < n && !flag[j]; j++) {
             const double qj = q[perm[j]];
-            if (!tt_close(qa, qj, l2, lh, ttol)) {
+            if (!tt_close(qa, qj, l2, lh, ttol, lam, tol)) {
                 pst[j] = 1;
                 qa = qj;
             } else {

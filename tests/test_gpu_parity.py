@@ -354,3 +354,37 @@ def test_bench_launch_configuration_against_oracle(gpu_lib, workload):
         g.close()
     finally:
         h.close()
+
+
+def _near_tolerance_case(lat, seed):
+    """A two-atom cell and the gap between two neighbouring distinct 2-theta values (an anchor and
+    the next line, both well apart from their other neighbours), as the oracle computes it."""
+    rng = np.random.default_rng(seed)
+    coef = synth.coef_table(rng)
+    b = synth.Batch(np.asarray([lat], np.float64), np.array([0, 2], np.int64), rng.random((2, 3)),
+                    np.array([26, 8], np.int16), np.ones(2), np.array([0.4, 0.9]), coef)
+    o = synth.Opts(synth.CU_KA, 0.0, 70.0, 1e-5, 0.0, 0)
+    u = np.unique(oracle.pattern(b, 0, o)["refl_tt"])
+    for i in range(1, len(u) - 2):
+        gap = u[i + 1] - u[i]
+        if 0.005 < gap < 0.3 and u[i] - u[i - 1] > 2 * gap and u[i + 2] - u[i + 1] > 2 * gap:
+            return b, o, gap
+    raise AssertionError("no isolated pair")
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("cell", ["orthorhombic", "triclinic"])
+def test_merge_decision_at_the_tolerance(gpu_lib, handle, prec, cell):
+    """Two lines whose 2-theta gap lies 2e-8 (relative) below or above the tolerance: the GPU
+    merges exactly when the oracle's FP64 difference of 2 asin(lambda |g| / 2) is below it."""
+    lat = [4.0, 4.004, 5.3, 90.0, 90.0, 90.0] if cell == "orthorhombic" else [4.7, 5.9, 6.4, 83.0, 101.0, 112.0]
+    b, o, gap = _near_tolerance_case(lat, 31)
+    counts = []
+    for rel in (2e-8, -2e-8):
+        oo = _opts(o, tt_tol=gap * (1 + rel))
+        ref = oracle.pattern_batch(b, oo, threads=1)
+        got = gpu_lib.compute(b, oo, prec, handle=handle)
+        st = compare_batch(got, ref, prec, oo.rel_cutoff, oo.scaled)
+        assert st["boundary"] == 0
+        counts.append(len(ref["peak_tt"][0]))
+    assert counts[0] + 1 == counts[1]  # the pair merges below the tolerance and not above it
