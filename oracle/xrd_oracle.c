@@ -12,7 +12,10 @@
  * definition: no blocking, no reordering, no shortcut (the full sphere of
  * reflections is enumerated, Friedel mates included).
  *
- * Parity pins for each function live in tests/test_oracle_*.py.
+ * Parity pins for each function live in tests/test_oracle_*.py. Agreement with
+ * pymatgen's own patterns is parity unpinned: its tabulated scattering-factor
+ * coefficients are not available, so every table here is a seeded stand-in
+ * passed in by the caller.
  */
 #include "xrd_oracle.h"
 
