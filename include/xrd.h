@@ -62,12 +62,17 @@ typedef struct {
     const double* coef;      /* [zmax + 1][4][2]: (a_i, b_i) of f(s) = Z - 41.78214 s^2 sum a_i exp(-b_i s^2) */
 } xrd_batch;
 
+/* Smallest accepted merge tolerance, degrees. */
+#define XRD_MIN_TT_TOL 1e-9
+
 /* Options (host struct). */
 typedef struct {
     double lambda;     /* wavelength, angstrom, > 0 */
     double tt_min;     /* 2-theta range in degrees, 0 <= tt_min < tt_max <= 180, both inclusive */
     double tt_max;
-    double tt_tol;     /* merge tolerance in degrees (>= 0): join the peak while 2theta - anchor < tt_tol */
+    double tt_tol;     /* merge tolerance in degrees, >= XRD_MIN_TT_TOL: join the peak while 2theta - anchor < tt_tol.
+                          Smaller values are refused (XRD_EINVAL): 2theta itself carries ~1e-13 degrees of
+                          rounding, and a reflection and its Friedel mate always share one peak. */
     double rel_cutoff; /* keep merged peaks with I > rel_cutoff * Imax; 0 keeps all; [0, 1) */
     int32_t scaled;    /* 1: scale intensities to 100 * (I / Imax); 0: absolute */
     int32_t precision; /* XRD_FP64, XRD_FP32_PHASE64 or XRD_FP32_PHASEFIX */

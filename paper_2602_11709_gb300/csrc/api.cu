@@ -206,7 +206,8 @@ int check_opts(xrd_handle* h, const xrd_opts* o)
     if (!(o->lambda > 0.0) || !std::isfinite(o->lambda)) return fail(h, XRD_EINVAL, "lambda must be finite and > 0");
     if (!(o->tt_min >= 0.0 && o->tt_min < o->tt_max && o->tt_max <= 180.0))
         return fail(h, XRD_EINVAL, "need 0 <= tt_min < tt_max <= 180");
-    if (!(o->tt_tol >= 0.0) || !std::isfinite(o->tt_tol)) return fail(h, XRD_EINVAL, "tt_tol must be finite and >= 0");
+    if (!(o->tt_tol >= XRD_MIN_TT_TOL) || !std::isfinite(o->tt_tol))
+        return fail(h, XRD_EINVAL, "tt_tol must be finite and >= 1e-9 degrees");
     if (!(o->rel_cutoff >= 0.0 && o->rel_cutoff < 1.0)) return fail(h, XRD_EINVAL, "rel_cutoff must be in [0, 1)");
     if (o->scaled != 0 && o->scaled != 1) return fail(h, XRD_EINVAL, "scaled must be 0 or 1");
     if (o->precision < XRD_FP64 || o->precision > XRD_FP32_PHASEFIX) return fail(h, XRD_EINVAL, "unknown precision");

@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libxrd.so")
 
 XRD_OK, XRD_EINVAL, XRD_ECAPACITY, XRD_ECUDA, XRD_ETIMEOUT = 0, 1, 2, 3, 4
 XRD_FP64, XRD_FP32_PHASE64, XRD_FP32_PHASEFIX = 0, 1, 2
+XRD_MIN_TT_TOL = 1e-9  # smallest merge tolerance the library accepts, degrees
 PRECISIONS = {"fp64": XRD_FP64, "fp32_phase64": XRD_FP32_PHASE64, "fp32_phasefix": XRD_FP32_PHASEFIX}
 STAGES = ["prep", "atoms", "count", "scan", "emit", "structure_factor", "post", "compact", "profile_sum"]
 # kernels xrd_pattern_batch launches per call: order, coef, atoms (a side stream), prep, count, scan, emit,

@@ -98,6 +98,18 @@ def test_every_struct_field_matches_c():
             assert int(got["%s.%s" % (S.__name__, f)]) == getattr(S, f).offset, (S.__name__, f)
 
 
+def test_header_constants_match_binding():
+    """Return codes, precisions and the smallest merge tolerance: the #defines of xrd.h equal the
+    binding's constants."""
+    text = open(HEADER).read()
+    m = re.search(r"#define\s+XRD_MIN_TT_TOL\s+([0-9.eE+-]+)", text)
+    assert m and float(m.group(1)) == xrd.XRD_MIN_TT_TOL
+    for name in ("XRD_OK", "XRD_EINVAL", "XRD_ECAPACITY", "XRD_ECUDA", "XRD_ETIMEOUT", "XRD_FP64",
+                 "XRD_FP32_PHASE64", "XRD_FP32_PHASEFIX"):
+        m = re.search(r"#define\s+%s\s+(\d+)\b" % name, text)
+        assert m and int(m.group(1)) == getattr(xrd, name), name
+
+
 def test_create_without_gpu_fails_cleanly(lib):
     import torch
     if torch.cuda.is_available():
