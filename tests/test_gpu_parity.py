@@ -187,6 +187,11 @@ def test_capacity_errors(gpu_lib, handle):
     with pytest.raises(xrd.XrdError) as e:
         handle.pattern_batch(db, xrd.make_opts(synth.Opts(wavelength=-1.0)), out, ws)
     assert e.value.code == xrd.XRD_EINVAL
+    for tol in (0.0, 1e-10, -1e-5, float("nan")):  # below the smallest merge tolerance
+        with pytest.raises(xrd.XrdError) as e:
+            handle.pattern_batch(db, xrd.make_opts(synth.Opts(tt_tol=tol), "fp32_phasefix"), out, ws)
+        assert e.value.code == xrd.XRD_EINVAL
+    handle.pattern_batch(db, xrd.make_opts(synth.Opts(tt_tol=xrd.XRD_MIN_TT_TOL), "fp32_phasefix"), out, ws)
     with pytest.raises(xrd.XrdError) as e:
         handle.pattern_batch(db, co, out, xrd.workspace(64))
     assert e.value.code == xrd.XRD_ECAPACITY
