@@ -122,7 +122,8 @@ class XRDCalculator:
     wavelength: a key of WAVELENGTHS or a value in angstrom. coef: the scattering-factor
     table, float64 [zmax + 1][4][2] of (a_i, b_i) in f(s) = Z - 41.78214 s^2 sum a_i exp(-b_i s^2).
     debye_waller_factors: {symbol: B in angstrom^2} (default 0). rel_cutoff: peaks at or below
-    this fraction of the largest are dropped (0 keeps all); tt_tol: merge tolerance in degrees.
+    this fraction of the largest are dropped (0 keeps all); tt_tol: merge tolerance in degrees
+    (at least xrd.XRD_MIN_TT_TOL = 1e-9).
     """
 
     def __init__(self, coef, wavelength="CuKa", debye_waller_factors=None, precision="fp32_phasefix",
