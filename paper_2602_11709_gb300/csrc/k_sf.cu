@@ -36,11 +36,23 @@ __device__ __forceinline__ float f_of(const Coef32& c, float zf, float s2)
     return fmaf(s2, fmaf(c.a[0], e0, fmaf(c.a[1], e1, fmaf(c.a[2], e2, c.a[3] * e3))), zf);
 }
 
-__device__ __forceinline__ float lp_of(float qf, float l2)
+// cos^2(theta) at theta = 90 degrees as FP64 evaluates it (cos of the double nearest pi/2,
+// squared): the floor of cos^2 theta, so that a reflection on the 2theta = 180 degrees
+// surface gets a large finite Lorentz factor instead of a division by zero.
+constexpr double kCos90Sq = 3.749399456654644e-33;
+
+// Lorentz-polarisation factor (1 + cos^2 2theta) / (sin^2 theta cos theta) with
+// sin^2 theta = X = q lambda^2 / 4. Up to 2theta = 90 degrees (X <= 1/2) the FP32
+// cos^2 theta = 1 - X is good to a few ulp; above, its relative error grows as
+// 1 / cos^2 theta (about 1.6e-5 at 170 degrees), so it is formed from |g|^2 in
+// FP64 there (q: the reflection's |g|^2).
+__device__ __forceinline__ float lp_of(float qf, float l2, const double* q, double lambda)
 {
     const float X = qf * l2;  // sin^2 theta
+    float u = 1.f - X;        // cos^2 theta
+    if (X > 0.5f) u = fmaxf((float)fma(-0.25 * lambda * lambda, *q, 1.0), (float)kCos90Sq);
     const float c2 = fmaf(-2.f, X, 1.f);
-    return fmaf(c2, c2, 1.f) / (X * sqrtf(1.f - X));
+    return fmaf(c2, c2, 1.f) / (X * sqrtf(u));
 }
 
 // d f / d s^2 = -41.78214 sum_i a_i exp(-b_i s^2)(1 - b_i s^2); with b_i = -bl_i ln 2
@@ -169,7 +181,7 @@ __device__ void sf_tile_fp32(const SfArgs& a, int64_t first, int len, int64_t j0
     for (int i = 0; i < kSfRB; i++) {
         if (i >= len) continue;
         const int64_t r = first + (int64_t)step * i;
-        const float I = fmaf(Fr[i], Fr[i], Fi[i] * Fi[i]) * lp_of(qf[i], l2);
+        const float I = fmaf(Fr[i], Fr[i], Fi[i] * Fi[i]) * lp_of(qf[i], l2, a.q + r, a.lambda);
         if (GRAD) {
             a.Fx[r] = make_float4(Fr[i], Fi[i], Gr[i], Gi[i]);
             a.Ig[r] = I;
@@ -212,7 +224,7 @@ __device__ void sf_tile_fp64(const SfArgs& a, int64_t first, int step, int len, 
         }
         const double X = (a.lambda * a.lambda * 0.25) * q;  // sin^2 theta
         const double c2 = 1.0 - 2.0 * X;                     // cos 2theta
-        const double lp = (1.0 + c2 * c2) / (X * sqrt(1.0 - X));
+        const double lp = (1.0 + c2 * c2) / (X * sqrt(fmax(1.0 - X, kCos90Sq)));
         if (act) {
             a.I[r] = (Fr * Fr + Fi * Fi) * lp;
             if (a.F) a.F[r] = make_float2((float)Fr, (float)Fi);

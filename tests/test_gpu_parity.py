@@ -393,3 +393,17 @@ def test_merge_decision_at_the_tolerance(gpu_lib, handle, prec, cell):
         assert st["boundary"] == 0
         counts.append(len(ref["peak_tt"][0]))
     assert counts[0] + 1 == counts[1]  # the pair merges below the tolerance and not above it
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_back_scattering_range(gpu_lib, handle, prec):
+    """2-theta up to 180 degrees: the Lorentz factor grows as 1 / cos(theta) and cos^2(theta) = 1 - sin^2(theta)
+    loses digits to cancellation near the back-scattering limit; intensities still within the bar."""
+    b, o = synth.small(n=48)
+    o = _opts(o, tt_min=0.0, tt_max=180.0)
+    ref = oracle.pattern_batch(b, o, threads=0)
+    got = gpu_lib.compute(b, o, prec, handle=handle)
+    assert got["sizes"]["n_refl"] * 2 == int(ref["n_refl"].sum())
+    st = compare_batch(got, ref, prec, o.rel_cutoff, o.scaled)
+    assert max(max(t) for t in ref["peak_tt"] if len(t)) > 175.0  # the batch reaches the limit
+    _report("back_scattering_" + prec, st)
