@@ -155,9 +155,12 @@ __global__ void __launch_bounds__(kGradThreads) k_grad_refl(const GradArgs a)
         const float I = a.Ig[r];
         const float dLdI = 2.f * sI;
         const float dLdT = 2.f * I * sT * inv_s2;
-        const float qf = d2f_pos(a.q[r]);
+        const double qd = a.q[r];
+        const float qf = d2f_pos(qd);
         const float X = qf * l2;  // sin^2 theta
-        const float c2 = fmaf(-2.f, X, 1.f), rt = sqrtf(1.f - X);
+        float cc = 1.f - X;       // cos^2 theta; above 2theta = 90 degrees from |g|^2 in FP64 (cancellation)
+        if (X > 0.5f) cc = fmaxf((float)fma(-a.l2d, qd, 1.0), (float)kCos90Sq);
+        const float c2 = fmaf(-2.f, X, 1.f), rt = sqrtf(cc);
         const float N = fmaf(c2, c2, 1.f), D = X * rt;
         const float lp = N / D;
         const float dlp = (-4.f * c2 * D - N * (rt - X / (2.f * rt))) / (D * D) * l2;

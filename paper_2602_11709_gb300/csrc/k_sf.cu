@@ -36,11 +36,6 @@ __device__ __forceinline__ float f_of(const Coef32& c, float zf, float s2)
     return fmaf(s2, fmaf(c.a[0], e0, fmaf(c.a[1], e1, fmaf(c.a[2], e2, c.a[3] * e3))), zf);
 }
 
-// cos^2(theta) at theta = 90 degrees as FP64 evaluates it (cos of the double nearest pi/2,
-// squared): the floor of cos^2 theta, so that a reflection on the 2theta = 180 degrees
-// surface gets a large finite Lorentz factor instead of a division by zero.
-constexpr double kCos90Sq = 3.749399456654644e-33;
-
 // Lorentz-polarisation factor (1 + cos^2 2theta) / (sin^2 theta cos theta) with
 // sin^2 theta = X = q lambda^2 / 4. Up to 2theta = 90 degrees (X <= 1/2) the FP32
 // cos^2 theta = 1 - X is good to a few ulp; above, its relative error grows as

@@ -9,6 +9,10 @@
 namespace xrd {
 
 constexpr double kPi = 3.14159265358979323846;
+// cos^2(theta) at theta = 90 degrees as FP64 evaluates it (cos of the double nearest pi/2,
+// squared): the floor of cos^2 theta, so that a reflection on the 2theta = 180 degrees
+// surface gets a large finite Lorentz factor instead of a division by zero.
+constexpr double kCos90Sq = 3.749399456654644e-33;
 constexpr double kFScale = 41.78214;  // Mott-Bethe factor 8 pi^2 a0 of f(s) (Sec. 1, atomic scattering factors)
 constexpr int kZmaxLimit = 255;
 constexpr int kHklLimit = 511;        // |h|, |k|, |l| fit the 10-bit fields of the packed key

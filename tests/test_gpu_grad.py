@@ -151,3 +151,25 @@ def test_bad_structures_get_zero_gradients(gpu_lib, handle):
     sl = b.atoms_of(1)
     assert np.all(got["d_frac"][sl] == 0.0) and np.all(got["d_B"][sl] == 0.0) and np.all(got["d_lat"][1] == 0.0)
     assert np.all(np.isfinite(got["d_frac"][b.atoms_of(0)]))
+
+
+def test_gradient_back_scattering(gpu_lib, handle):
+    """Reflections between 100 and 179.5 degrees, where the Lorentz factor and d(2theta)/d|g|^2 grow
+    as 1 / cos(theta) and cos^2(theta) = 1 - sin^2(theta) loses digits in FP32."""
+    idx = np.array([7, 11, 19])
+    b, _, o, _ = _grad_case(idx=idx)
+    o = synth.Opts(o.wavelength, 100.0, 179.5, o.tt_tol, 0.0, 0)
+    grid = synth.Grid(t0=100.0, dt=79.5 / 4095.0, n_pts=4096, fwhm=0.1)
+    rng = np.random.default_rng(17)
+    g = rng.standard_normal((b.n_struct, grid.n_pts))
+    got = _run(gpu_lib, handle, b, o, grid, dLdy=g)
+    assert np.all(got["status"] == 0)
+    for s in range(b.n_struct):
+        hkl, _ = oracle.enumerate_refl(b.lattice[s], o)
+        ref = oracle.broadened(b, s, hkl, o.wavelength, grid)
+        assert np.abs(got["y"][s] - ref).max() <= 1e-5 * ref.max(), s
+        df, dB, dl = oracle.broadened_grad(b, s, hkl, o.wavelength, grid, g[s].astype(np.float32).astype(np.float64))
+        sl = b.atoms_of(s)
+        for name, gv, rv in (("frac", got["d_frac"][sl], df), ("B", got["d_B"][sl], dB), ("lattice", got["d_lat"][s], dl)):
+            rel, cos = _cmp(gv, rv)
+            assert rel <= 1e-3 and cos >= 0.99999, (s, name, rel, cos)
