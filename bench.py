@@ -80,9 +80,11 @@ def reduce_over_ranks(terms, structures, seconds, world, device="cpu"):
 
 
 # DRAM bytes (read + write) of one k_sf launch per (workload, tile, warps, runs), from one ncu
-# capture of each shape as the kernel stands (dram__bytes_read.sum + dram__bytes_write.sum, the
-# written intensities stay in L2); other workloads and shapes: not captured (null)
-SF_TRAFFIC_BYTES = {("small", 64, 1, 0): 13618432, ("small", 64, 2, 0): 13618688, ("small", 64, 4, 0): 13618176,
+# capture of each shape (dram__bytes_read.sum + dram__bytes_write.sum, the written intensities
+# stay in L2), taken before k_sf formed cos^2(theta) in FP64 above 2theta = 90 degrees. That
+# change added a branch and a reload of |g|^2 for such reflections (never taken on the 0-90 degree
+# workloads), so `traffic` is reported as null and this capture beside it as the prior one.
+SF_TRAFFIC_BYTES_PRIOR = {("small", 64, 1, 0): 13618432, ("small", 64, 2, 0): 13618688, ("small", 64, 4, 0): 13618176,
                     ("small", 128, 1, 0): 13556224, ("small", 128, 2, 0): 13555968, ("small", 128, 4, 0): 13556224,
                     ("small", 128, 2, 1): 15159040, ("mixed", 128, 1, 0): 1243995648,
                     ("mixed", 64, 1, 0): 1247074816, ("large", 128, 1, 1): 228812544,
@@ -392,8 +394,12 @@ def run_ours(args):
             "patterns_per_s": pps,
             "roofline": {"bound": "alu", "unit": "Gterm/s", "achieved": achieved_gterms, "peak": peak_gterms,
                          "frac": achieved_gterms / peak_gterms,
-                         "traffic": SF_TRAFFIC_BYTES.get((args.workload,) + tuple(tuned or (128, 2, 0))),
+                         "traffic": None,
+                         "traffic_prior_capture": SF_TRAFFIC_BYTES_PRIOR.get((args.workload,) +
+                                                                             tuple(tuned or (128, 2, 0))),
                          "traffic_unit": "bytes per launch (dram read + write, ncu, this shape)",
+                         "traffic_note": "k_sf changed after its last ncu capture (cos^2 theta in FP64 above "
+                                         "2theta = 90 deg); traffic_prior_capture is the earlier kernel's",
                          "fma_floor_frac": (fma_cycles / (152.0 * SM_MAX_MHZ * 1e6)) / sf_avg,
                          "phase_seeds_per_term": w_seeds / max(terms_eval, 1),
                          "kernel": "k_sf", "peak_basis": "SFU: sin+cos at 16/clk/SM per phase seed (one per run of "
