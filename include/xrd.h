@@ -68,7 +68,9 @@ typedef struct {
 /* Options (host struct). */
 typedef struct {
     double lambda;     /* wavelength, angstrom, > 0 */
-    double tt_min;     /* 2-theta range in degrees, 0 <= tt_min < tt_max <= 180, both inclusive */
+    double tt_min;     /* 2-theta range in degrees, 0 <= tt_min < tt_max <= 180, both inclusive. The
+                          Lorentz factor diverges at 180 degrees: a reflection within ~1e-6 degrees of it
+                          gets a large finite factor that depends on the last bit of |g|^2. */
     double tt_max;
     double tt_tol;     /* merge tolerance in degrees, >= XRD_MIN_TT_TOL: join the peak while 2theta - anchor < tt_tol.
                           Smaller values are refused (XRD_EINVAL): 2theta itself carries ~1e-13 degrees of
