@@ -497,3 +497,60 @@ def test_batch_matches_single():
         assert np.array_equal(res["fam_hkl"][s], p["fam_hkl"])
         assert np.array_equal(res["fam_mult"][s], p["fam_mult"])
         assert np.array_equal(res["peak_fam_off"][s], p["peak_fam_off"])
+
+
+def _golden_diamond():
+    rows = []
+    with open(os.path.join(HERE, "golden", "diamond_cubic_lines.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            parts = line.split()
+            fams = []
+            for item in parts[2:]:
+                h, m = item.split(":")
+                fams.append((tuple(int(c) for c in h), int(m)))
+            rows.append((parts[0] == "yes", int(parts[1]), fams))
+    return rows
+
+
+def test_diamond_cubic_lines_and_extinctions():
+    """Diamond structure (fcc + fcc shifted by a quarter of the body diagonal): |F| = 8 f' for
+    h + k + l = 4n, 4 sqrt(2) f' for odd h + k + l, 0 for 4n + 2 and mixed parity; the kept lines,
+    their families (two at N = 27) and multiplicities, and their merged intensities."""
+    coef = synth.coef_table(np.random.default_rng(3))
+    a, B, Z = 5.431, 0.4, 14
+    fcc = np.array([[0, 0, 0], [0, .5, .5], [.5, 0, .5], [.5, .5, 0]], dtype=np.float64)
+    frac = np.vstack([fcc, (fcc + 0.25) % 1.0])
+    b = synth.Batch(np.array([[a, a, a, 90.0, 90.0, 90.0]]), np.array([0, 8], np.int64), frac,
+                    np.full(8, Z, np.int16), np.ones(8), np.full(8, B), coef)
+    o = synth.Opts(LAM, 0.0, 150.0, 1e-5, 1e-3, 0)
+    _, Gs, _ = oracle.metric(b.lattice[0])
+
+    def fprime(s2):
+        return oracle.fatom(coef, Z, s2) * math.exp(-B * s2)
+
+    def closed(h, k, l, s2):
+        if len({h % 2, k % 2, l % 2}) > 1 or (h + k + l) % 4 == 2:
+            return 0.0
+        return (8.0 if (h + k + l) % 4 == 0 else 4.0 * math.sqrt(2.0)) * fprime(s2)
+
+    for hkl in [(1, 1, 1), (2, 0, 0), (2, 2, 0), (2, 2, 2), (3, 3, 3), (5, 1, 1), (4, 0, 0), (4, 2, 0), (6, 0, 0),
+                (4, 4, 2), (6, 2, 2), (1, 0, 0), (2, 1, 0), (3, 2, 1), (-1, 1, 1), (-2, -2, 0), (3, -1, 1)]:
+        s2, _, _, _ = oracle.refl(oracle.q_of(Gs, *hkl), LAM)
+        F = oracle.sf(b, 0, *hkl, s2)
+        want = closed(*hkl, s2)
+        assert abs(F) == pytest.approx(want, rel=1e-12, abs=1e-12 * fprime(s2)), hkl
+    p = oracle.pattern(b, 0, o)
+    nmax = (2 * math.sin(math.radians(75.0)) / LAM) ** 2 * a * a
+    gold = [r for r in _golden_diamond() if r[0] and r[1] <= nmax]
+    assert [r[1] for r in gold] == [3, 8, 11, 16, 19, 24, 27, 32, 35, 40, 43]
+    assert len(p["peak_tt"]) == len(gold)
+    fo = p["peak_fam_off"]
+    for i, (_, n2, fams) in enumerate(gold):
+        got = [(tuple(int(x) for x in p["fam_hkl"][f]), int(p["fam_mult"][f])) for f in range(fo[i], fo[i + 1])]
+        assert sorted(got) == sorted(fams), (n2, got, fams)
+        assert p["peak_tt"][i] == pytest.approx(2 * math.degrees(math.asin(LAM * math.sqrt(n2) / (2 * a))), abs=1e-10)
+        s2, _, lp, _ = oracle.refl(oracle.q_of(Gs, *fams[0][0]), LAM)
+        want = sum(m * closed(*h, s2) ** 2 for h, m in fams) * lp
+        assert p["peak_I"][i] == pytest.approx(want, rel=1e-11), n2
