@@ -554,3 +554,43 @@ def test_diamond_cubic_lines_and_extinctions():
         s2, _, lp, _ = oracle.refl(oracle.q_of(Gs, *fams[0][0]), LAM)
         want = sum(m * closed(*h, s2) ** 2 for h, m in fams) * lp
         assert p["peak_I"][i] == pytest.approx(want, rel=1e-11), n2
+
+
+def test_hcp_structure_factor_and_lines():
+    """Hexagonal close packing (atoms at (1/3, 2/3, 1/4) and (2/3, 1/3, 3/4) of a hexagonal cell):
+    |F|^2 = 4 f'^2 cos^2(pi ((k - h) / 3 - l / 2)), so 00l vanishes for odd l and hh(-2h)l for odd l,
+    100 has f'^2 and 101 3 f'^2. Every merged line's intensity is the sum over its reflections."""
+    coef = synth.coef_table(np.random.default_rng(4))
+    a, c, B, Z = 3.209, 5.211, 0.6, 12
+    frac = np.array([[1 / 3, 2 / 3, 0.25], [2 / 3, 1 / 3, 0.75]])
+    b = synth.Batch(np.array([[a, a, c, 90.0, 90.0, 120.0]]), np.array([0, 2], np.int64), frac,
+                    np.full(2, Z, np.int16), np.ones(2), np.full(2, B), coef)
+    _, Gs, _ = oracle.metric(b.lattice[0])
+
+    def f2(h, k, l, s2):
+        fp = oracle.fatom(coef, Z, s2) * math.exp(-B * s2)
+        return 4.0 * fp * fp * math.cos(math.pi * ((k - h) / 3.0 - l / 2.0)) ** 2
+
+    for hkl in [(0, 0, 1), (0, 0, 2), (0, 0, 3), (1, 0, 0), (1, 0, 1), (1, 0, 2), (1, 1, 0), (1, 1, 1), (1, 1, 2),
+                (2, 0, 1), (2, -1, 3), (-1, 2, 1), (3, 0, 0), (2, 1, 1)]:
+        s2, _, _, _ = oracle.refl(oracle.q_of(Gs, *hkl), LAM)
+        F = oracle.sf(b, 0, *hkl, s2)
+        fp = oracle.fatom(coef, Z, s2) * math.exp(-B * s2)
+        assert abs(F) ** 2 == pytest.approx(f2(*hkl, s2), rel=1e-11, abs=1e-11 * fp * fp), hkl
+    s2, _, _, _ = oracle.refl(oracle.q_of(Gs, 1, 0, 0), LAM)
+    fp = oracle.fatom(coef, Z, s2) * math.exp(-B * s2)
+    assert f2(1, 0, 0, s2) == pytest.approx(fp * fp) and f2(0, 0, 1, s2) == pytest.approx(0.0, abs=1e-20)
+    # merged lines without a cutoff: every reflection of the sphere in exactly one line, line
+    # intensity = sum over its members of |F|^2 LP from the closed form
+    o = synth.Opts(LAM, 0.0, 120.0, 1e-5, 0.0, 0)
+    p = oracle.pattern(b, 0, o)
+    hkl, _ = oracle.enumerate_refl(b.lattice[0], o)
+    want = {}
+    for h, k, l in hkl:
+        s2, tt, lp, _ = oracle.refl(oracle.q_of(Gs, h, k, l), LAM)
+        key = round(tt, 6)
+        want[key] = want.get(key, 0.0) + f2(int(h), int(k), int(l), s2) * lp
+    assert len(p["peak_tt"]) == len(want)
+    scale = max(want.values())
+    for tt, I in zip(p["peak_tt"], p["peak_I"]):
+        assert I == pytest.approx(want[round(tt, 6)], rel=1e-9, abs=1e-12 * scale)
