@@ -171,7 +171,8 @@ int xrd_pattern_batch(xrd_handle* h, const xrd_batch* batch, const xrd_opts* opt
  * Gaussian cut at |t_k - 2theta_g| <= about 6 sigma (grid points b - W .. b + W + 1
  * around the grid cell b of 2theta_g, W = ceil(6 sigma / dt); the cut changes y by
  * less than 2e-8 of a peak). opts.precision must be XRD_FP32_PHASEFIX;
- * rel_cutoff, scaled and tt_tol are ignored. y is device float [n_struct][n_pts].
+ * rel_cutoff, scaled and tt_tol do not enter the result (they are validated as
+ * for xrd_pattern_batch). y is device float [n_struct][n_pts].
  * status (device [n_struct]) and totals (device [4]) as in xrd_pattern. The
  * workspace (>= sizes.ws_grad_bytes) keeps the reflection list, F and dF/ds^2
  * for xrd_pattern_grad: pass the same workspace, unmodified, to that call.
@@ -224,8 +225,9 @@ typedef struct {
  * Gaussian is skipped only on runs of 256 consecutive grid points where it
  * stays below 2^-40 of its peak (x^2 >= 40). grid.fwhm is ignored; grid.n_pts <= 2^22
  * and every 2-theta in [tt_min, tt_max] lies within 2^22 dt of t0.
- * opts.precision must be XRD_FP32_PHASEFIX; rel_cutoff, scaled and tt_tol are
- * ignored. y is device float [n_struct][n_pts]; status and totals as in
+ * opts.precision must be XRD_FP32_PHASEFIX; rel_cutoff, scaled and tt_tol do
+ * not enter the result (they are validated as for xrd_pattern_batch). y is
+ * device float [n_struct][n_pts]; status and totals as in
  * xrd_pattern_broadened. A structure whose effect parameters break the rules
  * of xrd_augment gets status XRD_EINVAL and a zero row, and counts in
  * totals[3]. Workspace as xrd_pattern_broadened (>= sizes.ws_grad_bytes); the
