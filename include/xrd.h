@@ -40,7 +40,7 @@ extern "C" {
 #define XRD_ECUDA 3     /* a CUDA call failed; see xrd_last_error */
 #define XRD_ETIMEOUT 4  /* a bounded device-side wait ran out */
 
-/* Precision of the structure-factor sum (Sec. 2, "structure-factor evaluation"). */
+/* Precision of the structure-factor sum (Sec. 2, the structure-factor sum). */
 #define XRD_FP64 0          /* every step in FP64 */
 #define XRD_FP32_PHASE64 1  /* phase h.x+k.y+l.z formed and reduced mod 1 in FP64, the rest in FP32 */
 #define XRD_FP32_PHASEFIX 2 /* coordinates in 32-bit fixed point, phase reduced mod 1 exactly in integers, the rest in FP32 */
@@ -137,8 +137,8 @@ void xrd_destroy(xrd_handle* h);
 const char* xrd_last_error(const xrd_handle* h);
 
 /*
- * Count the reflections of a batch (Sec. 2, "generation of reciprocal lattice
- * points within the physically accessible sphere") and size the workspace.
+ * Count the reflections of a batch (Sec. 2: the reciprocal-lattice points
+ * inside the sphere the 2-theta range reaches) and size the workspace.
  * Runs the enumeration count on `stream` and synchronises it. May allocate
  * device memory owned by the handle (never on the hot path). Per-structure
  * input errors are not reported here; xrd_pattern_batch reports them.
@@ -319,8 +319,15 @@ int xrd_stage_times(xrd_handle* h, float* ms, int n);
  *    allocating library routine.
  *  - The first call on a device looks up the array's device address
  *    (cudaGetSymbolAddress, which may load the module); make that first call
- *    before any stream capture on that device. The array then stays reserved
- *    on every device that used it until the process exits.
+ *    before any stream capture on that device. The address is cached with the
+ *    ID of the context it belongs to and looked up again when the device's
+ *    context changes (after cudaDeviceReset, say); make the first call after
+ *    such a change before any stream capture too.
+ *  - When the array is reserved depends on CUDA's module loading: with lazy
+ *    loading (the default) on a device the first time this entry point runs
+ *    there; with eager loading (CUDA_MODULE_LOADING=EAGER) on every device
+ *    where the library is loaded, called there or not. It stays reserved
+ *    until the process exits.
  *  - Limit: the per-structure and per-atom arrays (about 1.2 KB per
  *    structure and 72 bytes per atom) plus about 100 bytes per Friedel-unique
  *    reflection must fit in 64 MiB. A batch whose per-structure and per-atom

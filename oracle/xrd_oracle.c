@@ -30,7 +30,7 @@
 #define M_PI 3.14159265358979323846
 #endif
 
-/* Constant of the atomic scattering-factor expression (Sec. 1, "atomic scattering factors"). */
+/* Constant of the atomic scattering-factor expression (Sec. 1, atomic scattering factors). */
 #define ORC_F_SCALE 41.78214
 
 /* cos of an angle in degrees. 90, 60 and 120 degrees give their exact cosines. */
@@ -43,7 +43,7 @@ static double orc_cosd(double deg)
 }
 
 /*
- * Sec. 2, "reciprocal lattice points": the direct metric tensor
+ * Sec. 2, reciprocal-lattice points: the direct metric tensor
  *   G = [[a^2, ab cos(gamma), ac cos(beta)], [., b^2, bc cos(alpha)], [., ., c^2]]
  * and its inverse, the reciprocal metric Gs, by cofactors over the determinant.
  * |g|^2 = h^T Gs h is the squared length of the reciprocal vector (no 2 pi).
@@ -97,8 +97,8 @@ static int orc_opts_ok(const orc_opts* o)
 }
 
 /*
- * Sec. 2, "generation of reciprocal lattice points within the physically
- * accessible sphere": every integer g = (h, k, l) != 0 with
+ * Sec. 2, the reciprocal-lattice points inside the sphere that the 2-theta
+ * range reaches: every integer g = (h, k, l) != 0 with
  * r_min^2 <= |g|^2 <= r_max^2. The box |h| <= r_max a (+1) holds the whole
  * sphere because |h| = |g . a| <= |g| a. Loops run h, k, l ascending.
  */
@@ -152,8 +152,8 @@ double orc_f(const double* coef, int Z, double s2)
 }
 
 /*
- * Sec. 2, "nested loops for structure-factor evaluation by summing atomic
- * contributions for each reflection", with the Debye-Waller factor:
+ * Sec. 2: per reflection, the sum over the atoms' contributions, with the
+ * Debye-Waller factor:
  *   F(g) = sum_j occ_j f_j(s) exp(-B_j s^2) [cos 2 pi phi_j + i sin 2 pi phi_j],
  *   phi_j = h x_j + k y_j + l z_j.
  */

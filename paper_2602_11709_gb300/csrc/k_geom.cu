@@ -1,8 +1,8 @@
 // Steps S0-S1: per-structure geometry, atom packing and reflection enumeration.
 //
-// Sec. 2 of the paper lists "the generation of reciprocal lattice points within
-// the physically accessible sphere" as the first step of the numerical core:
-// every integer g = (h, k, l) != 0 with r_min <= |g| <= r_max, |g|^2 = h^T G* h.
+// Sec. 2: the first step of the numerical core enumerates the reciprocal-lattice
+// points that the wavelength and the 2-theta range can reach (a sphere in
+// reciprocal space): every integer g = (h, k, l) != 0 with r_min <= |g| <= r_max, |g|^2 = h^T G* h.
 // Friedel's law F(-g) = F(g)* makes g and -g identical in intensity, so only
 // the half-space (first nonzero of h, k, l positive) is enumerated; every kept
 // reflection stands for two.

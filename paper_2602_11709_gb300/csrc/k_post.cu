@@ -1,9 +1,9 @@
 // Steps S4-S6: sort by 2-theta, merge within the tolerance, hkl families,
 // intensity cutoff and scaling, then compaction into dense CSR outputs.
 //
-// Sec. 2 of the paper lists "pairwise operations for grouping
-// symmetry-equivalent reflections" and "the merging of reflections within
-// specified angular tolerances"; the optional cutoff (Sec. 2) keeps peaks above
+// Sec. 2: reflections closer in 2-theta than a tolerance are merged into one
+// peak, and the equivalent reflections of a peak are grouped into hkl families;
+// the optional cutoff (Sec. 2) keeps peaks above
 // a fraction of the largest one and Sec. 3 compares intensities on a 0-100 scale.
 //
 // One CTA per structure. Reflections of structures up to `cap_smem` live in
@@ -76,7 +76,10 @@ __device__ __noinline__ double tt_deg64(double q, double lambda)
 // 1e-6 relative, plus the rounding of 1 - lambda^2 q / 4 relative to cos^2(theta)
 // (~1.3e-7 / cos^2); a pair within 1e-5 + 1e-6 / cos^2 of the tolerance is
 // decided in FP64 from the definition instead, so that every merge decision is
-// the FP64 one.
+// an FP64 one. It is the same decision as a CPU evaluation of the definition
+// except for gaps within a few ulp of 2-theta of the tolerance: CUDA's asin
+// and the C library's asin are each accurate to about an ulp but are not
+// guaranteed to round alike, so such a gap may fall on either side.
 __device__ __forceinline__ bool tt_close(double qa, double qb, float l2, float lh, float ttol, double lambda,
                                          double tol)
 {

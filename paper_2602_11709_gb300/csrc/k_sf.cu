@@ -1,8 +1,7 @@
 // Steps S2-S3: per-reflection scalars, structure factor and intensity.
 //
-// Sec. 2 of the paper: "the nested loops for structure-factor evaluation by
-// summing atomic contributions for each reflection" with the
-// Lorentz-polarisation and Debye-Waller corrections:
+// Sec. 2: per reflection, the sum of the atoms' contributions (the structure
+// factor), corrected by the Lorentz-polarisation and Debye-Waller factors:
 //   F(g) = sum_j occ_j f_j(s) exp(-B_j s^2) exp(2 pi i (h x_j + k y_j + l z_j)),
 //   f(s) = Z - 41.78214 s^2 sum_i a_i exp(-b_i s^2),  s = |g| / 2,
 //   I = |F|^2 (1 + cos^2 2theta) / (sin^2 theta cos theta),  sin theta = lambda |g| / 2.
