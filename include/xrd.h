@@ -101,10 +101,24 @@ typedef struct {
     int32_t reserved; /* must be 0 */
 } xrd_grid;
 
+/* Bit of xrd_pattern.flags: the cell is hexagonal (alpha, beta within 5 deg of
+ * 90, gamma within 5 deg of 120, |a - b| < 0.01 A), so its families group the
+ * Miller-Bravais indices (h, k, i = -h - k, l); (h, k, i, l) follows from hkl. */
+#define XRD_FLAG_HEXAGONAL 1
+
 /* Pattern output: device buffers owned by the caller. Peaks and families are
  * dense CSR arrays over the batch, in structure order; within a structure
  * peaks ascend in 2-theta. A capacity of n_refl (from xrd_query_sizes) is
- * always enough for both peaks and families. */
+ * always enough for both peaks and families. When a capacity is too small
+ * every structure reports XRD_ECAPACITY, and totals[] says what was needed:
+ * for a workspace too small, totals[0] is the reflection count it must hold
+ * (xrd_query_sizes sizes it); for outputs too small, totals[0], totals[1]
+ * and totals[2] are the reflections, peaks and families the outputs need.
+ * The per-reflection list (refl_off != NULL) holds every Friedel-unique
+ * reflection (first nonzero of h, k, l positive; each stands for g and -g,
+ * which have the same intensity) before merging and cutoff, within a
+ * structure in the order of the merge: ascending |g|^2, ties by descending
+ * (h, k, l). Its capacity n_refl is enough. */
 typedef struct {
     int64_t cap_peaks;  /* capacity of the per-peak arrays */
     int64_t cap_fam;    /* capacity of the per-family arrays */
@@ -121,6 +135,12 @@ typedef struct {
                            convention of the calculator the paper accelerates (Sec. 2) */
     int32_t* status;    /* [n_struct]: XRD_OK, XRD_EINVAL (bad cell or atom) or XRD_ECAPACITY */
     int64_t* totals;    /* [4]: reflections (Friedel-unique), peaks, families, structures with an error */
+    int64_t cap_refl;   /* capacity of the per-reflection arrays (used when refl_off is not NULL) */
+    int64_t* refl_off;  /* [n_struct + 1] or NULL: reflections of structure s are refl_off[s] .. refl_off[s+1]-1 */
+    int32_t* refl_hkl;  /* [cap_refl][3]: (h, k, l) of each reflection */
+    double* refl_tt;    /* [cap_refl]: its 2-theta, degrees */
+    double* refl_I;     /* [cap_refl]: its intensity |F|^2 LP, unscaled and unmerged (that of g, and of -g) */
+    int32_t* flags;     /* [n_struct] or NULL: per-structure flag bits (XRD_FLAG_HEXAGONAL) */
 } xrd_pattern;
 
 /*
@@ -145,6 +165,33 @@ const char* xrd_last_error(const xrd_handle* h);
  */
 int xrd_query_sizes(xrd_handle* h, const xrd_batch* batch, const xrd_opts* opts, xrd_sizes* sizes,
                     void* stream /* cudaStream_t */);
+
+/*
+ * Accuracy of the FP32 variants. The agreement the paper quotes is per peak
+ * (Sec. 3: peak intensities relative to the largest, positions); the FP32
+ * variants hold every kept peak's intensity to 1e-5 of itself. The FP32 pass
+ * errs by about 1.5e-7 of sqrt(sum_j a_j^2) in F (a_j = occ_j exp(-B_j s^2)
+ * max(|f_j|, Z_j)), so a weak reflection, one whose atoms nearly cancel, has a
+ * large relative error. The call therefore re-evaluates, in double-float
+ * arithmetic (about 48 bits, from exact 64-bit fixed-point phases), every
+ * reflection whose 3-sigma error bound exceeds 4e-6 of max(I, c M) (M the
+ * structure's largest reflection intensity, c the cutoff fraction, 1e-3 when
+ * the cutoff is off): typically a few percent of the reflections.
+ * xrd_set_refine(h, 0) turns this off (a diagnostic: the FP32 pass alone).
+ */
+int xrd_set_refine(xrd_handle* h, int enabled);
+
+/*
+ * Friedel-unique reflection count of every structure (Sec. 2: the
+ * reciprocal-lattice points inside the sphere the 2-theta range reaches, one
+ * per pair g, -g): counts is a host array of n_struct. Runs the enumeration
+ * count on `stream` and synchronises it; may allocate device memory owned by
+ * the handle (never on the hot path). With the atom counts it gives each
+ * structure's structure-factor cost, R x N, which the multi-GPU path balances
+ * across ranks. An invalid cell counts 0.
+ */
+int xrd_reflection_counts(xrd_handle* h, const xrd_batch* batch, const xrd_opts* opts, int64_t* counts,
+                          void* stream /* cudaStream_t */);
 
 /*
  * The whole pattern of every structure (Sec. 2 steps, then Sec. 2's optional
@@ -263,12 +310,24 @@ int xrd_autotune(xrd_handle* h, const xrd_batch* batch, const xrd_opts* opts, co
  * this workspace (same batch): counts[0] = terms to evaluate (Friedel-unique
  * reflection x atom), counts[1] = phase-factor seeds (one sin/cos pair per term
  * with strided tiles, per run and atom with runs consecutive in l), counts[2] =
- * structure-factor tiles. Host array of 3. Reduces the workspace's per-structure counts on
+ * structure-factor tiles, counts[3] = reflections re-evaluated in double-float
+ * (FP32 variants). Host array of 4. Reduces the workspace's per-structure counts on
  * `stream` (one small kernel) and synchronises it. These counts set the SFU time floor of the
  * batch (the paper has no counterpart; it is for the roofline of the kernel).
  */
 int xrd_work_counts(xrd_handle* h, const xrd_batch* batch, const void* workspace, void* stream /* cudaStream_t */,
                     int64_t* counts);
+
+/*
+ * Issue rates of the units that bound the structure-factor kernel, measured on
+ * the handle's device (the paper has no counterpart: these are the peak of the
+ * kernel's roofline). rates[0..3] = MUFU sin, MUFU cos, MUFU ex2 and FP32 FMA
+ * operations per SM per clock (host array of 4): one CTA of 1024 threads with
+ * eight independent chains of the operation per thread, timed by the SM's
+ * clock64 counter. Allocates a few bytes of device memory and synchronises;
+ * not for the hot path.
+ */
+int xrd_unit_rates(xrd_handle* h, double* rates);
 
 /* Set the structure-factor launch shape directly (tile 64 or 128 reflections per
  * warp, 1, 2 or 4 warps per CTA; warps apply to XRD_FP32_PHASEFIX; runs = 1,
@@ -300,7 +359,7 @@ void xrd_graph_destroy(void* graph);
  * timed run least); 0: off (XRD_EINVAL for another value). xrd_stage_times
  * synchronises on the last event of the last recorded call and writes up to n
  * stage durations in milliseconds (order: prep, atoms, count, scan, emit,
- * structure factor, post, compact, profile sum; in mode 2 every stage but the
+ * structure factor, refine, post, compact, profile sum; in mode 2 every stage but the
  * structure factor reads 0; after an xrd_pattern_augmented call, in either
  * mode, only the profile sum -- the two kernels after the structure factors --
  * is timed and the others read 0) and returns the count. */
@@ -329,7 +388,7 @@ int xrd_stage_times(xrd_handle* h, float* ms, int n);
  *    where the library is loaded, called there or not. It stays reserved
  *    until the process exits.
  *  - Limit: the per-structure and per-atom arrays (about 1.2 KB per
- *    structure and 72 bytes per atom) plus about 100 bytes per Friedel-unique
+ *    structure and 120 bytes per atom) plus about 104 bytes per Friedel-unique
  *    reflection must fit in 64 MiB. A batch whose per-structure and per-atom
  *    part does not fit is rejected on the host with XRD_ECAPACITY; one whose
  *    reflections do not fit is flagged on the device (status XRD_ECAPACITY for

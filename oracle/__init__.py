@@ -232,6 +232,23 @@ def pattern_batch(batch, o, threads: int = 0):
     return res
 
 
+def refl_counts(batch, o, threads: int = 0) -> np.ndarray:
+    """Full-sphere reflection count of every structure (the enumeration only; OpenMP over structures)."""
+    n = batch.n_struct
+    cnt = np.zeros(max(n, 1), np.int64)
+    st = np.zeros(max(n, 1), np.int32)
+    lib().orc_pattern_batch(n, _p(np.ascontiguousarray(batch.lattice, dtype=np.float64), _D),
+                            _p(np.ascontiguousarray(batch.atom_off, dtype=np.int64), _I64),
+                            _p(np.ascontiguousarray(batch.frac, dtype=np.float64), _D),
+                            _p(np.ascontiguousarray(batch.Z, dtype=np.int16), _I16),
+                            _p(np.ascontiguousarray(batch.occ, dtype=np.float64), _D),
+                            _p(np.ascontiguousarray(batch.B, dtype=np.float64), _D),
+                            _p(np.ascontiguousarray(batch.coef, dtype=np.float64), _D), int(batch.zmax),
+                            C.byref(opts(o)), int(threads), 1, _p(cnt, _I64), None, None, None, None, None, None,
+                            None, None, None, _p(st, _I32))
+    return cnt[:n]
+
+
 def max_threads() -> int:
     return int(lib().orc_max_threads())
 

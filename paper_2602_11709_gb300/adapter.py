@@ -14,8 +14,8 @@ A site shared by several species becomes one atom record per species.
 pymatgen itself is not needed. Its atomic scattering-factor table is not
 shipped here, so the caller passes the coefficient table (a_i, b_i) per element.
 
-Hexagonal cells (see xrd.is_hexagonal) report 4-index (h, k, i, l) families,
-as the pymatgen calculator does.
+Hexagonal cells (the library sets xrd.XRD_FLAG_HEXAGONAL in the structure's
+flag word) report 4-index (h, k, i, l) families, as the pymatgen calculator does.
 """
 from __future__ import annotations
 
@@ -101,9 +101,10 @@ def batch_of(structures, coef, debye_waller_factors=None):
                  np.concatenate([p[4] for p in parts]) if parts else np.zeros(0), coef, zmax)
 
 
-def patterns_from(res, lattice):
-    """DiffractionPattern objects from the per-structure results of xrd.compute."""
-    hexa = xrd.is_hexagonal(lattice) if len(lattice) else np.zeros(0, bool)
+def patterns_from(res):
+    """DiffractionPattern objects from the per-structure results of xrd.compute; the library's flag
+    word says which structures report Miller-Bravais (4-index) families."""
+    hexa = (np.asarray(res["flags"]) & xrd.XRD_FLAG_HEXAGONAL) != 0
     out = []
     for s in range(len(res["peak_tt"])):
         fo, hkl, mult = res["peak_fam_off"][s], res["fam_hkl"][s], res["fam_mult"][s]
@@ -149,7 +150,7 @@ class XRDCalculator:
         o = Opts(self.wavelength, float(two_theta_range[0]), float(two_theta_range[1]), self.tt_tol,
                  self.rel_cutoff, 1 if scaled else 0)
         res = xrd.compute(b, o, self.precision, handle=self._h(), device=self.device)
-        return patterns_from(res, b.lattice)
+        return patterns_from(res)
 
     def get_pattern(self, structure, scaled=True, two_theta_range=(0, 90)):
         return self.get_patterns([structure], scaled, two_theta_range)[0]

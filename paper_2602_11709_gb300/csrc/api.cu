@@ -9,7 +9,7 @@
 
 #include "xrd_launch.h"
 
-constexpr int kEvents = 11;
+constexpr int kEvents = 12;
 
 struct xrd_handle {
     int device = 0;
@@ -31,18 +31,31 @@ struct xrd_handle {
     // beside the enumeration: forked by front, joined by order_done and atoms_done
     cudaEvent_t front = nullptr, order_done = nullptr, atoms_done = nullptr;
     unsigned long long* wbuf = nullptr;  // device [3]: xrd_work_counts result
+    xrd::RefineTables rtab{};            // tables of the accurate re-evaluation on the handle's device
+    int refine = 1;                      // re-evaluate weak reflections of the FP32 variants (xrd_set_refine)
 };
 
 namespace {
 
 constexpr int kRunsPerTileHost = xrd::kRunsPerTile;  // structure-factor tile: 32 runs (one per lane)
 // flags area, zeroed at the start of every call: 16 ints (see GeomArgs::abort_flag), then the
-// structure-factor work counters (3 x 64 bit) at byte kWorkOffset
+// structure-factor work counters (3 x 64 bit) at byte kWorkOffset, the re-evaluation's
+// structure counter (int) at kRefineCounterOffset and its reflection count (64 bit) at kRefinedOffset
 constexpr int kFlagBytes = 128;
 constexpr int kWorkOffset = 64;
+constexpr int kRefineCounterOffset = 88;
+constexpr int kRefinedOffset = 96;
 constexpr int kPostCap = 2048;  // reflections per structure kept in shared memory by k_post
-constexpr int kStages = 8;
-constexpr int kSfStage = 5;  // index of the structure-factor stage
+constexpr int kStages = 9;
+constexpr int kSfStage = 5;      // index of the structure-factor stage
+constexpr int kRefineStage = 6;  // index of the re-evaluation stage
+// Re-evaluation of weak reflections (FP32 variants): K = 3 times the per-term error of the FP32
+// pass (measured on this part: 2.0e-7 of sqrt(sum a_j^2) in F, every precision variant and launch
+// shape, largest deviation 6 times the RMS of its component along F), and the allowed error
+// without re-evaluation
+constexpr float kRefineEpsK = 3.f * 2.0e-7f;
+constexpr float kRefineTau = 4e-6f;
+constexpr double kRefineFloorNoCut = 1e-3;  // guarantee floor (fraction of the largest) with the cutoff off
 
 struct DeviceGuard {
     int prev = -1;
@@ -75,8 +88,8 @@ size_t al(size_t x) { return (x + 255) & ~size_t(255); }
 // Byte offsets of every array in the caller's workspace.
 struct Layout {
     size_t geo, refl_cnt, run_cnt, tcnt, refl_off, tile_off, order, atom_bad, cls_list, tile_tab, npk, nfm, fam_soff,
-        flags, coef32, atom32, atom64, astep;
-    size_t q, key, runs, I, g_perm, g_bkt, g_flag, g_pstart, g_psum, g_fcnt;
+        flags, coef32, atom32, atom64, astep, imax, cdd, atomr;
+    size_t q, key, runs, I, W2, g_perm, g_bkt, g_flag, g_pstart, g_psum, g_fcnt;
     size_t st_q, st_I, st_foff, st_hkl, st_mult;
     size_t parts;
     size_t total;
@@ -107,11 +120,15 @@ Layout layout(int64_t n, int64_t natoms, int zmax, int64_t R)
     L.atom32 = take(sizeof(xrd::Atom32) * natoms);
     L.atom64 = take(sizeof(xrd::Atom64) * natoms);
     L.astep = take(8 * natoms);
+    L.imax = take(4 * n);
+    L.cdd = take(sizeof(float4) * 4 * (zmax + 1));
+    L.atomr = take(sizeof(xrd::AtomR) * natoms);
     L.tile_tab = take(8 * (R / kRunsPerTileHost + n + 1));
     L.q = take(8 * R);
     L.key = take(4 * R);
     L.runs = take(4 * R);
     L.I = take(8 * R);
+    L.W2 = take(4 * R);
     L.g_perm = take(4 * R);
     L.g_bkt = take(4 * (R + n));
     L.g_flag = take(R);
@@ -299,6 +316,9 @@ xrd::GeomArgs geom_args(const xrd_batch* b, const xrd_opts* o, const Layout& L, 
     g.q = (double*)(ws + L.q);
     g.key = (uint32_t*)(ws + L.key);
     g.parts = (long long*)(ws + L.parts);
+    g.imax = (unsigned*)(ws + L.imax);
+    g.cdd = (float4*)(ws + L.cdd);
+    g.atomr = (xrd::AtomR*)(ws + L.atomr);
     return g;
 }
 
@@ -343,9 +363,10 @@ int xrd_create(xrd_handle** h, int device)
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->atoms_done, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMalloc(&p->wbuf, 64);
     if (e != cudaSuccess) { xrd_destroy(p); return XRD_ECUDA; }
-    p->ttab = xrd::init_tables(0);  // device tables (2-theta), once per handle, on the legacy stream
+    p->ttab = xrd::init_tables(0);  // device tables (2-theta, re-evaluation), once per handle, legacy stream
+    p->rtab = xrd::init_refine_tables(0);
     e = cudaStreamSynchronize(0);
-    if (e != cudaSuccess || !p->ttab) { xrd_destroy(p); return XRD_ECUDA; }
+    if (e != cudaSuccess || !p->ttab || !p->rtab.sc || !p->rtab.ex) { xrd_destroy(p); return XRD_ECUDA; }
     *h = p;
     return XRD_OK;
 }
@@ -370,6 +391,14 @@ void xrd_destroy(xrd_handle* h)
 
 const char* xrd_last_error(const xrd_handle* h) { return h ? h->err.c_str() : "NULL handle"; }
 
+int xrd_set_refine(xrd_handle* h, int enabled)
+{
+    if (!h) return XRD_EINVAL;
+    if (enabled != 0 && enabled != 1) return fail(h, XRD_EINVAL, "refine must be 0 or 1");
+    h->refine = enabled;
+    return XRD_OK;
+}
+
 int xrd_set_profiling(xrd_handle* h, int enabled)
 {
     if (!h) return XRD_EINVAL;
@@ -385,13 +414,13 @@ int xrd_stage_times(xrd_handle* h, float* ms, int n)
     DeviceGuard g(h->device);
     const int m = n < kStages + 1 ? n : kStages + 1;  // the pattern stages, then the augmented profile sum
     const bool aug = h->recorded == 3, sf_only = h->recorded == 2;
-    cudaError_t e = cudaEventSynchronize(h->ev[aug ? kEvents - 1 : (sf_only ? kSfStage + 1 : kStages)]);
+    cudaError_t e = cudaEventSynchronize(h->ev[aug ? kEvents - 1 : (sf_only ? kRefineStage + 1 : kStages)]);
     if (e != cudaSuccess) return -cuda_fail(h, e, "xrd_stage_times");
     for (int i = 0; i < m; i++) {
         ms[i] = 0.f;
         if (i == kStages) {
             if (aug) e = cudaEventElapsedTime(&ms[i], h->ev[kEvents - 2], h->ev[kEvents - 1]);
-        } else if (!aug && (!sf_only || i == kSfStage)) {
+        } else if (!aug && (!sf_only || i == kSfStage || i == kRefineStage)) {
             e = cudaEventElapsedTime(&ms[i], h->ev[i], h->ev[i + 1]);
         }
         if (e != cudaSuccess) return -cuda_fail(h, e, "xrd_stage_times");
@@ -399,23 +428,14 @@ int xrd_stage_times(xrd_handle* h, float* ms, int n)
     return m;
 }
 
-int xrd_query_sizes(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, xrd_sizes* sizes, void* stream)
+// Friedel-unique reflection count of every structure into cnt (host), on `st` (synchronised);
+// the scratch is the handle's own.
+static int count_reflections(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, cudaStream_t st,
+                             std::vector<int64_t>& cnt)
 {
-    if (!h) return XRD_EINVAL;
-    h->err.clear();
-    int rc = check_batch(h, b);
-    if (rc) return rc;
-    if ((rc = check_opts(h, o))) return rc;
-    if (!sizes) return fail(h, XRD_EINVAL, "sizes is NULL");
-    DeviceGuard g(h->device);
-    cudaStream_t st = (cudaStream_t)stream;
     const int64_t n = b->n_struct;
-    memset(sizes, 0, sizeof(*sizes));
-    if (n == 0) {
-        sizes->ws_bytes = layout(0, b->n_atoms, b->zmax, 0).total;
-        sizes->ws_grad_bytes = layout_grad(0, b->n_atoms, b->zmax, 0).total;
-        return XRD_OK;
-    }
+    cnt.assign(n, 0);
+    if (n == 0) return XRD_OK;
     const size_t need = al(sizeof(xrd::Geo) * n) + al(8 * n);
     if (h->qbuf_bytes < need) {
         if (h->qbuf) cudaFree(h->qbuf);
@@ -435,10 +455,46 @@ int xrd_query_sizes(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, xrd_si
     a.geo = (xrd::Geo*)((char*)h->qbuf + L.geo);
     a.refl_cnt = (int64_t*)((char*)h->qbuf + L.refl_cnt);
     xrd::launch_count_only(a, st);
-    std::vector<int64_t> cnt(n);
     cudaError_t e = cudaMemcpyAsync(cnt.data(), a.refl_cnt, 8 * n, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return cuda_fail(h, e, "xrd_query_sizes");
+    if (e != cudaSuccess) return cuda_fail(h, e, "reflection count");
+    return XRD_OK;
+}
+
+int xrd_reflection_counts(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, int64_t* counts, void* stream)
+{
+    if (!h) return XRD_EINVAL;
+    h->err.clear();
+    int rc = check_batch(h, b);
+    if (rc) return rc;
+    if ((rc = check_opts(h, o))) return rc;
+    if (!counts && b->n_struct > 0) return fail(h, XRD_EINVAL, "counts is NULL");
+    DeviceGuard g(h->device);
+    std::vector<int64_t> cnt;
+    if ((rc = count_reflections(h, b, o, (cudaStream_t)stream, cnt))) return rc;
+    for (size_t i = 0; i < cnt.size(); i++) counts[i] = cnt[i];
+    return XRD_OK;
+}
+
+int xrd_query_sizes(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, xrd_sizes* sizes, void* stream)
+{
+    if (!h) return XRD_EINVAL;
+    h->err.clear();
+    int rc = check_batch(h, b);
+    if (rc) return rc;
+    if ((rc = check_opts(h, o))) return rc;
+    if (!sizes) return fail(h, XRD_EINVAL, "sizes is NULL");
+    DeviceGuard g(h->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t n = b->n_struct;
+    memset(sizes, 0, sizeof(*sizes));
+    if (n == 0) {
+        sizes->ws_bytes = layout(0, b->n_atoms, b->zmax, 0).total;
+        sizes->ws_grad_bytes = layout_grad(0, b->n_atoms, b->zmax, 0).total;
+        return XRD_OK;
+    }
+    std::vector<int64_t> cnt;
+    if ((rc = count_reflections(h, b, o, st, cnt))) return rc;
     int64_t tot = 0, mx = 0, tiles = 0;
     for (int64_t c : cnt) {
         tot += c;
@@ -469,6 +525,11 @@ int xrd_pattern_batch(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, cons
     if (out->cap_peaks > 0 && (!out->two_theta || !out->intensity || !out->d_hkl))
         return fail(h, XRD_EINVAL, "a peak output pointer is NULL");
     if (out->cap_fam > 0 && (!out->hkl || !out->mult)) return fail(h, XRD_EINVAL, "a family output pointer is NULL");
+    if (out->refl_off) {
+        if (out->cap_refl < 0) return fail(h, XRD_EINVAL, "negative reflection capacity");
+        if (out->cap_refl > 0 && (!out->refl_hkl || !out->refl_tt || !out->refl_I))
+            return fail(h, XRD_EINVAL, "a per-reflection output pointer is NULL");
+    }
     if (!workspace || ((uintptr_t)workspace & 255)) return fail(h, XRD_EINVAL, "workspace must be 256-byte aligned");
     const int64_t cap_refl = refl_capacity(n, b->n_atoms, b->zmax, ws_bytes);
     if (cap_refl < 0) return fail(h, XRD_ECAPACITY, "workspace smaller than the per-structure part");
@@ -481,6 +542,8 @@ int xrd_pattern_batch(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, cons
     xrd::GeomArgs ga = geom_args(b, o, L, ws, cap_refl, out->totals, out->status, rb);
     ga.runs_mode = runs;
     ga.enum_threads = h->enum_threads;
+    ga.out_flags = out->flags;
+    const bool refine = h->refine && o->precision != XRD_FP64;
 
     const int prof = h->profiling;
     unsigned rec_flags = 0;  // inside a stream capture, stage events become timed graph nodes
@@ -490,8 +553,8 @@ int xrd_pattern_batch(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, cons
             rec_flags = cudaEventRecordExternal;
     }
     int stage = 0;
-    auto mark = [&]() {  // mode 2 marks only the two ends of the structure-factor stage
-        if (prof == 1 || (prof == 2 && (stage == kSfStage || stage == kSfStage + 1)))
+    auto mark = [&]() {  // mode 2 marks only the ends of the structure-factor and re-evaluation stages
+        if (prof == 1 || (prof == 2 && stage >= kSfStage && stage <= kRefineStage + 1))
             cudaEventRecordWithFlags(h->ev[stage], st, rec_flags);
         stage++;
     };
@@ -549,7 +612,39 @@ int xrd_pattern_batch(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, cons
     if (o->precision == XRD_FP64) sa.I = (double*)(ws + L.I);
     else sa.If = (float*)(ws + L.I);
     sa.F = nullptr;
+    if (refine) {
+        sa.W2 = (float*)(ws + L.W2);
+        sa.imax = ga.imax;
+    }
     xrd::launch_sf(sa, st, false);
+    mark();
+    if (refine) {
+        xrd::RefineArgs ra{};
+        ra.n_struct = (int)n;
+        ra.zmax = b->zmax;
+        ra.grid = h->sms;
+        ra.lambda = o->lambda;
+        ra.l2f = (float)(o->lambda * o->lambda * 0.25);
+        ra.eps_k = kRefineEpsK;
+        ra.tau = kRefineTau;
+        ra.cref = (float)(o->rel_cutoff > 0.0 ? o->rel_cutoff : kRefineFloorNoCut);
+        ra.abort_flag = ga.abort_flag;
+        ra.counter = (int*)(ws + L.flags + kRefineCounterOffset);
+        ra.nref = (unsigned long long*)(ws + L.flags + kRefinedOffset);
+        ra.refl_off = ga.refl_off;
+        ra.atom_off = b->atom_off;
+        ra.q = ga.q;
+        ra.key = ga.key;
+        ra.If = sa.If;
+        ra.W2 = sa.W2;
+        ra.imax = ga.imax;
+        ra.atomr = ga.atomr;
+        ra.cdd = ga.cdd;
+        ra.sc = h->rtab.sc;
+        ra.ex = h->rtab.ex;
+        ra.atom_bad = ga.atom_bad;
+        xrd::launch_refine(ra, st, prof == 0);
+    }
     mark();
 
     xrd::PostArgs pa{};
@@ -596,6 +691,14 @@ int xrd_pattern_batch(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, cons
     pa.st_mult = (int*)(ws + L.st_mult);
     pa.npk = (int64_t*)(ws + L.npk);
     pa.nfm = (int64_t*)(ws + L.nfm);
+    pa.l2h = (float)pa.l2d;
+    pa.l2l = (float)(pa.l2d - (double)pa.l2h);
+    if (out->refl_off && out->cap_refl > 0) {
+        pa.cap_refl = out->cap_refl;
+        pa.refl_hkl = out->refl_hkl;
+        pa.refl_tt = out->refl_tt;
+        pa.refl_I = out->refl_I;
+    }
     {  // the size classes run concurrently: fork to the side streams, join back
         cudaStream_t cs[xrd::kPostClasses] = {st};
         cudaEventRecord(h->fork, st);
@@ -664,17 +767,19 @@ int xrd_work_counts(xrd_handle* h, const xrd_batch* b, const void* workspace, vo
     ga.refl_cnt = (int64_t*)(ws + L.refl_cnt);
     ga.run_cnt = (int64_t*)(ws + L.run_cnt);
     ga.work = (unsigned long long*)(ws + L.flags + kWorkOffset);
-    uint64_t w[3] = {0, 0, 0};
+    uint64_t w[4] = {0, 0, 0, 0};
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = cudaMemsetAsync(h->wbuf, 0, 64, st);
     if (e == cudaSuccess) {
         xrd::launch_work(ga, h->wbuf, st);
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess) e = cudaMemcpyAsync(w, h->wbuf, sizeof(w), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(w, h->wbuf, 3 * sizeof(uint64_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(w + 3, ws + L.flags + kRefinedOffset, sizeof(uint64_t), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(h, e, "xrd_work_counts");
-    for (int i = 0; i < 3; i++) counts[i] = (int64_t)w[i];
+    for (int i = 0; i < 4; i++) counts[i] = (int64_t)w[i];
     return XRD_OK;
 }
 
@@ -725,8 +830,8 @@ int xrd_autotune(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, const xrd
                 h->sf_rb = keep_rb; h->sf_warps = keep_w; h->sf_runs = keep_runs; h->profiling = keep_prof;
                 return finish(rc);
             }
-            float ms[8];
-            const int m = xrd_stage_times(h, ms, 8);
+            float ms[kStages];
+            const int m = xrd_stage_times(h, ms, kStages);
             if (m < 0) {
                 h->sf_rb = keep_rb; h->sf_warps = keep_w; h->sf_runs = keep_runs; h->profiling = keep_prof;
                 return finish(-m);
@@ -751,8 +856,8 @@ int xrd_autotune(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, const xrd
         float t = 1e30f;
         for (int rep = 0; rep < 5; rep++) {
             const int rc = xrd_pattern_batch(h, b, &oo, out, workspace, ws_bytes, stream);
-            float ms[8];
-            const int m = rc == XRD_OK ? xrd_stage_times(h, ms, 8) : -rc;
+            float ms[kStages];
+            const int m = rc == XRD_OK ? xrd_stage_times(h, ms, kStages) : -rc;
             if (rc != XRD_OK || m < 0) {
                 h->enum_threads = keep_et; h->profiling = keep_prof;
                 return finish(rc != XRD_OK ? rc : -m);

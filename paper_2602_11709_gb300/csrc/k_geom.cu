@@ -34,8 +34,12 @@ __device__ __forceinline__ double cosd(double deg)
 // hexagonal flag. A large batch is throughput-bound and takes one lane per
 // structure (LANES = 1, no redundant work). Every value is rounded exactly as
 // in a one-thread evaluation either way.
+// Also zeroes the structure's largest-intensity slot (imax, written by the
+// structure-factor pass) and writes its flag word (bit 0: hexagonal) when the
+// pointers are given.
 template <int LANES>
-__global__ void k_prep(const double* __restrict__ lattice, int n, double rmax, Geo* __restrict__ geo)
+__global__ void k_prep(const double* __restrict__ lattice, int n, double rmax, Geo* __restrict__ geo,
+                       unsigned* __restrict__ imax, int32_t* __restrict__ flags)
 {
     pdl_enter();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -95,6 +99,8 @@ __global__ void k_prep(const double* __restrict__ lattice, int n, double rmax, G
             g.gl[j] = ok ? __double2float_rn(v - (double)v32) : 0.f;
         } else if (j == 6) {
             g.hex = fabs(al - 90.0) < 5.0 && fabs(be - 90.0) < 5.0 && fabs(ga - 120.0) < 5.0 && fabs(a - b) < 0.01;
+            if (imax) imax[s] = 0u;
+            if (flags) flags[s] = g.hex ? XRD_FLAG_HEXAGONAL : 0;
             int H = -1, K = -1, L = -1, st = XRD_EINVAL;
             if (ok) {
                 H = (int)floor(__dmul_rn(rmax, a)) + 1;
@@ -117,17 +123,26 @@ __global__ void k_prep(const double* __restrict__ lattice, int n, double rmax, G
 // 8 lanes per structure up to this many structures (latency-bound), one above (throughput-bound)
 constexpr int kPrepWideMax = 8192;
 
-static void prep_launch(bool pdl, const double* lattice, int n, double rmax, Geo* geo, cudaStream_t st);
+static void prep_launch(bool pdl, const double* lattice, int n, double rmax, Geo* geo, unsigned* imax,
+                        int32_t* flags, cudaStream_t st);
 
-// f(s) coefficients in the form the FP32 loops use (exp2 with the scale folded in).
-__global__ void k_coef(const double* __restrict__ coef, int zmax, Coef32* __restrict__ c32)
+// f(s) coefficients in the form the FP32 loops use (exp2 with the scale folded
+// in) and, for the accurate re-evaluation, (a_i, b_i) as two floats each
+// (cdd[4 z + i] = (a hi, a lo, b hi, b lo); skipped when cdd is null).
+__global__ void k_coef(const double* __restrict__ coef, int zmax, Coef32* __restrict__ c32, float4* __restrict__ cdd)
 {
     pdl_enter();
     for (int z = threadIdx.x; z <= zmax; z += blockDim.x) {
         Coef32 c;
         for (int i = 0; i < 4; i++) {
-            c.a[i] = (float)(-kFScale * coef[8 * z + 2 * i]);
-            c.bl[i] = (float)(-coef[8 * z + 2 * i + 1] * 1.4426950408889634);
+            const double av = coef[8 * z + 2 * i], bv = coef[8 * z + 2 * i + 1];
+            c.a[i] = (float)(-kFScale * av);
+            c.bl[i] = (float)(-bv * 1.4426950408889634);
+            if (cdd) {
+                const float ah = __double2float_rn(av), bh = __double2float_rn(bv);
+                cdd[4 * z + i] = make_float4(ah, __double2float_rn(av - (double)ah), bh,
+                                             __double2float_rn(bv - (double)bh));
+            }
         }
         c32[z] = c;
     }
@@ -140,7 +155,7 @@ __global__ void __launch_bounds__(128) k_atoms(const int64_t* __restrict__ atom_
                                                const double* __restrict__ occ, const double* __restrict__ Bf, int zmax,
                                                Geo* __restrict__ geo, int set_geo, int* __restrict__ atom_bad,
                                                Atom32* __restrict__ a32, Atom64* __restrict__ a64,
-                                               float2* __restrict__ astep)
+                                               float2* __restrict__ astep, AtomR* __restrict__ ar)
 {
     pdl_enter();
     __shared__ int off[kZmaxLimit + 1];
@@ -176,6 +191,10 @@ __global__ void __launch_bounds__(128) k_atoms(const int64_t* __restrict__ atom_
             Atom64 d{};
             a64[a0 + i] = d;
             if (astep) astep[a0 + i] = make_float2(1.f, 0.f);
+            if (ar) {
+                AtomR e{};
+                ar[a0 + i] = e;
+            }
         }
         return;
     }
@@ -228,6 +247,19 @@ __global__ void __launch_bounds__(128) k_atoms(const int64_t* __restrict__ atom_
             Atom64 d;
             d.x = x; d.y = y; d.z = w; d.B = bb; d.occ = o; d.zz = z; d.pad = 0;
             a64[a0 + pos] = d;
+            if (ar) {  // the accurate re-evaluation's record: 64-bit fixed point, two-float occ and B
+                AtomR e;
+                e.X = fix64(x);
+                e.Y = fix64(y);
+                e.Z = fix64(w);
+                e.oh = __double2float_rn(o);
+                e.ol = __double2float_rn(o - (double)e.oh);
+                e.bh = __double2float_rn(bb);
+                e.bl = __double2float_rn(bb - (double)e.bh);
+                e.z = z;
+                e.pad = 0;
+                ar[a0 + pos] = e;
+            }
         }
         __syncthreads();  // every read of off[] for this chunk is done
         if (i < na) atomicAdd(&off[z], 1);
@@ -792,10 +824,12 @@ static void launch_k(bool pdl, void (*k)(P...), dim3 grid, dim3 block, cudaStrea
     else k<<<grid, block, 0, st>>>(static_cast<P>(args)...);
 }
 
-static void prep_launch(bool pdl, const double* lattice, int n, double rmax, Geo* geo, cudaStream_t st)
+static void prep_launch(bool pdl, const double* lattice, int n, double rmax, Geo* geo, unsigned* imax,
+                        int32_t* flags, cudaStream_t st)
 {
-    if (n <= kPrepWideMax) launch_k(pdl, k_prep<8>, (n + 3) / 4, 32, st, lattice, n, rmax, geo);  // 4 per CTA
-    else launch_k(pdl, k_prep<1>, (n + 127) / 128, 128, st, lattice, n, rmax, geo);
+    if (n <= kPrepWideMax)  // 4 structures per CTA
+        launch_k(pdl, k_prep<8>, (n + 3) / 4, 32, st, lattice, n, rmax, geo, imax, flags);
+    else launch_k(pdl, k_prep<1>, (n + 127) / 128, 128, st, lattice, n, rmax, geo, imax, flags);
 }
 
 // Structure-factor work of the last call (for xrd_work_counts): terms = sum of
@@ -844,19 +878,19 @@ void launch_work(const GeomArgs& a, unsigned long long* out, cudaStream_t st)
 
 void launch_prep(const GeomArgs& a, cudaStream_t st, bool pdl)
 {
-    if (a.n_struct > 0) prep_launch(pdl, a.lattice, a.n_struct, a.rmax, a.geo, st);
+    if (a.n_struct > 0) prep_launch(pdl, a.lattice, a.n_struct, a.rmax, a.geo, a.imax, a.out_flags, st);
 }
 
 void launch_coef(const GeomArgs& a, cudaStream_t st, bool pdl)
 {
-    launch_k(pdl, k_coef, 1, 256, st, a.coef, a.zmax, a.coef32);
+    launch_k(pdl, k_coef, 1, 256, st, a.coef, a.zmax, a.coef32, a.cdd);
 }
 
 void launch_atoms(const GeomArgs& a, cudaStream_t st, bool pdl)
 {
     if (a.n_struct > 0)
         launch_k(pdl, k_atoms, a.n_struct, 128, st, a.atom_off, a.n_atoms, a.frac, a.Z, a.occ, a.B, a.zmax, a.geo,
-                 a.atoms_set_geo, a.atom_bad, a.atom32, a.atom64, a.runs_mode ? a.astep : (float2*)nullptr);
+                 a.atoms_set_geo, a.atom_bad, a.atom32, a.atom64, a.runs_mode ? a.astep : (float2*)nullptr, a.atomr);
 }
 
 void launch_order(const GeomArgs& a, cudaStream_t st, bool pdl)
@@ -868,7 +902,7 @@ void launch_count_only(const GeomArgs& a, cudaStream_t st)
 {
     const int n = a.n_struct;
     if (n <= 0) return;
-    prep_launch(false, a.lattice, n, a.rmax, a.geo, st);
+    prep_launch(false, a.lattice, n, a.rmax, a.geo, (unsigned*)nullptr, (int32_t*)nullptr, st);
     launch_pdl(k_count<false>, n, 256, 0, st, a.geo, a.r2min, a.r2max, (float)a.r2min, (float)a.r2max, 0,
                a.refl_cnt, (int64_t*)nullptr, (int*)nullptr);
 }

@@ -250,6 +250,19 @@ __device__ void post_structure(const PostArgs& a, int s, int64_t base, int n, co
         perm[r] = (PermT)v;
     }
     __syncthreads();
+    // ---- the caller's per-reflection list, in merge order ----
+    if (a.refl_hkl && base + n <= a.cap_refl) {
+        for (int p = tid; p < n; p += nt) {
+            const int v = perm[p];
+            const int64_t o = base + p;
+            const uint32_t kv = key[v];
+            a.refl_hkl[3 * o] = hkl_h(kv);
+            a.refl_hkl[3 * o + 1] = hkl_k(kv);
+            a.refl_hkl[3 * o + 2] = hkl_l(kv);
+            a.refl_tt[o] = two_theta_q(q[v], a.l2h, a.l2l, a.ttab);
+            a.refl_I[o] = FI ? (double)Is[v] : a.I[base + v];
+        }
+    }
     // ---- anchor merge: definite starts, then one thread per run ----
     int close_pair = 0;
     for (int i = tid; i < n; i += nt) {
@@ -490,12 +503,13 @@ __global__ void __launch_bounds__(kOutThreads) k_scan_out(const CompactArgs a)
             if (i < n) {
                 a.out.peak_off[i] = cp + vp[u];
                 a.fam_soff[i] = cf + vf[u];
+                if (a.out.refl_off) a.out.refl_off[i] = a.refl_off[i];
             }
         }
         cp += tp;
         cf += tf;
     }
-    const bool over = cp > a.cap_peaks || cf > a.cap_fam;
+    const bool over = cp > a.cap_peaks || cf > a.cap_fam || (a.out.refl_off && a.refl_off[n] > a.out.cap_refl);
     if (over)
         for (int i = tid; i < n; i += nt) a.out.status[i] = XRD_ECAPACITY;
     if (tid == 0) {
@@ -503,6 +517,7 @@ __global__ void __launch_bounds__(kOutThreads) k_scan_out(const CompactArgs a)
         a.fam_soff[n] = cf;
         a.out.totals[1] = cp;
         a.out.totals[2] = cf;
+        if (a.out.refl_off) a.out.refl_off[n] = a.refl_off[n];
         *a.out_abort = over;
         if (over) a.out.totals[3] = n;
         else a.out.fam_off[cp] = cf;
@@ -556,7 +571,7 @@ __global__ void __launch_bounds__(kOutThreads) k_scan_out_final(const CompactArg
     }
     __syncthreads();
     const long long cp = all[0], cf = all[1];
-    const bool over = cp > a.cap_peaks || cf > a.cap_fam;
+    const bool over = cp > a.cap_peaks || cf > a.cap_fam || (a.out.refl_off && a.refl_off[n] > a.out.cap_refl);
     long long vp[kOutItems], vf[kOutItems], tp, tf;
 #pragma unroll
     for (int u = 0; u < kOutItems; u++) {
@@ -572,10 +587,12 @@ __global__ void __launch_bounds__(kOutThreads) k_scan_out_final(const CompactArg
         if (i < n) {
             a.out.peak_off[i] = pre[0] + vp[u];
             a.fam_soff[i] = pre[1] + vf[u];
+            if (a.out.refl_off) a.out.refl_off[i] = a.refl_off[i];
             if (over) a.out.status[i] = XRD_ECAPACITY;
         }
     }
     if (b == 0 && tid == 0) {
+        if (a.out.refl_off) a.out.refl_off[n] = a.refl_off[n];
         a.out.peak_off[n] = cp;
         a.fam_soff[n] = cf;
         a.out.totals[1] = cp;

@@ -1,0 +1,282 @@
+// Accurate re-evaluation of the reflections whose FP32 intensity is not
+// accurate enough (FP32 pattern variants, between steps S3 and S4).
+//
+// The FP32 structure-factor pass rounds every term: sin/cos (MUFU, about 1e-7
+// absolute), the Debye-Waller and f(s) exponentials (MUFU ex2, about 5e-8
+// relative) and the blocked sum. Each term's error scales with
+// a_j = occ_j exp(-B_j s^2) max(|f_j|, Z_j), and the errors of different atoms
+// are independent, so |F| errs by about eps sqrt(sum_j a_j^2) (eps: the
+// per-term error) whatever |F| is. A weak reflection (|F| much below that
+// root-sum-square, the destructive interference of many atoms) then has a
+// large relative error in I = |F|^2 LP. The agreement the engine promises is
+// relative per kept peak (Sec. 3 compares peak intensities), so such
+// reflections are evaluated again here, term by term, in double-float
+// arithmetic (two FP32 numbers, about 48 bits) from exact 64-bit fixed-point
+// phases, with per-term errors near 1e-11.
+//
+// Which reflections: with dF = eps_k sqrt(sum a_j^2) (eps_k = K eps, a
+// K-sigma bound) the intensity's error bound is E = LP (2 |F| dF + dF^2). A
+// reflection is re-evaluated when E > tau max(I, c M), M the structure's
+// largest reflection intensity and c the cutoff fraction (1e-3 when the cutoff
+// is off). Every other reflection then errs by at most tau of its own
+// intensity, or by at most tau c M: a peak kept by the cutoff (above c times
+// the largest peak, itself at least 2 M) errs by at most tau times its
+// intensity per member of that kind.
+#include "xrd_dd.cuh"
+#include "xrd_launch.h"
+
+namespace xrd {
+
+static __device__ float4 g_sc_tab[256];  // cos and sin of 2 pi k / 256 as two floats each
+static __device__ float2 g_ex_tab[64];   // 2^(-j / 64) as two floats
+
+__global__ void k_refine_tab_init()
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < 256) {
+        double sn, cs;
+        sincospi(k / 128.0, &sn, &cs);
+        const DD c = dd_from_double(cs), s = dd_from_double(sn);
+        g_sc_tab[k] = make_float4(c.hi, c.lo, s.hi, s.lo);
+    }
+    if (k < 64) {
+        const DD e = dd_from_double(exp2(-k / 64.0));
+        g_ex_tab[k] = make_float2(e.hi, e.lo);
+    }
+}
+
+RefineTables init_refine_tables(cudaStream_t st)
+{
+    RefineTables t{};
+    k_refine_tab_init<<<1, 256, 0, st>>>();
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_sc_tab) != cudaSuccess) return RefineTables{};
+    t.sc = (const float4*)p;
+    if (cudaGetSymbolAddress(&p, g_ex_tab) != cudaSuccess) return RefineTables{};
+    t.ex = (const float2*)p;
+    return t;
+}
+
+// dd * 2^k for |k| <= 127 (results below 2^-126 become 0)
+__device__ __forceinline__ DD dd_pow2(DD a, int k)
+{
+    if (k < -126) return DD{0.f, 0.f};
+    const float sc = __int_as_float((127 + k) << 23);
+    return DD{a.hi * sc, a.lo * sc};
+}
+
+// exp(-x) in double-float for x >= -80: x = n ln2/64 + r, |r| <= ln2/128, so
+// exp(-x) = 2^-(n >> 6) 2^-((n & 63) / 64) exp(-r); ln2/64 in three parts
+// (Cody and Waite: n * C1 is exact for |n| < 2^16), exp(-r) by its Taylor
+// series to r^4 (next term below 4e-14). Relative error about 3e-10 (the
+// rounding of r to one float). Results below 2^-126 are returned as 0.
+__device__ __forceinline__ DD dd_exp_neg(DD x, const float2* __restrict__ tab)
+{
+    if (x.hi > 87.f) return DD{0.f, 0.f};
+    constexpr float kInvL = 92.33248138427734f;  // 64 / ln 2
+    constexpr float C1 = 0.01080322265625f, C2 = 2.720204065553844e-05f, C3 = -6.563933424574842e-13f;
+    const float t = x.hi * kInvL + 12582912.f;  // round to nearest integer (1.5 * 2^23)
+    const int n = __float_as_int(t) - 0x4B400000;
+    const float nf = t - 12582912.f;
+    float r = fmaf(-nf, C1, x.hi);
+    r = fmaf(-nf, C2, r);
+    r = fmaf(-nf, C3, r) + x.lo;
+    // exp(-r) = (1 - r) + r^2 (1/2 - r/6 + r^2/24)
+    const float p = r * r * fmaf(r, fmaf(r, 1.f / 24.f, -1.f / 6.f), 0.5f);
+    DD e = dd_fast2sum(1.f, -r);
+    e = dd_fast2sum(e.hi, e.lo + p);
+    const float2 T = tab[n & 63];
+    return dd_pow2(dd_mul(e, DD{T.x, T.y}), -(n >> 6));
+}
+
+// cos and sin of 2 pi P / 2^64: the nearest 1/256 turn from a table, the
+// remainder |delta| <= pi/256 by its Taylor series (sin to delta^3, next term
+// below 3e-12; cos to delta^4, next below 6e-15), combined by the angle sum.
+__device__ __forceinline__ void dd_sincos_turn(unsigned long long P, const float4* __restrict__ tab, DD& c, DD& s)
+{
+    const unsigned long long k = (P + (1ull << 55)) >> 56;
+    const long long d = (long long)(P - (k << 56));  // in [-2^55, 2^55): d 2^-64 turns
+    const float4 T = tab[k & 255];
+    const float th = (float)(int)(d >> 32) * 0x1p-32f;                  // exact: |d >> 32| < 2^23
+    const float tl = (float)(unsigned)(d & 0xFFFFFFFFll) * 0x1p-64f;    // rounded below 2^-72 turn
+    constexpr float P2h = 6.2831854820251465f, P2l = -1.7484555314695172e-07f;  // 2 pi
+    const float p = th * P2h;
+    float e = fmaf(th, P2h, -p);
+    e = fmaf(th, P2l, e);
+    e = fmaf(tl, P2h, e);
+    const DD dl = dd_fast2sum(p, e);  // delta = 2 pi (th + tl)
+    const float d2 = dl.hi * dl.hi;
+    const DD sd{dl.hi, fmaf(-d2 * dl.hi, 1.f / 6.f, dl.lo)};  // sin(delta)
+    const float cm = d2 * fmaf(-d2, 1.f / 24.f, 0.5f);       // 1 - cos(delta)
+    // cos(t + delta) = C - (C cm + S sin delta)
+    float q1 = T.z * sd.hi;
+    float e1 = fmaf(T.z, sd.hi, -q1);
+    e1 = fmaf(T.z, sd.lo, fmaf(T.w, sd.hi, e1));
+    e1 = fmaf(T.x, cm, e1);
+    c = dd_add(DD{T.x, T.y}, DD{-q1, -e1});
+    // sin(t + delta) = S + (C sin delta - S cm)
+    float q2 = T.x * sd.hi;
+    float e2 = fmaf(T.x, sd.hi, -q2);
+    e2 = fmaf(T.x, sd.lo, fmaf(T.y, sd.hi, e2));
+    e2 = fmaf(-T.z, cm, e2);
+    s = dd_add(DD{T.z, T.w}, DD{q2, e2});
+}
+
+// f(s) = Z - 41.78214 s^2 sum_i a_i exp(-b_i s^2) in double-float
+__device__ __forceinline__ DD f_dd(const float4* __restrict__ cdd, int z, DD s2, const float2* __restrict__ ex)
+{
+    DD sum{0.f, 0.f};
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        const float4 c = cdd[4 * z + i];
+        const DD e = dd_exp_neg(dd_mul(DD{c.z, c.w}, s2), ex);
+        sum = dd_add(sum, dd_mul(DD{c.x, c.y}, e));
+    }
+    constexpr float Fh = 41.78213882446289f, Fl = 1.1755371360777644e-06f;  // 41.78214
+    const DD t = dd_mul(dd_mul(sum, s2), DD{Fh, Fl});
+    return dd_add(DD{(float)z, 0.f}, dd_neg(t));
+}
+
+constexpr int kRefThreads = 256;  // also the reflections per work chunk
+constexpr int kRefWarps = kRefThreads / 32;
+
+// One warp re-evaluates reflection r of structure s: lanes take the
+// structure's (element-sorted) atoms 32 at a time; in each batch of 32 the
+// first lane of every run of one element evaluates f(s) and hands it to the
+// run's other lanes; then a two-float reduction across the warp, and lane 0
+// writes I = |F|^2 LP (LP in FP64).
+__device__ void refine_one(const RefineArgs& a, int64_t r, int s, const float4* ssc, const float2* sex)
+{
+    const int lane = threadIdx.x & 31;
+    const double q = a.q[r];
+    const uint32_t key = a.key[r];
+    const long long h = hkl_h(key), k = hkl_k(key), l = hkl_l(key);
+    const DD s2 = dd_mul_f(dd_from_double(q), 0.25f);  // exact scaling
+    const int64_t j0 = a.atom_off[s], j1 = a.atom_off[s + 1];
+    DD Fr{0.f, 0.f}, Fi{0.f, 0.f};
+    for (int64_t jb = j0; jb < j1; jb += 32) {
+        const int64_t j = jb + lane;
+        const bool live = j < j1;
+        AtomR at{};
+        if (live) at = a.atomr[j];
+        const int z = live ? at.z : -1;
+        const int zprev = __shfl_up_sync(0xffffffffu, z, 1);
+        const bool head = live && (lane == 0 || zprev != z);
+        const unsigned heads = __ballot_sync(0xffffffffu, head);
+        DD f{0.f, 0.f};
+        if (head) f = f_dd(a.cdd, z, s2, sex);
+        const int src = 31 - __clz(heads & ((2u << lane) - 1u));  // the last run head at or below this lane
+        f.hi = __shfl_sync(0xffffffffu, f.hi, src);
+        f.lo = __shfl_sync(0xffffffffu, f.lo, src);
+        if (live) {
+            const unsigned long long P = (unsigned long long)h * at.X + (unsigned long long)k * at.Y +
+                                         (unsigned long long)l * at.Z;
+            DD cs, sn;
+            dd_sincos_turn(P, ssc, cs, sn);
+            const DD dw = dd_exp_neg(dd_mul(DD{at.bh, at.bl}, s2), sex);
+            const DD w = dd_mul(dd_mul(DD{at.oh, at.ol}, f), dw);
+            Fr = dd_add(Fr, dd_mul(w, cs));
+            Fi = dd_add(Fi, dd_mul(w, sn));
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const DD tr{__shfl_xor_sync(0xffffffffu, Fr.hi, o), __shfl_xor_sync(0xffffffffu, Fr.lo, o)};
+        const DD ti{__shfl_xor_sync(0xffffffffu, Fi.hi, o), __shfl_xor_sync(0xffffffffu, Fi.lo, o)};
+        Fr = dd_add(Fr, tr);
+        Fi = dd_add(Fi, ti);
+    }
+    if (lane == 0) {
+        const double fr = dd_to_double(Fr), fi = dd_to_double(Fi);
+        const double X = (a.lambda * a.lambda * 0.25) * q;  // sin^2 theta
+        const double c2 = 1.0 - 2.0 * X;                     // cos 2theta
+        const double lp = (1.0 + c2 * c2) / (X * sqrt(fmax(1.0 - X, kCos90Sq)));
+        a.If[r] = (float)((fr * fr + fi * fi) * lp);
+        atomicAdd(a.nref, 1ull);
+    }
+}
+
+// largest s in [lo, n) with off[s] <= i, for off[lo] <= i < off[n]
+__device__ __forceinline__ int refl_owner(const int64_t* __restrict__ off, int lo, int n, int64_t i)
+{
+    int hi = n;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (off[mid] <= i) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Persistent CTAs claim chunks of 256 consecutive reflections of the batch (a
+// huge structure spreads over many CTAs); every thread tests one reflection,
+// the flagged ones go to a list, and the warps re-evaluate the list.
+__global__ void __launch_bounds__(kRefThreads) k_refine(const RefineArgs a)
+{
+    pdl_enter();
+    __shared__ float4 ssc[256];
+    __shared__ float2 sex[64];
+    __shared__ int64_t cand_r[kRefThreads];
+    __shared__ int cand_s[kRefThreads];
+    __shared__ int ncand, claim, s_first;
+    if (*a.abort_flag) return;
+    for (int i = threadIdx.x; i < 256; i += kRefThreads) ssc[i] = a.sc[i];
+    if (threadIdx.x < 64) sex[threadIdx.x] = a.ex[threadIdx.x];
+    const int w = threadIdx.x >> 5;
+    const int n = a.n_struct;
+    const int64_t total = a.refl_off[n];
+    const int64_t nchunks = (total + kRefThreads - 1) / kRefThreads;
+    const float cos90f = (float)kCos90Sq;
+    for (;;) {
+        __syncthreads();  // the previous chunk is done with the shared state
+        if (threadIdx.x == 0) {
+            claim = atomicAdd(a.counter, 1);
+            ncand = 0;
+            if (claim < nchunks) s_first = refl_owner(a.refl_off, 0, n, (int64_t)claim * kRefThreads);
+        }
+        __syncthreads();
+        if (claim >= nchunks) break;
+        const int64_t r = (int64_t)claim * kRefThreads + threadIdx.x;
+        if (r < total) {
+            int s = s_first;
+            for (int t = 0; t < 8 && a.refl_off[s + 1] <= r; t++) s++;
+            if (a.refl_off[s + 1] <= r) s = refl_owner(a.refl_off, s + 1, n, r);
+            const float I = a.If[r], A2 = a.W2[r];
+            const float X = d2f_pos(a.q[r]) * a.l2f;
+            const float c2 = fmaf(-2.f, X, 1.f);
+            const float lp = fmaf(c2, c2, 1.f) / (X * sqrtf(fmaxf(1.f - X, cos90f)));
+            const float dF = a.eps_k * sqrtf(A2);
+            const float E = lp * dF * fmaf(2.f, sqrtf(fmaxf(I, 0.f) / lp), dF);
+            const float floorI = a.cref * __uint_as_float(a.imax[s]);
+            const bool bad = a.atom_bad && a.atom_bad[s];
+            if (!bad && A2 > 0.f && E > a.tau * fmaxf(I, floorI)) {
+                const int p = atomicAdd(&ncand, 1);
+                cand_r[p] = r;
+                cand_s[p] = s;
+            }
+        }
+        __syncthreads();
+        const int nc = ncand;
+        for (int ci = w; ci < nc; ci += kRefWarps) refine_one(a, cand_r[ci], cand_s[ci], ssc, sex);
+    }
+}
+
+void launch_refine(const RefineArgs& a, cudaStream_t st, bool pdl)
+{
+    if (a.n_struct <= 0) return;
+    static int per_sm_cache[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int per_sm = (dev >= 0 && dev < 64) ? per_sm_cache[dev] : 0;
+    if (per_sm < 1) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_refine, kRefThreads, 0) != cudaSuccess ||
+            per_sm < 1)
+            per_sm = 1;
+        if (dev >= 0 && dev < 64) per_sm_cache[dev] = per_sm;
+    }
+    const int grid = min(a.grid * per_sm, a.n_struct);
+    if (pdl) launch_pdl(k_refine, grid, kRefThreads, 0, st, a);
+    else k_refine<<<grid, kRefThreads, 0, st>>>(a);
+}
+
+}  // namespace xrd

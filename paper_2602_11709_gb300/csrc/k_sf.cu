@@ -73,22 +73,32 @@ __device__ __forceinline__ float fprime_of(const Coef32& c, float s2)
 // rounding grows by a few ulp over a run of four): one sin/cos pair per run
 // instead of per reflection. Otherwise every reflection's phase is formed exactly (integer
 // phase) or in FP64 (XRD_FP32_PHASE64).
+//
+// Pattern variants (not GRAD): F is summed in FP32 over blocks of 8 atoms and
+// each block sum is added into a two-float total (Knuth's TwoSum), so the
+// rounding of the sum grows with the block size instead of the atom count
+// (plain FP32 summation over N atoms errs by about 2e-8 sqrt(N) of the terms'
+// root-sum-square). The lane also sums a_j^2, a_j = occ_j exp(-B_j s^2)
+// max(|f_j|, Z_j), the scale of each term's rounding error (f_j itself may
+// cancel to near zero; its rounding does not), and stores it for the
+// re-evaluation of weak reflections (k_refine). Returns the lane's largest I.
 // GRAD also accumulates dF/ds^2 = sum_j occ_j exp(-B_j s^2)(f_j' - B_j f_j) e^{i phi_j}.
 template <int PREC, bool GRAD, int kSfRB, bool RUNS>
-__device__ void sf_tile_fp32(const SfArgs& a, int64_t first, int len, int64_t j0, int64_t j1, Atom32* sat,
-                             float2* sstep, const Coef32* scoef, bool staged)
+__device__ float sf_tile_fp32(const SfArgs& a, int64_t first, int len, int64_t j0, int64_t j1, Atom32* sat,
+                              float2* sstep, const Coef32* scoef, bool staged)
 {
     constexpr float ln2 = 0.69314718055994531f;
     constexpr int step = RUNS ? 1 : 32;
+    constexpr bool ACC = !GRAD;  // blocked two-float sum and the error scale
     const int lane = threadIdx.x & 31;
-    float s2[kSfRB], qf[kSfRB], Fr[kSfRB], Fi[kSfRB], f[kSfRB];
+    float s2[kSfRB], Fr[kSfRB], Fi[kSfRB], f[kSfRB];
     float Gr[kSfRB], Gi[kSfRB], fp[kSfRB];
+    float Rh[kSfRB], Rl[kSfRB], Ih[kSfRB], Il[kSfRB], A2[kSfRB];
     uint32_t uh[kSfRB], uk[kSfRB], ul[kSfRB];
 #pragma unroll
     for (int i = 0; i < kSfRB; i++) {
         const int64_t r = first + (int64_t)step * (i < len ? i : 0);
-        qf[i] = d2f_pos(a.q[r]);
-        s2[i] = qf[i] * 0.25f;
+        s2[i] = d2f_pos(a.q[r]) * 0.25f;
         if (!RUNS || i == 0) {
             const uint32_t key = a.key[r];
             uh[i] = (uint32_t)hkl_h(key); uk[i] = (uint32_t)hkl_k(key); ul[i] = (uint32_t)hkl_l(key);
@@ -97,6 +107,7 @@ __device__ void sf_tile_fp32(const SfArgs& a, int64_t first, int len, int64_t j0
         }
         Fr[i] = 0.f; Fi[i] = 0.f; f[i] = 0.f;
         Gr[i] = 0.f; Gi[i] = 0.f; fp[i] = 0.f;
+        Rh[i] = 0.f; Rl[i] = 0.f; Ih[i] = 0.f; Il[i] = 0.f; A2[i] = 0.f;
     }
     constexpr bool kRotate = RUNS && PREC == XRD_FP32_PHASEFIX;
     int zc = -1;
@@ -134,6 +145,7 @@ __device__ void sf_tile_fp32(const SfArgs& a, int64_t first, int len, int64_t j0
                 const Atom64 d = a.atom64[c0 + jj];
                 dx = d.x; dy = d.y; dz = d.z;
             }
+            const bool fold = ACC && ((jj & 7) == 7 || jj == nc - 1);  // uniform
 #pragma unroll
             for (int i = 0; i < kSfRB; i++) {
                 if (!kRotate) {
@@ -148,6 +160,21 @@ __device__ void sf_tile_fp32(const SfArgs& a, int64_t first, int len, int64_t j0
                 const float w = f[i] * dw;
                 Fr[i] = fmaf(w, cs, Fr[i]);
                 Fi[i] = fmaf(w, sn, Fi[i]);
+                if (ACC) {
+                    const float m = dw * fmaxf(fabsf(f[i]), at.zf);
+                    A2[i] = fmaf(m, m, A2[i]);
+                    if (fold) {  // block sum into the two-float total
+                        float t = Rh[i] + Fr[i], bb = t - Rh[i];
+                        Rl[i] += (Rh[i] - (t - bb)) + (Fr[i] - bb);
+                        Rh[i] = t;
+                        t = Ih[i] + Fi[i];
+                        bb = t - Ih[i];
+                        Il[i] += (Ih[i] - (t - bb)) + (Fi[i] - bb);
+                        Ih[i] = t;
+                        Fr[i] = 0.f;
+                        Fi[i] = 0.f;
+                    }
+                }
                 if (GRAD) {
                     const float wd = fmaf(at.nb * ln2, f[i], fp[i]) * dw;
                     Gr[i] = fmaf(wd, cs, Gr[i]);
@@ -171,19 +198,25 @@ __device__ void sf_tile_fp32(const SfArgs& a, int64_t first, int len, int64_t j0
         }
     }
     const float l2 = (float)(a.lambda * a.lambda * 0.25);
+    float imax = 0.f;
 #pragma unroll
     for (int i = 0; i < kSfRB; i++) {
         if (i >= len) continue;
         const int64_t r = first + (int64_t)step * i;
-        const float I = fmaf(Fr[i], Fr[i], Fi[i] * Fi[i]) * lp_of(qf[i], l2, a.q + r, a.lambda);
+        const float qf = d2f_pos(a.q[r]);
+        const float fr = ACC ? Rh[i] + Rl[i] : Fr[i], fi = ACC ? Ih[i] + Il[i] : Fi[i];
+        const float I = fmaf(fr, fr, fi * fi) * lp_of(qf, l2, a.q + r, a.lambda);
         if (GRAD) {
             a.Fx[r] = make_float4(Fr[i], Fi[i], Gr[i], Gi[i]);
             a.Ig[r] = I;
         } else {
             a.If[r] = I;
-            if (a.F) a.F[r] = make_float2(Fr[i], Fi[i]);
+            if (a.W2) a.W2[r] = A2[i];
+            if (a.F) a.F[r] = make_float2(fr, fi);
+            imax = fmaxf(imax, I);
         }
     }
+    return imax;
 }
 
 // FP64 path: the lane's reflections one after another, every term in FP64.
@@ -230,11 +263,13 @@ __device__ void sf_tile_fp64(const SfArgs& a, int64_t first, int step, int len, 
 // queue in largest-first order (tiles of the structures with the most atoms
 // first). A structure's atoms stay staged in the warp's shared memory while its
 // consecutive tiles follow (when they fit one chunk).
-// Register caps: 64 for the integer-phase variant (32 resident warps per SM),
-// about 85 for the FP64-phase and gradient variants (24 warps).
+// Register caps: 64 for the integer-phase variant with 2 reflections per lane
+// (32 resident warps per SM), about 85 for the other FP32 variants (24 warps).
 template <int PREC, bool GRAD, int RB, int WARPS, bool RUNS>
-__global__ void __launch_bounds__(32 * WARPS, PREC == XRD_FP64 ? 1 : ((PREC == XRD_FP32_PHASEFIX && !GRAD) ? 32 / WARPS
-                                                                                                          : 24 / WARPS))
+__global__ void __launch_bounds__(32 * WARPS, PREC == XRD_FP64
+                                                  ? 1
+                                                  : ((PREC == XRD_FP32_PHASEFIX && !GRAD && RB == 2) ? 32 / WARPS
+                                                                                                     : 24 / WARPS))
     k_sf(const SfArgs a)
 {
     pdl_enter();
@@ -281,9 +316,14 @@ __global__ void __launch_bounds__(32 * WARPS, PREC == XRD_FP64 ? 1 : ((PREC == X
             sf_tile_fp64<RB>(a, first, RUNS ? 1 : 32, len, j0, j1);
         } else {
             const bool one_chunk = j1 - j0 <= kSfChunk;
-            sf_tile_fp32<PREC, GRAD, RB, RUNS>(a, first, len, j0, j1, sat[w], sstep[w], scoef,
-                                               one_chunk && s == staged_s);
+            float m = sf_tile_fp32<PREC, GRAD, RB, RUNS>(a, first, len, j0, j1, sat[w], sstep[w], scoef,
+                                                         one_chunk && s == staged_s);
             staged_s = one_chunk ? s : -1;
+            if (!GRAD && a.imax) {  // the structure's largest reflection intensity (I >= 0: integer order)
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+                if (lane == 0 && m > 0.f) atomicMax(a.imax + s, __float_as_uint(m));
+            }
         }
     }
 }

@@ -62,6 +62,32 @@ struct __align__(16) Coef32 {
     float bl[4];
 };
 
+// Atom record of the accurate re-evaluation (k_refine), element-sorted like
+// Atom32: coordinates in 64-bit fixed point, occupancy and B as two floats.
+struct __align__(16) AtomR {
+    unsigned long long X, Y, Z;  // round(x * 2^64) mod 2^64
+    float oh, ol;                // occupancy = oh + ol
+    float bh, bl;                // B = bh + bl (angstrom^2)
+    int32_t z;                   // element number
+    int32_t pad;
+};
+
+// round(v * 2^64) mod 2^64 for a finite double, by bit arithmetic (ties round up).
+__device__ __forceinline__ unsigned long long fix64(double v)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const int e = (int)((b >> 52) & 0x7FFull);
+    if (e == 0) return 0ull;  // zero or subnormal: below 2^-1022
+    const unsigned long long m = (b & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull;
+    const int sh = e - 1075 + 64;  // v * 2^64 = +-m * 2^sh
+    unsigned long long r;
+    if (sh >= 64) r = 0ull;
+    else if (sh >= 0) r = m << sh;
+    else if (sh > -64) r = (m >> (-sh)) + ((m >> (-sh - 1)) & 1ull);
+    else r = 0ull;
+    return (b >> 63) ? 0ull - r : r;
+}
+
 // Reflection key: (h + 512, k + 512, l + 512) in three 10-bit fields, so that
 // the unsigned order of keys is the lexicographic order of signed (h, k, l).
 __host__ __device__ __forceinline__ uint32_t hkl_pack(int h, int k, int l)

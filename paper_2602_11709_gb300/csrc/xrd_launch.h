@@ -46,6 +46,10 @@ struct GeomArgs {
     double* q;
     uint32_t* key;
     long long* parts;  // chunk sums of the multi-block scan (nullptr: single-block scan)
+    unsigned* imax;    // [n_struct] largest reflection intensity slot, zeroed by k_prep (or nullptr)
+    int32_t* out_flags;  // [n_struct] caller's flag words, written by k_prep (or nullptr)
+    float4* cdd;       // [(zmax + 1) * 4] (a, b) coefficients as two floats, by k_coef (or nullptr)
+    AtomR* atomr;      // [atoms] records of the accurate re-evaluation, by k_atoms (or nullptr)
 };
 
 struct SfArgs {
@@ -73,6 +77,38 @@ struct SfArgs {
     float2* F;   // optional per-reflection F (nullptr: not stored)
     float4* Fx;  // gradient path: (Re F, Im F, Re dF/ds^2, Im dF/ds^2) per reflection (nullptr otherwise)
     float* Ig;   // gradient path: |F|^2 LP per reflection
+    float* W2;   // FP32 pattern variants: sum_j a_j^2 per reflection, the scale of the sum's rounding (or nullptr)
+    unsigned* imax;  // FP32 pattern variants: [n_struct] bits of the largest reflection intensity (zeroed by k_prep)
+};
+
+// Device tables of the accurate re-evaluation (built once per handle).
+struct RefineTables {
+    const float4* sc;  // [256] cos and sin of 2 pi k / 256, two floats each
+    const float2* ex;  // [64] 2^(-j / 64) as two floats
+};
+
+struct RefineArgs {
+    int n_struct, zmax, grid;  // grid = number of SMs
+    double lambda;
+    float l2f;    // lambda^2 / 4
+    float eps_k;  // K times the relative error of one FP32 term: the bound of |dF| / sqrt(sum a_j^2)
+    float tau;    // intensity error allowed without re-evaluation, relative to max(I, cref M)
+    float cref;   // cutoff fraction (the floor of the guarantee), relative to the largest reflection M
+    const int* abort_flag;
+    int* counter;                 // work counter over chunks of 256 reflections (zeroed per call)
+    unsigned long long* nref;     // reflections re-evaluated (zeroed per call)
+    const int64_t* refl_off;
+    const int64_t* atom_off;
+    const double* q;
+    const uint32_t* key;
+    float* If;          // FP32 intensities, rewritten for the re-evaluated reflections
+    const float* W2;    // sum_j a_j^2 per reflection
+    const unsigned* imax;  // largest intensity of each structure (bits)
+    const AtomR* atomr;
+    const float4* cdd;
+    const float4* sc;
+    const float2* ex;
+    const int* atom_bad;
 };
 
 struct PostArgs {
@@ -110,6 +146,12 @@ struct PostArgs {
     const int* atom_bad;
     int32_t* status;
     int64_t* totals;
+    // the caller's per-reflection list in merge order (refl_hkl nullptr: not written)
+    int64_t cap_refl;
+    int32_t* refl_hkl;
+    double* refl_tt;
+    double* refl_I;
+    float l2h, l2l;  // lambda^2 / 4 as two floats (2-theta of the list)
 };
 
 struct CompactArgs {
@@ -197,6 +239,8 @@ void launch_scan_refl(const GeomArgs& a, cudaStream_t st, bool pdl);
 void launch_work(const GeomArgs& a, unsigned long long* out, cudaStream_t st);  // out: device [3], zeroed
 void launch_emit(const GeomArgs& a, cudaStream_t st, bool pdl);
 void launch_sf(const SfArgs& a, cudaStream_t st, bool pdl);
+RefineTables init_refine_tables(cudaStream_t st);  // fills the tables, returns their device addresses
+void launch_refine(const RefineArgs& a, cudaStream_t st, bool pdl);
 size_t post_smem_bytes(int cap);
 void launch_post(const PostArgs& a, const cudaStream_t* st);  // st[kPostClasses]
 void launch_compact(const CompactArgs& a, cudaStream_t st);

@@ -14,6 +14,9 @@ The five workloads stand in for the paper's MC3D and COD benchmark sets
                   occupied sites (COD-like large cells, Sec. 3 and 4.2).
 * ``mixed``    -- 100 000 cells, lognormal atom counts (median 20) and edges
                   (median 7 A): spans all reflection-count bins of Sec. 4.2.
+* ``stress``   -- one 50 A cell of 940 atoms at Mo K-alpha, 2-theta 2-60 deg
+                  (about 600 000 Friedel-unique reflections): the shape of the
+                  largest single structure of Sec. 4.2.
 * ``grad``     -- 512 cells of 8-128 atoms for the broadened-pattern gradient.
 * ``hexdis``   -- 256 cells, half hexagonal (a = b U[2.5, 6] A, c U[3, 12] A,
                   gamma 120 deg) and half P1, 2-24 sites each, a third of the
@@ -36,6 +39,7 @@ import numpy as np
 
 ZMAX = 83
 CU_KA = 1.54184
+MO_KA = 0.71073
 
 
 @dataclasses.dataclass
@@ -187,6 +191,19 @@ def large(seed: int = 3, n: int = 256) -> tuple[Batch, Opts]:
     counts = rng.integers(200, 2001, size=n)
     off, frac, Z, occ, B = _atoms(rng, counts, 3.0, partial=True)
     return Batch(np.hstack([edges, ang]), off, frac, Z, occ, B, coef), Opts(CU_KA, 5.0, 120.0)
+
+
+def stress(seed: int = 9, n: int = 1) -> tuple[Batch, Opts]:
+    """The shape of the largest single-structure case of Sec. 4.2 (a COD entry with a ~50 A cell,
+    940 atoms and more than 600 000 reflections at Mo K-alpha, 2-theta 2-60 deg): edges 50 A,
+    angles U[60, 120] deg (volume-factor rejection), 940 atoms, Z U{1..83}, B U[0, 3] A^2, 20 %
+    of sites with occ U[0.5, 1]; lambda 0.71073 A, 2-theta 2-60 deg."""
+    rng = np.random.default_rng(seed)
+    coef = coef_table(rng)
+    edges = np.full((n, 3), 50.0)
+    ang = _angles(rng, n)
+    off, frac, Z, occ, B = _atoms(rng, np.full(n, 940), 3.0, partial=True)
+    return Batch(np.hstack([edges, ang]), off, frac, Z, occ, B, coef), Opts(MO_KA, 2.0, 60.0)
 
 
 def mixed(seed: int = 4, n: int = 100_000) -> tuple[Batch, Opts]:

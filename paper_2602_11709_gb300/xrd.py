@@ -18,17 +18,21 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libxrd.so")
 XRD_OK, XRD_EINVAL, XRD_ECAPACITY, XRD_ECUDA, XRD_ETIMEOUT = 0, 1, 2, 3, 4
 XRD_FP64, XRD_FP32_PHASE64, XRD_FP32_PHASEFIX = 0, 1, 2
 XRD_MIN_TT_TOL = 1e-9  # smallest merge tolerance the library accepts, degrees
+XRD_NOALLOC_SCRATCH_BYTES = 64 << 20  # fixed device scratch of xrd_pattern_batch_noalloc
 PRECISIONS = {"fp64": XRD_FP64, "fp32_phase64": XRD_FP32_PHASE64, "fp32_phasefix": XRD_FP32_PHASEFIX}
-STAGES = ["prep", "atoms", "count", "scan", "emit", "structure_factor", "post", "compact", "profile_sum"]
+STAGES = ["prep", "atoms", "count", "scan", "emit", "structure_factor", "refine", "post", "compact", "profile_sum"]
+XRD_FLAG_HEXAGONAL = 1  # bit of the per-structure flag word: families by Miller-Bravais indices
 # kernels xrd_pattern_batch launches per call: order, coef, atoms (a side stream), prep, count, scan, emit,
-# structure factor, post (six size classes), output scan, compaction
-LAUNCHES_PER_BATCH = 16
+# structure factor, re-evaluation of weak reflections (FP32 variants), post (six size classes), output
+# scan, compaction
+LAUNCHES_PER_BATCH = 17
 
 
-def launches_per_batch(n_struct: int) -> int:
+def launches_per_batch(n_struct: int, refine: bool = True) -> int:
     """Kernels of one xrd_pattern_batch call: above two chunks of 4096 structures the reflection
-    scan and the output scan each take two kernels (chunk sums, then the chunks)."""
-    return LAUNCHES_PER_BATCH + (2 if (n_struct + 4095) // 4096 > 2 else 0)
+    scan and the output scan each take two kernels (chunk sums, then the chunks); the FP64
+    variant (or refine off) has no re-evaluation kernel."""
+    return LAUNCHES_PER_BATCH - (0 if refine else 1) + (2 if (n_struct + 4095) // 4096 > 2 else 0)
 
 
 class xrd_batch(C.Structure):
@@ -62,13 +66,15 @@ class xrd_pattern(C.Structure):
     _fields_ = [("cap_peaks", C.c_int64), ("cap_fam", C.c_int64), ("peak_off", C.c_void_p),
                 ("two_theta", C.c_void_p), ("intensity", C.c_void_p), ("d_hkl", C.c_void_p),
                 ("fam_off", C.c_void_p), ("hkl", C.c_void_p), ("mult", C.c_void_p), ("status", C.c_void_p),
-                ("totals", C.c_void_p)]
+                ("totals", C.c_void_p), ("cap_refl", C.c_int64), ("refl_off", C.c_void_p), ("refl_hkl", C.c_void_p),
+                ("refl_tt", C.c_void_p), ("refl_I", C.c_void_p), ("flags", C.c_void_p)]
 
 
 EXPORTS = ["xrd_create", "xrd_destroy", "xrd_last_error", "xrd_query_sizes", "xrd_pattern_batch",
            "xrd_set_profiling", "xrd_stage_times", "xrd_pattern_batch_noalloc", "xrd_pattern_broadened",
            "xrd_pattern_grad", "xrd_autotune", "xrd_set_sf_shape", "xrd_graph_create", "xrd_graph_launch",
-           "xrd_graph_destroy", "xrd_work_counts", "xrd_set_enum_threads", "xrd_pattern_augmented"]
+           "xrd_graph_destroy", "xrd_work_counts", "xrd_set_enum_threads", "xrd_pattern_augmented",
+           "xrd_set_refine", "xrd_unit_rates", "xrd_reflection_counts"]
 
 _lib = None
 
@@ -120,6 +126,13 @@ def load(path: str = LIB_PATH):
     L.xrd_work_counts.restype = C.c_int
     L.xrd_set_enum_threads.argtypes = [C.c_void_p, C.c_int]
     L.xrd_set_enum_threads.restype = C.c_int
+    L.xrd_set_refine.argtypes = [C.c_void_p, C.c_int]
+    L.xrd_set_refine.restype = C.c_int
+    L.xrd_unit_rates.argtypes = [C.c_void_p, C.POINTER(C.c_double)]
+    L.xrd_unit_rates.restype = C.c_int
+    L.xrd_reflection_counts.argtypes = [C.c_void_p, C.POINTER(xrd_batch), C.POINTER(xrd_opts), C.c_void_p,
+                                        C.c_void_p]
+    L.xrd_reflection_counts.restype = C.c_int
     L.xrd_set_sf_shape.restype = C.c_int
     L.xrd_graph_create.argtypes = [C.c_void_p, C.POINTER(xrd_batch), C.POINTER(xrd_opts), C.POINTER(xrd_pattern),
                                    C.c_void_p, C.c_size_t, C.POINTER(C.c_void_p)]
@@ -161,15 +174,6 @@ def _stream_ptr(stream):
     torch = _torch()
     s = stream if stream is not None else torch.cuda.current_stream()
     return C.c_void_p(s.cuda_stream)
-
-
-def is_hexagonal(lattice):
-    """Per structure: the cell counts as hexagonal (families by Miller-Bravais indices) when alpha and
-    beta lie within 5 degrees of 90, gamma within 5 degrees of 120 and |a - b| < 0.01 A -- the
-    device's rule, evaluated with the same double comparisons."""
-    lat = np.atleast_2d(np.asarray(lattice, dtype=np.float64))
-    return ((np.abs(lat[:, 3] - 90.0) < 5.0) & (np.abs(lat[:, 4] - 90.0) < 5.0) &
-            (np.abs(lat[:, 5] - 120.0) < 5.0) & (np.abs(lat[:, 0] - lat[:, 1]) < 0.01))
 
 
 def miller_bravais(hkl):
@@ -224,9 +228,10 @@ class DeviceBatch:
 
 
 class PatternBuffers:
-    """Caller-owned output arrays of xrd_pattern_batch (torch device tensors)."""
+    """Caller-owned output arrays of xrd_pattern_batch (torch device tensors). With refl=True the
+    per-reflection list (Friedel-unique hkl, 2-theta, unmerged intensity) is written too."""
 
-    def __init__(self, n_struct, cap, device="cuda"):
+    def __init__(self, n_struct, cap, device="cuda", refl=False):
         torch = _torch()
         cap = max(int(cap), 1)
         self.n_struct = n_struct
@@ -240,11 +245,26 @@ class PatternBuffers:
         self.mult = torch.zeros(cap, dtype=torch.int32, device=device)
         self.status = torch.zeros(max(n_struct, 1), dtype=torch.int32, device=device)
         self.totals = torch.zeros(4, dtype=torch.int64, device=device)
+        self.flags = torch.zeros(max(n_struct, 1), dtype=torch.int32, device=device)
+        self.refl = bool(refl)
+        if self.refl:
+            self.refl_off = torch.zeros(n_struct + 1, dtype=torch.int64, device=device)
+            self.refl_hkl = torch.zeros(cap, 3, dtype=torch.int32, device=device)
+            self.refl_tt = torch.zeros(cap, dtype=torch.float64, device=device)
+            self.refl_I = torch.zeros(cap, dtype=torch.float64, device=device)
 
     def c(self) -> xrd_pattern:
-        return xrd_pattern(self.cap, self.cap, self.peak_off.data_ptr(), self.two_theta.data_ptr(),
-                           self.intensity.data_ptr(), self.d_hkl.data_ptr(), self.fam_off.data_ptr(),
-                           self.hkl.data_ptr(), self.mult.data_ptr(), self.status.data_ptr(), self.totals.data_ptr())
+        p = xrd_pattern(self.cap, self.cap, self.peak_off.data_ptr(), self.two_theta.data_ptr(),
+                        self.intensity.data_ptr(), self.d_hkl.data_ptr(), self.fam_off.data_ptr(),
+                        self.hkl.data_ptr(), self.mult.data_ptr(), self.status.data_ptr(), self.totals.data_ptr())
+        p.flags = self.flags.data_ptr()
+        if self.refl:
+            p.cap_refl = self.cap
+            p.refl_off = self.refl_off.data_ptr()
+            p.refl_hkl = self.refl_hkl.data_ptr()
+            p.refl_tt = self.refl_tt.data_ptr()
+            p.refl_I = self.refl_I.data_ptr()
+        return p
 
     def to_host(self):
         """Per-structure arrays, in the same layout as the oracle's batch results."""
@@ -257,8 +277,17 @@ class PatternBuffers:
         fo = self.fam_off[:npk + 1].cpu().numpy()
         hkl = self.hkl[:nfm].cpu().numpy()
         mult = self.mult[:nfm].cpu().numpy()
-        res = {"totals": tot, "status": self.status[:self.n_struct].cpu().numpy(), "peak_tt": [], "peak_I": [],
+        res = {"totals": tot, "status": self.status[:self.n_struct].cpu().numpy(),
+               "flags": self.flags[:self.n_struct].cpu().numpy(), "peak_tt": [], "peak_I": [],
                "peak_d": [], "peak_fam_off": [], "fam_hkl": [], "fam_mult": []}
+        if self.refl:
+            ro = self.refl_off.cpu().numpy()
+            nr = int(ro[-1]) if self.n_struct else 0
+            rh, rt, ri = (self.refl_hkl[:nr].cpu().numpy(), self.refl_tt[:nr].cpu().numpy(),
+                          self.refl_I[:nr].cpu().numpy())
+            res["refl_hkl"] = [rh[ro[s]:ro[s + 1]] for s in range(self.n_struct)]
+            res["refl_tt"] = [rt[ro[s]:ro[s + 1]] for s in range(self.n_struct)]
+            res["refl_I"] = [ri[ro[s]:ro[s + 1]] for s in range(self.n_struct)]
         for s in range(self.n_struct):
             p0, p1 = int(off[s]), int(off[s + 1])
             f0 = int(fo[p0]) if p1 > p0 else 0
@@ -440,6 +469,14 @@ class Handle:
         self._check(self.lib.xrd_query_sizes(self.h, C.byref(b), C.byref(opts), C.byref(sz), _stream_ptr(stream)))
         return sz
 
+    def reflection_counts(self, db: DeviceBatch, opts: xrd_opts, stream=None) -> np.ndarray:
+        """Friedel-unique reflections of every structure (int64 numpy array)."""
+        cnt = np.zeros(max(db.n_struct, 1), dtype=np.int64)
+        b = db.c()
+        self._check(self.lib.xrd_reflection_counts(self.h, C.byref(b), C.byref(opts),
+                                                   C.c_void_p(cnt.ctypes.data), _stream_ptr(stream)))
+        return cnt[:db.n_struct]
+
     def pattern_batch(self, db: DeviceBatch, opts: xrd_opts, out: PatternBuffers, ws, stream=None):
         b = db.c()
         o = out.c()
@@ -521,11 +558,22 @@ class Handle:
         return tile.value, warps.value, runs.value
 
     def work_counts(self, db: DeviceBatch, ws, stream=None):
-        """Structure-factor work of the last call on ws: (terms, phase-factor seeds, f(s) evaluations)."""
+        """Structure-factor work of the last call on ws: (terms, phase-factor seeds, tiles, reflections
+        re-evaluated in double-float)."""
         b = db.c()
-        out = (C.c_int64 * 3)()
+        out = (C.c_int64 * 4)()
         self._check(self.lib.xrd_work_counts(self.h, C.byref(b), C.c_void_p(ws.data_ptr()), _stream_ptr(stream), out))
-        return int(out[0]), int(out[1]), int(out[2])
+        return int(out[0]), int(out[1]), int(out[2]), int(out[3])
+
+    def unit_rates(self):
+        """Measured issue rates (lane operations per SM per clock) of MUFU sin, cos, ex2 and FP32 FMA."""
+        out = (C.c_double * 4)()
+        self._check(self.lib.xrd_unit_rates(self.h, out))
+        return {"mufu_sin": out[0], "mufu_cos": out[1], "mufu_ex2": out[2], "ffma": out[3]}
+
+    def set_refine(self, enabled: bool):
+        """Re-evaluation of weak reflections of the FP32 variants (on by default; off is a diagnostic)."""
+        self._check(self.lib.xrd_set_refine(self.h, int(bool(enabled))))
 
     def set_enum_threads(self, threads: int):
         self._check(self.lib.xrd_set_enum_threads(self.h, int(threads)))
@@ -538,7 +586,8 @@ class Handle:
         return Graph(self, db, opts, out, ws)
 
     def set_profiling(self, mode):
-        """0/False off, 1/True events between all stages, 2 events around the structure factor only."""
+        """0/False off, 1/True events between all stages, 2 events around the structure factor and the
+        re-evaluation only."""
         self._check(self.lib.xrd_set_profiling(self.h, int(mode)))
 
     def stage_times(self):
@@ -582,15 +631,16 @@ def workspace(nbytes: int, device="cuda"):
     return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
 
 
-def compute(batch, opts, precision="fp32_phasefix", handle: Handle = None, device: int = 0):
-    """One-shot convenience: upload a host batch, size, run and download the patterns."""
+def compute(batch, opts, precision="fp32_phasefix", handle: Handle = None, device: int = 0, refl=False):
+    """One-shot convenience: upload a host batch, size, run and download the patterns (with refl=True
+    also the per-reflection list)."""
     torch = _torch()
     h = handle or Handle(device)
     dev = "cuda:%d" % device
     db = DeviceBatch.from_host(batch, dev)
     o = make_opts(opts, precision)
     sz = h.query_sizes(db, o)
-    out = PatternBuffers(db.n_struct, sz.n_refl, dev)
+    out = PatternBuffers(db.n_struct, sz.n_refl, dev, refl=refl)
     ws = workspace(sz.ws_bytes, dev)
     h.pattern_batch(db, o, out, ws)
     torch.cuda.synchronize(device)

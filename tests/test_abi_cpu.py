@@ -105,7 +105,7 @@ def test_header_constants_match_binding():
     m = re.search(r"#define\s+XRD_MIN_TT_TOL\s+([0-9.eE+-]+)", text)
     assert m and float(m.group(1)) == xrd.XRD_MIN_TT_TOL
     for name in ("XRD_OK", "XRD_EINVAL", "XRD_ECAPACITY", "XRD_ECUDA", "XRD_ETIMEOUT", "XRD_FP64",
-                 "XRD_FP32_PHASE64", "XRD_FP32_PHASEFIX"):
+                 "XRD_FP32_PHASE64", "XRD_FP32_PHASEFIX", "XRD_FLAG_HEXAGONAL"):
         m = re.search(r"#define\s+%s\s+(\d+)\b" % name, text)
         assert m and int(m.group(1)) == getattr(xrd, name), name
 
@@ -124,6 +124,7 @@ def test_null_handle_arguments(lib):
     assert lib.xrd_query_sizes(None, None, None, None, None) == xrd.XRD_EINVAL
     assert lib.xrd_pattern_batch(None, None, None, None, None, 0, None) == xrd.XRD_EINVAL
     assert lib.xrd_set_profiling(None, 1) == xrd.XRD_EINVAL
+    assert lib.xrd_set_refine(None, 1) == xrd.XRD_EINVAL
     lib.xrd_destroy(None)
 
 
@@ -138,9 +139,11 @@ def test_missing_library_fails_loudly(tmp_path):
 
 
 def test_launch_count_per_call():
-    """Kernels per xrd_pattern_batch call: 18 above two chunks of 4096 structures (two-kernel scans)."""
-    assert xrd.launches_per_batch(1024) == 16 and xrd.launches_per_batch(8192) == 16
-    assert xrd.launches_per_batch(8193) == 18 and xrd.launches_per_batch(100_000) == 18
+    """Kernels per xrd_pattern_batch call: 17 with the re-evaluation kernel of the FP32 variants (16
+    without), two more above two chunks of 4096 structures (two-kernel scans)."""
+    assert xrd.launches_per_batch(1024) == 17 and xrd.launches_per_batch(8192) == 17
+    assert xrd.launches_per_batch(8193) == 19 and xrd.launches_per_batch(100_000) == 19
+    assert xrd.launches_per_batch(1024, refine=False) == 16 and xrd.launches_per_batch(8193, refine=False) == 18
 
 
 def test_binding_argument_checks():

@@ -2,7 +2,7 @@
 import numpy as np
 import pytest
 
-from paper_2602_11709_gb300 import adapter, synth
+from paper_2602_11709_gb300 import adapter, xrd, synth
 
 
 class _El:
@@ -61,9 +61,9 @@ def test_wavelengths_and_hexagonal_output():
            "peak_d": [np.array([2.0, 1.5]), np.array([1.8])],
            "peak_fam_off": [np.array([0, 1, 3]), np.array([0, 1])],
            "fam_hkl": [np.array([[1, 0, 0], [1, 0, 1], [0, 0, 2]]), np.array([[1, 1, 0]])],
-           "fam_mult": [np.array([6, 12, 2]), np.array([4])], "status": np.array([0, 0])}
-    lat = np.array([[3.0, 3.0, 5.0, 90, 90, 120], [3.0, 3.0, 5.0, 90, 90, 90]])
-    pats = adapter.patterns_from(res, lat)
+           "fam_mult": [np.array([6, 12, 2]), np.array([4])], "status": np.array([0, 0]),
+           "flags": np.array([xrd.XRD_FLAG_HEXAGONAL, 0], np.int32)}
+    pats = adapter.patterns_from(res)
     assert pats[0].hkls == [[{"hkl": (1, 0, -1, 0), "multiplicity": 6}],
                             [{"hkl": (1, 0, -1, 1), "multiplicity": 12}, {"hkl": (0, 0, 0, 2), "multiplicity": 2}]]
     assert pats[1].hkls == [[{"hkl": (1, 1, 0), "multiplicity": 4}]]

@@ -104,7 +104,8 @@ def test_work_counts(gpu_lib):
             h.pattern_batch(db, co0, out, ws)
             res = out.to_host()
             half = np.array([m.sum() // 2 for m in res["fam_mult"]])
-            terms, seeds, nf = h.work_counts(db, ws)
+            terms, seeds, nf, refined = h.work_counts(db, ws)
+            assert 0 <= refined < int(half.sum())
             assert terms == int((half * atoms).sum())
             if runs:  # one seed per run: between reflections / 4 and the reflection count
                 assert int((np.ceil(half / 4) * atoms).sum()) <= seeds < terms
@@ -187,13 +188,13 @@ def test_profiling_modes(gpu_lib):
         h.set_profiling(1)
         h.pattern_batch(db, co, out, ws)
         st = h.stage_times()
-        assert len(st) == 9 and st["profile_sum"] == 0.0
+        assert len(st) == 10 and st["profile_sum"] == 0.0
         assert all(v > 0.0 for k, v in st.items() if k != "profile_sum")
         h.set_profiling(2)
         h.pattern_batch(db, co, out, ws)
         st = h.stage_times()
-        assert st["structure_factor"] > 0.0
-        assert all(v == 0.0 for k, v in st.items() if k != "structure_factor")
+        assert st["structure_factor"] > 0.0 and st["refine"] > 0.0
+        assert all(v == 0.0 for k, v in st.items() if k not in ("structure_factor", "refine"))
         with pytest.raises(xrd.XrdError):
             h.set_profiling(3)
         h.set_profiling(0)

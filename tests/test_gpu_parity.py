@@ -9,7 +9,7 @@ import pytest
 import oracle
 from paper_2602_11709_gb300 import synth
 
-from parity import compare_batch, families
+from parity import compare_batch, compare_reflections, families, half_space
 
 pytestmark = pytest.mark.gpu
 
@@ -407,3 +407,134 @@ def test_back_scattering_range(gpu_lib, handle, prec):
     st = compare_batch(got, ref, prec, o.rel_cutoff, o.scaled)
     assert max(max(t) for t in ref["peak_tt"] if len(t)) > 175.0  # the batch reaches the limit
     _report("back_scattering_" + prec, st)
+
+
+def _q_of(lat):
+    _, Gs, _ = oracle.metric(lat)
+    return lambda k: oracle.q_of(Gs, *k)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_reflection_list_against_oracle(gpu_lib, handle, prec):
+    """The per-reflection list (Friedel-unique hkl, 2-theta, unmerged intensity) of 128 small cells,
+    the NaCl cell and the two smallest large cells against the oracle's full sphere: the hkl set
+    bit-exact (a reflection within 4 ulp of a sphere radius^2 is reported as boundary-ambiguous),
+    every 2-theta to 1e-6 deg, every intensity to 1e-5 max(I, 1e-3 M) (FP32) / 1e-9 (FP64)."""
+    bl, ol = synth.large()
+    cases = [synth.small(n=128), synth.nacl(), (bl.subset(np.argsort(np.diff(bl.atom_off))[:2]), ol)]
+    tot = {"refl": 0, "ambiguous": 0, "max_tt": 0.0, "max_rel": 0.0}
+    for b, o in cases:
+        got = gpu_lib.compute(b, o, prec, handle=handle, refl=True)
+        assert int(got["totals"][0]) == sum(len(x) for x in got["refl_hkl"])
+        r2 = (oracle.r2(o.tt_min, o.wavelength), oracle.r2(o.tt_max, o.wavelength))
+        for s in range(b.n_struct):
+            ref = oracle.pattern(b, s, o, with_refl=True)
+            st = compare_reflections(got, ref, s, prec, _q_of(b.lattice[s]), r2)
+            tot["refl"] += st["refl"]
+            tot["ambiguous"] += st["ambiguous"]
+            tot["max_tt"] = max(tot["max_tt"], st["max_tt"])
+            tot["max_rel"] = max(tot["max_rel"], st["max_rel"])
+    assert tot["refl"] > 100000
+    _report("reflections_" + prec, tot)
+
+
+_LARGEST = {}
+
+
+def _largest_large_cells():
+    """The 16 cells of the large workload with the most structure-factor terms (atoms x volume), and
+    their oracle patterns (computed once per session: about a minute on the host cores)."""
+    if not _LARGEST:
+        b, o = synth.large()
+        work = np.diff(b.atom_off) * np.prod(b.lattice[:, :3], axis=1)
+        sub = b.subset(np.sort(np.argsort(work)[-16:]))
+        _LARGEST["case"] = (sub, o, oracle.pattern_batch(sub, o, threads=0))
+    return _LARGEST["case"]
+
+
+@pytest.mark.parametrize("prec", ["fp32_phasefix", "fp32_phase64"])
+def test_large_largest_cells(gpu_lib, handle, prec):
+    """Every peak of the 16 largest cells of the large workload (1100-2000 atoms, up to ~190 000
+    Friedel-unique reflections each, post-processing on global scratch) against the oracle."""
+    sub, o, ref = _largest_large_cells()
+    got = gpu_lib.compute(sub, o, prec, handle=handle)
+    assert got["sizes"]["max_refl"] > 6144  # the global-scratch size class
+    st = compare_batch(got, ref, prec, o.rel_cutoff, o.scaled)
+    assert st["pairs"] > 400000
+    _report("large_largest16_" + prec, st)
+
+
+@pytest.mark.parametrize("prec", ["fp32_phasefix", "fp64"])
+def test_stress_cell(gpu_lib, handle, prec):
+    """One 50 A cell of 940 atoms at Mo K-alpha, 2-theta 2-60 deg: about 680 000 Friedel-unique
+    reflections in one structure (the shape of the paper's largest COD case, Sec. 4.2). The hkl
+    set against the oracle's enumeration (bit-exact), 3000 sampled reflections against the oracle's
+    structure factor, and the peak list against its own reflections (sums and multiplicities)."""
+    b, o = synth.stress()
+    o0 = _opts(o, rel_cutoff=0.0, scaled=0)
+    got = gpu_lib.compute(b, o0, prec, handle=handle, refl=True)
+    assert got["status"][0] == 0
+    gh = got["refl_hkl"][0]
+    assert len(gh) > 600000
+    hkl_full, _ = oracle.enumerate_refl(b.lattice[0], o0)
+    ref_half = hkl_full[half_space(hkl_full)]
+    assert len(ref_half) * 2 == len(hkl_full)
+    key = lambda a: np.sort((a[:, 0].astype(np.int64) + 512) << 20 | (a[:, 1] + 512) << 10 | (a[:, 2] + 512))  # noqa
+    assert np.array_equal(key(gh), key(ref_half))
+    gI, gtt = got["refl_I"][0], got["refl_tt"][0]
+    M = gI.max()
+    _, Gs, _ = oracle.metric(b.lattice[0])
+    rng = np.random.default_rng(11)
+    pick = np.concatenate([rng.choice(len(gh), 2500, replace=False), np.argsort(gI)[:250], np.argsort(gI)[-250:]])
+    worst = 0.0
+    tol, floor = (1e-9, 1e-6) if prec == "fp64" else (1e-5, 1e-3)
+    for i in pick:
+        h, k, l = (int(v) for v in gh[i])
+        s2, tt, lp, d = oracle.refl(oracle.q_of(Gs, h, k, l), o0.wavelength)
+        Iref = abs(oracle.sf(b, 0, h, k, l, s2)) ** 2 * lp
+        assert abs(gtt[i] - tt) <= 1e-6
+        assert abs(gI[i] - Iref) <= tol * max(Iref, floor * M), (h, k, l, gI[i], Iref)
+        if Iref > floor * M:
+            worst = max(worst, abs(gI[i] - Iref) / Iref)
+    # peaks (uncut, unscaled): every reflection in exactly one family, intensities summing the pairs
+    assert int(got["fam_mult"][0].sum()) == 2 * len(gh)
+    assert abs(got["peak_I"][0].sum() - 2 * gI.sum()) <= 1e-6 * 2 * gI.sum()
+    _report("stress_" + prec, {"refl": len(gh), "max_rel": worst})
+
+
+def test_refinement_share_and_effect(gpu_lib, handle):
+    """The re-evaluation touches a few percent of the small batch's reflections; without it the
+    FP32 pass alone misses the elementwise bar that the tests above hold the library to."""
+    import torch
+    xrd = gpu_lib
+    b, o = synth.small()
+    ref = oracle.pattern_batch(b, o, threads=0)
+    db = xrd.DeviceBatch.from_host(b)
+    co = xrd.make_opts(o, "fp32_phasefix")
+    sz = handle.query_sizes(db, co)
+    ws = xrd.workspace(sz.ws_bytes)
+    worst = {}
+    try:
+        for on in (True, False):
+            handle.set_refine(on)
+            out = xrd.PatternBuffers(b.n_struct, sz.n_refl)
+            handle.pattern_batch(db, co, out, ws)
+            torch.cuda.synchronize()
+            refined = handle.work_counts(db, ws)[3]
+            if on:
+                assert 0 < refined < 0.2 * sz.n_refl, refined
+            else:
+                assert refined == 0
+            got = out.to_host()
+            w = 0.0
+            for s in range(b.n_struct):
+                gI, rI = got["peak_I"][s], ref["peak_I"][s]
+                if len(gI) == len(rI) and len(rI):
+                    m = rI > 1e-3 * 100.0
+                    w = max(w, float((np.abs(gI[m] - rI[m]) / rI[m]).max()) if m.any() else 0.0)
+            worst[on] = (w, refined)
+    finally:
+        handle.set_refine(True)
+    assert worst[True][0] <= 1e-5 and worst[False][0] > worst[True][0]
+    _report("refinement_small", {"max_rel_refined": worst[True][0], "max_rel_fp32_only": worst[False][0],
+                                 "refined": worst[True][1], "n_refl": int(sz.n_refl)})

@@ -58,15 +58,20 @@ def test_noalloc_capacity_limits(gpu_lib):
     xrd = gpu_lib
     h = xrd.Handle(0)
     try:
-        # reflections beyond the fixed scratch: flagged on the device for every structure
+        # reflections beyond the fixed scratch (1.03 million of about 104 bytes each), outputs with
+        # room for every peak and family: the scratch alone is too small, flagged on the device for
+        # every structure, and totals[0] gives the reflection count it would need
         b, o = synth.small()
         db = xrd.DeviceBatch.from_host(b)
         co = xrd.make_opts(o, "fp32_phasefix")
-        out = xrd.PatternBuffers(b.n_struct, 16)
+        sz = h.query_sizes(db, co)
+        assert sz.ws_bytes > xrd.XRD_NOALLOC_SCRATCH_BYTES
+        out = xrd.PatternBuffers(b.n_struct, sz.n_refl)
         h.pattern_batch_noalloc(db, co, out)
         torch.cuda.synchronize()
         assert np.all(out.status.cpu().numpy() == xrd.XRD_ECAPACITY)
         assert int(out.totals[3]) == b.n_struct
+        assert int(out.totals[0]) == sz.n_refl
         # per-structure arrays beyond the scratch: rejected on the host before any launch
         big = xrd.xrd_batch(2_000_000, db.zmax, db.n_atoms, db.lattice.data_ptr(), db.atom_off.data_ptr(),
                             db.frac.data_ptr(), db.Z.data_ptr(), db.occ.data_ptr(), db.B.data_ptr(),
@@ -84,3 +89,30 @@ def test_noalloc_capacity_limits(gpu_lib):
         assert np.all(out2.status.cpu().numpy() == 0)
     finally:
         h.close()
+
+
+def test_noalloc_after_handle_recreated(gpu_lib):
+    """The scratch address is looked up per context: a handle destroyed and created again on the
+    same device (same context) keeps giving the workspace entry point's results."""
+    import torch
+    xrd = gpu_lib
+    b, o = synth.small(seed=21, n=48)
+    db = xrd.DeviceBatch.from_host(b)
+    co = xrd.make_opts(o, "fp32_phasefix")
+    results = []
+    for _ in range(2):
+        h = xrd.Handle(0)
+        try:
+            sz = h.query_sizes(db, co)
+            out = xrd.PatternBuffers(b.n_struct, sz.n_refl)
+            h.pattern_batch_noalloc(db, co, out)
+            ref_out = xrd.PatternBuffers(b.n_struct, sz.n_refl)
+            h.pattern_batch(db, co, ref_out, xrd.workspace(sz.ws_bytes))
+            torch.cuda.synchronize()
+            got, ref = out.to_host(), ref_out.to_host()
+            compare_batch(got, ref, "fp32_phasefix", o.rel_cutoff, o.scaled)
+            results.append(got)
+        finally:
+            h.close()
+    for s in range(b.n_struct):
+        assert np.array_equal(results[0]["peak_I"][s], results[1]["peak_I"][s])
