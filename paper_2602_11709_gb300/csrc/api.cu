@@ -39,21 +39,19 @@ namespace {
 
 constexpr int kRunsPerTileHost = xrd::kRunsPerTile;  // structure-factor tile: 32 runs (one per lane)
 // flags area, zeroed at the start of every call: 16 ints (see GeomArgs::abort_flag), then the
-// structure-factor work counters (3 x 64 bit) at byte kWorkOffset, the re-evaluation's
-// structure counter (int) at kRefineCounterOffset and its reflection count (64 bit) at kRefinedOffset
+// structure-factor work counters (3 x 64 bit) at byte kWorkOffset and the re-evaluation's
+// reflection count (64 bit) at kRefinedOffset
 constexpr int kFlagBytes = 128;
 constexpr int kWorkOffset = 64;
-constexpr int kRefineCounterOffset = 88;
 constexpr int kRefinedOffset = 96;
 constexpr int kPostCap = 2048;  // reflections per structure kept in shared memory by k_post
 constexpr int kStages = 9;
 constexpr int kSfStage = 5;      // index of the structure-factor stage
 constexpr int kRefineStage = 6;  // index of the re-evaluation stage
-// Re-evaluation of weak reflections (FP32 variants): K = 3 times the per-term error of the FP32
-// pass (measured on this part: 2.0e-7 of sqrt(sum a_j^2) in F, every precision variant and launch
-// shape, largest deviation 6 times the RMS of its component along F), and the allowed error
-// without re-evaluation
-constexpr float kRefineEpsK = 3.f * 2.0e-7f;
+// Re-evaluation of weak reflections (FP32 variants): the bound of |dF| / sqrt(sum a_j^2) of the FP32
+// pass, about 4 times its measured RMS error (9e-8 with sin/cos on the FMA pipe, every precision
+// variant and launch shape), and the error allowed without re-evaluation
+constexpr float kRefineEpsK = 3.5e-7f;
 constexpr float kRefineTau = 4e-6f;
 constexpr double kRefineFloorNoCut = 1e-3;  // guarantee floor (fraction of the largest) with the cutoff off
 
@@ -89,7 +87,7 @@ size_t al(size_t x) { return (x + 255) & ~size_t(255); }
 struct Layout {
     size_t geo, refl_cnt, run_cnt, tcnt, refl_off, tile_off, order, atom_bad, cls_list, tile_tab, npk, nfm, fam_soff,
         flags, coef32, atom32, atom64, astep, imax, cdd, atomr;
-    size_t q, key, runs, I, W2, g_perm, g_bkt, g_flag, g_pstart, g_psum, g_fcnt;
+    size_t q, key, runs, I, W2, cand_r, cand_s, g_perm, g_bkt, g_flag, g_pstart, g_psum, g_fcnt;
     size_t st_q, st_I, st_foff, st_hkl, st_mult;
     size_t parts;
     size_t total;
@@ -129,6 +127,8 @@ Layout layout(int64_t n, int64_t natoms, int zmax, int64_t R)
     L.runs = take(4 * R);
     L.I = take(8 * R);
     L.W2 = take(4 * R);
+    L.cand_r = take(8 * R);
+    L.cand_s = take(4 * R);
     L.g_perm = take(4 * R);
     L.g_bkt = take(4 * (R + n));
     L.g_flag = take(R);
@@ -629,8 +629,9 @@ int xrd_pattern_batch(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, cons
         ra.tau = kRefineTau;
         ra.cref = (float)(o->rel_cutoff > 0.0 ? o->rel_cutoff : kRefineFloorNoCut);
         ra.abort_flag = ga.abort_flag;
-        ra.counter = (int*)(ws + L.flags + kRefineCounterOffset);
         ra.nref = (unsigned long long*)(ws + L.flags + kRefinedOffset);
+        ra.cand_r = (int64_t*)(ws + L.cand_r);
+        ra.cand_s = (int*)(ws + L.cand_s);
         ra.refl_off = ga.refl_off;
         ra.atom_off = b->atom_off;
         ra.q = ga.q;

@@ -192,7 +192,6 @@ __device__ void refine_one(const RefineArgs& a, int64_t r, int s, const float4* 
         const double c2 = 1.0 - 2.0 * X;                     // cos 2theta
         const double lp = (1.0 + c2 * c2) / (X * sqrt(fmax(1.0 - X, kCos90Sq)));
         a.If[r] = (float)((fr * fr + fi * fi) * lp);
-        atomicAdd(a.nref, 1ull);
     }
 }
 
@@ -208,39 +207,66 @@ __device__ __forceinline__ int refl_owner(const int64_t* __restrict__ off, int l
     return lo;
 }
 
-// Persistent CTAs claim chunks of 256 consecutive reflections of the batch (a
-// huge structure spreads over many CTAs); every thread tests one reflection,
-// the flagged ones go to a list, and the warps re-evaluate the list.
-__global__ void __launch_bounds__(kRefThreads) k_refine(const RefineArgs a)
+// Selection: every CTA takes one contiguous range of the batch's reflections
+// in chunks of 1024, four consecutive reflections per thread. The offsets of
+// the structures a chunk can touch are staged in shared memory (a window of
+// 128 structures from the chunk's first), so each thread finds its
+// structure by bisection there (in global memory only past the window). Flagged
+// reflections are appended to the candidate list, one atomic per warp.
+constexpr int kRefItems = 4;
+constexpr int kRefChunk = kRefThreads * kRefItems;
+constexpr int kRefWindow = 128;
+
+__global__ void __launch_bounds__(kRefThreads) k_refine_select(const RefineArgs a)
 {
     pdl_enter();
-    __shared__ float4 ssc[256];
-    __shared__ float2 sex[64];
-    __shared__ int64_t cand_r[kRefThreads];
-    __shared__ int cand_s[kRefThreads];
-    __shared__ int ncand, claim, s_first;
+    __shared__ int64_t woff[kRefWindow + 1];
+    __shared__ int s_cur;
     if (*a.abort_flag) return;
-    for (int i = threadIdx.x; i < 256; i += kRefThreads) ssc[i] = a.sc[i];
-    if (threadIdx.x < 64) sex[threadIdx.x] = a.ex[threadIdx.x];
-    const int w = threadIdx.x >> 5;
     const int n = a.n_struct;
     const int64_t total = a.refl_off[n];
-    const int64_t nchunks = (total + kRefThreads - 1) / kRefThreads;
+    const int64_t nch = (total + kRefChunk - 1) / kRefChunk;
+    const int64_t per = (nch + gridDim.x - 1) / gridDim.x;
+    const int64_t c_begin = (int64_t)blockIdx.x * per, c_end = min(c_begin + per, nch);
+    if (c_begin >= c_end) return;
+    if (threadIdx.x == 0) s_cur = refl_owner(a.refl_off, 0, n, c_begin * kRefChunk);
+    const int lane = threadIdx.x & 31;
     const float cos90f = (float)kCos90Sq;
-    for (;;) {
-        __syncthreads();  // the previous chunk is done with the shared state
-        if (threadIdx.x == 0) {
-            claim = atomicAdd(a.counter, 1);
-            ncand = 0;
-            if (claim < nchunks) s_first = refl_owner(a.refl_off, 0, n, (int64_t)claim * kRefThreads);
-        }
+    for (int64_t c = c_begin; c < c_end; c++) {
+        const int64_t r0 = c * kRefChunk;
+        __syncthreads();  // s_cur is set; the previous chunk is done with the window
+        const int sb = s_cur;
+        for (int i = threadIdx.x; i <= kRefWindow; i += kRefThreads) woff[i] = a.refl_off[min(sb + i, n)];
         __syncthreads();
-        if (claim >= nchunks) break;
-        const int64_t r = (int64_t)claim * kRefThreads + threadIdx.x;
-        if (r < total) {
-            int s = s_first;
-            for (int t = 0; t < 8 && a.refl_off[s + 1] <= r; t++) s++;
-            if (a.refl_off[s + 1] <= r) s = refl_owner(a.refl_off, s + 1, n, r);
+        const int64_t rt = r0 + (int64_t)kRefItems * threadIdx.x;  // this thread's first reflection
+        int k = 0;  // largest k < kRefWindow with woff[k] <= rt, if the window reaches rt
+        int s;
+        if (rt < woff[kRefWindow]) {
+            int lo = 0, hi = kRefWindow;
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (woff[mid] <= rt) lo = mid;
+                else hi = mid;
+            }
+            k = lo;
+            s = sb + k;
+        } else {
+            s = rt < total ? refl_owner(a.refl_off, min(sb + kRefWindow, n - 1), n, rt) : n - 1;
+        }
+        if (threadIdx.x == kRefThreads - 1) {  // next chunk's first structure: this thread's last reflection's
+            int sl = s;
+            const int64_t rl = min(rt + kRefItems, total) - 1;
+            while (sl + 1 < n && a.refl_off[sl + 1] <= rl) sl++;
+            s_cur = sl;
+        }
+        int64_t cr[kRefItems];
+        int cs[kRefItems];
+        int nf = 0;
+#pragma unroll
+        for (int u = 0; u < kRefItems; u++) {
+            const int64_t r = rt + u;
+            if (r >= total) break;
+            while (a.refl_off[s + 1] <= r) s++;  // at most a few steps: four consecutive reflections
             const float I = a.If[r], A2 = a.W2[r];
             const float X = d2f_pos(a.q[r]) * a.l2f;
             const float c2 = fmaf(-2.f, X, 1.f);
@@ -250,33 +276,66 @@ __global__ void __launch_bounds__(kRefThreads) k_refine(const RefineArgs a)
             const float floorI = a.cref * __uint_as_float(a.imax[s]);
             const bool bad = a.atom_bad && a.atom_bad[s];
             if (!bad && A2 > 0.f && E > a.tau * fmaxf(I, floorI)) {
-                const int p = atomicAdd(&ncand, 1);
-                cand_r[p] = r;
-                cand_s[p] = s;
+                cr[nf] = r;
+                cs[nf] = s;
+                nf++;
             }
         }
-        __syncthreads();
-        const int nc = ncand;
-        for (int ci = w; ci < nc; ci += kRefWarps) refine_one(a, cand_r[ci], cand_s[ci], ssc, sex);
+        // append: one atomic per warp
+        const int incl = warp_incl_scan(nf);
+        const int wtot = __shfl_sync(0xffffffffu, incl, 31);
+        unsigned long long base = 0;
+        if (lane == 31 && wtot > 0) base = atomicAdd(a.nref, (unsigned long long)wtot);
+        base = __shfl_sync(0xffffffffu, base, 31);
+        for (int i = 0; i < nf; i++) {
+            const unsigned long long o = base + (unsigned long long)(incl - nf + i);
+            a.cand_r[o] = cr[i];
+            a.cand_s[o] = cs[i];
+        }
     }
+}
+
+// Evaluation: every warp of a persistent grid takes candidates from the list
+// (a stride of the grid's warp count) and re-evaluates them.
+__global__ void __launch_bounds__(kRefThreads) k_refine_eval(const RefineArgs a)
+{
+    pdl_enter();
+    __shared__ float4 ssc[256];
+    __shared__ float2 sex[64];
+    if (*a.abort_flag) return;
+    const long long total = (long long)*a.nref;
+    if (total == 0) return;
+    for (int i = threadIdx.x; i < 256; i += kRefThreads) ssc[i] = a.sc[i];
+    if (threadIdx.x < 64) sex[threadIdx.x] = a.ex[threadIdx.x];
+    __syncthreads();
+    const long long nw = (long long)gridDim.x * kRefWarps;
+    for (long long i = (long long)blockIdx.x * kRefWarps + (threadIdx.x >> 5); i < total; i += nw)
+        refine_one(a, a.cand_r[i], a.cand_s[i], ssc, sex);
 }
 
 void launch_refine(const RefineArgs& a, cudaStream_t st, bool pdl)
 {
     if (a.n_struct <= 0) return;
-    static int per_sm_cache[64] = {};
+    static int per_sm_cache[64][2] = {};
     int dev = 0;
     cudaGetDevice(&dev);
-    int per_sm = (dev >= 0 && dev < 64) ? per_sm_cache[dev] : 0;
-    if (per_sm < 1) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_refine, kRefThreads, 0) != cudaSuccess ||
-            per_sm < 1)
-            per_sm = 1;
-        if (dev >= 0 && dev < 64) per_sm_cache[dev] = per_sm;
+    int per_sel = (dev >= 0 && dev < 64) ? per_sm_cache[dev][0] : 0, per_ev = (dev >= 0 && dev < 64) ? per_sm_cache[dev][1] : 0;
+    if (per_sel < 1 || per_ev < 1) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sel, k_refine_select, kRefThreads, 0) != cudaSuccess ||
+            per_sel < 1)
+            per_sel = 1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_ev, k_refine_eval, kRefThreads, 0) != cudaSuccess ||
+            per_ev < 1)
+            per_ev = 1;
+        if (dev >= 0 && dev < 64) {
+            per_sm_cache[dev][0] = per_sel;
+            per_sm_cache[dev][1] = per_ev;
+        }
     }
-    const int grid = min(a.grid * per_sm, a.n_struct);
-    if (pdl) launch_pdl(k_refine, grid, kRefThreads, 0, st, a);
-    else k_refine<<<grid, kRefThreads, 0, st>>>(a);
+    // every selection CTA takes a contiguous range of the reflections; the evaluation grid is persistent
+    if (pdl) launch_pdl(k_refine_select, a.grid * per_sel, kRefThreads, 0, st, a);
+    else k_refine_select<<<a.grid * per_sel, kRefThreads, 0, st>>>(a);
+    launch_pdl(k_refine_eval, a.grid * per_ev, kRefThreads, 0, st, a);
 }
 
 }  // namespace xrd

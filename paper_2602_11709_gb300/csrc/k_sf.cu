@@ -12,8 +12,9 @@
 // and every lane walks the same atom list (one broadcast read per atom feeds
 // four terms). Atoms are sorted by
 // element, so f(s) is evaluated once per element run (a warp-uniform branch).
-// The FP32 variants use the SFU for sin/cos (MUFU.SIN/COS) and exp2 (MUFU.EX2,
-// which this part issues at twice the sin/cos rate). FP64 arithmetic runs at
+// The pattern variants form sin/cos on the FMA pipe from the exact phase
+// (sincos_turn32) and use the SFU for exp2 (MUFU.EX2); the gradient variant
+// uses the SFU for sin/cos too (MUFU.SIN/COS). FP64 arithmetic runs at
 // about 1/64 of the FP32 rate here, so the phase is reduced either in FP64
 // (XRD_FP32_PHASE64) or exactly in 32-bit integers (XRD_FP32_PHASEFIX).
 #include "xrd_internal.cuh"
@@ -74,14 +75,18 @@ __device__ __forceinline__ float fprime_of(const Coef32& c, float s2)
 // instead of per reflection. Otherwise every reflection's phase is formed exactly (integer
 // phase) or in FP64 (XRD_FP32_PHASE64).
 //
-// Pattern variants (not GRAD): F is summed in FP32 over blocks of 8 atoms and
+// Pattern variants (not GRAD): sin and cos come from the FMA pipe
+// (sincos_turn32, five times more accurate than the SFU's), F is summed in FP32
+// over blocks of 8 atoms (16 with runs) and
 // each block sum is added into a two-float total (Knuth's TwoSum), so the
 // rounding of the sum grows with the block size instead of the atom count
 // (plain FP32 summation over N atoms errs by about 2e-8 sqrt(N) of the terms'
 // root-sum-square). The lane also sums a_j^2, a_j = occ_j exp(-B_j s^2)
 // max(|f_j|, Z_j), the scale of each term's rounding error (f_j itself may
 // cancel to near zero; its rounding does not), and stores it for the
-// re-evaluation of weak reflections (k_refine). Returns the lane's largest I.
+// re-evaluation of weak reflections (k_refine); with runs, once per run (its
+// reflections, consecutive in l, have nearly equal s^2). Returns the lane's
+// largest I.
 // GRAD also accumulates dF/ds^2 = sum_j occ_j exp(-B_j s^2)(f_j' - B_j f_j) e^{i phi_j}.
 template <int PREC, bool GRAD, int kSfRB, bool RUNS>
 __device__ float sf_tile_fp32(const SfArgs& a, int64_t first, int len, int64_t j0, int64_t j1, Atom32* sat,
@@ -110,6 +115,7 @@ __device__ float sf_tile_fp32(const SfArgs& a, int64_t first, int len, int64_t j
         Rh[i] = 0.f; Rl[i] = 0.f; Ih[i] = 0.f; Il[i] = 0.f; A2[i] = 0.f;
     }
     constexpr bool kRotate = RUNS && PREC == XRD_FP32_PHASEFIX;
+    constexpr int kFoldMask = kRotate ? 15 : 7;  // block size of the two-float sum: 16 atoms with runs, else 8
     int zc = -1;
     for (int64_t c0 = j0; c0 < j1; c0 += kSfChunk) {
         const int nc = (int)min((int64_t)kSfChunk, j1 - c0);
@@ -136,7 +142,8 @@ __device__ float sf_tile_fp32(const SfArgs& a, int64_t first, int len, int64_t j
             double dx = 0.0, dy = 0.0, dz = 0.0;
             if (kRotate) {
                 const uint32_t P = uh[0] * at.X + uk[0] * at.Y + ul[0] * at.Z;
-                __sincosf((float)(int32_t)P * kTwoPiOver2p32, &sn, &cs);
+                if (ACC) sincos_turn32(P, sn, cs);
+                else __sincosf((float)(int32_t)P * kTwoPiOver2p32, &sn, &cs);
                 const float2 st = sstep[jj];
                 cz = st.x;
                 sz = st.y;
@@ -145,7 +152,7 @@ __device__ float sf_tile_fp32(const SfArgs& a, int64_t first, int len, int64_t j
                 const Atom64 d = a.atom64[c0 + jj];
                 dx = d.x; dy = d.y; dz = d.z;
             }
-            const bool fold = ACC && ((jj & 7) == 7 || jj == nc - 1);  // uniform
+            const bool fold = ACC && ((jj & kFoldMask) == kFoldMask || jj == nc - 1);  // uniform
 #pragma unroll
             for (int i = 0; i < kSfRB; i++) {
                 if (!kRotate) {
@@ -154,15 +161,18 @@ __device__ float sf_tile_fp32(const SfArgs& a, int64_t first, int len, int64_t j
                         P = uh[i] * at.X + uk[i] * at.Y + ul[i] * at.Z;
                     else
                         P = fix32(fma((double)(int)uh[i], dx, fma((double)(int)uk[i], dy, (double)(int)ul[i] * dz)));
-                    __sincosf((float)(int32_t)P * kTwoPiOver2p32, &sn, &cs);
+                    if (ACC) sincos_turn32(P, sn, cs);
+                    else __sincosf((float)(int32_t)P * kTwoPiOver2p32, &sn, &cs);
                 }
                 const float dw = ex2_approx(fmaf(at.nb, s2[i], at.lo));
                 const float w = f[i] * dw;
                 Fr[i] = fmaf(w, cs, Fr[i]);
                 Fi[i] = fmaf(w, sn, Fi[i]);
                 if (ACC) {
-                    const float m = dw * fmaxf(fabsf(f[i]), at.zf);
-                    A2[i] = fmaf(m, m, A2[i]);
+                    if (!kRotate || i == 0) {  // a run's reflections share one scale (s^2 nearly equal)
+                        const float m = dw * fmaxf(fabsf(f[i]), at.zf);
+                        A2[i] = fmaf(m, m, A2[i]);
+                    }
                     if (fold) {  // block sum into the two-float total
                         float t = Rh[i] + Fr[i], bb = t - Rh[i];
                         Rl[i] += (Rh[i] - (t - bb)) + (Fr[i] - bb);
@@ -211,7 +221,7 @@ __device__ float sf_tile_fp32(const SfArgs& a, int64_t first, int len, int64_t j
             a.Ig[r] = I;
         } else {
             a.If[r] = I;
-            if (a.W2) a.W2[r] = A2[i];
+            if (a.W2) a.W2[r] = A2[kRotate ? 0 : i];
             if (a.F) a.F[r] = make_float2(fr, fi);
             imax = fmaxf(imax, I);
         }

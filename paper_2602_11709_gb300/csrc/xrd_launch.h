@@ -95,8 +95,9 @@ struct RefineArgs {
     float tau;    // intensity error allowed without re-evaluation, relative to max(I, cref M)
     float cref;   // cutoff fraction (the floor of the guarantee), relative to the largest reflection M
     const int* abort_flag;
-    int* counter;                 // work counter over chunks of 256 reflections (zeroed per call)
-    unsigned long long* nref;     // reflections re-evaluated (zeroed per call)
+    unsigned long long* nref;     // reflections re-evaluated: the candidate list's length (zeroed per call)
+    int64_t* cand_r;              // [reflections] candidate list: reflection index
+    int* cand_s;                  // [reflections] and its structure
     const int64_t* refl_off;
     const int64_t* atom_off;
     const double* q;

@@ -23,16 +23,16 @@ PRECISIONS = {"fp64": XRD_FP64, "fp32_phase64": XRD_FP32_PHASE64, "fp32_phasefix
 STAGES = ["prep", "atoms", "count", "scan", "emit", "structure_factor", "refine", "post", "compact", "profile_sum"]
 XRD_FLAG_HEXAGONAL = 1  # bit of the per-structure flag word: families by Miller-Bravais indices
 # kernels xrd_pattern_batch launches per call: order, coef, atoms (a side stream), prep, count, scan, emit,
-# structure factor, re-evaluation of weak reflections (FP32 variants), post (six size classes), output
-# scan, compaction
-LAUNCHES_PER_BATCH = 17
+# structure factor, re-evaluation of weak reflections (selection and evaluation, FP32 variants), post
+# (six size classes), output scan, compaction
+LAUNCHES_PER_BATCH = 18
 
 
 def launches_per_batch(n_struct: int, refine: bool = True) -> int:
     """Kernels of one xrd_pattern_batch call: above two chunks of 4096 structures the reflection
     scan and the output scan each take two kernels (chunk sums, then the chunks); the FP64
-    variant (or refine off) has no re-evaluation kernel."""
-    return LAUNCHES_PER_BATCH - (0 if refine else 1) + (2 if (n_struct + 4095) // 4096 > 2 else 0)
+    variant (or refine off) has no re-evaluation kernels."""
+    return LAUNCHES_PER_BATCH - (0 if refine else 2) + (2 if (n_struct + 4095) // 4096 > 2 else 0)
 
 
 class xrd_batch(C.Structure):

@@ -139,10 +139,10 @@ def test_missing_library_fails_loudly(tmp_path):
 
 
 def test_launch_count_per_call():
-    """Kernels per xrd_pattern_batch call: 17 with the re-evaluation kernel of the FP32 variants (16
-    without), two more above two chunks of 4096 structures (two-kernel scans)."""
-    assert xrd.launches_per_batch(1024) == 17 and xrd.launches_per_batch(8192) == 17
-    assert xrd.launches_per_batch(8193) == 19 and xrd.launches_per_batch(100_000) == 19
+    """Kernels per xrd_pattern_batch call: 18 with the two re-evaluation kernels of the FP32 variants
+    (16 without), two more above two chunks of 4096 structures (two-kernel scans)."""
+    assert xrd.launches_per_batch(1024) == 18 and xrd.launches_per_batch(8192) == 18
+    assert xrd.launches_per_batch(8193) == 20 and xrd.launches_per_batch(100_000) == 20
     assert xrd.launches_per_batch(1024, refine=False) == 16 and xrd.launches_per_batch(8193, refine=False) == 18
 
 

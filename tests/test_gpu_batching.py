@@ -215,15 +215,19 @@ def test_autotune_then_graph_on_another_stream(gpu_lib):
         db, co = _setup(xrd, b, o)
         sz = h.query_sizes(db, co)
         ws = xrd.workspace(sz.ws_bytes)
-        ref = _run(xrd, h, db, co, sz.n_refl, ws)
+        ref0 = _run(xrd, h, db, co, sz.n_refl, ws)  # default shape
         out = xrd.PatternBuffers(db.n_struct, sz.n_refl)
         h.set_profiling(2)
         h.autotune(db, co, out, ws)
         g = h.graph(db, co, out, ws)
         g.launch(torch.cuda.current_stream())
         torch.cuda.synchronize()
-        _same(ref, out.to_host())
+        got = out.to_host()
         h.set_profiling(0)
+        # the replay equals an eager call with the tuned shape bit for bit; a different shape (runs along
+        # l step the phase factor by rotations) agrees within the FP32 bar
+        _same(_run(xrd, h, db, co, sz.n_refl, ws), got)
+        _close(ref0, got, 1e-5)
     finally:
         h.close()
 

@@ -173,3 +173,77 @@ def test_gradient_back_scattering(gpu_lib, handle):
         for name, gv, rv in (("frac", got["d_frac"][sl], df), ("B", got["d_B"][sl], dB), ("lattice", got["d_lat"][s], dl)):
             rel, cos = _cmp(gv, rv)
             assert rel <= 1e-3 and cos >= 0.99999, (s, name, rel, cos)
+
+
+def test_gradient_against_finite_differences_of_the_gpu_forward(gpu_lib, handle):
+    """GPU gradients against 5-point central differences of the GPU's own broadened pattern, for
+    L = sum_k w_k y_k with fixed random w: coordinates and B of four atoms and the six lattice
+    parameters of three structures. The broadened path computes in FP32 (its y rounds at about
+    1e-7), so the steps are 1e-3 in fractional coordinates, 5e-2 A^2 in B (one atom's B moves L by
+    about 2 s^2 / N of itself), 1e-4 relative in the edges and 1e-3 deg in the angles: truncation
+    error (step^4) and rounding (1e-7 / step) both stay well below the bar. A lattice step that moves a reflection across a sphere surface
+    changes the reflection set (a jump, not a derivative): such parameters are skipped, and at
+    least four of the six must remain."""
+    import torch
+    xrd = gpu_lib
+    base, _, o, grid = _grad_case(idx=np.array([7, 11, 19]))
+    rng = np.random.default_rng(41)
+    w = rng.standard_normal(grid.n_pts)
+
+    def forward(b):
+        db = xrd.DeviceBatch.from_host(b)
+        co = xrd.make_opts(o, "fp32_phasefix")
+        sz = handle.query_sizes(db, co)
+        ws = xrd.workspace(sz.ws_grad_bytes)
+        y = torch.empty(1, grid.n_pts, dtype=torch.float32, device="cuda")
+        status = torch.zeros(1, dtype=torch.int32, device="cuda")
+        totals = torch.zeros(4, dtype=torch.int64, device="cuda")
+        handle.pattern_broadened(db, co, xrd.make_grid(grid), y, status, totals, ws)
+        torch.cuda.synchronize()
+        return float(np.dot(w, y.cpu().numpy()[0].astype(np.float64))), int(totals[0])
+
+    def fd(b, setter, h):
+        vals, counts = [], set()
+        for k in (2, 1, -1, -2):
+            bb = b.subset([0])
+            setter(bb, k * h)
+            L, n = forward(bb)
+            vals.append(L)
+            counts.add(n)
+        return (-vals[0] + 8 * vals[1] - 8 * vals[2] + vals[3]) / (12 * h), len(counts) == 1
+
+    checked_lat = 0
+    for s in range(base.n_struct):
+        b = base.subset([s])
+        got = _run(xrd, handle, b, o, grid, dLdy=w[None, :])
+        groups = {"frac": ([], []), "B": ([], []), "lattice": ([], [])}
+        for j in range(min(4, b.n_atoms)):
+            for c in range(3):
+                def set_x(bb, d, j=j, c=c):
+                    bb.frac[j, c] += d
+                v, _ = fd(b, set_x, 1e-3)
+                groups["frac"][0].append(got["d_frac"][j, c])
+                groups["frac"][1].append(v)
+
+            def set_b(bb, d, j=j):
+                bb.B[j] += d
+            v, _ = fd(b, set_b, 5e-2)  # one atom's share of L is small: a step well above the FP32 rounding
+            groups["B"][0].append(got["d_B"][j])
+            groups["B"][1].append(v)
+        for p in range(6):
+            h = 1e-4 * b.lattice[0, p] if p < 3 else 1e-3
+
+            def set_l(bb, d, p=p):
+                bb.lattice[0, p] += d
+            v, same = fd(b, set_l, h)
+            if same:
+                groups["lattice"][0].append(got["d_lat"][0, p])
+                groups["lattice"][1].append(v)
+                checked_lat += 1
+        # the bar of the oracle-gradient tests, per group, plus 2e-3 for the differences' own error
+        for name, (gv, rv) in groups.items():
+            if not gv:
+                continue
+            rel, cos = _cmp(gv, rv)
+            assert rel <= 3e-3 and cos >= 0.99999, (s, name, rel, cos)
+    assert checked_lat >= 4
