@@ -19,6 +19,9 @@ CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libxrd.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# The cluster kernel's CTAs read data the cluster's other CTAs wrote: its global loads are cached
+# in L2 only, where those writes are visible after a fence and a cluster barrier.
+FILE_FLAGS = {"k_post_big.cu": ["-Xptxas", "-dlcm=cg"]}
 
 
 def nvcc() -> str:
@@ -49,7 +52,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def compile_one(src):
         obj = os.path.join(LIBDIR, os.path.splitext(os.path.basename(src))[0] + ".o")
-        r = subprocess.run([nvcc()] + flags + ["-c", src, "-o", obj], capture_output=True, text=True)
+        extra = FILE_FLAGS.get(os.path.basename(src), [])
+        r = subprocess.run([nvcc()] + flags + extra + ["-c", src, "-o", obj], capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed on %s:\n%s" % (src, r.stderr))
         if verbose and r.stderr:

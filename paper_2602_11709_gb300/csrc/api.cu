@@ -25,8 +25,8 @@ struct xrd_handle {
     int sf_runs = 0;                    // lanes take runs consecutive in l (integer phase only)
     int enum_threads = 256;             // threads per structure of the enumeration kernels (xrd_autotune)
     // side streams for the concurrent post-processing size classes (fork/join by events)
-    cudaStream_t side[xrd::kPostClasses - 1] = {};
-    cudaEvent_t fork = nullptr, join[xrd::kPostClasses - 1] = {};
+    cudaStream_t side[xrd::kPostStreams - 1] = {};
+    cudaEvent_t fork = nullptr, join[xrd::kPostStreams - 1] = {};
     // the input-only front (coefficients, atom packing, largest-first order) runs on side[0]
     // beside the enumeration: forked by front, joined by order_done and atoms_done
     cudaEvent_t front = nullptr, order_done = nullptr, atoms_done = nullptr;
@@ -89,7 +89,7 @@ struct Layout {
         flags, coef32, atom32, atom64, astep, imax, cdd, atomr;
     size_t q, key, runs, I, W2, cand_r, cand_s, g_perm, g_bkt, g_flag, g_pstart, g_psum, g_fcnt;
     size_t st_q, st_I, st_foff, st_hkl, st_mult;
-    size_t parts;
+    size_t parts, cpart;
     size_t total;
 };
 
@@ -141,6 +141,7 @@ Layout layout(int64_t n, int64_t natoms, int zmax, int64_t R)
     L.st_hkl = take(12 * R);
     L.st_mult = take(4 * R);
     L.parts = take(scan_parts_bytes(n));
+    L.cpart = take(8 * 2 * xrd::kPostClusterMax * xrd::kPostClustersMax);
     L.total = o;
     return L;
 }
@@ -352,7 +353,7 @@ int xrd_create(xrd_handle** h, int device)
         e = cudaEventCreate(&p->ev[i]);
         if (e != cudaSuccess) { xrd_destroy(p); return XRD_ECUDA; }
     }
-    for (int i = 0; i < xrd::kPostClasses - 1; i++) {
+    for (int i = 0; i < xrd::kPostStreams - 1; i++) {
         e = cudaStreamCreateWithFlags(&p->side[i], cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->join[i], cudaEventDisableTiming);
         if (e != cudaSuccess) { xrd_destroy(p); return XRD_ECUDA; }
@@ -377,7 +378,7 @@ void xrd_destroy(xrd_handle* h)
     DeviceGuard g(h->device);
     for (int i = 0; i < kEvents; i++)
         if (h->ev[i]) cudaEventDestroy(h->ev[i]);
-    for (int i = 0; i < xrd::kPostClasses - 1; i++) {
+    for (int i = 0; i < xrd::kPostStreams - 1; i++) {
         if (h->side[i]) cudaStreamDestroy(h->side[i]);
         if (h->join[i]) cudaEventDestroy(h->join[i]);
     }
@@ -694,6 +695,7 @@ int xrd_pattern_batch(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, cons
     pa.nfm = (int64_t*)(ws + L.nfm);
     pa.l2h = (float)pa.l2d;
     pa.l2l = (float)(pa.l2d - (double)pa.l2h);
+    pa.cpart = (long long*)(ws + L.cpart);
     if (out->refl_off && out->cap_refl > 0) {
         pa.cap_refl = out->cap_refl;
         pa.refl_hkl = out->refl_hkl;
@@ -701,14 +703,14 @@ int xrd_pattern_batch(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, cons
         pa.refl_I = out->refl_I;
     }
     {  // the size classes run concurrently: fork to the side streams, join back
-        cudaStream_t cs[xrd::kPostClasses] = {st};
+        cudaStream_t cs[xrd::kPostStreams] = {st};
         cudaEventRecord(h->fork, st);
-        for (int i = 1; i < xrd::kPostClasses; i++) {
+        for (int i = 1; i < xrd::kPostStreams; i++) {
             cs[i] = h->side[i - 1];
             cudaStreamWaitEvent(cs[i], h->fork, 0);
         }
         xrd::launch_post(pa, cs);
-        for (int i = 1; i < xrd::kPostClasses; i++) {
+        for (int i = 1; i < xrd::kPostStreams; i++) {
             cudaEventRecord(h->join[i - 1], cs[i]);
             cudaStreamWaitEvent(st, h->join[i - 1], 0);
         }

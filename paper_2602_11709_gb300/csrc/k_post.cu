@@ -17,6 +17,7 @@
 // between definite starts are resolved one thread per run.
 #include "xrd_internal.cuh"
 #include "xrd_launch.h"
+#include "xrd_post.cuh"
 
 namespace xrd {
 
@@ -56,82 +57,6 @@ const TTab* init_tables(cudaStream_t st)
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_ttab) != cudaSuccess) return nullptr;
     return (const TTab*)p;
-}
-
-// 2-theta in degrees from |g|^2 in FP64, the definition 2 asin(lambda |g| / 2)
-// with every step rounded on its own (no contraction), sin(theta) clamped at 1.
-__device__ __noinline__ double tt_deg64(double q, double lambda)
-{
-    double sth = __dmul_rn(__dmul_rn(lambda, __dsqrt_rn(q)), 0.5);
-    if (sth > 1.0) sth = 1.0;
-    return __dmul_rn(__dmul_rn(2.0, asin(sth)), 180.0 / kPi);
-}
-
-// Merge test: 2theta(qb) - 2theta(qa) < tol for qb >= qa > 0. With
-// x = lambda sqrt(q) / 2 = sin theta and c = cos theta,
-// tan((2theta_b - 2theta_a) / 4) = (xb - xa) / (ca + cb) and
-// xb - xa = (lambda / 2)(qb - qa) / (sqrt qa + sqrt qb); qb - qa is exact in FP64
-// for close values. Comparing against ttol = tan(tol / 4) (tol in radians)
-// leaves neither a division nor an arctangent. This FP32 form is good to about
-// 1e-6 relative, plus the rounding of 1 - lambda^2 q / 4 relative to cos^2(theta)
-// (~1.3e-7 / cos^2); a pair within 1e-5 + 1e-6 / cos^2 of the tolerance is
-// decided in FP64 from the definition instead, so that every merge decision is
-// an FP64 one. It is the same decision as a CPU evaluation of the definition
-// except for gaps within a few ulp of 2-theta of the tolerance: CUDA's asin
-// and the C library's asin are each accurate to about an ulp but are not
-// guaranteed to round alike, so such a gap may fall on either side.
-__device__ __forceinline__ bool tt_close(double qa, double qb, float l2, float lh, float ttol, double lambda,
-                                         double tol)
-{
-    if (dbits(qb) <= dbits(qa)) return ttol > 0.f;  // equal |g|^2: a gap of 0
-    if (ttol == INFINITY) return true;              // tol above 180 degrees: every gap is below it
-    const float dqf = d2f_pos(qb - qa);
-    const float qaf = d2f_pos(qa), qbf = d2f_pos(qb);
-    const float ua = fmaxf(fmaf(-l2, qaf, 1.f), 1e-30f), ub = fmaxf(fmaf(-l2, qbf, 1.f), 1e-30f);
-    const float sq = qaf * rsqrtf(qaf) + qbf * rsqrtf(qbf);
-    const float c = ua * rsqrtf(ua) + ub * rsqrtf(ub);
-    const float lhs = lh * dqf, rhs = ttol * (sq * c);
-    const float band = fmaf(1e-6f, __frcp_rn(fminf(ua, ub)), 1e-5f);
-    if (!(fabsf(lhs - rhs) <= band * rhs)) return lhs < rhs;
-    return __dsub_rn(tt_deg64(qb, lambda), tt_deg64(qa, lambda)) < tol;
-}
-
-// Family key: the absolute values of the indices sorted descending, packed:
-// (h, k, l) and a 0, or for a hexagonal cell the Miller-Bravais (h, k, i = -h - k, l)
-// (|i| <= 1022 fits the 10-bit fields). Families are the classes of equal keys.
-__device__ __forceinline__ unsigned long long family_key(uint32_t key, bool hex)
-{
-    const int h = hkl_h(key), k = hkl_k(key);
-    int v0 = abs(h), v1 = abs(k), v2 = abs(hkl_l(key)), v3 = hex ? abs(h + k) : 0, t;
-    // sorting network for 4 values, descending
-    if (v1 > v0) { t = v0; v0 = v1; v1 = t; }
-    if (v3 > v2) { t = v2; v2 = v3; v3 = t; }
-    if (v2 > v0) { t = v0; v0 = v2; v2 = t; }
-    if (v3 > v1) { t = v1; v1 = v3; v3 = t; }
-    if (v2 > v1) { t = v1; v1 = v2; v2 = t; }
-    return ((unsigned long long)v0 << 30) | ((unsigned long long)v1 << 20) | ((unsigned long long)v2 << 10) |
-           (unsigned long long)v3;
-}
-
-// number of distinct families among the members i0..i1-1 of one peak
-template <typename PermT>
-__device__ __forceinline__ int count_families(const uint32_t* key, const PermT* perm, int i0, int i1, bool hex)
-{
-    int nfam = 0;
-    for (int i = i0; i < i1; i++) {
-        const unsigned long long fk = family_key(key[perm[i]], hex);
-        bool lead = true;
-        for (int j = i0; j < i && lead; j++) lead = family_key(key[perm[j]], hex) != fk;
-        nfam += lead;
-    }
-    return nfam;
-}
-
-// sort order: ascending |g|^2, ties by descending (h, k, l)
-__device__ __forceinline__ bool before(double qa, uint32_t ka, double qb, uint32_t kb)
-{
-    const unsigned long long a = dbits(qa), b = dbits(qb);  // q > 0: bit order is numeric order
-    return a < b || (a == b && ka > kb);
 }
 
 // The common case of a structure whose sorted reflections are all farther apart
@@ -427,6 +352,9 @@ __global__ void __launch_bounds__(NT) k_post(const PostArgs a, int cls)
         const int li = claim;
         if (li >= cnt) break;
         const int s = list[li];
+        const int64_t base = a.refl_off[s];
+        const int n = (int)(a.refl_off[s + 1] - base);
+        if (CAP == 0 && a.big && n > post_big_min(cnt, a.grid)) continue;  // the cluster kernel's
         if (a.atom_bad && a.atom_bad[s]) {  // an invalid atom: no peaks, the structure reports XRD_EINVAL
             if (threadIdx.x == 0) {
                 a.npk[s] = 0;
@@ -438,8 +366,6 @@ __global__ void __launch_bounds__(NT) k_post(const PostArgs a, int cls)
             }
             continue;
         }
-        const int64_t base = a.refl_off[s];
-        const int n = (int)(a.refl_off[s + 1] - base);
         if (n == 0) {
             if (threadIdx.x == 0) { a.npk[s] = 0; a.nfm[s] = 0; }
             continue;
@@ -686,11 +612,16 @@ static void launch_post_class(const PostArgs& a, int cls, cudaStream_t st)
     k_post<CAP, NT, FI><<<grid, NT, smem, st>>>(a, cls);
 }
 
-// st[c]: the stream of size class c (the caller forks and joins them)
+// st[c]: the stream of size class c, st[kPostClasses] that of the clusters (the caller forks and joins them)
 template <bool FI>
 static void launch_post_fi(const PostArgs& a, const cudaStream_t* st)
 {
-    launch_post_class<0, 1024, FI>(a, 5, st[5]);
+    // the last class: structures above kPostBigMin reflections one thread-block cluster each (beside
+    // the rest), the others one CTA each; without a cluster that fits, one CTA each for all
+    PostArgs b = a;
+    b.big = 1;
+    if (!launch_post_big(b, 5, st[kPostClasses])) b.big = 0;
+    launch_post_class<0, 1024, FI>(b, 5, st[5]);
     launch_post_class<kPostCap4, 1024, FI>(a, 4, st[4]);
     launch_post_class<kPostCap3, 512, FI>(a, 3, st[3]);
     launch_post_class<kPostCap2, 256, FI>(a, 2, st[2]);

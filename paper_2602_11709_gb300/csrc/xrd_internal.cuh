@@ -22,6 +22,21 @@ constexpr int kHklLimit = 511;        // |h|, |k|, |l| fit the 10-bit fields of 
 constexpr int kPostClasses = 6;
 constexpr int kRunsPerTile = 32;  // structure-factor tile: one run of reflections per lane of a warp
 constexpr int kPostCap0 = 256, kPostCap1 = 512, kPostCap2 = 1536, kPostCap3 = 3072, kPostCap4 = 6144;
+// Structures of the last class above a size threshold run one thread-block cluster each
+// (k_post_big): above kPostBigMin reflections when the class holds at most one structure per eight
+// SMs (a few big structures would otherwise set the time), else above kPostBigMinMany (many big
+// structures keep every SM busy one CTA each, which has more throughput). At most kPostClusterMax
+// CTAs per cluster and kPostClustersMax clusters (each with a partial-result area in the
+// workspace); the kernel runs beside the others on a stream of its own.
+constexpr int kPostBigMin = 65536;
+constexpr int kPostBigMinMany = 262144;
+__host__ __device__ __forceinline__ int post_big_min(int class_count, int sms)
+{
+    return class_count * 8 <= sms ? kPostBigMin : kPostBigMinMany;
+}
+constexpr int kPostClusterMax = 16;
+constexpr int kPostClustersMax = 64;
+constexpr int kPostStreams = kPostClasses + 1;
 __host__ __device__ __forceinline__ int post_class(long long c)
 {
     return c <= kPostCap0 ? 0 : c <= kPostCap1 ? 1 : c <= kPostCap2 ? 2 : c <= kPostCap3 ? 3 : c <= kPostCap4 ? 4 : 5;

@@ -153,6 +153,8 @@ struct PostArgs {
     double* refl_tt;
     double* refl_I;
     float l2h, l2l;  // lambda^2 / 4 as two floats (2-theta of the list)
+    long long* cpart;  // [kPostClustersMax][2 kPostClusterMax] partial results of the cluster kernel (or nullptr)
+    int big;           // 1: the cluster kernel takes the last class's structures above post_big_min reflections
 };
 
 struct CompactArgs {
@@ -243,7 +245,8 @@ void launch_sf(const SfArgs& a, cudaStream_t st, bool pdl);
 RefineTables init_refine_tables(cudaStream_t st);  // fills the tables, returns their device addresses
 void launch_refine(const RefineArgs& a, cudaStream_t st, bool pdl);
 size_t post_smem_bytes(int cap);
-void launch_post(const PostArgs& a, const cudaStream_t* st);  // st[kPostClasses]
+void launch_post(const PostArgs& a, const cudaStream_t* st);  // st[kPostStreams]: a stream per class, then the clusters'
+bool launch_post_big(const PostArgs& a, int cls, cudaStream_t st);  // false: no cluster fits (use one CTA)
 void launch_compact(const CompactArgs& a, cudaStream_t st);
 const TTab* init_tables(cudaStream_t st);  // fills the 2-theta table, returns its device address
 size_t broaden_smem_bytes(int n_pts, int W);
