@@ -139,11 +139,11 @@ def test_missing_library_fails_loudly(tmp_path):
 
 
 def test_launch_count_per_call():
-    """Kernels per xrd_pattern_batch call: 18 with the two re-evaluation kernels of the FP32 variants
-    (16 without), two more above two chunks of 4096 structures (two-kernel scans)."""
-    assert xrd.launches_per_batch(1024) == 18 and xrd.launches_per_batch(8192) == 18
-    assert xrd.launches_per_batch(8193) == 20 and xrd.launches_per_batch(100_000) == 20
-    assert xrd.launches_per_batch(1024, refine=False) == 16 and xrd.launches_per_batch(8193, refine=False) == 18
+    """Kernels per xrd_pattern_batch call: 19 with the two re-evaluation kernels of the FP32 variants
+    (17 without), two more above two chunks of 4096 structures (two-kernel scans)."""
+    assert xrd.launches_per_batch(1024) == 19 and xrd.launches_per_batch(8192) == 19
+    assert xrd.launches_per_batch(8193) == 21 and xrd.launches_per_batch(100_000) == 21
+    assert xrd.launches_per_batch(1024, refine=False) == 17 and xrd.launches_per_batch(8193, refine=False) == 19
 
 
 def test_binding_argument_checks():
