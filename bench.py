@@ -14,6 +14,7 @@ through their own graphs.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload mixed|large|small|stress|nacl] [--path pattern|augmented|grad]
                   [--sf-shape TILE,WARPS,RUNS | --no-tune] [--no-extras]
+                  [--profile-calls K [--subset N]]
 
 Under torchrun (N > 1) each rank takes a cost-balanced share (largest
 processing time first on reflections x atoms) of a batch N times larger (weak
@@ -94,7 +95,7 @@ def reduce_over_ranks(terms, structures, seconds, world, device="cpu"):
 # DRAM bytes (read + write) of one k_sf launch per (workload, tile, warps, runs): dram__bytes_read.sum +
 # dram__bytes_write.sum from one ncu capture of the current kernel on each timed shape (profiles/);
 # a shape without a capture of the current kernel reports null.
-SF_TRAFFIC_BYTES = {}
+SF_TRAFFIC_BYTES = {("mixed", 128, 1, 1): 1.66e9}
 N_SMS = 152
 SM_MAX_MHZ = 2070.0
 GRAD_WORKLOAD = ("grad: 512 seeded P1 cells, a,b,c U[3,15] A, angles U[60,120] deg, 8-128 atoms, Z U{1..83}, "
@@ -493,7 +494,8 @@ def run_ours(args):
                    "patterns_per_s": r["patterns_per_s"]}
         tuned = main["tuned"]
         roofl = dict(main.get("roofline", {}))
-        roofl.update({"traffic": SF_TRAFFIC_BYTES.get((args.workload,) + tuple(tuned or (128, 2, 0))),
+        roofl.update({"unit_rates_per_clk_per_sm": {k: round(v, 2) for k, v in roof.rates.items()},
+                      "traffic": SF_TRAFFIC_BYTES.get((args.workload,) + tuple(tuned or (128, 2, 0))),
                       "traffic_unit": "bytes per launch (dram read + write, ncu, this shape)",
                       "peak_basis": "arithmetic floor from unit rates measured in this run (xrd_unit_rates: FFMA "
                                     "%.1f, MUFU ex2 %.1f per clk per SM) x %d SMs at the sampled SM clock %.0f MHz: "
@@ -897,6 +899,31 @@ def _refl_off_of(h, db, co, sz, d):
     return out.refl_off.cpu().numpy()
 
 
+def run_profile_calls(args):
+    """--profile-calls K: K untimed xrd_pattern_batch calls on the workload (its first --subset
+    structures), launch shape --sf-shape (default 128,1,1), no graph, no autotuning, no oracle: the
+    program that profiler captures run. Prints the work counts of the last call."""
+    import torch
+    from paper_2602_11709_gb300 import xrd
+    b, o = load_workload(args.workload)
+    if 0 < args.subset < b.n_struct:
+        b = b.subset(np.arange(args.subset))
+    h = xrd.Handle(0)
+    h.set_sf_shape(*[int(v) for v in (args.sf_shape or "128,1,1").split(",")])
+    db = xrd.DeviceBatch.from_host(b)
+    co = xrd.make_opts(o, args.precision)
+    sz = h.query_sizes(db, co)
+    out = xrd.PatternBuffers(b.n_struct, sz.n_refl)
+    ws = xrd.workspace(sz.ws_bytes)
+    for _ in range(args.profile_calls):
+        h.pattern_batch(db, co, out, ws)
+    torch.cuda.synchronize()
+    t = h.work_counts(db, ws)
+    print(json.dumps({"workload": args.workload, "n_struct": b.n_struct, "n_refl": int(sz.n_refl),
+                      "calls": args.profile_calls, "terms": int(t[0]), "seeds": int(t[1]), "refined": int(t[3]),
+                      "totals": [int(v) for v in out.totals.tolist()]}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -917,12 +944,18 @@ def main():
                          "broadened pattern and its gradient (512 structures, 4096 points)")
     ap.add_argument("--no-extras", action="store_true",
                     help="mixed workload: skip the large, NaCl, stress and small sub-records")
+    ap.add_argument("--profile-calls", type=int, default=0,
+                    help="K > 0: K untimed pattern calls (fixed --sf-shape, default 128,1,1) for profiler "
+                         "captures; prints work counts instead of a bench line")
+    ap.add_argument("--subset", type=int, default=0, help="with --profile-calls: the first N structures only")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.workload is None:
         args.workload = "small" if args.path == "augmented" else "mixed"
-    if args.path == "grad":
+    if args.profile_calls > 0:
+        run_profile_calls(args)
+    elif args.path == "grad":
         run_grad(args)
     elif args.path == "augmented":
         run_augmented(args)

@@ -297,7 +297,7 @@ int xrd_pattern_augmented(xrd_handle* h, const xrd_batch* batch, const xrd_opts*
  * runs) -- times the stages a shape changes (count, scan, emit, structure
  * factor; the minimum of four calls) with CUDA events, synchronising `stream`,
  * and keeps the fastest shape in the handle, then picks the enumeration
- * kernels' threads per structure (64, 128 or 256) the same way; later calls with opts.tile = -1 use
+ * kernels' launch shape (xrd_set_enum_threads) the same way; later calls with opts.tile = -1 use
  * it. Writes the chosen tile, warps and runs (0 or 1) if the pointers are not
  * NULL. Returns after `stream` has been synchronised (every tuning call has
  * finished). Not capturable.
@@ -322,11 +322,11 @@ int xrd_work_counts(xrd_handle* h, const xrd_batch* batch, const void* workspace
 /*
  * Issue rates of the units that bound the structure-factor kernel, measured on
  * the handle's device (the paper has no counterpart: these are the peak of the
- * kernel's roofline). rates[0..3] = MUFU sin, MUFU cos, MUFU ex2 and FP32 FMA
- * operations per SM per clock (host array of 4): one CTA of 1024 threads with
- * eight independent chains of the operation per thread, timed by the SM's
- * clock64 counter. Allocates a few bytes of device memory and synchronises;
- * not for the hot path.
+ * kernel's roofline). rates[0..4] = MUFU sin, MUFU cos, MUFU ex2, FP32 FMA and
+ * FP64 FMA operations per SM per clock (host array of 5): one CTA of 1024
+ * threads with eight independent chains of the operation per thread, timed by
+ * the SM's clock64 counter. Allocates a few bytes of device memory and
+ * synchronises; not for the hot path.
  */
 int xrd_unit_rates(xrd_handle* h, double* rates);
 
@@ -335,8 +335,10 @@ int xrd_unit_rates(xrd_handle* h, double* rates);
  * with tile 128 and XRD_FP32_PHASEFIX only, makes lanes take runs consecutive in l). */
 int xrd_set_sf_shape(xrd_handle* h, int tile, int warps, int runs);
 
-/* Threads per structure of the enumeration kernels (64, 128 or 256; 256 by default).
- * The emitted order of reflections changes with it, the pattern does not. */
+/* Launch shape of the enumeration kernels (256 by default): 64, 128 or 256 threads per CTA
+ * with one warp per structure (the CTA's whole block takes the few structures above 1024
+ * columns or 4096 reflections), or 512 or 1024 threads with one CTA per structure.
+ * Neither the order of the enumerated reflections nor the pattern changes with it. */
 int xrd_set_enum_threads(xrd_handle* h, int threads);
 
 /*
@@ -388,7 +390,7 @@ int xrd_stage_times(xrd_handle* h, float* ms, int n);
  *    there; with eager loading (CUDA_MODULE_LOADING=EAGER) on every device
  *    where the library is loaded, called there or not. It stays reserved
  *    until the process exits.
- *  - Limit: the per-structure and per-atom arrays (about 1.2 KB per
+ *  - Limit: the per-structure and per-atom arrays (about 250 bytes per
  *    structure and 120 bytes per atom) plus about 116 bytes per Friedel-unique
  *    reflection must fit in 64 MiB. A batch whose per-structure and per-atom
  *    part does not fit is rejected on the host with XRD_ECAPACITY; one whose

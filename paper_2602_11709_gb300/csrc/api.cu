@@ -85,11 +85,11 @@ size_t al(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Byte offsets of every array in the caller's workspace.
 struct Layout {
-    size_t geo, refl_cnt, run_cnt, tcnt, refl_off, tile_off, order, atom_bad, cls_list, tile_tab, npk, nfm, fam_soff,
+    size_t geo, refl_cnt, run_cnt, refl_off, tile_off, order, atom_bad, cls_list, tile_tab, npk, nfm, fam_soff,
         flags, coef32, atom32, atom64, astep, imax, cdd, atomr;
-    size_t q, key, runs, I, W2, cand_r, cand_s, g_perm, g_bkt, g_flag, g_pstart, g_psum, g_fcnt;
+    size_t q, key, runs, I, Eb, cand_r, cand_s, g_perm, g_bkt, g_flag, g_pstart, g_psum, g_fcnt;
     size_t st_q, st_I, st_foff, st_hkl, st_mult;
-    size_t parts, cpart;
+    size_t parts, oparts, cpart;
     size_t total;
 };
 
@@ -104,7 +104,6 @@ Layout layout(int64_t n, int64_t natoms, int zmax, int64_t R)
     L.geo = take(sizeof(xrd::Geo) * n);
     L.refl_cnt = take(8 * n);
     L.run_cnt = take(8 * n);
-    L.tcnt = take(4 * 2 * 256 * n);
     L.refl_off = take(8 * (n + 1));
     L.tile_off = take(4 * (n + 1));
     L.order = take(4 * n);
@@ -126,7 +125,7 @@ Layout layout(int64_t n, int64_t natoms, int zmax, int64_t R)
     L.key = take(4 * R);
     L.runs = take(4 * R);
     L.I = take(8 * R);
-    L.W2 = take(4 * R);
+    L.Eb = take(4 * R);
     L.cand_r = take(8 * R);
     L.cand_s = take(4 * R);
     L.g_perm = take(4 * R);
@@ -141,6 +140,7 @@ Layout layout(int64_t n, int64_t natoms, int zmax, int64_t R)
     L.st_hkl = take(12 * R);
     L.st_mult = take(4 * R);
     L.parts = take(scan_parts_bytes(n));
+    L.oparts = take(xrd::order_parts_bytes(n));
     L.cpart = take(8 * 2 * xrd::kPostClusterMax * xrd::kPostClustersMax);
     L.total = o;
     return L;
@@ -149,9 +149,9 @@ Layout layout(int64_t n, int64_t natoms, int zmax, int64_t R)
 // Workspace of the broadened-pattern / gradient path: the geometry prefix of
 // the pattern layout plus the per-reflection state kept for the backward pass.
 struct LayoutG {
-    size_t geo, refl_cnt, run_cnt, tcnt, refl_off, tile_off, order, atom_bad, tile_tab, flags, coef32, atom32, atom64,
+    size_t geo, refl_cnt, run_cnt, refl_off, tile_off, order, atom_bad, tile_tab, flags, coef32, atom32, atom64,
         astep;
-    size_t q, key, runs, Fx, Ig, tb, td, perm, U, V, aorder, parts;
+    size_t q, key, runs, Fx, Ig, tb, td, perm, U, V, aorder, parts, oparts;
     size_t total;
 };
 
@@ -163,7 +163,6 @@ LayoutG layout_grad(int64_t n, int64_t natoms, int zmax, int64_t R)
     L.geo = take(sizeof(xrd::Geo) * n);
     L.refl_cnt = take(8 * n);
     L.run_cnt = take(8 * n);
-    L.tcnt = take(4 * 2 * 256 * n);
     L.refl_off = take(8 * (n + 1));
     L.tile_off = take(4 * (n + 1));
     L.order = take(4 * n);
@@ -186,6 +185,7 @@ LayoutG layout_grad(int64_t n, int64_t natoms, int zmax, int64_t R)
     L.V = take(4 * R);
     L.aorder = take(4 * n);
     L.parts = take(scan_parts_bytes(n));
+    L.oparts = take(xrd::order_parts_bytes(n));
     L.total = o;
     return L;
 }
@@ -301,7 +301,6 @@ xrd::GeomArgs geom_args(const xrd_batch* b, const xrd_opts* o, const Layout& L, 
     g.atom64 = (xrd::Atom64*)(ws + L.atom64);
     g.refl_cnt = (int64_t*)(ws + L.refl_cnt);
     g.run_cnt = (int64_t*)(ws + L.run_cnt);
-    g.tcnt = (int*)(ws + L.tcnt);
     g.runs = (int*)(ws + L.runs);
     g.astep = (float2*)(ws + L.astep);
     g.work = (unsigned long long*)(ws + L.flags + kWorkOffset);
@@ -312,11 +311,13 @@ xrd::GeomArgs geom_args(const xrd_batch* b, const xrd_opts* o, const Layout& L, 
     g.tile_tab = (int2*)(ws + L.tile_tab);
     g.cls_list = (int*)(ws + L.cls_list);
     g.abort_flag = (int*)(ws + L.flags);
+    g.enum_ctr = g.abort_flag + 26;
     g.totals = totals;
     g.status = status;
     g.q = (double*)(ws + L.q);
     g.key = (uint32_t*)(ws + L.key);
     g.parts = (long long*)(ws + L.parts);
+    g.oparts = xrd::order_parts_bytes(b->n_struct) ? (int*)(ws + L.oparts) : nullptr;
     g.imax = (unsigned*)(ws + L.imax);
     g.cdd = (float4*)(ws + L.cdd);
     g.atomr = (xrd::AtomR*)(ws + L.atomr);
@@ -437,7 +438,7 @@ static int count_reflections(xrd_handle* h, const xrd_batch* b, const xrd_opts* 
     const int64_t n = b->n_struct;
     cnt.assign(n, 0);
     if (n == 0) return XRD_OK;
-    const size_t need = al(sizeof(xrd::Geo) * n) + al(8 * n);
+    const size_t need = al(sizeof(xrd::Geo) * n) + al(8 * n) + al(16);
     if (h->qbuf_bytes < need) {
         if (h->qbuf) cudaFree(h->qbuf);
         h->qbuf = nullptr;
@@ -455,6 +456,8 @@ static int count_reflections(xrd_handle* h, const xrd_batch* b, const xrd_opts* 
     a.lattice = b->lattice;
     a.geo = (xrd::Geo*)((char*)h->qbuf + L.geo);
     a.refl_cnt = (int64_t*)((char*)h->qbuf + L.refl_cnt);
+    a.enum_ctr = (int*)((char*)h->qbuf + L.refl_cnt + al(8 * n));  // the counting kernel's claim counter
+    cudaMemsetAsync(a.enum_ctr, 0, 16, st);
     xrd::launch_count_only(a, st);
     cudaError_t e = cudaMemcpyAsync(cnt.data(), a.refl_cnt, 8 * n, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -614,7 +617,8 @@ int xrd_pattern_batch(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, cons
     else sa.If = (float*)(ws + L.I);
     sa.F = nullptr;
     if (refine) {
-        sa.W2 = (float*)(ws + L.W2);
+        sa.Eb = (float*)(ws + L.Eb);
+        sa.eps_k = kRefineEpsK;
         sa.imax = ga.imax;
     }
     xrd::launch_sf(sa, st, false);
@@ -626,7 +630,8 @@ int xrd_pattern_batch(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, cons
         ra.grid = h->sms;
         ra.lambda = o->lambda;
         ra.l2f = (float)(o->lambda * o->lambda * 0.25);
-        ra.eps_k = kRefineEpsK;
+        ra.l2h = ra.l2f;
+        ra.l2l = (float)(o->lambda * o->lambda * 0.25 - (double)ra.l2h);
         ra.tau = kRefineTau;
         ra.cref = (float)(o->rel_cutoff > 0.0 ? o->rel_cutoff : kRefineFloorNoCut);
         ra.abort_flag = ga.abort_flag;
@@ -638,7 +643,7 @@ int xrd_pattern_batch(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, cons
         ra.q = ga.q;
         ra.key = ga.key;
         ra.If = sa.If;
-        ra.W2 = sa.W2;
+        ra.Eb = sa.Eb;
         ra.imax = ga.imax;
         ra.atomr = ga.atomr;
         ra.cdd = ga.cdd;
@@ -749,8 +754,8 @@ int xrd_pattern_batch(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, cons
 int xrd_set_enum_threads(xrd_handle* h, int threads)
 {
     if (!h) return XRD_EINVAL;
-    if (threads != 64 && threads != 128 && threads != 256)
-        return fail(h, XRD_EINVAL, "enumeration threads must be 64, 128 or 256");
+    if (threads != 64 && threads != 128 && threads != 256 && threads != 512 && threads != 1024)
+        return fail(h, XRD_EINVAL, "enumeration threads must be 64, 128, 256, 512 or 1024");
     h->enum_threads = threads;
     return XRD_OK;
 }
@@ -849,12 +854,12 @@ int xrd_autotune(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, const xrd
     h->sf_rb = brb;
     h->sf_warps = bw;
     h->sf_runs = bruns;
-    // then the enumeration's CTA size with that shape: many small structures fill more SMs with
-    // 64- or 128-thread CTAs, large ones need 256 threads
+    // then the enumeration's launch shape with that shape: one warp per structure (64-256 threads
+    // per CTA) for many small structures, one CTA of 512 or 1024 threads per structure for large ones
     const int keep_et = h->enum_threads;
     float best_et = 1e30f;
     int bet = keep_et;
-    for (int et : {256, 128, 64}) {
+    for (int et : {256, 128, 64, 512, 1024}) {
         h->enum_threads = et;
         float t = 1e30f;
         for (int rep = 0; rep < 5; rep++) {
@@ -1014,7 +1019,6 @@ static void launch_front(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, c
     ga.atom64 = (xrd::Atom64*)(ws + L.atom64);
     ga.refl_cnt = (int64_t*)(ws + L.refl_cnt);
     ga.run_cnt = (int64_t*)(ws + L.run_cnt);
-    ga.tcnt = (int*)(ws + L.tcnt);
     ga.runs = (int*)(ws + L.runs);
     ga.astep = ga.runs_mode ? (float2*)(ws + L.astep) : nullptr;
     ga.work = (unsigned long long*)(ws + L.flags + kWorkOffset);
@@ -1025,11 +1029,13 @@ static void launch_front(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, c
     ga.atoms_set_geo = 1;  // atoms run before the enumeration here
     ga.tile_tab = (int2*)(ws + L.tile_tab);
     ga.abort_flag = (int*)(ws + L.flags);
+    ga.enum_ctr = ga.abort_flag + 26;
     ga.totals = totals;
     ga.status = status;
     ga.q = (double*)(ws + L.q);
     ga.key = (uint32_t*)(ws + L.key);
     ga.parts = (long long*)(ws + L.parts);
+    ga.oparts = xrd::order_parts_bytes(n) ? (int*)(ws + L.oparts) : nullptr;
     cudaMemsetAsync(ws + L.flags, 0, kFlagBytes, st);
     xrd::launch_prep(ga, st, false);
     xrd::launch_coef(ga, st, true);

@@ -301,38 +301,13 @@ __device__ __forceinline__ void column_range(const float* gf, int L, int h, int 
     if (h == 0 && k == 0 && lo < 1) lo = 1;  // half-space: (0, 0, l > 0)
 }
 
-// |g|^2 of the emitted reflections along one column (h, k), in two-float
-// arithmetic (about 1e-14 relative): the value that sorting, merging and the
-// outputs use. The inside/outside decision on the sphere boundary does not use
-// it; that one is made on the fixed-order FP64 value (q_exact).
-struct ColumnQ {
-    F2 t, g33, g13, g23;
-    float fh, fk;
-    __device__ ColumnQ(const Geo& g, int h, int k)
-    {
-        fh = (float)h;
-        fk = (float)k;
-        const F2 G11{g.gf[0], g.gl[0]}, G22{g.gf[1], g.gl[1]}, G12{2.f * g.gf[3], 2.f * g.gl[3]};
-        t = f2_add(f2_add(f2_mul_int(G11, (float)(h * h)), f2_mul_int(G22, (float)(k * k))),
-                   f2_mul_int(G12, (float)(h * k)));
-        g33 = F2{g.gf[2], g.gl[2]};
-        g13 = F2{2.f * g.gf[4], 2.f * g.gl[4]};
-        g23 = F2{2.f * g.gf[5], 2.f * g.gl[5]};
-    }
-    __device__ __forceinline__ double at(int l) const
-    {
-        const float fl = (float)l;
-        const F2 v = f2_add(f2_add(t, f2_mul_int(g33, fl * fl)),
-                            f2_add(f2_mul_int(g13, fh * fl), f2_mul_int(g23, fk * fl)));
-        return f2d_fast(v.hi) + f2d_fast(v.lo);
-    }
-};
+__device__ __noinline__ int q_side_exact(const double* gs, int h, int k, int l, double r);
 
-// Inside test of one (h, k, l): an FP32 evaluation decides every candidate
-// farther than a bound on its rounding error from the sphere surfaces; the rest
-// take the exact FP64 test. Returns 1 (inside), 0 (outside).
-__device__ __forceinline__ int inside(const Geo& g, int h, int k, int l, double r2min, double r2max, float r2minf,
-                                      float r2maxf)
+// Side of |g|^2 against a squared radius r for one (h, k, l): an FP32
+// evaluation decides every candidate farther from r than a bound on its
+// rounding error; the rest compare the fixed-order FP64 value (q_exact).
+// Returns -1 (|g|^2 < r), 0 (equal) or 1 (|g|^2 > r).
+__device__ __forceinline__ int q_side(const Geo& g, const double* gsg, int h, int k, int l, double r, float rf)
 {
     const float* gf = g.gf;
     const float hh = (float)(h * h), kk = (float)(k * k), ll = (float)(l * l);
@@ -342,167 +317,437 @@ __device__ __forceinline__ int inside(const Geo& g, int h, int k, int l, double 
     const float qf = fmaf(2.f, o1 + o2 + o3, diag);
     const float qa = fmaf(2.f, fabsf(o1) + fabsf(o2) + fabsf(o3), diag);
     const float m = 4e-6f * qa + 1e-30f;
-    if (qf > r2maxf + m || qf < r2minf - m) return 0;
-    if (qf < r2maxf - m && qf > r2minf + m) return 1;
-    const double q = q_exact(g.gs, h, k, l);
-    return (q >= r2min && q <= r2max) ? 1 : 0;
+    if (qf > rf + m) return 1;
+    if (qf < rf - m) return -1;
+    return q_side_exact(gsg, h, k, l, r);
+}
+
+// The reflections of column (h, k) are the l of [a, b] outside [c, d] (c > d:
+// the column misses the inner sphere). Along a column |g|^2 is a convex
+// quadratic in l; its second difference 2 G*33 exceeds the rounding error of the
+// fixed-order FP64 value by many orders of magnitude, so the l that pass the
+// per-reflection test r2min <= |g|^2 <= r2max are exactly an interval minus an
+// inner interval. Their ends are found by testing l inward from the FP32
+// superset bounds of column_range, a few tests per column instead of one per l.
+struct ColSpan {
+    int a, b, c, d;
+    __device__ int count() const { return a > b ? 0 : (b - a + 1) - (c <= d ? d - c + 1 : 0); }
+    __device__ int first_part() const { return a > b ? 0 : (c <= d ? c - a : b - a + 1); }  // l in [a, c)
+};
+
+__device__ __forceinline__ ColSpan column_span(const Geo& g, const double* gsg, int h, int k, double r2min,
+                                               double r2max, float r2minf, float r2maxf)
+{
+    ColSpan sp{1, 0, 1, 0};
+    int lo, hi;
+    column_range(g.gf, g.L, h, k, r2maxf, lo, hi);
+    while (lo <= hi && q_side(g, gsg, h, k, lo, r2max, r2maxf) > 0) lo++;
+    while (hi > lo && q_side(g, gsg, h, k, hi, r2max, r2maxf) > 0) hi--;
+    if (lo > hi) return sp;
+    sp.a = lo;
+    sp.b = hi;
+    if (r2min > 0.0) {
+        int c0, d0;
+        column_range(g.gf, g.L, h, k, r2minf, c0, d0);
+        c0 = max(c0, lo);
+        d0 = min(d0, hi);
+        while (c0 <= d0 && q_side(g, gsg, h, k, c0, r2min, r2minf) >= 0) c0++;
+        while (d0 > c0 && q_side(g, gsg, h, k, d0, r2min, r2minf) >= 0) d0--;
+        if (c0 <= d0) {
+            sp.c = c0;
+            sp.d = d0;
+        }
+    }
+    return sp;
+}
+
+// Columns of the half-space (h > 0, or h = 0 and k >= 0) in their emission
+// order: h ascending, then k ascending; l ascending within a column.
+__device__ __forceinline__ int n_columns(const Geo& g)
+{
+    return (g.status == XRD_OK && g.H >= 0) ? (g.K + 1) + g.H * (2 * g.K + 1) : 0;
+}
+__device__ __forceinline__ void column_hk(const Geo& g, int c, int& h, int& k)
+{
+    if (c <= g.K) {
+        h = 0;
+        k = c;
+        return;
+    }
+    const int nk = 2 * g.K + 1, r = c - (g.K + 1);
+    h = 1 + r / nk;
+    k = r % nk - g.K;
 }
 
 // Runs: the structure-factor kernel gives each lane a run of at most rb
 // reflections that are consecutive in l within one column, so that it can step
 // the phase factor exp(2 pi i g.x) from l to l + 1 by one complex rotation.
-// A run starts at a column's first reflection, after a gap in l (the inner
-// sphere), or after rb reflections. Run entries: (first reflection within the
-// structure) << 3 | length.
-struct RunState {
-    int len = 0;      // reflections in the open run (0: none)
-    int start = 0;    // its first reflection
-    int prev_l = 0;   // l of the last reflection
-};
+// Each of a column's (at most two) contiguous parts is cut into runs of rb
+// from its first l, the last one shorter. Run entries: (first reflection
+// within the structure) << 3 | length.
+__device__ __forceinline__ int runs_of(int n, int rb) { return (n + rb - 1) / rb; }
 
-// Count (EMIT = false) or write (EMIT = true) the reflections of one structure
-// (and, with rb > 0, its runs). Each thread takes columns (h, k) in a strided
-// order; when emitting, block scans of the per-thread counts give every thread
-// fixed output ranges, so the emitted order is deterministic and no atomics are
-// needed. The counting pass (k_count) keeps each thread's counts, so the
-// emitting pass (k_emit, same block size and column order) skips the recount.
-template <bool EMIT, bool RUNS>
-__device__ void enumerate_struct(const Geo& g, double r2min, double r2max, float r2minf, float r2maxf, int rb,
-                                 int64_t base, int64_t cap, double* __restrict__ qo, uint32_t* __restrict__ ko,
-                                 int* __restrict__ runo, int* tmp, int& local, int& local_runs)
+// Exclusive block scan of one (x, y) pair per thread, with the block totals.
+// tmp: 66 ints of shared memory; the caller synchronises before reusing it.
+__device__ __forceinline__ void block_scan_pair(int x, int y, int* tmp, int& ex, int& ey, int& tx, int& ty)
 {
-    const int nk = 2 * g.K + 1;
-    const int ncol = (g.H + 1) * nk;
-    if (!EMIT) {
-        local = 0;
-        local_runs = 0;
-        for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
-            const int h = c / nk, k = c % nk - g.K;
-            if (h == 0 && k < 0) continue;  // half-space: h > 0, or h = 0 and k >= 0
-            int lo, hi;
-            column_range(g.gf, g.L, h, k, r2maxf, lo, hi);
-            int rl = 0, pl = lo - 2;
-            for (int l = lo; l <= hi; l++) {
-                if (!inside(g, h, k, l, r2min, r2max, r2minf, r2maxf)) continue;
-                local++;
-                if (RUNS) {
-                    if (rl == 0 || l != pl + 1 || rl == rb) {
-                        local_runs++;
-                        rl = 0;
-                    }
-                    rl++;
-                    pl = l;
-                }
+    const int nw = blockDim.x >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ix = warp_incl_scan(x), iy = warp_incl_scan(y);
+    if (lane == 31) {
+        tmp[w] = ix;
+        tmp[33 + w] = iy;
+    }
+    __syncthreads();
+    if (w == 0) {
+        const int sx = lane < nw ? tmp[lane] : 0, sy = lane < nw ? tmp[33 + lane] : 0;
+        const int px = warp_incl_scan(sx), py = warp_incl_scan(sy);
+        if (lane < nw) {
+            tmp[lane] = px - sx;
+            tmp[33 + lane] = py - sy;
+        }
+        if (lane == 31) {
+            tmp[32] = px;
+            tmp[65] = py;
+        }
+    }
+    __syncthreads();
+    ex = tmp[w] + ix - x;
+    ey = tmp[33 + w] + iy - y;
+    tx = tmp[32];
+    ty = tmp[65];
+}
+
+// Launch shapes of counting and emission (enum_threads): with 64, 128 or 256
+// threads per CTA every warp takes one structure at a time, claimed from a
+// counter, so the fixed cost of a structure (the loads of its cell, the
+// scans) is a warp's, not a CTA's, and a small structure's columns fill a
+// warp's lanes; with 512 or 1024 threads every structure has a CTA of its own
+// (batches of large cells).
+constexpr int kEnumMaxThreads = 1024;
+constexpr int kWarpModeMaxThreads = 256;
+constexpr int kWarpRecInts = 2 * 33 + 8 * 32;  // one warp's chunk of 32 column records
+
+__host__ __device__ inline bool enum_per_warp(int threads) { return threads <= kWarpModeMaxThreads; }
+__host__ __device__ inline int enum_cta_ints(int threads) { return 2 * (threads + 1) + 8 * threads; }
+size_t enum_smem_bytes(int threads)
+{
+    return 4 * ((enum_per_warp(threads) ? (threads / 32) * kWarpRecInts : 0) + enum_cta_ints(threads));
+}
+
+// The exact comparison of a candidate within the FP32 error bound of a sphere
+// surface, kept out of line so that the rare FP64 evaluation is a branch, not
+// work that every caller does.
+__device__ __noinline__ int q_side_exact(const double* gs, int h, int k, int l, double r)
+{
+    const double q = q_exact(gs, h, k, l);
+    return q > r ? 1 : (q < r ? -1 : 0);
+}
+
+// Reflections and runs of column c.
+__device__ __forceinline__ ColSpan column_counts(const Geo& g, const double* gsg, int c, double r2min, double r2max,
+                                                 float r2minf, float r2maxf, int rb, bool runs, int& h, int& k, int& n,
+                                                 int& nr)
+{
+    column_hk(g, c, h, k);
+    const ColSpan sp = column_span(g, gsg, h, k, r2min, r2max, r2minf, r2maxf);
+    n = sp.count();
+    nr = 0;
+    if (runs) {
+        const int n1 = sp.first_part();
+        nr = runs_of(n1, rb) + runs_of(n - n1, rb);
+    }
+    return sp;
+}
+
+__device__ __forceinline__ int warp_sum_int(int v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Reflection (and, with rb > 0, run) counts per structure. With one warp per
+// structure the warps claim structures from a counter (ctr, zero at launch),
+// so a CTA is not held by its slowest structure; every structure, however
+// many columns it has, is counted by one warp.
+template <bool RUNS>
+__global__ void __launch_bounds__(kEnumMaxThreads) k_count(const Geo* __restrict__ geo, int n_struct, double r2min,
+                                                           double r2max, float r2minf, float r2maxf, int rb,
+                                                           int64_t* __restrict__ cnt, int64_t* __restrict__ run_cnt,
+                                                           int* __restrict__ ctr)
+{
+    pdl_enter();
+    __shared__ int tmp[66];
+    const int nt = blockDim.x, lane = threadIdx.x & 31;
+    if (enum_per_warp(nt)) {
+        for (;;) {
+            int s = 0;
+            if (lane == 0) s = atomicAdd(ctr, 1);
+            s = __shfl_sync(0xffffffffu, s, 0);
+            if (s >= n_struct) break;
+            const Geo g = geo[s];
+            const int ncol = n_columns(g);
+            int local = 0, local_runs = 0;
+            for (int c = lane; c < ncol; c += 32) {
+                int h, k, m, mr;
+                column_counts(g, geo[s].gs, c, r2min, r2max, r2minf, r2maxf, rb, RUNS, h, k, m, mr);
+                local += m;
+                local_runs += mr;
+            }
+            local = warp_sum_int(local);
+            if (RUNS) local_runs = warp_sum_int(local_runs);
+            if (lane == 0) {
+                cnt[s] = local;
+                if (RUNS && run_cnt) run_cnt[s] = local_runs;
             }
         }
         return;
     }
-    // exclusive offsets of this thread's reflections and runs within the structure
-    const int nw = blockDim.x >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int inc = warp_incl_scan(local), incr = warp_incl_scan(local_runs);
-    if (lane == 31) {
-        tmp[w] = inc;
-        tmp[33 + w] = incr;
-    }
-    __syncthreads();
-    if (w == 0) {
-        const int sv = lane < nw ? tmp[lane] : 0, sr = lane < nw ? tmp[33 + lane] : 0;
-        const int si = warp_incl_scan(sv), sj = warp_incl_scan(sr);
-        if (lane < nw) {
-            tmp[lane] = si - sv;
-            tmp[33 + lane] = sj - sr;
-        }
-    }
-    __syncthreads();
-    int pos = tmp[w] + inc - local;
-    int rpos = tmp[33 + w] + incr - local_runs;
-    for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
-        const int h = c / nk, k = c % nk - g.K;
-        if (h == 0 && k < 0) continue;
-        int lo, hi;
-        column_range(g.gf, g.L, h, k, r2maxf, lo, hi);
-        const ColumnQ cq(g, h, k);
-        RunState run;
-        for (int l = lo; l <= hi; l++) {
-            if (!inside(g, h, k, l, r2min, r2max, r2minf, r2maxf)) continue;
-            if (RUNS && (run.len == 0 || l != run.prev_l + 1 || run.len == rb)) {
-                if (run.len > 0 && rpos < cap) runo[base + rpos] = (run.start << 3) | run.len;
-                if (run.len > 0) rpos++;
-                run.start = pos;
-                run.len = 0;
-            }
-            if (RUNS) {
-                run.len++;
-                run.prev_l = l;
-            }
-            if (pos < cap) {
-                qo[base + pos] = cq.at(l);
-                ko[base + pos] = hkl_pack(h, k, l);
-            }
-            pos++;
-        }
-        if (RUNS && run.len > 0) {
-            if (rpos < cap) runo[base + rpos] = (run.start << 3) | run.len;
-            rpos++;
-        }
-    }
-}
-
-template <bool RUNS>
-__global__ void __launch_bounds__(256) k_count(const Geo* __restrict__ geo, double r2min, double r2max,
-                                               float r2minf, float r2maxf, int rb, int64_t* __restrict__ cnt,
-                                               int64_t* __restrict__ run_cnt, int* __restrict__ tcnt)
-{
-    pdl_enter();
-    __shared__ int tmp[34];
-    const int s = blockIdx.x;
-    const Geo g = geo[s];
+    const int sb = blockIdx.x;  // one CTA per structure
+    if (sb >= n_struct) return;
+    const Geo g = geo[sb];
+    const int ncol = n_columns(g);
     int local = 0, local_runs = 0;
-    if (g.status == XRD_OK && g.H >= 0)
-        enumerate_struct<false, RUNS>(g, r2min, r2max, r2minf, r2maxf, rb, 0, 0, nullptr, nullptr, nullptr, tmp,
-                                      local, local_runs);
-    if (tcnt) {
-        tcnt[(int64_t)s * 2 * blockDim.x + threadIdx.x] = local;
-        if (RUNS) tcnt[(int64_t)s * 2 * blockDim.x + blockDim.x + threadIdx.x] = local_runs;
+    for (int c = threadIdx.x; c < ncol; c += nt) {
+        int h, k, m, mr;
+        column_counts(g, geo[sb].gs, c, r2min, r2max, r2minf, r2maxf, rb, RUNS, h, k, m, mr);
+        local += m;
+        local_runs += mr;
     }
-    const int n = block_sum_int(local, tmp);
-    if (threadIdx.x == 0) cnt[s] = n;
-    if (RUNS && run_cnt) {
-        __syncthreads();
-        const int nr = block_sum_int(local_runs, tmp);
-        if (threadIdx.x == 0) run_cnt[s] = nr;
+    int ex, ey, tx, ty;
+    block_scan_pair(local, local_runs, tmp, ex, ey, tx, ty);
+    if (threadIdx.x == 0) {
+        cnt[sb] = tx;
+        if (RUNS && run_cnt) run_cnt[sb] = ty;
     }
 }
 
-// Also writes the structure's runs (rb > 0) and its entries of the
-// structure-factor tile table from tile_off[s]: (s, first run) of each tile of
-// 32 runs, or (s, first reflection) of each tile of tile_refl reflections.
+// Column records of one chunk of columns, for the flat emission: offsets, the
+// l interval and gap, (h, k), and the column's |g|^2 as a polynomial in l,
+// q(l) = t + u l + G*33 l^2 with t = G*11 h^2 + G*22 k^2 + 2 G*12 hk and
+// u = 2 G*13 h + 2 G*23 k in two-float arithmetic (about 1e-14 relative).
+struct ChunkCols {
+    int* off;   // [m + 1] exclusive reflection offsets within the chunk
+    int* roff;  // [m + 1] exclusive run offsets
+    int* a;     // first l
+    int* c;     // first l of the inner gap (INT_MAX: none)
+    int* gap;   // its length
+    int* hk;    // (h << 16) | (k & 0xffff)
+    float *th, *tl, *uh, *ul;
+};
+
+__device__ __forceinline__ ChunkCols chunk_cols(int* b, int m)
+{
+    ChunkCols cc;
+    cc.off = b;
+    cc.roff = b + (m + 1);
+    int* r = b + 2 * (m + 1);
+    cc.a = r;
+    cc.c = r + m;
+    cc.gap = r + 2 * m;
+    cc.hk = r + 3 * m;
+    cc.th = (float*)(r + 4 * m);
+    cc.tl = (float*)(r + 5 * m);
+    cc.uh = (float*)(r + 6 * m);
+    cc.ul = (float*)(r + 7 * m);
+    return cc;
+}
+
+__device__ __forceinline__ void put_col(const ChunkCols& cc, int i, const Geo& g, const ColSpan& sp, int h, int k)
+{
+    cc.a[i] = sp.a;
+    cc.c[i] = sp.c <= sp.d ? sp.c : INT_MAX;
+    cc.gap[i] = sp.c <= sp.d ? sp.d - sp.c + 1 : 0;
+    cc.hk[i] = (h << 16) | (k & 0xffff);
+    const F2 G11{g.gf[0], g.gl[0]}, G22{g.gf[1], g.gl[1]}, G12{2.f * g.gf[3], 2.f * g.gl[3]};
+    const F2 G13{2.f * g.gf[4], 2.f * g.gl[4]}, G23{2.f * g.gf[5], 2.f * g.gl[5]};
+    const F2 t = f2_add(f2_add(f2_mul_int(G11, (float)(h * h)), f2_mul_int(G22, (float)(k * k))),
+                        f2_mul_int(G12, (float)(h * k)));
+    const F2 u = f2_add(f2_mul_int(G13, (float)h), f2_mul_int(G23, (float)k));
+    cc.th[i] = t.hi;
+    cc.tl[i] = t.lo;
+    cc.uh[i] = u.hi;
+    cc.ul[i] = u.lo;
+}
+
+// Writes the chunk's reflections (and runs): thread t of nt takes positions t,
+// t + nt, ...; each finds its column by bisection over the m offsets, so the
+// writes of consecutive threads are consecutive.
 template <bool RUNS>
-__global__ void __launch_bounds__(256) k_emit(const Geo* __restrict__ geo, double r2min, double r2max,
-                                              float r2minf, float r2maxf, int rb, int tile_refl,
-                                              const int64_t* __restrict__ refl_off,
-                                              const int64_t* __restrict__ run_cnt, const int* __restrict__ tcnt,
-                                              const int* __restrict__ abort_flag, double* __restrict__ q,
-                                              uint32_t* __restrict__ key, int* __restrict__ runs,
-                                              const int* __restrict__ tile_off, int2* __restrict__ tile_tab)
+__device__ __forceinline__ void emit_chunk(const F2 g33, const ChunkCols& cc, int m, int tot, int rtot, int t, int nt,
+                                           int rb, int64_t base, int64_t cap, int done, int done_runs,
+                                           double* __restrict__ q, uint32_t* __restrict__ key, int* __restrict__ runs)
+{
+    for (int p = t; p < tot; p += nt) {
+        int lo = 0, hi = m - 1;  // last column with off <= p
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (cc.off[mid] <= p) lo = mid;
+            else hi = mid - 1;
+        }
+        const int hk = cc.hk[lo];
+        int l = cc.a[lo] + (p - cc.off[lo]);
+        if (l >= cc.c[lo]) l += cc.gap[lo];
+        const int64_t pos = done + p;
+        if (pos < cap) {
+            const float fl = (float)l;
+            const F2 v = f2_add(f2_add(F2{cc.th[lo], cc.tl[lo]}, f2_mul_int(g33, fl * fl)),
+                                f2_mul_int(F2{cc.uh[lo], cc.ul[lo]}, fl));
+            q[base + pos] = f2d_fast(v.hi) + f2d_fast(v.lo);
+            key[base + pos] = hkl_pack(hk >> 16, (int)(short)(hk & 0xffff), l);
+        }
+    }
+    if (RUNS) {
+        for (int p = t; p < rtot; p += nt) {
+            int lo = 0, hi = m - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (cc.roff[mid] <= p) lo = mid;
+                else hi = mid - 1;
+            }
+            const int n = cc.off[lo + 1] - cc.off[lo];
+            const int n1 = cc.gap[lo] > 0 ? cc.c[lo] - cc.a[lo] : n;
+            const int j = p - cc.roff[lo], r1 = runs_of(n1, rb);
+            const int first = j < r1 ? j * rb : n1 + (j - r1) * rb;
+            const int len = j < r1 ? min(rb, n1 - j * rb) : min(rb, n - n1 - (j - r1) * rb);
+            const int64_t rpos = done_runs + p;
+            if (rpos < cap) runs[base + rpos] = ((done + cc.off[lo] + first) << 3) | len;
+        }
+    }
+}
+
+// The structure's entries of the structure-factor tile table from tile_off[s]:
+// (s, first run) of each tile of 32 runs (rb > 0), or (s, first reflection)
+// of each tile of tile_refl reflections.
+__device__ __forceinline__ void write_tiles(int s, int rb, int tile_refl, int64_t units, const int* __restrict__ tile_off,
+                                            int2* __restrict__ tile_tab, int t, int nt)
+{
+    const int per = rb > 0 ? kRunsPerTile : tile_refl;
+    const int ntl = (int)((units + per - 1) / per), t0 = tile_off[s];
+    for (int i = t; i < ntl; i += nt) tile_tab[t0 + i] = make_int2(s, i * per);
+}
+
+// Writes |g|^2 and the packed (h, k, l) of every reflection of each structure
+// (and its runs, rb > 0) from refl_off[s], and its tile-table entries. The
+// columns are taken 32 (one warp) or blockDim (the CTA) at a time: each thread
+// finds its column's span, a scan places the columns, and the warp or CTA then
+// writes the chunk's reflections and runs as one flat, coalesced range. The
+// output order is the column order above, l ascending, whatever the launch shape.
+// With one warp per structure the warps claim structures from ctr[0]; given the
+// post-processing size-class lists (cls_list, cls_cnt), the structures above
+// kPostCap3 reflections (the two largest classes) are left to whole CTAs,
+// which claim them from ctr[1] once the warps are done. ctr: zero at launch.
+// Dynamic shared memory: enum_smem_bytes(blockDim).
+template <bool RUNS>
+__global__ void __launch_bounds__(kEnumMaxThreads) k_emit(const Geo* __restrict__ geo, int n_struct, double r2min,
+                                                          double r2max, float r2minf, float r2maxf, int rb,
+                                                          int tile_refl, const int64_t* __restrict__ refl_off,
+                                                          const int64_t* __restrict__ run_cnt,
+                                                          const int* __restrict__ abort_flag, double* __restrict__ q,
+                                                          uint32_t* __restrict__ key, int* __restrict__ runs,
+                                                          const int* __restrict__ tile_off, int2* __restrict__ tile_tab,
+                                                          int* __restrict__ ctr, const int* __restrict__ cls_list,
+                                                          const int* __restrict__ cls_cnt)
 {
     pdl_enter();
+    extern __shared__ int esm[];
     __shared__ int tmp[66];
+    __shared__ int s_big;
     if (*abort_flag) return;
-    const int s = blockIdx.x;
-    const Geo g = geo[s];
-    const int64_t base = refl_off[s], cap = refl_off[s + 1] - base;
-    if (tile_tab) {  // rb > 0: tiles of 32 runs; otherwise tiles of tile_refl reflections
-        const int per = rb > 0 ? kRunsPerTile : tile_refl;
-        const int64_t units = rb > 0 ? run_cnt[s] : cap;
-        const int nt = (int)((units + per - 1) / per), t0 = tile_off[s];
-        for (int t = threadIdx.x; t < nt; t += blockDim.x) tile_tab[t0 + t] = make_int2(s, t * per);
+    const int nt = blockDim.x, t = threadIdx.x;
+    const bool per_warp = enum_per_warp(nt);
+    const int w = t >> 5, lane = t & 31;
+    const int64_t big_min = cls_list ? kPostCap3 : INT64_MAX;
+    int nbig = 0;
+    if (per_warp) {
+        const ChunkCols cc = chunk_cols(esm + enum_cta_ints(nt) + w * kWarpRecInts, 32);
+        for (;;) {
+            int s = 0;
+            if (lane == 0) s = atomicAdd(ctr, 1);
+            s = __shfl_sync(0xffffffffu, s, 0);
+            if (s >= n_struct) break;
+            const int64_t base = refl_off[s], cap = refl_off[s + 1] - base;
+            if (tile_tab) write_tiles(s, rb, tile_refl, rb > 0 ? run_cnt[s] : cap, tile_off, tile_tab, lane, 32);
+            if (cap <= 0 || cap > big_min) continue;
+            const Geo g = geo[s];
+            const F2 g33{g.gf[2], g.gl[2]};
+            const int ncol = n_columns(g);
+            int done = 0, done_runs = 0;
+            for (int c0 = 0; c0 < ncol; c0 += 32) {
+                const int c = c0 + lane;
+                int m = 0, mr = 0;
+                if (c < ncol) {
+                    int h, k;
+                    const ColSpan sp =
+                        column_counts(g, geo[s].gs, c, r2min, r2max, r2minf, r2maxf, rb, RUNS, h, k, m, mr);
+                    put_col(cc, lane, g, sp, h, k);
+                }
+                const int im = warp_incl_scan(m), imr = RUNS ? warp_incl_scan(mr) : 0;
+                cc.off[lane] = im - m;
+                if (RUNS) cc.roff[lane] = imr - mr;
+                const int tot = __shfl_sync(0xffffffffu, im, 31);
+                const int rtot = RUNS ? __shfl_sync(0xffffffffu, imr, 31) : 0;
+                if (lane == 0) {
+                    cc.off[32] = tot;
+                    cc.roff[32] = rtot;
+                }
+                __syncwarp();
+                emit_chunk<RUNS>(g33, cc, 32, tot, rtot, lane, 32, rb, base, cap, done, done_runs, q, key, runs);
+                done += tot;
+                done_runs += rtot;
+                __syncwarp();  // the records are read before the next chunk rewrites them
+            }
+        }
+        if (!cls_list) return;
+        nbig = cls_cnt[4] + cls_cnt[5];
+        if (nbig == 0) return;
     }
-    if (g.status == XRD_OK && g.H >= 0 && cap > 0) {
-        int local = tcnt[(int64_t)s * 2 * blockDim.x + threadIdx.x];
-        int local_runs = RUNS ? tcnt[(int64_t)s * 2 * blockDim.x + blockDim.x + threadIdx.x] : 0;
-        enumerate_struct<true, RUNS>(g, r2min, r2max, r2minf, r2maxf, rb, base, cap, q, key, runs, tmp, local,
-                                     local_runs);
+    const ChunkCols cc = chunk_cols(esm, nt);
+    for (int it = 0;; it++) {  // the structures taken by the whole CTA
+        int sb;
+        if (per_warp) {
+            __syncthreads();  // s_big and the chunk records are free
+            if (t == 0) s_big = atomicAdd(ctr + 1, 1);
+            __syncthreads();
+            const int j = s_big;
+            if (j >= nbig) break;
+            const int n5 = cls_cnt[5];  // the largest class first
+            sb = j < n5 ? cls_list[(int64_t)5 * n_struct + j] : cls_list[(int64_t)4 * n_struct + (j - n5)];
+        } else {
+            if (it > 0) break;
+            sb = blockIdx.x;  // one CTA per structure
+            if (sb >= n_struct) break;
+        }
+        const int64_t base = refl_off[sb], capb = refl_off[sb + 1] - base;
+        if (!per_warp && tile_tab) write_tiles(sb, rb, tile_refl, rb > 0 ? run_cnt[sb] : capb, tile_off, tile_tab, t, nt);
+        if (capb <= 0) continue;
+        const Geo g = geo[sb];
+        const F2 g33{g.gf[2], g.gl[2]};
+        const int ncol = n_columns(g);
+        int done = 0, done_runs = 0;
+        for (int c0 = 0; c0 < ncol; c0 += nt) {
+            const int c = c0 + t;
+            int m = 0, mr = 0;
+            if (c < ncol) {
+                int h, k;
+                const ColSpan sp =
+                    column_counts(g, geo[sb].gs, c, r2min, r2max, r2minf, r2maxf, rb, RUNS, h, k, m, mr);
+                put_col(cc, t, g, sp, h, k);
+            }
+            int ex, ey, tx, ty;
+            block_scan_pair(m, mr, tmp, ex, ey, tx, ty);
+            cc.off[t] = ex;
+            cc.roff[t] = ey;
+            if (t == 0) {
+                cc.off[nt] = tx;
+                cc.roff[nt] = ty;
+            }
+            __syncthreads();
+            emit_chunk<RUNS>(g33, cc, nt, tx, ty, t, nt, rb, base, capb, done, done_runs, q, key, runs);
+            done += tx;
+            done_runs += ty;
+            __syncthreads();  // the chunk's records are read; the next chunk rewrites them
+        }
     }
 }
 
@@ -817,6 +1062,66 @@ __global__ void __launch_bounds__(kScanThreads) k_order(const int64_t* __restric
     }
 }
 
+// Multi-block form of the same order (more than two chunks of kScanItems *
+// kScanThreads structures). k_order_parts histograms each chunk into
+// oparts[chunk][bin]; k_order_final starts each bin of a chunk after all
+// structures of the earlier bins and those of the same bin in earlier chunks,
+// then scatters the chunk as k_order does.
+__global__ void __launch_bounds__(kScanThreads) k_order_parts(const int64_t* __restrict__ atom_off, int n,
+                                                              int* __restrict__ oparts)
+{
+    pdl_enter();
+    __shared__ int bins[kOrderBins];
+    const int nt = blockDim.x, tid = threadIdx.x, base = blockIdx.x * kScanItems * nt;
+    for (int b = tid; b < kOrderBins; b += nt) bins[b] = 0;
+    __syncthreads();
+    int b[kScanItems];
+#pragma unroll
+    for (int u = 0; u < kScanItems; u++) {
+        const int i = base + u * nt + tid;
+        b[u] = i < n ? order_bin(atom_off, i) : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < kScanItems; u++) warp_aggregated_slot(bins, b[u], base + u * nt + tid < n);
+    __syncthreads();
+    for (int j = tid; j < kOrderBins; j += nt) oparts[(size_t)blockIdx.x * kOrderBins + j] = bins[j];
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_order_final(const int64_t* __restrict__ atom_off, int n,
+                                                              const int* __restrict__ oparts, int* __restrict__ order)
+{
+    pdl_enter();
+    __shared__ int bins[kOrderBins], before[kOrderBins];
+    __shared__ int tmp[66];
+    const int nt = blockDim.x, tid = threadIdx.x, ch = blockIdx.x, nch = gridDim.x, base = ch * kScanItems * nt;
+    for (int j = tid; j < kOrderBins; j += nt) {
+        int tot = 0, bef = 0;
+        for (int c = 0; c < nch; c++) {
+            const int v = oparts[(size_t)c * kOrderBins + j];
+            tot += v;
+            bef += c < ch ? v : 0;
+        }
+        bins[j] = tot;
+        before[j] = bef;
+    }
+    __syncthreads();
+    block_excl_scan(bins, kOrderBins, tmp);
+    for (int j = tid; j < kOrderBins; j += nt) bins[j] += before[j];
+    __syncthreads();
+    int b[kScanItems];
+#pragma unroll
+    for (int u = 0; u < kScanItems; u++) {
+        const int i = base + u * nt + tid;
+        b[u] = i < n ? order_bin(atom_off, i) : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < kScanItems; u++) {
+        const int i = base + u * nt + tid;
+        const int slot = warp_aggregated_slot(bins, b[u], i < n);
+        if (i < n) order[slot] = i;
+    }
+}
+
 template <typename... P, typename... A>
 static void launch_k(bool pdl, void (*k)(P...), dim3 grid, dim3 block, cudaStream_t st, A... args)
 {
@@ -895,7 +1200,20 @@ void launch_atoms(const GeomArgs& a, cudaStream_t st, bool pdl)
 
 void launch_order(const GeomArgs& a, cudaStream_t st, bool pdl)
 {
-    if (a.n_struct > 0) launch_k(pdl, k_order, 1, kScanThreads, st, a.atom_off, a.n_struct, a.order);
+    if (a.n_struct <= 0) return;
+    const int nch = (a.n_struct + kScanItems * kScanThreads - 1) / (kScanItems * kScanThreads);
+    if (nch <= 2 || !a.oparts) {
+        launch_k(pdl, k_order, 1, kScanThreads, st, a.atom_off, a.n_struct, a.order);
+        return;
+    }
+    launch_k(pdl, k_order_parts, nch, kScanThreads, st, a.atom_off, a.n_struct, a.oparts);
+    launch_k(true, k_order_final, nch, kScanThreads, st, a.atom_off, a.n_struct, (const int*)a.oparts, a.order);
+}
+
+size_t order_parts_bytes(int64_t n)
+{
+    const int64_t nch = (n + kScanItems * kScanThreads - 1) / (kScanItems * kScanThreads);
+    return nch > 2 ? (size_t)4 * kOrderBins * nch : 0;
 }
 
 void launch_count_only(const GeomArgs& a, cudaStream_t st)
@@ -903,16 +1221,22 @@ void launch_count_only(const GeomArgs& a, cudaStream_t st)
     const int n = a.n_struct;
     if (n <= 0) return;
     prep_launch(false, a.lattice, n, a.rmax, a.geo, (unsigned*)nullptr, (int32_t*)nullptr, st);
-    launch_pdl(k_count<false>, n, 256, 0, st, a.geo, a.r2min, a.r2max, (float)a.r2min, (float)a.r2max, 0,
-               a.refl_cnt, (int64_t*)nullptr, (int*)nullptr);
+    launch_pdl(k_count<false>, (n + 7) / 8, 256, 0, st, a.geo, n, a.r2min,
+               a.r2max, (float)a.r2min, (float)a.r2max, 0, a.refl_cnt, (int64_t*)nullptr, a.enum_ctr);
+}
+
+static int enum_grid(const GeomArgs& a)
+{
+    const int per = enum_per_warp(a.enum_threads) ? a.enum_threads / 32 : 1;  // structures per CTA
+    return (a.n_struct + per - 1) / per;
 }
 
 void launch_count(const GeomArgs& a, cudaStream_t st, bool pdl)
 {
     if (a.n_struct > 0)
-        launch_k(pdl, a.runs_mode ? k_count<true> : k_count<false>, a.n_struct, a.enum_threads, st, a.geo, a.r2min,
-                 a.r2max,
-                 (float)a.r2min, (float)a.r2max, a.runs_mode ? a.rb : 0, a.refl_cnt, a.run_cnt, a.tcnt);
+        launch_k(pdl, a.runs_mode ? k_count<true> : k_count<false>, enum_grid(a), a.enum_threads, st, a.geo,
+                 a.n_struct, a.r2min, a.r2max,
+                 (float)a.r2min, (float)a.r2max, a.runs_mode ? a.rb : 0, a.refl_cnt, a.run_cnt, a.enum_ctr);
 }
 
 int scan_chunks(int n) { return (n + kScanItems * kScanThreads - 1) / (kScanItems * kScanThreads); }
@@ -936,13 +1260,20 @@ void launch_scan_refl(const GeomArgs& a, cudaStream_t st, bool pdl)
 
 void launch_emit(const GeomArgs& a, cudaStream_t st, bool pdl)
 {
-    if (a.n_struct > 0)
-        launch_k(pdl, a.runs_mode ? k_emit<true> : k_emit<false>, a.n_struct, a.enum_threads, st, a.geo, a.r2min,
-                 a.r2max,
-                 (float)a.r2min, (float)a.r2max,
-                 a.runs_mode ? a.rb : 0, 32 * a.rb,
-                 (const int64_t*)a.refl_off, (const int64_t*)a.run_cnt, (const int*)a.tcnt, (const int*)a.abort_flag,
-                 a.q, a.key, a.runs, (const int*)a.tile_off, a.tile_tab);
+    if (a.n_struct <= 0) return;
+    auto k = a.runs_mode ? k_emit<true> : k_emit<false>;
+    const size_t smem = enum_smem_bytes(a.enum_threads);
+    if (pdl)
+        launch_pdl(k, enum_grid(a), a.enum_threads, smem, st, a.geo, a.n_struct, a.r2min, a.r2max, (float)a.r2min,
+                   (float)a.r2max, a.runs_mode ? a.rb : 0, 32 * a.rb, (const int64_t*)a.refl_off,
+                   (const int64_t*)a.run_cnt, (const int*)a.abort_flag, a.q, a.key, a.runs, (const int*)a.tile_off,
+                   a.tile_tab, a.enum_ctr + 1, (const int*)a.cls_list, (const int*)(a.abort_flag + 4));
+    else
+        k<<<enum_grid(a), a.enum_threads, smem, st>>>(a.geo, a.n_struct, a.r2min, a.r2max, (float)a.r2min,
+                                                       (float)a.r2max, a.runs_mode ? a.rb : 0, 32 * a.rb,
+                                                       a.refl_off, a.run_cnt, a.abort_flag, a.q, a.key, a.runs,
+                                                       a.tile_off, a.tile_tab, a.enum_ctr + 1, a.cls_list,
+                                                       a.abort_flag + 4);
 }
 
 }  // namespace xrd

@@ -151,7 +151,10 @@ __device__ void refine_one(const RefineArgs& a, int64_t r, int s, const float4* 
     const double q = a.q[r];
     const uint32_t key = a.key[r];
     const long long h = hkl_h(key), k = hkl_k(key), l = hkl_l(key);
-    const DD s2 = dd_mul_f(dd_from_double(q), 0.25f);  // exact scaling
+    float qh, ql;
+    split_pos(q, qh, ql);                                // |g|^2 as two floats, no FP64 arithmetic
+    const DD qd = dd_fast2sum(qh, ql);
+    const DD s2 = dd_mul_f(qd, 0.25f);  // exact scaling
     const int64_t j0 = a.atom_off[s], j1 = a.atom_off[s + 1];
     DD Fr{0.f, 0.f}, Fi{0.f, 0.f};
     for (int64_t jb = j0; jb < j1; jb += 32) {
@@ -187,11 +190,16 @@ __device__ void refine_one(const RefineArgs& a, int64_t r, int s, const float4* 
         Fi = dd_add(Fi, ti);
     }
     if (lane == 0) {
-        const double fr = dd_to_double(Fr), fi = dd_to_double(Fi);
-        const double X = (a.lambda * a.lambda * 0.25) * q;  // sin^2 theta
-        const double c2 = 1.0 - 2.0 * X;                     // cos 2theta
-        const double lp = (1.0 + c2 * c2) / (X * sqrt(fmax(1.0 - X, kCos90Sq)));
-        a.If[r] = (float)((fr * fr + fi * fi) * lp);
+        // |F|^2 in double-float; LP in FP32 from sin^2 theta = X as two floats, with
+        // cos^2 theta = (1 - Xh) - Xl (1 - Xh exact for Xh >= 1/2): a few ulp whatever 2-theta
+        const DD F2 = dd_add(dd_mul(Fr, Fr), dd_mul(Fi, Fi));
+        const float Xh = qd.hi * a.l2h;
+        const float Xl = fmaf(qd.hi, a.l2h, -Xh) + fmaf(qd.hi, a.l2l, qd.lo * a.l2h);
+        const float X = Xh + Xl;
+        const float u = fmaxf((1.f - Xh) - Xl, (float)kCos90Sq);
+        const float c2 = fmaf(-2.f, X, 1.f);
+        const float lp = fmaf(c2, c2, 1.f) / (X * sqrtf(u));
+        a.If[r] = (F2.hi + F2.lo) * lp;
     }
 }
 
@@ -231,7 +239,6 @@ __global__ void __launch_bounds__(kRefThreads) k_refine_select(const RefineArgs 
     if (c_begin >= c_end) return;
     if (threadIdx.x == 0) s_cur = refl_owner(a.refl_off, 0, n, c_begin * kRefChunk);
     const int lane = threadIdx.x & 31;
-    const float cos90f = (float)kCos90Sq;
     for (int64_t c = c_begin; c < c_end; c++) {
         const int64_t r0 = c * kRefChunk;
         __syncthreads();  // s_cur is set; the previous chunk is done with the window
@@ -267,15 +274,10 @@ __global__ void __launch_bounds__(kRefThreads) k_refine_select(const RefineArgs 
             const int64_t r = rt + u;
             if (r >= total) break;
             while (a.refl_off[s + 1] <= r) s++;  // at most a few steps: four consecutive reflections
-            const float I = a.If[r], A2 = a.W2[r];
-            const float X = d2f_pos(a.q[r]) * a.l2f;
-            const float c2 = fmaf(-2.f, X, 1.f);
-            const float lp = fmaf(c2, c2, 1.f) / (X * sqrtf(fmaxf(1.f - X, cos90f)));
-            const float dF = a.eps_k * sqrtf(A2);
-            const float E = lp * dF * fmaf(2.f, sqrtf(fmaxf(I, 0.f) / lp), dF);
+            const float I = a.If[r], E = a.Eb[r];
             const float floorI = a.cref * __uint_as_float(a.imax[s]);
             const bool bad = a.atom_bad && a.atom_bad[s];
-            if (!bad && A2 > 0.f && E > a.tau * fmaxf(I, floorI)) {
+            if (!bad && E > 0.f && E > a.tau * fmaxf(I, floorI)) {
                 cr[nf] = r;
                 cs[nf] = s;
                 nf++;

@@ -215,13 +215,17 @@ __device__ float sf_tile_fp32(const SfArgs& a, int64_t first, int len, int64_t j
         const int64_t r = first + (int64_t)step * i;
         const float qf = d2f_pos(a.q[r]);
         const float fr = ACC ? Rh[i] + Rl[i] : Fr[i], fi = ACC ? Ih[i] + Il[i] : Fi[i];
-        const float I = fmaf(fr, fr, fi * fi) * lp_of(qf, l2, a.q + r, a.lambda);
+        const float F2 = fmaf(fr, fr, fi * fi), lp = lp_of(qf, l2, a.q + r, a.lambda);
+        const float I = F2 * lp;
         if (GRAD) {
             a.Fx[r] = make_float4(Fr[i], Fi[i], Gr[i], Gi[i]);
             a.Ig[r] = I;
         } else {
             a.If[r] = I;
-            if (a.W2) a.W2[r] = A2[kRotate ? 0 : i];
+            if (ACC && a.Eb) {
+                const float dF = a.eps_k * sqrtf(A2[kRotate ? 0 : i]);
+                a.Eb[r] = lp * dF * fmaf(2.f, sqrtf(F2), dF);
+            }
             if (a.F) a.F[r] = make_float2(fr, fi);
             imax = fmaxf(imax, I);
         }

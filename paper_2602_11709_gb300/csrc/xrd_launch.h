@@ -29,7 +29,6 @@ struct GeomArgs {
     float2* astep;   // [atoms] exp(2 pi i z) of each element-sorted atom
     int64_t* refl_cnt;
     int64_t* run_cnt;  // [n_struct] runs of each structure
-    int* tcnt;       // [n_struct][2][enum_threads] per-thread reflection and run counts of the counting pass
     int* runs;       // [reflections] run entries (first reflection within the structure << 3 | length)
     unsigned long long* work;  // [3] structure-factor work: terms, phase-factor seeds, tiles (k_scan_refl)
     int64_t* refl_off;
@@ -40,12 +39,14 @@ struct GeomArgs {
     int atoms_set_geo;  // k_atoms also marks such structures invalid in geo (only when it runs before k_count)
     int* cls_list;   // [kPostClasses][n_struct] post-processing size classes (nullptr: not built)
     int* abort_flag; // flags[0]; flags[1] output abort, flags[2] tile queue, flags[4..9] class counts,
-                     // flags[10..15] class work counters
+                     // flags[10..15] class work counters, flags[26..28] enumeration claims
     int64_t* totals;
     int32_t* status;
     double* q;
     uint32_t* key;
     long long* parts;  // chunk sums of the multi-block scan (nullptr: single-block scan)
+    int* oparts;       // [chunks][4096] bin counts of the multi-block order (nullptr: one-block order)
+    int* enum_ctr;     // flags[26..28]: structure claims of counting, of emission's warps and of its CTAs
     unsigned* imax;    // [n_struct] largest reflection intensity slot, zeroed by k_prep (or nullptr)
     int32_t* out_flags;  // [n_struct] caller's flag words, written by k_prep (or nullptr)
     float4* cdd;       // [(zmax + 1) * 4] (a, b) coefficients as two floats, by k_coef (or nullptr)
@@ -77,7 +78,9 @@ struct SfArgs {
     float2* F;   // optional per-reflection F (nullptr: not stored)
     float4* Fx;  // gradient path: (Re F, Im F, Re dF/ds^2, Im dF/ds^2) per reflection (nullptr otherwise)
     float* Ig;   // gradient path: |F|^2 LP per reflection
-    float* W2;   // FP32 pattern variants: sum_j a_j^2 per reflection, the scale of the sum's rounding (or nullptr)
+    float* Eb;   // FP32 pattern variants: bound of the intensity's rounding error per reflection (or nullptr):
+                 // LP dF (2 |F| + dF) with dF = eps_k sqrt(sum_j a_j^2), a_j = occ DW max(|f|, Z)
+    float eps_k; // K times the relative error of one FP32 term (the bound of |dF| / sqrt(sum a_j^2))
     unsigned* imax;  // FP32 pattern variants: [n_struct] bits of the largest reflection intensity (zeroed by k_prep)
 };
 
@@ -90,8 +93,8 @@ struct RefineTables {
 struct RefineArgs {
     int n_struct, zmax, grid;  // grid = number of SMs
     double lambda;
-    float l2f;    // lambda^2 / 4
-    float eps_k;  // K times the relative error of one FP32 term: the bound of |dF| / sqrt(sum a_j^2)
+    float l2f;       // lambda^2 / 4
+    float l2h, l2l;  // lambda^2 / 4 as two floats
     float tau;    // intensity error allowed without re-evaluation, relative to max(I, cref M)
     float cref;   // cutoff fraction (the floor of the guarantee), relative to the largest reflection M
     const int* abort_flag;
@@ -103,7 +106,7 @@ struct RefineArgs {
     const double* q;
     const uint32_t* key;
     float* If;          // FP32 intensities, rewritten for the re-evaluated reflections
-    const float* W2;    // sum_j a_j^2 per reflection
+    const float* Eb;    // bound of the FP32 intensity's rounding error per reflection (k_sf)
     const unsigned* imax;  // largest intensity of each structure (bits)
     const AtomR* atomr;
     const float4* cdd;
@@ -236,6 +239,7 @@ void launch_prep(const GeomArgs& a, cudaStream_t st, bool pdl);
 void launch_coef(const GeomArgs& a, cudaStream_t st, bool pdl);
 void launch_atoms(const GeomArgs& a, cudaStream_t st, bool pdl);
 void launch_order(const GeomArgs& a, cudaStream_t st, bool pdl);
+size_t order_parts_bytes(int64_t n);  // bytes of GeomArgs::oparts for n structures (0: one-block order)
 void launch_count(const GeomArgs& a, cudaStream_t st, bool pdl);
 void launch_count_only(const GeomArgs& a, cudaStream_t st);
 void launch_scan_refl(const GeomArgs& a, cudaStream_t st, bool pdl);

@@ -566,10 +566,11 @@ class Handle:
         return int(out[0]), int(out[1]), int(out[2]), int(out[3])
 
     def unit_rates(self):
-        """Measured issue rates (lane operations per SM per clock) of MUFU sin, cos, ex2 and FP32 FMA."""
-        out = (C.c_double * 4)()
+        """Measured issue rates (lane operations per SM per clock) of MUFU sin, cos, ex2, FP32 FMA and
+        FP64 FMA."""
+        out = (C.c_double * 5)()
         self._check(self.lib.xrd_unit_rates(self.h, out))
-        return {"mufu_sin": out[0], "mufu_cos": out[1], "mufu_ex2": out[2], "ffma": out[3]}
+        return {"mufu_sin": out[0], "mufu_cos": out[1], "mufu_ex2": out[2], "ffma": out[3], "dfma": out[4]}
 
     def set_refine(self, enabled: bool):
         """Re-evaluation of weak reflections of the FP32 variants (on by default; off is a diagnostic)."""

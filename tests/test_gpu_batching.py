@@ -74,8 +74,9 @@ def test_all_launch_shapes(gpu_lib):
                 _same(ref["runs"], got)
         _close(ref[128], ref["runs"], 2e-6)
         h.set_sf_shape(128, 2, 0)
-        h.set_enum_threads(128)  # another emission order, the same pattern
-        _same(ref[128], _run(xrd, h, db, co, sz.n_refl, ws))
+        for et in (64, 128, 512, 1024):  # one warp or one CTA per structure: the same order and pattern
+            h.set_enum_threads(et)
+            _same(ref[128], _run(xrd, h, db, co, sz.n_refl, ws))
         h.set_enum_threads(256)
         out = xrd.PatternBuffers(db.n_struct, sz.n_refl)
         tile, warps, runs = h.autotune(db, co, out, ws)
