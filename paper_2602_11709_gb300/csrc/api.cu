@@ -544,6 +544,7 @@ int xrd_pattern_batch(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, cons
     int rb, warps, runs;
     sf_shape(h, o, rb, warps, runs);
     xrd::GeomArgs ga = geom_args(b, o, L, ws, cap_refl, out->totals, out->status, rb);
+    ga.sctab = h->rtab.sc;
     ga.runs_mode = runs;
     ga.enum_threads = h->enum_threads;
     ga.out_flags = out->flags;
@@ -999,6 +1000,7 @@ static void launch_front(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, c
     ga.n_struct = (int)n;
     ga.zmax = b->zmax;
     ga.n_atoms = b->n_atoms;
+    ga.sctab = h->rtab.sc;
     int rb, warps, runs;
     sf_shape(h, o, rb, warps, runs);
     ga.rb = rb;

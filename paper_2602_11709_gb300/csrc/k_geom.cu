@@ -10,6 +10,7 @@
 // |g|^2 is evaluated in one fixed order with every product and sum rounded on
 // its own (no fused multiply-add), so the set of reflections on the sphere
 // boundary is decided exactly as a plain FP64 evaluation of the same order.
+#include "xrd_dd.cuh"
 #include "xrd_internal.cuh"
 #include "xrd_launch.h"
 
@@ -155,7 +156,8 @@ __global__ void __launch_bounds__(128) k_atoms(const int64_t* __restrict__ atom_
                                                const double* __restrict__ occ, const double* __restrict__ Bf, int zmax,
                                                Geo* __restrict__ geo, int set_geo, int* __restrict__ atom_bad,
                                                Atom32* __restrict__ a32, Atom64* __restrict__ a64,
-                                               float2* __restrict__ astep, AtomR* __restrict__ ar)
+                                               float2* __restrict__ astep, AtomR* __restrict__ ar,
+                                               const float4* __restrict__ sctab)
 {
     pdl_enter();
     __shared__ int off[kZmaxLimit + 1];
@@ -239,10 +241,11 @@ __global__ void __launch_bounds__(128) k_atoms(const int64_t* __restrict__ atom_
             r.src = (int)i;
             r.zf = (float)z;
             a32[a0 + pos] = r;
-            if (astep) {  // the l -> l + 1 step of the phase factor (runs), from the same fixed-point z
-                double sz, cz;
-                sincospi((double)(int32_t)r.Z * 0x1p-31, &sz, &cz);
-                astep[a0 + pos] = make_float2((float)cz, (float)sz);
+            if (astep) {  // the l -> l + 1 step of the phase factor (runs), from the same fixed-point z:
+                          // cos and sin of 2 pi z in double-float (FP32 operations), rounded to floats
+                DD cz, sz;
+                dd_sincos_turn((unsigned long long)r.Z << 32, sctab, cz, sz);
+                astep[a0 + pos] = make_float2(cz.hi + cz.lo, sz.hi + sz.lo);
             }
             Atom64 d;
             d.x = x; d.y = y; d.z = w; d.B = bb; d.occ = o; d.zz = z; d.pad = 0;
@@ -1195,7 +1198,8 @@ void launch_atoms(const GeomArgs& a, cudaStream_t st, bool pdl)
 {
     if (a.n_struct > 0)
         launch_k(pdl, k_atoms, a.n_struct, 128, st, a.atom_off, a.n_atoms, a.frac, a.Z, a.occ, a.B, a.zmax, a.geo,
-                 a.atoms_set_geo, a.atom_bad, a.atom32, a.atom64, a.runs_mode ? a.astep : (float2*)nullptr, a.atomr);
+                 a.atoms_set_geo, a.atom_bad, a.atom32, a.atom64, a.runs_mode ? a.astep : (float2*)nullptr, a.atomr,
+                 a.sctab);
 }
 
 void launch_order(const GeomArgs& a, cudaStream_t st, bool pdl)

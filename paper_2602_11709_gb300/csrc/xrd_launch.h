@@ -47,6 +47,7 @@ struct GeomArgs {
     long long* parts;  // chunk sums of the multi-block scan (nullptr: single-block scan)
     int* oparts;       // [chunks][4096] bin counts of the multi-block order (nullptr: one-block order)
     int* enum_ctr;     // flags[26..28]: structure claims of counting, of emission's warps and of its CTAs
+    const float4* sctab;  // [256] cos and sin of 2 pi k / 256 as two floats (the re-evaluation's table)
     unsigned* imax;    // [n_struct] largest reflection intensity slot, zeroed by k_prep (or nullptr)
     int32_t* out_flags;  // [n_struct] caller's flag words, written by k_prep (or nullptr)
     float4* cdd;       // [(zmax + 1) * 4] (a, b) coefficients as two floats, by k_coef (or nullptr)

@@ -29,10 +29,10 @@ LAUNCHES_PER_BATCH = 19
 
 
 def launches_per_batch(n_struct: int, refine: bool = True) -> int:
-    """Kernels of one xrd_pattern_batch call: above two chunks of 4096 structures the reflection
-    scan and the output scan each take two kernels (chunk sums, then the chunks); the FP64
-    variant (or refine off) has no re-evaluation kernels."""
-    return LAUNCHES_PER_BATCH - (0 if refine else 2) + (2 if (n_struct + 4095) // 4096 > 2 else 0)
+    """Kernels of one xrd_pattern_batch call: above two chunks of 4096 structures the
+    largest-first order, the reflection scan and the output scan each take two kernels (chunk
+    sums, then the chunks); the FP64 variant (or refine off) has no re-evaluation kernels."""
+    return LAUNCHES_PER_BATCH - (0 if refine else 2) + (3 if (n_struct + 4095) // 4096 > 2 else 0)
 
 
 class xrd_batch(C.Structure):
