@@ -145,9 +145,9 @@ typedef struct {
 
 /*
  * Create a handle bound to CUDA device `device`. Returns XRD_OK or
- * XRD_ECUDA/XRD_EINVAL. The handle owns six non-blocking side streams: the
- * post-processing size classes of xrd_pattern_batch (and the thread-block
- * clusters of its largest structures) run on them concurrently,
+ * XRD_ECUDA/XRD_EINVAL. The handle owns eight non-blocking side streams: the
+ * nine post-processing size classes of xrd_pattern_batch (the largest as flat
+ * device-wide passes) run on them and the caller's stream concurrently,
  * forked from and joined back into the caller's stream by events (so a
  * capture of the call on the caller's stream takes them in as branches).
  */

@@ -19,9 +19,8 @@ CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libxrd.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-# The cluster kernel's CTAs read data the cluster's other CTAs wrote: its global loads are cached
-# in L2 only, where those writes are visible after a fence and a cluster barrier.
-FILE_FLAGS = {"k_post_big.cu": ["-Xptxas", "-dlcm=cg"]}
+# extra nvcc flags of single translation units (none at present)
+FILE_FLAGS = {}
 
 
 def nvcc() -> str:

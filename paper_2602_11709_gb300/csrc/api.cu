@@ -38,13 +38,13 @@ struct xrd_handle {
 namespace {
 
 constexpr int kRunsPerTileHost = xrd::kRunsPerTile;  // structure-factor tile: 32 runs (one per lane)
-// flags area, zeroed at the start of every call: 16 ints (see GeomArgs::abort_flag), then the
-// structure-factor work counters (3 x 64 bit) at byte kWorkOffset and the re-evaluation's
-// reflection count (64 bit) at kRefinedOffset
-constexpr int kFlagBytes = 128;
+// flags area, zeroed at the start of every call: flag words (see GeomArgs::abort_flag), the
+// structure-factor work counters (3 x 64 bit) at byte kWorkOffset, the re-evaluation's
+// reflection count (64 bit) at kRefinedOffset, the enumeration claims at int 26 and the post
+// class counts and work counters at ints kFlagClsCnt and kFlagClsNext
+constexpr int kFlagBytes = 256;
 constexpr int kWorkOffset = 64;
 constexpr int kRefinedOffset = 96;
-constexpr int kPostCap = 2048;  // reflections per structure kept in shared memory by k_post
 constexpr int kStages = 9;
 constexpr int kSfStage = 5;      // index of the structure-factor stage
 constexpr int kRefineStage = 6;  // index of the re-evaluation stage
@@ -89,12 +89,12 @@ struct Layout {
         flags, coef32, atom32, atom64, astep, imax, cdd, atomr;
     size_t q, key, runs, I, Eb, cand_r, cand_s, g_perm, g_bkt, g_flag, g_pstart, g_psum, g_fcnt;
     size_t st_q, st_I, st_foff, st_hkl, st_mult;
-    size_t parts, oparts, cpart;
+    size_t parts, oparts, pf, pf_sq, pf_sI;
     size_t total;
 };
 
 // chunk sums of the multi-block scans: 9 words per chunk of 4096 structures
-size_t scan_parts_bytes(int64_t n) { return 8 * 9 * (size_t)((n + 4095) / 4096 + 1); }
+size_t scan_parts_bytes(int64_t n) { return 8 * (3 + xrd::kPostClasses) * (size_t)((n + 4095) / 4096 + 1); }
 
 Layout layout(int64_t n, int64_t natoms, int zmax, int64_t R)
 {
@@ -126,8 +126,8 @@ Layout layout(int64_t n, int64_t natoms, int zmax, int64_t R)
     L.runs = take(4 * R);
     L.I = take(8 * R);
     L.Eb = take(4 * R);
-    L.cand_r = take(8 * R);
-    L.cand_s = take(4 * R);
+    L.cand_r = take(8 * (R + 1));  // also the kept-peak and family scans of the flat post passes
+    L.cand_s = take(4 * (R + 1));  // also their peak starts and ids
     L.g_perm = take(4 * R);
     L.g_bkt = take(4 * (R + n));
     L.g_flag = take(R);
@@ -141,7 +141,9 @@ Layout layout(int64_t n, int64_t natoms, int zmax, int64_t R)
     L.st_mult = take(4 * R);
     L.parts = take(scan_parts_bytes(n));
     L.oparts = take(xrd::order_parts_bytes(n));
-    L.cpart = take(8 * 2 * xrd::kPostClusterMax * xrd::kPostClustersMax);
+    L.pf = take(4 * (n + 1) + 8 * n + 16 + 8 * 2 * xrd::kPfScanBlocksMax + 64);
+    L.pf_sq = take(8 * R);  // sorted records of the flat post passes
+    L.pf_sI = take(8 * R);
     L.total = o;
     return L;
 }
@@ -658,7 +660,6 @@ int xrd_pattern_batch(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, cons
     xrd::PostArgs pa{};
     pa.n_struct = (int)n;
     pa.geo = ga.geo;
-    pa.cap_smem = kPostCap;
     pa.scaled = o->scaled;
     pa.lambda = o->lambda;
     pa.tol = o->tt_tol;
@@ -680,8 +681,8 @@ int xrd_pattern_batch(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, cons
     pa.I = sa.I;
     pa.If = sa.If;
     pa.cls_list = ga.cls_list;
-    pa.cls_cnt = ga.abort_flag + 4;
-    pa.cls_next = ga.abort_flag + 4 + xrd::kPostClasses;
+    pa.cls_cnt = ga.abort_flag + xrd::kFlagClsCnt;
+    pa.cls_next = ga.abort_flag + xrd::kFlagClsNext;
     pa.atom_bad = ga.atom_bad;
     pa.status = out->status;
     pa.totals = out->totals;
@@ -701,7 +702,25 @@ int xrd_pattern_batch(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, cons
     pa.nfm = (int64_t*)(ws + L.nfm);
     pa.l2h = (float)pa.l2d;
     pa.l2l = (float)(pa.l2d - (double)pa.l2h);
-    pa.cpart = (long long*)(ws + L.cpart);
+    {
+        char* pf = ws + L.pf;
+        pa.pf_parts = (long long*)pf;
+        pa.pf_smax = (unsigned long long*)(pf + 8 * 2 * xrd::kPfScanBlocksMax);
+        pa.pf_voff = (int*)(pf + 8 * 2 * xrd::kPfScanBlocksMax + 8 * n);
+        pa.pf_scal = pa.pf_voff + (n + 1);
+        pa.pf_pst = (int*)(ws + L.cand_s);
+        pa.pf_pj = (int*)(ws + L.Eb);
+        pa.pf_kidx = (int*)(ws + L.cand_r);
+        pa.pf_fidx = pa.pf_kidx + (cap_refl + 1);
+        // bucket-order records in arrays that are free between the scatter and the rank
+        pa.pf_bq = (double*)(ws + L.cand_r);
+        pa.pf_bk = (uint32_t*)(ws + L.cand_s);
+        pa.pf_bI = (double*)(ws + L.g_psum);
+        pa.pf_bb = (int*)(ws + L.Eb);
+        pa.pf_sq = (double*)(ws + L.pf_sq);
+        pa.pf_sk = (uint32_t*)(ws + L.g_perm);
+        pa.pf_sI = (double*)(ws + L.pf_sI);
+    }
     if (out->refl_off && out->cap_refl > 0) {
         pa.cap_refl = out->cap_refl;
         pa.refl_hkl = out->refl_hkl;

@@ -638,7 +638,7 @@ __device__ __forceinline__ void write_tiles(int s, int rb, int tile_refl, int64_
 // output order is the column order above, l ascending, whatever the launch shape.
 // With one warp per structure the warps claim structures from ctr[0]; given the
 // post-processing size-class lists (cls_list, cls_cnt), the structures above
-// kPostCap3 reflections (the two largest classes) are left to whole CTAs,
+// kPostCap6 reflections (the two largest classes) are left to whole CTAs,
 // which claim them from ctr[1] once the warps are done. ctr: zero at launch.
 // Dynamic shared memory: enum_smem_bytes(blockDim).
 template <bool RUNS>
@@ -660,7 +660,7 @@ __global__ void __launch_bounds__(kEnumMaxThreads) k_emit(const Geo* __restrict_
     const int nt = blockDim.x, t = threadIdx.x;
     const bool per_warp = enum_per_warp(nt);
     const int w = t >> 5, lane = t & 31;
-    const int64_t big_min = cls_list ? kPostCap3 : INT64_MAX;
+    const int64_t big_min = cls_list ? kPostCap6 : INT64_MAX;
     int nbig = 0;
     if (per_warp) {
         const ChunkCols cc = chunk_cols(esm + enum_cta_ints(nt) + w * kWarpRecInts, 32);
@@ -702,7 +702,7 @@ __global__ void __launch_bounds__(kEnumMaxThreads) k_emit(const Geo* __restrict_
             }
         }
         if (!cls_list) return;
-        nbig = cls_cnt[4] + cls_cnt[5];
+        nbig = cls_cnt[kPostFlatClass - 1] + cls_cnt[kPostFlatClass];
         if (nbig == 0) return;
     }
     const ChunkCols cc = chunk_cols(esm, nt);
@@ -714,8 +714,9 @@ __global__ void __launch_bounds__(kEnumMaxThreads) k_emit(const Geo* __restrict_
             __syncthreads();
             const int j = s_big;
             if (j >= nbig) break;
-            const int n5 = cls_cnt[5];  // the largest class first
-            sb = j < n5 ? cls_list[(int64_t)5 * n_struct + j] : cls_list[(int64_t)4 * n_struct + (j - n5)];
+            const int n5 = cls_cnt[kPostFlatClass];  // the largest class first
+            sb = j < n5 ? cls_list[(int64_t)kPostFlatClass * n_struct + j]
+                        : cls_list[(int64_t)(kPostFlatClass - 1) * n_struct + (j - n5)];
         } else {
             if (it > 0) break;
             sb = blockIdx.x;  // one CTA per structure
@@ -874,7 +875,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_refl(const int64_t* __res
         }
         refl_off[n] = total;
         tile_off[n] = over ? 0 : (int)tcarry;
-        for (int k = 0; k < kPostClasses; k++) abort_flag[4 + k] = over ? 0 : ccnt[k];
+        for (int k = 0; k < kPostClasses; k++) abort_flag[kFlagClsCnt + k] = over ? 0 : ccnt[k];
         totals[0] = total;
         totals[1] = 0;
         totals[2] = 0;
@@ -1014,7 +1015,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_refl_final(const int64_t*
         }
         refl_off[n] = total;
         tile_off[n] = over ? 0 : (int)all[2];
-        for (int k = 0; k < kPostClasses; k++) abort_flag[4 + k] = over ? 0 : (int)all[3 + k];
+        for (int k = 0; k < kPostClasses; k++) abort_flag[kFlagClsCnt + k] = over ? 0 : (int)all[3 + k];
         totals[0] = total;
         totals[1] = 0;
         totals[2] = 0;
@@ -1271,13 +1272,13 @@ void launch_emit(const GeomArgs& a, cudaStream_t st, bool pdl)
         launch_pdl(k, enum_grid(a), a.enum_threads, smem, st, a.geo, a.n_struct, a.r2min, a.r2max, (float)a.r2min,
                    (float)a.r2max, a.runs_mode ? a.rb : 0, 32 * a.rb, (const int64_t*)a.refl_off,
                    (const int64_t*)a.run_cnt, (const int*)a.abort_flag, a.q, a.key, a.runs, (const int*)a.tile_off,
-                   a.tile_tab, a.enum_ctr + 1, (const int*)a.cls_list, (const int*)(a.abort_flag + 4));
+                   a.tile_tab, a.enum_ctr + 1, (const int*)a.cls_list, (const int*)(a.abort_flag + kFlagClsCnt));
     else
         k<<<enum_grid(a), a.enum_threads, smem, st>>>(a.geo, a.n_struct, a.r2min, a.r2max, (float)a.r2min,
                                                        (float)a.r2max, a.runs_mode ? a.rb : 0, 32 * a.rb,
                                                        a.refl_off, a.run_cnt, a.abort_flag, a.q, a.key, a.runs,
                                                        a.tile_off, a.tile_tab, a.enum_ctr + 1, a.cls_list,
-                                                       a.abort_flag + 4);
+                                                       a.abort_flag + kFlagClsCnt);
 }
 
 }  // namespace xrd

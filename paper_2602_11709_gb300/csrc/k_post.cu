@@ -331,12 +331,13 @@ __device__ void post_structure(const PostArgs& a, int s, int64_t base, int n, co
 
 // Persistent CTAs over one size class of structures (a list built by the scan
 // kernel, largest first), each CTA claiming the next structure from a counter.
-// CAP > 0: the structure's reflections live in shared memory (n <= CAP); the
-// FP32 variants also stage the intensities there, in the second half of the
-// peak-sum area (FP32 peak sums use the first half). CAP == 0: global scratch.
+// The structure's reflections live in shared memory (n <= CAP); the FP32
+// variants also stage the intensities there, in the second half of the
+// peak-sum area (FP32 peak sums use the first half).
 template <int CAP, int NT, bool FI>
 __global__ void __launch_bounds__(NT) k_post(const PostArgs a, int cls)
 {
+    static_assert(CAP > 0, "the largest class runs as the flat passes");
     pdl_enter();
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int tmp[66];
@@ -354,7 +355,6 @@ __global__ void __launch_bounds__(NT) k_post(const PostArgs a, int cls)
         const int s = list[li];
         const int64_t base = a.refl_off[s];
         const int n = (int)(a.refl_off[s + 1] - base);
-        if (CAP == 0 && a.big && n > post_big_min(cnt, a.grid)) continue;  // the cluster kernel's
         if (a.atom_bad && a.atom_bad[s]) {  // an invalid atom: no peaks, the structure reports XRD_EINVAL
             if (threadIdx.x == 0) {
                 a.npk[s] = 0;
@@ -370,7 +370,7 @@ __global__ void __launch_bounds__(NT) k_post(const PostArgs a, int cls)
             if (threadIdx.x == 0) { a.npk[s] = 0; a.nfm[s] = 0; }
             continue;
         }
-        if (CAP > 0) {
+        {
             const size_t c = (size_t)CAP;
             unsigned char* p = smem;
             double* sq = (double*)p; p += align16(c * 8);
@@ -389,10 +389,6 @@ __global__ void __launch_bounds__(NT) k_post(const PostArgs a, int cls)
             }
             __syncthreads();
             post_structure<uint16_t, FI>(a, s, base, n, sq, sk, sI, perm, bkt, flag, pst, psum, fcnt, tmp, dtmp);
-        } else {
-            post_structure<int, FI>(a, s, base, n, a.q + base, a.key + base, FI ? a.If + base : nullptr,
-                                    a.g_perm + base, a.g_bkt + base + s, a.g_flag + base, a.g_pstart + base,
-                                    a.g_psum + base, a.g_fcnt + base, tmp, dtmp);
         }
     }
 }
@@ -596,7 +592,7 @@ __global__ void __launch_bounds__(kCompactThreads) k_compact(const CompactArgs a
 template <int CAP, int NT, bool FI>
 static void launch_post_class(const PostArgs& a, int cls, cudaStream_t st)
 {
-    const size_t smem = CAP > 0 ? post_smem_bytes(CAP) : 0;
+    const size_t smem = post_smem_bytes(CAP);
     static int per_sm_cache[64] = {};
     int dev = 0;
     cudaGetDevice(&dev);
@@ -612,19 +608,17 @@ static void launch_post_class(const PostArgs& a, int cls, cudaStream_t st)
     k_post<CAP, NT, FI><<<grid, NT, smem, st>>>(a, cls);
 }
 
-// st[c]: the stream of size class c, st[kPostClasses] that of the clusters (the caller forks and joins them)
+// st[c]: the stream of size class c (the caller forks and joins them); the largest first
 template <bool FI>
 static void launch_post_fi(const PostArgs& a, const cudaStream_t* st)
 {
-    // the last class: structures above kPostBigMin reflections one thread-block cluster each (beside
-    // the rest), the others one CTA each; without a cluster that fits, one CTA each for all
-    PostArgs b = a;
-    b.big = 1;
-    if (!launch_post_big(b, 5, st[kPostClasses])) b.big = 0;
-    launch_post_class<0, 1024, FI>(b, 5, st[5]);
-    launch_post_class<kPostCap4, 1024, FI>(a, 4, st[4]);
-    launch_post_class<kPostCap3, 512, FI>(a, 3, st[3]);
-    launch_post_class<kPostCap2, 256, FI>(a, 2, st[2]);
+    launch_post_flat(a, kPostFlatClass, st[kPostFlatClass]);
+    launch_post_class<kPostCap7, 1024, FI>(a, 7, st[7]);
+    launch_post_class<kPostCap6, 512, FI>(a, 6, st[6]);
+    launch_post_class<kPostCap5, 512, FI>(a, 5, st[5]);
+    launch_post_class<kPostCap4, 256, FI>(a, 4, st[4]);
+    launch_post_class<kPostCap3, 256, FI>(a, 3, st[3]);
+    launch_post_class<kPostCap2, 192, FI>(a, 2, st[2]);
     launch_post_class<kPostCap1, 128, FI>(a, 1, st[1]);
     launch_post_class<kPostCap0, 64, FI>(a, 0, st[0]);
 }

@@ -1,0 +1,508 @@
+// Steps S4-S6 for the largest size class (structures above 6144 reflections):
+// sort by 2-theta, anchor merge, families, cutoff and scaling (Sec. 2, Sec. 3)
+// as flat passes over all of the class's reflections at once.
+//
+// One CTA per structure on global scratch leaves most SMs idle when a few
+// structures hold most of the reflections (256 cells of 20 000-190 000
+// reflections, or the single 50 A cell of Sec. 4.2 with 680 000). Here the
+// class's structures are laid end to end in one virtual index space (virtual
+// offsets voff[j] in class-list order), every step is a grid-stride loop over
+// that space, and the per-structure block steps become device-wide ones:
+//  1. bucket of every reflection on |g|^3 (n_j buckets for a structure of n_j
+//     reflections, laid out from voff[j] like its reflections), counts by
+//     atomics;
+//  2. one exclusive scan over all buckets: since a structure's buckets hold
+//     exactly its n_j reflections, bucket starts are sorted positions;
+//  3. scatter of (|g|^2, key, I, bucket) records into bucket order, then each
+//     record's rank among the members of its own bucket on the full key
+//     (|g|^2, then -h, -k, -l), which places it in sorted order: every later
+//     pass reads the sorted records sequentially instead of through a
+//     permutation;
+//  4. the anchor merge: a definite start where the gap to the previous
+//     reflection is >= tol, one thread per run of close reflections;
+//  5. a scan of the peak starts gives peak ids; per peak the merged intensity,
+//     the family count, and the structure's largest peak (atomic maximum);
+//  6. one scan of kept peaks and of their families; per kept peak the staging
+//     of the outputs, as the one-CTA kernel writes them.
+// The decisions and the order of every floating-point operation are those of
+// the one-CTA kernel (k_post.cu), so the outputs are identical. Scans are two
+// kernels (segment sums, then segments offset by the sums before them) over
+// lengths read from device memory, so the launch sequence is fixed and
+// capturable.
+#include "xrd_internal.cuh"
+#include "xrd_launch.h"
+#include "xrd_post.cuh"
+
+namespace xrd {
+
+constexpr int kPfThreads = 256;      // grid-stride element kernels
+constexpr int kPfScanThreads = 1024;  // scans and the prologue
+
+// largest j in [0, c5) with voff[j] <= v (voff[c5] > v)
+__device__ __forceinline__ int vowner(const int* __restrict__ voff, int c5, int v)
+{
+    int lo = 0, hi = c5;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (voff[mid] <= v) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int2 warp_incl_scan2(int2 v)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int x = __shfl_up_sync(0xffffffffu, v.x, o), y = __shfl_up_sync(0xffffffffu, v.y, o);
+        if (lane >= o) {
+            v.x += x;
+            v.y += y;
+        }
+    }
+    return v;
+}
+
+// Exclusive block scan of one int2 per thread; returns the block total. tmp: 66 ints.
+__device__ __forceinline__ int2 block_scan_int2(int2 v, int2& excl, int* tmp)
+{
+    const int nw = blockDim.x >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int2 inc = warp_incl_scan2(v);
+    if (lane == 31) {
+        tmp[w] = inc.x;
+        tmp[33 + w] = inc.y;
+    }
+    __syncthreads();
+    if (w == 0) {
+        const int2 sv = make_int2(lane < nw ? tmp[lane] : 0, lane < nw ? tmp[33 + lane] : 0);
+        const int2 si = warp_incl_scan2(sv);
+        if (lane < nw) {
+            tmp[lane] = si.x - sv.x;
+            tmp[33 + lane] = si.y - sv.y;
+        }
+        if (lane == 31) {
+            tmp[32] = si.x;
+            tmp[65] = si.y;
+        }
+    }
+    __syncthreads();
+    excl = make_int2(tmp[w] + inc.x - v.x, tmp[33 + w] + inc.y - v.y);
+    const int2 tot = make_int2(tmp[32], tmp[65]);
+    __syncthreads();  // tmp is free again
+    return tot;
+}
+
+// ---- the three scanned sequences ----
+struct SrcBkt {  // bucket counts -> bucket starts, in place; length V
+    static __device__ int len(const PostArgs& a) { return a.pf_scal[0]; }
+    static __device__ int2 load(const PostArgs& a, int i) { return make_int2(a.g_bkt[i], 0); }
+    static __device__ void store(const PostArgs& a, int i, int2 e) { a.g_bkt[i] = e.x; }
+    static __device__ void total(const PostArgs& a, int n, int2 t) { a.g_bkt[n] = t.x; }
+};
+struct SrcPst {  // peak starts -> peak ids, in place; length V; the peak count into pf_scal[1]
+    static __device__ int len(const PostArgs& a) { return a.pf_scal[0]; }
+    static __device__ int2 load(const PostArgs& a, int i) { return make_int2(a.pf_pst[i], 0); }
+    static __device__ void store(const PostArgs& a, int i, int2 e) { a.pf_pst[i] = e.x; }
+    static __device__ void total(const PostArgs& a, int n, int2 t)
+    {
+        a.pf_pst[n] = t.x;
+        a.pf_scal[1] = t.x;
+    }
+};
+template <bool FI>
+struct SrcKeep {  // per peak (kept, its families if kept) -> kidx, fidx; length = the peak count
+    static __device__ int len(const PostArgs& a) { return a.pf_scal[1]; }
+    static __device__ int2 load(const PostArgs& a, int k)
+    {
+        const unsigned long long m = a.pf_smax[a.pf_pj[k]];
+        bool keep;
+        if (FI) {
+            const float imaxf = __uint_as_float((uint32_t)m);
+            keep = a.cutoff == 0.0 ||
+                   __float_as_uint(((const float*)a.g_psum)[k]) > __float_as_uint((float)a.cutoff * imaxf);
+        } else {
+            const double imax = __longlong_as_double((long long)m);
+            keep = a.cutoff == 0.0 || dbits(a.g_psum[k]) > dbits(a.cutoff * imax);
+        }
+        return make_int2(keep ? 1 : 0, keep ? a.g_fcnt[k] : 0);
+    }
+    static __device__ void store(const PostArgs& a, int k, int2 e)
+    {
+        a.pf_kidx[k] = e.x;
+        a.pf_fidx[k] = e.y;
+    }
+    static __device__ void total(const PostArgs& a, int n, int2 t)
+    {
+        a.pf_kidx[n] = t.x;
+        a.pf_fidx[n] = t.y;
+    }
+};
+
+// Segment sums: block b takes [b seg, (b + 1) seg) of [0, len).
+template <class S>
+__global__ void __launch_bounds__(kPfScanThreads) k_pf_scan_parts(const PostArgs a)
+{
+    pdl_enter();
+    __shared__ int tmp[66];
+    if (*a.abort_flag) return;
+    const int n = S::len(a), G = gridDim.x;
+    const int seg = (n + G - 1) / G;
+    const int lo = min((int)blockIdx.x * seg, n), hi = min(lo + seg, n);
+    int2 s = make_int2(0, 0);
+    for (int i = lo + (int)threadIdx.x; i < hi; i += blockDim.x) {
+        const int2 v = S::load(a, i);
+        s.x += v.x;
+        s.y += v.y;
+    }
+    int2 e;
+    const int2 t = block_scan_int2(s, e, tmp);
+    if (threadIdx.x == 0) {
+        a.pf_parts[blockIdx.x] = t.x;
+        a.pf_parts[G + blockIdx.x] = t.y;
+    }
+}
+
+// Each segment scanned in chunks of blockDim, offset by the sums of the segments before it.
+template <class S>
+__global__ void __launch_bounds__(kPfScanThreads) k_pf_scan_final(const PostArgs a)
+{
+    pdl_enter();
+    __shared__ int tmp[66];
+    if (*a.abort_flag) return;
+    const int n = S::len(a), G = gridDim.x;
+    const int seg = (n + G - 1) / G;
+    const int lo = min((int)blockIdx.x * seg, n), hi = min(lo + seg, n);
+    int2 carry = make_int2(0, 0), all = make_int2(0, 0);
+    for (int b = 0; b < G; b++) {
+        const int x = (int)a.pf_parts[b], y = (int)a.pf_parts[G + b];
+        if (b < (int)blockIdx.x) {
+            carry.x += x;
+            carry.y += y;
+        }
+        all.x += x;
+        all.y += y;
+    }
+    for (int c0 = lo; c0 < hi; c0 += blockDim.x) {
+        const int i = c0 + (int)threadIdx.x;
+        const int2 v = i < hi ? S::load(a, i) : make_int2(0, 0);
+        int2 e;
+        const int2 t = block_scan_int2(v, e, tmp);
+        if (i < hi) S::store(a, i, make_int2(carry.x + e.x, carry.y + e.y));
+        carry.x += t.x;
+        carry.y += t.y;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) S::total(a, n, all);
+}
+
+// Prologue: the virtual offsets of the class's structures (a structure with an
+// invalid atom gets none and reports XRD_EINVAL), the structure maxima cleared;
+// every block clears the bucket counts over [0, V).
+__global__ void __launch_bounds__(kPfScanThreads) k_pf_prep(const PostArgs a, int cls)
+{
+    pdl_enter();
+    __shared__ int tmp[66];
+    if (*a.abort_flag) return;
+    const int c5 = a.cls_cnt[cls];
+    const int* __restrict__ list = a.cls_list + (int64_t)cls * a.n_struct;
+    int carry = 0;
+    for (int c0 = 0; c0 < c5; c0 += blockDim.x) {
+        const int j = c0 + (int)threadIdx.x;
+        int nj = 0;
+        if (j < c5) {
+            const int s = list[j];
+            const bool bad = a.atom_bad && a.atom_bad[s];
+            nj = bad ? 0 : (int)(a.refl_off[s + 1] - a.refl_off[s]);
+            if (blockIdx.x == 0) {
+                a.pf_smax[j] = 0ull;
+                if (bad) {
+                    a.npk[s] = 0;
+                    a.nfm[s] = 0;
+                    if (a.status[s] == XRD_OK) {
+                        a.status[s] = XRD_EINVAL;
+                        atomicAdd((unsigned long long*)&a.totals[3], 1ull);
+                    }
+                }
+            }
+        }
+        int2 e;
+        const int2 t = block_scan_int2(make_int2(nj, 0), e, tmp);
+        if (blockIdx.x == 0 && j < c5) a.pf_voff[j] = carry + e.x;
+        carry += t.x;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.pf_voff[c5] = carry;
+        a.pf_scal[0] = carry;
+    }
+    for (int i = (int)(blockIdx.x * blockDim.x + threadIdx.x); i < carry; i += (int)(gridDim.x * blockDim.x))
+        a.g_bkt[i] = 0;
+}
+
+// 1. bucket of every reflection; g_fcnt holds the virtual bucket until the ranks are taken
+__global__ void __launch_bounds__(kPfThreads) k_pf_bucket(const PostArgs a, int cls)
+{
+    pdl_enter();
+    if (*a.abort_flag) return;
+    const int V = a.pf_scal[0], c5 = a.cls_cnt[cls];
+    const int* __restrict__ list = a.cls_list + (int64_t)cls * a.n_struct;
+    const float lo3 = a.lo3, hi3 = a.hi3;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < V; v += gridDim.x * blockDim.x) {
+        const int j = vowner(a.pf_voff, c5, v);
+        const int first = a.pf_voff[j], nb = a.pf_voff[j + 1] - first;
+        const int64_t r = a.refl_off[list[j]] + (v - first);
+        const float scale = (float)nb / (hi3 - lo3);
+        const float qf = d2f_pos(a.q[r]);
+        int b = (int)((qf * sqrtf(qf) - lo3) * scale);
+        b = min(max(b, 0), nb - 1);
+        a.g_fcnt[v] = first + b;
+        atomicAdd(&a.g_bkt[first + b], 1);
+    }
+}
+
+// 3a. scatter of each reflection's record into bucket order (cand_r: |g|^2,
+// cand_s: key, g_psum: I, Eb: virtual bucket); g_bkt ends as the bucket ends
+template <bool FI>
+__global__ void __launch_bounds__(kPfThreads) k_pf_scatter(const PostArgs a, int cls)
+{
+    pdl_enter();
+    if (*a.abort_flag) return;
+    const int V = a.pf_scal[0], c5 = a.cls_cnt[cls];
+    const int* __restrict__ list = a.cls_list + (int64_t)cls * a.n_struct;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < V; v += gridDim.x * blockDim.x) {
+        const int j = vowner(a.pf_voff, c5, v);
+        const int64_t r = a.refl_off[list[j]] + (v - a.pf_voff[j]);
+        const int vb = a.g_fcnt[v];
+        const int pos = atomicAdd(&a.g_bkt[vb], 1);
+        a.pf_bq[pos] = a.q[r];
+        a.pf_bk[pos] = a.key[r];
+        if (FI) ((float*)a.pf_bI)[pos] = a.If[r];
+        else a.pf_bI[pos] = a.I[r];
+        a.pf_bb[pos] = vb;
+    }
+}
+
+// 3b. rank within the bucket on the full key; the record goes to its sorted position
+template <bool FI>
+__global__ void __launch_bounds__(kPfThreads) k_pf_rank(const PostArgs a)
+{
+    pdl_enter();
+    if (*a.abort_flag) return;
+    const int V = a.pf_scal[0];
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < V; p += gridDim.x * blockDim.x) {
+        const int vb = a.pf_bb[p];
+        const int b0 = vb ? a.g_bkt[vb - 1] : 0, b1 = a.g_bkt[vb];
+        const double qv = a.pf_bq[p];
+        const uint32_t kv = a.pf_bk[p];
+        int r = b0;
+        for (int i = b0; i < b1 && b1 - b0 > 1; i++) r += before(a.pf_bq[i], a.pf_bk[i], qv, kv);  // false for i == p
+        a.pf_sq[r] = qv;
+        a.pf_sk[r] = kv;
+        if (FI) ((float*)a.pf_sI)[r] = ((const float*)a.pf_bI)[p];
+        else a.pf_sI[r] = a.pf_bI[p];
+    }
+}
+
+// 4. anchor merge (and the caller's per-reflection list in merge order): pf_pst
+// and g_flag mark the peak starts
+template <bool FI>
+__global__ void __launch_bounds__(kPfThreads) k_pf_merge(const PostArgs a, int cls)
+{
+    pdl_enter();
+    if (*a.abort_flag) return;
+    const int V = a.pf_scal[0], c5 = a.cls_cnt[cls];
+    const int* __restrict__ list = a.cls_list + (int64_t)cls * a.n_struct;
+    const float l2 = a.l2f, lh = a.lhf, ttol = a.ttol;
+    const double lam = a.lambda, tol = a.tol;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < V; p += gridDim.x * blockDim.x) {
+        const int j = vowner(a.pf_voff, c5, p);
+        const int first = a.pf_voff[j], end = a.pf_voff[j + 1];
+        const double qv = a.pf_sq[p];
+        if (a.refl_hkl) {
+            const int64_t rb = a.refl_off[list[j]];
+            if (rb + (end - first) <= a.cap_refl) {
+                const int64_t o = rb + (p - first);
+                const uint32_t kv = a.pf_sk[p];
+                a.refl_hkl[3 * o] = hkl_h(kv);
+                a.refl_hkl[3 * o + 1] = hkl_k(kv);
+                a.refl_hkl[3 * o + 2] = hkl_l(kv);
+                a.refl_tt[o] = two_theta_q(qv, a.l2h, a.l2l, a.ttab);
+                a.refl_I[o] = FI ? (double)((const float*)a.pf_sI)[p] : a.pf_sI[p];
+            }
+        }
+        const bool start = p == first || !tt_close(a.pf_sq[p - 1], qv, l2, lh, ttol, lam, tol);
+        if (!start) continue;  // written by the thread of its run's definite start
+        a.pf_pst[p] = 1;
+        a.g_flag[p] = 1;
+        double qa = qv, qprev = qv;
+        for (int i = p + 1; i < end; i++) {
+            const double qi = a.pf_sq[i];
+            if (!tt_close(qprev, qi, l2, lh, ttol, lam, tol)) break;  // the next definite start
+            qprev = qi;
+            const int ps = tt_close(qa, qi, l2, lh, ttol, lam, tol) ? 0 : 1;
+            if (ps) qa = qi;
+            a.pf_pst[i] = ps;
+            a.g_flag[i] = (uint8_t)ps;
+        }
+    }
+}
+
+// 5. per peak: start position, structure, merged intensity, family count; the
+// structure's largest peak sum (bits of a non-negative float or double)
+template <bool FI>
+__global__ void __launch_bounds__(kPfThreads) k_pf_peaks(const PostArgs a, int cls)
+{
+    pdl_enter();
+    if (*a.abort_flag) return;
+    const int V = a.pf_scal[0], c5 = a.cls_cnt[cls];
+    const int* __restrict__ list = a.cls_list + (int64_t)cls * a.n_struct;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < V; p += gridDim.x * blockDim.x) {
+        if (!a.g_flag[p]) continue;
+        const int j = vowner(a.pf_voff, c5, p);
+        const int end = a.pf_voff[j + 1];
+        const bool hex = a.geo[list[j]].hex != 0;
+        const int k = a.pf_pst[p];
+        int e = p + 1;
+        while (e < end && !a.g_flag[e]) e++;
+        a.g_pstart[k] = p;
+        a.pf_pj[k] = j;
+        unsigned long long bits;
+        if (FI) {
+            const float* sI = (const float*)a.pf_sI;
+            float sum = 2.f * sI[p];
+            for (int i = p + 1; i < e; i++) sum = fmaf(2.f, sI[i], sum);
+            ((float*)a.g_psum)[k] = sum;
+            bits = __float_as_uint(sum);
+        } else {
+            double sum = 0.0;
+            for (int i = p; i < e; i++) sum += 2.0 * a.pf_sI[i];
+            a.g_psum[k] = sum;
+            bits = dbits(sum);
+        }
+        int nfam = 1;
+        if (e - p > 1) {  // distinct family keys among the members
+            nfam = 0;
+            for (int i = p; i < e; i++) {
+                const unsigned long long fk = family_key(a.pf_sk[i], hex);
+                bool lead = true;
+                for (int m = p; m < i && lead; m++) lead = family_key(a.pf_sk[m], hex) != fk;
+                nfam += lead;
+            }
+        }
+        a.g_fcnt[k] = nfam;
+        unsigned long long* mx = a.pf_smax + j;
+        if (bits > *(volatile unsigned long long*)mx) atomicMax(mx, bits);
+    }
+}
+
+// 6. staging of kept peaks and their families at the structure's reflection
+// offset, and its kept-peak and family counts
+template <bool FI>
+__global__ void __launch_bounds__(kPfThreads) k_pf_stage(const PostArgs a, int cls)
+{
+    pdl_enter();
+    if (*a.abort_flag) return;
+    const int NP = a.pf_scal[1], c5 = a.cls_cnt[cls];
+    const int* __restrict__ list = a.cls_list + (int64_t)cls * a.n_struct;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < NP; k += gridDim.x * blockDim.x) {
+        const int j = a.pf_pj[k];
+        const int s = list[j];
+        const int first = a.pf_voff[j], end = a.pf_voff[j + 1];
+        const int k0 = a.pf_pst[first], k1 = a.pf_pst[end];  // the structure's peaks: [k0, k1)
+        const int kb = a.pf_kidx[k0], fb = a.pf_fidx[k0];
+        const int64_t rb = a.refl_off[s];
+        if (k == k0) {
+            a.npk[s] = a.pf_kidx[k1] - kb;
+            a.nfm[s] = a.pf_fidx[k1] - fb;
+        }
+        if (a.pf_kidx[k + 1] == a.pf_kidx[k]) continue;  // below the cutoff
+        const int i0 = a.g_pstart[k];
+        int i1 = i0 + 1;
+        while (i1 < end && !a.g_flag[i1]) i1++;
+        const int64_t o = rb + (a.pf_kidx[k] - kb);
+        a.st_q[o] = a.pf_sq[i0];
+        const unsigned long long m = a.pf_smax[j];
+        if (FI) {
+            const float imaxf = __uint_as_float((uint32_t)m);
+            const float inv_imaxf = imaxf > 0.f ? 1.f / imaxf : 0.f;
+            const float ps = ((const float*)a.g_psum)[k];
+            a.st_I[o] = f2d_fast((a.scaled && imaxf > 0.f) ? (ps == imaxf ? 100.f : 100.f * (ps * inv_imaxf)) : ps);
+        } else {
+            const double imax = __longlong_as_double((long long)m);
+            const double inv_imax = imax > 0.0 ? 1.0 / imax : 0.0;
+            const double ps = a.g_psum[k];
+            a.st_I[o] = (a.scaled && imax > 0.0) ? (ps == imax ? 100.0 : 100.0 * (ps * inv_imax)) : ps;
+        }
+        const int fo0 = a.pf_fidx[k] - fb;
+        a.st_foff[o] = fo0;
+        if (i1 - i0 == 1) {
+            const uint32_t rep = a.pf_sk[i0];
+            const int64_t fo = rb + fo0;
+            a.st_hkl[3 * fo] = hkl_h(rep);
+            a.st_hkl[3 * fo + 1] = hkl_k(rep);
+            a.st_hkl[3 * fo + 2] = hkl_l(rep);
+            a.st_mult[fo] = 2;
+            continue;
+        }
+        const bool hex = a.geo[s].hex != 0;
+        auto kf = [&](int i) { return a.pf_sk[i]; };
+        for (int i = i0; i < i1; i++) {  // families, ranked by descending representative
+            const unsigned long long fk = family_key(kf(i), hex);
+            bool lead = true;
+            for (int jj = i0; jj < i && lead; jj++) lead = family_key(kf(jj), hex) != fk;
+            if (!lead) continue;
+            uint32_t rep = 0;
+            int cnt = 0;
+            for (int jj = i0; jj < i1; jj++)
+                if (family_key(kf(jj), hex) == fk) {
+                    rep = max(rep, kf(jj));
+                    cnt++;
+                }
+            int rank = 0;
+            for (int mm = i0; mm < i1; mm++) {
+                const unsigned long long fm = family_key(kf(mm), hex);
+                if (fm == fk) continue;
+                bool lm = true;
+                for (int jj = i0; jj < mm && lm; jj++) lm = family_key(kf(jj), hex) != fm;
+                if (!lm) continue;
+                uint32_t rm = 0;
+                for (int jj = i0; jj < i1; jj++)
+                    if (family_key(kf(jj), hex) == fm) rm = max(rm, kf(jj));
+                rank += rm > rep;
+            }
+            const int64_t fo = rb + fo0 + rank;
+            a.st_hkl[3 * fo] = hkl_h(rep);
+            a.st_hkl[3 * fo + 1] = hkl_k(rep);
+            a.st_hkl[3 * fo + 2] = hkl_l(rep);
+            a.st_mult[fo] = 2 * cnt;
+        }
+    }
+}
+
+template <bool FI>
+static void launch_flat_fi(const PostArgs& a, int cls, cudaStream_t st)
+{
+    const int G = a.grid * 2;  // scans and prologue: two 1024-thread CTAs per SM
+    const int E = a.grid * 8;  // element kernels: eight 256-thread CTAs per SM
+    launch_pdl(k_pf_prep, G, kPfScanThreads, 0, st, a, cls);
+    launch_pdl(k_pf_bucket, E, kPfThreads, 0, st, a, cls);
+    launch_pdl(k_pf_scan_parts<SrcBkt>, G, kPfScanThreads, 0, st, a);
+    launch_pdl(k_pf_scan_final<SrcBkt>, G, kPfScanThreads, 0, st, a);
+    launch_pdl(k_pf_scatter<FI>, E, kPfThreads, 0, st, a, cls);
+    launch_pdl(k_pf_rank<FI>, E, kPfThreads, 0, st, a);
+    launch_pdl(k_pf_merge<FI>, E, kPfThreads, 0, st, a, cls);
+    launch_pdl(k_pf_scan_parts<SrcPst>, G, kPfScanThreads, 0, st, a);
+    launch_pdl(k_pf_scan_final<SrcPst>, G, kPfScanThreads, 0, st, a);
+    launch_pdl(k_pf_peaks<FI>, E, kPfThreads, 0, st, a, cls);
+    launch_pdl(k_pf_scan_parts<SrcKeep<FI>>, G, kPfScanThreads, 0, st, a);
+    launch_pdl(k_pf_scan_final<SrcKeep<FI>>, G, kPfScanThreads, 0, st, a);
+    launch_pdl(k_pf_stage<FI>, E, kPfThreads, 0, st, a, cls);
+}
+
+void launch_post_flat(const PostArgs& a, int cls, cudaStream_t st)
+{
+    if (a.n_struct <= 0 || !a.pf_voff) return;
+    if (a.If) launch_flat_fi<true>(a, cls, st);
+    else launch_flat_fi<false>(a, cls, st);
+}
+
+}  // namespace xrd

@@ -17,30 +17,32 @@ constexpr double kFScale = 41.78214;  // Mott-Bethe factor 8 pi^2 a0 of f(s) (Se
 constexpr int kZmaxLimit = 255;
 constexpr int kHklLimit = 511;        // |h|, |k|, |l| fit the 10-bit fields of the packed key
 // Post-processing size classes: structures with at most kPostCap[c] reflections
-// (held in shared memory) go to class c; larger ones to the last class (global
-// scratch). Threads per CTA: 64, 128, 256, 512, 1024, 1024.
-constexpr int kPostClasses = 6;
+// (held in shared memory, 35 B per reflection) go to class c, one CTA each with
+// 64, 128, 192, 256, 256, 512, 512 or 1024 threads; finer classes at the small
+// end keep the shared memory of a CTA close to what its structure needs, so
+// more structures are in flight per SM. Larger structures go to the last
+// class, processed by flat device-wide passes (k_post_flat.cu). Every class
+// runs on a stream of its own.
+constexpr int kPostClasses = 9;
 constexpr int kRunsPerTile = 32;  // structure-factor tile: one run of reflections per lane of a warp
-constexpr int kPostCap0 = 256, kPostCap1 = 512, kPostCap2 = 1536, kPostCap3 = 3072, kPostCap4 = 6144;
-// Structures of the last class above a size threshold run one thread-block cluster each
-// (k_post_big): above kPostBigMin reflections when the class holds at most one structure per eight
-// SMs (a few big structures would otherwise set the time), else above kPostBigMinMany (many big
-// structures keep every SM busy one CTA each, which has more throughput). At most kPostClusterMax
-// CTAs per cluster and kPostClustersMax clusters (each with a partial-result area in the
-// workspace); the kernel runs beside the others on a stream of its own.
-constexpr int kPostBigMin = 65536;
-constexpr int kPostBigMinMany = 262144;
-__host__ __device__ __forceinline__ int post_big_min(int class_count, int sms)
-{
-    return class_count * 8 <= sms ? kPostBigMin : kPostBigMinMany;
-}
-constexpr int kPostClusterMax = 16;
-constexpr int kPostClustersMax = 64;
-constexpr int kPostStreams = kPostClasses + 1;
+constexpr int kPostCap0 = 256, kPostCap1 = 512, kPostCap2 = 768, kPostCap3 = 1024, kPostCap4 = 1536,
+              kPostCap5 = 2048, kPostCap6 = 3072, kPostCap7 = 6144;
+constexpr int kPostFlatClass = kPostClasses - 1;
+constexpr int kPostStreams = kPostClasses;
 __host__ __device__ __forceinline__ int post_class(long long c)
 {
-    return c <= kPostCap0 ? 0 : c <= kPostCap1 ? 1 : c <= kPostCap2 ? 2 : c <= kPostCap3 ? 3 : c <= kPostCap4 ? 4 : 5;
+    return c <= kPostCap0   ? 0
+           : c <= kPostCap1 ? 1
+           : c <= kPostCap2 ? 2
+           : c <= kPostCap3 ? 3
+           : c <= kPostCap4 ? 4
+           : c <= kPostCap5 ? 5
+           : c <= kPostCap6 ? 6
+           : c <= kPostCap7 ? 7
+                            : 8;
 }
+// Flag words of a call (ints of the zeroed flags area): the class counts and the classes' work counters.
+constexpr int kFlagClsCnt = 32, kFlagClsNext = 48;
 
 // Per-structure geometry written by k_prep (step S0).
 struct Geo {

@@ -38,8 +38,8 @@ struct GeomArgs {
     int* atom_bad;   // [n_struct] 1 where an atom of the structure is invalid
     int atoms_set_geo;  // k_atoms also marks such structures invalid in geo (only when it runs before k_count)
     int* cls_list;   // [kPostClasses][n_struct] post-processing size classes (nullptr: not built)
-    int* abort_flag; // flags[0]; flags[1] output abort, flags[2] tile queue, flags[4..9] class counts,
-                     // flags[10..15] class work counters, flags[26..28] enumeration claims
+    int* abort_flag; // flags[0]; flags[1] output abort, flags[2] tile queue, flags[26..28] enumeration
+                     // claims, flags[kFlagClsCnt + c] class counts, flags[kFlagClsNext + c] class work counters
     int64_t* totals;
     int32_t* status;
     double* q;
@@ -117,7 +117,7 @@ struct RefineArgs {
 };
 
 struct PostArgs {
-    int n_struct, cap_smem, scaled, grid;  // grid = number of SMs
+    int n_struct, scaled, grid;  // grid = number of SMs
     double lambda, tol, cutoff, r2min, r2max;
     double l2d;                          // lambda^2 / 4
     const TTab* ttab;                    // 2-theta table (device)
@@ -132,7 +132,7 @@ struct PostArgs {
     const int* cls_list;  // [kPostClasses][n_struct] structures of each size class, largest first
     const int* cls_cnt;   // [kPostClasses]
     int* cls_next;        // [kPostClasses] work counters (zero at launch)
-    // global scratch for structures larger than cap_smem (indexed by reflection)
+    // scratch of the flat passes of the largest class (indexed by reflection)
     int* g_perm;
     int* g_bkt;   // n_refl + n_struct entries
     uint8_t* g_flag;
@@ -157,9 +157,24 @@ struct PostArgs {
     double* refl_tt;
     double* refl_I;
     float l2h, l2l;  // lambda^2 / 4 as two floats (2-theta of the list)
-    long long* cpart;  // [kPostClustersMax][2 kPostClusterMax] partial results of the cluster kernel (or nullptr)
-    int big;           // 1: the cluster kernel takes the last class's structures above post_big_min reflections
+    // the flat passes of the largest class (k_post_flat.cu)
+    int* pf_voff;                  // [n_struct + 1] virtual offsets of the class's structures
+    unsigned long long* pf_smax;   // [n_struct] bits of each structure's largest peak sum
+    int* pf_scal;                  // [4]: reflections of the class (V), its peaks
+    long long* pf_parts;           // [2 kPfScanBlocksMax] segment sums of the scans
+    int* pf_pst;                   // [reflections + 1] peak starts, then peak ids
+    int* pf_pj;                    // [reflections] structure (class-list position) of each peak
+    int* pf_kidx;                  // [reflections + 1] kept-peak index of each peak
+    int* pf_fidx;                  // [reflections + 1] family offset of each peak
+    double* pf_bq;                 // [reflections] records in bucket order: |g|^2,
+    uint32_t* pf_bk;               //   key,
+    double* pf_bI;                 //   intensity (FP32 in the low word for the FP32 variants),
+    int* pf_bb;                    //   bucket
+    double* pf_sq;                 // [reflections] the same records in sorted order: |g|^2,
+    uint32_t* pf_sk;               //   key,
+    double* pf_sI;                 //   intensity
 };
+constexpr int kPfScanBlocksMax = 1024;
 
 struct CompactArgs {
     int n_struct, grid;  // grid = number of SMs
@@ -250,8 +265,8 @@ void launch_sf(const SfArgs& a, cudaStream_t st, bool pdl);
 RefineTables init_refine_tables(cudaStream_t st);  // fills the tables, returns their device addresses
 void launch_refine(const RefineArgs& a, cudaStream_t st, bool pdl);
 size_t post_smem_bytes(int cap);
-void launch_post(const PostArgs& a, const cudaStream_t* st);  // st[kPostStreams]: a stream per class, then the clusters'
-bool launch_post_big(const PostArgs& a, int cls, cudaStream_t st);  // false: no cluster fits (use one CTA)
+void launch_post_flat(const PostArgs& a, int cls, cudaStream_t st);
+void launch_post(const PostArgs& a, const cudaStream_t* st);  // st[kPostStreams]: a stream per class
 void launch_compact(const CompactArgs& a, cudaStream_t st);
 const TTab* init_tables(cudaStream_t st);  // fills the 2-theta table, returns its device address
 size_t broaden_smem_bytes(int n_pts, int W);

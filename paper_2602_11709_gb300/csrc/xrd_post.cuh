@@ -1,6 +1,6 @@
 // Merge, family and sort-order helpers of the post-processing kernels (steps
-// S4-S5), shared by the one-CTA-per-structure kernel (k_post.cu) and the
-// cluster kernel for the largest structures (k_post_big.cu).
+// S4-S6), shared by the one-CTA-per-structure kernel (k_post.cu) and the flat
+// passes of the largest structures (k_post_flat.cu).
 #pragma once
 
 #include "xrd_internal.cuh"

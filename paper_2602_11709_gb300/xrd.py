@@ -24,8 +24,8 @@ STAGES = ["prep", "atoms", "count", "scan", "emit", "structure_factor", "refine"
 XRD_FLAG_HEXAGONAL = 1  # bit of the per-structure flag word: families by Miller-Bravais indices
 # kernels xrd_pattern_batch launches per call: order, coef, atoms (a side stream), prep, count, scan, emit,
 # structure factor, re-evaluation of weak reflections (selection and evaluation, FP32 variants), post
-# (six size classes and the cluster kernel of the largest structures), output scan, compaction
-LAUNCHES_PER_BATCH = 19
+# (eight shared-memory size classes and the 13 flat passes of the largest), output scan, compaction
+LAUNCHES_PER_BATCH = 33
 
 
 def launches_per_batch(n_struct: int, refine: bool = True) -> int:

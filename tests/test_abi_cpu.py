@@ -139,11 +139,11 @@ def test_missing_library_fails_loudly(tmp_path):
 
 
 def test_launch_count_per_call():
-    """Kernels per xrd_pattern_batch call: 19 with the two re-evaluation kernels of the FP32 variants
-    (17 without), three more above two chunks of 4096 structures (two-kernel order and scans)."""
-    assert xrd.launches_per_batch(1024) == 19 and xrd.launches_per_batch(8192) == 19
-    assert xrd.launches_per_batch(8193) == 22 and xrd.launches_per_batch(100_000) == 22
-    assert xrd.launches_per_batch(1024, refine=False) == 17 and xrd.launches_per_batch(8193, refine=False) == 20
+    """Kernels per xrd_pattern_batch call: 33 with the two re-evaluation kernels of the FP32 variants
+    (31 without), three more above two chunks of 4096 structures (two-kernel order and scans)."""
+    assert xrd.launches_per_batch(1024) == 33 and xrd.launches_per_batch(8192) == 33
+    assert xrd.launches_per_batch(8193) == 36 and xrd.launches_per_batch(100_000) == 36
+    assert xrd.launches_per_batch(1024, refine=False) == 31 and xrd.launches_per_batch(8193, refine=False) == 34
 
 
 def test_binding_argument_checks():
