@@ -347,7 +347,11 @@ __global__ void __launch_bounds__(kPfThreads) k_pf_merge(const PostArgs a, int c
 }
 
 // 5. per peak: start position, structure, merged intensity, family count; the
-// structure's largest peak sum (bits of a non-negative float or double)
+// structure's largest peak sum (bits of a non-negative float or double). The
+// lanes of a warp take consecutive positions; when they all lie in one
+// structure (the common case) the warp combines its maxima first and one lane
+// updates the structure's slot, so the slot sees one atomic per warp, not one
+// per peak.
 template <bool FI>
 __global__ void __launch_bounds__(kPfThreads) k_pf_peaks(const PostArgs a, int cls)
 {
@@ -355,42 +359,59 @@ __global__ void __launch_bounds__(kPfThreads) k_pf_peaks(const PostArgs a, int c
     if (*a.abort_flag) return;
     const int V = a.pf_scal[0], c5 = a.cls_cnt[cls];
     const int* __restrict__ list = a.cls_list + (int64_t)cls * a.n_struct;
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < V; p += gridDim.x * blockDim.x) {
-        if (!a.g_flag[p]) continue;
-        const int j = vowner(a.pf_voff, c5, p);
-        const int end = a.pf_voff[j + 1];
-        const bool hex = a.geo[list[j]].hex != 0;
-        const int k = a.pf_pst[p];
-        int e = p + 1;
-        while (e < end && !a.g_flag[e]) e++;
-        a.g_pstart[k] = p;
-        a.pf_pj[k] = j;
-        unsigned long long bits;
-        if (FI) {
-            const float* sI = (const float*)a.pf_sI;
-            float sum = 2.f * sI[p];
-            for (int i = p + 1; i < e; i++) sum = fmaf(2.f, sI[i], sum);
-            ((float*)a.g_psum)[k] = sum;
-            bits = __float_as_uint(sum);
-        } else {
-            double sum = 0.0;
-            for (int i = p; i < e; i++) sum += 2.0 * a.pf_sI[i];
-            a.g_psum[k] = sum;
-            bits = dbits(sum);
-        }
-        int nfam = 1;
-        if (e - p > 1) {  // distinct family keys among the members
-            nfam = 0;
-            for (int i = p; i < e; i++) {
-                const unsigned long long fk = family_key(a.pf_sk[i], hex);
-                bool lead = true;
-                for (int m = p; m < i && lead; m++) lead = family_key(a.pf_sk[m], hex) != fk;
-                nfam += lead;
+    const int lane = threadIdx.x & 31;
+    const int stride = gridDim.x * blockDim.x;
+    for (int p0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); p0 < V; p0 += stride) {  // warp-uniform
+        const int p = p0 + lane;
+        unsigned long long bits = 0ull;
+        int j = -1;
+        if (p < V && a.g_flag[p]) {
+            j = vowner(a.pf_voff, c5, p);
+            const int end = a.pf_voff[j + 1];
+            const bool hex = a.geo[list[j]].hex != 0;
+            const int k = a.pf_pst[p];
+            int e = p + 1;
+            while (e < end && !a.g_flag[e]) e++;
+            a.g_pstart[k] = p;
+            a.pf_pj[k] = j;
+            if (FI) {
+                const float* sI = (const float*)a.pf_sI;
+                float sum = 2.f * sI[p];
+                for (int i = p + 1; i < e; i++) sum = fmaf(2.f, sI[i], sum);
+                ((float*)a.g_psum)[k] = sum;
+                bits = __float_as_uint(sum);
+            } else {
+                double sum = 0.0;
+                for (int i = p; i < e; i++) sum += 2.0 * a.pf_sI[i];
+                a.g_psum[k] = sum;
+                bits = dbits(sum);
             }
+            int nfam = 1;
+            if (e - p > 1) {  // distinct family keys among the members
+                nfam = 0;
+                for (int i = p; i < e; i++) {
+                    const unsigned long long fk = family_key(a.pf_sk[i], hex);
+                    bool lead = true;
+                    for (int m = p; m < i && lead; m++) lead = family_key(a.pf_sk[m], hex) != fk;
+                    nfam += lead;
+                }
+            }
+            a.g_fcnt[k] = nfam;
         }
-        a.g_fcnt[k] = nfam;
-        unsigned long long* mx = a.pf_smax + j;
-        if (bits > *(volatile unsigned long long*)mx) atomicMax(mx, bits);
+        const unsigned act = __ballot_sync(0xffffffffu, j >= 0);
+        if (!act) continue;
+        const int j0 = __shfl_sync(0xffffffffu, j, __ffs(act) - 1);
+        if (__all_sync(0xffffffffu, j < 0 || j == j0)) {  // one structure: combine, then one atomic
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) bits = max(bits, __shfl_xor_sync(0xffffffffu, bits, o));
+            if (lane == 0) {
+                unsigned long long* mx = a.pf_smax + j0;
+                if (bits > *(volatile unsigned long long*)mx) atomicMax(mx, bits);
+            }
+        } else if (j >= 0) {
+            unsigned long long* mx = a.pf_smax + j;
+            if (bits > *(volatile unsigned long long*)mx) atomicMax(mx, bits);
+        }
     }
 }
 
