@@ -344,10 +344,26 @@ def measure_pattern(h, b, o, precision, dev, steps, warmup, flush, stream, tune=
             if k != "profile_sum":
                 acc[k] = acc.get(k, 0.0) + v / nst
     h.set_profiling(0)
+    # post-processing (sort, merge, families, cutoff, staging) and compaction against HBM: algorithmic
+    # bytes per Friedel-unique reflection (|g|^2, key, intensity read), per kept peak (staged |g|^2,
+    # intensity, family offset; compaction: those read, 2-theta, d, intensity, family offset written)
+    # and per family (hkl, multiplicity staged; compaction: read and written)
+    ib = 8 if precision == "fp64" else 4
+    npk, nfm = int(totals[1]), int(totals[2])
+    post_bytes = (12 + ib) * int(sz.n_refl) + 20 * npk + 16 * nfm
+    comp_bytes = (20 + 32) * npk + (16 + 16) * nfm
+    hbm = measured_hbm_gbs()
+    hbm_rec = {}
+    for stage, nbytes in (("post", post_bytes), ("compact", comp_bytes)):
+        t = acc.get(stage)
+        if t:
+            gbs = nbytes / (t / 1e3) / 1e9
+            hbm_rec[stage] = {"ms": t, "algorithmic_bytes": nbytes, "achieved_gbs": gbs, "hbm_frac": gbs / hbm[0],
+                              "peak_gbs": hbm[0], "peak_basis": hbm[1]}
     res = {"n_struct": b.n_struct, "ms_per_step": float(np.mean(ms)), "step_ms": ms, "terms_full": terms_full,
            "terms_eval": terms_eval, "n_refl": int(sz.n_refl), "refined": int(refined),
            "sf_ms": sf_ms, "refine_ms": ref_ms, "stage_ms": acc, "tuned": tuned, "seeds": w_seeds,
-           "f_evals": f_evals}
+           "f_evals": f_evals, "hbm_stages": hbm_rec}
     res["terms_per_s"] = terms_full / (res["ms_per_step"] / 1e3)
     res["patterns_per_s"] = b.n_struct / (res["ms_per_step"] / 1e3)
     runs = bool(tuned and tuned[2])
@@ -368,6 +384,16 @@ def measure_pattern(h, b, o, precision, dev, steps, warmup, flush, stream, tune=
     graph.close()
     graph1.close()
     return res, (db, co, sz)
+
+
+def measured_hbm_gbs():
+    """HBM copy bandwidth of the GB300s (MEASURED_PEAKS.json beside this file), else the
+    earlier single measurement used as the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback 6.8 TB/s"
 
 
 def d2h_ceiling(nbytes, dev):
@@ -475,7 +501,8 @@ def run_ours(args):
             rec = {"workload": WORKLOADS[name], "ms_per_step": rx["ms_per_step"], "terms_per_s": rx["terms_per_s"],
                    "patterns_per_s": rx["patterns_per_s"], "reflections_friedel_unique": rx["n_refl"],
                    "refined_reflections": rx["refined"], "sf_ms": rx["sf_ms"], "refine_ms": rx["refine_ms"],
-                   "stage_ms": rx["stage_ms"], "other_precisions": rx["other_precisions"],
+                   "stage_ms": rx["stage_ms"], "hbm_stages": rx["hbm_stages"],
+                   "other_precisions": rx["other_precisions"],
                    "sf_shape": {"tile": rx["tuned"][0], "warps": rx["tuned"][1], "runs_in_l": rx["tuned"][2]}
                    if rx["tuned"] else "default"}
             if "roofline" in rx:
@@ -531,6 +558,7 @@ def run_ours(args):
             "gpu_launches": xrd.launches_per_batch(b.n_struct, args.precision != "fp64") * args.steps,
             "stage_ms": main["stage_ms"],
             "stage_ms_note": "separate pass with events between all stages (adds time per stage)",
+            "hbm_stages": main["hbm_stages"],
             "other_precisions": main["other_precisions"],
         }
         if "fp64" in main["other_precisions"]:

@@ -335,6 +335,26 @@ int xrd_unit_rates(xrd_handle* h, double* rates);
  * with tile 128 and XRD_FP32_PHASEFIX only, makes lanes take runs consecutive in l). */
 int xrd_set_sf_shape(xrd_handle* h, int tile, int warps, int runs);
 
+/*
+ * Symmetry-aware family mode (the calculator interface of Sec. 2 groups the
+ * equivalent reflections of a peak into families): with n_ops > 0, the
+ * reflections of a merged peak are grouped by their orbits under the given
+ * point group instead of by permutation and sign of (h, k, l) (or of
+ * (h, k, i, l) for a hexagonal cell). ops: host array [n_ops][3][3] of
+ * integer matrices M acting on (h, k, l) as a column vector, entries -1, 0 or
+ * 1, n_ops <= 48 (any generating set's closure, e.g. the 48 operations of
+ * m-3m; Friedel's law adds the inversion by itself). The family of g is
+ * {M g, -M g}; its representative is still the lexicographically largest
+ * member present in the peak, and its multiplicity the number of members over
+ * the full sphere. For a structure with that symmetry, the multiplicities are
+ * the orbit sizes of International Tables. The operations are copied
+ * (synchronously) to the handle's device; n_ops = 0 restores the default. The
+ * mode applies to later xrd_query_sizes and xrd_pattern_batch calls on the
+ * handle (its workspace holds 16 more bytes per reflection) and adds two kernel
+ * launches per call.
+ */
+int xrd_set_point_group(xrd_handle* h, const int32_t* ops, int n_ops);
+
 /* Launch shape of the enumeration kernels (256 by default): 64, 128 or 256 threads per CTA
  * with one warp per structure (the CTA's whole block takes the few structures above 1024
  * columns or 4096 reflections), or 512 or 1024 threads with one CTA per structure.

@@ -24,7 +24,8 @@ _I16 = C.POINTER(C.c_int16)
 
 class Opts(C.Structure):
     _fields_ = [("lambda_", C.c_double), ("tt_min", C.c_double), ("tt_max", C.c_double),
-                ("tt_tol", C.c_double), ("cutoff", C.c_double), ("scaled", C.c_int)]
+                ("tt_tol", C.c_double), ("cutoff", C.c_double), ("scaled", C.c_int),
+                ("n_pg", C.c_int), ("pg", C.POINTER(C.c_int32))]
 
 
 class _Out(C.Structure):
@@ -79,9 +80,17 @@ def _p(a, t):
 
 
 def opts(o) -> Opts:
-    """Oracle options from any object with wavelength/tt_min/tt_max/tt_tol/rel_cutoff/scaled."""
-    return Opts(float(o.wavelength), float(o.tt_min), float(o.tt_max), float(o.tt_tol),
-                float(o.rel_cutoff), int(o.scaled))
+    """Oracle options from any object with wavelength/tt_min/tt_max/tt_tol/rel_cutoff/scaled and,
+    optionally, point_group: integer operations [n][3][3] on (h, k, l) (families by its orbits)."""
+    pg = getattr(o, "point_group", None)
+    if pg is None or len(pg) == 0:
+        return Opts(float(o.wavelength), float(o.tt_min), float(o.tt_max), float(o.tt_tol),
+                    float(o.rel_cutoff), int(o.scaled), 0, None)
+    arr = np.ascontiguousarray(np.asarray(pg, dtype=np.int32).reshape(-1, 3, 3))
+    oo = Opts(float(o.wavelength), float(o.tt_min), float(o.tt_max), float(o.tt_tol),
+              float(o.rel_cutoff), int(o.scaled), int(arr.shape[0]), arr.ctypes.data_as(C.POINTER(C.c_int32)))
+    oo._pg_arr = arr  # keeps the operations alive as long as the options
+    return oo
 
 
 def metric(lat):

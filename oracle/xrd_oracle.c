@@ -208,6 +208,30 @@ static void orc_family_key(int h, int k, int l, int hex, int key[4])
     for (int i = 0; i < 4; i++) key[i] = v[i];
 }
 
+/* Family key under a caller's point group (the symmetry-aware mode of the
+ * calculator-style interface, N3): the family of g is its orbit
+ * {M g, -M g : M in the group} (Friedel's law adds the inversion), and its key
+ * the lexicographically largest member of the orbit, padded with 0. */
+static void orc_family_key_pg(int h, int k, int l, int n_pg, const int32_t* pg, int key[4])
+{
+    int best[3] = {h, k, l};
+    if (-h > best[0] || (-h == best[0] && (-k > best[1] || (-k == best[1] && -l > best[2])))) {
+        best[0] = -h; best[1] = -k; best[2] = -l;
+    }
+    for (int m = 0; m < n_pg; m++) {
+        const int32_t* M = pg + 9 * m;
+        const int v[3] = {M[0] * h + M[1] * k + M[2] * l, M[3] * h + M[4] * k + M[5] * l,
+                          M[6] * h + M[7] * k + M[8] * l};
+        for (int sgn = 1; sgn >= -1; sgn -= 2) {
+            const int w[3] = {sgn * v[0], sgn * v[1], sgn * v[2]};
+            if (w[0] > best[0] || (w[0] == best[0] && (w[1] > best[1] || (w[1] == best[1] && w[2] > best[2])))) {
+                best[0] = w[0]; best[1] = w[1]; best[2] = w[2];
+            }
+        }
+    }
+    key[0] = best[0]; key[1] = best[1]; key[2] = best[2]; key[3] = 0;
+}
+
 /* Lexicographic comparison of signed (h, k, l) triples: >0 when a > b. */
 static int orc_lex(const int a[3], const int b[3])
 {
@@ -306,11 +330,12 @@ int orc_pattern(const double lat[6], long n, const double* frac, const int16_t* 
         out->peak_fam_off[nk] = nf;
 
         /* families: members equal up to permutation and sign of (h, k, l), or of
-         * (h, k, i, l) for a hexagonal cell */
+         * (h, k, i, l) for a hexagonal cell, or in one orbit of the caller's point group */
         long m = 0;
         for (long i = i0; i < start[p + 1]; i++) {
             int key[4], hv[3] = {r[i].h, r[i].k, r[i].l};
-            orc_family_key(hv[0], hv[1], hv[2], hex, key);
+            if (o->n_pg > 0) orc_family_key_pg(hv[0], hv[1], hv[2], o->n_pg, o->pg, key);
+            else orc_family_key(hv[0], hv[1], hv[2], hex, key);
             long f;
             for (f = 0; f < m; f++)
                 if (fkey[4 * f] == key[0] && fkey[4 * f + 1] == key[1] && fkey[4 * f + 2] == key[2] &&

@@ -32,6 +32,8 @@ typedef struct {
     double tt_tol;   /* merge tolerance, degrees */
     double cutoff;   /* keep peaks with I > cutoff * Imax; 0 keeps all */
     int scaled;      /* 1: scale intensities so that the largest is 100 */
+    int n_pg;        /* 0: families by permutation and sign (R5, R17); > 0: by the point group below */
+    const int32_t* pg; /* [n_pg][3][3] integer operations on (h, k, l) as a column vector */
 } orc_opts;
 
 /* Direct metric G and reciprocal metric Gs = G^-1; returns 0, or -1 for an invalid cell. */

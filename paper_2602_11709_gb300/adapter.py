@@ -42,6 +42,44 @@ WAVELENGTHS = {
 }
 
 
+# Generators of the Laue groups as operations on reflection indices (h, k, l) (column vector);
+# hexagonal and trigonal groups in hexagonal axes. laue_group_ops closes them under products
+# (with the inversion), giving the point group that xrd_set_point_group takes.
+_E = ((1, 0, 0), (0, 1, 0), (0, 0, 1))
+_C2B = ((-1, 0, 0), (0, 1, 0), (0, 0, -1))  # 2-fold about b (monoclinic unique axis b)
+_MX = ((-1, 0, 0), (0, 1, 0), (0, 0, 1))    # h -> -h
+_MY = ((1, 0, 0), (0, -1, 0), (0, 0, 1))    # k -> -k
+_C4 = ((0, -1, 0), (1, 0, 0), (0, 0, 1))    # 4-fold about c
+_SW = ((0, 1, 0), (1, 0, 0), (0, 0, 1))     # h <-> k
+_C3D = ((0, 0, 1), (1, 0, 0), (0, 1, 0))    # 3-fold about [111]
+_C6 = ((0, -1, 0), (1, 1, 0), (0, 0, 1))    # 6-fold about c, hexagonal axes: (h, k, l) -> (-k, h + k, l)
+_C3 = ((-1, -1, 0), (1, 0, 0), (0, 0, 1))   # 3-fold about c, hexagonal axes
+LAUE_GENERATORS = {
+    "-1": (), "2/m": (_C2B,), "mmm": (_MX, _MY), "4/m": (_C4,), "4/mmm": (_C4, _SW),
+    "-3": (_C3,), "-3m": (_C3, _SW), "6/m": (_C6,), "6/mmm": (_C6, _SW), "m-3": (_MX, _MY, _C3D),
+    "m-3m": (_C4, _C3D),
+}
+
+
+def laue_group_ops(name: str) -> np.ndarray:
+    """Operations [n][3][3] of a Laue group (a key of LAUE_GENERATORS): the closure of its
+    generators and the inversion under matrix products."""
+    gens = [np.array(g, dtype=np.int64) for g in LAUE_GENERATORS[name]] + [-np.eye(3, dtype=np.int64)]
+    ops = {tuple(np.eye(3, dtype=np.int64).ravel())}
+    frontier = [np.eye(3, dtype=np.int64)]
+    while frontier:
+        nxt = []
+        for m in frontier:
+            for g in gens:
+                p = g @ m
+                t = tuple(p.ravel())
+                if t not in ops:
+                    ops.add(t)
+                    nxt.append(p)
+        frontier = nxt
+    return np.array(sorted(ops), dtype=np.int32).reshape(-1, 3, 3)
+
+
 @dataclasses.dataclass
 class DiffractionPattern:
     x: np.ndarray        # 2-theta of each peak, degrees, ascending
@@ -124,11 +162,13 @@ class XRDCalculator:
     table, float64 [zmax + 1][4][2] of (a_i, b_i) in f(s) = Z - 41.78214 s^2 sum a_i exp(-b_i s^2).
     debye_waller_factors: {symbol: B in angstrom^2} (default 0). rel_cutoff: peaks at or below
     this fraction of the largest are dropped (0 keeps all); tt_tol: merge tolerance in degrees
-    (at least xrd.XRD_MIN_TT_TOL = 1e-9).
+    (at least xrd.XRD_MIN_TT_TOL = 1e-9). point_group: None (families by permutation and sign),
+    a Laue group name of LAUE_GENERATORS, or integer operations [n][3][3] on (h, k, l): families
+    are then the orbits of that group (xrd_set_point_group).
     """
 
     def __init__(self, coef, wavelength="CuKa", debye_waller_factors=None, precision="fp32_phasefix",
-                 rel_cutoff=1e-3, tt_tol=1e-5, handle=None, device=0):
+                 rel_cutoff=1e-3, tt_tol=1e-5, handle=None, device=0, point_group=None):
         self.wavelength = WAVELENGTHS[wavelength] if isinstance(wavelength, str) else float(wavelength)
         self.coef = np.ascontiguousarray(coef, dtype=np.float64)
         self.dw = dict(debye_waller_factors or {})
@@ -137,6 +177,8 @@ class XRDCalculator:
         self.tt_tol = float(tt_tol)
         self.device = device
         self._handle = handle
+        # symmetry-aware families: a Laue group name (laue_group_ops) or operations [n][3][3]
+        self.point_group = laue_group_ops(point_group) if isinstance(point_group, str) else point_group
 
     def _h(self):
         if self._handle is None:
@@ -149,6 +191,7 @@ class XRDCalculator:
         b = batch_of(structures, self.coef, self.dw)
         o = Opts(self.wavelength, float(two_theta_range[0]), float(two_theta_range[1]), self.tt_tol,
                  self.rel_cutoff, 1 if scaled else 0)
+        o.point_group = self.point_group
         res = xrd.compute(b, o, self.precision, handle=self._h(), device=self.device)
         return patterns_from(res)
 

@@ -32,6 +32,8 @@ struct xrd_handle {
     cudaEvent_t front = nullptr, order_done = nullptr, atoms_done = nullptr;
     unsigned long long* wbuf = nullptr;  // device [3]: xrd_work_counts result
     xrd::RefineTables rtab{};            // tables of the accurate re-evaluation on the handle's device
+    int8_t* pg = nullptr;                // device [kMaxPgOps][9]: the point group of the family mode
+    int npg = 0;                         // its operations (0: families by permutation and sign)
     int refine = 1;                      // re-evaluate weak reflections of the FP32 variants (xrd_set_refine)
 };
 
@@ -89,14 +91,14 @@ struct Layout {
         flags, coef32, atom32, atom64, astep, imax, cdd, atomr;
     size_t q, key, runs, I, Eb, cand_r, cand_s, g_perm, g_bkt, g_flag, g_pstart, g_psum, g_fcnt;
     size_t st_q, st_I, st_foff, st_hkl, st_mult;
-    size_t parts, oparts, pf, pf_sq, pf_sI;
+    size_t parts, oparts, pf, pf_sq, pf_sI, fkg, pf_sfk;
     size_t total;
 };
 
 // chunk sums of the multi-block scans: 9 words per chunk of 4096 structures
 size_t scan_parts_bytes(int64_t n) { return 8 * (3 + xrd::kPostClasses) * (size_t)((n + 4095) / 4096 + 1); }
 
-Layout layout(int64_t n, int64_t natoms, int zmax, int64_t R)
+Layout layout(int64_t n, int64_t natoms, int zmax, int64_t R, bool pg = false)
 {
     Layout L{};
     size_t o = 0;
@@ -144,6 +146,8 @@ Layout layout(int64_t n, int64_t natoms, int zmax, int64_t R)
     L.pf = take(4 * (n + 1) + 8 * n + 16 + 8 * 2 * xrd::kPfScanBlocksMax + 64);
     L.pf_sq = take(8 * R);  // sorted records of the flat post passes
     L.pf_sI = take(8 * R);
+    L.fkg = take(pg ? 8 * R : 0);    // family keys under the caller's point group (that mode only)
+    L.pf_sfk = take(pg ? 8 * R : 0);
     L.total = o;
     return L;
 }
@@ -206,15 +210,15 @@ int64_t refl_capacity_grad(int64_t n, int64_t natoms, int zmax, size_t ws_bytes)
 }
 
 // Largest reflection capacity whose layout fits in ws_bytes.
-int64_t refl_capacity(int64_t n, int64_t natoms, int zmax, size_t ws_bytes)
+int64_t refl_capacity(int64_t n, int64_t natoms, int zmax, size_t ws_bytes, bool pg = false)
 {
-    const size_t fixed = layout(n, natoms, zmax, 0).total;
+    const size_t fixed = layout(n, natoms, zmax, 0, pg).total;
     if (ws_bytes < fixed) return -1;
     // layout(R).total grows with R: binary search for the largest R that fits
     int64_t lo = 0, hi = (int64_t)((ws_bytes - fixed) / 64) + 1;
     while (hi - lo > 1) {
         const int64_t mid = lo + (hi - lo) / 2;
-        if (layout(n, natoms, zmax, mid).total <= ws_bytes) lo = mid;
+        if (layout(n, natoms, zmax, mid, pg).total <= ws_bytes) lo = mid;
         else hi = mid;
     }
     return lo;
@@ -390,6 +394,7 @@ void xrd_destroy(xrd_handle* h)
         if (ev) cudaEventDestroy(ev);
     if (h->qbuf) cudaFree(h->qbuf);
     if (h->wbuf) cudaFree(h->wbuf);
+    if (h->pg) cudaFree(h->pg);
     delete h;
 }
 
@@ -495,7 +500,7 @@ int xrd_query_sizes(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, xrd_si
     const int64_t n = b->n_struct;
     memset(sizes, 0, sizeof(*sizes));
     if (n == 0) {
-        sizes->ws_bytes = layout(0, b->n_atoms, b->zmax, 0).total;
+        sizes->ws_bytes = layout(0, b->n_atoms, b->zmax, 0, h->npg > 0).total;
         sizes->ws_grad_bytes = layout_grad(0, b->n_atoms, b->zmax, 0).total;
         return XRD_OK;
     }
@@ -510,7 +515,7 @@ int xrd_query_sizes(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, xrd_si
     sizes->n_refl = tot;
     sizes->max_refl = mx;
     sizes->n_tiles = tiles;
-    sizes->ws_bytes = layout(n, b->n_atoms, b->zmax, tot).total;
+    sizes->ws_bytes = layout(n, b->n_atoms, b->zmax, tot, h->npg > 0).total;
     sizes->ws_grad_bytes = layout_grad(n, b->n_atoms, b->zmax, tot).total;
     return XRD_OK;
 }
@@ -537,12 +542,13 @@ int xrd_pattern_batch(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, cons
             return fail(h, XRD_EINVAL, "a per-reflection output pointer is NULL");
     }
     if (!workspace || ((uintptr_t)workspace & 255)) return fail(h, XRD_EINVAL, "workspace must be 256-byte aligned");
-    const int64_t cap_refl = refl_capacity(n, b->n_atoms, b->zmax, ws_bytes);
+    const bool pg = h->npg > 0;
+    const int64_t cap_refl = refl_capacity(n, b->n_atoms, b->zmax, ws_bytes, pg);
     if (cap_refl < 0) return fail(h, XRD_ECAPACITY, "workspace smaller than the per-structure part");
     DeviceGuard g(h->device);
     cudaStream_t st = (cudaStream_t)stream;
     char* ws = (char*)workspace;
-    const Layout L = layout(n, b->n_atoms, b->zmax, cap_refl);
+    const Layout L = layout(n, b->n_atoms, b->zmax, cap_refl, pg);
     int rb, warps, runs;
     sf_shape(h, o, rb, warps, runs);
     xrd::GeomArgs ga = geom_args(b, o, L, ws, cap_refl, out->totals, out->status, rb);
@@ -721,12 +727,19 @@ int xrd_pattern_batch(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, cons
         pa.pf_sk = (uint32_t*)(ws + L.g_perm);
         pa.pf_sI = (double*)(ws + L.pf_sI);
     }
+    if (pg) {
+        pa.pg = h->pg;
+        pa.npg = h->npg;
+        pa.fkg = (const unsigned long long*)(ws + L.fkg);
+        pa.pf_sfk = (unsigned long long*)(ws + L.pf_sfk);
+    }
     if (out->refl_off && out->cap_refl > 0) {
         pa.cap_refl = out->cap_refl;
         pa.refl_hkl = out->refl_hkl;
         pa.refl_tt = out->refl_tt;
         pa.refl_I = out->refl_I;
     }
+    if (pg) xrd::launch_pg_keys(pa, (unsigned long long*)(ws + L.fkg), st);
     {  // the size classes run concurrently: fork to the side streams, join back
         cudaStream_t cs[xrd::kPostStreams] = {st};
         cudaEventRecord(h->fork, st);
@@ -768,6 +781,28 @@ int xrd_pattern_batch(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, cons
     h->recorded = prof;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(h, e, "xrd_pattern_batch launch");
+    return XRD_OK;
+}
+
+int xrd_set_point_group(xrd_handle* h, const int32_t* ops, int n_ops)
+{
+    if (!h) return XRD_EINVAL;
+    h->err.clear();
+    if (n_ops < 0 || n_ops > xrd::kMaxPgOps) return fail(h, XRD_EINVAL, "a point group has 0 to 48 operations");
+    if (n_ops > 0 && !ops) return fail(h, XRD_EINVAL, "point-group operations are NULL");
+    int8_t host[xrd::kMaxPgOps * 9] = {};
+    for (int i = 0; i < 9 * n_ops; i++) {
+        if (ops[i] < -1 || ops[i] > 1) return fail(h, XRD_EINVAL, "point-group matrix entries must be -1, 0 or 1");
+        host[i] = (int8_t)ops[i];
+    }
+    DeviceGuard g(h->device);
+    if (!h->pg) {
+        cudaError_t e = cudaMalloc(&h->pg, sizeof(host));
+        if (e != cudaSuccess) return cuda_fail(h, e, "xrd_set_point_group: cudaMalloc");
+    }
+    cudaError_t e = cudaMemcpy(h->pg, host, sizeof(host), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(h, e, "xrd_set_point_group: cudaMemcpy");
+    h->npg = n_ops;
     return XRD_OK;
 }
 

@@ -137,6 +137,11 @@ __device__ void post_structure(const PostArgs& a, int s, int64_t base, int n, co
     const float l2 = a.l2f, lh = a.lhf, ttol = a.ttol;
     const double lam = a.lambda, tol = a.tol;
     const bool hex = a.geo[s].hex != 0;  // Miller-Bravais families
+    // family key of the member at merge position i: the caller's point group (precomputed per
+    // reflection), else permutation and sign (Miller-Bravais for a hexagonal cell)
+    auto fk = [&](int i) -> unsigned long long {
+        return a.fkg ? a.fkg[base + perm[i]] : family_key(key[perm[i]], hex);
+    };
     // ---- bucket sort on |g|^3 in [r2min^1.5, r2max^1.5] (a monotone map of |g|^2) ----
     // fcnt holds each reflection's bucket and pst the bucket-ordered reflections
     // until the merge step needs them.
@@ -233,7 +238,7 @@ __device__ void post_structure(const PostArgs& a, int s, int64_t base, int n, co
             float sum = 2.f * Ig[perm[i0]];
             for (int i = i0 + 1; i < i1; i++) sum = fmaf(2.f, Ig[perm[i]], sum);
             ps[p] = sum;
-            fcnt[p] = i1 - i0 == 1 ? 1 : count_families(key, perm, i0, i1, hex);
+            fcnt[p] = i1 - i0 == 1 ? 1 : count_families(fk, i0, i1);
             lmax = max(lmax, (unsigned long long)__float_as_uint(sum));
         }
         imaxf = __uint_as_float((uint32_t)block_max_u64(lmax, (unsigned long long*)dtmp));
@@ -253,7 +258,7 @@ __device__ void post_structure(const PostArgs& a, int s, int64_t base, int n, co
             double sum = 0.0;
             for (int i = i0; i < i1; i++) sum += 2.0 * Ig[perm[i]];
             psum[p] = sum;
-            fcnt[p] = i1 - i0 == 1 ? 1 : count_families(key, perm, i0, i1, hex);
+            fcnt[p] = i1 - i0 == 1 ? 1 : count_families(fk, i0, i1);
             lmax = max(lmax, dbits(sum));
         }
         imax = __longlong_as_double((long long)block_max_u64(lmax, (unsigned long long*)dtmp));
@@ -296,24 +301,24 @@ __device__ void post_structure(const PostArgs& a, int s, int64_t base, int n, co
         }
         // families: leaders are first members of each family; rank by descending representative
         for (int i = i0; i < i1; i++) {
-            const unsigned long long fk = family_key(key[perm[i]], hex);
+            const unsigned long long fi = fk(i);
             bool lead = true;
-            for (int j = i0; j < i && lead; j++) lead = family_key(key[perm[j]], hex) != fk;
+            for (int j = i0; j < i && lead; j++) lead = fk(j) != fi;
             if (!lead) continue;
             uint32_t rep = 0;
             int cnt = 0;
             for (int j = i0; j < i1; j++)
-                if (family_key(key[perm[j]], hex) == fk) { rep = max(rep, key[perm[j]]); cnt++; }
+                if (fk(j) == fi) { rep = max(rep, key[perm[j]]); cnt++; }
             int rank = 0;
             for (int m = i0; m < i1; m++) {  // other leaders with a larger representative
-                const unsigned long long fm = family_key(key[perm[m]], hex);
-                if (fm == fk) continue;
+                const unsigned long long fm = fk(m);
+                if (fm == fi) continue;
                 bool lm = true;
-                for (int j = i0; j < m && lm; j++) lm = family_key(key[perm[j]], hex) != fm;
+                for (int j = i0; j < m && lm; j++) lm = fk(j) != fm;
                 if (!lm) continue;
                 uint32_t rm = 0;
                 for (int j = i0; j < i1; j++)
-                    if (family_key(key[perm[j]], hex) == fm) rm = max(rm, key[perm[j]]);
+                    if (fk(j) == fm) rm = max(rm, key[perm[j]]);
                 rank += rm > rep;
             }
             const int64_t fo = base + fcnt[p] + rank;
@@ -621,6 +626,22 @@ static void launch_post_fi(const PostArgs& a, const cudaStream_t* st)
     launch_post_class<kPostCap2, 192, FI>(a, 2, st[2]);
     launch_post_class<kPostCap1, 128, FI>(a, 1, st[1]);
     launch_post_class<kPostCap0, 64, FI>(a, 0, st[0]);
+}
+
+// With a caller's point group: the family key of every reflection of the batch
+// (once per call; the post kernels then compare keys instead of forming orbits).
+__global__ void __launch_bounds__(256) k_pg_keys(const PostArgs a, unsigned long long* __restrict__ fkg)
+{
+    pdl_enter();
+    if (*a.abort_flag) return;
+    const int64_t total = a.refl_off[a.n_struct];
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < total; r += (int64_t)gridDim.x * blockDim.x)
+        fkg[r] = pg_family_key(a.key[r], a.pg, a.npg);
+}
+
+void launch_pg_keys(const PostArgs& a, unsigned long long* fkg, cudaStream_t st)
+{
+    if (a.n_struct > 0 && fkg) launch_pdl(k_pg_keys, a.grid * 8, 256, 0, st, a, fkg);
 }
 
 // a.grid = number of SMs

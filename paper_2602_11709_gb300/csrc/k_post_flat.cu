@@ -302,6 +302,16 @@ __global__ void __launch_bounds__(kPfThreads) k_pf_rank(const PostArgs a)
     }
 }
 
+// 3c. with a caller's point group: the family key of every sorted record
+__global__ void __launch_bounds__(kPfThreads) k_pf_pgkeys(const PostArgs a)
+{
+    pdl_enter();
+    if (*a.abort_flag) return;
+    const int V = a.pf_scal[0];
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < V; p += gridDim.x * blockDim.x)
+        a.pf_sfk[p] = pg_family_key(a.pf_sk[p], a.pg, a.npg);
+}
+
 // 4. anchor merge (and the caller's per-reflection list in merge order): pf_pst
 // and g_flag mark the peak starts
 template <bool FI>
@@ -389,12 +399,10 @@ __global__ void __launch_bounds__(kPfThreads) k_pf_peaks(const PostArgs a, int c
             int nfam = 1;
             if (e - p > 1) {  // distinct family keys among the members
                 nfam = 0;
-                for (int i = p; i < e; i++) {
-                    const unsigned long long fk = family_key(a.pf_sk[i], hex);
-                    bool lead = true;
-                    for (int m = p; m < i && lead; m++) lead = family_key(a.pf_sk[m], hex) != fk;
-                    nfam += lead;
-                }
+                auto fk = [&](int i) -> unsigned long long {
+                    return a.pf_sfk ? a.pf_sfk[i] : family_key(a.pf_sk[i], hex);
+                };
+                nfam = count_families(fk, p, e);
             }
             a.g_fcnt[k] = nfam;
         }
@@ -466,28 +474,29 @@ __global__ void __launch_bounds__(kPfThreads) k_pf_stage(const PostArgs a, int c
         }
         const bool hex = a.geo[s].hex != 0;
         auto kf = [&](int i) { return a.pf_sk[i]; };
+        auto fkf = [&](int i) -> unsigned long long { return a.pf_sfk ? a.pf_sfk[i] : family_key(kf(i), hex); };
         for (int i = i0; i < i1; i++) {  // families, ranked by descending representative
-            const unsigned long long fk = family_key(kf(i), hex);
+            const unsigned long long fk = fkf(i);
             bool lead = true;
-            for (int jj = i0; jj < i && lead; jj++) lead = family_key(kf(jj), hex) != fk;
+            for (int jj = i0; jj < i && lead; jj++) lead = fkf(jj) != fk;
             if (!lead) continue;
             uint32_t rep = 0;
             int cnt = 0;
             for (int jj = i0; jj < i1; jj++)
-                if (family_key(kf(jj), hex) == fk) {
+                if (fkf(jj) == fk) {
                     rep = max(rep, kf(jj));
                     cnt++;
                 }
             int rank = 0;
             for (int mm = i0; mm < i1; mm++) {
-                const unsigned long long fm = family_key(kf(mm), hex);
+                const unsigned long long fm = fkf(mm);
                 if (fm == fk) continue;
                 bool lm = true;
-                for (int jj = i0; jj < mm && lm; jj++) lm = family_key(kf(jj), hex) != fm;
+                for (int jj = i0; jj < mm && lm; jj++) lm = fkf(jj) != fm;
                 if (!lm) continue;
                 uint32_t rm = 0;
                 for (int jj = i0; jj < i1; jj++)
-                    if (family_key(kf(jj), hex) == fm) rm = max(rm, kf(jj));
+                    if (fkf(jj) == fm) rm = max(rm, kf(jj));
                 rank += rm > rep;
             }
             const int64_t fo = rb + fo0 + rank;
@@ -510,6 +519,7 @@ static void launch_flat_fi(const PostArgs& a, int cls, cudaStream_t st)
     launch_pdl(k_pf_scan_final<SrcBkt>, G, kPfScanThreads, 0, st, a);
     launch_pdl(k_pf_scatter<FI>, E, kPfThreads, 0, st, a, cls);
     launch_pdl(k_pf_rank<FI>, E, kPfThreads, 0, st, a);
+    if (a.pf_sfk) launch_pdl(k_pf_pgkeys, E, kPfThreads, 0, st, a);
     launch_pdl(k_pf_merge<FI>, E, kPfThreads, 0, st, a, cls);
     launch_pdl(k_pf_scan_parts<SrcPst>, G, kPfScanThreads, 0, st, a);
     launch_pdl(k_pf_scan_final<SrcPst>, G, kPfScanThreads, 0, st, a);

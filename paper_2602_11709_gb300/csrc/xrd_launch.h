@@ -173,7 +173,14 @@ struct PostArgs {
     double* pf_sq;                 // [reflections] the same records in sorted order: |g|^2,
     uint32_t* pf_sk;               //   key,
     double* pf_sI;                 //   intensity
+    // the symmetry-aware family mode: the caller's point group (nullptr, 0: permutation and sign)
+    const int8_t* pg;              // [npg][3][3] operations on (h, k, l), entries in {-1, 0, 1}
+    int npg;
+    const unsigned long long* fkg; // [reflections] family key of every reflection under pg (or nullptr)
+    unsigned long long* pf_sfk;    // [reflections] the same for the sorted records of the flat passes
 };
+constexpr int kMaxPgOps = 48;
+void launch_pg_keys(const PostArgs& a, unsigned long long* fkg, cudaStream_t st);
 constexpr int kPfScanBlocksMax = 1024;
 
 struct CompactArgs {

@@ -62,15 +62,39 @@ static __device__ __forceinline__ unsigned long long family_key(uint32_t key, bo
            (unsigned long long)v3;
 }
 
-// number of distinct families among the members i0..i1-1 of one peak
-template <typename PermT>
-static __device__ __forceinline__ int count_families(const uint32_t* key, const PermT* perm, int i0, int i1, bool hex)
+// Family key under a caller's point group (the symmetry-aware mode): the family
+// of g is its orbit {M g, -M g} over the group's operations M (Friedel's law adds
+// the inversion); the key is the orbit's lexicographically largest member,
+// packed in 12-bit fields (operations have entries in {-1, 0, 1}, so an image of
+// an index within +-511 stays within +-1533).
+static __device__ __forceinline__ unsigned long long pg_pack(int a, int b, int c)
+{
+    return ((unsigned long long)(a + 2048) << 24) | ((unsigned long long)(b + 2048) << 12) |
+           (unsigned long long)(c + 2048);
+}
+static __device__ __forceinline__ unsigned long long pg_family_key(uint32_t key, const int8_t* __restrict__ ops,
+                                                                   int n)
+{
+    const int h = hkl_h(key), k = hkl_k(key), l = hkl_l(key);
+    unsigned long long best = max(pg_pack(h, k, l), pg_pack(-h, -k, -l));
+    for (int m = 0; m < n; m++) {
+        const int8_t* M = ops + 9 * m;
+        const int x = M[0] * h + M[1] * k + M[2] * l, y = M[3] * h + M[4] * k + M[5] * l,
+                  z = M[6] * h + M[7] * k + M[8] * l;
+        best = max(best, max(pg_pack(x, y, z), pg_pack(-x, -y, -z)));
+    }
+    return best;
+}
+
+// number of distinct families among the members i0..i1-1 of one peak; fk(i): the family key of member i
+template <typename FK>
+static __device__ __forceinline__ int count_families(FK fk, int i0, int i1)
 {
     int nfam = 0;
     for (int i = i0; i < i1; i++) {
-        const unsigned long long fk = family_key(key[perm[i]], hex);
+        const unsigned long long k = fk(i);
         bool lead = true;
-        for (int j = i0; j < i && lead; j++) lead = family_key(key[perm[j]], hex) != fk;
+        for (int j = i0; j < i && lead; j++) lead = fk(j) != k;
         nfam += lead;
     }
     return nfam;

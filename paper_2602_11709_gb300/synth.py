@@ -84,6 +84,7 @@ class Opts:
     tt_tol: float = 1e-5
     rel_cutoff: float = 1e-3
     scaled: int = 1
+    point_group: object = None  # operations [n][3][3] on (h, k, l): families by its orbits (None: default)
 
 
 def coef_table(rng: np.random.Generator, zmax: int = ZMAX) -> np.ndarray:

@@ -74,7 +74,7 @@ EXPORTS = ["xrd_create", "xrd_destroy", "xrd_last_error", "xrd_query_sizes", "xr
            "xrd_set_profiling", "xrd_stage_times", "xrd_pattern_batch_noalloc", "xrd_pattern_broadened",
            "xrd_pattern_grad", "xrd_autotune", "xrd_set_sf_shape", "xrd_graph_create", "xrd_graph_launch",
            "xrd_graph_destroy", "xrd_work_counts", "xrd_set_enum_threads", "xrd_pattern_augmented",
-           "xrd_set_refine", "xrd_unit_rates", "xrd_reflection_counts"]
+           "xrd_set_refine", "xrd_unit_rates", "xrd_reflection_counts", "xrd_set_point_group"]
 
 _lib = None
 
@@ -125,6 +125,8 @@ def load(path: str = LIB_PATH):
     L.xrd_work_counts.argtypes = [C.c_void_p, C.POINTER(xrd_batch), C.c_void_p, C.c_void_p, C.POINTER(C.c_int64)]
     L.xrd_work_counts.restype = C.c_int
     L.xrd_set_enum_threads.argtypes = [C.c_void_p, C.c_int]
+    L.xrd_set_point_group.argtypes = [C.c_void_p, C.c_void_p, C.c_int]
+    L.xrd_set_point_group.restype = C.c_int
     L.xrd_set_enum_threads.restype = C.c_int
     L.xrd_set_refine.argtypes = [C.c_void_p, C.c_int]
     L.xrd_set_refine.restype = C.c_int
@@ -576,6 +578,15 @@ class Handle:
         """Re-evaluation of weak reflections of the FP32 variants (on by default; off is a diagnostic)."""
         self._check(self.lib.xrd_set_refine(self.h, int(bool(enabled))))
 
+    def set_point_group(self, ops=None):
+        """Families by the orbits of a point group: integer operations [n][3][3] (entries -1, 0, 1) acting
+        on (h, k, l) as a column vector, n <= 48; None or [] restores permutation and sign."""
+        if ops is None or len(ops) == 0:
+            self._check(self.lib.xrd_set_point_group(self.h, None, 0))
+            return
+        arr = np.ascontiguousarray(np.asarray(ops, dtype=np.int32).reshape(-1, 3, 3))
+        self._check(self.lib.xrd_set_point_group(self.h, arr.ctypes.data, int(arr.shape[0])))
+
     def set_enum_threads(self, threads: int):
         self._check(self.lib.xrd_set_enum_threads(self.h, int(threads)))
 
@@ -637,6 +648,7 @@ def compute(batch, opts, precision="fp32_phasefix", handle: Handle = None, devic
     also the per-reflection list)."""
     torch = _torch()
     h = handle or Handle(device)
+    h.set_point_group(getattr(opts, "point_group", None))  # the options' point group, or none
     dev = "cuda:%d" % device
     db = DeviceBatch.from_host(batch, dev)
     o = make_opts(opts, precision)

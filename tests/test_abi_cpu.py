@@ -125,6 +125,7 @@ def test_null_handle_arguments(lib):
     assert lib.xrd_pattern_batch(None, None, None, None, None, 0, None) == xrd.XRD_EINVAL
     assert lib.xrd_set_profiling(None, 1) == xrd.XRD_EINVAL
     assert lib.xrd_set_refine(None, 1) == xrd.XRD_EINVAL
+    assert lib.xrd_set_point_group(None, None, 0) == xrd.XRD_EINVAL
     lib.xrd_destroy(None)
 
 
