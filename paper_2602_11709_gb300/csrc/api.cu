@@ -627,7 +627,9 @@ int xrd_pattern_batch(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, cons
     sa.F = nullptr;
     if (refine) {
         sa.Eb = (float*)(ws + L.Eb);
+        sa.Es = (int*)(ws + L.g_fcnt);  // free until the post-processing
         sa.eps_k = kRefineEpsK;
+        sa.tau = kRefineTau;
         sa.imax = ga.imax;
     }
     xrd::launch_sf(sa, st, false);
@@ -653,6 +655,7 @@ int xrd_pattern_batch(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, cons
         ra.key = ga.key;
         ra.If = sa.If;
         ra.Eb = sa.Eb;
+        ra.Es = sa.Es;
         ra.imax = ga.imax;
         ra.atomr = ga.atomr;
         ra.cdd = ga.cdd;

@@ -138,96 +138,59 @@ __device__ void refine_one(const RefineArgs& a, int64_t r, int s, const float4* 
     }
 }
 
-// largest s in [lo, n) with off[s] <= i, for off[lo] <= i < off[n]
-__device__ __forceinline__ int refl_owner(const int64_t* __restrict__ off, int lo, int n, int64_t i)
-{
-    int hi = n;
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (off[mid] <= i) lo = mid;
-        else hi = mid;
-    }
-    return lo;
-}
 
-// Selection: every CTA takes one contiguous range of the batch's reflections
-// in chunks of 1024, four consecutive reflections per thread. The offsets of
-// the structures a chunk can touch are staged in shared memory (a window of
-// 128 structures from the chunk's first), so each thread finds its
-// structure by bisection there (in global memory only past the window). Flagged
-// reflections are appended to the candidate list, one atomic per warp.
-constexpr int kRefItems = 4;
-constexpr int kRefChunk = kRefThreads * kRefItems;
-constexpr int kRefWindow = 128;
+// Selection: one streaming pass over the reflections (error bound and
+// intensity, 8 bytes each). Every candidate has E > tau I (the criterion is
+// E > tau max(I, c M)); for those few the structure-factor kernel has noted the
+// structure, whose floor c M decides. Candidates are appended with one atomic
+// per warp.
+__device__ __forceinline__ bool refine_take(const RefineArgs& a, int64_t r, float E, float I, int& s)
+{
+    if (!(E > 0.f && E > a.tau * I)) return false;
+    s = a.Es[r];
+    const float floorI = a.cref * __uint_as_float(a.imax[s]);
+    const bool bad = a.atom_bad && a.atom_bad[s];
+    return !bad && E > a.tau * fmaxf(I, floorI);
+}
 
 __global__ void __launch_bounds__(kRefThreads) k_refine_select(const RefineArgs a)
 {
     pdl_enter();
-    __shared__ int64_t woff[kRefWindow + 1];
-    __shared__ int s_cur;
     if (*a.abort_flag) return;
-    const int n = a.n_struct;
-    const int64_t total = a.refl_off[n];
-    const int64_t nch = (total + kRefChunk - 1) / kRefChunk;
-    const int64_t per = (nch + gridDim.x - 1) / gridDim.x;
-    const int64_t c_begin = (int64_t)blockIdx.x * per, c_end = min(c_begin + per, nch);
-    if (c_begin >= c_end) return;
-    if (threadIdx.x == 0) s_cur = refl_owner(a.refl_off, 0, n, c_begin * kRefChunk);
+    const int64_t total = a.refl_off[a.n_struct];
     const int lane = threadIdx.x & 31;
-    for (int64_t c = c_begin; c < c_end; c++) {
-        const int64_t r0 = c * kRefChunk;
-        __syncthreads();  // s_cur is set; the previous chunk is done with the window
-        const int sb = s_cur;
-        for (int i = threadIdx.x; i <= kRefWindow; i += kRefThreads) woff[i] = a.refl_off[min(sb + i, n)];
-        __syncthreads();
-        const int64_t rt = r0 + (int64_t)kRefItems * threadIdx.x;  // this thread's first reflection
-        int k = 0;  // largest k < kRefWindow with woff[k] <= rt, if the window reaches rt
-        int s;
-        if (rt < woff[kRefWindow]) {
-            int lo = 0, hi = kRefWindow;
-            while (hi - lo > 1) {
-                const int mid = (lo + hi) >> 1;
-                if (woff[mid] <= rt) lo = mid;
-                else hi = mid;
-            }
-            k = lo;
-            s = sb + k;
+    // a warp takes 128 consecutive reflections at a time, four per lane in one 16-byte load of each
+    // array (both 256-byte aligned), so that several loads are in flight per thread
+    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t b0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 128; b0 < total; b0 += nwarp * 128) {
+        const int64_t r4 = b0 + 4 * lane;
+        float E[4] = {0.f, 0.f, 0.f, 0.f}, I[4] = {0.f, 0.f, 0.f, 0.f};
+        if (r4 + 4 <= total) {
+            const float4 e4 = *reinterpret_cast<const float4*>(a.Eb + r4);
+            const float4 i4 = *reinterpret_cast<const float4*>(a.If + r4);
+            E[0] = e4.x; E[1] = e4.y; E[2] = e4.z; E[3] = e4.w;
+            I[0] = i4.x; I[1] = i4.y; I[2] = i4.z; I[3] = i4.w;
         } else {
-            s = rt < total ? refl_owner(a.refl_off, min(sb + kRefWindow, n - 1), n, rt) : n - 1;
+            for (int j = 0; j < 4; j++)
+                if (r4 + j < total) {
+                    E[j] = a.Eb[r4 + j];
+                    I[j] = a.If[r4 + j];
+                }
         }
-        if (threadIdx.x == kRefThreads - 1) {  // next chunk's first structure: this thread's last reflection's
-            int sl = s;
-            const int64_t rl = min(rt + kRefItems, total) - 1;
-            while (sl + 1 < n && a.refl_off[sl + 1] <= rl) sl++;
-            s_cur = sl;
-        }
-        int64_t cr[kRefItems];
-        int cs[kRefItems];
-        int nf = 0;
 #pragma unroll
-        for (int u = 0; u < kRefItems; u++) {
-            const int64_t r = rt + u;
-            if (r >= total) break;
-            while (a.refl_off[s + 1] <= r) s++;  // at most a few steps: four consecutive reflections
-            const float I = a.If[r], E = a.Eb[r];
-            const float floorI = a.cref * __uint_as_float(a.imax[s]);
-            const bool bad = a.atom_bad && a.atom_bad[s];
-            if (!bad && E > 0.f && E > a.tau * fmaxf(I, floorI)) {
-                cr[nf] = r;
-                cs[nf] = s;
-                nf++;
+        for (int j = 0; j < 4; j++) {
+            int s = 0;
+            const bool take = r4 + j < total && refine_take(a, r4 + j, E[j], I[j], s);
+            const unsigned m = __ballot_sync(0xffffffffu, take);
+            if (!m) continue;
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(a.nref, (unsigned long long)__popc(m));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (take) {
+                const unsigned long long o = base + __popc(m & ((1u << lane) - 1u));
+                a.cand_r[o] = r4 + j;
+                a.cand_s[o] = s;
             }
-        }
-        // append: one atomic per warp
-        const int incl = warp_incl_scan(nf);
-        const int wtot = __shfl_sync(0xffffffffu, incl, 31);
-        unsigned long long base = 0;
-        if (lane == 31 && wtot > 0) base = atomicAdd(a.nref, (unsigned long long)wtot);
-        base = __shfl_sync(0xffffffffu, base, 31);
-        for (int i = 0; i < nf; i++) {
-            const unsigned long long o = base + (unsigned long long)(incl - nf + i);
-            a.cand_r[o] = cr[i];
-            a.cand_s[o] = cs[i];
         }
     }
 }
@@ -269,7 +232,7 @@ void launch_refine(const RefineArgs& a, cudaStream_t st, bool pdl)
             per_sm_cache[dev][1] = per_ev;
         }
     }
-    // every selection CTA takes a contiguous range of the reflections; the evaluation grid is persistent
+    // grid-stride selection over the reflections; the evaluation grid is persistent
     if (pdl) launch_pdl(k_refine_select, a.grid * per_sel, kRefThreads, 0, st, a);
     else k_refine_select<<<a.grid * per_sel, kRefThreads, 0, st>>>(a);
     launch_pdl(k_refine_eval, a.grid * per_ev, kRefThreads, 0, st, a);

@@ -89,7 +89,7 @@ __device__ __forceinline__ float fprime_of(const Coef32& c, float s2)
 // largest I.
 // GRAD also accumulates dF/ds^2 = sum_j occ_j exp(-B_j s^2)(f_j' - B_j f_j) e^{i phi_j}.
 template <int PREC, bool GRAD, int kSfRB, bool RUNS>
-__device__ float sf_tile_fp32(const SfArgs& a, int64_t first, int len, int64_t j0, int64_t j1, Atom32* sat,
+__device__ float sf_tile_fp32(const SfArgs& a, int s, int64_t first, int len, int64_t j0, int64_t j1, Atom32* sat,
                               float2* sstep, const Coef32* scoef, bool staged)
 {
     constexpr float ln2 = 0.69314718055994531f;
@@ -223,8 +223,12 @@ __device__ float sf_tile_fp32(const SfArgs& a, int64_t first, int len, int64_t j
         } else {
             a.If[r] = I;
             if (ACC && a.Eb) {
+                // the bound of the rounding error of I; a reflection can need the re-evaluation only if
+                // it exceeds tau of I (the criterion is E > tau max(I, c M)): then its structure is noted
                 const float dF = a.eps_k * sqrtf(A2[kRotate ? 0 : i]);
-                a.Eb[r] = lp * dF * fmaf(2.f, sqrtf(F2), dF);
+                const float E = lp * dF * fmaf(2.f, sqrtf(F2), dF);
+                a.Eb[r] = E;
+                if (E > a.tau * I) a.Es[r] = s;
             }
             if (a.F) a.F[r] = make_float2(fr, fi);
             imax = fmaxf(imax, I);
@@ -330,7 +334,7 @@ __global__ void __launch_bounds__(32 * WARPS, PREC == XRD_FP64
             sf_tile_fp64<RB>(a, first, RUNS ? 1 : 32, len, j0, j1);
         } else {
             const bool one_chunk = j1 - j0 <= kSfChunk;
-            float m = sf_tile_fp32<PREC, GRAD, RB, RUNS>(a, first, len, j0, j1, sat[w], sstep[w], scoef,
+            float m = sf_tile_fp32<PREC, GRAD, RB, RUNS>(a, s, first, len, j0, j1, sat[w], sstep[w], scoef,
                                                          one_chunk && s == staged_s);
             staged_s = one_chunk ? s : -1;
             if (!GRAD && a.imax) {  // the structure's largest reflection intensity (I >= 0: integer order)

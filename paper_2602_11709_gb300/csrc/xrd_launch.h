@@ -81,7 +81,9 @@ struct SfArgs {
     float* Ig;   // gradient path: |F|^2 LP per reflection
     float* Eb;   // FP32 pattern variants: bound of the intensity's rounding error per reflection (or nullptr):
                  // LP dF (2 |F| + dF) with dF = eps_k sqrt(sum_j a_j^2), a_j = occ DW max(|f|, Z)
+    int* Es;     // the structure of each reflection whose bound exceeds tau times its intensity (others: unset)
     float eps_k; // K times the relative error of one FP32 term (the bound of |dF| / sqrt(sum a_j^2))
+    float tau;
     unsigned* imax;  // FP32 pattern variants: [n_struct] bits of the largest reflection intensity (zeroed by k_prep)
 };
 
@@ -108,6 +110,7 @@ struct RefineArgs {
     const uint32_t* key;
     float* If;          // FP32 intensities, rewritten for the re-evaluated reflections
     const float* Eb;    // bound of the FP32 intensity's rounding error per reflection (k_sf)
+    const int* Es;      // the reflection's structure where Eb > tau If (k_sf)
     const unsigned* imax;  // largest intensity of each structure (bits)
     const AtomR* atomr;
     const float4* cdd;
