@@ -89,9 +89,9 @@ size_t al(size_t x) { return (x + 255) & ~size_t(255); }
 struct Layout {
     size_t geo, refl_cnt, run_cnt, refl_off, tile_off, order, atom_bad, cls_list, tile_tab, npk, nfm, fam_soff,
         flags, coef32, atom32, atom64, astep, imax, cdd, atomr;
-    size_t q, key, runs, I, Eb, cand_r, cand_s, g_perm, g_bkt, g_flag, g_pstart, g_psum, g_fcnt;
-    size_t st_q, st_I, st_foff, st_hkl, st_mult;
-    size_t parts, oparts, pf, pf_sq, pf_sI, fkg, pf_sfk;
+    size_t q, key, runs, I, Eb, cand_r, cand_s, g_bkt, g_flag, g_pstart, g_psum, g_fcnt;
+    size_t st_q, st_I, st_foff, st_key, st_mult;
+    size_t parts, oparts, pf, pf_rec, fkg, pf_sfk;
     size_t total;
 };
 
@@ -130,7 +130,6 @@ Layout layout(int64_t n, int64_t natoms, int zmax, int64_t R, bool pg = false)
     L.Eb = take(4 * R);
     L.cand_r = take(8 * (R + 1));  // also the kept-peak and family scans of the flat post passes
     L.cand_s = take(4 * (R + 1));  // also their peak starts and ids
-    L.g_perm = take(4 * R);
     L.g_bkt = take(4 * (R + n));
     L.g_flag = take(R);
     L.g_pstart = take(4 * R);
@@ -139,13 +138,12 @@ Layout layout(int64_t n, int64_t natoms, int zmax, int64_t R, bool pg = false)
     L.st_q = take(8 * R);
     L.st_I = take(8 * R);
     L.st_foff = take(4 * R);
-    L.st_hkl = take(12 * R);
+    L.st_key = take(4 * R);
     L.st_mult = take(4 * R);
     L.parts = take(scan_parts_bytes(n));
     L.oparts = take(xrd::order_parts_bytes(n));
     L.pf = take(4 * (n + 1) + 8 * n + 16 + 8 * 2 * xrd::kPfScanBlocksMax + 64);
-    L.pf_sq = take(8 * R);  // sorted records of the flat post passes
-    L.pf_sI = take(8 * R);
+    L.pf_rec = take(16 * R);  // records of the flat post passes
     L.fkg = take(pg ? 8 * R : 0);    // family keys under the caller's point group (that mode only)
     L.pf_sfk = take(pg ? 8 * R : 0);
     L.total = o;
@@ -692,11 +690,11 @@ int xrd_pattern_batch(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, cons
     pa.cls_list = ga.cls_list;
     pa.cls_cnt = ga.abort_flag + xrd::kFlagClsCnt;
     pa.cls_next = ga.abort_flag + xrd::kFlagClsNext;
+    pa.pf_bar = ga.abort_flag + xrd::kFlagPfBar;
     pa.atom_bad = ga.atom_bad;
     pa.status = out->status;
     pa.totals = out->totals;
     pa.grid = h->sms;
-    pa.g_perm = (int*)(ws + L.g_perm);
     pa.g_bkt = (int*)(ws + L.g_bkt);
     pa.g_flag = (uint8_t*)(ws + L.g_flag);
     pa.g_pstart = (int*)(ws + L.g_pstart);
@@ -705,7 +703,7 @@ int xrd_pattern_batch(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, cons
     pa.st_q = (double*)(ws + L.st_q);
     pa.st_I = (double*)(ws + L.st_I);
     pa.st_foff = (int*)(ws + L.st_foff);
-    pa.st_hkl = (int*)(ws + L.st_hkl);
+    pa.st_key = (uint32_t*)(ws + L.st_key);
     pa.st_mult = (int*)(ws + L.st_mult);
     pa.npk = (int64_t*)(ws + L.npk);
     pa.nfm = (int64_t*)(ws + L.nfm);
@@ -721,14 +719,8 @@ int xrd_pattern_batch(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, cons
         pa.pf_pj = (int*)(ws + L.Eb);
         pa.pf_kidx = (int*)(ws + L.cand_r);
         pa.pf_fidx = pa.pf_kidx + (cap_refl + 1);
-        // bucket-order records in arrays that are free between the scatter and the rank
-        pa.pf_bq = (double*)(ws + L.cand_r);
-        pa.pf_bk = (uint32_t*)(ws + L.cand_s);
-        pa.pf_bI = (double*)(ws + L.g_psum);
-        pa.pf_bb = (int*)(ws + L.Eb);
-        pa.pf_sq = (double*)(ws + L.pf_sq);
-        pa.pf_sk = (uint32_t*)(ws + L.g_perm);
-        pa.pf_sI = (double*)(ws + L.pf_sI);
+        pa.pf_rec = (xrd::PfRec*)(ws + L.pf_rec);
+        pa.pf_rI = (double*)(ws + L.cand_r);  // until the kept-peak scan
     }
     if (pg) {
         pa.pg = h->pg;
@@ -775,7 +767,8 @@ int xrd_pattern_batch(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, cons
     ca.l2l = (float)(pa.l2d - (double)ca.l2h);
     ca.ttab = h->ttab;
     ca.st_foff = pa.st_foff;
-    ca.st_hkl = pa.st_hkl;
+    ca.st_key = pa.st_key;
+    ca.fi = pa.If != nullptr;
     ca.st_mult = pa.st_mult;
     ca.out_abort = ga.abort_flag + 1;
     ca.out = *out;

@@ -6,12 +6,12 @@
 // the optional cutoff (Sec. 2) keeps peaks above
 // a fraction of the largest one and Sec. 3 compares intensities on a 0-100 scale.
 //
-// One CTA per structure. Reflections of structures up to `cap_smem` live in
-// shared memory; larger ones use the same code on global scratch (generic
-// pointers). The sort is a bucket sort in |g|^3 (reflections are uniform in
-// the volume of the sphere, so buckets are nearly equally full); each
-// reflection then takes its rank among the members of its own bucket on the
-// full key (|g|^2, then -h, -k, -l), one thread per reflection.
+// One CTA per structure of up to 6144 reflections, held in shared memory (the
+// larger ones run as the flat passes of k_post_flat.cu). The sort is a bucket
+// sort in |g|^3 (reflections are uniform in the volume of the sphere, so
+// buckets are nearly equally full); each reflection then takes its rank among
+// the members of its own bucket on the full key (|g|^2, then -h, -k, -l), one
+// thread per reflection.
 // The anchor rule is sequential, so it is split: a reflection whose gap to its
 // predecessor is >= tol always opens a peak (a definite start); the short runs
 // between definite starts are resolved one thread per run.
@@ -107,16 +107,14 @@ __device__ void post_singles(const PostArgs& a, int s, int64_t base, int n, cons
         a.st_q[o] = q[v];
         if (FI) {
             const float ps = ((const float*)psum)[p];
-            a.st_I[o] = f2d_fast((a.scaled && imaxf > 0.f) ? (ps == imaxf ? 100.f : 100.f * (ps * inv_imaxf)) : ps);
+            ((float*)a.st_I)[o] = (a.scaled && imaxf > 0.f) ? (ps == imaxf ? 100.f : 100.f * (ps * inv_imaxf)) : ps;
         } else {
             const double ps = psum[p];
             a.st_I[o] = (a.scaled && imax > 0.0) ? (ps == imax ? 100.0 : 100.0 * (ps * inv_imax)) : ps;
         }
         a.st_foff[o] = pst[p];  // one family per kept peak
         const uint32_t rep = key[v];
-        a.st_hkl[3 * o] = hkl_h(rep);
-        a.st_hkl[3 * o + 1] = hkl_k(rep);
-        a.st_hkl[3 * o + 2] = hkl_l(rep);
+        a.st_key[o] = rep;
         a.st_mult[o] = 2;
     }
     if (tid == 0) {
@@ -284,7 +282,7 @@ __device__ void post_structure(const PostArgs& a, int s, int64_t base, int n, co
         a.st_q[o] = q[perm[i0]];  // anchor |g|^2: 2-theta and d are formed during compaction
         if (FI) {  // the largest peak maps to exactly 100
             const float ps = ((const float*)psum)[p];
-            a.st_I[o] = f2d_fast((a.scaled && imaxf > 0.f) ? (ps == imaxf ? 100.f : 100.f * (ps * inv_imaxf)) : ps);
+            ((float*)a.st_I)[o] = (a.scaled && imaxf > 0.f) ? (ps == imaxf ? 100.f : 100.f * (ps * inv_imaxf)) : ps;
         } else {
             const double ps = psum[p];
             a.st_I[o] = (a.scaled && imax > 0.0) ? (ps == imax ? 100.0 : 100.0 * (ps * inv_imax)) : ps;
@@ -293,9 +291,7 @@ __device__ void post_structure(const PostArgs& a, int s, int64_t base, int n, co
         if (i1 - i0 == 1) {  // one reflection: one family of multiplicity 2 (g and -g)
             const uint32_t rep = key[perm[i0]];
             const int64_t fo = base + fcnt[p];
-            a.st_hkl[3 * fo] = hkl_h(rep);
-            a.st_hkl[3 * fo + 1] = hkl_k(rep);
-            a.st_hkl[3 * fo + 2] = hkl_l(rep);
+            a.st_key[fo] = rep;
             a.st_mult[fo] = 2;
             continue;
         }
@@ -322,9 +318,7 @@ __device__ void post_structure(const PostArgs& a, int s, int64_t base, int n, co
                 rank += rm > rep;
             }
             const int64_t fo = base + fcnt[p] + rank;
-            a.st_hkl[3 * fo] = hkl_h(rep);
-            a.st_hkl[3 * fo + 1] = hkl_k(rep);
-            a.st_hkl[3 * fo + 2] = hkl_l(rep);
+            a.st_key[fo] = rep;
             a.st_mult[fo] = 2 * cnt;
         }
     }
@@ -575,16 +569,17 @@ __global__ void __launch_bounds__(kCompactThreads) k_compact(const CompactArgs a
             const double qa = a.st_q[src];
             a.out.two_theta[P] = two_theta_q(qa, a.l2h, a.l2l, a.ttab);
             a.out.d_hkl[P] = inv_sqrt_df(qa);
-            a.out.intensity[P] = a.st_I[src];
+            a.out.intensity[P] = a.fi ? f2d_fast(((const float*)a.st_I)[src]) : a.st_I[src];
             const int64_t fs = a.fam_soff[s];
             const int64_t f0 = fs + a.st_foff[src];
             const int64_t f1 = P + 1 < pe ? fs + a.st_foff[src + 1] : a.fam_soff[s + 1];
             a.out.fam_off[P] = f0;
             for (int64_t F = f0; F < f1; F++) {
                 const int64_t fsrc = rb + (F - fs);
-                a.out.hkl[3 * F] = a.st_hkl[3 * fsrc];
-                a.out.hkl[3 * F + 1] = a.st_hkl[3 * fsrc + 1];
-                a.out.hkl[3 * F + 2] = a.st_hkl[3 * fsrc + 2];
+                const uint32_t rep = a.st_key[fsrc];
+                a.out.hkl[3 * F] = hkl_h(rep);
+                a.out.hkl[3 * F + 1] = hkl_k(rep);
+                a.out.hkl[3 * F + 2] = hkl_l(rep);
                 a.out.mult[F] = a.st_mult[fsrc];
             }
         }
@@ -604,6 +599,9 @@ static void launch_post_class(const PostArgs& a, int cls, cudaStream_t st)
     int per_sm = (dev >= 0 && dev < 64) ? per_sm_cache[dev] : 0;
     if (per_sm < 1) {
         if (smem > 48 * 1024) cudaFuncSetAttribute(k_post<CAP, NT, FI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        // all of the unified L1 / shared storage as shared memory: more structures in flight per SM
+        cudaFuncSetAttribute(k_post<CAP, NT, FI>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_post<CAP, NT, FI>, NT, smem) != cudaSuccess ||
             per_sm < 1)
             per_sm = 1;

@@ -13,10 +13,9 @@
 //     atomics;
 //  2. one exclusive scan over all buckets: since a structure's buckets hold
 //     exactly its n_j reflections, bucket starts are sorted positions;
-//  3. scatter of (|g|^2, key, I, bucket) records into bucket order, then each
-//     record's rank among the members of its own bucket on the full key
-//     (|g|^2, then -h, -k, -l), which places it in sorted order: every later
-//     pass reads the sorted records sequentially instead of through a
+//  3. scatter of 16-byte (|g|^2, key, I) records into bucket order, then each
+//     bucket sorted in place on the full key (|g|^2, then -h, -k, -l): every
+//     later pass reads the sorted records sequentially instead of through a
 //     permutation;
 //  4. the anchor merge: a definite start where the gap to the previous
 //     reflection is >= tol, one thread per run of close reflections;
@@ -25,18 +24,64 @@
 //  6. one scan of kept peaks and of their families; per kept peak the staging
 //     of the outputs, as the one-CTA kernel writes them.
 // The decisions and the order of every floating-point operation are those of
-// the one-CTA kernel (k_post.cu), so the outputs are identical. Scans are two
-// kernels (segment sums, then segments offset by the sums before them) over
-// lengths read from device memory, so the launch sequence is fixed and
-// capturable.
+// the one-CTA kernel (k_post.cu), so the outputs are identical. All steps run
+// in one cooperative launch separated by grid-wide barriers; a scan is two
+// steps (segment sums, then segments offset by the sums before them) over a
+// length read from device memory, so the launch is fixed and capturable.
 #include "xrd_internal.cuh"
 #include "xrd_launch.h"
 #include "xrd_post.cuh"
 
 namespace xrd {
 
-constexpr int kPfThreads = 256;      // grid-stride element kernels
-constexpr int kPfScanThreads = 1024;  // scans and the prologue
+constexpr int kPfThreads = 1024;  // one CTA per SM: 152 arrivals per grid barrier
+constexpr unsigned long long kPfWaitNs = 1000000000ull;  // grid barrier time limit: 1 s
+
+__device__ __forceinline__ unsigned long long pf_now_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid-wide barrier of the cooperative launch (every CTA is resident). bar[0]
+// counts arrivals, bar[1] is the generation, bar[2] the failure word; all three
+// are zero at the start of a batch. The last CTA to arrive clears the count and
+// advances the generation; the others wait for the generation to move, for at
+// most kPfWaitNs, or until a failure is posted. Returns false (every CTA, within
+// the time limit) once any wait has run out.
+__device__ bool pf_grid_sync(int* bar, int G)
+{
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile int* vb = bar;
+        int good = vb[2] == 0;
+        if (good) {
+            const int gen = vb[1];
+            __threadfence();
+            if (atomicAdd(&bar[0], 1) == G - 1) {
+                atomicExch(&bar[0], 0);
+                __threadfence();
+                atomicAdd(&bar[1], 1);
+            } else {
+                const unsigned long long t0 = pf_now_ns();
+                while (vb[1] == gen) {
+                    if (vb[2] != 0 || pf_now_ns() - t0 > kPfWaitNs) {
+                        atomicExch(&bar[2], 1);
+                        good = 0;
+                        break;
+                    }
+                    __nanosleep(128);
+                }
+            }
+            __threadfence();
+        }
+        ok = good;
+    }
+    __syncthreads();
+    return ok != 0;
+}
 
 // largest j in [0, c5) with voff[j] <= v (voff[c5] > v)
 __device__ __forceinline__ int vowner(const int* __restrict__ voff, int c5, int v)
@@ -141,14 +186,12 @@ struct SrcKeep {  // per peak (kept, its families if kept) -> kidx, fidx; length
 
 // Segment sums: block b takes [b seg, (b + 1) seg) of [0, len).
 template <class S>
-__global__ void __launch_bounds__(kPfScanThreads) k_pf_scan_parts(const PostArgs a)
+__device__ void pf_scan_parts(const PostArgs& a, int B, int G)
 {
-    pdl_enter();
     __shared__ int tmp[66];
-    if (*a.abort_flag) return;
-    const int n = S::len(a), G = gridDim.x;
+    const int n = S::len(a);
     const int seg = (n + G - 1) / G;
-    const int lo = min((int)blockIdx.x * seg, n), hi = min(lo + seg, n);
+    const int lo = min((int)B * seg, n), hi = min(lo + seg, n);
     int2 s = make_int2(0, 0);
     for (int i = lo + (int)threadIdx.x; i < hi; i += blockDim.x) {
         const int2 v = S::load(a, i);
@@ -158,25 +201,23 @@ __global__ void __launch_bounds__(kPfScanThreads) k_pf_scan_parts(const PostArgs
     int2 e;
     const int2 t = block_scan_int2(s, e, tmp);
     if (threadIdx.x == 0) {
-        a.pf_parts[blockIdx.x] = t.x;
-        a.pf_parts[G + blockIdx.x] = t.y;
+        a.pf_parts[B] = t.x;
+        a.pf_parts[G + B] = t.y;
     }
 }
 
 // Each segment scanned in chunks of blockDim, offset by the sums of the segments before it.
 template <class S>
-__global__ void __launch_bounds__(kPfScanThreads) k_pf_scan_final(const PostArgs a)
+__device__ void pf_scan_final(const PostArgs& a, int B, int G)
 {
-    pdl_enter();
     __shared__ int tmp[66];
-    if (*a.abort_flag) return;
-    const int n = S::len(a), G = gridDim.x;
+    const int n = S::len(a);
     const int seg = (n + G - 1) / G;
-    const int lo = min((int)blockIdx.x * seg, n), hi = min(lo + seg, n);
+    const int lo = min((int)B * seg, n), hi = min(lo + seg, n);
     int2 carry = make_int2(0, 0), all = make_int2(0, 0);
     for (int b = 0; b < G; b++) {
         const int x = (int)a.pf_parts[b], y = (int)a.pf_parts[G + b];
-        if (b < (int)blockIdx.x) {
+        if (b < (int)B) {
             carry.x += x;
             carry.y += y;
         }
@@ -192,17 +233,15 @@ __global__ void __launch_bounds__(kPfScanThreads) k_pf_scan_final(const PostArgs
         carry.x += t.x;
         carry.y += t.y;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) S::total(a, n, all);
+    if (B == 0 && threadIdx.x == 0) S::total(a, n, all);
 }
 
 // Prologue: the virtual offsets of the class's structures (a structure with an
 // invalid atom gets none and reports XRD_EINVAL), the structure maxima cleared;
 // every block clears the bucket counts over [0, V).
-__global__ void __launch_bounds__(kPfScanThreads) k_pf_prep(const PostArgs a, int cls)
+__device__ void pf_prep(const PostArgs& a, int cls, int B, int G)
 {
-    pdl_enter();
     __shared__ int tmp[66];
-    if (*a.abort_flag) return;
     const int c5 = a.cls_cnt[cls];
     const int* __restrict__ list = a.cls_list + (int64_t)cls * a.n_struct;
     int carry = 0;
@@ -213,7 +252,7 @@ __global__ void __launch_bounds__(kPfScanThreads) k_pf_prep(const PostArgs a, in
             const int s = list[j];
             const bool bad = a.atom_bad && a.atom_bad[s];
             nj = bad ? 0 : (int)(a.refl_off[s + 1] - a.refl_off[s]);
-            if (blockIdx.x == 0) {
+            if (B == 0) {
                 a.pf_smax[j] = 0ull;
                 if (bad) {
                     a.npk[s] = 0;
@@ -227,125 +266,129 @@ __global__ void __launch_bounds__(kPfScanThreads) k_pf_prep(const PostArgs a, in
         }
         int2 e;
         const int2 t = block_scan_int2(make_int2(nj, 0), e, tmp);
-        if (blockIdx.x == 0 && j < c5) a.pf_voff[j] = carry + e.x;
+        if (B == 0 && j < c5) a.pf_voff[j] = carry + e.x;
         carry += t.x;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (B == 0 && threadIdx.x == 0) {
         a.pf_voff[c5] = carry;
         a.pf_scal[0] = carry;
     }
-    for (int i = (int)(blockIdx.x * blockDim.x + threadIdx.x); i < carry; i += (int)(gridDim.x * blockDim.x))
+    for (int i = (int)(B * blockDim.x + threadIdx.x); i < carry; i += (int)(G * blockDim.x))
         a.g_bkt[i] = 0;
 }
 
-// 1. bucket of every reflection; g_fcnt holds the virtual bucket until the ranks are taken
-__global__ void __launch_bounds__(kPfThreads) k_pf_bucket(const PostArgs a, int cls)
+// Virtual bucket of reflection v of class-list structure j (first = voff[j]):
+// n_j buckets in |g|^3 over [r2min^1.5, r2max^1.5]
+__device__ __forceinline__ int pf_bucket_of(const PostArgs& a, double q, int first, int nb)
 {
-    pdl_enter();
-    if (*a.abort_flag) return;
+    const float scale = (float)nb / (a.hi3 - a.lo3);
+    const float qf = d2f_pos(q);
+    int b = (int)((qf * sqrtf(qf) - a.lo3) * scale);
+    return first + min(max(b, 0), nb - 1);
+}
+
+// 1. bucket counts
+__device__ void pf_bucket(const PostArgs& a, int cls, int B, int G)
+{
     const int V = a.pf_scal[0], c5 = a.cls_cnt[cls];
     const int* __restrict__ list = a.cls_list + (int64_t)cls * a.n_struct;
-    const float lo3 = a.lo3, hi3 = a.hi3;
-    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < V; v += gridDim.x * blockDim.x) {
+    for (int v = B * blockDim.x + threadIdx.x; v < V; v += G * blockDim.x) {
         const int j = vowner(a.pf_voff, c5, v);
-        const int first = a.pf_voff[j], nb = a.pf_voff[j + 1] - first;
+        const int first = a.pf_voff[j];
         const int64_t r = a.refl_off[list[j]] + (v - first);
-        const float scale = (float)nb / (hi3 - lo3);
-        const float qf = d2f_pos(a.q[r]);
-        int b = (int)((qf * sqrtf(qf) - lo3) * scale);
-        b = min(max(b, 0), nb - 1);
-        a.g_fcnt[v] = first + b;
-        atomicAdd(&a.g_bkt[first + b], 1);
+        atomicAdd(&a.g_bkt[pf_bucket_of(a, a.q[r], first, a.pf_voff[j + 1] - first)], 1);
     }
 }
 
-// 3a. scatter of each reflection's record into bucket order (cand_r: |g|^2,
-// cand_s: key, g_psum: I, Eb: virtual bucket); g_bkt ends as the bucket ends
+// 3a. scatter of each reflection's 16-byte record into bucket order (the bucket
+// is formed again, by the same arithmetic); g_bkt ends as the bucket ends
 template <bool FI>
-__global__ void __launch_bounds__(kPfThreads) k_pf_scatter(const PostArgs a, int cls)
+__device__ void pf_scatter(const PostArgs& a, int cls, int B, int G)
 {
-    pdl_enter();
-    if (*a.abort_flag) return;
     const int V = a.pf_scal[0], c5 = a.cls_cnt[cls];
     const int* __restrict__ list = a.cls_list + (int64_t)cls * a.n_struct;
-    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < V; v += gridDim.x * blockDim.x) {
+    for (int v = B * blockDim.x + threadIdx.x; v < V; v += G * blockDim.x) {
         const int j = vowner(a.pf_voff, c5, v);
-        const int64_t r = a.refl_off[list[j]] + (v - a.pf_voff[j]);
-        const int vb = a.g_fcnt[v];
-        const int pos = atomicAdd(&a.g_bkt[vb], 1);
-        a.pf_bq[pos] = a.q[r];
-        a.pf_bk[pos] = a.key[r];
-        if (FI) ((float*)a.pf_bI)[pos] = a.If[r];
-        else a.pf_bI[pos] = a.I[r];
-        a.pf_bb[pos] = vb;
+        const int first = a.pf_voff[j];
+        const int64_t r = a.refl_off[list[j]] + (v - first);
+        PfRec rec;
+        rec.q = a.q[r];
+        rec.key = a.key[r];
+        rec.I = FI ? a.If[r] : 0.f;
+        const int pos = atomicAdd(&a.g_bkt[pf_bucket_of(a, rec.q, first, a.pf_voff[j + 1] - first)], 1);
+        a.pf_rec[pos] = rec;
+        if (!FI) a.pf_rI[pos] = a.I[r];
     }
 }
 
-// 3b. rank within the bucket on the full key; the record goes to its sorted position
+// 3b. each bucket sorted in place on the full key (|g|^2, then -h, -k, -l) by
+// one thread: buckets hold about one reflection on average, so an insertion
+// sort over the bucket's few contiguous records
 template <bool FI>
-__global__ void __launch_bounds__(kPfThreads) k_pf_rank(const PostArgs a)
+__device__ void pf_sortb(const PostArgs& a, int B, int G)
 {
-    pdl_enter();
-    if (*a.abort_flag) return;
     const int V = a.pf_scal[0];
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < V; p += gridDim.x * blockDim.x) {
-        const int vb = a.pf_bb[p];
+    PfRec* __restrict__ rec = a.pf_rec;
+    for (int vb = B * blockDim.x + threadIdx.x; vb < V; vb += G * blockDim.x) {
         const int b0 = vb ? a.g_bkt[vb - 1] : 0, b1 = a.g_bkt[vb];
-        const double qv = a.pf_bq[p];
-        const uint32_t kv = a.pf_bk[p];
-        int r = b0;
-        for (int i = b0; i < b1 && b1 - b0 > 1; i++) r += before(a.pf_bq[i], a.pf_bk[i], qv, kv);  // false for i == p
-        a.pf_sq[r] = qv;
-        a.pf_sk[r] = kv;
-        if (FI) ((float*)a.pf_sI)[r] = ((const float*)a.pf_bI)[p];
-        else a.pf_sI[r] = a.pf_bI[p];
+        for (int i = b0 + 1; i < b1; i++) {
+            const PfRec x = rec[i];
+            const double xI = FI ? 0.0 : a.pf_rI[i];
+            int j = i - 1;
+            for (; j >= b0; j--) {
+                const PfRec y = rec[j];
+                if (!before(x.q, x.key, y.q, y.key)) break;
+                rec[j + 1] = y;
+                if (!FI) a.pf_rI[j + 1] = a.pf_rI[j];
+            }
+            if (j + 1 != i) {
+                rec[j + 1] = x;
+                if (!FI) a.pf_rI[j + 1] = xI;
+            }
+        }
     }
 }
 
 // 3c. with a caller's point group: the family key of every sorted record
-__global__ void __launch_bounds__(kPfThreads) k_pf_pgkeys(const PostArgs a)
+__device__ void pf_pgkeys(const PostArgs& a, int B, int G)
 {
-    pdl_enter();
-    if (*a.abort_flag) return;
     const int V = a.pf_scal[0];
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < V; p += gridDim.x * blockDim.x)
-        a.pf_sfk[p] = pg_family_key(a.pf_sk[p], a.pg, a.npg);
+    for (int p = B * blockDim.x + threadIdx.x; p < V; p += G * blockDim.x)
+        a.pf_sfk[p] = pg_family_key(a.pf_rec[p].key, a.pg, a.npg);
 }
 
 // 4. anchor merge (and the caller's per-reflection list in merge order): pf_pst
 // and g_flag mark the peak starts
 template <bool FI>
-__global__ void __launch_bounds__(kPfThreads) k_pf_merge(const PostArgs a, int cls)
+__device__ void pf_merge(const PostArgs& a, int cls, int B, int G)
 {
-    pdl_enter();
-    if (*a.abort_flag) return;
     const int V = a.pf_scal[0], c5 = a.cls_cnt[cls];
     const int* __restrict__ list = a.cls_list + (int64_t)cls * a.n_struct;
     const float l2 = a.l2f, lh = a.lhf, ttol = a.ttol;
     const double lam = a.lambda, tol = a.tol;
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < V; p += gridDim.x * blockDim.x) {
+    for (int p = B * blockDim.x + threadIdx.x; p < V; p += G * blockDim.x) {
         const int j = vowner(a.pf_voff, c5, p);
         const int first = a.pf_voff[j], end = a.pf_voff[j + 1];
-        const double qv = a.pf_sq[p];
+        const double qv = a.pf_rec[p].q;
         if (a.refl_hkl) {
             const int64_t rb = a.refl_off[list[j]];
             if (rb + (end - first) <= a.cap_refl) {
                 const int64_t o = rb + (p - first);
-                const uint32_t kv = a.pf_sk[p];
+                const uint32_t kv = a.pf_rec[p].key;
                 a.refl_hkl[3 * o] = hkl_h(kv);
                 a.refl_hkl[3 * o + 1] = hkl_k(kv);
                 a.refl_hkl[3 * o + 2] = hkl_l(kv);
                 a.refl_tt[o] = two_theta_q(qv, a.l2h, a.l2l, a.ttab);
-                a.refl_I[o] = FI ? (double)((const float*)a.pf_sI)[p] : a.pf_sI[p];
+                a.refl_I[o] = FI ? (double)a.pf_rec[p].I : a.pf_rI[p];
             }
         }
-        const bool start = p == first || !tt_close(a.pf_sq[p - 1], qv, l2, lh, ttol, lam, tol);
+        const bool start = p == first || !tt_close(a.pf_rec[p - 1].q, qv, l2, lh, ttol, lam, tol);
         if (!start) continue;  // written by the thread of its run's definite start
         a.pf_pst[p] = 1;
         a.g_flag[p] = 1;
         double qa = qv, qprev = qv;
         for (int i = p + 1; i < end; i++) {
-            const double qi = a.pf_sq[i];
+            const double qi = a.pf_rec[i].q;
             if (!tt_close(qprev, qi, l2, lh, ttol, lam, tol)) break;  // the next definite start
             qprev = qi;
             const int ps = tt_close(qa, qi, l2, lh, ttol, lam, tol) ? 0 : 1;
@@ -363,15 +406,13 @@ __global__ void __launch_bounds__(kPfThreads) k_pf_merge(const PostArgs a, int c
 // updates the structure's slot, so the slot sees one atomic per warp, not one
 // per peak.
 template <bool FI>
-__global__ void __launch_bounds__(kPfThreads) k_pf_peaks(const PostArgs a, int cls)
+__device__ void pf_peaks(const PostArgs& a, int cls, int B, int G)
 {
-    pdl_enter();
-    if (*a.abort_flag) return;
     const int V = a.pf_scal[0], c5 = a.cls_cnt[cls];
     const int* __restrict__ list = a.cls_list + (int64_t)cls * a.n_struct;
     const int lane = threadIdx.x & 31;
-    const int stride = gridDim.x * blockDim.x;
-    for (int p0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); p0 < V; p0 += stride) {  // warp-uniform
+    const int stride = G * blockDim.x;
+    for (int p0 = B * blockDim.x + (threadIdx.x & ~31); p0 < V; p0 += stride) {  // warp-uniform
         const int p = p0 + lane;
         unsigned long long bits = 0ull;
         int j = -1;
@@ -385,14 +426,14 @@ __global__ void __launch_bounds__(kPfThreads) k_pf_peaks(const PostArgs a, int c
             a.g_pstart[k] = p;
             a.pf_pj[k] = j;
             if (FI) {
-                const float* sI = (const float*)a.pf_sI;
-                float sum = 2.f * sI[p];
-                for (int i = p + 1; i < e; i++) sum = fmaf(2.f, sI[i], sum);
+                const PfRec* __restrict__ rec = a.pf_rec;
+                float sum = 2.f * rec[p].I;
+                for (int i = p + 1; i < e; i++) sum = fmaf(2.f, rec[i].I, sum);
                 ((float*)a.g_psum)[k] = sum;
                 bits = __float_as_uint(sum);
             } else {
                 double sum = 0.0;
-                for (int i = p; i < e; i++) sum += 2.0 * a.pf_sI[i];
+                for (int i = p; i < e; i++) sum += 2.0 * a.pf_rI[i];
                 a.g_psum[k] = sum;
                 bits = dbits(sum);
             }
@@ -400,7 +441,7 @@ __global__ void __launch_bounds__(kPfThreads) k_pf_peaks(const PostArgs a, int c
             if (e - p > 1) {  // distinct family keys among the members
                 nfam = 0;
                 auto fk = [&](int i) -> unsigned long long {
-                    return a.pf_sfk ? a.pf_sfk[i] : family_key(a.pf_sk[i], hex);
+                    return a.pf_sfk ? a.pf_sfk[i] : family_key(a.pf_rec[i].key, hex);
                 };
                 nfam = count_families(fk, p, e);
             }
@@ -426,13 +467,11 @@ __global__ void __launch_bounds__(kPfThreads) k_pf_peaks(const PostArgs a, int c
 // 6. staging of kept peaks and their families at the structure's reflection
 // offset, and its kept-peak and family counts
 template <bool FI>
-__global__ void __launch_bounds__(kPfThreads) k_pf_stage(const PostArgs a, int cls)
+__device__ void pf_stage(const PostArgs& a, int cls, int B, int G)
 {
-    pdl_enter();
-    if (*a.abort_flag) return;
-    const int NP = a.pf_scal[1], c5 = a.cls_cnt[cls];
+    const int NP = a.pf_scal[1];
     const int* __restrict__ list = a.cls_list + (int64_t)cls * a.n_struct;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < NP; k += gridDim.x * blockDim.x) {
+    for (int k = B * blockDim.x + threadIdx.x; k < NP; k += G * blockDim.x) {
         const int j = a.pf_pj[k];
         const int s = list[j];
         const int first = a.pf_voff[j], end = a.pf_voff[j + 1];
@@ -448,13 +487,13 @@ __global__ void __launch_bounds__(kPfThreads) k_pf_stage(const PostArgs a, int c
         int i1 = i0 + 1;
         while (i1 < end && !a.g_flag[i1]) i1++;
         const int64_t o = rb + (a.pf_kidx[k] - kb);
-        a.st_q[o] = a.pf_sq[i0];
+        a.st_q[o] = a.pf_rec[i0].q;
         const unsigned long long m = a.pf_smax[j];
         if (FI) {
             const float imaxf = __uint_as_float((uint32_t)m);
             const float inv_imaxf = imaxf > 0.f ? 1.f / imaxf : 0.f;
             const float ps = ((const float*)a.g_psum)[k];
-            a.st_I[o] = f2d_fast((a.scaled && imaxf > 0.f) ? (ps == imaxf ? 100.f : 100.f * (ps * inv_imaxf)) : ps);
+            ((float*)a.st_I)[o] = (a.scaled && imaxf > 0.f) ? (ps == imaxf ? 100.f : 100.f * (ps * inv_imaxf)) : ps;
         } else {
             const double imax = __longlong_as_double((long long)m);
             const double inv_imax = imax > 0.0 ? 1.0 / imax : 0.0;
@@ -464,16 +503,14 @@ __global__ void __launch_bounds__(kPfThreads) k_pf_stage(const PostArgs a, int c
         const int fo0 = a.pf_fidx[k] - fb;
         a.st_foff[o] = fo0;
         if (i1 - i0 == 1) {
-            const uint32_t rep = a.pf_sk[i0];
+            const uint32_t rep = a.pf_rec[i0].key;
             const int64_t fo = rb + fo0;
-            a.st_hkl[3 * fo] = hkl_h(rep);
-            a.st_hkl[3 * fo + 1] = hkl_k(rep);
-            a.st_hkl[3 * fo + 2] = hkl_l(rep);
+            a.st_key[fo] = rep;
             a.st_mult[fo] = 2;
             continue;
         }
         const bool hex = a.geo[s].hex != 0;
-        auto kf = [&](int i) { return a.pf_sk[i]; };
+        auto kf = [&](int i) { return a.pf_rec[i].key; };
         auto fkf = [&](int i) -> unsigned long long { return a.pf_sfk ? a.pf_sfk[i] : family_key(kf(i), hex); };
         for (int i = i0; i < i1; i++) {  // families, ranked by descending representative
             const unsigned long long fk = fkf(i);
@@ -500,33 +537,87 @@ __global__ void __launch_bounds__(kPfThreads) k_pf_stage(const PostArgs a, int c
                 rank += rm > rep;
             }
             const int64_t fo = rb + fo0 + rank;
-            a.st_hkl[3 * fo] = hkl_h(rep);
-            a.st_hkl[3 * fo + 1] = hkl_k(rep);
-            a.st_hkl[3 * fo + 2] = hkl_l(rep);
+            a.st_key[fo] = rep;
             a.st_mult[fo] = 2 * cnt;
         }
     }
 }
 
+// A barrier that ran out: the class's structures report XRD_ETIMEOUT and no peaks.
+__device__ void pf_fail(const PostArgs& a, int cls, int B, int G)
+{
+    const int c5 = a.cls_cnt[cls];
+    const int* __restrict__ list = a.cls_list + (int64_t)cls * a.n_struct;
+    for (int j = B * blockDim.x + threadIdx.x; j < c5; j += G * blockDim.x) {
+        const int s = list[j];
+        a.npk[s] = 0;
+        a.nfm[s] = 0;
+        if (atomicExch(&a.status[s], XRD_ETIMEOUT) == XRD_OK) atomicAdd((unsigned long long*)&a.totals[3], 1ull);
+    }
+}
+
+// All passes in one cooperative launch: the CTAs of the grid are resident at
+// once and a grid-wide barrier separates the passes, so a batch without
+// structures in this class pays one launch, and a batch with them no launch gaps.
+template <bool FI>
+__global__ void __launch_bounds__(kPfThreads) k_pf_fused(const PostArgs a, int cls)
+{
+    pdl_enter();
+    if (*a.abort_flag) return;  // set before this launch: the same for every CTA
+    const int B = blockIdx.x, G = gridDim.x;
+    int* bar = a.pf_bar;
+#define PF_SYNC()                          \
+    if (!pf_grid_sync(bar, G)) {           \
+        pf_fail(a, cls, B, G);             \
+        return;                            \
+    }
+    pf_prep(a, cls, B, G);
+    PF_SYNC();
+    if (a.pf_scal[0] == 0) return;  // no reflection in this class (every CTA reads the same value)
+    pf_bucket(a, cls, B, G);
+    PF_SYNC();
+    pf_scan_parts<SrcBkt>(a, B, G);
+    PF_SYNC();
+    pf_scan_final<SrcBkt>(a, B, G);
+    PF_SYNC();
+    pf_scatter<FI>(a, cls, B, G);
+    PF_SYNC();
+    pf_sortb<FI>(a, B, G);
+    PF_SYNC();
+    if (a.pf_sfk) {
+        pf_pgkeys(a, B, G);
+        PF_SYNC();
+    }
+    pf_merge<FI>(a, cls, B, G);
+    PF_SYNC();
+    pf_scan_parts<SrcPst>(a, B, G);
+    PF_SYNC();
+    pf_scan_final<SrcPst>(a, B, G);
+    PF_SYNC();
+    pf_peaks<FI>(a, cls, B, G);
+    PF_SYNC();
+    pf_scan_parts<SrcKeep<FI>>(a, B, G);
+    PF_SYNC();
+    pf_scan_final<SrcKeep<FI>>(a, B, G);
+    PF_SYNC();
+    pf_stage<FI>(a, cls, B, G);
+#undef PF_SYNC
+}
+
 template <bool FI>
 static void launch_flat_fi(const PostArgs& a, int cls, cudaStream_t st)
 {
-    const int G = a.grid * 2;  // scans and prologue: two 1024-thread CTAs per SM
-    const int E = a.grid * 8;  // element kernels: eight 256-thread CTAs per SM
-    launch_pdl(k_pf_prep, G, kPfScanThreads, 0, st, a, cls);
-    launch_pdl(k_pf_bucket, E, kPfThreads, 0, st, a, cls);
-    launch_pdl(k_pf_scan_parts<SrcBkt>, G, kPfScanThreads, 0, st, a);
-    launch_pdl(k_pf_scan_final<SrcBkt>, G, kPfScanThreads, 0, st, a);
-    launch_pdl(k_pf_scatter<FI>, E, kPfThreads, 0, st, a, cls);
-    launch_pdl(k_pf_rank<FI>, E, kPfThreads, 0, st, a);
-    if (a.pf_sfk) launch_pdl(k_pf_pgkeys, E, kPfThreads, 0, st, a);
-    launch_pdl(k_pf_merge<FI>, E, kPfThreads, 0, st, a, cls);
-    launch_pdl(k_pf_scan_parts<SrcPst>, G, kPfScanThreads, 0, st, a);
-    launch_pdl(k_pf_scan_final<SrcPst>, G, kPfScanThreads, 0, st, a);
-    launch_pdl(k_pf_peaks<FI>, E, kPfThreads, 0, st, a, cls);
-    launch_pdl(k_pf_scan_parts<SrcKeep<FI>>, G, kPfScanThreads, 0, st, a);
-    launch_pdl(k_pf_scan_final<SrcKeep<FI>>, G, kPfScanThreads, 0, st, a);
-    launch_pdl(k_pf_stage<FI>, E, kPfThreads, 0, st, a, cls);
+    // one CTA per SM (40 registers x 1024 threads fit), every CTA resident
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(min(a.grid, kPfScanBlocksMax));
+    cfg.blockDim = dim3(kPfThreads);
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k_pf_fused<FI>, a, cls);
 }
 
 void launch_post_flat(const PostArgs& a, int cls, cudaStream_t st)

@@ -153,17 +153,39 @@ __device__ __forceinline__ bool refine_take(const RefineArgs& a, int64_t r, floa
     return !bad && E > a.tau * fmaxf(I, floorI);
 }
 
+// A CTA collects its candidates in shared memory and appends them to the list
+// with one atomic per flush: candidates are rare (a fraction of a percent), and
+// one atomic per warp on the list's single counter had serialised.
+constexpr int kSelCap = 2048;  // shared-memory candidates per CTA; flushed above kSelCap - 4 kRefThreads
+
 __global__ void __launch_bounds__(kRefThreads) k_refine_select(const RefineArgs a)
 {
     pdl_enter();
+    __shared__ int64_t sr[kSelCap];
+    __shared__ int ss[kSelCap];
+    __shared__ int sn;
+    __shared__ unsigned long long sbase;
     if (*a.abort_flag) return;
     const int64_t total = a.refl_off[a.n_struct];
-    const int lane = threadIdx.x & 31;
-    // a warp takes 128 consecutive reflections at a time, four per lane in one 16-byte load of each
-    // array (both 256-byte aligned), so that several loads are in flight per thread
-    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t b0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 128; b0 < total; b0 += nwarp * 128) {
-        const int64_t r4 = b0 + 4 * lane;
+    if (threadIdx.x == 0) sn = 0;
+    __syncthreads();
+    auto flush = [&]() {
+        const int m = sn;
+        if (threadIdx.x == 0 && m > 0) sbase = atomicAdd(a.nref, (unsigned long long)m);
+        __syncthreads();
+        for (int i = threadIdx.x; i < m; i += kRefThreads) {
+            a.cand_r[sbase + i] = sr[i];
+            a.cand_s[sbase + i] = ss[i];
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) sn = 0;
+        __syncthreads();
+    };
+    // the CTA takes 4 kRefThreads consecutive reflections at a time, four per thread in one 16-byte
+    // load of each array (both 256-byte aligned)
+    constexpr int kChunk = 4 * kRefThreads;
+    for (int64_t c0 = (int64_t)blockIdx.x * kChunk; c0 < total; c0 += (int64_t)gridDim.x * kChunk) {
+        const int64_t r4 = c0 + 4 * threadIdx.x;
         float E[4] = {0.f, 0.f, 0.f, 0.f}, I[4] = {0.f, 0.f, 0.f, 0.f};
         if (r4 + 4 <= total) {
             const float4 e4 = *reinterpret_cast<const float4*>(a.Eb + r4);
@@ -179,20 +201,18 @@ __global__ void __launch_bounds__(kRefThreads) k_refine_select(const RefineArgs 
         }
 #pragma unroll
         for (int j = 0; j < 4; j++) {
-            int s = 0;
-            const bool take = r4 + j < total && refine_take(a, r4 + j, E[j], I[j], s);
-            const unsigned m = __ballot_sync(0xffffffffu, take);
-            if (!m) continue;
-            unsigned long long base = 0;
-            if (lane == 0) base = atomicAdd(a.nref, (unsigned long long)__popc(m));
-            base = __shfl_sync(0xffffffffu, base, 0);
-            if (take) {
-                const unsigned long long o = base + __popc(m & ((1u << lane) - 1u));
-                a.cand_r[o] = r4 + j;
-                a.cand_s[o] = s;
+            int st = 0;
+            if (r4 + j < total && refine_take(a, r4 + j, E[j], I[j], st)) {
+                const int slot = atomicAdd(&sn, 1);
+                sr[slot] = r4 + j;
+                ss[slot] = st;
             }
         }
+        __syncthreads();
+        if (sn > kSelCap - kChunk) flush();  // uniform: every thread reads sn after the barrier
     }
+    __syncthreads();
+    flush();
 }
 
 // Evaluation: every warp of a persistent grid takes candidates from the list

@@ -42,7 +42,7 @@ __host__ __device__ __forceinline__ int post_class(long long c)
                             : 8;
 }
 // Flag words of a call (ints of the zeroed flags area): the class counts and the classes' work counters.
-constexpr int kFlagClsCnt = 32, kFlagClsNext = 48;
+constexpr int kFlagClsCnt = 32, kFlagClsNext = 48, kFlagPfBar = 4;
 
 // Per-structure geometry written by k_prep (step S0).
 struct Geo {

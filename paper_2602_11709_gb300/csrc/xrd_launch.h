@@ -38,7 +38,7 @@ struct GeomArgs {
     int* atom_bad;   // [n_struct] 1 where an atom of the structure is invalid
     int atoms_set_geo;  // k_atoms also marks such structures invalid in geo (only when it runs before k_count)
     int* cls_list;   // [kPostClasses][n_struct] post-processing size classes (nullptr: not built)
-    int* abort_flag; // flags[0]; flags[1] output abort, flags[2] tile queue, flags[26..28] enumeration
+    int* abort_flag; // flags[0]; flags[1] output abort, flags[2] tile queue, flags[4..6] flat-pass grid barrier, flags[26..28] enumeration
                      // claims, flags[kFlagClsCnt + c] class counts, flags[kFlagClsNext + c] class work counters
     int64_t* totals;
     int32_t* status;
@@ -119,6 +119,13 @@ struct RefineArgs {
     const int* atom_bad;
 };
 
+// A reflection record of the flat post passes: one 16-byte load or store.
+struct __align__(16) PfRec {
+    double q;
+    uint32_t key;
+    float I;
+};
+
 struct PostArgs {
     int n_struct, scaled, grid;  // grid = number of SMs
     double lambda, tol, cutoff, r2min, r2max;
@@ -136,17 +143,16 @@ struct PostArgs {
     const int* cls_cnt;   // [kPostClasses]
     int* cls_next;        // [kPostClasses] work counters (zero at launch)
     // scratch of the flat passes of the largest class (indexed by reflection)
-    int* g_perm;
     int* g_bkt;   // n_refl + n_struct entries
     uint8_t* g_flag;
     int* g_pstart;
     double* g_psum;
     int* g_fcnt;
     // staging of kept peaks and families (indexed by reflection offset)
-    double* st_q;   // anchor |g|^2 of each kept peak
-    double* st_I;
+    double* st_q;      // anchor |g|^2 of each kept peak
+    double* st_I;      // its intensity: FP64, or FP32 (first half) in the FP32 variants
     int* st_foff;
-    int* st_hkl;   // 3 per family
+    uint32_t* st_key;  // packed hkl of each family's representative
     int* st_mult;
     int64_t* npk;  // kept peaks per structure
     int64_t* nfm;  // families of kept peaks per structure
@@ -161,6 +167,7 @@ struct PostArgs {
     double* refl_I;
     float l2h, l2l;  // lambda^2 / 4 as two floats (2-theta of the list)
     // the flat passes of the largest class (k_post_flat.cu)
+    int* pf_bar;                   // flags[kFlagPfBar..+2]: grid barrier of the flat passes (zero at launch)
     int* pf_voff;                  // [n_struct + 1] virtual offsets of the class's structures
     unsigned long long* pf_smax;   // [n_struct] bits of each structure's largest peak sum
     int* pf_scal;                  // [4]: reflections of the class (V), its peaks
@@ -169,13 +176,8 @@ struct PostArgs {
     int* pf_pj;                    // [reflections] structure (class-list position) of each peak
     int* pf_kidx;                  // [reflections + 1] kept-peak index of each peak
     int* pf_fidx;                  // [reflections + 1] family offset of each peak
-    double* pf_bq;                 // [reflections] records in bucket order: |g|^2,
-    uint32_t* pf_bk;               //   key,
-    double* pf_bI;                 //   intensity (FP32 in the low word for the FP32 variants),
-    int* pf_bb;                    //   bucket
-    double* pf_sq;                 // [reflections] the same records in sorted order: |g|^2,
-    uint32_t* pf_sk;               //   key,
-    double* pf_sI;                 //   intensity
+    PfRec* pf_rec;                 // [reflections] (|g|^2, key, FP32 intensity) records, bucket then sorted order
+    double* pf_rI;                 // [reflections] FP64 intensities beside them (the FP64 variant)
     // the symmetry-aware family mode: the caller's point group (nullptr, 0: permutation and sign)
     const int8_t* pg;              // [npg][3][3] operations on (h, k, l), entries in {-1, 0, 1}
     int npg;
@@ -199,8 +201,9 @@ struct CompactArgs {
     float l2h, l2l;        // lambda^2 / 4 as two floats
     const TTab* ttab;      // 2-theta table
     const int* st_foff;
-    const int* st_hkl;
+    const uint32_t* st_key;
     const int* st_mult;
+    int fi;             // st_I holds FP32 intensities
     int* out_abort;     // set when the output capacity is too small
     long long* parts;   // chunk sums of the multi-block scan (nullptr: single-block scan)
     xrd_pattern out;

@@ -25,14 +25,16 @@ XRD_FLAG_HEXAGONAL = 1  # bit of the per-structure flag word: families by Miller
 # kernels xrd_pattern_batch launches per call: order, coef, atoms (a side stream), prep, count, scan, emit,
 # structure factor, re-evaluation of weak reflections (selection and evaluation, FP32 variants), post
 # (eight shared-memory size classes and the 13 flat passes of the largest), output scan, compaction
-LAUNCHES_PER_BATCH = 33
+LAUNCHES_PER_BATCH = 21
 
 
-def launches_per_batch(n_struct: int, refine: bool = True) -> int:
+def launches_per_batch(n_struct: int, refine: bool = True, point_group: bool = False) -> int:
     """Kernels of one xrd_pattern_batch call: above two chunks of 4096 structures the
     largest-first order, the reflection scan and the output scan each take two kernels (chunk
-    sums, then the chunks); the FP64 variant (or refine off) has no re-evaluation kernels."""
-    return LAUNCHES_PER_BATCH - (0 if refine else 2) + (3 if (n_struct + 4095) // 4096 > 2 else 0)
+    sums, then the chunks); the FP64 variant (or refine off) has no re-evaluation kernels; a
+    caller's point group adds the family-key kernel."""
+    return (LAUNCHES_PER_BATCH - (0 if refine else 2) + (3 if (n_struct + 4095) // 4096 > 2 else 0)
+            + (1 if point_group else 0))
 
 
 class xrd_batch(C.Structure):

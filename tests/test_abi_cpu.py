@@ -140,11 +140,13 @@ def test_missing_library_fails_loudly(tmp_path):
 
 
 def test_launch_count_per_call():
-    """Kernels per xrd_pattern_batch call: 33 with the two re-evaluation kernels of the FP32 variants
-    (31 without), three more above two chunks of 4096 structures (two-kernel order and scans)."""
-    assert xrd.launches_per_batch(1024) == 33 and xrd.launches_per_batch(8192) == 33
-    assert xrd.launches_per_batch(8193) == 36 and xrd.launches_per_batch(100_000) == 36
-    assert xrd.launches_per_batch(1024, refine=False) == 31 and xrd.launches_per_batch(8193, refine=False) == 34
+    """Kernels per xrd_pattern_batch call: 21 with the two re-evaluation kernels of the FP32 variants
+    (19 without), three more above two chunks of 4096 structures (two-kernel order and scans), one
+    more with a caller's point group (family keys)."""
+    assert xrd.launches_per_batch(1024) == 21 and xrd.launches_per_batch(8192) == 21
+    assert xrd.launches_per_batch(8193) == 24 and xrd.launches_per_batch(100_000) == 24
+    assert xrd.launches_per_batch(1024, refine=False) == 19 and xrd.launches_per_batch(8193, refine=False) == 22
+    assert xrd.launches_per_batch(1024, point_group=True) == 22
 
 
 def test_binding_argument_checks():
