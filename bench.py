@@ -347,11 +347,12 @@ def measure_pattern(h, b, o, precision, dev, steps, warmup, flush, stream, tune=
     # post-processing (sort, merge, families, cutoff, staging) and compaction against HBM: algorithmic
     # bytes per Friedel-unique reflection (|g|^2, key, intensity read), per kept peak (staged |g|^2,
     # intensity, family offset; compaction: those read, 2-theta, d, intensity, family offset written)
-    # and per family (hkl, multiplicity staged; compaction: read and written)
+    # and per family (packed hkl and multiplicity staged; compaction: those read, hkl and
+    # multiplicity written)
     ib = 8 if precision == "fp64" else 4
     npk, nfm = int(totals[1]), int(totals[2])
-    post_bytes = (12 + ib) * int(sz.n_refl) + 20 * npk + 16 * nfm
-    comp_bytes = (20 + 32) * npk + (16 + 16) * nfm
+    post_bytes = (12 + ib) * int(sz.n_refl) + (12 + ib) * npk + 8 * nfm
+    comp_bytes = (12 + ib + 32) * npk + (8 + 16) * nfm
     hbm = measured_hbm_gbs()
     hbm_rec = {}
     for stage, nbytes in (("post", post_bytes), ("compact", comp_bytes)):

@@ -6,8 +6,10 @@
 // structures hold most of the reflections (256 cells of 20 000-190 000
 // reflections, or the single 50 A cell of Sec. 4.2 with 680 000). Here the
 // class's structures are laid end to end in one virtual index space (virtual
-// offsets voff[j] in class-list order), every step is a grid-stride loop over
-// that space, and the per-structure block steps become device-wide ones:
+// offsets voff[j] in class-list order), every step is a loop over that space
+// (each CTA one contiguous block of it, its threads following their structure
+// forward; the scatter strides over the whole grid instead), and the
+// per-structure block steps become device-wide ones:
 //  1. bucket of every reflection on |g|^3 (n_j buckets for a structure of n_j
 //     reflections, laid out from voff[j] like its reflections), counts by
 //     atomics;
@@ -34,7 +36,8 @@
 
 namespace xrd {
 
-constexpr int kPfThreads = 1024;  // one CTA per SM: 152 arrivals per grid barrier
+constexpr int kPfThreads = 1024;
+constexpr int kPfCtasPerSm = 2;  // 64 warps per SM for the latency-bound passes (32 registers a thread)
 constexpr unsigned long long kPfWaitNs = 1000000000ull;  // grid barrier time limit: 1 s
 
 __device__ __forceinline__ unsigned long long pf_now_ns()
@@ -215,7 +218,7 @@ __device__ void pf_scan_final(const PostArgs& a, int B, int G)
     const int seg = (n + G - 1) / G;
     const int lo = min((int)B * seg, n), hi = min(lo + seg, n);
     int2 carry = make_int2(0, 0), all = make_int2(0, 0);
-    for (int b = 0; b < G; b++) {
+    for (int b = threadIdx.x; b < G; b += blockDim.x) {  // the sums of the segments before this one, and of all
         const int x = (int)a.pf_parts[b], y = (int)a.pf_parts[G + b];
         if (b < (int)B) {
             carry.x += x;
@@ -224,6 +227,9 @@ __device__ void pf_scan_final(const PostArgs& a, int B, int G)
         all.x += x;
         all.y += y;
     }
+    int2 e;
+    carry = block_scan_int2(carry, e, tmp);
+    all = block_scan_int2(all, e, tmp);
     for (int c0 = lo; c0 < hi; c0 += blockDim.x) {
         const int i = c0 + (int)threadIdx.x;
         const int2 v = i < hi ? S::load(a, i) : make_int2(0, 0);
@@ -279,43 +285,75 @@ __device__ void pf_prep(const PostArgs& a, int cls, int B, int G)
 
 // Virtual bucket of reflection v of class-list structure j (first = voff[j]):
 // n_j buckets in |g|^3 over [r2min^1.5, r2max^1.5]
-__device__ __forceinline__ int pf_bucket_of(const PostArgs& a, double q, int first, int nb)
+__device__ __forceinline__ int pf_bucket_of(const PostArgs& a, float scale_inv, double q, int first, int nb)
 {
-    const float scale = (float)nb / (a.hi3 - a.lo3);
     const float qf = d2f_pos(q);
-    int b = (int)((qf * sqrtf(qf) - a.lo3) * scale);
+    int b = (int)((qf * sqrtf(qf) - a.lo3) * ((float)nb * scale_inv));
     return first + min(max(b, 0), nb - 1);
 }
+
+// The element passes give each CTA one contiguous block of the index space
+// [0, len); its threads step through it by blockDim, so a thread's indices
+// rise and its structure changes rarely (a structure spans >= 6144 indices).
+__device__ __forceinline__ void pf_block(int len, int B, int G, int& lo, int& hi)
+{
+    const int per = (len + G - 1) / G;
+    lo = min(B * per, len);
+    hi = min(lo + per, len);
+}
+
+// The class-list structure that owns virtual index v, followed forward:
+// one bisection for a thread's first index, then a step past each end.
+struct PfOwner {
+    int j = -1, first = 0, end = 0;
+    int64_t rb = 0;  // reflection offset of the structure
+    __device__ __forceinline__ void at(const PostArgs& a, const int* __restrict__ list, int c5, int v)
+    {
+        if (j >= 0 && v < end) return;
+        j = j < 0 ? vowner(a.pf_voff, c5, v) : j + 1;
+        while (a.pf_voff[j + 1] <= v) j++;
+        first = a.pf_voff[j];
+        end = a.pf_voff[j + 1];
+        rb = a.refl_off[list[j]];
+    }
+};
 
 // 1. bucket counts
 __device__ void pf_bucket(const PostArgs& a, int cls, int B, int G)
 {
     const int V = a.pf_scal[0], c5 = a.cls_cnt[cls];
     const int* __restrict__ list = a.cls_list + (int64_t)cls * a.n_struct;
-    for (int v = B * blockDim.x + threadIdx.x; v < V; v += G * blockDim.x) {
-        const int j = vowner(a.pf_voff, c5, v);
-        const int first = a.pf_voff[j];
-        const int64_t r = a.refl_off[list[j]] + (v - first);
-        atomicAdd(&a.g_bkt[pf_bucket_of(a, a.q[r], first, a.pf_voff[j + 1] - first)], 1);
+    const float scale_inv = 1.f / (a.hi3 - a.lo3);
+    int lo, hi;
+    pf_block(V, B, G, lo, hi);
+    PfOwner w;
+    for (int v = lo + threadIdx.x; v < hi; v += blockDim.x) {
+        w.at(a, list, c5, v);
+        atomicAdd(&a.g_bkt[pf_bucket_of(a, scale_inv, a.q[w.rb + (v - w.first)], w.first, w.end - w.first)], 1);
     }
 }
 
 // 3a. scatter of each reflection's 16-byte record into bucket order (the bucket
-// is formed again, by the same arithmetic); g_bkt ends as the bucket ends
+// is formed again, by the same arithmetic); g_bkt ends as the bucket ends.
+// Grid-stride, unlike the other passes: the whole grid works on the same one or
+// two structures at a time, so that their bucket starts (returning atomics)
+// and their records (scattered 16-byte stores) stay in L2.
 template <bool FI>
 __device__ void pf_scatter(const PostArgs& a, int cls, int B, int G)
 {
     const int V = a.pf_scal[0], c5 = a.cls_cnt[cls];
     const int* __restrict__ list = a.cls_list + (int64_t)cls * a.n_struct;
+    const float scale_inv = 1.f / (a.hi3 - a.lo3);
+    PfOwner w;
     for (int v = B * blockDim.x + threadIdx.x; v < V; v += G * blockDim.x) {
-        const int j = vowner(a.pf_voff, c5, v);
-        const int first = a.pf_voff[j];
-        const int64_t r = a.refl_off[list[j]] + (v - first);
+        if (v >= w.end) w.j = -1;  // a stride crosses structures: bisect again
+        w.at(a, list, c5, v);
+        const int64_t r = w.rb + (v - w.first);
         PfRec rec;
         rec.q = a.q[r];
         rec.key = a.key[r];
         rec.I = FI ? a.If[r] : 0.f;
-        const int pos = atomicAdd(&a.g_bkt[pf_bucket_of(a, rec.q, first, a.pf_voff[j + 1] - first)], 1);
+        const int pos = atomicAdd(&a.g_bkt[pf_bucket_of(a, scale_inv, rec.q, w.first, w.end - w.first)], 1);
         a.pf_rec[pos] = rec;
         if (!FI) a.pf_rI[pos] = a.I[r];
     }
@@ -329,7 +367,9 @@ __device__ void pf_sortb(const PostArgs& a, int B, int G)
 {
     const int V = a.pf_scal[0];
     PfRec* __restrict__ rec = a.pf_rec;
-    for (int vb = B * blockDim.x + threadIdx.x; vb < V; vb += G * blockDim.x) {
+    int lo, hi;
+    pf_block(V, B, G, lo, hi);
+    for (int vb = lo + threadIdx.x; vb < hi; vb += blockDim.x) {
         const int b0 = vb ? a.g_bkt[vb - 1] : 0, b1 = a.g_bkt[vb];
         for (int i = b0 + 1; i < b1; i++) {
             const PfRec x = rec[i];
@@ -353,8 +393,9 @@ __device__ void pf_sortb(const PostArgs& a, int B, int G)
 __device__ void pf_pgkeys(const PostArgs& a, int B, int G)
 {
     const int V = a.pf_scal[0];
-    for (int p = B * blockDim.x + threadIdx.x; p < V; p += G * blockDim.x)
-        a.pf_sfk[p] = pg_family_key(a.pf_rec[p].key, a.pg, a.npg);
+    int lo, hi;
+    pf_block(V, B, G, lo, hi);
+    for (int p = lo + threadIdx.x; p < hi; p += blockDim.x) a.pf_sfk[p] = pg_family_key(a.pf_rec[p].key, a.pg, a.npg);
 }
 
 // 4. anchor merge (and the caller's per-reflection list in merge order): pf_pst
@@ -366,29 +407,31 @@ __device__ void pf_merge(const PostArgs& a, int cls, int B, int G)
     const int* __restrict__ list = a.cls_list + (int64_t)cls * a.n_struct;
     const float l2 = a.l2f, lh = a.lhf, ttol = a.ttol;
     const double lam = a.lambda, tol = a.tol;
-    for (int p = B * blockDim.x + threadIdx.x; p < V; p += G * blockDim.x) {
-        const int j = vowner(a.pf_voff, c5, p);
-        const int first = a.pf_voff[j], end = a.pf_voff[j + 1];
-        const double qv = a.pf_rec[p].q;
+    const PfRec* __restrict__ rec = a.pf_rec;
+    int lo, hi;
+    pf_block(V, B, G, lo, hi);
+    PfOwner w;
+    for (int p = lo + threadIdx.x; p < hi; p += blockDim.x) {
+        w.at(a, list, c5, p);
+        const double qv = rec[p].q;
         if (a.refl_hkl) {
-            const int64_t rb = a.refl_off[list[j]];
-            if (rb + (end - first) <= a.cap_refl) {
-                const int64_t o = rb + (p - first);
-                const uint32_t kv = a.pf_rec[p].key;
+            if (w.rb + (w.end - w.first) <= a.cap_refl) {
+                const int64_t o = w.rb + (p - w.first);
+                const uint32_t kv = rec[p].key;
                 a.refl_hkl[3 * o] = hkl_h(kv);
                 a.refl_hkl[3 * o + 1] = hkl_k(kv);
                 a.refl_hkl[3 * o + 2] = hkl_l(kv);
                 a.refl_tt[o] = two_theta_q(qv, a.l2h, a.l2l, a.ttab);
-                a.refl_I[o] = FI ? (double)a.pf_rec[p].I : a.pf_rI[p];
+                a.refl_I[o] = FI ? (double)rec[p].I : a.pf_rI[p];
             }
         }
-        const bool start = p == first || !tt_close(a.pf_rec[p - 1].q, qv, l2, lh, ttol, lam, tol);
+        const bool start = p == w.first || !tt_close(rec[p - 1].q, qv, l2, lh, ttol, lam, tol);
         if (!start) continue;  // written by the thread of its run's definite start
         a.pf_pst[p] = 1;
         a.g_flag[p] = 1;
         double qa = qv, qprev = qv;
-        for (int i = p + 1; i < end; i++) {
-            const double qi = a.pf_rec[i].q;
+        for (int i = p + 1; i < w.end; i++) {
+            const double qi = rec[i].q;
             if (!tt_close(qprev, qi, l2, lh, ttol, lam, tol)) break;  // the next definite start
             qprev = qi;
             const int ps = tt_close(qa, qi, l2, lh, ttol, lam, tol) ? 0 : 1;
@@ -411,22 +454,27 @@ __device__ void pf_peaks(const PostArgs& a, int cls, int B, int G)
     const int V = a.pf_scal[0], c5 = a.cls_cnt[cls];
     const int* __restrict__ list = a.cls_list + (int64_t)cls * a.n_struct;
     const int lane = threadIdx.x & 31;
-    const int stride = G * blockDim.x;
-    for (int p0 = B * blockDim.x + (threadIdx.x & ~31); p0 < V; p0 += stride) {  // warp-uniform
+    const PfRec* __restrict__ rec = a.pf_rec;
+    int lo, hi;
+    pf_block(V, B, G, lo, hi);
+    PfOwner w;
+    bool hex = false;
+    for (int p0 = lo + (threadIdx.x & ~31); p0 < hi; p0 += blockDim.x) {  // warp-uniform
         const int p = p0 + lane;
         unsigned long long bits = 0ull;
         int j = -1;
-        if (p < V && a.g_flag[p]) {
-            j = vowner(a.pf_voff, c5, p);
-            const int end = a.pf_voff[j + 1];
-            const bool hex = a.geo[list[j]].hex != 0;
+        if (p < hi && a.g_flag[p]) {
+            if (w.j < 0 || p >= w.end) {
+                w.at(a, list, c5, p);
+                hex = a.geo[list[w.j]].hex != 0;
+            }
+            j = w.j;
             const int k = a.pf_pst[p];
             int e = p + 1;
-            while (e < end && !a.g_flag[e]) e++;
+            while (e < w.end && !a.g_flag[e]) e++;
             a.g_pstart[k] = p;
             a.pf_pj[k] = j;
             if (FI) {
-                const PfRec* __restrict__ rec = a.pf_rec;
                 float sum = 2.f * rec[p].I;
                 for (int i = p + 1; i < e; i++) sum = fmaf(2.f, rec[i].I, sum);
                 ((float*)a.g_psum)[k] = sum;
@@ -439,9 +487,8 @@ __device__ void pf_peaks(const PostArgs& a, int cls, int B, int G)
             }
             int nfam = 1;
             if (e - p > 1) {  // distinct family keys among the members
-                nfam = 0;
                 auto fk = [&](int i) -> unsigned long long {
-                    return a.pf_sfk ? a.pf_sfk[i] : family_key(a.pf_rec[i].key, hex);
+                    return a.pf_sfk ? a.pf_sfk[i] : family_key(rec[i].key, hex);
                 };
                 nfam = count_families(fk, p, e);
             }
@@ -465,52 +512,69 @@ __device__ void pf_peaks(const PostArgs& a, int cls, int B, int G)
 }
 
 // 6. staging of kept peaks and their families at the structure's reflection
-// offset, and its kept-peak and family counts
+// offset, and its kept-peak and family counts. The structure's peaks are
+// contiguous in k, so its constants are read once per thread and structure.
 template <bool FI>
 __device__ void pf_stage(const PostArgs& a, int cls, int B, int G)
 {
     const int NP = a.pf_scal[1];
     const int* __restrict__ list = a.cls_list + (int64_t)cls * a.n_struct;
-    for (int k = B * blockDim.x + threadIdx.x; k < NP; k += G * blockDim.x) {
-        const int j = a.pf_pj[k];
-        const int s = list[j];
-        const int first = a.pf_voff[j], end = a.pf_voff[j + 1];
-        const int k0 = a.pf_pst[first], k1 = a.pf_pst[end];  // the structure's peaks: [k0, k1)
-        const int kb = a.pf_kidx[k0], fb = a.pf_fidx[k0];
-        const int64_t rb = a.refl_off[s];
+    const PfRec* __restrict__ rec = a.pf_rec;
+    int lo, hi;
+    pf_block(NP, B, G, lo, hi);
+    int j = -1, s = 0, end = 0, k0 = 0, k1 = 0, kb = 0, fb = 0;
+    int64_t rb = 0;
+    bool hex = false;
+    double imax = 0.0, inv_imax = 0.0;
+    float imaxf = 0.f, inv_imaxf = 0.f;
+    for (int k = lo + threadIdx.x; k < hi; k += blockDim.x) {
+        if (j < 0 || k >= k1) {  // the structure of peak k: [k0, k1) are its peaks
+            j = a.pf_pj[k];
+            s = list[j];
+            const int first = a.pf_voff[j];
+            end = a.pf_voff[j + 1];
+            k0 = a.pf_pst[first];
+            k1 = a.pf_pst[end];
+            kb = a.pf_kidx[k0];
+            fb = a.pf_fidx[k0];
+            rb = a.refl_off[s];
+            hex = a.geo[s].hex != 0;
+            const unsigned long long m = a.pf_smax[j];
+            if (FI) {
+                imaxf = __uint_as_float((uint32_t)m);
+                inv_imaxf = imaxf > 0.f ? 1.f / imaxf : 0.f;
+            } else {
+                imax = __longlong_as_double((long long)m);
+                inv_imax = imax > 0.0 ? 1.0 / imax : 0.0;
+            }
+        }
         if (k == k0) {
             a.npk[s] = a.pf_kidx[k1] - kb;
             a.nfm[s] = a.pf_fidx[k1] - fb;
         }
-        if (a.pf_kidx[k + 1] == a.pf_kidx[k]) continue;  // below the cutoff
+        const int ki = a.pf_kidx[k];
+        if (a.pf_kidx[k + 1] == ki) continue;  // below the cutoff
         const int i0 = a.g_pstart[k];
         int i1 = i0 + 1;
         while (i1 < end && !a.g_flag[i1]) i1++;
-        const int64_t o = rb + (a.pf_kidx[k] - kb);
-        a.st_q[o] = a.pf_rec[i0].q;
-        const unsigned long long m = a.pf_smax[j];
+        const int64_t o = rb + (ki - kb);
+        a.st_q[o] = rec[i0].q;
         if (FI) {
-            const float imaxf = __uint_as_float((uint32_t)m);
-            const float inv_imaxf = imaxf > 0.f ? 1.f / imaxf : 0.f;
             const float ps = ((const float*)a.g_psum)[k];
             ((float*)a.st_I)[o] = (a.scaled && imaxf > 0.f) ? (ps == imaxf ? 100.f : 100.f * (ps * inv_imaxf)) : ps;
         } else {
-            const double imax = __longlong_as_double((long long)m);
-            const double inv_imax = imax > 0.0 ? 1.0 / imax : 0.0;
             const double ps = a.g_psum[k];
             a.st_I[o] = (a.scaled && imax > 0.0) ? (ps == imax ? 100.0 : 100.0 * (ps * inv_imax)) : ps;
         }
         const int fo0 = a.pf_fidx[k] - fb;
         a.st_foff[o] = fo0;
         if (i1 - i0 == 1) {
-            const uint32_t rep = a.pf_rec[i0].key;
             const int64_t fo = rb + fo0;
-            a.st_key[fo] = rep;
+            a.st_key[fo] = rec[i0].key;
             a.st_mult[fo] = 2;
             continue;
         }
-        const bool hex = a.geo[s].hex != 0;
-        auto kf = [&](int i) { return a.pf_rec[i].key; };
+        auto kf = [&](int i) { return rec[i].key; };
         auto fkf = [&](int i) -> unsigned long long { return a.pf_sfk ? a.pf_sfk[i] : family_key(kf(i), hex); };
         for (int i = i0; i < i1; i++) {  // families, ranked by descending representative
             const unsigned long long fk = fkf(i);
@@ -560,7 +624,7 @@ __device__ void pf_fail(const PostArgs& a, int cls, int B, int G)
 // once and a grid-wide barrier separates the passes, so a batch without
 // structures in this class pays one launch, and a batch with them no launch gaps.
 template <bool FI>
-__global__ void __launch_bounds__(kPfThreads) k_pf_fused(const PostArgs a, int cls)
+__global__ void __launch_bounds__(kPfThreads, kPfCtasPerSm) k_pf_fused(const PostArgs a, int cls)
 {
     pdl_enter();
     if (*a.abort_flag) return;  // set before this launch: the same for every CTA
@@ -607,9 +671,9 @@ __global__ void __launch_bounds__(kPfThreads) k_pf_fused(const PostArgs a, int c
 template <bool FI>
 static void launch_flat_fi(const PostArgs& a, int cls, cudaStream_t st)
 {
-    // one CTA per SM (40 registers x 1024 threads fit), every CTA resident
+    // kPfCtasPerSm CTAs per SM (the launch bounds cap the registers so that they fit): every CTA resident
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(min(a.grid, kPfScanBlocksMax));
+    cfg.gridDim = dim3(min(a.grid * kPfCtasPerSm, kPfScanBlocksMax));
     cfg.blockDim = dim3(kPfThreads);
     cfg.stream = st;
     cudaLaunchAttribute at[1];
