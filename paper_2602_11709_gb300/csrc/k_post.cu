@@ -21,17 +21,26 @@
 
 namespace xrd {
 
-// Size classes (reflections per structure held in shared memory); the scan
-// kernel sorts structures into them with the same bounds.
+__host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
-__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
-
-size_t post_smem_bytes(int cap)
+__host__ __device__ constexpr size_t post_smem_of(size_t c)
 {
-    const size_t c = (size_t)cap;
     // q, key, perm (16 bit), bucket ends, flags, peak starts, peak sums, family counts
     return align16(c * 8) + align16(c * 4) + align16(c * 2) + align16((c + 1) * 4) + align16(c) + align16(c * 4) +
            align16(c * 8) + align16(c * 4);
+}
+
+size_t post_smem_bytes(int cap) { return post_smem_of((size_t)cap); }
+
+// CTAs per SM that the shared memory of a class allows (228 KB per SM; about
+// 2 KB more per CTA for the static arrays and the per-CTA reservation), at most
+// 2048 threads: the launch bounds ask the compiler to fit that many CTAs in the
+// register file too.
+__host__ __device__ constexpr int post_min_blocks(int cap, int nt)
+{
+    const int b = (int)((228u * 1024u) / (post_smem_of((size_t)cap) + 2048u));
+    const int t = 2048 / nt;
+    return b < 1 ? 1 : (b < t ? b : t);
 }
 
 static __device__ TTab g_ttab[kTabN + 1];
@@ -334,7 +343,7 @@ __device__ void post_structure(const PostArgs& a, int s, int64_t base, int n, co
 // variants also stage the intensities there, in the second half of the
 // peak-sum area (FP32 peak sums use the first half).
 template <int CAP, int NT, bool FI>
-__global__ void __launch_bounds__(NT) k_post(const PostArgs a, int cls)
+__global__ void __launch_bounds__(NT, post_min_blocks(CAP, NT)) k_post(const PostArgs a, int cls)
 {
     static_assert(CAP > 0, "the largest class runs as the flat passes");
     pdl_enter();
