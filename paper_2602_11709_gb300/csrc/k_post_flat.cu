@@ -2,8 +2,8 @@
 // sort by 2-theta, anchor merge, families, cutoff and scaling (Sec. 2, Sec. 3)
 // as flat passes over all of the class's reflections at once.
 //
-// One CTA per structure on global scratch leaves most SMs idle when a few
-// structures hold most of the reflections (256 cells of 20 000-190 000
+// One CTA per structure (on global scratch, beyond shared memory) would leave
+// most SMs idle when a few structures hold most of the reflections (256 cells of 20 000-190 000
 // reflections, or the single 50 A cell of Sec. 4.2 with 680 000). Here the
 // class's structures are laid end to end in one virtual index space (virtual
 // offsets voff[j] in class-list order), every step is a loop over that space

@@ -24,7 +24,8 @@ STAGES = ["prep", "atoms", "count", "scan", "emit", "structure_factor", "refine"
 XRD_FLAG_HEXAGONAL = 1  # bit of the per-structure flag word: families by Miller-Bravais indices
 # kernels xrd_pattern_batch launches per call: order, coef, atoms (a side stream), prep, count, scan, emit,
 # structure factor, re-evaluation of weak reflections (selection and evaluation, FP32 variants), post
-# (eight shared-memory size classes and the 13 flat passes of the largest), output scan, compaction
+# (eight shared-memory size classes and one cooperative kernel of flat passes for the largest), output scan,
+# compaction
 LAUNCHES_PER_BATCH = 21
 
 

@@ -455,7 +455,7 @@ def _largest_large_cells():
 @pytest.mark.parametrize("prec", ["fp32_phasefix", "fp32_phase64"])
 def test_large_largest_cells(gpu_lib, handle, prec):
     """Every peak of the 16 largest cells of the large workload (1100-2000 atoms, up to ~190 000
-    Friedel-unique reflections each, post-processing on global scratch) against the oracle."""
+    Friedel-unique reflections each, post-processing by the flat passes) against the oracle."""
     sub, o, ref = _largest_large_cells()
     got = gpu_lib.compute(sub, o, prec, handle=handle)
     assert got["sizes"]["max_refl"] > 6144  # the global-scratch size class
