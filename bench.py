@@ -95,7 +95,7 @@ def reduce_over_ranks(terms, structures, seconds, world, device="cpu"):
 # DRAM bytes (read + write) of one k_sf launch per (workload, tile, warps, runs): dram__bytes_read.sum +
 # dram__bytes_write.sum from one ncu capture of the current kernel on each timed shape (profiles/);
 # a shape without a capture of the current kernel reports null.
-SF_TRAFFIC_BYTES = {("mixed", 128, 1, 1): 1.66e9}
+SF_TRAFFIC_BYTES = {("mixed", 128, 1, 1): 1.81e9}
 N_SMS = 152
 SM_MAX_MHZ = 2070.0
 GRAD_WORKLOAD = ("grad: 512 seeded P1 cells, a,b,c U[3,15] A, angles U[60,120] deg, 8-128 atoms, Z U{1..83}, "
