@@ -361,6 +361,15 @@ int xrd_set_point_group(xrd_handle* h, const int32_t* ops, int n_ops);
  * Neither the order of the enumerated reflections nor the pattern changes with it. */
 int xrd_set_enum_threads(xrd_handle* h, int threads);
 
+/* Test hook of the bounded device-side wait. The flat post-processing passes of
+ * structures above 6144 reflections run as one cooperative kernel whose passes
+ * are separated by a grid-wide barrier; each wait there is bounded to about one
+ * second, after which that kernel's structures report XRD_ETIMEOUT (no peaks)
+ * and the call completes. extra > 0 makes the barrier wait for `extra` arrivals
+ * that never come, so that the bound is exercised on purpose; 0 (the default)
+ * restores normal operation. XRD_EINVAL for extra < 0 or > 1024. */
+int xrd_test_flat_barrier(xrd_handle* h, int extra);
+
 /*
  * CUDA graph of one xrd_pattern_batch call with exactly these arguments (the
  * device buffers are baked into the graph: replays read the batch's current

@@ -35,6 +35,7 @@ struct xrd_handle {
     int8_t* pg = nullptr;                // device [kMaxPgOps][9]: the point group of the family mode
     int npg = 0;                         // its operations (0: families by permutation and sign)
     int refine = 1;                      // re-evaluate weak reflections of the FP32 variants (xrd_set_refine)
+    int bar_extra = 0;                   // xrd_test_flat_barrier: arrivals the flat passes' barrier waits for in vain
 };
 
 namespace {
@@ -691,6 +692,7 @@ int xrd_pattern_batch(xrd_handle* h, const xrd_batch* b, const xrd_opts* o, cons
     pa.cls_cnt = ga.abort_flag + xrd::kFlagClsCnt;
     pa.cls_next = ga.abort_flag + xrd::kFlagClsNext;
     pa.pf_bar = ga.abort_flag + xrd::kFlagPfBar;
+    pa.pf_bar_extra = h->bar_extra;
     pa.atom_bad = ga.atom_bad;
     pa.status = out->status;
     pa.totals = out->totals;
@@ -799,6 +801,14 @@ int xrd_set_point_group(xrd_handle* h, const int32_t* ops, int n_ops)
     cudaError_t e = cudaMemcpy(h->pg, host, sizeof(host), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(h, e, "xrd_set_point_group: cudaMemcpy");
     h->npg = n_ops;
+    return XRD_OK;
+}
+
+int xrd_test_flat_barrier(xrd_handle* h, int extra)
+{
+    if (!h) return XRD_EINVAL;
+    if (extra < 0 || extra > 1024) return fail(h, XRD_EINVAL, "extra must be in 0..1024");
+    h->bar_extra = extra;
     return XRD_OK;
 }
 

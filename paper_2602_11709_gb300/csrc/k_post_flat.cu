@@ -52,8 +52,9 @@ __device__ __forceinline__ unsigned long long pf_now_ns()
 // are zero at the start of a batch. The last CTA to arrive clears the count and
 // advances the generation; the others wait for the generation to move, for at
 // most kPfWaitNs, or until a failure is posted. Returns false (every CTA, within
-// the time limit) once any wait has run out.
-__device__ bool pf_grid_sync(int* bar, int G)
+// the time limit) once any wait has run out. `extra` arrivals that never come
+// (a test of the bounded wait; 0 otherwise) make every wait run out.
+__device__ bool pf_grid_sync(int* bar, int G, int extra)
 {
     __shared__ int ok;
     __syncthreads();
@@ -63,7 +64,7 @@ __device__ bool pf_grid_sync(int* bar, int G)
         if (good) {
             const int gen = vb[1];
             __threadfence();
-            if (atomicAdd(&bar[0], 1) == G - 1) {
+            if (atomicAdd(&bar[0], 1) == G - 1 + extra) {
                 atomicExch(&bar[0], 0);
                 __threadfence();
                 atomicAdd(&bar[1], 1);
@@ -630,8 +631,9 @@ __global__ void __launch_bounds__(kPfThreads, kPfCtasPerSm) k_pf_fused(const Pos
     if (*a.abort_flag) return;  // set before this launch: the same for every CTA
     const int B = blockIdx.x, G = gridDim.x;
     int* bar = a.pf_bar;
+    const int extra = a.pf_bar_extra;
 #define PF_SYNC()                          \
-    if (!pf_grid_sync(bar, G)) {           \
+    if (!pf_grid_sync(bar, G, extra)) {    \
         pf_fail(a, cls, B, G);             \
         return;                            \
     }

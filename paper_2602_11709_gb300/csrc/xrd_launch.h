@@ -168,6 +168,7 @@ struct PostArgs {
     float l2h, l2l;  // lambda^2 / 4 as two floats (2-theta of the list)
     // the flat passes of the largest class (k_post_flat.cu)
     int* pf_bar;                   // flags[kFlagPfBar..+2]: grid barrier of the flat passes (zero at launch)
+    int pf_bar_extra;              // arrivals the barrier also waits for (a test of its bounded wait; 0)
     int* pf_voff;                  // [n_struct + 1] virtual offsets of the class's structures
     unsigned long long* pf_smax;   // [n_struct] bits of each structure's largest peak sum
     int* pf_scal;                  // [4]: reflections of the class (V), its peaks

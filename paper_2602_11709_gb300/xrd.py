@@ -77,7 +77,8 @@ EXPORTS = ["xrd_create", "xrd_destroy", "xrd_last_error", "xrd_query_sizes", "xr
            "xrd_set_profiling", "xrd_stage_times", "xrd_pattern_batch_noalloc", "xrd_pattern_broadened",
            "xrd_pattern_grad", "xrd_autotune", "xrd_set_sf_shape", "xrd_graph_create", "xrd_graph_launch",
            "xrd_graph_destroy", "xrd_work_counts", "xrd_set_enum_threads", "xrd_pattern_augmented",
-           "xrd_set_refine", "xrd_unit_rates", "xrd_reflection_counts", "xrd_set_point_group"]
+           "xrd_set_refine", "xrd_unit_rates", "xrd_reflection_counts", "xrd_set_point_group",
+           "xrd_test_flat_barrier"]
 
 _lib = None
 
@@ -130,6 +131,8 @@ def load(path: str = LIB_PATH):
     L.xrd_set_enum_threads.argtypes = [C.c_void_p, C.c_int]
     L.xrd_set_point_group.argtypes = [C.c_void_p, C.c_void_p, C.c_int]
     L.xrd_set_point_group.restype = C.c_int
+    L.xrd_test_flat_barrier.argtypes = [C.c_void_p, C.c_int]
+    L.xrd_test_flat_barrier.restype = C.c_int
     L.xrd_set_enum_threads.restype = C.c_int
     L.xrd_set_refine.argtypes = [C.c_void_p, C.c_int]
     L.xrd_set_refine.restype = C.c_int
@@ -589,6 +592,11 @@ class Handle:
             return
         arr = np.ascontiguousarray(np.asarray(ops, dtype=np.int32).reshape(-1, 3, 3))
         self._check(self.lib.xrd_set_point_group(self.h, arr.ctypes.data, int(arr.shape[0])))
+
+    def test_flat_barrier(self, extra: int):
+        """Test hook: the flat post passes' grid barrier waits for `extra` arrivals that never come,
+        so that its bounded wait runs out (those structures report XRD_ETIMEOUT); 0 restores it."""
+        self._check(self.lib.xrd_test_flat_barrier(self.h, int(extra)))
 
     def set_enum_threads(self, threads: int):
         self._check(self.lib.xrd_set_enum_threads(self.h, int(threads)))

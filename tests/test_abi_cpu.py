@@ -126,6 +126,7 @@ def test_null_handle_arguments(lib):
     assert lib.xrd_set_profiling(None, 1) == xrd.XRD_EINVAL
     assert lib.xrd_set_refine(None, 1) == xrd.XRD_EINVAL
     assert lib.xrd_set_point_group(None, None, 0) == xrd.XRD_EINVAL
+    assert lib.xrd_test_flat_barrier(None, 0) == xrd.XRD_EINVAL
     lib.xrd_destroy(None)
 
 
