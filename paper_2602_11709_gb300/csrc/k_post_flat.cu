@@ -673,9 +673,21 @@ __global__ void __launch_bounds__(kPfThreads, kPfCtasPerSm) k_pf_fused(const Pos
 template <bool FI>
 static void launch_flat_fi(const PostArgs& a, int cls, cudaStream_t st)
 {
-    // kPfCtasPerSm CTAs per SM (the launch bounds cap the registers so that they fit): every CTA resident
+    // kPfCtasPerSm CTAs per SM (the launch bounds cap the registers so that they fit), or fewer if the
+    // occupancy query says so: every CTA of the cooperative grid must be resident
+    static int per_sm_cache[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int per_sm = (dev >= 0 && dev < 64) ? per_sm_cache[dev] : 0;
+    if (per_sm < 1) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pf_fused<FI>, kPfThreads, 0) != cudaSuccess ||
+            per_sm < 1)
+            per_sm = 1;
+        per_sm = min(per_sm, kPfCtasPerSm);
+        if (dev >= 0 && dev < 64) per_sm_cache[dev] = per_sm;
+    }
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(min(a.grid * kPfCtasPerSm, kPfScanBlocksMax));
+    cfg.gridDim = dim3(min(a.grid * per_sm, kPfScanBlocksMax));
     cfg.blockDim = dim3(kPfThreads);
     cfg.stream = st;
     cudaLaunchAttribute at[1];
