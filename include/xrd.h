@@ -420,7 +420,7 @@ int xrd_stage_times(xrd_handle* h, float* ms, int n);
  *    where the library is loaded, called there or not. It stays reserved
  *    until the process exits.
  *  - Limit: the per-structure and per-atom arrays (about 250 bytes per
- *    structure and 120 bytes per atom) plus about 108 bytes per Friedel-unique
+ *    structure and 120 bytes per atom) plus about 105 bytes per Friedel-unique
  *    reflection must fit in 64 MiB. A batch whose per-structure and per-atom
  *    part does not fit is rejected on the host with XRD_ECAPACITY; one whose
  *    reflections do not fit is flagged on the device (status XRD_ECAPACITY for

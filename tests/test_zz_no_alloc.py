@@ -58,7 +58,7 @@ def test_noalloc_capacity_limits(gpu_lib):
     xrd = gpu_lib
     h = xrd.Handle(0)
     try:
-        # reflections beyond the fixed scratch (1.03 million of about 108 bytes each), outputs with
+        # reflections beyond the fixed scratch (1.03 million of about 105 bytes each), outputs with
         # room for every peak and family: the scratch alone is too small, flagged on the device for
         # every structure, and totals[0] gives the reflection count it would need
         b, o = synth.small()
