@@ -23,7 +23,6 @@ namespace xrd {
 
 constexpr int kGradThreads = 256;
 constexpr int kAtomChunkRefl = 1024;  // reflections staged per chunk in k_grad_atoms
-constexpr float kLn2 = 0.69314718055994531f;
 constexpr float kLog2e = 1.4426950408889634f;
 
 // ---------------------------------------------------------------- forward: broadened pattern
